@@ -1,0 +1,290 @@
+"""Block-structured level hierarchy with recursive time subcycling
+(Sec. 2 and 2.1, Fig. 2).
+
+* Level l has spacing dx_l = dx_0 / 2^l and step dt_l = dt_0 / 2^l (Eqs. 1-3).
+* Each level is a list of disjoint boxes (inclusive lo/hi in the level's index
+  space, aligned to and multiples of the blocking factor); only level 0 covers
+  the periodic domain.  Every box carries ``g`` ghost layers.
+* Ghost fill of a box (psi components, the only ones the stencil reads):
+  a ghost cell, wrapped periodically, that lies in a box of the same level is
+  copied from it; otherwise it is prolonged from the next coarser level with
+  the spatial weights of ``interp`` applied to coarse values interpolated in
+  time between the coarse states at the start and end of the coarse step
+  (fraction alpha of that step).
+* One RK4 step of level l fills ghosts before every stage at the stage time:
+  the fine sub-step i in {0, 1} of the coarse step has stage fractions
+  alpha = (i + c_s) / 2, c = (0, 1/2, 1/2, 1).
+* advance(l): keep the level's state as "old", take one RK4 step; if a finer
+  level exists, advance it twice, then synchronise: every coarse cell covered
+  by the finer level becomes the mean of its 8 children (all four fields).
+* eta: level 0 advances by repeated addition of dt_0; the finer level's
+  sub-step i starts at eta_parent_start + i * dt_l.
+
+Parity: the ingredients are pinned individually (stencil, rk4, interp,
+winding); the hierarchy itself has no closed form.  Pins here: a fine level
+covering the whole domain reproduces a uniform fine-lattice run bit for bit
+and restricts onto the coarse level exactly; a polynomial coarse field is
+prolonged exactly into fine ghosts -- tests/test_oracle_amr.py.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import interp, winding
+from .eom import EOMParams, rhs
+from .energy import energy_box
+from .stencil import laplacian_padded
+
+C_RK = (0.0, 0.5, 0.5, 1.0)
+A_RK = (0.0, 0.5, 0.5, 1.0)
+
+
+class Level:
+    def __init__(self, lev, boxes, n, dx, dt, g, bf):
+        self.lev, self.n, self.dx, self.dt, self.g, self.bf = lev, n, dx, dt, g, bf
+        self.boxes = [(tuple(int(v) for v in lo), tuple(int(v) for v in hi)) for lo, hi in boxes]
+        if n % bf:
+            raise ValueError("domain not a multiple of the blocking factor")
+        nb = n // bf
+        self.owner = -np.ones((nb, nb, nb), dtype=np.int64)
+        for b, (lo, hi) in enumerate(self.boxes):
+            for d in range(3):
+                if lo[d] % bf or (hi[d] + 1) % bf or lo[d] < 0 or hi[d] >= n or hi[d] < lo[d]:
+                    raise ValueError(f"box {b} not aligned to blocking factor / outside domain")
+            blk = self.owner[lo[2] // bf:(hi[2] + 1) // bf, lo[1] // bf:(hi[1] + 1) // bf,
+                             lo[0] // bf:(hi[0] + 1) // bf]
+            if (blk >= 0).any():
+                raise ValueError("boxes overlap")
+            blk[...] = b
+        self.data = [np.zeros((4,) + self.padded_shape(b)) for b in range(len(self.boxes))]
+        self.old = None
+        self.eta = None
+
+    def padded_shape(self, b):
+        lo, hi = self.boxes[b]
+        g = self.g
+        return (hi[2] - lo[2] + 1 + 2 * g, hi[1] - lo[1] + 1 + 2 * g, hi[0] - lo[0] + 1 + 2 * g)
+
+    def valid(self, b):
+        g = self.g
+        nz, ny, nx = (s - 2 * g for s in self.padded_shape(b))
+        return (slice(None), slice(g, g + nz), slice(g, g + ny), slice(g, g + nx))
+
+    def owners_of(self, kz, ky, kx):
+        """Box index owning (already wrapped) cells, -1 where uncovered."""
+        bf = self.bf
+        return self.owner[kz // bf, ky // bf, kx // bf]
+
+    def gather(self, arrays, comp, kz, ky, kx):
+        """Values of valid cells (wrapped indices) from per-box arrays."""
+        own = self.owners_of(kz, ky, kx)
+        if (own < 0).any():
+            raise ValueError("coarse stencil reaches outside the coarser level (nesting)")
+        out = np.empty(kz.shape)
+        g = self.g
+        for s in np.unique(own):
+            sel = own == s
+            lo = self.boxes[s][0]
+            out[sel] = arrays[s][comp][kz[sel] - lo[2] + g, ky[sel] - lo[1] + g, kx[sel] - lo[0] + g]
+        return out
+
+    def set_dense(self, fields):
+        """Fill valid cells from four dense arrays over the level domain."""
+        for b, (lo, hi) in enumerate(self.boxes):
+            v = self.valid(b)
+            for c in range(4):
+                self.data[b][c][v[1:]] = fields[c][lo[2]:hi[2] + 1, lo[1]:hi[1] + 1, lo[0]:hi[0] + 1]
+
+    def covered_mask(self, b, finer):
+        """True where a valid cell of box b is covered by the finer level."""
+        lo, hi = self.boxes[b]
+        shp = tuple(hi[d] - lo[d] + 1 for d in (2, 1, 0))
+        m = np.zeros(shp, dtype=bool)
+        if finer is None:
+            return m
+        for flo, fhi in finer.boxes:
+            clo = [flo[d] // 2 for d in range(3)]
+            chi = [(fhi[d] + 1) // 2 - 1 for d in range(3)]
+            ilo = [max(clo[d], lo[d]) for d in range(3)]
+            ihi = [min(chi[d], hi[d]) for d in range(3)]
+            if all(ilo[d] <= ihi[d] for d in range(3)):
+                m[ilo[2] - lo[2]:ihi[2] - lo[2] + 1, ilo[1] - lo[1]:ihi[1] - lo[1] + 1,
+                  ilo[0] - lo[0]:ihi[0] - lo[0] + 1] = True
+        return m
+
+
+def fill_ghosts(level: Level, arrays, coarse: Level | None, alpha: float, interp_type: int,
+                comps=(0, 1)):
+    """Fill the ghost layers of ``arrays`` (one padded array per box of
+    ``level``) for the given components; see the module docstring."""
+    g, n = level.g, level.n
+    for b, (lo, hi) in enumerate(level.boxes):
+        arr = arrays[b]
+        shp = level.padded_shape(b)
+        pz, py, px = np.indices(shp)
+        kz, ky, kx = pz + lo[2] - g, py + lo[1] - g, px + lo[0] - g
+        interior = ((pz >= g) & (pz < shp[0] - g) & (py >= g) & (py < shp[1] - g)
+                    & (px >= g) & (px < shp[2] - g))
+        gh = ~interior
+        gpz, gpy, gpx = pz[gh], py[gh], px[gh]
+        wz, wy, wx = kz[gh] % n, ky[gh] % n, kx[gh] % n
+        own = level.owners_of(wz, wy, wx)
+        for s in np.unique(own[own >= 0]):
+            sel = own == s
+            slo = level.boxes[s][0]
+            for c in comps:
+                arr[c][gpz[sel], gpy[sel], gpx[sel]] = arrays[s][c][
+                    wz[sel] - slo[2] + g, wy[sel] - slo[1] + g, wx[sel] - slo[0] + g]
+        sel = own < 0
+        if sel.any():
+            if coarse is None:
+                raise ValueError("uncovered ghost cell on a level without a coarser level")
+            nc = coarse.n
+            for c in comps:
+                def coarse_at(Kz, Ky, Kx, c=c):
+                    Kz, Ky, Kx = Kz % nc, Ky % nc, Kx % nc
+                    vo = coarse.gather(coarse.old, c, Kz, Ky, Kx)
+                    vn = coarse.gather(coarse.data, c, Kz, Ky, Kx)
+                    return interp.time_lerp(vo, vn, alpha)
+                arr[c][gpz[sel], gpy[sel], gpx[sel]] = interp.prolong_points(
+                    coarse_at, (wz[sel], wy[sel], wx[sel]), interp_type)
+
+
+def rhs_box(arr, g, dx, eta, p: EOMParams):
+    v = (slice(g, arr.shape[1] - g), slice(g, arr.shape[2] - g), slice(g, arr.shape[3] - g))
+    lap1 = laplacian_padded(arr[0], g, dx, p.order)
+    lap2 = laplacian_padded(arr[1], g, dx, p.order)
+    return np.stack(rhs(arr[0][v], arr[1][v], arr[2][v], arr[3][v], lap1, lap2, eta, p))
+
+
+class Hierarchy:
+    """Levels 0..L-1 with fixed (or externally regridded) boxes."""
+
+    def __init__(self, levels, params: EOMParams, interp_type: int = 4):
+        self.levels = levels
+        self.p = params
+        self.interp_type = interp_type
+        self.tag_log = []          # optional (lev, eta, [tags per box]) at stage 1
+        self.record_tags = False
+
+    def coarse_of(self, lev):
+        return self.levels[lev - 1] if lev > 0 else None
+
+    def rk4_level(self, lev, sub):
+        L = self.levels[lev]
+        C = self.coarse_of(lev)
+        g, dt, eta = L.g, L.dt, L.eta
+        y0 = [a.copy() for a in L.data]
+        Y = [a.copy() for a in y0]
+        ks = []
+        for s in range(4):
+            alpha = (sub + C_RK[s]) / 2.0
+            if s > 0:
+                for b in range(len(Y)):
+                    v = L.valid(b)
+                    Y[b][v] = y0[b][v] + (A_RK[s] * dt) * ks[s - 1][b]
+            fill_ghosts(L, Y, C, alpha, self.interp_type)
+            if s == 0 and self.record_tags:
+                self.tag_log.append((lev, eta, [winding.cell_tags_padded(a[0], a[1], g) for a in Y]))
+            ks.append([rhs_box(Y[b], g, L.dx, eta + C_RK[s] * dt, self.p) for b in range(len(Y))])
+        for b in range(len(Y)):
+            v = L.valid(b)
+            L.data[b][v] = y0[b][v] + (dt / 6.0) * (ks[0][b] + 2.0 * ks[1][b] + 2.0 * ks[2][b] + ks[3][b])
+
+    def restrict(self, fine_lev):
+        F = self.levels[fine_lev]
+        Cl = self.levels[fine_lev - 1]
+        gc = Cl.g
+        for b, (flo, fhi) in enumerate(F.boxes):
+            fv = F.data[b][F.valid(b)]
+            red = np.stack([interp.restrict_block(fv[c]) for c in range(4)])
+            clo = [flo[d] // 2 for d in range(3)]
+            nz, ny, nx = red.shape[1:]
+            kz, ky, kx = np.indices((nz, ny, nx))
+            kz, ky, kx = kz + clo[2], ky + clo[1], kx + clo[0]
+            own = Cl.owners_of(kz, ky, kx)
+            if (own < 0).any():
+                raise ValueError("fine level not covered by the coarse level")
+            for s in np.unique(own):
+                sel = own == s
+                slo = Cl.boxes[s][0]
+                for c in range(4):
+                    Cl.data[s][c][kz[sel] - slo[2] + gc, ky[sel] - slo[1] + gc,
+                                  kx[sel] - slo[0] + gc] = red[c][sel]
+
+    def advance(self, lev=0, sub=0, parent_eta=None):
+        L = self.levels[lev]
+        if lev > 0:
+            L.eta = parent_eta + sub * L.dt
+        eta_start = L.eta
+        L.old = [a.copy() for a in L.data]
+        self.rk4_level(lev, sub)
+        L.eta = eta_start + L.dt
+        if lev + 1 < len(self.levels):
+            for i in (0, 1):
+                self.advance(lev + 1, i, eta_start)
+            self.restrict(lev + 1)
+
+    def step(self):
+        """One coarse step (level 0 by dt_0, every finer level subcycled)."""
+        self.advance(0, 0)
+
+    # -- diagnostics at the synchronised time -------------------------------
+    def _filled(self, lev):
+        L = self.levels[lev]
+        arrs = [a.copy() for a in L.data]
+        C = self.coarse_of(lev)
+        if C is not None and C.old is None:
+            C.old = [a.copy() for a in C.data]
+        fill_ghosts(L, arrs, C, 1.0, self.interp_type)
+        return arrs
+
+    def tags(self, lev):
+        L = self.levels[lev]
+        arrs = self._filled(lev)
+        return [winding.cell_tags_padded(a[0], a[1], L.g) for a in arrs]
+
+    def energy(self):
+        """[kin, grad, pot, total, string_length] over the uncovered cells of
+        every level (each level at its own eta, equal after a coarse step)."""
+        K = G = P = S = 0.0
+        for lev, L in enumerate(self.levels):
+            arrs = self._filled(lev)
+            finer = self.levels[lev + 1] if lev + 1 < len(self.levels) else None
+            vol = L.dx ** 3
+            for b in range(len(L.boxes)):
+                unc = ~L.covered_mask(b, finer)
+                k, gr, po, nst = energy_box(arrs[b], L.g, L.dx, L.eta, self.p, uncovered=unc)
+                K += k * vol
+                G += gr * vol
+                P += po * vol
+                S += nst * L.dx
+        return np.array([K, G, P, K + G + P, S])
+
+
+def make_hierarchy(n0, dx0, dt0, g, bf, level_boxes, params: EOMParams, interp_type=4, eta0=0.1):
+    """level_boxes[l] = list of (lo, hi) for level l (level 0 usually the one
+    box covering the domain)."""
+    levels = []
+    for l, boxes in enumerate(level_boxes):
+        L = Level(l, boxes, n0 * 2 ** l, dx0 / 2 ** l, dt0 / 2 ** l, g, bf)
+        L.eta = eta0
+        levels.append(L)
+    return Hierarchy(levels, params, interp_type)
+
+
+def prolong_level_from_coarse(fine: Level, coarse: Level, interp_type: int, comps=(0, 1, 2, 3)):
+    """Initialise every valid cell of ``fine`` by prolongation of the coarse
+    level's current state (used to create refined levels from a coarse
+    initial state)."""
+    if coarse.old is None:
+        coarse.old = [a.copy() for a in coarse.data]
+    nc = coarse.n
+    for b, (lo, hi) in enumerate(fine.boxes):
+        kz, ky, kx = np.indices(tuple(hi[d] - lo[d] + 1 for d in (2, 1, 0)))
+        kz, ky, kx = kz + lo[2], ky + lo[1], kx + lo[0]
+        v = fine.valid(b)
+        for c in comps:
+            def coarse_at(Kz, Ky, Kx, c=c):
+                return coarse.gather(coarse.data, c, Kz % nc, Ky % nc, Kx % nc)
+            fine.data[b][c][v[1:]] = interp.prolong_points(coarse_at, (kz, ky, kx), interp_type)

@@ -1,0 +1,102 @@
+"""Pins of the oracle's level hierarchy (Sec. 2.1): subcycling of a fine
+level that covers the whole domain must reproduce a uniform fine run bit for
+bit and restrict exactly onto the coarse level; ghost cells prolonged from a
+polynomial coarse field must equal its exact fine cell averages."""
+import numpy as np
+import pytest
+
+from oracle import amr, interp, rk4
+from oracle.eom import EOMParams
+from paper_2404_02950_gb300 import inputs
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_full_cover_fine_level_equals_uniform_fine_run(order):
+    n0, dx0, dt0, g, bf = 8, 0.25, 1.0 / 16, 3, 4
+    p = EOMParams(order=order)
+    eta0 = 0.5                       # dyadic times keep eta sums exact
+    fine0 = inputs.random_snapshot(16, seed=4, amp=0.8)
+    coarse0 = [interp.restrict_block(f) for f in fine0]
+    h = amr.make_hierarchy(n0, dx0, dt0, g, bf,
+                           [[((0, 0, 0), (7, 7, 7))],
+                            [((0, 0, 0), (7, 15, 15)), ((8, 0, 0), (15, 7, 15)),
+                             ((8, 8, 0), (15, 15, 15))]],
+                           p, interp_type=4, eta0=eta0)
+    h.levels[0].set_dense(coarse0)
+    h.levels[1].set_dense(fine0)
+    nsteps = 2
+    for _ in range(nsteps):
+        h.step()
+    ref, _ = rk4.evolve_periodic(fine0, eta0, dt0 / 2, dx0 / 2, 2 * nsteps, p)
+    L1 = h.levels[1]
+    for b, (lo, hi) in enumerate(L1.boxes):
+        got = L1.data[b][L1.valid(b)]
+        for c in range(4):
+            exp = ref[c][lo[2]:hi[2] + 1, lo[1]:hi[1] + 1, lo[0]:hi[0] + 1]
+            assert np.array_equal(got[c], exp)
+    L0 = h.levels[0]
+    got0 = L0.data[0][L0.valid(0)]
+    for c in range(4):
+        assert np.array_equal(got0[c], interp.restrict_block(ref[c]))
+    assert L0.eta == L1.eta == eta0 + nsteps * dt0
+
+
+def _avg_poly(coef, lo, hi):
+    return sum(c * (hi ** (p + 1) - lo ** (p + 1)) / ((p + 1) * (hi - lo)) for p, c in enumerate(coef))
+
+
+def test_ghost_prolongation_exact_for_polynomials_with_time_interp():
+    n0, g, bf = 16, 3, 4
+    p = EOMParams(order=6)
+    h = amr.make_hierarchy(n0, 1.0, 0.25, g, bf,
+                           [[((0, 0, 0), (15, 15, 15))], [((12, 8, 12), (19, 23, 19))]],
+                           p, interp_type=4, eta0=1.0)
+    rng = np.random.default_rng(7)
+    polys = [[[float(v) / 8 for v in rng.integers(-8, 8, size=5)] for _ in range(3)] for _ in range(2)]
+
+    def coarse_avgs(P):
+        px, py, pz = P
+        ax = np.arange(n0, dtype=np.float64)
+        ax_ = [_avg_poly(px, i - 0.5, i + 0.5) for i in ax]
+        ay_ = [_avg_poly(py, i - 0.5, i + 0.5) for i in ax]
+        az_ = [_avg_poly(pz, i - 0.5, i + 0.5) for i in ax]
+        return np.einsum("k,j,i->kji", az_, ay_, ax_)
+
+    C0 = h.levels[0]
+    old = coarse_avgs(polys[0])
+    new = coarse_avgs(polys[1])
+    C0.set_dense([old, old, old, old])
+    C0.old = [a.copy() for a in C0.data]
+    C0.set_dense([new, new, new, new])
+    alpha = 0.25
+    F = h.levels[1]
+    arrs = [a.copy() for a in F.data]
+    amr.fill_ghosts(F, arrs, C0, alpha, 4)
+    lo, hi = F.boxes[0]
+    a = arrs[0]
+    checked = 0
+    for pz_ in range(a.shape[1]):
+        for py_ in range(a.shape[2]):
+            for px_ in range(a.shape[3]):
+                if g <= pz_ < a.shape[1] - g and g <= py_ < a.shape[2] - g and g <= px_ < a.shape[3] - g:
+                    continue
+                f = (px_ + lo[0] - g, py_ + lo[1] - g, pz_ + lo[2] - g)
+                exp = 0.0
+                for wgt, P in ((1 - alpha, polys[0]), (alpha, polys[1])):
+                    e = 1.0
+                    for d in range(3):
+                        e *= _avg_poly(P[d], f[d] / 2 - 0.5, f[d] / 2)
+                    exp += wgt * e
+                assert abs(a[0][pz_, py_, px_] - exp) <= 1e-12 * max(1.0, abs(exp))
+                checked += 1
+    assert checked == a.shape[1] * a.shape[2] * a.shape[3] - 8 * 16 * 8
+
+
+def test_nesting_violation_raises():
+    h = amr.make_hierarchy(8, 1.0, 0.25, 3, 4,
+                           [[((0, 0, 0), (3, 7, 7))], [((0, 0, 0), (3, 3, 3))]],
+                           EOMParams(), interp_type=4, eta0=1.0)
+    arrs = [a.copy() for a in h.levels[1].data]
+    h.levels[0].old = h.levels[0].data
+    with pytest.raises(ValueError):
+        amr.fill_ghosts(h.levels[1], arrs, h.levels[0], 0.0, 4)
