@@ -1,0 +1,333 @@
+"""Benchmark of the fused RK4 hot path on GB300.
+
+Default workload: the uniform 512^3 periodic lattice (6th-order Laplacian,
+classic RK4, Gaussian random initial field with k_max = pi/(8 dx), dx = 1/8,
+dt = dx/4, eta from 0.1) with winding tags and energy partials fused into
+stage 1.  The headline ``value`` is the FP32 + Kahan form in cell-updates/s
+(one update = one valid cell advanced one full RK4 step); the FP64 form is
+timed on the same field and reported under ``fp64_plain``.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one process per GPU) every rank advances its own
+replica (the path needs no exchange on one level): value = all ranks'
+updates / max-over-ranks time, scaling "weak".  ``--impl reference`` times
+the CPU FP64 oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_CELLS = 512
+DX = 0.125
+DT = DX / 4
+ETA0 = 0.1
+ORDER = 6
+KAHAN_VALUES = 76          # field values moved per cell-update, FP32 + Kahan (fused schedule)
+F64_VALUES = 68            # FP64
+WORKLOAD = ("uniform 512^3 periodic lattice, 6th-order Laplacian, classic RK4, Gaussian init "
+            "k_max=pi/(8dx), dx=1/8, dt=dx/4, eta0=0.1, tags+energy fused in stage 1")
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _stage_traffic():
+    """DRAM bytes per stage-kernel launch from the committed ncu summary, if
+    it was taken on the current kernel source (else None)."""
+    src = os.path.join(ROOT, "paper_2404_02950_gb300", "csrc", "stage.cu")
+    f = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(f):
+        return None
+    d = json.load(open(f))
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    e = d.get("stage_kernel_f32_g3")
+    if e and e.get("source_sha") == h:
+        return e.get("bytes_per_launch")
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--id={self.gpu_index}",
+               "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+               "--format=csv,noheader,nounits", "-lms", "100"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _gpu_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids) and ids[local_rank].isdigit():
+            return int(ids[local_rank])
+    return local_rank
+
+
+def cpu_oracle_sample(budget_s=12.0, n=96):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the workload:
+    an n^3 periodic lattice with the same dx, dt, order and init recipe."""
+    from oracle import rk4
+    from oracle.eom import EOMParams
+    from paper_2404_02950_gb300 import inputs
+    y = inputs.gaussian_field(n, n / 16.0, seed=0)
+    p = EOMParams(order=ORDER)
+    eta = ETA0
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        y = rk4.rk4_step_periodic(y, eta, DT, DX, p)
+        eta += DT
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or steps >= 50:
+            break
+    return {"value": n ** 3 * steps / el, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} RK4 step(s) of a {n}^3 periodic lattice (same dx, dt, order 6, init recipe), "
+                      f"numpy FP64, {el:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    per_step = []
+    base = None
+    for _ in range(args.warmup + args.steps):
+        r = cpu_oracle_sample(budget_s=max(2.0, 20.0 / max(1, args.steps + args.warmup)), n=64)
+        per_step.append(r)
+        base = r
+    vals = [r["value"] for r in per_step[args.warmup:]]
+    v = float(np.mean(vals))
+    line = {"metric": "cell-updates/s (one valid cell advanced one full RK4 step)", "value": v,
+            "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 64 ** 3 / v * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "64^3 crop of the same recipe"},
+            "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": base["sample"]},
+            "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _time_form(slh, torch, prec, y0_dense, n, K, W, dist, flags):
+    """Warm up, then time K steps of one precision; returns a dict."""
+    h = slh.Hierarchy(n, DX, nghost=3, bf=16, prec=prec, max_levels=1)
+    boxes = [((0, 0, 0), (n - 1, n - 1, n - 1))]
+    h.init_level(0, boxes)
+    h.set_state(0, y0_dense.astype(h.np_dtype))
+    h.set_eta(ETA0)
+    p = slh.EOMParams(order=ORDER)
+    for _ in range(W):
+        h.advance(DT, p, flags=flags)
+    h.sync()
+    h.profile(True, True)
+    stream = h.stream
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(K):
+        h.advance(DT, p, flags=flags)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    stage = h.profile_read(slh.SLH_PROF_STAGE)
+    ghost = h.profile_read(slh.SLH_PROF_GHOST)
+    tim = h.profile_read(slh.SLH_PROF_TIME)
+    h.profile(False, True)
+    E = h.reduce_energy(p, mode=1)
+    out = dict(ms=ms, stage_ms=stage[0], stage_launches=stage[1], stage_bytes=stage[2],
+               ghost_ms=ghost[0], ghost_launches=ghost[1], time_launches=tim[1], energy=E.tolist())
+    return h, out
+
+
+def run_ours(args, rank, world, local_rank, dist):
+    import torch
+    import paper_2404_02950_gb300 as slh
+    from paper_2404_02950_gb300 import inputs
+    if not os.path.exists(slh.LIB_PATH):
+        from paper_2404_02950_gb300 import build
+        build.build()
+    torch.cuda.set_device(local_rank)
+    n, K, W = N_CELLS, args.steps, args.warmup
+    y0 = inputs.gaussian_field(n, n / 16.0, seed=rank)
+    boxes = [((0, 0, 0), (n - 1, n - 1, n - 1))]
+    dense = slh.dense_from_boxes(y0, boxes)
+    del y0
+    flags = slh.SLH_FUSE_ENERGY | slh.SLH_USE_GRAPH * 0
+    peak, peak_kind = _peaks()
+
+    # FP32 + Kahan (headline), with clock sampling over its timed region
+    with ClockSampler(_gpu_index(local_rank)) as clk:
+        h32, r32 = _time_form(slh, torch, "f32", dense, n, K, W, dist, flags)
+    clocks = clk.summary()
+
+    # end to end through the C ABI with host buffers: upload the step's input
+    # from pinned memory, advance, read the step's energy back
+    pinned = torch.from_numpy(dense.astype(np.float32)).pin_memory()
+    p = slh.EOMParams(order=ORDER)
+    h32.set_state(0, pinned)
+    h32.advance(DT, p, flags=flags)
+    h32.reduce_energy(p, mode=1)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        h32.set_state(0, pinned)
+        h32.advance(DT, p, flags=flags)
+        h32.reduce_energy(p, mode=1)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    h2d = pinned.numel() * 4
+    h32.close()
+    del h32, pinned
+    torch.cuda.empty_cache()
+
+    # FP64 plain on the same field
+    h64, r64 = _time_form(slh, torch, "f64", dense, n, K, W, dist, flags)
+    h64.close()
+    del h64
+    torch.cuda.empty_cache()
+
+    ms = r32["ms"]
+    e2e_ms = e2e_s * 1e3
+    if dist is not None:
+        t = torch.tensor([ms, e2e_ms, r64["ms"]], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_ms, ms64 = (float(v) for v in t.tolist())
+    else:
+        ms64 = r64["ms"]
+    cells = float(n) ** 3
+    value = world * cells * K / (ms / 1e3)
+    launches = r32["stage_launches"] + r32["ghost_launches"] + r32["time_launches"]
+    achieved = r32["stage_bytes"] / (r32["stage_ms"] / 1e3) / 1e9
+    ach64 = r64["stage_bytes"] / (r64["stage_ms"] / 1e3) / 1e9
+    if rank != 0:
+        return
+    line = {
+        "metric": "cell-updates/s (one valid cell advanced one full RK4 step)",
+        "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": n ** 3, "order": ORDER, "precision": "FP32 + Kahan",
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (10.9 GB of level buffers)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": _stage_traffic(),
+                     "kernel": "stage_kernel<float,3,32,16>", "peak_kind": peak_kind,
+                     "alg_bytes_per_cell_update": KAHAN_VALUES * 4},
+        "fp64_plain": {"value": world * cells * K / (ms64 / 1e3), "unit": "cell-updates/s",
+                       "ms_per_step": ms64 / K, "stage_achieved_gbs": ach64,
+                       "hbm_frac": ach64 / peak, "alg_bytes_per_cell_update": F64_VALUES * 8},
+        "stage_share": r32["stage_ms"] / ms,
+        "energy_f32": r32["energy"], "energy_f64": r64["energy"],
+        "e2e": {"value": world * cells * K / (e2e_ms / 1e3), "unit": "cell-updates/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4 * 8},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1:
+        line["cpu_baseline"] = cpu_oracle_sample()
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(local_rank)
+        td.init_process_group("nccl")
+        dist = td
+    run_ours(args, rank, world, local_rank, dist)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,264 @@
+/*
+ * slh.h -- C ABI of the GB300 AMR axion-string stepper.
+ *
+ * The library advances the complex scalar psi = psi1 + i psi2 and its momenta
+ * Pi1, Pi2 of arXiv:2404.02950 (sledgehamr) Sec. 3.1 on a block-structured
+ * hierarchy of periodic levels (Sec. 2): ghost-padded boxes, refinement
+ * ratio 2, dt_l = dt_0 / 2^l (Eqs. 1-3), recursive time subcycling with
+ * spatial + temporal ghost interpolation and fine-to-coarse averaging at
+ * synchronisation (Sec. 2.1, Fig. 2), classic RK4 (integrator type 4 of the
+ * "integrator" table), string-winding refinement tags (the problem-specific
+ * tagging hook of Sec. 4.2) and Berger-Rigoutsos style regridding
+ * (Sec. 2.2-2.3).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Status: every function returns slh_status; 0 is success, negative values
+ *    are the SLH_ERR_* codes below.  slh_last_error() returns a thread-local
+ *    message describing the last failure.  No C++ exception crosses the ABI.
+ *  - Device-side failures (a bounded wait that gave up, a consistency check
+ *    inside a kernel) are latched in a device word; the next synchronising
+ *    call (slh_sync, slh_reduce_energy, slh_tag, slh_get_state to host)
+ *    returns them.  Kernels never trap.
+ *  - Streams: every call that launches work is asynchronous on the stream
+ *    given to slh_create (a cudaStream_t passed as void*), except where noted.
+ *  - Ownership: field buffers are allocated by the caller (e.g. PyTorch) and
+ *    passed as device pointers; the library never frees them and never
+ *    retains them past slh_init_level of the same level or slh_destroy.
+ *    The library owns only metadata (box tables, block maps, work lists,
+ *    reduction partials, CUDA graphs), released by slh_destroy.
+ *  - Layout: arrays are x fastest, then y, then z.  A box (slh_box) holds
+ *    inclusive lo/hi cell indices in its level's index space; boxes of a
+ *    level are disjoint, multiples of and aligned to the blocking factor.
+ *    In device buffers each box is stored component by component
+ *    (psi1, psi2, Pi1, Pi2) with nghost ghost layers in y and z and a
+ *    16-byte aligned x padding; slh_level_layout reports the offsets.
+ *    "Dense" host/device arrays (slh_set_state / slh_get_state, tags) hold
+ *    only valid cells: [box][component][z][y][x] with boxes in list order.
+ */
+#ifndef SLH_H
+#define SLH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t slh_status;
+
+#define SLH_OK 0
+#define SLH_ERR_INVALID_ARG (-1)  /* null pointer, bad enum, inconsistent sizes */
+#define SLH_ERR_OUT_OF_RANGE (-2) /* box outside the domain, level index, capacity */
+#define SLH_ERR_CUDA (-3)         /* a CUDA runtime call failed */
+#define SLH_ERR_TIMEOUT (-4)      /* a bounded device wait gave up */
+#define SLH_ERR_NOMEM (-5)        /* metadata allocation failed */
+#define SLH_ERR_DEVICE (-6)       /* a device-side consistency check failed */
+#define SLH_ERR_STATE (-7)        /* call out of order (level not initialised ...) */
+
+/* Storage / arithmetic precision of the fields. */
+#define SLH_F64 0        /* FP64 fields, FP64 arithmetic */
+#define SLH_F32_KAHAN 2  /* FP32 fields and arithmetic, Kahan-compensated final
+                            RK update; FP64 only for eta, its coefficients and
+                            the reductions */
+
+/* Buffers of one level (device pointers handed to slh_init_level). */
+#define SLH_BUF_Y 0      /* state y_n (rotates with SLH_BUF_YB every step) */
+#define SLH_BUF_YA 1     /* RK stage value */
+#define SLH_BUF_YB 2     /* RK stage value / the level's previous state */
+#define SLH_BUF_D 3      /* RK increment accumulator */
+#define SLH_BUF_C 4      /* Kahan compensation (SLH_F32_KAHAN only, else NULL) */
+#define SLH_NBUF 5
+
+/* slh_rk_step / slh_advance flags */
+#define SLH_FUSE_TAG 1u     /* stage 1 also writes the winding tags of y_n */
+#define SLH_FUSE_ENERGY 2u  /* stage 1 also accumulates the energy of y_n */
+#define SLH_USE_GRAPH 4u    /* slh_advance: replay a captured CUDA graph */
+
+/* slh_fill_ghosts modes */
+#define SLH_GHOSTS 0     /* fill psi ghosts of the level's state */
+#define SLH_RESTRICT 1   /* average the level onto the next coarser one
+                            (covered cells, all four fields), then refill
+                            this level's psi ghosts */
+
+/* Profiling counters (slh_profile_read kinds) */
+#define SLH_PROF_STAGE 0
+#define SLH_PROF_GHOST 1
+#define SLH_PROF_RESTRICT 2
+#define SLH_PROF_DIAG 3
+#define SLH_PROF_TIME 4
+#define SLH_PROF_NKINDS 5
+
+typedef struct {
+  int32_t lo[3];
+  int32_t hi[3];
+} slh_box;
+
+/* Coefficients of the equations of motion (Sec. 3.1, Eqs. EOM1-EOM2):
+ *   psi_i' = Pi_i
+ *   Pi_i'  = -c_fric Pi_i + lap psi_i - psi_i (c_pot (psi1^2+psi2^2-1) + a)
+ * with c_fric = 2/eta (friction = 1) or 0, c_pot = lambda eta^eta_power
+ * (eta_power 2 as in the paper, 0 freezes it), the Laplacian of accuracy
+ * lap_order in {2,4,6} (the 7/13/19-point stencils of App. A, ghost width
+ * lap_order/2), and ghost prolongation interp_type in {0,2,4} (the
+ * "interpolation_type" entry of the "amr" table; 4 = quartic conservative). */
+typedef struct {
+  double lambda;
+  double a;
+  int32_t friction;
+  int32_t eta_power;
+  int32_t lap_order;
+  int32_t interp_type;
+} slh_eom_params;
+
+typedef struct slh_ctx slh_ctx;
+
+/* Message of the last failure on this thread ("" if none). */
+const char* slh_last_error(void);
+
+/* Create a hierarchy whose level 0 spans n0^3 cells of spacing dx0 on a
+ * periodic domain.  nghost in [1,4] ghost layers (>= lap_order/2, and >= 2
+ * for quartic prolongation), blocking_factor a power of two >= 2 dividing
+ * n0, prec SLH_F64 or SLH_F32_KAHAN, max_levels in [1,8], stream a
+ * cudaStream_t (NULL = legacy default stream).  Allocates metadata only.
+ * Errors: INVALID_ARG, NOMEM, CUDA. */
+slh_status slh_create(slh_ctx** ctx, int32_t n0, double dx0, int32_t nghost,
+                      int32_t blocking_factor, int32_t prec, int32_t max_levels,
+                      void* stream);
+
+/* Release the metadata of ctx (field buffers stay with the caller). */
+void slh_destroy(slh_ctx* ctx);
+
+/* Element counts of one level buffer for the given boxes, without a
+ * context.  box_offsets (nboxes entries, may be NULL) receives each box's
+ * element offset; box_geom (4*nboxes, may be NULL) receives pitch (x row
+ * length incl. padding), padded ny, padded nz and the component stride in
+ * elements.  The valid cell (x,y,z) of box b, component c, sits at
+ *   off_b + c*cstride_b + ((z-lo_z+nghost)*pny_b + (y-lo_y+nghost))*pitch_b
+ *         + (x-lo_x+4).
+ * *total_elems receives the buffer length in elements; *nvalid the number
+ * of valid cells over all boxes.  Errors: INVALID_ARG. */
+slh_status slh_level_layout(int32_t nghost, const slh_box* boxes, int32_t nboxes,
+                            int64_t* box_offsets, int64_t* box_geom,
+                            int64_t* total_elems, int64_t* nvalid);
+
+/* Define level lev (0 <= lev < max_levels; levels are defined in order,
+ * redefining a level drops the finer ones) with its boxes in the level's
+ * index space (domain n0*2^lev).  bufs[SLH_NBUF] are caller-owned device
+ * buffers of total_elems elements of the context precision (bufs[SLH_BUF_C]
+ * NULL unless SLH_F32_KAHAN); tags_dev, if not NULL, holds nvalid bytes for
+ * fused tags.  Level 0 must cover the domain; level lev>0 must lie inside
+ * level lev-1 with a gap of at least one block of blocking_factor/2 cells of
+ * lev-1 (nesting, Sec. 2.1).  Ghost cells and the Kahan buffer are zeroed.
+ * Errors: INVALID_ARG, OUT_OF_RANGE, NOMEM, CUDA. */
+slh_status slh_init_level(slh_ctx* ctx, int32_t lev, const slh_box* boxes, int32_t nboxes,
+                          void* const* bufs, uint8_t* tags_dev);
+
+/* Copy the four fields of level lev from / to a dense valid-cell array
+ * ([box][comp][z][y][x], context precision).  src/dst on the host
+ * (is_host = 1, ideally pinned) or the device.  slh_set_state also sets the
+ * level's previous state equal to it and zeroes the Kahan compensation.
+ * slh_get_state to host synchronises.  Errors: INVALID_ARG, STATE, CUDA. */
+slh_status slh_set_state(slh_ctx* ctx, int32_t lev, const void* src, int32_t src_is_host);
+slh_status slh_get_state(slh_ctx* ctx, int32_t lev, void* dst, int32_t dst_is_host);
+
+/* Set the conformal time eta of every level (kept in FP64 on the device). */
+slh_status slh_set_eta(slh_ctx* ctx, double eta);
+/* Read eta of level lev (synchronises). */
+slh_status slh_get_eta(slh_ctx* ctx, int32_t lev, double* eta);
+
+/* One classic RK4 step (Tab. "integrator", type 4) of level lev by
+ * dt_lev = dt0 / 2^lev.  For lev > 0, sub in {0,1} is the sub-step within
+ * the coarser level's step: the level starts at eta_coarse_start +
+ * sub*dt_lev and each stage fills psi ghosts from the coarser level at time
+ * fraction (sub + c_s)/2, c = (0, 1/2, 1/2, 1) (Sec. 2.1).  Before each
+ * stage the ghost fill of level lev runs; the four fused stage kernels then
+ * compute the RHS of Sec. 3.1 with the stage-time coefficients.  flags:
+ * SLH_FUSE_TAG (tags of y_n into the level's tags_dev), SLH_FUSE_ENERGY
+ * (energy partials of y_n, read with slh_reduce_energy mode 1).
+ * Errors: INVALID_ARG, STATE, CUDA. */
+slh_status slh_rk_step(slh_ctx* ctx, int32_t lev, int32_t sub, double dt0,
+                       const slh_eom_params* p, uint32_t flags);
+
+/* One coarse step of the whole hierarchy: the Berger-Oliger recursion of
+ * Sec. 2.1 / Fig. 2 (level l one step, level l+1 twice, then
+ * SLH_RESTRICT of l+1 onto l).  flags as slh_rk_step plus SLH_USE_GRAPH
+ * (capture the step into a CUDA graph on first use and replay it; the
+ * graph is rebuilt when a level or the parameters change).
+ * Errors: INVALID_ARG, STATE, CUDA. */
+slh_status slh_advance(slh_ctx* ctx, double dt0, const slh_eom_params* p, uint32_t flags);
+
+/* Ghost fill / synchronisation of level lev (Sec. 2.1).  mode SLH_GHOSTS:
+ * psi ghosts of the level's state from its own boxes (periodic wrap) and,
+ * where uncovered, by ratio-2 prolongation (interp_type 0/2/4) of the
+ * coarser level interpolated in time at fraction alpha in [0,1] between its
+ * previous and current state.  mode SLH_RESTRICT (lev >= 1): every cell of
+ * lev-1 covered by lev becomes the mean of its 8 children (sums in FP64),
+ * then lev's ghosts are refilled at alpha = 1.  Errors: INVALID_ARG, STATE,
+ * CUDA. */
+slh_status slh_fill_ghosts(slh_ctx* ctx, int32_t lev, double alpha, int32_t interp_type,
+                           int32_t mode);
+
+/* String-winding tags of level lev's state (rule: a cell is tagged when one
+ * of the 12 plaquettes it is a corner of has nonzero winding; plaquette
+ * winding counted from the signs of Im psi and of the cross products of
+ * neighbouring corners, in FP64).  Ghosts are filled first (alpha = 1).
+ * tags_dev: nvalid bytes (dense valid-cell layout) written 0/1.
+ * *n_tagged_host (may be NULL) receives the count (synchronises).
+ * Errors: INVALID_ARG, STATE, CUDA, and latched device errors. */
+slh_status slh_tag(slh_ctx* ctx, int32_t lev, uint8_t* tags_dev, int64_t* n_tagged_host);
+
+/* Block mask for regridding from level lev: the tags of lev, grown by
+ * n_error_buf cells (cube, periodic, across boxes), coarsened to blocks of
+ * blocking_factor/2 cells: mask_host[(bz*nb + by)*nb + bx] = 1 when the
+ * grown tag set meets block (bx,by,bz), nb = (n0*2^lev)/(blocking_factor/2).
+ * Synchronises.  Errors: INVALID_ARG, STATE, CUDA. */
+slh_status slh_tag_blocks(slh_ctx* ctx, int32_t lev, int32_t n_error_buf, uint8_t* mask_host);
+
+/* Host-only, deterministic regrid: dense tags over a level's whole index
+ * domain dims[3] (x,y,z; uint8, x fastest) -> boxes of the next finer level
+ * (Sec. 2.2-2.3): grow tags by n_error_buf (cube, periodic), coarsen to
+ * blocks of blocking_factor/2 cells, keep blocks inside the parent boxes
+ * eroded by one block (parent NULL / nparent 0: the periodic domain), and
+ * cluster Berger-Rigoutsos style: accept a box when 10*tags >= 7*volume,
+ * sides <= max_box fine cells and inside the allowed blocks; else cut at the
+ * zero-signature plane nearest the centre, else at the strongest sign change
+ * of the signature's second difference, else halve the longest side (ties:
+ * lowest axis x<y<z, then lowest plane).  Output boxes are in the finer
+ * level's cells, sorted by (lo_z, lo_y, lo_x).  cap = capacity of out.
+ * Errors: INVALID_ARG, OUT_OF_RANGE (cap too small; *nout = needed). */
+slh_status slh_regrid_boxes(const uint8_t* tags_host, const int32_t dims[3],
+                            int32_t blocking_factor, int32_t n_error_buf, int32_t max_box,
+                            const slh_box* parent, int32_t nparent, slh_box* out, int32_t cap,
+                            int32_t* nout);
+
+/* Energy and string length of the hierarchy over the cells not covered by
+ * a finer level, each level at its own eta:
+ *   out[0] = sum 1/2 (Pi1^2 + Pi2^2) dx^3
+ *   out[1] = sum -1/2 (psi1 L psi1 + psi2 L psi2) dx^3   (L = FD Laplacian)
+ *   out[2] = sum [c_pot/4 (|psi|^2-1)^2 + a/2 |psi|^2] dx^3
+ *   out[3] = out[0] + out[1] + out[2]
+ *   out[4] = (number of plaquettes with nonzero winding) dx
+ * mode 0: compute now (fills ghosts at alpha = 1 first).  mode 1: return the
+ * partials fused into the last SLH_FUSE_ENERGY stage 1 (energy of the state
+ * at the start of that step; single level only).  FP64 accumulation in a
+ * fixed order (bit-reproducible).  Synchronises.
+ * Errors: INVALID_ARG, STATE, CUDA, and latched device errors. */
+slh_status slh_reduce_energy(slh_ctx* ctx, const slh_eom_params* p, int32_t mode, double out[5]);
+
+/* Wait for the stream and return any latched device error (then clear it). */
+slh_status slh_sync(slh_ctx* ctx);
+
+/* Profiling: when enabled, CUDA events bracket every launch and the device
+ * time per kind (SLH_PROF_*) is accumulated; slh_profile_read synchronises
+ * and returns the total milliseconds, the number of launches and the
+ * algorithmic bytes those launches moved (field values read + written per
+ * valid cell, ghost and halo re-reads excluded).  enable 0/1; reset clears. */
+slh_status slh_profile(slh_ctx* ctx, int32_t enable, int32_t reset);
+slh_status slh_profile_read(slh_ctx* ctx, int32_t kind, double* ms, int64_t* launches,
+                            double* alg_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SLH_H */

@@ -1,1 +1,323 @@
-"""GB300-native AMR axion-string stepper (placeholder; binding added with the library)."""
+"""GB300-native AMR axion-string stepper (arXiv:2404.02950, sledgehamr).
+
+Thin Python binding of the C ABI declared in ``include/slh.h``: every
+function below marshals arguments and calls the CUDA library
+``lib/libslh.so``; every step of the computation runs in its kernels.
+PyTorch provides device memory (the level buffers) and the CUDA stream.
+There is no CPU fallback: a missing library raises.
+
+Low-level names mirror the ABI (``slh_create``, ``slh_init_level``,
+``slh_rk_step``, ``slh_advance``, ``slh_tag``, ``slh_tag_blocks``,
+``slh_fill_ghosts``, ``slh_regrid_boxes``, ``slh_reduce_energy`` ...);
+``Hierarchy`` bundles a context with the torch buffers it needs.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libslh.so")
+
+SLH_OK = 0
+SLH_F64 = 0
+SLH_F32_KAHAN = 2
+SLH_NBUF = 5
+SLH_BUF_Y, SLH_BUF_YA, SLH_BUF_YB, SLH_BUF_D, SLH_BUF_C = range(5)
+SLH_FUSE_TAG = 1
+SLH_FUSE_ENERGY = 2
+SLH_USE_GRAPH = 4
+SLH_GHOSTS = 0
+SLH_RESTRICT = 1
+SLH_PROF_STAGE, SLH_PROF_GHOST, SLH_PROF_RESTRICT, SLH_PROF_DIAG, SLH_PROF_TIME = range(5)
+
+ERRORS = {-1: "INVALID_ARG", -2: "OUT_OF_RANGE", -3: "CUDA", -4: "TIMEOUT", -5: "NOMEM",
+          -6: "DEVICE", -7: "STATE"}
+
+# every entry point declared in include/slh.h
+ABI_SYMBOLS = (
+    "slh_last_error", "slh_create", "slh_destroy", "slh_level_layout", "slh_init_level",
+    "slh_set_state", "slh_get_state", "slh_set_eta", "slh_get_eta", "slh_rk_step",
+    "slh_advance", "slh_fill_ghosts", "slh_tag", "slh_tag_blocks", "slh_regrid_boxes",
+    "slh_reduce_energy", "slh_sync", "slh_profile", "slh_profile_read",
+)
+
+
+class SlhError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"slh error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class slh_box(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_int32 * 3), ("hi", ctypes.c_int32 * 3)]
+
+
+class slh_eom_params(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("a", ctypes.c_double), ("friction", ctypes.c_int32),
+                ("eta_power", ctypes.c_int32), ("lap_order", ctypes.c_int32),
+                ("interp_type", ctypes.c_int32)]
+
+
+@dataclass(frozen=True)
+class EOMParams:
+    """Coefficients of Sec. 3.1: lambda, a, friction on/off, eta power of the
+    potential coefficient, Laplacian accuracy order and ghost interpolation."""
+    lam: float = 1.0
+    a: float = 0.0
+    friction: bool = True
+    eta_power: int = 2
+    order: int = 2
+    interp_type: int = 4
+
+    def c(self):
+        return slh_eom_params(self.lam, self.a, int(self.friction), self.eta_power, self.order,
+                              self.interp_type)
+
+
+_lib = None
+
+
+def lib():
+    """Load ``libslh.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2404_02950_gb300.build` "
+                           "(or __graft_entry__.build()); there is no CPU fallback")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "slh_last_error": (ctypes.c_char_p, []),
+        "slh_create": (i32, [P(vp), i32, dbl, i32, i32, i32, i32, vp]),
+        "slh_destroy": (None, [vp]),
+        "slh_level_layout": (i32, [i32, P(slh_box), i32, P(i64), P(i64), P(i64), P(i64)]),
+        "slh_init_level": (i32, [vp, i32, P(slh_box), i32, P(vp), vp]),
+        "slh_set_state": (i32, [vp, i32, vp, i32]),
+        "slh_get_state": (i32, [vp, i32, vp, i32]),
+        "slh_set_eta": (i32, [vp, dbl]),
+        "slh_get_eta": (i32, [vp, i32, P(dbl)]),
+        "slh_rk_step": (i32, [vp, i32, i32, dbl, P(slh_eom_params), ctypes.c_uint32]),
+        "slh_advance": (i32, [vp, dbl, P(slh_eom_params), ctypes.c_uint32]),
+        "slh_fill_ghosts": (i32, [vp, i32, dbl, i32, i32]),
+        "slh_tag": (i32, [vp, i32, vp, P(i64)]),
+        "slh_tag_blocks": (i32, [vp, i32, i32, vp]),
+        "slh_regrid_boxes": (i32, [vp, P(i32), i32, i32, i32, P(slh_box), i32, P(slh_box), i32, P(i32)]),
+        "slh_reduce_energy": (i32, [vp, P(slh_eom_params), i32, P(dbl)]),
+        "slh_sync": (i32, [vp]),
+        "slh_profile": (i32, [vp, i32, i32]),
+        "slh_profile_read": (i32, [vp, i32, P(dbl), P(i64), P(dbl)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != SLH_OK:
+        msg = lib().slh_last_error().decode(errors="replace")
+        raise SlhError(status, msg)
+
+
+def _boxes(boxes):
+    arr = (slh_box * max(1, len(boxes)))()
+    for i, (lo, hi) in enumerate(boxes):
+        arr[i].lo[:] = [int(v) for v in lo]
+        arr[i].hi[:] = [int(v) for v in hi]
+    return arr
+
+
+# ---------------------------------------------------------------------------
+# ABI-named wrappers
+
+def slh_level_layout(nghost, boxes):
+    """(box_offsets, box_geom (n,4), total_elems, nvalid) of a level layout."""
+    n = len(boxes)
+    offs = (ctypes.c_int64 * max(1, n))()
+    geom = (ctypes.c_int64 * max(1, 4 * n))()
+    tot, nv = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().slh_level_layout(nghost, _boxes(boxes), n, offs, geom, ctypes.byref(tot), ctypes.byref(nv)))
+    return (np.array(offs[:n], dtype=np.int64), np.array(geom[:4 * n], dtype=np.int64).reshape(n, 4),
+            tot.value, nv.value)
+
+
+def slh_regrid_boxes(tags, blocking_factor, n_error_buf, max_box, parent=None):
+    """Host-only regrid of a dense uint8 tag array [z, y, x] (Sec. 2.2-2.3);
+    returns [((lo_x, lo_y, lo_z), (hi_x, hi_y, hi_z)), ...] of the finer level."""
+    t = np.ascontiguousarray(np.asarray(tags, dtype=np.uint8))
+    dims = (ctypes.c_int32 * 3)(t.shape[2], t.shape[1], t.shape[0])
+    par = _boxes(parent) if parent else None
+    npar = len(parent) if parent else 0
+    nout = ctypes.c_int32(0)
+    cap = 64
+    while True:
+        out = (slh_box * cap)()
+        st = lib().slh_regrid_boxes(t.ctypes.data, dims, blocking_factor, n_error_buf, max_box, par, npar,
+                                    out, cap, ctypes.byref(nout))
+        if st == -2 and nout.value > cap:
+            cap = nout.value
+            continue
+        _check(st)
+        return [(tuple(out[i].lo), tuple(out[i].hi)) for i in range(nout.value)]
+
+
+def dense_from_boxes(fields, boxes):
+    """Pack four [z, y, x] domain arrays into the dense valid-cell layout
+    [box][comp][z][y][x] (host numpy)."""
+    parts = []
+    for lo, hi in boxes:
+        for c in range(4):
+            parts.append(np.asarray(fields[c])[lo[2]:hi[2] + 1, lo[1]:hi[1] + 1, lo[0]:hi[0] + 1].ravel())
+    return np.concatenate(parts)
+
+
+def boxes_from_dense(dense, boxes):
+    """Split a dense valid-cell array into per-box (4, nz, ny, nx) arrays."""
+    out, off = [], 0
+    for lo, hi in boxes:
+        n = [hi[d] - lo[d] + 1 for d in range(3)]
+        vol = n[0] * n[1] * n[2]
+        out.append(np.asarray(dense[off:off + 4 * vol]).reshape(4, n[2], n[1], n[0]))
+        off += 4 * vol
+    return out
+
+
+class Hierarchy:
+    """A context plus the torch-allocated buffers of its levels.
+
+    n0: level-0 cells per axis; dx0: level-0 spacing; nghost: ghost layers;
+    bf: blocking factor; prec: 'f64' or 'f32' (FP32 + Kahan)."""
+
+    def __init__(self, n0, dx0, nghost=3, bf=8, prec="f64", max_levels=1, device="cuda:0", stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.prec = SLH_F64 if prec == "f64" else SLH_F32_KAHAN
+        self.dtype = torch.float64 if self.prec == SLH_F64 else torch.float32
+        self.np_dtype = np.float64 if self.prec == SLH_F64 else np.float32
+        # a stream of its own: CUDA graphs cannot capture the legacy default stream
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        self.nghost, self.bf, self.n0, self.dx0 = nghost, bf, n0, dx0
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib().slh_create(ctypes.byref(h), n0, dx0, nghost, bf, self.prec, max_levels,
+                                    ctypes.c_void_p(self.stream.cuda_stream)))
+        self.h = h
+        self.levels = {}
+
+    def close(self):
+        if self.h:
+            lib().slh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_level(self, lev, boxes, fused_tags=False):
+        torch = self.torch
+        _, geom, total, nvalid = slh_level_layout(self.nghost, boxes)
+        bufs = []
+        for i in range(SLH_NBUF):
+            if i == SLH_BUF_C and self.prec == SLH_F64:
+                bufs.append(None)
+            else:
+                bufs.append(torch.empty(int(total), dtype=self.dtype, device=self.device))
+        tags = torch.zeros(int(nvalid), dtype=torch.uint8, device=self.device) if fused_tags else None
+        ptrs = (ctypes.c_void_p * SLH_NBUF)(*[b.data_ptr() if b is not None else None for b in bufs])
+        _check(lib().slh_init_level(self.h, lev, _boxes(boxes), len(boxes), ptrs,
+                                    ctypes.c_void_p(tags.data_ptr()) if tags is not None else None))
+        for l in list(self.levels):
+            if l >= lev:
+                del self.levels[l]
+        self.levels[lev] = dict(boxes=list(boxes), bufs=bufs, tags=tags, nvalid=int(nvalid), total=int(total),
+                                steps=0)
+        return self.levels[lev]
+
+    def state_buffer(self, lev):
+        """The torch buffer currently holding the level's state (the state
+        and previous-state buffers swap roles after every RK step)."""
+        info = self.levels[lev]
+        return info["bufs"][SLH_BUF_Y if info["steps"] % 2 == 0 else SLH_BUF_YB]
+
+    def set_state(self, lev, dense):
+        """dense: host numpy array (or CUDA tensor) in the dense valid-cell
+        layout of the context precision."""
+        torch = self.torch
+        if isinstance(dense, torch.Tensor):
+            t = dense.to(self.dtype).contiguous()
+            _check(lib().slh_set_state(self.h, lev, ctypes.c_void_p(t.data_ptr()), 0 if t.is_cuda else 1))
+            if not t.is_cuda:
+                self.sync()
+            self._keep = t
+        else:
+            a = np.ascontiguousarray(np.asarray(dense, dtype=self.np_dtype))
+            _check(lib().slh_set_state(self.h, lev, ctypes.c_void_p(a.ctypes.data), 1))
+            self.sync()
+
+    def get_state(self, lev):
+        n = 4 * self.levels[lev]["nvalid"]
+        out = np.empty(n, dtype=self.np_dtype)
+        _check(lib().slh_get_state(self.h, lev, ctypes.c_void_p(out.ctypes.data), 1))
+        return out
+
+    def set_eta(self, eta):
+        _check(lib().slh_set_eta(self.h, float(eta)))
+
+    def get_eta(self, lev=0):
+        v = ctypes.c_double()
+        _check(lib().slh_get_eta(self.h, lev, ctypes.byref(v)))
+        return v.value
+
+    def rk_step(self, lev, dt0, params: EOMParams, sub=0, flags=0):
+        p = params.c()
+        _check(lib().slh_rk_step(self.h, lev, sub, float(dt0), ctypes.byref(p), flags))
+        self.levels[lev]["steps"] += 1
+
+    def advance(self, dt0, params: EOMParams, flags=0):
+        p = params.c()
+        _check(lib().slh_advance(self.h, float(dt0), ctypes.byref(p), flags))
+        for l, info in self.levels.items():
+            info["steps"] += 2 ** l
+
+    def fill_ghosts(self, lev, alpha=1.0, interp_type=4, mode=SLH_GHOSTS):
+        _check(lib().slh_fill_ghosts(self.h, lev, float(alpha), interp_type, mode))
+
+    def tag(self, lev):
+        t = self.torch.zeros(self.levels[lev]["nvalid"], dtype=self.torch.uint8, device=self.device)
+        n = ctypes.c_int64()
+        _check(lib().slh_tag(self.h, lev, ctypes.c_void_p(t.data_ptr()), ctypes.byref(n)))
+        return t, n.value
+
+    def tag_blocks(self, lev, n_error_buf):
+        nb = (self.n0 << lev) // (self.bf // 2)
+        m = np.zeros((nb, nb, nb), dtype=np.uint8)
+        _check(lib().slh_tag_blocks(self.h, lev, n_error_buf, ctypes.c_void_p(m.ctypes.data)))
+        return m
+
+    def reduce_energy(self, params: EOMParams, mode=0):
+        p = params.c()
+        out = (ctypes.c_double * 5)()
+        _check(lib().slh_reduce_energy(self.h, ctypes.byref(p), mode, out))
+        return np.array(out[:])
+
+    def sync(self):
+        _check(lib().slh_sync(self.h))
+
+    def profile(self, enable=True, reset=True):
+        _check(lib().slh_profile(self.h, int(enable), int(reset)))
+
+    def profile_read(self, kind):
+        ms, n, b = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+        _check(lib().slh_profile_read(self.h, kind, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)))
+        return ms.value, n.value, b.value

@@ -1,0 +1,812 @@
+// C ABI of the GB300 AMR stepper: context and level management, state I/O,
+// the RK4 step of one level (Tab. "integrator", type 4), the subcycled
+// coarse step (Sec. 2.1, Fig. 2) with optional CUDA-graph replay, and the
+// synchronising diagnostics (tags, energy, regrid block mask).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "slh_internal.cuh"
+
+namespace slh {
+
+static thread_local std::string g_last_error;
+
+slh_status fail(slh_status code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+slh_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(SLH_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+bool make_layout(int g, const slh_box* boxes, int nboxes, Layout* out, std::string* why) {
+  out->boxes.clear();
+  long long off = 0, voff = 0;
+  for (int b = 0; b < nboxes; ++b) {
+    BoxDev B;
+    memset(&B, 0, sizeof(B));
+    for (int d = 0; d < 3; ++d) {
+      B.lo[d] = boxes[b].lo[d];
+      B.n[d] = boxes[b].hi[d] - boxes[b].lo[d] + 1;
+      if (B.n[d] <= 0) {
+        if (why) *why = "box " + std::to_string(b) + " has hi < lo";
+        return false;
+      }
+    }
+    B.pitch = (int)round_up(XPAD + B.n[0] + g, 8);
+    B.pny = B.n[1] + 2 * g;
+    B.pnz = B.n[2] + 2 * g;
+    B.cs = round_up((long long)B.pitch * B.pny * B.pnz, 32);
+    off = round_up(off, 64);
+    B.off = off;
+    off += NCOMP * B.cs;
+    B.voff = voff;
+    voff += (long long)B.n[0] * B.n[1] * B.n[2];
+    out->boxes.push_back(B);
+  }
+  out->total = round_up(off, 64);
+  out->nvalid = voff;
+  return true;
+}
+
+void prof_begin(slh_ctx* c, int kind, double bytes) {
+  if (!c->prof) return;
+  ProfRec r;
+  cudaEventCreate(&r.a);
+  cudaEventCreate(&r.b);
+  r.kind = kind;
+  r.bytes = bytes;
+  cudaEventRecord(r.a, c->stream);
+  c->prof_open.push_back(r);
+}
+
+void prof_end(slh_ctx* c) {
+  if (!c->prof || c->prof_open.empty()) return;
+  cudaEventRecord(c->prof_open.back().b, c->stream);
+}
+
+static void free_level(Level& L) {
+  cudaFree(L.d_boxes);
+  cudaFree(L.d_bmap);
+  cudaFree(L.d_slabs);
+  cudaFree(L.d_slab_off);
+  cudaFree(L.d_items);
+  cudaFree(L.d_covered);
+  cudaFree(L.d_ritems);
+  cudaFree(L.d_roff);
+  cudaFree(L.d_epart);
+  cudaFree(L.d_tagtmp);
+  L = Level();
+}
+
+static void drop_graphs(slh_ctx* c) {
+  for (int i = 0; i < 2; ++i)
+    if (c->graph[i]) {
+      cudaGraphExecDestroy(c->graph[i]);
+      c->graph[i] = nullptr;
+    }
+  c->graph_key = 0;
+}
+
+template <typename V>
+static slh_status upload(V** dptr, const std::vector<V>& h) {
+  cudaFree(*dptr);
+  *dptr = nullptr;
+  if (h.empty()) return SLH_OK;
+  cudaError_t e = cudaMalloc((void**)dptr, sizeof(V) * h.size());
+  if (e != cudaSuccess) return fail(SLH_ERR_NOMEM, "cudaMalloc of %zu bytes: %s", sizeof(V) * h.size(), cudaGetErrorString(e));
+  SLH_CUDA(cudaMemcpy(*dptr, h.data(), sizeof(V) * h.size(), cudaMemcpyHostToDevice));
+  return SLH_OK;
+}
+
+static int ilog2(int v) {
+  int s = 0;
+  while ((1 << s) < v) ++s;
+  return s;
+}
+
+static size_t elem_size(const slh_ctx* c) { return c->prec == SLH_F64 ? 8 : 4; }
+
+// mark, for the coarser level lev-1, the blocks of bf/2 cells covered by lev
+static slh_status build_covered(slh_ctx* c, int lev) {
+  Level& C = c->lev[lev - 1];
+  Level& F = c->lev[lev];
+  const int r = c->bf / 2;
+  const int nb = C.n_dom / r;
+  std::vector<uint8_t> m((size_t)nb * nb * nb, 0);
+  for (const slh_box& b : F.boxes) {
+    int lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = (b.lo[d] / 2) / r;
+      hi[d] = ((b.hi[d] + 1) / 2) / r - 1;
+    }
+    for (int z = lo[2]; z <= hi[2]; ++z)
+      for (int y = lo[1]; y <= hi[1]; ++y)
+        for (int x = lo[0]; x <= hi[0]; ++x) m[((size_t)z * nb + y) * nb + x] = 1;
+  }
+  C.ncov = nb;
+  return upload(&C.d_covered, m);
+}
+
+}  // namespace slh
+
+using namespace slh;
+
+extern "C" {
+
+const char* slh_last_error(void) { return g_last_error.c_str(); }
+
+slh_status slh_level_layout(int32_t nghost, const slh_box* boxes, int32_t nboxes, int64_t* box_offsets,
+                            int64_t* box_geom, int64_t* total_elems, int64_t* nvalid) {
+  if (!boxes || nboxes < 0 || nghost < 1 || nghost > 4) return fail(SLH_ERR_INVALID_ARG, "layout: bad arguments");
+  Layout lay;
+  std::string why;
+  if (!make_layout(nghost, boxes, nboxes, &lay, &why)) return fail(SLH_ERR_INVALID_ARG, "layout: %s", why.c_str());
+  for (int b = 0; b < nboxes; ++b) {
+    if (box_offsets) box_offsets[b] = lay.boxes[b].off;
+    if (box_geom) {
+      box_geom[4 * b + 0] = lay.boxes[b].pitch;
+      box_geom[4 * b + 1] = lay.boxes[b].pny;
+      box_geom[4 * b + 2] = lay.boxes[b].pnz;
+      box_geom[4 * b + 3] = lay.boxes[b].cs;
+    }
+  }
+  if (total_elems) *total_elems = lay.total;
+  if (nvalid) *nvalid = lay.nvalid;
+  return SLH_OK;
+}
+
+slh_status slh_create(slh_ctx** out, int32_t n0, double dx0, int32_t nghost, int32_t bf, int32_t prec,
+                      int32_t max_levels, void* stream) {
+  if (!out) return fail(SLH_ERR_INVALID_ARG, "create: ctx pointer is null");
+  *out = nullptr;
+  if (nghost < 1 || nghost > 4) return fail(SLH_ERR_INVALID_ARG, "create: nghost must be in [1,4]");
+  if (bf < 2 || (bf & (bf - 1))) return fail(SLH_ERR_INVALID_ARG, "create: blocking factor must be a power of two >= 2");
+  if (n0 < bf || n0 % bf) return fail(SLH_ERR_INVALID_ARG, "create: n0 must be a positive multiple of the blocking factor");
+  if (prec != SLH_F64 && prec != SLH_F32_KAHAN) return fail(SLH_ERR_INVALID_ARG, "create: unknown precision %d", prec);
+  if (max_levels < 1 || max_levels > MAX_LEVELS) return fail(SLH_ERR_INVALID_ARG, "create: max_levels must be in [1,8]");
+  if (!(dx0 > 0.0)) return fail(SLH_ERR_INVALID_ARG, "create: dx0 must be positive");
+  slh_ctx* c = new (std::nothrow) slh_ctx();
+  if (!c) return fail(SLH_ERR_NOMEM, "create: out of host memory");
+  c->n0 = n0;
+  c->dx0 = dx0;
+  c->g = nghost;
+  c->bf = bf;
+  c->prec = prec;
+  c->max_levels = max_levels;
+  c->stream = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_time, sizeof(double) * 2 * MAX_LEVELS);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_levsum, sizeof(double) * 4 * MAX_LEVELS);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_count, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_time, 0, sizeof(double) * 2 * MAX_LEVELS, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+  if (e != cudaSuccess) {
+    slh_destroy(c);
+    return cuda_fail(e, "create");
+  }
+  *out = c;
+  return SLH_OK;
+}
+
+void slh_destroy(slh_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
+  for (int l = 0; l < MAX_LEVELS; ++l) free_level(c->lev[l]);
+  for (auto& r : c->prof_open) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  cudaFree(c->d_time);
+  cudaFree(c->d_err);
+  cudaFree(c->d_levsum);
+  cudaFree(c->d_count);
+  cudaFree(c->d_blockmask);
+  delete c;
+}
+
+slh_status slh_init_level(slh_ctx* c, int32_t lev, const slh_box* boxes, int32_t nboxes, void* const* bufs,
+                          uint8_t* tags_dev) {
+  if (!c || !boxes || !bufs || nboxes < 1) return fail(SLH_ERR_INVALID_ARG, "init_level: null argument or no boxes");
+  if (lev < 0 || lev >= c->max_levels) return fail(SLH_ERR_OUT_OF_RANGE, "init_level: level %d outside [0,%d)", lev, c->max_levels);
+  if (lev > c->nlevels) return fail(SLH_ERR_STATE, "init_level: level %d defined before level %d", lev, c->nlevels);
+  for (int i = 0; i < SLH_NBUF; ++i) {
+    const bool need = (i != SLH_BUF_C) || c->prec == SLH_F32_KAHAN;
+    if (need && !bufs[i]) return fail(SLH_ERR_INVALID_ARG, "init_level: buffer %d is null", i);
+  }
+  const int ndom = c->n0 << lev;
+  const int bf = c->bf;
+  const int nbd = ndom / bf;
+  std::vector<int> bmap((size_t)nbd * nbd * nbd, -1);
+  for (int b = 0; b < nboxes; ++b) {
+    const slh_box& B = boxes[b];
+    for (int d = 0; d < 3; ++d) {
+      if (B.lo[d] < 0 || B.hi[d] >= ndom || B.hi[d] < B.lo[d])
+        return fail(SLH_ERR_OUT_OF_RANGE, "init_level: box %d outside the level domain [0,%d)", b, ndom);
+      if (B.lo[d] % bf || (B.hi[d] + 1) % bf)
+        return fail(SLH_ERR_INVALID_ARG, "init_level: box %d not aligned to the blocking factor %d", b, bf);
+    }
+    for (int z = B.lo[2] / bf; z <= B.hi[2] / bf; ++z)
+      for (int y = B.lo[1] / bf; y <= B.hi[1] / bf; ++y)
+        for (int x = B.lo[0] / bf; x <= B.hi[0] / bf; ++x) {
+          int& o = bmap[((size_t)z * nbd + y) * nbd + x];
+          if (o >= 0) return fail(SLH_ERR_INVALID_ARG, "init_level: boxes %d and %d overlap", o, b);
+          o = b;
+        }
+  }
+  if (lev == 0) {
+    for (int v : bmap)
+      if (v < 0) return fail(SLH_ERR_INVALID_ARG, "init_level: level 0 must cover the periodic domain");
+  } else {
+    // nesting: the coarse projection grown by one block of bf/2 coarse cells
+    // must lie inside level lev-1 (periodic).  A block of bf/2 coarse cells
+    // lies inside a coarse box iff its enclosing block of bf cells does
+    // (coarse boxes are aligned to bf).
+    Level& C = c->lev[lev - 1];
+    const int r = bf / 2;
+    const int nbc = C.n_dom / r;
+    for (int b = 0; b < nboxes; ++b) {
+      int lo[3], hi[3];
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = (boxes[b].lo[d] / 2) / r - 1;
+        hi[d] = ((boxes[b].hi[d] + 1) / 2) / r;
+      }
+      for (int z = lo[2]; z <= hi[2]; ++z)
+        for (int y = lo[1]; y <= hi[1]; ++y)
+          for (int x = lo[0]; x <= hi[0]; ++x) {
+            const int wx = ((x % nbc) + nbc) % nbc, wy = ((y % nbc) + nbc) % nbc, wz = ((z % nbc) + nbc) % nbc;
+            const int own = C.h_bmap[((size_t)(wz / 2) * C.nb_dom + wy / 2) * C.nb_dom + wx / 2];
+            if (own < 0)
+              return fail(SLH_ERR_OUT_OF_RANGE,
+                          "init_level: box %d of level %d is not nested in level %d with a gap of %d coarse cells", b,
+                          lev, lev - 1, r);
+          }
+    }
+  }
+  // drop this level and every finer one
+  cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
+  for (int l = lev; l < MAX_LEVELS; ++l) free_level(c->lev[l]);
+  if (lev > 0) {
+    cudaFree(c->lev[lev - 1].d_covered);
+    c->lev[lev - 1].d_covered = nullptr;
+  }
+  c->nlevels = lev;
+
+  Level& L = c->lev[lev];
+  L.n_dom = ndom;
+  L.nb_dom = nbd;
+  L.dx = c->dx0 / (double)(1 << lev);
+  L.boxes.assign(boxes, boxes + nboxes);
+  std::string why;
+  if (!make_layout(c->g, boxes, nboxes, &L.lay, &why)) return fail(SLH_ERR_INVALID_ARG, "init_level: %s", why.c_str());
+  for (int i = 0; i < SLH_NBUF; ++i) L.buf[i] = bufs[i];
+  if (c->prec != SLH_F32_KAHAN) L.buf[SLH_BUF_C] = nullptr;
+  L.tags_dev = tags_dev;
+  L.role_y = SLH_BUF_Y;
+  L.role_prev = SLH_BUF_YB;
+  slh_status st;
+  if ((st = upload(&L.d_boxes, L.lay.boxes)) != SLH_OK) return st;
+  if ((st = upload(&L.d_bmap, bmap)) != SLH_OK) return st;
+  L.h_bmap = bmap;
+
+  // ghost shell slabs
+  const int g = c->g;
+  std::vector<GhostSlab> slabs;
+  std::vector<long long> soff;
+  long long tot = 0;
+  for (int b = 0; b < nboxes; ++b) {
+    const BoxDev& B = L.lay.boxes[b];
+    const int n0 = B.n[0], n1 = B.n[1], n2 = B.n[2];
+    GhostSlab s6[6] = {
+        {b, {-g, -g, -g}, {n0 + 2 * g, n1 + 2 * g, g}},
+        {b, {-g, -g, n2}, {n0 + 2 * g, n1 + 2 * g, g}},
+        {b, {-g, -g, 0}, {n0 + 2 * g, g, n2}},
+        {b, {-g, n1, 0}, {n0 + 2 * g, g, n2}},
+        {b, {-g, 0, 0}, {g, n1, n2}},
+        {b, {n0, 0, 0}, {g, n1, n2}},
+    };
+    for (auto& s : s6) {
+      slabs.push_back(s);
+      soff.push_back(tot);
+      tot += (long long)s.e[0] * s.e[1] * s.e[2];
+    }
+  }
+  L.nslabs = (int)slabs.size();
+  L.nghost_cells = tot;
+  if ((st = upload(&L.d_slabs, slabs)) != SLH_OK) return st;
+  if ((st = upload(&L.d_slab_off, soff)) != SLH_OK) return st;
+
+  // stage work items: z chunk outer, then y, then x tiles, box by box
+  L.tile_x = 32;
+  L.tile_y = c->prec == SLH_F64 ? 8 : 16;
+  L.zlen = 64;
+  std::vector<int4> items;
+  for (int b = 0; b < nboxes; ++b) {
+    const BoxDev& B = L.lay.boxes[b];
+    for (int z0 = 0; z0 < B.n[2]; z0 += L.zlen)
+      for (int y0 = 0; y0 < B.n[1]; y0 += L.tile_y)
+        for (int x0 = 0; x0 < B.n[0]; x0 += L.tile_x) items.push_back(make_int4(b, x0, y0, z0));
+  }
+  L.nitems = (int)items.size();
+  if ((st = upload(&L.d_items, items)) != SLH_OK) return st;
+
+  // restriction items onto lev-1
+  if (lev > 0) {
+    std::vector<RestrictItem> ri;
+    std::vector<long long> roff;
+    long long rt = 0;
+    for (int b = 0; b < nboxes; ++b) {
+      RestrictItem it;
+      it.fbox = b;
+      for (int d = 0; d < 3; ++d) it.n[d] = L.lay.boxes[b].n[d] / 2;
+      ri.push_back(it);
+      roff.push_back(rt);
+      rt += (long long)it.n[0] * it.n[1] * it.n[2];
+    }
+    L.nritems = (int)ri.size();
+    L.nrcells = rt;
+    if ((st = upload(&L.d_ritems, ri)) != SLH_OK) return st;
+    if ((st = upload(&L.d_roff, roff)) != SLH_OK) return st;
+  }
+
+  // energy partials
+  L.epart_cap = c->num_sms * 32;
+  {
+    cudaError_t e = cudaMalloc(&L.d_epart, sizeof(double) * 4 * L.epart_cap);
+    if (e != cudaSuccess) return fail(SLH_ERR_NOMEM, "init_level: energy partials: %s", cudaGetErrorString(e));
+  }
+  L.defined = true;
+  c->nlevels = lev + 1;
+  if (lev > 0 && (st = build_covered(c, lev)) != SLH_OK) return st;
+
+  const size_t bytes = (size_t)L.lay.total * elem_size(c);
+  for (int i = 0; i < SLH_NBUF; ++i)
+    if (L.buf[i]) SLH_CUDA(cudaMemsetAsync(L.buf[i], 0, bytes, c->stream));
+  return SLH_OK;
+}
+
+static slh_status copy_state(slh_ctx* c, int lev, void* host_or_dev, bool to_device) {
+  Level& L = c->lev[lev];
+  const size_t s = elem_size(c);
+  char* dense = static_cast<char*>(host_or_dev);
+  char* buf = static_cast<char*>(L.buf[L.role_y]);
+  for (size_t b = 0; b < L.lay.boxes.size(); ++b) {
+    const BoxDev& B = L.lay.boxes[b];
+    const long long vol = (long long)B.n[0] * B.n[1] * B.n[2];
+    for (int comp = 0; comp < NCOMP; ++comp) {
+      cudaMemcpy3DParms p;
+      memset(&p, 0, sizeof(p));
+      cudaPitchedPtr dptr = make_cudaPitchedPtr(dense + (size_t)(NCOMP * B.voff + comp * vol) * s, B.n[0] * s, B.n[0], B.n[1]);
+      cudaPitchedPtr bptr = make_cudaPitchedPtr(buf + (size_t)(B.off + comp * B.cs) * s, (size_t)B.pitch * s, B.pitch, B.pny);
+      if (to_device) {
+        p.srcPtr = dptr;
+        p.dstPtr = bptr;
+        p.dstPos = make_cudaPos(XPAD * s, c->g, c->g);
+      } else {
+        p.srcPtr = bptr;
+        p.srcPos = make_cudaPos(XPAD * s, c->g, c->g);
+        p.dstPtr = dptr;
+      }
+      p.extent = make_cudaExtent(B.n[0] * s, B.n[1], B.n[2]);
+      p.kind = cudaMemcpyDefault;
+      SLH_CUDA(cudaMemcpy3DAsync(&p, c->stream));
+    }
+  }
+  return SLH_OK;
+}
+
+slh_status slh_set_state(slh_ctx* c, int32_t lev, const void* src, int32_t src_is_host) {
+  (void)src_is_host;
+  if (!c || !src) return fail(SLH_ERR_INVALID_ARG, "set_state: null argument");
+  if (lev < 0 || lev >= c->nlevels) return fail(SLH_ERR_STATE, "set_state: level %d not defined", lev);
+  Level& L = c->lev[lev];
+  slh_status st = copy_state(c, lev, const_cast<void*>(src), true);
+  if (st != SLH_OK) return st;
+  const size_t bytes = (size_t)L.lay.total * elem_size(c);
+  SLH_CUDA(cudaMemcpyAsync(L.buf[L.role_prev], L.buf[L.role_y], bytes, cudaMemcpyDeviceToDevice, c->stream));
+  if (L.buf[SLH_BUF_C]) SLH_CUDA(cudaMemsetAsync(L.buf[SLH_BUF_C], 0, bytes, c->stream));
+  return SLH_OK;
+}
+
+slh_status slh_get_state(slh_ctx* c, int32_t lev, void* dst, int32_t dst_is_host) {
+  if (!c || !dst) return fail(SLH_ERR_INVALID_ARG, "get_state: null argument");
+  if (lev < 0 || lev >= c->nlevels) return fail(SLH_ERR_STATE, "get_state: level %d not defined", lev);
+  slh_status st = copy_state(c, lev, dst, false);
+  if (st != SLH_OK) return st;
+  if (dst_is_host) return slh_sync(c);
+  return SLH_OK;
+}
+
+}  // extern "C"
+
+__global__ void set_eta_kernel(double* t, double eta) {
+  const int i = threadIdx.x;
+  if (i < 2 * MAX_LEVELS) t[i] = eta;
+}
+
+extern "C" {
+
+slh_status slh_set_eta(slh_ctx* c, double eta) {
+  if (!c) return fail(SLH_ERR_INVALID_ARG, "set_eta: null ctx");
+  set_eta_kernel<<<1, 32, 0, c->stream>>>(c->d_time, eta);
+  SLH_CUDA(cudaGetLastError());
+  return SLH_OK;
+}
+
+slh_status slh_get_eta(slh_ctx* c, int32_t lev, double* eta) {
+  if (!c || !eta) return fail(SLH_ERR_INVALID_ARG, "get_eta: null argument");
+  if (lev < 0 || lev >= MAX_LEVELS) return fail(SLH_ERR_OUT_OF_RANGE, "get_eta: level %d", lev);
+  SLH_CUDA(cudaMemcpyAsync(eta, c->d_time + 2 * lev, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  SLH_CUDA(cudaStreamSynchronize(c->stream));
+  return SLH_OK;
+}
+
+static slh_status check_params(const slh_eom_params* p) {
+  if (!p) return fail(SLH_ERR_INVALID_ARG, "null eom params");
+  if (p->lap_order != 2 && p->lap_order != 4 && p->lap_order != 6)
+    return fail(SLH_ERR_INVALID_ARG, "lap_order must be 2, 4 or 6 (got %d)", p->lap_order);
+  if (p->eta_power != 0 && p->eta_power != 2) return fail(SLH_ERR_INVALID_ARG, "eta_power must be 0 or 2");
+  if (p->interp_type != 0 && p->interp_type != 2 && p->interp_type != 4)
+    return fail(SLH_ERR_INVALID_ARG, "interp_type must be 0, 2 or 4");
+  return SLH_OK;
+}
+
+static slh_status rk_step_impl(slh_ctx* c, int lev, int sub, double dt0, const slh_eom_params& p, uint32_t flags) {
+  Level& L = c->lev[lev];
+  if (c->g < p.lap_order / 2) return fail(SLH_ERR_INVALID_ARG, "nghost %d < Laplacian half width %d", c->g, p.lap_order / 2);
+  const double dt = std::ldexp(dt0, -lev);
+  const double cRK[4] = {0.0, 0.5, 0.5, 1.0};
+  const double aRK[4] = {0.5, 0.5, 1.0, 0.0};
+  const double bRK[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+  const size_t s = elem_size(c);
+  const double V = (double)L.lay.nvalid;
+  slh_status st;
+  prof_begin(c, SLH_PROF_TIME, 0.0);
+  st = launch_time_begin(c, lev, sub, dt);
+  prof_end(c);
+  if (st != SLH_OK) return st;
+  const int ybuf = L.role_y, nbuf = L.role_prev;
+  const int in_role[4] = {ybuf, SLH_BUF_YA, nbuf, SLH_BUF_YA};
+  const int out_role[4] = {SLH_BUF_YA, nbuf, SLH_BUF_YA, nbuf};
+  const double vals[4] = {12.0, 20.0, 20.0, c->prec == SLH_F32_KAHAN ? 24.0 : 16.0};
+  for (int k = 0; k < 4; ++k) {
+    const double alpha = lev > 0 ? (sub + cRK[k]) / 2.0 : 1.0;
+    prof_begin(c, SLH_PROF_GHOST, (double)L.nghost_cells * 2 * 2 * s);
+    st = launch_ghosts(c, lev, in_role[k], alpha, p.interp_type);
+    prof_end(c);
+    if (st != SLH_OK) return st;
+    StageLaunch sl;
+    memset(&sl, 0, sizeof(sl));
+    sl.stage = k + 1;
+    sl.yin = L.buf[in_role[k]];
+    sl.yn = L.buf[ybuf];
+    sl.dacc = L.buf[SLH_BUF_D];
+    sl.yout = L.buf[out_role[k]];
+    sl.comp = k == 3 ? L.buf[SLH_BUF_C] : nullptr;
+    sl.c_stage = cRK[k] * dt;
+    sl.ha = aRK[k] * dt;
+    sl.hb = bRK[k] * dt;
+    sl.lev = lev;
+    double extra = 0.0;
+    if (k == 0 && (flags & SLH_FUSE_TAG)) {
+      if (!L.tags_dev) return fail(SLH_ERR_STATE, "rk_step: SLH_FUSE_TAG needs tags_dev at init_level");
+      sl.tags = L.tags_dev;
+      extra = 1.0;
+    }
+    if (k == 0 && (flags & SLH_FUSE_ENERGY)) {
+      sl.epart = L.d_epart;
+      sl.covered = L.d_covered;
+      sl.cov_shift = ilog2(c->bf / 2);
+      sl.cov_nb = L.ncov;
+    }
+    prof_begin(c, SLH_PROF_STAGE, V * (vals[k] * s + extra));
+    int used = 0;
+    st = launch_stage(c, L, p, sl, &used);
+    prof_end(c);
+    if (st != SLH_OK) return st;
+    if (k == 0 && (flags & SLH_FUSE_ENERGY)) L.fused_energy_ctas = used;
+  }
+  L.role_y = nbuf;
+  L.role_prev = ybuf;
+  return SLH_OK;
+}
+
+slh_status slh_rk_step(slh_ctx* c, int32_t lev, int32_t sub, double dt0, const slh_eom_params* p, uint32_t flags) {
+  if (!c) return fail(SLH_ERR_INVALID_ARG, "rk_step: null ctx");
+  slh_status st = check_params(p);
+  if (st != SLH_OK) return st;
+  if (lev < 0 || lev >= c->nlevels) return fail(SLH_ERR_STATE, "rk_step: level %d not defined", lev);
+  if (sub != 0 && sub != 1) return fail(SLH_ERR_INVALID_ARG, "rk_step: sub must be 0 or 1");
+  if (!(dt0 > 0.0)) return fail(SLH_ERR_INVALID_ARG, "rk_step: dt0 must be positive");
+  return rk_step_impl(c, lev, sub, dt0, *p, flags);
+}
+
+static slh_status fill_impl(slh_ctx* c, int lev, double alpha, int itype, int mode) {
+  Level& L = c->lev[lev];
+  const size_t s = elem_size(c);
+  if (mode == SLH_RESTRICT) {
+    prof_begin(c, SLH_PROF_RESTRICT, (double)L.nrcells * NCOMP * 9 * s);
+    slh_status st = launch_restrict(c, lev);
+    prof_end(c);
+    if (st != SLH_OK) return st;
+    alpha = 1.0;
+  }
+  prof_begin(c, SLH_PROF_GHOST, (double)L.nghost_cells * 2 * 2 * s);
+  slh_status st = launch_ghosts(c, lev, L.role_y, alpha, itype);
+  prof_end(c);
+  return st;
+}
+
+static slh_status advance_rec(slh_ctx* c, int lev, int sub, double dt0, const slh_eom_params& p, uint32_t flags) {
+  slh_status st = rk_step_impl(c, lev, sub, dt0, p, flags);
+  if (st != SLH_OK) return st;
+  if (lev + 1 < c->nlevels) {
+    for (int i = 0; i < 2; ++i)
+      if ((st = advance_rec(c, lev + 1, i, dt0, p, flags)) != SLH_OK) return st;
+    if ((st = fill_impl(c, lev + 1, 1.0, p.interp_type, SLH_RESTRICT)) != SLH_OK) return st;
+  }
+  return SLH_OK;
+}
+
+static unsigned long long graph_key(slh_ctx* c, double dt0, const slh_eom_params& p, uint32_t flags) {
+  unsigned long long h = 1469598103934665603ull;
+  auto mix = [&](const void* d, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(d);
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  };
+  mix(&dt0, sizeof(dt0));
+  mix(&p, sizeof(p));
+  mix(&flags, sizeof(flags));
+  mix(&c->nlevels, sizeof(int));
+  for (int l = 0; l < c->nlevels; ++l) {
+    mix(&c->lev[l].d_boxes, sizeof(void*));
+    mix(c->lev[l].buf, sizeof(c->lev[l].buf));
+    mix(&c->lev[l].role_y, sizeof(int));
+  }
+  return h | 1ull;
+}
+
+slh_status slh_advance(slh_ctx* c, double dt0, const slh_eom_params* p, uint32_t flags) {
+  if (!c) return fail(SLH_ERR_INVALID_ARG, "advance: null ctx");
+  slh_status st = check_params(p);
+  if (st != SLH_OK) return st;
+  if (c->nlevels < 1) return fail(SLH_ERR_STATE, "advance: no level defined");
+  if (!(dt0 > 0.0)) return fail(SLH_ERR_INVALID_ARG, "advance: dt0 must be positive");
+  if (!(flags & SLH_USE_GRAPH) || c->prof) return advance_rec(c, 0, 0, dt0, *p, flags);
+
+  // graph replay: the graph depends on the rotation parity of level 0 only
+  // (finer levels take an even number of steps per coarse step)
+  uint32_t f = flags & ~SLH_USE_GRAPH;
+  Level& L0 = c->lev[0];
+  const int parity = L0.role_y == SLH_BUF_Y ? 0 : 1;
+  // key of the configuration with level-0 rotation normalised
+  const int saved0 = L0.role_y, savedp0 = L0.role_prev;
+  L0.role_y = SLH_BUF_Y;
+  const unsigned long long key = graph_key(c, dt0, *p, f);
+  L0.role_y = saved0;
+  if (key != c->graph_key) {
+    drop_graphs(c);
+    c->graph_key = key;
+  }
+  if (!c->graph[parity]) {
+    int saved[MAX_LEVELS][2];
+    for (int l = 0; l < c->nlevels; ++l) {
+      saved[l][0] = c->lev[l].role_y;
+      saved[l][1] = c->lev[l].role_prev;
+    }
+    cudaGraph_t gr;
+    SLH_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    slh_status cst = advance_rec(c, 0, 0, dt0, *p, f);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &gr);
+    for (int l = 0; l < c->nlevels; ++l) {
+      c->lev[l].role_y = saved[l][0];
+      c->lev[l].role_prev = saved[l][1];
+    }
+    if (cst != SLH_OK) return cst;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c->graph[parity], gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  SLH_CUDA(cudaGraphLaunch(c->graph[parity], c->stream));
+  (void)savedp0;
+  // apply the rotation the replayed step performed
+  std::swap(L0.role_y, L0.role_prev);
+  return SLH_OK;
+}
+
+slh_status slh_fill_ghosts(slh_ctx* c, int32_t lev, double alpha, int32_t itype, int32_t mode) {
+  if (!c) return fail(SLH_ERR_INVALID_ARG, "fill_ghosts: null ctx");
+  if (lev < 0 || lev >= c->nlevels) return fail(SLH_ERR_STATE, "fill_ghosts: level %d not defined", lev);
+  if (mode != SLH_GHOSTS && mode != SLH_RESTRICT) return fail(SLH_ERR_INVALID_ARG, "fill_ghosts: bad mode");
+  if (mode == SLH_RESTRICT && lev == 0) return fail(SLH_ERR_INVALID_ARG, "fill_ghosts: level 0 has no coarser level");
+  if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(SLH_ERR_INVALID_ARG, "fill_ghosts: alpha outside [0,1]");
+  if (itype != 0 && itype != 2 && itype != 4) return fail(SLH_ERR_INVALID_ARG, "fill_ghosts: interp_type must be 0, 2 or 4");
+  return fill_impl(c, lev, alpha, itype, mode);
+}
+
+slh_status slh_sync(slh_ctx* c) {
+  if (!c) return fail(SLH_ERR_INVALID_ARG, "sync: null ctx");
+  SLH_CUDA(cudaStreamSynchronize(c->stream));
+  int err = 0;
+  SLH_CUDA(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    SLH_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
+    if (err == DERR_TIMEOUT) return fail(SLH_ERR_TIMEOUT, "device: a bounded wait gave up");
+    if (err == DERR_NESTING) return fail(SLH_ERR_DEVICE, "device: ghost prolongation reached a cell the coarser level does not cover");
+    if (err == DERR_RESTRICT) return fail(SLH_ERR_DEVICE, "device: restriction target outside the coarser level");
+    return fail(SLH_ERR_DEVICE, "device error %d", err);
+  }
+  return SLH_OK;
+}
+
+static slh_status diag_pass(slh_ctx* c, int lev, const slh_eom_params& p, uint8_t* tags, bool energy, int* used) {
+  Level& L = c->lev[lev];
+  slh_status st;
+  if ((st = fill_impl(c, lev, 1.0, p.interp_type, SLH_GHOSTS)) != SLH_OK) return st;
+  StageLaunch sl;
+  memset(&sl, 0, sizeof(sl));
+  sl.stage = 0;
+  sl.yin = L.buf[L.role_y];
+  sl.lev = lev;
+  sl.c_stage = 0.0;
+  sl.tags = tags;
+  if (tags) {
+    SLH_CUDA(cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), c->stream));
+    sl.tagcount = c->d_count;
+  }
+  if (energy) {
+    sl.epart = L.d_epart;
+    sl.covered = L.d_covered;
+    sl.cov_shift = ilog2(c->bf / 2);
+    sl.cov_nb = L.ncov;
+  }
+  sl.cur_eta = true;   // diagnostics evaluate at the level's current eta
+  prof_begin(c, SLH_PROF_DIAG, (double)L.lay.nvalid * 4 * elem_size(c));
+  st = launch_stage(c, L, p, sl, used);
+  prof_end(c);
+  return st;
+}
+
+slh_status slh_tag(slh_ctx* c, int32_t lev, uint8_t* tags_dev, int64_t* n_tagged) {
+  if (!c || !tags_dev) return fail(SLH_ERR_INVALID_ARG, "tag: null argument");
+  if (lev < 0 || lev >= c->nlevels) return fail(SLH_ERR_STATE, "tag: level %d not defined", lev);
+  // the winding tags read psi only; the cheapest stencil variant runs them
+  const slh_eom_params p = {1.0, 0.0, 1, 2, 2, 4};
+  int used = 0;
+  slh_status st = diag_pass(c, lev, p, tags_dev, false, &used);
+  if (st != SLH_OK) return st;
+  if (n_tagged) {
+    unsigned long long cnt = 0;
+    SLH_CUDA(cudaMemcpyAsync(&cnt, c->d_count, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+    st = slh_sync(c);
+    if (st != SLH_OK) return st;
+    *n_tagged = (int64_t)cnt;
+  }
+  return SLH_OK;
+}
+
+slh_status slh_tag_blocks(slh_ctx* c, int32_t lev, int32_t nbuf, uint8_t* mask_host) {
+  if (!c || !mask_host) return fail(SLH_ERR_INVALID_ARG, "tag_blocks: null argument");
+  if (lev < 0 || lev >= c->nlevels) return fail(SLH_ERR_STATE, "tag_blocks: level %d not defined", lev);
+  if (nbuf < 0) return fail(SLH_ERR_INVALID_ARG, "tag_blocks: n_error_buf < 0");
+  Level& L = c->lev[lev];
+  if (!L.d_tagtmp) {
+    cudaError_t e = cudaMalloc(&L.d_tagtmp, (size_t)L.lay.nvalid);
+    if (e != cudaSuccess) return fail(SLH_ERR_NOMEM, "tag_blocks: %s", cudaGetErrorString(e));
+  }
+  slh_status st = slh_tag(c, lev, L.d_tagtmp, nullptr);
+  if (st != SLH_OK) return st;
+  const int r = c->bf / 2;
+  const int nb = L.n_dom / r;
+  const size_t nmask = (size_t)nb * nb * nb;
+  if (c->blockmask_cap < nmask) {
+    cudaFree(c->d_blockmask);
+    c->d_blockmask = nullptr;
+    cudaError_t e = cudaMalloc(&c->d_blockmask, nmask);
+    if (e != cudaSuccess) return fail(SLH_ERR_NOMEM, "tag_blocks: %s", cudaGetErrorString(e));
+    c->blockmask_cap = nmask;
+  }
+  SLH_CUDA(cudaMemsetAsync(c->d_blockmask, 0, nmask, c->stream));
+  if ((st = launch_tag_blocks(c, L, L.d_tagtmp, nbuf, r, c->d_blockmask, nb)) != SLH_OK) return st;
+  SLH_CUDA(cudaMemcpyAsync(mask_host, c->d_blockmask, nmask, cudaMemcpyDeviceToHost, c->stream));
+  return slh_sync(c);
+}
+
+slh_status slh_reduce_energy(slh_ctx* c, const slh_eom_params* p, int32_t mode, double out[5]) {
+  if (!c || !out) return fail(SLH_ERR_INVALID_ARG, "reduce_energy: null argument");
+  slh_status st = check_params(p);
+  if (st != SLH_OK) return st;
+  if (c->nlevels < 1) return fail(SLH_ERR_STATE, "reduce_energy: no level defined");
+  double sums[MAX_LEVELS][4];
+  int nl = c->nlevels;
+  if (mode == 1) {
+    Level& L = c->lev[0];
+    if (c->nlevels != 1 || L.fused_energy_ctas <= 0)
+      return fail(SLH_ERR_STATE, "reduce_energy: no fused energy partials (single level, SLH_FUSE_ENERGY)");
+    if ((st = launch_energy_final(c, L.d_epart, L.fused_energy_ctas, c->d_levsum)) != SLH_OK) return st;
+    nl = 1;
+  } else if (mode == 0) {
+    for (int l = 0; l < nl; ++l) {
+      int used = 0;
+      if ((st = diag_pass(c, l, *p, nullptr, true, &used)) != SLH_OK) return st;
+      if ((st = launch_energy_final(c, c->lev[l].d_epart, used, c->d_levsum + 4 * l)) != SLH_OK) return st;
+    }
+  } else {
+    return fail(SLH_ERR_INVALID_ARG, "reduce_energy: mode must be 0 or 1");
+  }
+  SLH_CUDA(cudaMemcpyAsync(sums, c->d_levsum, sizeof(double) * 4 * nl, cudaMemcpyDeviceToHost, c->stream));
+  if ((st = slh_sync(c)) != SLH_OK) return st;
+  double K = 0, G = 0, P = 0, S = 0;
+  for (int l = 0; l < nl; ++l) {
+    const double dx = c->lev[l].dx, vol = dx * dx * dx;
+    K += sums[l][0] * vol;
+    G += sums[l][1] * vol;
+    P += sums[l][2] * vol;
+    S += sums[l][3] * dx;
+  }
+  out[0] = K;
+  out[1] = G;
+  out[2] = P;
+  out[3] = K + G + P;
+  out[4] = S;
+  return SLH_OK;
+}
+
+slh_status slh_profile(slh_ctx* c, int32_t enable, int32_t reset) {
+  if (!c) return fail(SLH_ERR_INVALID_ARG, "profile: null ctx");
+  if (reset) {
+    cudaStreamSynchronize(c->stream);
+    for (auto& r : c->prof_open) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    c->prof_open.clear();
+    for (int k = 0; k < SLH_PROF_NKINDS; ++k) {
+      c->prof_ms[k] = 0;
+      c->prof_n[k] = 0;
+      c->prof_bytes[k] = 0;
+    }
+  }
+  c->prof = enable != 0;
+  return SLH_OK;
+}
+
+slh_status slh_profile_read(slh_ctx* c, int32_t kind, double* ms, int64_t* launches, double* bytes) {
+  if (!c) return fail(SLH_ERR_INVALID_ARG, "profile_read: null ctx");
+  if (kind < 0 || kind >= SLH_PROF_NKINDS) return fail(SLH_ERR_INVALID_ARG, "profile_read: bad kind");
+  SLH_CUDA(cudaStreamSynchronize(c->stream));
+  for (auto& r : c->prof_open) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+      c->prof_ms[r.kind] += t;
+      c->prof_n[r.kind] += 1;
+      c->prof_bytes[r.kind] += r.bytes;
+    }
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  c->prof_open.clear();
+  if (ms) *ms = c->prof_ms[kind];
+  if (launches) *launches = c->prof_n[kind];
+  if (bytes) *bytes = c->prof_bytes[kind];
+  return SLH_OK;
+}
+
+}  // extern "C"

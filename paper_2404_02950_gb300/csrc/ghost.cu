@@ -1,0 +1,303 @@
+// Inter-level transfer (Sec. 2.1): ghost fill of a level's psi components
+// from its own boxes (periodic wrap) or, where no box of the level covers a
+// ghost cell, by ratio-2 prolongation of the coarser level interpolated in
+// time; restriction of a fine level onto the covered coarse cells; and the
+// small kernel that advances the per-level conformal time.
+#include "slh_internal.cuh"
+
+namespace slh {
+
+template <typename T>
+struct GhostArgs {
+  const BoxDev* boxes;
+  const GhostSlab* slabs;
+  const long long* slab_off;
+  int nslabs;
+  long long total;
+  T* y;
+  int gl;
+  const int* bmap;
+  int bshift, nbd, ndom;
+  // coarser level
+  const BoxDev* cboxes;
+  const T* cold;
+  const T* cnew;
+  const int* cbmap;
+  int cbshift, cnbd, cndom;
+  double alpha;
+  int itype;
+  int* err;
+};
+
+__device__ __forceinline__ int wrapi(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+__device__ __forceinline__ long long cell_index(const BoxDev& B, int gl, int x, int y, int z) {
+  // valid-relative (x, y, z), may lie in the ghost shell
+  return B.off + ((long long)(z + gl) * B.pny + (y + gl)) * B.pitch + (x + XPAD);
+}
+
+// 1D prolongation weights for offsets -2..2 (type 4: fine-cell average of
+// the quartic matching five coarse averages; type 2: quadratic through
+// three coarse centres evaluated at the fine centre; type 0: parent value).
+// child 0 is the lower half of the coarse cell, child 1 the upper half.
+__device__ __forceinline__ double pw(int itype, int child, int off) {
+  if (itype == 4) {
+    const int j = child == 0 ? off : -off;  // child 1 is the mirror image
+    switch (j) {
+      case -2: return -3.0 / 128.0;
+      case -1: return 11.0 / 64.0;
+      case 0: return 1.0;
+      case 1: return -11.0 / 64.0;
+      default: return 3.0 / 128.0;
+    }
+  }
+  if (itype == 2) {
+    const int j = child == 0 ? off : -off;
+    switch (j) {
+      case -1: return 5.0 / 32.0;
+      case 0: return 15.0 / 16.0;
+      case 1: return -3.0 / 32.0;
+      default: return 0.0;
+    }
+  }
+  return off == 0 ? 1.0 : 0.0;
+}
+
+template <typename T>
+__global__ void ghost_kernel(const GhostArgs<T> A) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < A.total; t += stride) {
+    // slab lookup (binary search over prefix offsets)
+    int lo = 0, hi = A.nslabs - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (A.slab_off[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const GhostSlab S = A.slabs[lo];
+    const long long loc = t - A.slab_off[lo];
+    const int i = (int)(loc % S.e[0]);
+    const int j = (int)((loc / S.e[0]) % S.e[1]);
+    const int k = (int)(loc / ((long long)S.e[0] * S.e[1]));
+    const BoxDev B = A.boxes[S.box];
+    const int rx = S.s[0] + i, ry = S.s[1] + j, rz = S.s[2] + k;
+    const int wx = wrapi(B.lo[0] + rx, A.ndom), wy = wrapi(B.lo[1] + ry, A.ndom), wz = wrapi(B.lo[2] + rz, A.ndom);
+    const long long dst = cell_index(B, A.gl, rx, ry, rz);
+    const int own = A.bmap[((long long)(wz >> A.bshift) * A.nbd + (wy >> A.bshift)) * A.nbd + (wx >> A.bshift)];
+    if (own >= 0) {
+      const BoxDev Sb = A.boxes[own];
+      const long long src = cell_index(Sb, A.gl, wx - Sb.lo[0], wy - Sb.lo[1], wz - Sb.lo[2]);
+      A.y[dst] = A.y[src];
+      A.y[dst + B.cs] = A.y[src + Sb.cs];
+      continue;
+    }
+    if (A.cboxes == nullptr) {
+      atomicCAS(A.err, 0, DERR_NESTING);
+      continue;
+    }
+    // prolongation from the coarser level at time fraction alpha
+    const int Px = wx >> 1, Py = wy >> 1, Pz = wz >> 1;
+    const int cx = wx & 1, cy = wy & 1, cz = wz & 1;
+    const int rad = A.itype == 4 ? 2 : (A.itype == 2 ? 1 : 0);
+    const double al = A.alpha, bl = 1.0 - A.alpha;
+    double acc0 = 0.0, acc1 = 0.0;
+    bool bad = false;
+    for (int oz = -rad; oz <= rad; ++oz) {
+      const double wzv = pw(A.itype, cz, oz);
+      const int qz = wrapi(Pz + oz, A.cndom);
+      for (int oy = -rad; oy <= rad; ++oy) {
+        const double wyv = pw(A.itype, cy, oy);
+        const int qy = wrapi(Py + oy, A.cndom);
+        for (int ox = -rad; ox <= rad; ++ox) {
+          const double wxv = pw(A.itype, cx, ox);
+          const int qx = wrapi(Px + ox, A.cndom);
+          const int cown = A.cbmap[((long long)(qz >> A.cbshift) * A.cnbd + (qy >> A.cbshift)) * A.cnbd + (qx >> A.cbshift)];
+          if (cown < 0) {
+            bad = true;
+            continue;
+          }
+          const BoxDev C = A.cboxes[cown];
+          const long long ci = cell_index(C, A.gl, qx - C.lo[0], qy - C.lo[1], qz - C.lo[2]);
+          const double v0 = bl * (double)A.cold[ci] + al * (double)A.cnew[ci];
+          const double v1 = bl * (double)A.cold[ci + C.cs] + al * (double)A.cnew[ci + C.cs];
+          const double wgt = wzv * wyv * wxv;
+          acc0 += wgt * v0;
+          acc1 += wgt * v1;
+        }
+      }
+    }
+    if (bad) atomicCAS(A.err, 0, DERR_NESTING);
+    A.y[dst] = (T)acc0;
+    A.y[dst + B.cs] = (T)acc1;
+  }
+}
+
+template <typename T>
+static slh_status ghosts_t(slh_ctx* c, int lev, int role, double alpha, int itype) {
+  Level& L = c->lev[lev];
+  if (L.nghost_cells == 0) return SLH_OK;
+  GhostArgs<T> A;
+  A.boxes = L.d_boxes;
+  A.slabs = L.d_slabs;
+  A.slab_off = L.d_slab_off;
+  A.nslabs = L.nslabs;
+  A.total = L.nghost_cells;
+  A.y = static_cast<T*>(L.buf[role]);
+  A.gl = c->g;
+  A.bmap = L.d_bmap;
+  int sh = 0;
+  while ((1 << sh) < c->bf) ++sh;
+  A.bshift = sh;
+  A.nbd = L.nb_dom;
+  A.ndom = L.n_dom;
+  if (lev > 0) {
+    Level& C = c->lev[lev - 1];
+    A.cboxes = C.d_boxes;
+    A.cold = static_cast<const T*>(C.buf[C.role_prev]);
+    A.cnew = static_cast<const T*>(C.buf[C.role_y]);
+    A.cbmap = C.d_bmap;
+    A.cbshift = sh;
+    A.cnbd = C.nb_dom;
+    A.cndom = C.n_dom;
+  } else {
+    A.cboxes = nullptr;
+    A.cold = A.cnew = nullptr;
+    A.cbmap = nullptr;
+    A.cbshift = 0;
+    A.cnbd = A.cndom = 0;
+  }
+  A.alpha = alpha;
+  A.itype = itype;
+  A.err = c->d_err;
+  const int threads = 256;
+  long long blocks = (L.nghost_cells + threads - 1) / threads;
+  const long long cap = (long long)c->num_sms * 8;
+  if (blocks > cap) blocks = cap;
+  ghost_kernel<T><<<(int)blocks, threads, 0, c->stream>>>(A);
+  SLH_CUDA(cudaGetLastError());
+  return SLH_OK;
+}
+
+slh_status launch_ghosts(slh_ctx* c, int lev, int role, double alpha, int itype) {
+  if (itype != 0 && itype != 2 && itype != 4)
+    return fail(SLH_ERR_INVALID_ARG, "interp_type must be 0, 2 or 4 (got %d)", itype);
+  return c->prec == SLH_F64 ? ghosts_t<double>(c, lev, role, alpha, itype)
+                            : ghosts_t<float>(c, lev, role, alpha, itype);
+}
+
+// ---------------------------------------------------------------------------
+// restriction: coarse cell = mean of its 8 children (FP64 sum, order x, y, z)
+
+template <typename T>
+struct RestrictArgs {
+  const BoxDev* fboxes;
+  const RestrictItem* items;
+  const long long* off;
+  int nitems;
+  long long total;
+  const T* fy;
+  const BoxDev* cboxes;
+  T* cy;
+  const int* cbmap;
+  int cbshift, cnbd;
+  int gl;
+  int* err;
+};
+
+template <typename T>
+__global__ void restrict_kernel(const RestrictArgs<T> A) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < A.total; t += stride) {
+    int lo = 0, hi = A.nitems - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (A.off[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const RestrictItem I = A.items[lo];
+    const long long loc = t - A.off[lo];
+    const int i = (int)(loc % I.n[0]);
+    const int j = (int)((loc / I.n[0]) % I.n[1]);
+    const int k = (int)(loc / ((long long)I.n[0] * I.n[1]));
+    const BoxDev F = A.fboxes[I.fbox];
+    const int gx = (F.lo[0] >> 1) + i, gy = (F.lo[1] >> 1) + j, gz = (F.lo[2] >> 1) + k;
+    const int own = A.cbmap[((long long)(gz >> A.cbshift) * A.cnbd + (gy >> A.cbshift)) * A.cnbd + (gx >> A.cbshift)];
+    if (own < 0) {
+      atomicCAS(A.err, 0, DERR_RESTRICT);
+      continue;
+    }
+    const BoxDev C = A.cboxes[own];
+    const long long dsti = cell_index(C, A.gl, gx - C.lo[0], gy - C.lo[1], gz - C.lo[2]);
+    const long long f000 = cell_index(F, A.gl, 2 * i, 2 * j, 2 * k);
+    const long long sy = F.pitch, sz = (long long)F.pny * F.pitch;
+#pragma unroll
+    for (int c = 0; c < NCOMP; ++c) {
+      const T* f = A.fy + f000 + c * F.cs;
+      double s = (double)f[0];
+      s += (double)f[1];
+      s += (double)f[sy];
+      s += (double)f[sy + 1];
+      s += (double)f[sz];
+      s += (double)f[sz + 1];
+      s += (double)f[sz + sy];
+      s += (double)f[sz + sy + 1];
+      A.cy[dsti + c * C.cs] = (T)(s * 0.125);
+    }
+  }
+}
+
+template <typename T>
+static slh_status restrict_t(slh_ctx* c, int fl) {
+  Level& F = c->lev[fl];
+  Level& C = c->lev[fl - 1];
+  if (F.nrcells == 0) return SLH_OK;
+  RestrictArgs<T> A;
+  A.fboxes = F.d_boxes;
+  A.items = F.d_ritems;
+  A.off = F.d_roff;
+  A.nitems = F.nritems;
+  A.total = F.nrcells;
+  A.fy = static_cast<const T*>(F.buf[F.role_y]);
+  A.cboxes = C.d_boxes;
+  A.cy = static_cast<T*>(C.buf[C.role_y]);
+  A.cbmap = C.d_bmap;
+  int sh = 0;
+  while ((1 << sh) < c->bf) ++sh;
+  A.cbshift = sh;
+  A.cnbd = C.nb_dom;
+  A.gl = c->g;
+  A.err = c->d_err;
+  const int threads = 256;
+  long long blocks = (F.nrcells + threads - 1) / threads;
+  const long long cap = (long long)c->num_sms * 8;
+  if (blocks > cap) blocks = cap;
+  restrict_kernel<T><<<(int)blocks, threads, 0, c->stream>>>(A);
+  SLH_CUDA(cudaGetLastError());
+  return SLH_OK;
+}
+
+slh_status launch_restrict(slh_ctx* c, int fine_lev) {
+  return c->prec == SLH_F64 ? restrict_t<double>(c, fine_lev) : restrict_t<float>(c, fine_lev);
+}
+
+// ---------------------------------------------------------------------------
+// conformal time bookkeeping (FP64 on the device):
+//   level 0: eta_start = eta;  eta = eta_start + dt_0
+//   level l: eta_start = eta_start[l-1] + sub * dt_l;  eta = eta_start + dt_l
+
+__global__ void time_begin_kernel(double* t, int lev, int sub, double dt_l) {
+  double es;
+  if (lev == 0) es = t[0];
+  else es = t[2 * (lev - 1) + 1] + (double)sub * dt_l;
+  t[2 * lev + 1] = es;
+  t[2 * lev] = es + dt_l;
+}
+
+slh_status launch_time_begin(slh_ctx* c, int lev, int sub, double dt_l) {
+  time_begin_kernel<<<1, 1, 0, c->stream>>>(c->d_time, lev, sub, dt_l);
+  SLH_CUDA(cudaGetLastError());
+  return SLH_OK;
+}
+
+}  // namespace slh

@@ -1,0 +1,279 @@
+// Host-side regrid (Sec. 2.2-2.3): buffered tags -> blocks -> nested
+// Berger-Rigoutsos style clustering -> boxes of the next finer level.
+// Deterministic: every choice is made by integer comparisons with fixed tie
+// breaks, so the box list depends only on the tag mask.
+#include <algorithm>
+#include <cstdint>
+#include <cstdlib>
+#include <vector>
+
+#include "slh_internal.cuh"
+
+namespace slh {
+namespace {
+
+struct Grid {
+  int nx = 0, ny = 0, nz = 0;
+  std::vector<uint8_t> v;
+  Grid() = default;
+  Grid(int x, int y, int z) : nx(x), ny(y), nz(z), v((size_t)x * y * z, 0) {}
+  uint8_t& at(int x, int y, int z) { return v[((size_t)z * ny + y) * nx + x]; }
+  uint8_t at(int x, int y, int z) const { return v[((size_t)z * ny + y) * nx + x]; }
+};
+
+// cube dilation with periodic wrap, one axis at a time
+Grid dilate(const Grid& in, int nbuf) {
+  Grid cur = in;
+  for (int axis = 0; axis < 3 && nbuf > 0; ++axis) {
+    Grid nxt(cur.nx, cur.ny, cur.nz);
+    const int n = axis == 0 ? cur.nx : axis == 1 ? cur.ny : cur.nz;
+    for (int z = 0; z < cur.nz; ++z)
+      for (int y = 0; y < cur.ny; ++y)
+        for (int x = 0; x < cur.nx; ++x) {
+          if (!cur.at(x, y, z)) continue;
+          for (int s = -nbuf; s <= nbuf; ++s) {
+            int p[3] = {x, y, z};
+            p[axis] = ((p[axis] + s) % n + n) % n;
+            nxt.at(p[0], p[1], p[2]) = 1;
+          }
+        }
+    cur.v.swap(nxt.v);
+  }
+  return cur;
+}
+
+// inclusive 3D prefix sums for O(1) box counts
+struct Prefix {
+  int nx, ny, nz;
+  std::vector<int64_t> s;
+  explicit Prefix(const Grid& g) : nx(g.nx), ny(g.ny), nz(g.nz), s((size_t)(nx + 1) * (ny + 1) * (nz + 1), 0) {
+    for (int z = 0; z < nz; ++z)
+      for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x)
+          S(x + 1, y + 1, z + 1) = g.at(x, y, z) + S(x, y + 1, z + 1) + S(x + 1, y, z + 1) + S(x + 1, y + 1, z) -
+                                   S(x, y, z + 1) - S(x, y + 1, z) - S(x + 1, y, z) + S(x, y, z);
+  }
+  int64_t& S(int x, int y, int z) { return s[((size_t)z * (ny + 1) + y) * (nx + 1) + x]; }
+  int64_t S(int x, int y, int z) const { return s[((size_t)z * (ny + 1) + y) * (nx + 1) + x]; }
+  int64_t count(const int lo[3], const int hi[3]) const {
+    const int x0 = lo[0], y0 = lo[1], z0 = lo[2], x1 = hi[0] + 1, y1 = hi[1] + 1, z1 = hi[2] + 1;
+    return S(x1, y1, z1) - S(x0, y1, z1) - S(x1, y0, z1) - S(x1, y1, z0) + S(x0, y0, z1) + S(x0, y1, z0) +
+           S(x1, y0, z0) - S(x0, y0, z0);
+  }
+};
+
+struct BR {
+  const Grid& M;
+  const Prefix& PM;
+  const Prefix& PA;
+  int max_blocks;
+  std::vector<slh_box> out;
+
+  BR(const Grid& m, const Prefix& pm, const Prefix& pa, int mb) : M(m), PM(pm), PA(pa), max_blocks(mb) {}
+
+  void signatures(const int lo[3], const int hi[3], std::vector<int64_t> sig[3]) const {
+    for (int d = 0; d < 3; ++d) sig[d].assign(hi[d] - lo[d] + 1, 0);
+    for (int z = lo[2]; z <= hi[2]; ++z)
+      for (int y = lo[1]; y <= hi[1]; ++y)
+        for (int x = lo[0]; x <= hi[0]; ++x)
+          if (M.at(x, y, z)) {
+            ++sig[0][x - lo[0]];
+            ++sig[1][y - lo[1]];
+            ++sig[2][z - lo[2]];
+          }
+  }
+
+  // shrink to the tags' bounding box; false when the box holds no tag
+  bool shrink(int lo[3], int hi[3]) const {
+    if (PM.count(lo, hi) == 0) return false;
+    std::vector<int64_t> sig[3];
+    signatures(lo, hi, sig);
+    for (int d = 0; d < 3; ++d) {
+      int a = 0, b = (int)sig[d].size() - 1;
+      while (sig[d][a] == 0) ++a;
+      while (sig[d][b] == 0) --b;
+      const int base = lo[d];
+      lo[d] = base + a;
+      hi[d] = base + b;
+    }
+    return true;
+  }
+
+  void choose_cut(const int lo[3], const int hi[3], int* axis, int* cut) const {
+    std::vector<int64_t> sig[3];
+    signatures(lo, hi, sig);
+    int n[3];
+    for (int d = 0; d < 3; ++d) n[d] = hi[d] - lo[d] + 1;
+    // a. zero-signature plane nearest the centre
+    bool found = false;
+    long bk0 = 0;
+    int bd = 0, bc = 0;
+    for (int d = 0; d < 3; ++d)
+      for (int c = 1; c <= n[d] - 2; ++c)
+        if (sig[d][c] == 0) {
+          const long k0 = std::labs(2L * c - n[d]);
+          if (!found || k0 < bk0 || (k0 == bk0 && (d < bd || (d == bd && c < bc)))) {
+            found = true;
+            bk0 = k0;
+            bd = d;
+            bc = c;
+          }
+        }
+    if (found) {
+      *axis = bd;
+      *cut = bc;
+      return;
+    }
+    // b. strongest sign change of the second difference
+    long long bs = -1;
+    for (int d = 0; d < 3; ++d) {
+      if (n[d] < 4) continue;
+      std::vector<long long> lap(n[d], 0);
+      for (int i = 1; i <= n[d] - 2; ++i) lap[i] = sig[d][i - 1] - 2 * sig[d][i] + sig[d][i + 1];
+      for (int i = 1; i <= n[d] - 3; ++i) {
+        if ((lap[i] < 0 && lap[i + 1] > 0) || (lap[i] > 0 && lap[i + 1] < 0)) {
+          const int c = i + 1;
+          const long long st = std::llabs(lap[i + 1] - lap[i]);
+          const long k0 = std::labs(2L * c - n[d]);
+          bool better = false;
+          if (!found || st > bs) better = true;
+          else if (st == bs) {
+            if (k0 < bk0) better = true;
+            else if (k0 == bk0 && (d < bd || (d == bd && c < bc))) better = true;
+          }
+          if (better) {
+            found = true;
+            bs = st;
+            bk0 = k0;
+            bd = d;
+            bc = c;
+          }
+        }
+      }
+    }
+    if (found) {
+      *axis = bd;
+      *cut = bc;
+      return;
+    }
+    // c. halve the longest side (lowest axis on ties)
+    int d = 0;
+    for (int q = 1; q < 3; ++q)
+      if (n[q] > n[d]) d = q;
+    *axis = d;
+    *cut = n[d] / 2;
+  }
+
+  void rec(int lo_in[3], int hi_in[3]) {
+    int lo[3] = {lo_in[0], lo_in[1], lo_in[2]}, hi[3] = {hi_in[0], hi_in[1], hi_in[2]};
+    if (!shrink(lo, hi)) return;
+    int64_t vol = 1;
+    int mx = 0;
+    for (int d = 0; d < 3; ++d) {
+      const int n = hi[d] - lo[d] + 1;
+      vol *= n;
+      mx = std::max(mx, n);
+    }
+    const int64_t ntag = PM.count(lo, hi);
+    const bool ok = 10 * ntag >= 7 * vol && mx <= max_blocks && PA.count(lo, hi) == vol;
+    if (ok) {
+      slh_box b;
+      for (int d = 0; d < 3; ++d) {
+        b.lo[d] = lo[d];
+        b.hi[d] = hi[d];
+      }
+      out.push_back(b);
+      return;
+    }
+    int axis = 0, cut = 0;
+    choose_cut(lo, hi, &axis, &cut);
+    int lhi[3] = {hi[0], hi[1], hi[2]};
+    lhi[axis] = lo[axis] + cut - 1;
+    int rlo[3] = {lo[0], lo[1], lo[2]};
+    rlo[axis] = lo[axis] + cut;
+    rec(lo, lhi);
+    rec(rlo, hi);
+  }
+};
+
+}  // namespace
+
+slh_status regrid_boxes_impl(const uint8_t* tags, const int dims[3], int bf, int nbuf, int max_box,
+                             const slh_box* parent, int nparent, std::vector<slh_box>* out) {
+  if (!tags || !dims || !out) return fail(SLH_ERR_INVALID_ARG, "regrid: null argument");
+  if (bf < 2 || (bf & (bf - 1))) return fail(SLH_ERR_INVALID_ARG, "regrid: blocking factor must be a power of two >= 2");
+  if (max_box < bf || max_box % bf) return fail(SLH_ERR_INVALID_ARG, "regrid: max_box must be a positive multiple of the blocking factor");
+  if (nbuf < 0) return fail(SLH_ERR_INVALID_ARG, "regrid: n_error_buf < 0");
+  const int r = bf / 2;
+  for (int d = 0; d < 3; ++d)
+    if (dims[d] <= 0 || dims[d] % r) return fail(SLH_ERR_INVALID_ARG, "regrid: dims must be positive multiples of blocking_factor/2");
+  Grid T(dims[0], dims[1], dims[2]);
+  for (size_t i = 0; i < T.v.size(); ++i) T.v[i] = tags[i] ? 1 : 0;
+  Grid D = dilate(T, nbuf);
+  const int bx = dims[0] / r, by = dims[1] / r, bz = dims[2] / r;
+  Grid B(bx, by, bz);
+  for (int z = 0; z < dims[2]; ++z)
+    for (int y = 0; y < dims[1]; ++y)
+      for (int x = 0; x < dims[0]; ++x)
+        if (D.at(x, y, z)) B.at(x / r, y / r, z / r) = 1;
+  Grid A(bx, by, bz);
+  if (parent == nullptr || nparent == 0) {
+    std::fill(A.v.begin(), A.v.end(), 1);
+  } else {
+    Grid P(bx, by, bz);
+    for (int i = 0; i < nparent; ++i) {
+      const slh_box& pb = parent[i];
+      for (int d = 0; d < 3; ++d) {
+        if (pb.lo[d] % r || (pb.hi[d] + 1) % r || pb.lo[d] < 0 || pb.hi[d] >= dims[d] || pb.hi[d] < pb.lo[d])
+          return fail(SLH_ERR_INVALID_ARG, "regrid: parent box %d not aligned to blocking_factor/2 or outside dims", i);
+      }
+      for (int z = pb.lo[2] / r; z < (pb.hi[2] + 1) / r; ++z)
+        for (int y = pb.lo[1] / r; y < (pb.hi[1] + 1) / r; ++y)
+          for (int x = pb.lo[0] / r; x < (pb.hi[0] + 1) / r; ++x) P.at(x, y, z) = 1;
+    }
+    Grid notP(bx, by, bz);
+    for (size_t i = 0; i < P.v.size(); ++i) notP.v[i] = P.v[i] ? 0 : 1;
+    Grid G = dilate(notP, 1);
+    for (size_t i = 0; i < G.v.size(); ++i) A.v[i] = G.v[i] ? 0 : 1;
+  }
+  Grid M(bx, by, bz);
+  for (size_t i = 0; i < M.v.size(); ++i) M.v[i] = (B.v[i] && A.v[i]) ? 1 : 0;
+  Prefix PM(M), PA(A);
+  BR br(M, PM, PA, max_box / bf);
+  int lo[3] = {0, 0, 0}, hi[3] = {bx - 1, by - 1, bz - 1};
+  br.rec(lo, hi);
+  out->clear();
+  for (const slh_box& b : br.out) {
+    slh_box f;
+    for (int d = 0; d < 3; ++d) {
+      f.lo[d] = b.lo[d] * bf;
+      f.hi[d] = (b.hi[d] + 1) * bf - 1;
+    }
+    out->push_back(f);
+  }
+  std::sort(out->begin(), out->end(), [](const slh_box& a, const slh_box& b) {
+    if (a.lo[2] != b.lo[2]) return a.lo[2] < b.lo[2];
+    if (a.lo[1] != b.lo[1]) return a.lo[1] < b.lo[1];
+    return a.lo[0] < b.lo[0];
+  });
+  return SLH_OK;
+}
+
+}  // namespace slh
+
+extern "C" slh_status slh_regrid_boxes(const uint8_t* tags_host, const int32_t dims[3], int32_t blocking_factor,
+                                       int32_t n_error_buf, int32_t max_box, const slh_box* parent,
+                                       int32_t nparent, slh_box* out, int32_t cap, int32_t* nout) {
+  if (!nout) return slh::fail(SLH_ERR_INVALID_ARG, "regrid: nout is null");
+  if (nparent < 0) return slh::fail(SLH_ERR_INVALID_ARG, "regrid: nparent < 0");
+  int d3[3] = {dims ? dims[0] : 0, dims ? dims[1] : 0, dims ? dims[2] : 0};
+  std::vector<slh_box> boxes;
+  slh_status st = slh::regrid_boxes_impl(tags_host, dims ? d3 : nullptr, blocking_factor, n_error_buf, max_box,
+                                         parent, nparent, &boxes);
+  if (st != SLH_OK) return st;
+  *nout = (int32_t)boxes.size();
+  if ((int32_t)boxes.size() > cap || (!out && !boxes.empty()))
+    return slh::fail(SLH_ERR_OUT_OF_RANGE, "regrid: %d boxes exceed capacity %d", (int)boxes.size(), cap);
+  for (size_t i = 0; i < boxes.size(); ++i) out[i] = boxes[i];
+  return SLH_OK;
+}

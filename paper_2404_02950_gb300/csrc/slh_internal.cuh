@@ -1,0 +1,180 @@
+// Internal structures of the GB300 AMR stepper (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "slh.h"
+
+namespace slh {
+
+// x padding in front of the first valid cell of every row: keeps the first
+// valid cell 16-byte aligned for FP32 and FP64 and is >= every ghost width.
+constexpr int XPAD = 4;
+constexpr int NCOMP = 4;
+constexpr int MAX_LEVELS = 8;
+
+// Per-box geometry as the kernels see it.
+struct BoxDev {
+  int lo[3];        // first valid cell, level index space
+  int n[3];         // valid extents
+  int pitch;        // padded x row length (elements)
+  int pny, pnz;     // padded y / z extents (n + 2 g)
+  int pad_;
+  long long off;    // element offset of component 0
+  long long cs;     // component stride (elements)
+  long long voff;   // offset of the box's first valid cell in dense valid-cell arrays
+};
+
+// One rectangular piece of a box's ghost shell: cells start..start+ext-1 in
+// valid-relative coordinates (-g .. n+g-1).
+struct GhostSlab {
+  int box;
+  int s[3];
+  int e[3];
+};
+
+// Restriction work: one fine box, its coarse region.
+struct RestrictItem {
+  int fbox;
+  int n[3];         // coarse extents = fine extents / 2
+};
+
+struct Layout {
+  std::vector<BoxDev> boxes;
+  long long total = 0;
+  long long nvalid = 0;
+};
+
+bool make_layout(int g, const slh_box* boxes, int nboxes, Layout* out, std::string* why);
+
+struct Level {
+  bool defined = false;
+  int n_dom = 0;                 // cells per axis of the level's periodic domain
+  double dx = 0, dtfac = 1;      // dt_l = dt0 * dtfac
+  std::vector<slh_box> boxes;
+  Layout lay;
+  void* buf[SLH_NBUF] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int role_y = SLH_BUF_Y;        // buffer currently holding y_n
+  int role_prev = SLH_BUF_YB;    // buffer holding the previous state
+  uint8_t* tags_dev = nullptr;   // caller-owned (fused tags)
+  // device metadata (owned)
+  BoxDev* d_boxes = nullptr;
+  int* d_bmap = nullptr;         // block owner map, blocks of bf cells
+  std::vector<int> h_bmap;       // host mirror of the block owner map
+  int nb_dom = 0;
+  GhostSlab* d_slabs = nullptr;
+  long long* d_slab_off = nullptr;
+  int nslabs = 0;
+  long long nghost_cells = 0;
+  int4* d_items = nullptr;       // stage work items (box, x0, y0, z0)
+  int nitems = 0;
+  int tile_x = 32, tile_y = 8, zlen = 64;
+  uint8_t* d_covered = nullptr;  // covered by the finer level, blocks of bf/2 cells
+  int ncov = 0;
+  RestrictItem* d_ritems = nullptr;  // restriction of this level onto lev-1
+  long long* d_roff = nullptr;
+  int nritems = 0;
+  long long nrcells = 0;
+  double* d_epart = nullptr;     // energy partials (per CTA x 4)
+  int epart_cap = 0;
+  int fused_energy_ctas = 0;     // CTAs of the last fused-energy stage 1
+  uint8_t* d_tagtmp = nullptr;   // internal tags for slh_tag_blocks
+};
+
+struct ProfRec {
+  cudaEvent_t a, b;
+  int kind;
+  double bytes;
+};
+
+}  // namespace slh
+
+struct slh_ctx {
+  int n0 = 0;
+  double dx0 = 0;
+  int g = 0;
+  int bf = 0;
+  int prec = SLH_F64;
+  int max_levels = 1;
+  int nlevels = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  slh::Level lev[slh::MAX_LEVELS];
+  double* d_time = nullptr;      // [2*MAX_LEVELS]: eta[l], eta_start[l]
+  int* d_err = nullptr;          // latched device error code
+  double* d_levsum = nullptr;    // [MAX_LEVELS][4] per-level energy sums
+  unsigned long long* d_count = nullptr;
+  uint8_t* d_blockmask = nullptr;
+  size_t blockmask_cap = 0;
+  // profiling
+  bool prof = false;
+  std::vector<slh::ProfRec> prof_open;
+  double prof_ms[SLH_PROF_NKINDS] = {0};
+  long long prof_n[SLH_PROF_NKINDS] = {0};
+  double prof_bytes[SLH_PROF_NKINDS] = {0};
+  // CUDA graph of one coarse step
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  unsigned long long graph_key = 0;
+  int graph_parity = 0;
+};
+
+namespace slh {
+
+// error reporting (thread-local message)
+slh_status fail(slh_status code, const char* fmt, ...);
+slh_status cuda_fail(cudaError_t e, const char* what);
+
+#define SLH_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return slh::cuda_fail(e_, #call); \
+  } while (0)
+
+// device error codes latched in ctx->d_err
+constexpr int DERR_NESTING = 1;   // prolongation stencil reached an uncovered coarse cell
+constexpr int DERR_RESTRICT = 2;  // fine cell projected outside the coarse level
+constexpr int DERR_TIMEOUT = 3;   // a bounded wait gave up
+
+// launchers (stage.cu, ghost.cu, diag.cu)
+struct StageLaunch {
+  int stage;            // 0 = diagnostics only, 1..4
+  const void* yin;
+  const void* yn;
+  void* dacc;
+  void* yout;
+  void* comp;
+  double c_stage;       // c_s * dt
+  double ha, hb;        // a_{s+1} dt, b_s dt
+  uint8_t* tags;
+  double* epart;        // per CTA x 4 (kin, grad, pot, pierced count)
+  unsigned long long* tagcount;
+  const uint8_t* covered;
+  int cov_shift, cov_nb;
+  int lev;
+  bool cur_eta;         // evaluate at eta[lev] (diagnostics) instead of eta_start[lev] + c_stage
+};
+slh_status launch_stage(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s,
+                        int* ctas_used);
+int stage_grid(slh_ctx* c, Level& L, int order);
+
+slh_status launch_ghosts(slh_ctx* c, int lev, int role, double alpha, int itype);
+slh_status launch_restrict(slh_ctx* c, int fine_lev);
+slh_status launch_energy_final(slh_ctx* c, const double* epart, int n, double* out4);
+slh_status launch_tag_blocks(slh_ctx* c, Level& L, const uint8_t* tags, int nbuf, int r,
+                             uint8_t* mask, int nb);
+slh_status launch_time_begin(slh_ctx* c, int lev, int sub, double dt_l);
+
+// profiling helpers
+void prof_begin(slh_ctx* c, int kind, double bytes);
+void prof_end(slh_ctx* c);
+
+// host regrid
+slh_status regrid_boxes_impl(const uint8_t* tags, const int dims[3], int bf, int nbuf, int max_box,
+                             const slh_box* parent, int nparent, std::vector<slh_box>* out);
+
+}  // namespace slh

@@ -1,0 +1,201 @@
+"""GPU vs oracle parity on uniform periodic lattices (one level): the fused
+RK4 stage kernels (Laplacian + RHS of Sec. 3.1 + RK4), the fused and
+standalone winding tags, and the energy reduction.
+
+Tolerances: FP64 fields within 1e-12 relative L2 of the oracle after 100
+steps (the two sides differ only in rounding order and FMA contraction);
+tags bit-exact on identical snapshots; FP32 + Kahan fields within 1e-4
+relative L2 of the FP64 oracle and string length within 1%."""
+import numpy as np
+import pytest
+
+import paper_2404_02950_gb300 as slh
+from oracle import energy as oenergy
+from oracle import rk4 as ork4
+from oracle import winding as owinding
+from paper_2404_02950_gb300 import inputs
+from tests.helpers import download_domain, oparams, rel_l2, tags_domain, uniform_hierarchy, upload
+
+pytestmark = pytest.mark.gpu
+
+# the 64^3 plain-method workload with dx read as 1/8 (dt = dx/4, eta 0.1 -> 3.225)
+N0, DX0, ETA0 = 64, 0.125, 0.1
+DT0 = DX0 / 4
+
+
+def _config0_fields(n=N0, seed=0):
+    return inputs.gaussian_field(n, n / 8.0, seed)
+
+
+def test_config0_f64_100_steps_fields_and_tags():
+    p = slh.EOMParams(order=2)
+    y0 = _config0_fields()
+    h, boxes = uniform_hierarchy(N0, DX0, prec="f64", nghost=1, bf=8, fused_tags=True)
+    upload(h, 0, y0, boxes)
+    h.set_eta(ETA0)
+    op = oparams(p)
+    y, eta = y0, ETA0
+    tag_checks = 0
+    for step in range(100):
+        snap = download_domain(h, 0, boxes, N0) if step % 10 == 0 else None
+        h.rk_step(0, DT0, p, flags=slh.SLH_FUSE_TAG)
+        if snap is not None:
+            gtags = tags_domain(h.levels[0]["tags"].cpu().numpy(), boxes, N0)
+            assert np.array_equal(gtags, owinding.cell_tags_periodic(snap[0], snap[1])), step
+            tag_checks += 1
+        y = ork4.rk4_step_periodic(y, eta, DT0, DX0, op)
+        eta = eta + DT0
+    g = download_domain(h, 0, boxes, N0)
+    for c in range(4):
+        assert rel_l2(g[c], y[c]) <= 1e-12, (c, rel_l2(g[c], y[c]))
+    assert h.get_eta(0) == eta
+    assert tag_checks == 10
+
+
+@pytest.mark.parametrize("order", [4, 6])
+def test_high_order_f64_multibox_ragged(order):
+    """A 48^3 level split into uneven boxes (ragged tiles, same-level ghost
+    copies across boxes and the periodic wrap)."""
+    n, dx = 48, 0.2
+    boxes = [((0, 0, 0), (15, 47, 47)), ((16, 0, 0), (47, 15, 47)), ((16, 16, 0), (47, 47, 15)),
+             ((16, 16, 16), (47, 47, 47))]
+    p = slh.EOMParams(order=order, lam=1.0, a=0.05)
+    y0 = inputs.gaussian_field(n, 6.0, seed=3)
+    y0 = (y0[0], y0[1], 0.3 * y0[1], -0.2 * y0[0])
+    h, _ = uniform_hierarchy(n, dx, prec="f64", nghost=3, bf=16, boxes=boxes)
+    upload(h, 0, y0, boxes)
+    h.set_eta(0.7)
+    y, eta = y0, 0.7
+    for _ in range(10):
+        h.rk_step(0, 0.05, p)
+        y = ork4.rk4_step_periodic(y, eta, 0.05, dx, oparams(p))
+        eta += 0.05
+    g = download_domain(h, 0, boxes, n)
+    for c in range(4):
+        assert rel_l2(g[c], y[c]) <= 1e-12
+
+
+def test_frozen_friction_free_energy_conservation_on_gpu():
+    n, dx = 32, 0.25
+    p = slh.EOMParams(order=4, friction=False, eta_power=0, lam=1.0)
+    y0 = inputs.gaussian_field(n, 4.0, seed=9)
+    h, boxes = uniform_hierarchy(n, dx, prec="f64")
+    upload(h, 0, y0, boxes)
+    h.set_eta(1.0)
+    E0 = h.reduce_energy(p)
+    assert abs(E0[3] - oenergy.energy_periodic(y0, 1.0, dx, oparams(p))[3]) <= 1e-12 * abs(E0[3])
+    drift = []
+    for dt in (0.04, 0.02):
+        upload(h, 0, y0, boxes)
+        for _ in range(int(round(0.8 / dt))):
+            h.rk_step(0, dt, p)
+        drift.append(abs(h.reduce_energy(p)[3] - E0[3]))
+    assert 10.0 < drift[0] / drift[1] < 40.0, drift
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_energy_and_tags_match_oracle_on_snapshot(prec):
+    n, dx = 40, 0.125
+    p = slh.EOMParams(order=6, a=0.1)
+    y0 = inputs.gaussian_field(n, 5.0, seed=1)
+    y0 = (y0[0], y0[1], 0.5 * y0[0], 0.25 * y0[1])
+    boxes = [((0, 0, 0), (39, 39, 19)), ((0, 0, 20), (39, 39, 39))]
+    h, _ = uniform_hierarchy(n, dx, prec=prec, nghost=3, bf=4, boxes=boxes, fused_tags=True)
+    upload(h, 0, y0, boxes)
+    h.set_eta(2.5)
+    snap = download_domain(h, 0, boxes, n)      # exactly what the GPU holds (FP32 rounded)
+    E = h.reduce_energy(p)
+    Eo = oenergy.energy_periodic(snap, 2.5, dx, oparams(p))
+    tol = 1e-12 if prec == "f64" else 2e-6
+    for k in range(4):
+        assert abs(E[k] - Eo[k]) <= tol * max(abs(Eo[k]), 1e-300), (k, E[k], Eo[k])
+    assert E[4] == Eo[4]
+    t, cnt = h.tag(0)
+    otags = owinding.cell_tags_periodic(snap[0], snap[1])
+    assert np.array_equal(tags_domain(t.cpu().numpy(), boxes, n), otags)
+    assert cnt == int(otags.sum())
+    # fused energy of stage 1 equals the standalone reduction of the same state
+    h.rk_step(0, 0.01, p, flags=slh.SLH_FUSE_ENERGY)
+    Ef = h.reduce_energy(p, mode=1)
+    for k in range(4):
+        assert abs(Ef[k] - E[k]) <= (1e-13 if prec == "f64" else 2e-6) * abs(E[k])
+    assert Ef[4] == E[4]
+
+
+def test_config0_f32_kahan_within_bounds():
+    p = slh.EOMParams(order=2)
+    y0 = _config0_fields()
+    h, boxes = uniform_hierarchy(N0, DX0, prec="f32", nghost=1, bf=8)
+    upload(h, 0, y0, boxes)
+    h.set_eta(ETA0)
+    y, eta = y0, ETA0
+    for _ in range(100):
+        h.rk_step(0, DT0, p)
+        y = ork4.rk4_step_periodic(y, eta, DT0, DX0, oparams(p))
+        eta += DT0
+    g = download_domain(h, 0, boxes, N0)
+    errs = [rel_l2(g[c], y[c]) for c in range(4)]
+    assert max(errs) <= 1e-4, errs
+    Lg = owinding.string_length_periodic(g[0], g[1], DX0)
+    Lo = owinding.string_length_periodic(y[0], y[1], DX0)
+    assert abs(Lg - Lo) <= 0.01 * Lo
+
+
+def test_graph_replay_matches_direct_steps():
+    n, dx = 32, 0.25
+    p = slh.EOMParams(order=4)
+    y0 = inputs.gaussian_field(n, 4.0, seed=2)
+    ha, boxes = uniform_hierarchy(n, dx, prec="f64")
+    hb, _ = uniform_hierarchy(n, dx, prec="f64")
+    for h in (ha, hb):
+        upload(h, 0, y0, boxes)
+        h.set_eta(0.5)
+    for _ in range(5):
+        ha.advance(0.05, p)
+        hb.advance(0.05, p, flags=slh.SLH_USE_GRAPH)
+    a = ha.get_state(0)
+    b = hb.get_state(0)
+    assert np.array_equal(a, b)
+    assert ha.get_eta(0) == hb.get_eta(0)
+
+
+def _local_rk4_center(y, idx, half, eta, dt, dx, op):
+    """The oracle's RK4 step at one cell from a periodic patch of the global
+    snapshot (the patch is wide enough that its wrap does not reach the centre)."""
+    k, j, i = idx
+    n = y[0].shape[0]
+    rz = np.arange(k - half, k + half + 1) % n
+    ry = np.arange(j - half, j + half + 1) % n
+    rx = np.arange(i - half, i + half + 1) % n
+    patch = tuple(a[np.ix_(rz, ry, rx)] for a in y)
+    out = ork4.rk4_step_periodic(patch, eta, dt, dx, op)
+    return np.array([o[half, half, half] for o in out])
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_full_size_512_order6_sampled(prec):
+    """512^3, 6th-order Laplacian, one RK4 step in the benchmark's launch
+    configuration; 48 sampled cells computed one by one by the oracle."""
+    import torch
+    n, dx = 512, 0.125
+    p = slh.EOMParams(order=6)
+    y0 = inputs.gaussian_field(n, n / 16.0, seed=0)
+    h, boxes = uniform_hierarchy(n, dx, prec=prec, nghost=3, bf=16)
+    upload(h, 0, y0, boxes)
+    h.set_eta(ETA0)
+    dt = dx / 4
+    h.rk_step(0, dt, p)
+    g = h.get_state(0).reshape(4, n, n, n)
+    rng = np.random.default_rng(5)
+    idx = [tuple(int(v) for v in rng.integers(0, n, size=3)) for _ in range(44)]
+    idx += [(0, 0, 0), (n - 1, n - 1, n - 1), (0, n - 1, 5), (n - 1, 3, 0)]
+    half = 4 * 3 + 1
+    tol = 1e-12 if prec == "f64" else 1e-5
+    for c3 in idx:
+        exp = _local_rk4_center(y0, c3, half, ETA0, dt, dx, oparams(p))
+        got = g[:, c3[0], c3[1], c3[2]].astype(np.float64)
+        scale = max(1.0, float(np.max(np.abs(exp))))
+        assert np.max(np.abs(got - exp)) <= tol * scale, (c3, got, exp)
+    del h
+    torch.cuda.empty_cache()
