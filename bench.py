@@ -183,6 +183,7 @@ def _time_form(slh, torch, prec, y0_dense, n, K, W, dist, flags):
     h.set_state(0, y0_dense.astype(h.np_dtype))
     h.set_eta(ETA0)
     p = slh.EOMParams(order=ORDER)
+    chosen, tune_ms = h.autotune(0, p, reps=3)
     for _ in range(W):
         h.advance(DT, p, flags=flags)
     h.sync()
@@ -201,13 +202,16 @@ def _time_form(slh, torch, prec, y0_dense, n, K, W, dist, flags):
     if dist is not None:
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
+    per_stage = [h.profile_read(k)[0] for k in (slh.SLH_PROF_S1, slh.SLH_PROF_S2, slh.SLH_PROF_S3,
+                                                 slh.SLH_PROF_S4)]
     stage = h.profile_read(slh.SLH_PROF_STAGE)
     ghost = h.profile_read(slh.SLH_PROF_GHOST)
     tim = h.profile_read(slh.SLH_PROF_TIME)
     h.profile(False, True)
     E = h.reduce_energy(p, mode=1)
     out = dict(ms=ms, stage_ms=stage[0], stage_launches=stage[1], stage_bytes=stage[2],
-               ghost_ms=ghost[0], ghost_launches=ghost[1], time_launches=tim[1], energy=E.tolist())
+               ghost_ms=ghost[0], ghost_launches=ghost[1], time_launches=tim[1], energy=E.tolist(),
+               per_stage_ms=[m / K for m in per_stage], tile_variant=chosen, tune_ms=tune_ms)
     return h, out
 
 
@@ -291,6 +295,9 @@ def run_ours(args, rank, world, local_rank, dist):
                        "ms_per_step": ms64 / K, "stage_achieved_gbs": ach64,
                        "hbm_frac": ach64 / peak, "alg_bytes_per_cell_update": F64_VALUES * 8},
         "stage_share": r32["stage_ms"] / ms,
+        "per_stage_ms": {"f32": r32["per_stage_ms"], "f64": r64["per_stage_ms"]},
+        "autotune": {"f32": {"chosen": r32["tile_variant"], "ms": r32["tune_ms"]},
+                     "f64": {"chosen": r64["tile_variant"], "ms": r64["tune_ms"]}},
         "energy_f32": r32["energy"], "energy_f64": r64["energy"],
         "e2e": {"value": world * cells * K / (e2e_ms / 1e3), "unit": "cell-updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4 * 8},

@@ -82,12 +82,16 @@ typedef int32_t slh_status;
                             this level's psi ghosts */
 
 /* Profiling counters (slh_profile_read kinds) */
-#define SLH_PROF_STAGE 0
+#define SLH_PROF_STAGE 0     /* all four RK stages (sum of SLH_PROF_S1..S4) */
 #define SLH_PROF_GHOST 1
 #define SLH_PROF_RESTRICT 2
 #define SLH_PROF_DIAG 3
 #define SLH_PROF_TIME 4
-#define SLH_PROF_NKINDS 5
+#define SLH_PROF_S1 5        /* RK stage 1 .. 4 separately */
+#define SLH_PROF_S2 6
+#define SLH_PROF_S3 7
+#define SLH_PROF_S4 8
+#define SLH_PROF_NKINDS 9
 
 typedef struct {
   int32_t lo[3];
@@ -245,6 +249,20 @@ slh_status slh_regrid_boxes(const uint8_t* tags_host, const int32_t dims[3],
  * fixed order (bit-reproducible).  Synchronises.
  * Errors: INVALID_ARG, STATE, CUDA, and latched device errors. */
 slh_status slh_reduce_energy(slh_ctx* ctx, const slh_eom_params* p, int32_t mode, double out[5]);
+
+/* Stage-kernel tile shape of level lev: variant indexes a fixed table of
+ * (x extent, y extent, TMA pipeline depth, z-march length) shapes; 0 is the
+ * default.  Synchronises.  Errors: INVALID_ARG, STATE, OUT_OF_RANGE. */
+slh_status slh_set_tile(slh_ctx* ctx, int32_t lev, int32_t variant);
+
+/* Autotuner: time every tile variant on level lev's own boxes (reps
+ * launches of a stage that reads the state and writes only the scratch
+ * buffers SLH_BUF_YA and SLH_BUF_D), keep the fastest.  *chosen receives its
+ * index, ms_out (may be NULL, one entry per variant) the mean milliseconds.
+ * Call between steps, outside stream capture.  Synchronises.
+ * Errors: INVALID_ARG, STATE, CUDA. */
+slh_status slh_autotune(slh_ctx* ctx, int32_t lev, const slh_eom_params* p, int32_t reps, int32_t* chosen,
+                        double* ms_out);
 
 /* Wait for the stream and return any latched device error (then clear it). */
 slh_status slh_sync(slh_ctx* ctx);

@@ -32,7 +32,8 @@ SLH_FUSE_ENERGY = 2
 SLH_USE_GRAPH = 4
 SLH_GHOSTS = 0
 SLH_RESTRICT = 1
-SLH_PROF_STAGE, SLH_PROF_GHOST, SLH_PROF_RESTRICT, SLH_PROF_DIAG, SLH_PROF_TIME = range(5)
+(SLH_PROF_STAGE, SLH_PROF_GHOST, SLH_PROF_RESTRICT, SLH_PROF_DIAG, SLH_PROF_TIME,
+ SLH_PROF_S1, SLH_PROF_S2, SLH_PROF_S3, SLH_PROF_S4) = range(9)
 
 ERRORS = {-1: "INVALID_ARG", -2: "OUT_OF_RANGE", -3: "CUDA", -4: "TIMEOUT", -5: "NOMEM",
           -6: "DEVICE", -7: "STATE"}
@@ -42,7 +43,7 @@ ABI_SYMBOLS = (
     "slh_last_error", "slh_create", "slh_destroy", "slh_level_layout", "slh_init_level",
     "slh_set_state", "slh_get_state", "slh_set_eta", "slh_get_eta", "slh_rk_step",
     "slh_advance", "slh_fill_ghosts", "slh_tag", "slh_tag_blocks", "slh_regrid_boxes",
-    "slh_reduce_energy", "slh_sync", "slh_profile", "slh_profile_read",
+    "slh_reduce_energy", "slh_sync", "slh_profile", "slh_profile_read", "slh_set_tile", "slh_autotune",
 )
 
 
@@ -112,6 +113,8 @@ def lib():
         "slh_sync": (i32, [vp]),
         "slh_profile": (i32, [vp, i32, i32]),
         "slh_profile_read": (i32, [vp, i32, P(dbl), P(i64), P(dbl)]),
+        "slh_set_tile": (i32, [vp, i32, i32]),
+        "slh_autotune": (i32, [vp, i32, P(slh_eom_params), i32, P(i32), P(dbl)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -313,6 +316,23 @@ class Hierarchy:
 
     def sync(self):
         _check(lib().slh_sync(self.h))
+
+    def set_tile(self, lev, variant):
+        _check(lib().slh_set_tile(self.h, lev, variant))
+
+    def autotune(self, lev, params: EOMParams, reps=3, nvariants=8):
+        """Time every stage-kernel tile variant on this level; keep the fastest.
+        Returns (chosen index, [ms per variant])."""
+        p = params.c()
+        ch = ctypes.c_int32()
+        ms = (ctypes.c_double * nvariants)(*([-1.0] * nvariants))
+        _check(lib().slh_autotune(self.h, lev, ctypes.byref(p), reps, ctypes.byref(ch), ms))
+        return ch.value, [v for v in ms[:] if v >= 0]
+
+    def fused_tags(self, lev):
+        """Host copy of the tags written by the last SLH_FUSE_TAG stage 1."""
+        self.sync()
+        return self.levels[lev]["tags"].cpu().numpy()
 
     def profile(self, enable=True, reset=True):
         _check(lib().slh_profile(self.h, int(enable), int(reset)))

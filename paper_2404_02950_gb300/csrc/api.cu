@@ -78,11 +78,12 @@ void prof_end(slh_ctx* c) {
 }
 
 static void free_level(Level& L) {
+  free_tmaps(L);
+  cudaFree(L.tile.d_items);
   cudaFree(L.d_boxes);
   cudaFree(L.d_bmap);
   cudaFree(L.d_slabs);
   cudaFree(L.d_slab_off);
-  cudaFree(L.d_items);
   cudaFree(L.d_covered);
   cudaFree(L.d_ritems);
   cudaFree(L.d_roff);
@@ -138,6 +139,25 @@ static slh_status build_covered(slh_ctx* c, int lev) {
   }
   C.ncov = nb;
   return upload(&C.d_covered, m);
+}
+
+// Stage work items of a tile variant: box by box, z chunk outer, then y,
+// then x tiles (consecutive CTAs share halo planes in L2).
+static slh_status set_tile(slh_ctx* c, Level& L, const TileVariant& v) {
+  (void)c;
+  std::vector<int4> items;
+  for (size_t b = 0; b < L.lay.boxes.size(); ++b) {
+    const BoxDev& B = L.lay.boxes[b];
+    for (int z0 = 0; z0 < B.n[2]; z0 += v.zlen)
+      for (int y0 = 0; y0 < B.n[1]; y0 += v.ty)
+        for (int x0 = 0; x0 < B.n[0]; x0 += v.tx) items.push_back(make_int4((int)b, x0, y0, z0));
+  }
+  slh_status st = upload(&L.tile.d_items, items);
+  if (st != SLH_OK) return st;
+  L.tile.v = v;
+  L.tile.nitems = (int)items.size();
+  L.tile.zlen = v.zlen;
+  return SLH_OK;
 }
 
 }  // namespace slh
@@ -332,19 +352,11 @@ slh_status slh_init_level(slh_ctx* c, int32_t lev, const slh_box* boxes, int32_t
   if ((st = upload(&L.d_slabs, slabs)) != SLH_OK) return st;
   if ((st = upload(&L.d_slab_off, soff)) != SLH_OK) return st;
 
-  // stage work items: z chunk outer, then y, then x tiles, box by box
-  L.tile_x = 32;
-  L.tile_y = c->prec == SLH_F64 ? 8 : 16;
-  L.zlen = 64;
-  std::vector<int4> items;
-  for (int b = 0; b < nboxes; ++b) {
-    const BoxDev& B = L.lay.boxes[b];
-    for (int z0 = 0; z0 < B.n[2]; z0 += L.zlen)
-      for (int y0 = 0; y0 < B.n[1]; y0 += L.tile_y)
-        for (int x0 = 0; x0 < B.n[0]; x0 += L.tile_x) items.push_back(make_int4(b, x0, y0, z0));
+  {
+    int nv = 0;
+    const TileVariant* vs = tile_variants(c->prec, &nv);
+    if ((st = set_tile(c, L, vs[0])) != SLH_OK) return st;
   }
-  L.nitems = (int)items.size();
-  if ((st = upload(&L.d_items, items)) != SLH_OK) return st;
 
   // restriction items onto lev-1
   if (lev > 0) {
@@ -494,11 +506,11 @@ static slh_status rk_step_impl(slh_ctx* c, int lev, int sub, double dt0, const s
     StageLaunch sl;
     memset(&sl, 0, sizeof(sl));
     sl.stage = k + 1;
-    sl.yin = L.buf[in_role[k]];
-    sl.yn = L.buf[ybuf];
-    sl.dacc = L.buf[SLH_BUF_D];
-    sl.yout = L.buf[out_role[k]];
-    sl.comp = k == 3 ? L.buf[SLH_BUF_C] : nullptr;
+    sl.in_buf = in_role[k];
+    sl.yn_buf = ybuf;
+    sl.d_buf = SLH_BUF_D;
+    sl.out_buf = out_role[k];
+    sl.c_buf = (k == 3 && L.buf[SLH_BUF_C]) ? SLH_BUF_C : -1;
     sl.c_stage = cRK[k] * dt;
     sl.ha = aRK[k] * dt;
     sl.hb = bRK[k] * dt;
@@ -515,7 +527,7 @@ static slh_status rk_step_impl(slh_ctx* c, int lev, int sub, double dt0, const s
       sl.cov_shift = ilog2(c->bf / 2);
       sl.cov_nb = L.ncov;
     }
-    prof_begin(c, SLH_PROF_STAGE, V * (vals[k] * s + extra));
+    prof_begin(c, SLH_PROF_S1 + k, V * (vals[k] * s + extra));
     int used = 0;
     st = launch_stage(c, L, p, sl, &used);
     prof_end(c);
@@ -663,7 +675,11 @@ static slh_status diag_pass(slh_ctx* c, int lev, const slh_eom_params& p, uint8_
   StageLaunch sl;
   memset(&sl, 0, sizeof(sl));
   sl.stage = 0;
-  sl.yin = L.buf[L.role_y];
+  sl.in_buf = L.role_y;
+  sl.yn_buf = L.role_y;
+  sl.d_buf = SLH_BUF_D;
+  sl.out_buf = SLH_BUF_YA;
+  sl.c_buf = -1;
   sl.lev = lev;
   sl.c_stage = 0.0;
   sl.tags = tags;
@@ -769,6 +785,72 @@ slh_status slh_reduce_energy(slh_ctx* c, const slh_eom_params* p, int32_t mode, 
   return SLH_OK;
 }
 
+slh_status slh_set_tile(slh_ctx* c, int32_t lev, int32_t variant) {
+  if (!c) return fail(SLH_ERR_INVALID_ARG, "set_tile: null ctx");
+  if (lev < 0 || lev >= c->nlevels) return fail(SLH_ERR_STATE, "set_tile: level %d not defined", lev);
+  int nv = 0;
+  const TileVariant* vs = tile_variants(c->prec, &nv);
+  if (variant < 0 || variant >= nv) return fail(SLH_ERR_OUT_OF_RANGE, "set_tile: variant %d outside [0,%d)", variant, nv);
+  SLH_CUDA(cudaStreamSynchronize(c->stream));
+  drop_graphs(c);
+  return set_tile(c, c->lev[lev], vs[variant]);
+}
+
+slh_status slh_autotune(slh_ctx* c, int32_t lev, const slh_eom_params* p, int32_t reps, int32_t* chosen,
+                        double* ms_out) {
+  if (!c) return fail(SLH_ERR_INVALID_ARG, "autotune: null ctx");
+  slh_status st = check_params(p);
+  if (st != SLH_OK) return st;
+  if (lev < 0 || lev >= c->nlevels) return fail(SLH_ERR_STATE, "autotune: level %d not defined", lev);
+  if (reps < 1) reps = 3;
+  Level& L = c->lev[lev];
+  int nv = 0;
+  const TileVariant* vs = tile_variants(c->prec, &nv);
+  const bool was_prof = c->prof;
+  c->prof = false;
+  cudaEvent_t e0, e1;
+  SLH_CUDA(cudaEventCreate(&e0));
+  SLH_CUDA(cudaEventCreate(&e1));
+  int best = 0;
+  float best_ms = 0.f;
+  for (int v = 0; v < nv; ++v) {
+    if ((st = set_tile(c, L, vs[v])) != SLH_OK) break;
+    // a stage-2 launch that reads the state and writes only scratch buffers
+    StageLaunch sl;
+    memset(&sl, 0, sizeof(sl));
+    sl.stage = 2;
+    sl.in_buf = L.role_y;
+    sl.yn_buf = L.role_y;
+    sl.d_buf = SLH_BUF_D;
+    sl.out_buf = SLH_BUF_YA;
+    sl.c_buf = -1;
+    sl.ha = sl.hb = 0.0;
+    sl.lev = lev;
+    if ((st = launch_stage(c, L, *p, sl, nullptr)) != SLH_OK) break;
+    cudaEventRecord(e0, c->stream);
+    for (int r = 0; r < reps; ++r)
+      if ((st = launch_stage(c, L, *p, sl, nullptr)) != SLH_OK) break;
+    if (st != SLH_OK) break;
+    cudaEventRecord(e1, c->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms_out) ms_out[v] = ms / reps;
+    if (v == 0 || ms < best_ms) {
+      best_ms = ms;
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->prof = was_prof;
+  if (st != SLH_OK) return st;
+  drop_graphs(c);
+  if ((st = set_tile(c, L, vs[best])) != SLH_OK) return st;
+  if (chosen) *chosen = best;
+  return slh_sync(c);
+}
+
 slh_status slh_profile(slh_ctx* c, int32_t enable, int32_t reset) {
   if (!c) return fail(SLH_ERR_INVALID_ARG, "profile: null ctx");
   if (reset) {
@@ -803,6 +885,19 @@ slh_status slh_profile_read(slh_ctx* c, int32_t kind, double* ms, int64_t* launc
     cudaEventDestroy(r.b);
   }
   c->prof_open.clear();
+  if (kind == SLH_PROF_STAGE) {
+    double m = 0, b = 0;
+    long long n = 0;
+    for (int k = SLH_PROF_S1; k <= SLH_PROF_S4; ++k) {
+      m += c->prof_ms[k];
+      n += c->prof_n[k];
+      b += c->prof_bytes[k];
+    }
+    if (ms) *ms = m;
+    if (launches) *launches = n;
+    if (bytes) *bytes = b;
+    return SLH_OK;
+  }
   if (ms) *ms = c->prof_ms[kind];
   if (launches) *launches = c->prof_n[kind];
   if (bytes) *bytes = c->prof_bytes[kind];

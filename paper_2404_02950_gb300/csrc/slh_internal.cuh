@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -43,6 +44,19 @@ struct RestrictItem {
   int n[3];         // coarse extents = fine extents / 2
 };
 
+// A stage-kernel tile shape: x and y extent of the CTA's cell column, the
+// TMA pipeline depth (planes in flight) and the z-march length of one item.
+struct TileVariant {
+  int tx, ty, p, zlen;
+};
+
+struct Tile {
+  TileVariant v{32, 16, 2, 64};
+  int4* d_items = nullptr;       // work items (box, x0, y0, z0)
+  int nitems = 0;
+  int zlen = 64;
+};
+
 struct Layout {
   std::vector<BoxDev> boxes;
   long long total = 0;
@@ -70,9 +84,8 @@ struct Level {
   long long* d_slab_off = nullptr;
   int nslabs = 0;
   long long nghost_cells = 0;
-  int4* d_items = nullptr;       // stage work items (box, x0, y0, z0)
-  int nitems = 0;
-  int tile_x = 32, tile_y = 8, zlen = 64;
+  Tile tile;                     // stage work items for the chosen tile variant
+  std::map<unsigned long long, void*> tmaps;   // device tensor maps per (G, TX, TY)
   uint8_t* d_covered = nullptr;  // covered by the finer level, blocks of bf/2 cells
   int ncov = 0;
   RestrictItem* d_ritems = nullptr;  // restriction of this level onto lev-1
@@ -143,11 +156,7 @@ constexpr int DERR_TIMEOUT = 3;   // a bounded wait gave up
 // launchers (stage.cu, ghost.cu, diag.cu)
 struct StageLaunch {
   int stage;            // 0 = diagnostics only, 1..4
-  const void* yin;
-  const void* yn;
-  void* dacc;
-  void* yout;
-  void* comp;
+  int in_buf, yn_buf, d_buf, out_buf, c_buf;   // physical buffer indices (-1: unused)
   double c_stage;       // c_s * dt
   double ha, hb;        // a_{s+1} dt, b_s dt
   uint8_t* tags;
@@ -160,7 +169,8 @@ struct StageLaunch {
 };
 slh_status launch_stage(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s,
                         int* ctas_used);
-int stage_grid(slh_ctx* c, Level& L, int order);
+const TileVariant* tile_variants(int prec, int* n);
+void free_tmaps(Level& L);
 
 slh_status launch_ghosts(slh_ctx* c, int lev, int role, double alpha, int itype);
 slh_status launch_restrict(slh_ctx* c, int fine_lev);

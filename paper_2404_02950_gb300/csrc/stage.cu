@@ -1,21 +1,36 @@
 // Fused RK4 stage kernel: finite-difference Laplacian (App. A), right-hand
 // side of the axion-string system (Sec. 3.1, Eqs. EOM1-EOM2), classic RK4
-// stage combination (integrator type 4), and -- in stage 1 or the
-// diagnostics-only pass -- the string-winding tags and energy partials of
-// the stage input.
+// stage combination (integrator type 4), and -- in the diagnostics variant
+// (stage 1 with fused tags/energy, or the diagnostics-only pass) -- the
+// string-winding tags and the energy partials of the stage input.
 //
-// Work decomposition: a persistent grid walks a list of (box, x0, y0, z0)
-// tiles; each CTA marches along z through a TX x TY column tile, keeping a
-// ring of 2G+2 halo'd psi1/psi2 planes in shared memory that cp.async
-// streams from global memory one plane ahead.  Pointwise data (momenta, y_n,
-// the increment accumulator, the Kahan compensation) is read straight from
-// global memory into registers, coalesced along x.  Every value a cell needs
-// is read once from HBM per stage (halo re-reads hit L2).
+// Work decomposition.  A persistent grid walks a list of (box, x0, y0, z0)
+// tiles; each CTA marches along z through a TX x TY column of cells.  The
+// z-planes a CTA needs form one continuous stream of "load steps" across all
+// its tiles; one elected thread issues, P steps ahead of the consumers, TMA
+// tensor copies (cp.async.bulk.tensor) of
+//   - the halo'd psi1/psi2 plane (TX+8 by TY+2G cells, 16-byte aligned in x),
+//   - the pointwise operands of the plane G below it (momenta of the stage
+//     input, y_n, the increment accumulator, the Kahan compensation),
+// into shared-memory rings whose completion is tracked by mbarrier
+// transaction counts.  Consumers read the 2G+1 psi planes of the stencil from
+// the ring and write outputs with coalesced stores.  Every waiting loop is
+// bounded; on expiry the CTA latches DERR_TIMEOUT, drains its copies with a
+// bounded wait and leaves.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
 
 #include "slh_internal.cuh"
 
 namespace slh {
+
+constexpr int NPW_MAX = 7;   // pointwise boxes: Pi | y_n(0,1) y_n(2,3) | D(0,1) D(2,3) | C(0,1) C(2,3)
+constexpr long long WAIT_LIMIT = 1ll << 22;
 
 template <typename T>
 struct StageArgs {
@@ -23,15 +38,13 @@ struct StageArgs {
   const int4* items;
   int nitems;
   int zlen;
-  int gl;                  // ghost layers of the level layout
-  const T* yin;            // stage input Y_s
-  const T* yn;             // y_n (stages 2..4)
-  T* dacc;                 // increment accumulator
-  T* yout;                 // Y_{s+1} or y_{n+1}
-  T* comp;                 // Kahan compensation (stage 4, FP32) or null
-  int stage;               // 0 = diagnostics only
-  const double* eta_start; // device eta at the start of the step
-  double c_stage;          // c_s * dt
+  int gl;                   // ghost layers of the level layout
+  const CUtensorMap* tmaps; // [box][buffer][kind 0 = halo'd psi, 1 = pointwise]
+  int in_buf, yn_buf, d_buf, out_buf, c_buf;   // physical buffer indices (-1: none)
+  T* bufs[SLH_NBUF];
+  int stage;                // 0 = diagnostics only, 1..4
+  const double* eta_start;  // device eta at the start of the step (or current eta)
+  double c_stage;           // c_s * dt
   double lambda, a;
   int friction, eta_power;
   double inv_dx2;
@@ -41,22 +54,52 @@ struct StageArgs {
   unsigned long long* tagcount;
   const uint8_t* covered;
   int cov_shift, cov_nb;
+  int* err;
 };
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
+// ---------------------------------------------------------------------------
+// PTX helpers (TMA, mbarrier)
 
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// bounded wait on a phase of an mbarrier; false if the limit expired
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  for (long long i = 0; i < WAIT_LIMIT; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_load4(unsigned dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                          unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(
+          dst),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
 // Winding contribution of the edge a -> b: +1 when it leaves the upper half
 // plane (Im >= 0) turning counter-clockwise, -1 when it enters it turning
-// clockwise (the sign of X = Re a Im b - Im a Re b); products and the
-// difference rounded separately in FP64 (exact sign for FP32 inputs).
+// clockwise, by the exact sign of X = Re a Im b - Im a Re b.
+
 __device__ __forceinline__ int edge_delta(double ar, double ai, double br, double bi) {
   const bool ua = ai >= 0.0, ub = bi >= 0.0;
   if (ua == ub) return 0;
@@ -65,31 +108,90 @@ __device__ __forceinline__ int edge_delta(double ar, double ai, double br, doubl
   return X < 0.0 ? -1 : 0;
 }
 
-// Central second-difference weights w_m, m = 1..G (the centre weight is
-// -2 sum w_m and drops out of the difference form used below).
+// FP32 inputs: the sign of X from the rounded products whenever their
+// difference exceeds the worst-case rounding error (each product is within
+// 2^-24 of its value, the difference within 2^-24 more); otherwise the
+// products, exact in FP64, are formed in FP64.  Same sign as the FP64 form.
+__device__ __forceinline__ int edge_delta(float ar, float ai, float br, float bi) {
+  const bool ua = ai >= 0.0f, ub = bi >= 0.0f;
+  if (ua == ub) return 0;
+  const float p = __fmul_rn(ar, bi), q = __fmul_rn(ai, br);
+  const float d = __fsub_rn(p, q);
+  const float bound = __fmul_rn(__fadd_rn(fabsf(p), fabsf(q)), 4.76837158203125e-07f);  // 2^-21
+  float s;
+  if (fabsf(d) > bound && bound > 1e-30f) {
+    s = d;
+  } else {
+    const double X = __dsub_rn(__dmul_rn((double)ar, (double)bi), __dmul_rn((double)ai, (double)br));
+    s = X > 0.0 ? 1.0f : (X < 0.0 ? -1.0f : 0.0f);
+  }
+  if (ua) return s > 0.0f ? 1 : 0;
+  return s < 0.0f ? -1 : 0;
+}
+
+// Central second-difference weights w_m, m = 0..G (w_0 the centre weight).
 template <int G>
 __device__ __forceinline__ double lap_w(int m);
 template <>
-__device__ __forceinline__ double lap_w<1>(int) { return 1.0; }
+__device__ __forceinline__ double lap_w<1>(int m) { return m == 0 ? -2.0 : 1.0; }
 template <>
-__device__ __forceinline__ double lap_w<2>(int m) { return m == 1 ? 4.0 / 3.0 : -1.0 / 12.0; }
+__device__ __forceinline__ double lap_w<2>(int m) { return m == 0 ? -2.5 : (m == 1 ? 4.0 / 3.0 : -1.0 / 12.0); }
 template <>
 __device__ __forceinline__ double lap_w<3>(int m) {
-  return m == 1 ? 1.5 : (m == 2 ? -0.15 : 1.0 / 90.0);
+  return m == 0 ? -49.0 / 18.0 : (m == 1 ? 1.5 : (m == 2 ? -0.15 : 1.0 / 90.0));
 }
 
-template <typename T, int G, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY) stage_kernel(const StageArgs<T> A) {
-  constexpr int NT = TX * TY;
-  constexpr int VEC = 16 / sizeof(T);
-  constexpr int SXL = TX + 8;          // loaded row: valid x0-4 .. x0+TX+3
-  constexpr int SY = TY + 2 * G;
-  constexpr int R = 2 * G + 2;         // ring of planes
-  constexpr int PLANE = SY * SXL;
-  constexpr int CROW = SXL / VEC;
-  constexpr int CHUNKS = 2 * SY * CROW;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* ring = reinterpret_cast<T*>(smem_raw);
+// shared-memory geometry of one kernel variant
+template <typename T, int G, int TX, int TY, int P>
+struct Geo {
+  static constexpr int SXL = TX + 8;
+  static constexpr int SY = TY + 2 * G;
+  static constexpr int RPSI = 2 * G + 1 + P;
+  static constexpr int RPW = P + 1;
+  static constexpr int PSI_BYTES = 2 * SY * SXL * (int)sizeof(T);
+  static constexpr int PSI_STRIDE = (PSI_BYTES + 127) / 128 * 128;
+  static constexpr int PW2 = 2 * TY * TX * (int)sizeof(T);
+  static constexpr int NPW = sizeof(T) == 4 ? NPW_MAX : NPW_MAX - 2;
+  static constexpr int PW_STRIDE = (NPW * PW2 + 127) / 128 * 128;
+  static constexpr int BAR_BYTES = 128;
+  static constexpr int SMEM = BAR_BYTES + RPSI * PSI_STRIDE + RPW * PW_STRIDE;
+};
+
+struct Cursor {
+  int item, q, box, x0, y0, z0, z1;
+  bool valid;
+};
+
+template <int G>
+__device__ __forceinline__ void cursor_load(Cursor& c, const int4* items, const BoxDev* boxes, int nitems, int zlen) {
+  c.valid = c.item < nitems;
+  if (!c.valid) return;
+  const int4 it = items[c.item];
+  c.box = it.x;
+  c.x0 = it.y;
+  c.y0 = it.z;
+  c.z0 = it.w;
+  c.z1 = min(it.w + zlen, boxes[it.x].n[2]);
+  c.q = c.z0 - G;
+}
+
+template <int G>
+__device__ __forceinline__ void cursor_next(Cursor& c, const int4* items, const BoxDev* boxes, int nitems, int zlen) {
+  if (++c.q <= c.z1 + G - 1) return;
+  c.item += gridDim.x;
+  cursor_load<G>(c, items, boxes, nitems, zlen);
+}
+
+template <typename T, int G, int TX, int TY, int P, bool DIAG>
+__global__ void __launch_bounds__(TX* TY, 1) stage_kernel(const StageArgs<T> A) {
+  using GE = Geo<T, G, TX, TY, P>;
+  constexpr int SXL = GE::SXL, SY = GE::SY, RPSI = GE::RPSI, RPW = GE::RPW;
+  constexpr int PLANE = SY * SXL;   // elements of one psi component plane
+  constexpr int TXY = TX * TY;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem);
+  unsigned char* psi_base = smem + GE::BAR_BYTES;
+  unsigned char* pw_base = psi_base + RPSI * GE::PSI_STRIDE;
 
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
@@ -100,147 +202,176 @@ __global__ void __launch_bounds__(TX* TY) stage_kernel(const StageArgs<T> A) {
   const double cpd = A.eta_power == 2 ? A.lambda * (eta * eta) : A.lambda;
   const T c_fric = (T)cfd, c_pot = (T)cpd, a_c = (T)A.a;
   const T ha = (T)A.ha, hb = (T)A.hb, idx2 = (T)A.inv_dx2;
-  const bool diag = (A.tags != nullptr) || (A.epart != nullptr);
+  const int stage = A.stage;
+  const bool has_c = A.c_buf >= 0;
+  // pointwise boxes this stage needs: Pi always; y_n and D from stage 2; C in stage 4
+  const int npw = stage >= 2 ? ((stage == 4 && has_c) ? 7 : 5) : 1;
+  const unsigned step_bytes_pw = (unsigned)(npw * GE::PW2);
+
+  if (tid == 0) {
+    for (int i = 0; i < RPSI; ++i) mbar_init(smem_u32(&bars[i]), 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  Cursor cc, pc;
+  cc.item = blockIdx.x;
+  cursor_load<G>(cc, A.items, A.boxes, A.nitems, A.zlen);
+  pc = cc;
+
+  // issue the copies of load step t (cursor c) -- elected thread only
+  auto issue = [&](const Cursor& c, long long t) {
+    const int slot = (int)(t % RPSI);
+    const unsigned bar = smem_u32(&bars[slot]);
+    const bool pw = (c.q - G >= c.z0);
+    mbar_expect_tx(bar, (unsigned)GE::PSI_BYTES + (pw ? step_bytes_pw : 0u));
+    const CUtensorMap* mb = A.tmaps + (size_t)c.box * SLH_NBUF * 2;
+    tma_load4(smem_u32(psi_base + slot * GE::PSI_STRIDE), mb + 2 * A.in_buf + 0, c.x0, c.y0 - G + gl, c.q + gl, 0,
+              bar);
+    if (pw) {
+      unsigned char* dst = pw_base + (int)(t % RPW) * GE::PW_STRIDE;
+      const int xp = c.x0 + XPAD, yp = c.y0 + gl, zp = c.q - G + gl;
+      tma_load4(smem_u32(dst), mb + 2 * A.in_buf + 1, xp, yp, zp, 2, bar);
+      if (stage >= 2) {
+        tma_load4(smem_u32(dst + 1 * GE::PW2), mb + 2 * A.yn_buf + 1, xp, yp, zp, 0, bar);
+        tma_load4(smem_u32(dst + 2 * GE::PW2), mb + 2 * A.yn_buf + 1, xp, yp, zp, 2, bar);
+        tma_load4(smem_u32(dst + 3 * GE::PW2), mb + 2 * A.d_buf + 1, xp, yp, zp, 0, bar);
+        tma_load4(smem_u32(dst + 4 * GE::PW2), mb + 2 * A.d_buf + 1, xp, yp, zp, 2, bar);
+        if (stage == 4 && has_c) {
+          tma_load4(smem_u32(dst + 5 * GE::PW2), mb + 2 * A.c_buf + 1, xp, yp, zp, 0, bar);
+          tma_load4(smem_u32(dst + 6 * GE::PW2), mb + 2 * A.c_buf + 1, xp, yp, zp, 2, bar);
+        }
+      }
+    }
+  };
+
+  long long issued = 0;
+  if (tid == 0) {
+    for (int i = 0; i < P && pc.valid; ++i) {
+      issue(pc, issued++);
+      cursor_next<G>(pc, A.items, A.boxes, A.nitems, A.zlen);
+    }
+  }
 
   double s_kin = 0.0, s_grad = 0.0, s_pot = 0.0;
   unsigned long long n_pierced = 0, n_tagged = 0;
+  T i_kin = 0, i_grad = 0, i_pot = 0;
+  int cur_box = -1;
+  BoxDev B;
+  bool aborted = false;
 
-  for (int item = blockIdx.x; item < A.nitems; item += gridDim.x) {
-    const int4 it = A.items[item];
-    const BoxDev B = A.boxes[it.x];
-    const int x0 = it.y, y0 = it.z, z0 = it.w;
-    const int z1 = min(z0 + A.zlen, B.n[2]);
-    const int x = x0 + tx, y = y0 + ty;
-    const bool active = (x < B.n[0]) && (y < B.n[1]);
-    const long long rowstride = B.pitch;
-    const long long planestride = (long long)B.pny * B.pitch;
-    T i_kin = 0, i_grad = 0, i_pot = 0;
-
-    auto load_plane = [&](int zz) {
-      const int slot = (zz - z0 + G) % R;
-      T* dst = ring + slot * 2 * PLANE;
-      const long long pz = zz + gl;
-      for (int ch = tid; ch < CHUNKS; ch += NT) {
-        const int comp = ch / (SY * CROW);
-        const int rem = ch - comp * (SY * CROW);
-        const int row = rem / CROW;
-        const int cc = rem - row * CROW;
-        const int py = y0 - G + row + gl;
-        const int px = x0 + cc * VEC;
-        if (py < B.pny && px < B.pitch) {
-          const T* src = A.yin + B.off + comp * B.cs + pz * planestride + (long long)py * rowstride + px;
-          cp_async16(dst + comp * PLANE + row * SXL + cc * VEC, src);
-        }
-      }
-    };
-
-    for (int j = 0; j < 2 * G + 1; ++j) {
-      load_plane(z0 - G + j);
-      cp_async_commit();
+  long long t = 0;
+  for (; cc.valid; ++t) {
+    if (tid == 0 && pc.valid) {
+      fence_proxy_async();
+      issue(pc, issued++);
+      cursor_next<G>(pc, A.items, A.boxes, A.nitems, A.zlen);
     }
+    const int slot = (int)(t % RPSI);
+    const bool ok = mbar_wait(smem_u32(&bars[slot]), (unsigned)((t / RPSI) & 1));
 
-    for (int z = z0; z < z1; ++z) {
-      if (z + G + 1 <= z1 + G - 1) load_plane(z + G + 1);
-      cp_async_commit();
-
-      // pointwise operands of this cell (issued before the wait)
-      const long long e0 = B.off + (long long)(z + gl) * planestride + (long long)(y + gl) * rowstride + x + XPAD;
-      T P1 = 0, P2 = 0, yn0 = 0, yn1 = 0, yn2 = 0, yn3 = 0, d0 = 0, d1 = 0, d2 = 0, d3 = 0;
-      T k0c = 0, k1c = 0, k2c = 0, k3c = 0;
-      if (active) {
-        P1 = A.yin[e0 + 2 * B.cs];
-        P2 = A.yin[e0 + 3 * B.cs];
-        if (A.stage >= 2) {
-          yn0 = A.yn[e0];
-          yn1 = A.yn[e0 + B.cs];
-          yn2 = A.yn[e0 + 2 * B.cs];
-          yn3 = A.yn[e0 + 3 * B.cs];
-          d0 = A.dacc[e0];
-          d1 = A.dacc[e0 + B.cs];
-          d2 = A.dacc[e0 + 2 * B.cs];
-          d3 = A.dacc[e0 + 3 * B.cs];
-          if (A.stage == 4 && A.comp != nullptr) {
-            k0c = A.comp[e0];
-            k1c = A.comp[e0 + B.cs];
-            k2c = A.comp[e0 + 2 * B.cs];
-            k3c = A.comp[e0 + 3 * B.cs];
-          }
-        }
+    const int z = cc.q - G;
+    if (ok && z >= cc.z0) {
+      if (cc.box != cur_box) {
+        B = A.boxes[cc.box];
+        cur_box = cc.box;
       }
-
-      cp_async_wait<1>();
-      __syncthreads();
-
-      if (active) {
+      const int x = cc.x0 + tx, y = cc.y0 + ty;
+      if (x < B.n[0] && y < B.n[1]) {
+        const T* ring = reinterpret_cast<const T*>(psi_base);
         auto S = [&](int c, int dx, int dy, int dz) -> T {
-          const int slot = (z + dz - z0 + G) % R;
-          return ring[(slot * 2 + c) * PLANE + (ty + G + dy) * SXL + 4 + tx + dx];
+          const int sl = (int)((t + (RPSI - G) + dz) % RPSI);
+          return ring[(sl * (GE::PSI_STRIDE / (int)sizeof(T))) + c * PLANE + (ty + G + dy) * SXL + 4 + tx + dx];
         };
+        const T* pwp = reinterpret_cast<const T*>(pw_base + (int)(t % RPW) * GE::PW_STRIDE);
+        auto PWv = [&](int box, int comp) -> T { return pwp[box * 2 * TXY + comp * TXY + ty * TX + tx]; };
         const T p1 = S(0, 0, 0, 0), p2 = S(1, 0, 0, 0);
-        T l1 = 0, l2 = 0;
-        {
-          T sx1 = 0, sy1 = 0, sz1 = 0, sx2 = 0, sy2 = 0, sz2 = 0;
+        T l1, l2;
+        if (sizeof(T) == 8) {
+          // textbook form sum_m w_m (f(+m) + f(-m)) + 3 w_0 f(0): fewest FP64 operations
+          T a1 = (T)(3.0 * lap_w<G>(0)) * p1, a2 = (T)(3.0 * lap_w<G>(0)) * p2;
 #pragma unroll
           for (int m = 1; m <= G; ++m) {
             const T w = (T)lap_w<G>(m);
-            sx1 += w * ((S(0, m, 0, 0) - p1) + (S(0, -m, 0, 0) - p1));
-            sy1 += w * ((S(0, 0, m, 0) - p1) + (S(0, 0, -m, 0) - p1));
-            sz1 += w * ((S(0, 0, 0, m) - p1) + (S(0, 0, 0, -m) - p1));
-            sx2 += w * ((S(1, m, 0, 0) - p2) + (S(1, -m, 0, 0) - p2));
-            sy2 += w * ((S(1, 0, m, 0) - p2) + (S(1, 0, -m, 0) - p2));
-            sz2 += w * ((S(1, 0, 0, m) - p2) + (S(1, 0, 0, -m) - p2));
+            a1 += w * (((S(0, m, 0, 0) + S(0, -m, 0, 0)) + (S(0, 0, m, 0) + S(0, 0, -m, 0))) +
+                       (S(0, 0, 0, m) + S(0, 0, 0, -m)));
+            a2 += w * (((S(1, m, 0, 0) + S(1, -m, 0, 0)) + (S(1, 0, m, 0) + S(1, 0, -m, 0))) +
+                       (S(1, 0, 0, m) + S(1, 0, 0, -m)));
           }
-          l1 = ((sx1 + sy1) + sz1) * idx2;
-          l2 = ((sx2 + sy2) + sz2) * idx2;
+          l1 = a1 * idx2;
+          l2 = a2 * idx2;
+        } else {
+          // difference form sum_m w_m ((f(+m) - f0) + (f(-m) - f0)): the
+          // differences of neighbouring values are exact, which keeps FP32
+          // cancellation error at the level of the curvature itself
+          T a1 = 0, a2 = 0;
+#pragma unroll
+          for (int m = 1; m <= G; ++m) {
+            const T w = (T)lap_w<G>(m);
+            a1 += w * ((((S(0, m, 0, 0) - p1) + (S(0, -m, 0, 0) - p1)) + ((S(0, 0, m, 0) - p1) + (S(0, 0, -m, 0) - p1))) +
+                       ((S(0, 0, 0, m) - p1) + (S(0, 0, 0, -m) - p1)));
+            a2 += w * ((((S(1, m, 0, 0) - p2) + (S(1, -m, 0, 0) - p2)) + ((S(1, 0, m, 0) - p2) + (S(1, 0, -m, 0) - p2))) +
+                       ((S(1, 0, 0, m) - p2) + (S(1, 0, 0, -m) - p2)));
+          }
+          l1 = a1 * idx2;
+          l2 = a2 * idx2;
         }
+        const T P1 = PWv(0, 0), P2 = PWv(0, 1);
         const T r2 = p1 * p1 + p2 * p2;
         const T pot = c_pot * (r2 - (T)1) + a_c;
         const T kP1 = (-c_fric) * P1 + l1 - p1 * pot;
         const T kP2 = (-c_fric) * P2 + l2 - p2 * pot;
-
-        if (A.stage == 1) {
-          A.yout[e0] = p1 + ha * P1;
-          A.yout[e0 + B.cs] = p2 + ha * P2;
-          A.yout[e0 + 2 * B.cs] = P1 + ha * kP1;
-          A.yout[e0 + 3 * B.cs] = P2 + ha * kP2;
-          A.dacc[e0] = hb * P1;
-          A.dacc[e0 + B.cs] = hb * P2;
-          A.dacc[e0 + 2 * B.cs] = hb * kP1;
-          A.dacc[e0 + 3 * B.cs] = hb * kP2;
-        } else if (A.stage == 2 || A.stage == 3) {
-          A.yout[e0] = yn0 + ha * P1;
-          A.yout[e0 + B.cs] = yn1 + ha * P2;
-          A.yout[e0 + 2 * B.cs] = yn2 + ha * kP1;
-          A.yout[e0 + 3 * B.cs] = yn3 + ha * kP2;
-          A.dacc[e0] = d0 + hb * P1;
-          A.dacc[e0 + B.cs] = d1 + hb * P2;
-          A.dacc[e0 + 2 * B.cs] = d2 + hb * kP1;
-          A.dacc[e0 + 3 * B.cs] = d3 + hb * kP2;
-        } else if (A.stage == 4) {
-          const T inc0 = d0 + hb * P1, inc1 = d1 + hb * P2;
-          const T inc2 = d2 + hb * kP1, inc3 = d3 + hb * kP2;
-          if (A.comp != nullptr) {
-            // compensated sum y + inc carrying the rounding error in comp
-            T v, t;
-            v = inc0 - k0c; t = yn0 + v; A.comp[e0] = (t - yn0) - v; A.yout[e0] = t;
-            v = inc1 - k1c; t = yn1 + v; A.comp[e0 + B.cs] = (t - yn1) - v; A.yout[e0 + B.cs] = t;
-            v = inc2 - k2c; t = yn2 + v; A.comp[e0 + 2 * B.cs] = (t - yn2) - v; A.yout[e0 + 2 * B.cs] = t;
-            v = inc3 - k3c; t = yn3 + v; A.comp[e0 + 3 * B.cs] = (t - yn3) - v; A.yout[e0 + 3 * B.cs] = t;
+        const long long e0 = B.off + (long long)(z + gl) * B.pny * B.pitch + (long long)(y + gl) * B.pitch + x + XPAD;
+        const long long cs = B.cs;
+        if (stage == 1) {
+          T* yo = A.bufs[A.out_buf];
+          T* dd = A.bufs[A.d_buf];
+          yo[e0] = p1 + ha * P1;
+          yo[e0 + cs] = p2 + ha * P2;
+          yo[e0 + 2 * cs] = P1 + ha * kP1;
+          yo[e0 + 3 * cs] = P2 + ha * kP2;
+          dd[e0] = hb * P1;
+          dd[e0 + cs] = hb * P2;
+          dd[e0 + 2 * cs] = hb * kP1;
+          dd[e0 + 3 * cs] = hb * kP2;
+        } else if (stage == 2 || stage == 3) {
+          T* yo = A.bufs[A.out_buf];
+          T* dd = A.bufs[A.d_buf];
+          yo[e0] = PWv(1, 0) + ha * P1;
+          yo[e0 + cs] = PWv(1, 1) + ha * P2;
+          yo[e0 + 2 * cs] = PWv(2, 0) + ha * kP1;
+          yo[e0 + 3 * cs] = PWv(2, 1) + ha * kP2;
+          dd[e0] = PWv(3, 0) + hb * P1;
+          dd[e0 + cs] = PWv(3, 1) + hb * P2;
+          dd[e0 + 2 * cs] = PWv(4, 0) + hb * kP1;
+          dd[e0 + 3 * cs] = PWv(4, 1) + hb * kP2;
+        } else if (stage == 4) {
+          T* yo = A.bufs[A.out_buf];
+          const T y0v = PWv(1, 0), y1v = PWv(1, 1), y2v = PWv(2, 0), y3v = PWv(2, 1);
+          const T inc0 = PWv(3, 0) + hb * P1, inc1 = PWv(3, 1) + hb * P2;
+          const T inc2 = PWv(4, 0) + hb * kP1, inc3 = PWv(4, 1) + hb * kP2;
+          if (has_c) {
+            // compensated sum y + inc, the rounding error carried in C
+            T* cc_ = A.bufs[A.c_buf];
+            T v, s;
+            v = inc0 - PWv(5, 0); s = y0v + v; cc_[e0] = (s - y0v) - v; yo[e0] = s;
+            v = inc1 - PWv(5, 1); s = y1v + v; cc_[e0 + cs] = (s - y1v) - v; yo[e0 + cs] = s;
+            v = inc2 - PWv(6, 0); s = y2v + v; cc_[e0 + 2 * cs] = (s - y2v) - v; yo[e0 + 2 * cs] = s;
+            v = inc3 - PWv(6, 1); s = y3v + v; cc_[e0 + 3 * cs] = (s - y3v) - v; yo[e0 + 3 * cs] = s;
           } else {
-            A.yout[e0] = yn0 + inc0;
-            A.yout[e0 + B.cs] = yn1 + inc1;
-            A.yout[e0 + 2 * B.cs] = yn2 + inc2;
-            A.yout[e0 + 3 * B.cs] = yn3 + inc3;
+            yo[e0] = y0v + inc0;
+            yo[e0 + cs] = y1v + inc1;
+            yo[e0 + 2 * cs] = y2v + inc2;
+            yo[e0 + 3 * cs] = y3v + inc3;
           }
         }
-
-        if (diag) {
-          // plaquette windings around this cell (12 plaquettes, 3 owned)
+        if (DIAG) {
+          // windings of the 12 plaquettes around the cell (3 owned by it)
           bool tagged = false;
           int owned = 0;
 #pragma unroll
           for (int w = 0; w < 3; ++w) {
-            // (u, v) in-plane unit offsets: normal z: (x, y); x: (y, z); y: (z, x)
+            // in-plane unit offsets (u, v): normal z: (x, y); x: (y, z); y: (z, x)
             const int ux = (w == 0) ? 1 : 0, uy = (w == 1) ? 1 : 0, uz = (w == 2) ? 1 : 0;
             const int vx = (w == 2) ? 1 : 0, vy = (w == 0) ? 1 : 0, vz = (w == 1) ? 1 : 0;
 #pragma unroll
@@ -248,13 +379,12 @@ __global__ void __launch_bounds__(TX* TY) stage_kernel(const StageArgs<T> A) {
 #pragma unroll
               for (int b = 0; b < 2; ++b) {
                 const int ox = -a * ux - b * vx, oy = -a * uy - b * vy, oz = -a * uz - b * vz;
-                const double r0 = (double)S(0, ox, oy, oz), i0 = (double)S(1, ox, oy, oz);
-                const double r1 = (double)S(0, ox + ux, oy + uy, oz + uz), i1 = (double)S(1, ox + ux, oy + uy, oz + uz);
-                const double r2c = (double)S(0, ox + ux + vx, oy + uy + vy, oz + uz + vz),
-                             i2c = (double)S(1, ox + ux + vx, oy + uy + vy, oz + uz + vz);
-                const double r3 = (double)S(0, ox + vx, oy + vy, oz + vz), i3 = (double)S(1, ox + vx, oy + vy, oz + vz);
-                const int Wn = edge_delta(r0, i0, r1, i1) + edge_delta(r1, i1, r2c, i2c) +
-                               edge_delta(r2c, i2c, r3, i3) + edge_delta(r3, i3, r0, i0);
+                const T r0 = S(0, ox, oy, oz), i0 = S(1, ox, oy, oz);
+                const T r1 = S(0, ox + ux, oy + uy, oz + uz), i1 = S(1, ox + ux, oy + uy, oz + uz);
+                const T rr = S(0, ox + ux + vx, oy + uy + vy, oz + uz + vz), ii = S(1, ox + ux + vx, oy + uy + vy, oz + uz + vz);
+                const T r3 = S(0, ox + vx, oy + vy, oz + vz), i3 = S(1, ox + vx, oy + vy, oz + vz);
+                const int Wn = edge_delta(r0, i0, r1, i1) + edge_delta(r1, i1, rr, ii) + edge_delta(rr, ii, r3, i3) +
+                               edge_delta(r3, i3, r0, i0);
                 if (Wn != 0) {
                   tagged = true;
                   if (a == 0 && b == 0) ++owned;
@@ -283,17 +413,36 @@ __global__ void __launch_bounds__(TX* TY) stage_kernel(const StageArgs<T> A) {
           }
         }
       }
-      __syncthreads();
     }
-    s_kin += (double)i_kin;
-    s_grad += (double)i_grad;
-    s_pot += (double)i_pot;
+    const bool last_of_item = (cc.q == cc.z1 + G - 1);
+    if (DIAG && last_of_item) {
+      s_kin += (double)i_kin;
+      s_grad += (double)i_grad;
+      s_pot += (double)i_pot;
+      i_kin = i_grad = i_pot = 0;
+    }
+    if (__syncthreads_or(!ok)) {
+      aborted = true;
+      break;
+    }
+    cursor_next<G>(cc, A.items, A.boxes, A.nitems, A.zlen);
   }
 
-  if (A.epart != nullptr || A.tagcount != nullptr) {
-    // fixed-order block reduction: warp shuffles, then warp 0 over warps
-    __shared__ double red[4][NT / 32];
-    __shared__ unsigned long long redt[NT / 32];
+  if (aborted) {
+    // latch the error and drain every copy still in flight (bounded)
+    if (tid == 0) {
+      atomicCAS(A.err, 0, DERR_TIMEOUT);
+      for (long long u = t; u < issued; ++u) mbar_wait(smem_u32(&bars[u % RPSI]), (unsigned)((u / RPSI) & 1));
+    }
+    __syncthreads();
+    return;
+  }
+
+  if (DIAG && (A.epart != nullptr || A.tagcount != nullptr)) {
+    // fixed-order block reduction: warp shuffles, then thread 0 over warps
+    constexpr int NW = TXY / 32;
+    __shared__ double red[4][NW];
+    __shared__ unsigned long long redt[NW];
     double v0 = s_kin, v1 = s_grad, v2 = s_pot, v3 = (double)n_pierced;
     unsigned long long vt = n_tagged;
 #pragma unroll
@@ -316,7 +465,7 @@ __global__ void __launch_bounds__(TX* TY) stage_kernel(const StageArgs<T> A) {
     if (tid == 0) {
       double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
       unsigned long long at = 0;
-      for (int w = 0; w < NT / 32; ++w) {
+      for (int w = 0; w < NW; ++w) {
         a0 += red[0][w];
         a1 += red[1][w];
         a2 += red[2][w];
@@ -334,38 +483,98 @@ __global__ void __launch_bounds__(TX* TY) stage_kernel(const StageArgs<T> A) {
   }
 }
 
-template <typename T, int G, int TX, int TY>
-static size_t stage_smem() {
-  return (size_t)(2 * G + 2) * 2 * (TY + 2 * G) * (TX + 8) * sizeof(T);
+// ---------------------------------------------------------------------------
+// host side: tensor maps, variant table, launch
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
 }
 
-template <typename T, int G, int TX, int TY>
-static int stage_occupancy() {
+// Tensor maps of every (box, buffer): kind 0 the halo'd psi box
+// {TX+8, TY+2G, 1, 2}, kind 1 the pointwise box {TX, TY, 1, 2}, over the
+// 4D view {pitch, pny, pnz, 4 components} of the box; out-of-range parts of
+// a box read as zero.
+static slh_status build_tmaps(slh_ctx* c, Level& L, int G, int TX, int TY, CUtensorMap** out) {
+  const unsigned long long key = ((unsigned long long)G << 32) | ((unsigned long long)TX << 16) | (unsigned)TY;
+  auto it = L.tmaps.find(key);
+  if (it != L.tmaps.end()) {
+    *out = static_cast<CUtensorMap*>(it->second);
+    return SLH_OK;
+  }
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return fail(SLH_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const size_t es = c->prec == SLH_F64 ? 8 : 4;
+  const int nb = (int)L.lay.boxes.size();
+  std::vector<CUtensorMap> maps((size_t)nb * SLH_NBUF * 2);
+  for (int b = 0; b < nb; ++b) {
+    const BoxDev& B = L.lay.boxes[b];
+    for (int k = 0; k < SLH_NBUF; ++k) {
+      for (int kind = 0; kind < 2; ++kind) {
+        CUtensorMap& m = maps[((size_t)b * SLH_NBUF + k) * 2 + kind];
+        memset(&m, 0, sizeof(m));
+        if (!L.buf[k]) continue;
+        void* base = static_cast<char*>(L.buf[k]) + (size_t)B.off * es;
+        cuuint64_t dims[4] = {(cuuint64_t)B.pitch, (cuuint64_t)B.pny, (cuuint64_t)B.pnz, 4};
+        cuuint64_t strides[3] = {(cuuint64_t)B.pitch * es, (cuuint64_t)B.pitch * B.pny * es, (cuuint64_t)B.cs * es};
+        cuuint32_t box[4] = {(cuuint32_t)(kind == 0 ? TX + 8 : TX), (cuuint32_t)(kind == 0 ? TY + 2 * G : TY), 1, 2};
+        cuuint32_t estr[4] = {1, 1, 1, 1};
+        CUresult r = enc(&m, es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+          return fail(SLH_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for box %d buffer %d", (int)r, b, k);
+      }
+    }
+  }
+  CUtensorMap* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(CUtensorMap) * maps.size());
+  if (e != cudaSuccess) return fail(SLH_ERR_NOMEM, "tensor maps: %s", cudaGetErrorString(e));
+  e = cudaMemcpy(d, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    return cuda_fail(e, "tensor maps upload");
+  }
+  L.tmaps[key] = d;
+  *out = d;
+  return SLH_OK;
+}
+
+template <typename T, int G, int TX, int TY, int P, bool DIAG>
+static slh_status launch_v(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s, int* ctas_used) {
+  using GE = Geo<T, G, TX, TY, P>;
   static int occ = -1;
   if (occ < 0) {
-    const size_t smem = stage_smem<T, G, TX, TY>();
-    cudaFuncSetAttribute(stage_kernel<T, G, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(stage_kernel<T, G, TX, TY, P, DIAG>, cudaFuncAttributeMaxDynamicSharedMemorySize, GE::SMEM);
     int o = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, stage_kernel<T, G, TX, TY>, TX * TY, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, stage_kernel<T, G, TX, TY, P, DIAG>, TX * TY, GE::SMEM);
     occ = o > 0 ? o : 1;
   }
-  return occ;
-}
-
-template <typename T, int G, int TX, int TY>
-static slh_status launch_t(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s,
-                           int* ctas_used) {
+  CUtensorMap* maps = nullptr;
+  slh_status st = build_tmaps(c, L, G, TX, TY, &maps);
+  if (st != SLH_OK) return st;
+  const Tile& tile = L.tile;
   StageArgs<T> A;
   A.boxes = L.d_boxes;
-  A.items = L.d_items;
-  A.nitems = L.nitems;
-  A.zlen = L.zlen;
+  A.items = tile.d_items;
+  A.nitems = tile.nitems;
+  A.zlen = tile.zlen;
   A.gl = c->g;
-  A.yin = static_cast<const T*>(s.yin);
-  A.yn = static_cast<const T*>(s.yn);
-  A.dacc = static_cast<T*>(s.dacc);
-  A.yout = static_cast<T*>(s.yout);
-  A.comp = static_cast<T*>(s.comp);
+  A.tmaps = maps;
+  A.in_buf = s.in_buf;
+  A.yn_buf = s.yn_buf;
+  A.d_buf = s.d_buf;
+  A.out_buf = s.out_buf;
+  A.c_buf = s.c_buf;
+  for (int k = 0; k < SLH_NBUF; ++k) A.bufs[k] = static_cast<T*>(L.buf[k]);
   A.stage = s.stage;
   A.eta_start = c->d_time + 2 * s.lev + (s.cur_eta ? 0 : 1);
   A.c_stage = s.c_stage;
@@ -382,49 +591,65 @@ static slh_status launch_t(slh_ctx* c, Level& L, const slh_eom_params& p, const 
   A.covered = s.covered;
   A.cov_shift = s.cov_shift;
   A.cov_nb = s.cov_nb;
-  const int occ = stage_occupancy<T, G, TX, TY>();
+  A.err = c->d_err;
   int grid = occ * c->num_sms;
-  if (grid > L.nitems) grid = L.nitems;
+  if (grid > tile.nitems) grid = tile.nitems;
   if (grid < 1) grid = 1;
   if (s.epart != nullptr && grid > L.epart_cap) grid = L.epart_cap;
   if (ctas_used) *ctas_used = grid;
-  if (L.nitems == 0) return SLH_OK;
-  stage_kernel<T, G, TX, TY><<<grid, TX * TY, stage_smem<T, G, TX, TY>(), c->stream>>>(A);
+  if (tile.nitems == 0) return SLH_OK;
+  stage_kernel<T, G, TX, TY, P, DIAG><<<grid, TX * TY, GE::SMEM, c->stream>>>(A);
   SLH_CUDA(cudaGetLastError());
   return SLH_OK;
 }
 
-template <typename T, int TY>
-static slh_status dispatch_g(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s, int* u) {
+template <typename T, int TX, int TY, int P, bool DIAG>
+static slh_status by_order(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s, int* u) {
   switch (p.lap_order) {
-    case 2: return launch_t<T, 1, 32, TY>(c, L, p, s, u);
-    case 4: return launch_t<T, 2, 32, TY>(c, L, p, s, u);
-    case 6: return launch_t<T, 3, 32, TY>(c, L, p, s, u);
+    case 2: return launch_v<T, 1, TX, TY, P, DIAG>(c, L, p, s, u);
+    case 4: return launch_v<T, 2, TX, TY, P, DIAG>(c, L, p, s, u);
+    case 6: return launch_v<T, 3, TX, TY, P, DIAG>(c, L, p, s, u);
     default: return fail(SLH_ERR_INVALID_ARG, "lap_order must be 2, 4 or 6 (got %d)", p.lap_order);
   }
 }
 
-slh_status launch_stage(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s,
-                        int* ctas_used) {
-  if (c->prec == SLH_F64) {
-    if (L.tile_y != 8) return fail(SLH_ERR_STATE, "tile mismatch");
-    return dispatch_g<double, 8>(c, L, p, s, ctas_used);
-  }
-  if (L.tile_y != 16) return fail(SLH_ERR_STATE, "tile mismatch");
-  return dispatch_g<float, 16>(c, L, p, s, ctas_used);
+template <typename T, int TX, int TY, int P>
+static slh_status by_diag(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s, int* u) {
+  const bool diag = s.tags != nullptr || s.epart != nullptr;
+  return diag ? by_order<T, TX, TY, P, true>(c, L, p, s, u) : by_order<T, TX, TY, P, false>(c, L, p, s, u);
 }
 
-int stage_grid(slh_ctx* c, Level& L, int order) {
-  int occ = 1;
-  const int G = order / 2;
-  if (c->prec == SLH_F64) {
-    occ = G == 1 ? stage_occupancy<double, 1, 32, 8>() : G == 2 ? stage_occupancy<double, 2, 32, 8>()
-                                                                 : stage_occupancy<double, 3, 32, 8>();
-  } else {
-    occ = G == 1 ? stage_occupancy<float, 1, 32, 16>() : G == 2 ? stage_occupancy<float, 2, 32, 16>()
-                                                                 : stage_occupancy<float, 3, 32, 16>();
+// Tile variants (x extent, y extent, pipeline depth) the autotuner chooses
+// among; variant 0 is the default.
+const TileVariant* tile_variants(int prec, int* n) {
+  static const TileVariant f32[] = {{32, 16, 2, 64}, {32, 8, 3, 64}, {32, 16, 3, 128}, {16, 16, 2, 64}};
+  static const TileVariant f64[] = {{32, 8, 2, 64}, {32, 4, 3, 64}, {16, 8, 2, 64}};
+  if (prec == SLH_F64) {
+    *n = 3;
+    return f64;
   }
-  return occ * c->num_sms;
+  *n = 4;
+  return f32;
+}
+
+slh_status launch_stage(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s, int* ctas_used) {
+  const TileVariant& v = L.tile.v;
+  if (c->prec == SLH_F64) {
+    if (v.tx == 32 && v.ty == 8 && v.p == 2) return by_diag<double, 32, 8, 2>(c, L, p, s, ctas_used);
+    if (v.tx == 32 && v.ty == 4 && v.p == 3) return by_diag<double, 32, 4, 3>(c, L, p, s, ctas_used);
+    if (v.tx == 16 && v.ty == 8 && v.p == 2) return by_diag<double, 16, 8, 2>(c, L, p, s, ctas_used);
+  } else {
+    if (v.tx == 32 && v.ty == 16 && v.p == 2) return by_diag<float, 32, 16, 2>(c, L, p, s, ctas_used);
+    if (v.tx == 32 && v.ty == 8 && v.p == 3) return by_diag<float, 32, 8, 3>(c, L, p, s, ctas_used);
+    if (v.tx == 32 && v.ty == 16 && v.p == 3) return by_diag<float, 32, 16, 3>(c, L, p, s, ctas_used);
+    if (v.tx == 16 && v.ty == 16 && v.p == 2) return by_diag<float, 16, 16, 2>(c, L, p, s, ctas_used);
+  }
+  return fail(SLH_ERR_STATE, "no stage kernel for tile %dx%d depth %d", v.tx, v.ty, v.p);
+}
+
+void free_tmaps(Level& L) {
+  for (auto& kv : L.tmaps) cudaFree(kv.second);
+  L.tmaps.clear();
 }
 
 }  // namespace slh

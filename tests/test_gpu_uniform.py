@@ -40,7 +40,7 @@ def test_config0_f64_100_steps_fields_and_tags():
         snap = download_domain(h, 0, boxes, N0) if step % 10 == 0 else None
         h.rk_step(0, DT0, p, flags=slh.SLH_FUSE_TAG)
         if snap is not None:
-            gtags = tags_domain(h.levels[0]["tags"].cpu().numpy(), boxes, N0)
+            gtags = tags_domain(h.fused_tags(0), boxes, N0)
             assert np.array_equal(gtags, owinding.cell_tags_periodic(snap[0], snap[1])), step
             tag_checks += 1
         y = ork4.rk4_step_periodic(y, eta, DT0, DX0, op)
@@ -199,3 +199,50 @@ def test_full_size_512_order6_sampled(prec):
         assert np.max(np.abs(got - exp)) <= tol * scale, (c3, got, exp)
     del h
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("prec,nvar", [("f64", 3), ("f32", 4)])
+def test_every_tile_variant_matches_oracle(prec, nvar):
+    """Each stage-kernel tile shape the autotuner may pick gives the oracle's
+    result (ragged 40-cell boxes, 6th order, fused tags in stage 1)."""
+    n, dx = 40, 0.125
+    p = slh.EOMParams(order=6)
+    y0 = inputs.gaussian_field(n, 5.0, seed=4)
+    boxes = [((0, 0, 0), (39, 39, 19)), ((0, 0, 20), (39, 39, 39))]
+    ref, eta = y0, 0.5
+    for _ in range(3):
+        ref = ork4.rk4_step_periodic(ref, eta, 0.02, dx, oparams(p))
+        eta += 0.02
+    otags = owinding.cell_tags_periodic(y0[0], y0[1])
+    tol = 1e-12 if prec == "f64" else 1e-5
+    for v in range(nvar):
+        h, _ = uniform_hierarchy(n, dx, prec=prec, nghost=3, bf=4, boxes=boxes, fused_tags=True)
+        h.set_tile(0, v)
+        upload(h, 0, y0, boxes)
+        h.set_eta(0.5)
+        snap = download_domain(h, 0, boxes, n)
+        h.rk_step(0, 0.02, p, flags=slh.SLH_FUSE_TAG)
+        assert np.array_equal(tags_domain(h.fused_tags(0), boxes, n),
+                              owinding.cell_tags_periodic(snap[0], snap[1])), v
+        if prec == "f64":
+            assert np.array_equal(tags_domain(h.fused_tags(0), boxes, n), otags)
+        for _ in range(2):
+            h.rk_step(0, 0.02, p)
+        g = download_domain(h, 0, boxes, n)
+        for c in range(4):
+            assert rel_l2(g[c], ref[c]) <= tol, (v, c, rel_l2(g[c], ref[c]))
+        h.close()
+
+
+def test_autotune_keeps_state_and_picks_a_variant():
+    n, dx = 64, 0.125
+    p = slh.EOMParams(order=6)
+    y0 = inputs.gaussian_field(n, 8.0, seed=6)
+    h, boxes = uniform_hierarchy(n, dx, prec="f32", nghost=3, bf=16)
+    upload(h, 0, y0, boxes)
+    h.set_eta(0.3)
+    before = h.get_state(0)
+    chosen, ms = h.autotune(0, p, reps=2)
+    assert 0 <= chosen < len(ms) and len(ms) == 4 and all(m > 0 for m in ms)
+    assert ms[chosen] == min(ms)
+    assert np.array_equal(before, h.get_state(0))
