@@ -617,6 +617,20 @@ slh_status slh_advance(slh_ctx* c, double dt0, const slh_eom_params* p, uint32_t
     c->graph_key = key;
   }
   if (!c->graph[parity]) {
+    // everything a launch sets up lazily (tensor maps, kernel attributes) is
+    // prepared before capture: allocations are not allowed while capturing
+    for (int l = 0; l < c->nlevels; ++l) {
+      for (int diag = 0; diag < 2; ++diag) {
+        StageLaunch sl;
+        memset(&sl, 0, sizeof(sl));
+        sl.dry = true;
+        sl.stage = 1;
+        sl.lev = l;
+        sl.c_buf = -1;
+        if (diag) sl.tags = reinterpret_cast<uint8_t*>(1);
+        if ((st = launch_stage(c, c->lev[l], *p, sl, nullptr)) != SLH_OK) return st;
+      }
+    }
     int saved[MAX_LEVELS][2];
     for (int l = 0; l < c->nlevels; ++l) {
       saved[l][0] = c->lev[l].role_y;

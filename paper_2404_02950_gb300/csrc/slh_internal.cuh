@@ -166,6 +166,7 @@ struct StageLaunch {
   int cov_shift, cov_nb;
   int lev;
   bool cur_eta;         // evaluate at eta[lev] (diagnostics) instead of eta_start[lev] + c_stage
+  bool dry;             // set up tensor maps and kernel attributes only, launch nothing
 };
 slh_status launch_stage(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s,
                         int* ctas_used);

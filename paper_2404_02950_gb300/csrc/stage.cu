@@ -561,6 +561,7 @@ static slh_status launch_v(slh_ctx* c, Level& L, const slh_eom_params& p, const 
   CUtensorMap* maps = nullptr;
   slh_status st = build_tmaps(c, L, G, TX, TY, &maps);
   if (st != SLH_OK) return st;
+  if (s.dry) return SLH_OK;   // preparation only (before stream capture)
   const Tile& tile = L.tile;
   StageArgs<T> A;
   A.boxes = L.d_boxes;
