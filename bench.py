@@ -223,7 +223,7 @@ def run_ours(args, rank, world, local_rank, dist):
         from paper_2404_02950_gb300 import build
         build.build()
     torch.cuda.set_device(local_rank)
-    n, K, W = N_CELLS, args.steps, args.warmup
+    n, K, W = args.cells, args.steps, args.warmup
     y0 = inputs.gaussian_field(n, n / 16.0, seed=rank)
     boxes = [((0, 0, 0), (n - 1, n - 1, n - 1))]
     dense = slh.dense_from_boxes(y0, boxes)
@@ -235,6 +235,10 @@ def run_ours(args, rank, world, local_rank, dist):
     with ClockSampler(_gpu_index(local_rank)) as clk:
         h32, r32 = _time_form(slh, torch, "f32", dense, n, K, W, dist, flags)
     clocks = clk.summary()
+    if args.profile_only:
+        # short run for profilers: no e2e leg, no FP64 form, no JSON line
+        h32.close()
+        return
 
     # end to end through the C ABI with host buffers: upload the step's input
     # from pinned memory, advance, read the step's energy back
@@ -284,7 +288,7 @@ def run_ours(args, rank, world, local_rank, dist):
         "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": n ** 3, "order": ORDER, "precision": "FP32 + Kahan",
+        "config": {"workload": WORKLOAD if n == N_CELLS else WORKLOAD.replace("512^3", f"{n}^3"), "cells": n ** 3, "order": ORDER, "precision": "FP32 + Kahan",
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (10.9 GB of level buffers)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -315,6 +319,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cells", type=int, default=N_CELLS, help="lattice cells per axis (default 512)")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="time only the FP32 form and print nothing (for ncu captures of a small case)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

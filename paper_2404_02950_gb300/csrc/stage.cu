@@ -271,145 +271,163 @@ __global__ void __launch_bounds__(TX* TY, 1) stage_kernel(const StageArgs<T> A) 
     const bool ok = mbar_wait(smem_u32(&bars[slot]), (unsigned)((t / RPSI) & 1));
 
     const int z = cc.q - G;
-    if (ok && z >= cc.z0) {
-      if (cc.box != cur_box) {
-        B = A.boxes[cc.box];
-        cur_box = cc.box;
+    const bool compute = ok && z >= cc.z0;
+    // diagnostics need the plaquette masks of plane z0-1 too: the last
+    // prologue step of an item computes them
+    const bool premask = DIAG && ok && z == cc.z0 - 1;
+    if ((compute || premask) && cc.box != cur_box) {
+      B = A.boxes[cc.box];
+      cur_box = cc.box;
+    }
+    const int x = cc.x0 + tx, y = cc.y0 + ty;
+    const bool active = (compute || premask) && x < B.n[0] && y < B.n[1];
+    const T* ring = reinterpret_cast<const T*>(psi_base);
+    auto S = [&](int c, int dx, int dy, int dz) -> T {
+      const int sl = (int)((t + (RPSI - G) + dz) % RPSI);
+      return ring[(sl * (GE::PSI_STRIDE / (int)sizeof(T))) + c * PLANE + (ty + G + dy) * SXL + 4 + tx + dx];
+    };
+    T p1 = 0, p2 = 0, l1 = 0, l2 = 0, P1 = 0, P2 = 0, r2 = 0;
+    if (compute && active) {
+      const T* pwp = reinterpret_cast<const T*>(pw_base + (int)(t % RPW) * GE::PW_STRIDE);
+      auto PWv = [&](int box, int comp) -> T { return pwp[box * 2 * TXY + comp * TXY + ty * TX + tx]; };
+      p1 = S(0, 0, 0, 0);
+      p2 = S(1, 0, 0, 0);
+      if (sizeof(T) == 8) {
+        // textbook form sum_m w_m (f(+m) + f(-m)) + 3 w_0 f(0): fewest FP64 operations
+        T a1 = (T)(3.0 * lap_w<G>(0)) * p1, a2 = (T)(3.0 * lap_w<G>(0)) * p2;
+#pragma unroll
+        for (int m = 1; m <= G; ++m) {
+          const T w = (T)lap_w<G>(m);
+          a1 += w * (((S(0, m, 0, 0) + S(0, -m, 0, 0)) + (S(0, 0, m, 0) + S(0, 0, -m, 0))) +
+                     (S(0, 0, 0, m) + S(0, 0, 0, -m)));
+          a2 += w * (((S(1, m, 0, 0) + S(1, -m, 0, 0)) + (S(1, 0, m, 0) + S(1, 0, -m, 0))) +
+                     (S(1, 0, 0, m) + S(1, 0, 0, -m)));
+        }
+        l1 = a1 * idx2;
+        l2 = a2 * idx2;
+      } else {
+        // difference form sum_m w_m ((f(+m) - f0) + (f(-m) - f0)): the
+        // differences of neighbouring values are exact, which keeps FP32
+        // cancellation error at the level of the curvature itself
+        T a1 = 0, a2 = 0;
+#pragma unroll
+        for (int m = 1; m <= G; ++m) {
+          const T w = (T)lap_w<G>(m);
+          a1 += w * ((((S(0, m, 0, 0) - p1) + (S(0, -m, 0, 0) - p1)) + ((S(0, 0, m, 0) - p1) + (S(0, 0, -m, 0) - p1))) +
+                     ((S(0, 0, 0, m) - p1) + (S(0, 0, 0, -m) - p1)));
+          a2 += w * ((((S(1, m, 0, 0) - p2) + (S(1, -m, 0, 0) - p2)) + ((S(1, 0, m, 0) - p2) + (S(1, 0, -m, 0) - p2))) +
+                     ((S(1, 0, 0, m) - p2) + (S(1, 0, 0, -m) - p2)));
+        }
+        l1 = a1 * idx2;
+        l2 = a2 * idx2;
       }
-      const int x = cc.x0 + tx, y = cc.y0 + ty;
-      if (x < B.n[0] && y < B.n[1]) {
-        const T* ring = reinterpret_cast<const T*>(psi_base);
-        auto S = [&](int c, int dx, int dy, int dz) -> T {
-          const int sl = (int)((t + (RPSI - G) + dz) % RPSI);
-          return ring[(sl * (GE::PSI_STRIDE / (int)sizeof(T))) + c * PLANE + (ty + G + dy) * SXL + 4 + tx + dx];
-        };
-        const T* pwp = reinterpret_cast<const T*>(pw_base + (int)(t % RPW) * GE::PW_STRIDE);
-        auto PWv = [&](int box, int comp) -> T { return pwp[box * 2 * TXY + comp * TXY + ty * TX + tx]; };
-        const T p1 = S(0, 0, 0, 0), p2 = S(1, 0, 0, 0);
-        T l1, l2;
-        if (sizeof(T) == 8) {
-          // textbook form sum_m w_m (f(+m) + f(-m)) + 3 w_0 f(0): fewest FP64 operations
-          T a1 = (T)(3.0 * lap_w<G>(0)) * p1, a2 = (T)(3.0 * lap_w<G>(0)) * p2;
-#pragma unroll
-          for (int m = 1; m <= G; ++m) {
-            const T w = (T)lap_w<G>(m);
-            a1 += w * (((S(0, m, 0, 0) + S(0, -m, 0, 0)) + (S(0, 0, m, 0) + S(0, 0, -m, 0))) +
-                       (S(0, 0, 0, m) + S(0, 0, 0, -m)));
-            a2 += w * (((S(1, m, 0, 0) + S(1, -m, 0, 0)) + (S(1, 0, m, 0) + S(1, 0, -m, 0))) +
-                       (S(1, 0, 0, m) + S(1, 0, 0, -m)));
-          }
-          l1 = a1 * idx2;
-          l2 = a2 * idx2;
+      P1 = PWv(0, 0);
+      P2 = PWv(0, 1);
+      r2 = p1 * p1 + p2 * p2;
+      const T pot = c_pot * (r2 - (T)1) + a_c;
+      const T kP1 = (-c_fric) * P1 + l1 - p1 * pot;
+      const T kP2 = (-c_fric) * P2 + l2 - p2 * pot;
+      const long long e0 = B.off + (long long)(z + gl) * B.pny * B.pitch + (long long)(y + gl) * B.pitch + x + XPAD;
+      const long long cs = B.cs;
+      if (stage == 1) {
+        T* yo = A.bufs[A.out_buf];
+        T* dd = A.bufs[A.d_buf];
+        yo[e0] = p1 + ha * P1;
+        yo[e0 + cs] = p2 + ha * P2;
+        yo[e0 + 2 * cs] = P1 + ha * kP1;
+        yo[e0 + 3 * cs] = P2 + ha * kP2;
+        dd[e0] = hb * P1;
+        dd[e0 + cs] = hb * P2;
+        dd[e0 + 2 * cs] = hb * kP1;
+        dd[e0 + 3 * cs] = hb * kP2;
+      } else if (stage == 2 || stage == 3) {
+        T* yo = A.bufs[A.out_buf];
+        T* dd = A.bufs[A.d_buf];
+        yo[e0] = PWv(1, 0) + ha * P1;
+        yo[e0 + cs] = PWv(1, 1) + ha * P2;
+        yo[e0 + 2 * cs] = PWv(2, 0) + ha * kP1;
+        yo[e0 + 3 * cs] = PWv(2, 1) + ha * kP2;
+        dd[e0] = PWv(3, 0) + hb * P1;
+        dd[e0 + cs] = PWv(3, 1) + hb * P2;
+        dd[e0 + 2 * cs] = PWv(4, 0) + hb * kP1;
+        dd[e0 + 3 * cs] = PWv(4, 1) + hb * kP2;
+      } else if (stage == 4) {
+        T* yo = A.bufs[A.out_buf];
+        const T y0v = PWv(1, 0), y1v = PWv(1, 1), y2v = PWv(2, 0), y3v = PWv(2, 1);
+        const T inc0 = PWv(3, 0) + hb * P1, inc1 = PWv(3, 1) + hb * P2;
+        const T inc2 = PWv(4, 0) + hb * kP1, inc3 = PWv(4, 1) + hb * kP2;
+        if (has_c) {
+          // compensated sum y + inc, the rounding error carried in C
+          T* cc_ = A.bufs[A.c_buf];
+          T v, sm;
+          v = inc0 - PWv(5, 0); sm = y0v + v; cc_[e0] = (sm - y0v) - v; yo[e0] = sm;
+          v = inc1 - PWv(5, 1); sm = y1v + v; cc_[e0 + cs] = (sm - y1v) - v; yo[e0 + cs] = sm;
+          v = inc2 - PWv(6, 0); sm = y2v + v; cc_[e0 + 2 * cs] = (sm - y2v) - v; yo[e0 + 2 * cs] = sm;
+          v = inc3 - PWv(6, 1); sm = y3v + v; cc_[e0 + 3 * cs] = (sm - y3v) - v; yo[e0 + 3 * cs] = sm;
         } else {
-          // difference form sum_m w_m ((f(+m) - f0) + (f(-m) - f0)): the
-          // differences of neighbouring values are exact, which keeps FP32
-          // cancellation error at the level of the curvature itself
-          T a1 = 0, a2 = 0;
-#pragma unroll
-          for (int m = 1; m <= G; ++m) {
-            const T w = (T)lap_w<G>(m);
-            a1 += w * ((((S(0, m, 0, 0) - p1) + (S(0, -m, 0, 0) - p1)) + ((S(0, 0, m, 0) - p1) + (S(0, 0, -m, 0) - p1))) +
-                       ((S(0, 0, 0, m) - p1) + (S(0, 0, 0, -m) - p1)));
-            a2 += w * ((((S(1, m, 0, 0) - p2) + (S(1, -m, 0, 0) - p2)) + ((S(1, 0, m, 0) - p2) + (S(1, 0, -m, 0) - p2))) +
-                       ((S(1, 0, 0, m) - p2) + (S(1, 0, 0, -m) - p2)));
-          }
-          l1 = a1 * idx2;
-          l2 = a2 * idx2;
+          yo[e0] = y0v + inc0;
+          yo[e0 + cs] = y1v + inc1;
+          yo[e0 + 2 * cs] = y2v + inc2;
+          yo[e0 + 3 * cs] = y3v + inc3;
         }
-        const T P1 = PWv(0, 0), P2 = PWv(0, 1);
-        const T r2 = p1 * p1 + p2 * p2;
-        const T pot = c_pot * (r2 - (T)1) + a_c;
-        const T kP1 = (-c_fric) * P1 + l1 - p1 * pot;
-        const T kP2 = (-c_fric) * P2 + l2 - p2 * pot;
-        const long long e0 = B.off + (long long)(z + gl) * B.pny * B.pitch + (long long)(y + gl) * B.pitch + x + XPAD;
-        const long long cs = B.cs;
-        if (stage == 1) {
-          T* yo = A.bufs[A.out_buf];
-          T* dd = A.bufs[A.d_buf];
-          yo[e0] = p1 + ha * P1;
-          yo[e0 + cs] = p2 + ha * P2;
-          yo[e0 + 2 * cs] = P1 + ha * kP1;
-          yo[e0 + 3 * cs] = P2 + ha * kP2;
-          dd[e0] = hb * P1;
-          dd[e0 + cs] = hb * P2;
-          dd[e0 + 2 * cs] = hb * kP1;
-          dd[e0 + 3 * cs] = hb * kP2;
-        } else if (stage == 2 || stage == 3) {
-          T* yo = A.bufs[A.out_buf];
-          T* dd = A.bufs[A.d_buf];
-          yo[e0] = PWv(1, 0) + ha * P1;
-          yo[e0 + cs] = PWv(1, 1) + ha * P2;
-          yo[e0 + 2 * cs] = PWv(2, 0) + ha * kP1;
-          yo[e0 + 3 * cs] = PWv(2, 1) + ha * kP2;
-          dd[e0] = PWv(3, 0) + hb * P1;
-          dd[e0 + cs] = PWv(3, 1) + hb * P2;
-          dd[e0 + 2 * cs] = PWv(4, 0) + hb * kP1;
-          dd[e0 + 3 * cs] = PWv(4, 1) + hb * kP2;
-        } else if (stage == 4) {
-          T* yo = A.bufs[A.out_buf];
-          const T y0v = PWv(1, 0), y1v = PWv(1, 1), y2v = PWv(2, 0), y3v = PWv(2, 1);
-          const T inc0 = PWv(3, 0) + hb * P1, inc1 = PWv(3, 1) + hb * P2;
-          const T inc2 = PWv(4, 0) + hb * kP1, inc3 = PWv(4, 1) + hb * kP2;
-          if (has_c) {
-            // compensated sum y + inc, the rounding error carried in C
-            T* cc_ = A.bufs[A.c_buf];
-            T v, s;
-            v = inc0 - PWv(5, 0); s = y0v + v; cc_[e0] = (s - y0v) - v; yo[e0] = s;
-            v = inc1 - PWv(5, 1); s = y1v + v; cc_[e0 + cs] = (s - y1v) - v; yo[e0 + cs] = s;
-            v = inc2 - PWv(6, 0); s = y2v + v; cc_[e0 + 2 * cs] = (s - y2v) - v; yo[e0 + 2 * cs] = s;
-            v = inc3 - PWv(6, 1); s = y3v + v; cc_[e0 + 3 * cs] = (s - y3v) - v; yo[e0 + 3 * cs] = s;
-          } else {
-            yo[e0] = y0v + inc0;
-            yo[e0 + cs] = y1v + inc1;
-            yo[e0 + 2 * cs] = y2v + inc2;
-            yo[e0 + 3 * cs] = y3v + inc3;
-          }
+      }
+    }
+    if (DIAG) {
+      // Plaquette windings.  Edge terms are antisymmetric (delta(b,a) =
+      // -delta(a,b)), so the three plaquettes owned by a cell follow from the
+      // 9 edges leaving it and its +x, +y, +z neighbours; each cell publishes
+      // its 3-bit "winding != 0" mask for plane z in shared memory, and its
+      // tag is the OR over the 12 plaquettes it is a corner of (owners c,
+      // c-u, c-v, c-u-v), read back from the masks of planes z and z-1.
+      __shared__ unsigned char mk[2][TY + 1][TX + 1];
+      auto E = [&](int ax, int ay, int az, int bx, int by, int bz) -> int {
+        return edge_delta(S(0, ax, ay, az), S(1, ax, ay, az), S(0, bx, by, bz), S(1, bx, by, bz));
+      };
+      auto mask_at = [&](int ox, int oy) -> unsigned {
+        const int ex_c = E(ox, oy, 0, ox + 1, oy, 0), ey_c = E(ox, oy, 0, ox, oy + 1, 0);
+        const int ez_c = E(ox, oy, 0, ox, oy, 1);
+        const int ey_cx = E(ox + 1, oy, 0, ox + 1, oy + 1, 0), ex_cy = E(ox, oy + 1, 0, ox + 1, oy + 1, 0);
+        const int ez_cy = E(ox, oy + 1, 0, ox, oy + 1, 1), ey_cz = E(ox, oy, 1, ox, oy + 1, 1);
+        const int ex_cz = E(ox, oy, 1, ox + 1, oy, 1), ez_cx = E(ox + 1, oy, 0, ox + 1, oy, 1);
+        const int wxy = ex_c + ey_cx - ex_cy - ey_c;   // normal z: c, c+x, c+x+y, c+y
+        const int wyz = ey_c + ez_cy - ey_cz - ez_c;   // normal x: c, c+y, c+y+z, c+z
+        const int wzx = ez_c + ex_cz - ez_cx - ex_c;   // normal y: c, c+z, c+z+x, c+x
+        return (wxy != 0 ? 1u : 0u) | (wyz != 0 ? 2u : 0u) | (wzx != 0 ? 4u : 0u);
+      };
+      const int pz = z & 1;
+      unsigned own = 0;
+      if (active) {
+        own = mask_at(0, 0);
+        mk[pz][ty + 1][tx + 1] = (unsigned char)own;
+        if (tx == 0) mk[pz][ty + 1][0] = (unsigned char)mask_at(-1, 0);
+        if (ty == 0) mk[pz][0][tx + 1] = (unsigned char)mask_at(0, -1);
+        if (tx == 0 && ty == 0) mk[pz][0][0] = (unsigned char)mask_at(-1, -1);
+      }
+      __syncthreads();
+      if (compute && active) {
+        const int pm = pz ^ 1;
+        const unsigned m00 = own, m0x = mk[pz][ty + 1][tx], m0y = mk[pz][ty][tx + 1], m0xy = mk[pz][ty][tx];
+        const unsigned q00 = mk[pm][ty + 1][tx + 1], q0y = mk[pm][ty][tx + 1], q0x = mk[pm][ty + 1][tx];
+        const unsigned tg = ((m00 | m0x | m0y | m0xy) & 1u) | ((m00 | m0y | q00 | q0y) & 2u) |
+                            ((m00 | q00 | m0x | q0x) & 4u);
+        const bool tagged = tg != 0;
+        if (A.tags != nullptr) {
+          A.tags[B.voff + ((long long)z * B.n[1] + y) * B.n[0] + x] = tagged ? 1 : 0;
+          n_tagged += tagged ? 1 : 0;
         }
-        if (DIAG) {
-          // windings of the 12 plaquettes around the cell (3 owned by it)
-          bool tagged = false;
-          int owned = 0;
-#pragma unroll
-          for (int w = 0; w < 3; ++w) {
-            // in-plane unit offsets (u, v): normal z: (x, y); x: (y, z); y: (z, x)
-            const int ux = (w == 0) ? 1 : 0, uy = (w == 1) ? 1 : 0, uz = (w == 2) ? 1 : 0;
-            const int vx = (w == 2) ? 1 : 0, vy = (w == 0) ? 1 : 0, vz = (w == 1) ? 1 : 0;
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-#pragma unroll
-              for (int b = 0; b < 2; ++b) {
-                const int ox = -a * ux - b * vx, oy = -a * uy - b * vy, oz = -a * uz - b * vz;
-                const T r0 = S(0, ox, oy, oz), i0 = S(1, ox, oy, oz);
-                const T r1 = S(0, ox + ux, oy + uy, oz + uz), i1 = S(1, ox + ux, oy + uy, oz + uz);
-                const T rr = S(0, ox + ux + vx, oy + uy + vy, oz + uz + vz), ii = S(1, ox + ux + vx, oy + uy + vy, oz + uz + vz);
-                const T r3 = S(0, ox + vx, oy + vy, oz + vz), i3 = S(1, ox + vx, oy + vy, oz + vz);
-                const int Wn = edge_delta(r0, i0, r1, i1) + edge_delta(r1, i1, rr, ii) + edge_delta(rr, ii, r3, i3) +
-                               edge_delta(r3, i3, r0, i0);
-                if (Wn != 0) {
-                  tagged = true;
-                  if (a == 0 && b == 0) ++owned;
-                }
-              }
-            }
+        if (A.epart != nullptr) {
+          bool cov = false;
+          if (A.covered != nullptr) {
+            const int gx = (B.lo[0] + x) >> A.cov_shift, gy = (B.lo[1] + y) >> A.cov_shift,
+                      gz = (B.lo[2] + z) >> A.cov_shift;
+            cov = A.covered[((long long)gz * A.cov_nb + gy) * A.cov_nb + gx] != 0;
           }
-          if (A.tags != nullptr) {
-            A.tags[B.voff + ((long long)z * B.n[1] + y) * B.n[0] + x] = tagged ? 1 : 0;
-            n_tagged += tagged ? 1 : 0;
-          }
-          if (A.epart != nullptr) {
-            bool cov = false;
-            if (A.covered != nullptr) {
-              const int gx = (B.lo[0] + x) >> A.cov_shift, gy = (B.lo[1] + y) >> A.cov_shift,
-                        gz = (B.lo[2] + z) >> A.cov_shift;
-              cov = A.covered[((long long)gz * A.cov_nb + gy) * A.cov_nb + gx] != 0;
-            }
-            if (!cov) {
-              const T dd = r2 - (T)1;
-              i_kin += (T)0.5 * (P1 * P1 + P2 * P2);
-              i_grad += (T)(-0.5) * (p1 * l1 + p2 * l2);
-              i_pot += ((T)0.25 * c_pot) * (dd * dd) + ((T)0.5 * a_c) * r2;
-              n_pierced += owned;
-            }
+          if (!cov) {
+            const T dd = r2 - (T)1;
+            i_kin += (T)0.5 * (P1 * P1 + P2 * P2);
+            i_grad += (T)(-0.5) * (p1 * l1 + p2 * l2);
+            i_pot += ((T)0.25 * c_pot) * (dd * dd) + ((T)0.5 * a_c) * r2;
+            n_pierced += __popc(own);
           }
         }
       }
