@@ -112,19 +112,20 @@ __device__ __forceinline__ int edge_delta(double ar, double ai, double br, doubl
 // difference exceeds the worst-case rounding error (each product is within
 // 2^-24 of its value, the difference within 2^-24 more); otherwise the
 // products, exact in FP64, are formed in FP64.  Same sign as the FP64 form.
+// near-tie fallback kept out of line so the FP64 work is never if-converted
+// into the common path
+__device__ __noinline__ float exact_cross_sign(float ar, float ai, float br, float bi) {
+  const double X = __dsub_rn(__dmul_rn((double)ar, (double)bi), __dmul_rn((double)ai, (double)br));
+  return X > 0.0 ? 1.0f : (X < 0.0 ? -1.0f : 0.0f);
+}
+
 __device__ __forceinline__ int edge_delta(float ar, float ai, float br, float bi) {
   const bool ua = ai >= 0.0f, ub = bi >= 0.0f;
   if (ua == ub) return 0;
   const float p = __fmul_rn(ar, bi), q = __fmul_rn(ai, br);
   const float d = __fsub_rn(p, q);
   const float bound = __fmul_rn(__fadd_rn(fabsf(p), fabsf(q)), 4.76837158203125e-07f);  // 2^-21
-  float s;
-  if (fabsf(d) > bound && bound > 1e-30f) {
-    s = d;
-  } else {
-    const double X = __dsub_rn(__dmul_rn((double)ar, (double)bi), __dmul_rn((double)ai, (double)br));
-    s = X > 0.0 ? 1.0f : (X < 0.0 ? -1.0f : 0.0f);
-  }
+  const float s = (fabsf(d) > bound && bound > 1e-30f) ? d : exact_cross_sign(ar, ai, br, bi);
   if (ua) return s > 0.0f ? 1 : 0;
   return s < 0.0f ? -1 : 0;
 }
@@ -220,8 +221,8 @@ __global__ void __launch_bounds__(TX* TY, 1) stage_kernel(const StageArgs<T> A) 
   pc = cc;
 
   // issue the copies of load step t (cursor c) -- elected thread only
-  auto issue = [&](const Cursor& c, long long t) {
-    const int slot = (int)(t % RPSI);
+  // (slot = load step mod RPSI, pslot = load step mod RPW)
+  auto issue = [&](const Cursor& c, int slot, int pslot) {
     const unsigned bar = smem_u32(&bars[slot]);
     const bool pw = (c.q - G >= c.z0);
     mbar_expect_tx(bar, (unsigned)GE::PSI_BYTES + (pw ? step_bytes_pw : 0u));
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(TX* TY, 1) stage_kernel(const StageArgs<T> A) 
     tma_load4(smem_u32(psi_base + slot * GE::PSI_STRIDE), mb + 2 * A.in_buf + 0, c.x0, c.y0 - G + gl, c.q + gl, 0,
               bar);
     if (pw) {
-      unsigned char* dst = pw_base + (int)(t % RPW) * GE::PW_STRIDE;
+      unsigned char* dst = pw_base + pslot * GE::PW_STRIDE;
       const int xp = c.x0 + XPAD, yp = c.y0 + gl, zp = c.q - G + gl;
       tma_load4(smem_u32(dst), mb + 2 * A.in_buf + 1, xp, yp, zp, 2, bar);
       if (stage >= 2) {
@@ -245,10 +246,15 @@ __global__ void __launch_bounds__(TX* TY, 1) stage_kernel(const StageArgs<T> A) 
     }
   };
 
-  long long issued = 0;
+  // ring positions are tracked incrementally in 32-bit registers:
+  // consumer step t -> (slot, pslot, parity), producer step t+P -> (islot, ipslot)
+  int issued = 0, islot = 0, ipslot = 0;
   if (tid == 0) {
     for (int i = 0; i < P && pc.valid; ++i) {
-      issue(pc, issued++);
+      issue(pc, islot, ipslot);
+      ++issued;
+      if (++islot == RPSI) islot = 0;
+      if (++ipslot == RPW) ipslot = 0;
       cursor_next<G>(pc, A.items, A.boxes, A.nitems, A.zlen);
     }
   }
@@ -259,16 +265,21 @@ __global__ void __launch_bounds__(TX* TY, 1) stage_kernel(const StageArgs<T> A) 
   int cur_box = -1;
   BoxDev B;
   bool aborted = false;
+  const int thread_off = (ty + G) * SXL + 4 + tx;
+  constexpr int PSI_T = GE::PSI_STRIDE / (int)sizeof(T);
 
-  long long t = 0;
+  int t = 0, slot = 0, pslot = 0;
+  unsigned parity = 0;
   for (; cc.valid; ++t) {
     if (tid == 0 && pc.valid) {
       fence_proxy_async();
-      issue(pc, issued++);
+      issue(pc, islot, ipslot);
+      ++issued;
+      if (++islot == RPSI) islot = 0;
+      if (++ipslot == RPW) ipslot = 0;
       cursor_next<G>(pc, A.items, A.boxes, A.nitems, A.zlen);
     }
-    const int slot = (int)(t % RPSI);
-    const bool ok = mbar_wait(smem_u32(&bars[slot]), (unsigned)((t / RPSI) & 1));
+    const bool ok = mbar_wait(smem_u32(&bars[slot]), parity);
 
     const int z = cc.q - G;
     const bool compute = ok && z >= cc.z0;
@@ -281,14 +292,18 @@ __global__ void __launch_bounds__(TX* TY, 1) stage_kernel(const StageArgs<T> A) 
     }
     const int x = cc.x0 + tx, y = cc.y0 + ty;
     const bool active = (compute || premask) && x < B.n[0] && y < B.n[1];
-    const T* ring = reinterpret_cast<const T*>(psi_base);
-    auto S = [&](int c, int dx, int dy, int dz) -> T {
-      const int sl = (int)((t + (RPSI - G) + dz) % RPSI);
-      return ring[(sl * (GE::PSI_STRIDE / (int)sizeof(T))) + c * PLANE + (ty + G + dy) * SXL + 4 + tx + dx];
-    };
+    // this thread's cell in each of the 2G+1 planes z-G..z+G of the ring
+    const T* pl[2 * G + 1];
+#pragma unroll
+    for (int k = 0; k <= 2 * G; ++k) {
+      int sl = slot - 2 * G + k;
+      if (sl < 0) sl += RPSI;
+      pl[k] = reinterpret_cast<const T*>(psi_base) + sl * PSI_T + thread_off;
+    }
+    auto S = [&](int c, int dx, int dy, int dz) -> T { return pl[dz + G][c * PLANE + dy * SXL + dx]; };
     T p1 = 0, p2 = 0, l1 = 0, l2 = 0, P1 = 0, P2 = 0, r2 = 0;
     if (compute && active) {
-      const T* pwp = reinterpret_cast<const T*>(pw_base + (int)(t % RPW) * GE::PW_STRIDE);
+      const T* pwp = reinterpret_cast<const T*>(pw_base + pslot * GE::PW_STRIDE);
       auto PWv = [&](int box, int comp) -> T { return pwp[box * 2 * TXY + comp * TXY + ty * TX + tx]; };
       p1 = S(0, 0, 0, 0);
       p2 = S(1, 0, 0, 0);
@@ -443,6 +458,11 @@ __global__ void __launch_bounds__(TX* TY, 1) stage_kernel(const StageArgs<T> A) 
       aborted = true;
       break;
     }
+    if (++slot == RPSI) {
+      slot = 0;
+      parity ^= 1u;
+    }
+    if (++pslot == RPW) pslot = 0;
     cursor_next<G>(cc, A.items, A.boxes, A.nitems, A.zlen);
   }
 
@@ -450,7 +470,7 @@ __global__ void __launch_bounds__(TX* TY, 1) stage_kernel(const StageArgs<T> A) 
     // latch the error and drain every copy still in flight (bounded)
     if (tid == 0) {
       atomicCAS(A.err, 0, DERR_TIMEOUT);
-      for (long long u = t; u < issued; ++u) mbar_wait(smem_u32(&bars[u % RPSI]), (unsigned)((u / RPSI) & 1));
+      for (int u = t; u < issued; ++u) mbar_wait(smem_u32(&bars[u % RPSI]), (unsigned)((u / RPSI) & 1));
     }
     __syncthreads();
     return;
