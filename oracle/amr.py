@@ -75,17 +75,33 @@ class Level:
         bf = self.bf
         return self.owner[kz // bf, ky // bf, kx // bf]
 
-    def gather(self, arrays, comp, kz, ky, kx):
-        """Values of valid cells (wrapped indices) from per-box arrays."""
+    def gather(self, sources, comps, kz, ky, kx):
+        """Values of valid cells (wrapped indices) from each list of per-box
+        arrays in ``sources``: shape (len(sources), len(comps)) + kz.shape."""
         own = self.owners_of(kz, ky, kx)
         if (own < 0).any():
             raise ValueError("coarse stencil reaches outside the coarser level (nesting)")
-        out = np.empty(kz.shape)
+        out = np.empty((len(sources), len(comps)) + kz.shape)
         g = self.g
-        for s in np.unique(own):
+        for s in range(len(self.boxes)):
             sel = own == s
+            if not sel.any():
+                continue
             lo = self.boxes[s][0]
-            out[sel] = arrays[s][comp][kz[sel] - lo[2] + g, ky[sel] - lo[1] + g, kx[sel] - lo[0] + g]
+            iz, iy, ix = kz[sel] - lo[2] + g, ky[sel] - lo[1] + g, kx[sel] - lo[0] + g
+            for si, arrays in enumerate(sources):
+                for ci, c in enumerate(comps):
+                    out[si, ci][sel] = arrays[s][c][iz, iy, ix]
+        return out
+
+    def dense(self, arrays, comps):
+        """The level's valid cells of ``comps`` as arrays over its whole
+        periodic domain, NaN where no box of the level lies."""
+        out = np.full((len(comps), self.n, self.n, self.n), np.nan)
+        for b, (lo, hi) in enumerate(self.boxes):
+            v = self.valid(b)
+            for ci, c in enumerate(comps):
+                out[ci, lo[2]:hi[2] + 1, lo[1]:hi[1] + 1, lo[0]:hi[0] + 1] = arrays[b][c][v[1:]]
         return out
 
     def set_dense(self, fields):
@@ -140,14 +156,20 @@ def fill_ghosts(level: Level, arrays, coarse: Level | None, alpha: float, interp
             if coarse is None:
                 raise ValueError("uncovered ghost cell on a level without a coarser level")
             nc = coarse.n
-            for c in comps:
-                def coarse_at(Kz, Ky, Kx, c=c):
-                    Kz, Ky, Kx = Kz % nc, Ky % nc, Kx % nc
-                    vo = coarse.gather(coarse.old, c, Kz, Ky, Kx)
-                    vn = coarse.gather(coarse.data, c, Kz, Ky, Kx)
-                    return interp.time_lerp(vo, vn, alpha)
-                arr[c][gpz[sel], gpy[sel], gpx[sel]] = interp.prolong_points(
-                    coarse_at, (wz[sel], wy[sel], wx[sel]), interp_type)
+
+            # coarse state at fraction alpha of its step, over its whole domain
+            Da = interp.time_lerp(coarse.dense(coarse.old, comps), coarse.dense(coarse.data, comps),
+                                  alpha).reshape(len(comps), -1)
+
+            def coarse_at(Kz, Ky, Kx):
+                v = Da[:, ((Kz % nc) * nc + Ky % nc) * nc + Kx % nc]
+                if np.isnan(v).any():
+                    raise ValueError("coarse stencil reaches outside the coarser level (nesting)")
+                return v
+
+            vals = interp.prolong_points(coarse_at, (wz[sel], wy[sel], wx[sel]), interp_type)
+            for ci, c in enumerate(comps):
+                arr[c][gpz[sel], gpy[sel], gpx[sel]] = vals[ci]
 
 
 def rhs_box(arr, g, dx, eta, p: EOMParams):
@@ -284,7 +306,8 @@ def prolong_level_from_coarse(fine: Level, coarse: Level, interp_type: int, comp
         kz, ky, kx = np.indices(tuple(hi[d] - lo[d] + 1 for d in (2, 1, 0)))
         kz, ky, kx = kz + lo[2], ky + lo[1], kx + lo[0]
         v = fine.valid(b)
-        for c in comps:
-            def coarse_at(Kz, Ky, Kx, c=c):
-                return coarse.gather(coarse.data, c, Kz % nc, Ky % nc, Kx % nc)
-            fine.data[b][c][v[1:]] = interp.prolong_points(coarse_at, (kz, ky, kx), interp_type)
+        def coarse_at(Kz, Ky, Kx):
+            return coarse.gather([coarse.data], comps, Kz % nc, Ky % nc, Kx % nc)[0]
+        vals = interp.prolong_points(coarse_at, (kz, ky, kx), interp_type)
+        for ci, c in enumerate(comps):
+            fine.data[b][c][v[1:]] = vals[ci]

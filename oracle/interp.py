@@ -91,23 +91,31 @@ def prolong_points(coarse_at, fine_idx, interp_type: int):
     coarse_at(kz, ky, kx) -> array of coarse values at integer coarse indices
     (the caller resolves periodicity, boxes and time interpolation).
     fine_idx = (fz, fy, fx) integer arrays of fine indices.
-    The sum runs over offsets z (outer), y, x (inner) in increasing order.
+    All stencil values are gathered in one call; the weighted sum then runs
+    over offsets z (outer), y, x (inner) in increasing order.
     """
-    fz, fy, fx = (np.asarray(a, dtype=np.int64) for a in fine_idx)
+    fz, fy, fx = (np.asarray(a, dtype=np.int64).ravel() for a in fine_idx)
+    shape = np.shape(fine_idx[0])
     W = weights_1d(interp_type)
     Pz, Py, Px = fz // 2, fy // 2, fx // 2
     rz, ry, rx = fz - 2 * Pz, fy - 2 * Py, fx - 2 * Px
     offs = W[0][0]
-    wz = [np.where(rz == 0, float(W[0][1][a]), float(W[1][1][a])) for a in range(len(offs))]
-    wy = [np.where(ry == 0, float(W[0][1][a]), float(W[1][1][a])) for a in range(len(offs))]
-    wx = [np.where(rx == 0, float(W[0][1][a]), float(W[1][1][a])) for a in range(len(offs))]
-    acc = np.zeros(fz.shape)
-    for a, oz in enumerate(offs):
-        for b, oy in enumerate(offs):
-            for c, ox in enumerate(offs):
-                v = coarse_at(Pz + oz, Py + oy, Px + ox)
-                acc = acc + (wz[a] * wy[b] * wx[c]) * v
-    return acc
+    no = len(offs)
+    wz = [np.where(rz == 0, float(W[0][1][a]), float(W[1][1][a])) for a in range(no)]
+    wy = [np.where(ry == 0, float(W[0][1][a]), float(W[1][1][a])) for a in range(no)]
+    wx = [np.where(rx == 0, float(W[0][1][a]), float(W[1][1][a])) for a in range(no)]
+    oz, oy, ox = np.meshgrid(offs, offs, offs, indexing="ij")
+    oz, oy, ox = oz.ravel(), oy.ravel(), ox.ravel()
+    V = coarse_at(Pz[:, None] + oz[None, :], Py[:, None] + oy[None, :], Px[:, None] + ox[None, :])
+    # V may carry leading axes (several components): (..., n, no^3)
+    acc = np.zeros(V.shape[:-1])
+    j = 0
+    for a in range(no):
+        for b in range(no):
+            for c in range(no):
+                acc = acc + (wz[a] * wy[b] * wx[c]) * V[..., j]
+                j += 1
+    return acc.reshape(V.shape[:-2] + shape)
 
 
 def restrict_block(fine):

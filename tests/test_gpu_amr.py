@@ -34,7 +34,7 @@ def _dense(level):
 
 def _oracle_hierarchy(p, nlev=3, itype=4):
     h = oamr.make_hierarchy(N0, DX0, DT0, G, BF, LEVEL_BOXES[:nlev], oparams(p), interp_type=itype, eta0=ETA0)
-    y = inputs.string_loop(N0, 7.0, 2.0, DX0)
+    y = inputs.string_loop(N0, 3.0, 2.0, DX0)
     h.levels[0].set_dense(y)
     for l in range(1, nlev):
         oamr.prolong_level_from_coarse(h.levels[l], h.levels[l - 1], itype)
