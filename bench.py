@@ -179,7 +179,7 @@ def _time_form(slh, torch, prec, y0_dense, n, K, W, dist, flags):
     """Warm up, then time K steps of one precision; returns a dict."""
     h = slh.Hierarchy(n, DX, nghost=3, bf=16, prec=prec, max_levels=1)
     boxes = [((0, 0, 0), (n - 1, n - 1, n - 1))]
-    h.init_level(0, boxes)
+    h.init_level(0, boxes, fused_tags=True)
     h.set_state(0, y0_dense.astype(h.np_dtype))
     h.set_eta(ETA0)
     p = slh.EOMParams(order=ORDER)
@@ -228,7 +228,7 @@ def run_ours(args, rank, world, local_rank, dist):
     boxes = [((0, 0, 0), (n - 1, n - 1, n - 1))]
     dense = slh.dense_from_boxes(y0, boxes)
     del y0
-    flags = slh.SLH_FUSE_ENERGY | slh.SLH_USE_GRAPH * 0
+    flags = slh.SLH_FUSE_TAG | slh.SLH_FUSE_ENERGY
     peak, peak_kind = _peaks()
 
     # FP32 + Kahan (headline), with clock sampling over its timed region

@@ -104,16 +104,15 @@ __device__ __forceinline__ int edge_delta(double ar, double ai, double br, doubl
   const bool ua = ai >= 0.0, ub = bi >= 0.0;
   if (ua == ub) return 0;
   const double X = __dsub_rn(__dmul_rn(ar, bi), __dmul_rn(ai, br));
-  if (ua) return X > 0.0 ? 1 : 0;
-  return X < 0.0 ? -1 : 0;
+  return (int)(ua && X > 0.0) - (int)(ub && X < 0.0);
 }
 
 // FP32 inputs: the sign of X from the rounded products whenever their
 // difference exceeds the worst-case rounding error (each product is within
 // 2^-24 of its value, the difference within 2^-24 more); otherwise the
 // products, exact in FP64, are formed in FP64.  Same sign as the FP64 form.
-// near-tie fallback kept out of line so the FP64 work is never if-converted
-// into the common path
+// The near-tie fallback is kept out of line so that FP64 work is never
+// if-converted into the common, branch-free path.
 __device__ __noinline__ float exact_cross_sign(float ar, float ai, float br, float bi) {
   const double X = __dsub_rn(__dmul_rn((double)ar, (double)bi), __dmul_rn((double)ai, (double)br));
   return X > 0.0 ? 1.0f : (X < 0.0 ? -1.0f : 0.0f);
@@ -121,13 +120,11 @@ __device__ __noinline__ float exact_cross_sign(float ar, float ai, float br, flo
 
 __device__ __forceinline__ int edge_delta(float ar, float ai, float br, float bi) {
   const bool ua = ai >= 0.0f, ub = bi >= 0.0f;
-  if (ua == ub) return 0;
   const float p = __fmul_rn(ar, bi), q = __fmul_rn(ai, br);
-  const float d = __fsub_rn(p, q);
+  float s = __fsub_rn(p, q);
   const float bound = __fmul_rn(__fadd_rn(fabsf(p), fabsf(q)), 4.76837158203125e-07f);  // 2^-21
-  const float s = (fabsf(d) > bound && bound > 1e-30f) ? d : exact_cross_sign(ar, ai, br, bi);
-  if (ua) return s > 0.0f ? 1 : 0;
-  return s < 0.0f ? -1 : 0;
+  if (ua != ub && !(fabsf(s) > bound && bound > 1e-30f)) s = exact_cross_sign(ar, ai, br, bi);
+  return (int)(ua && !ub && s > 0.0f) - (int)(!ua && ub && s < 0.0f);
 }
 
 // Central second-difference weights w_m, m = 0..G (w_0 the centre weight).
@@ -292,12 +289,14 @@ __global__ void __launch_bounds__(TX* TY, 1) stage_kernel(const StageArgs<T> A) 
     }
     const int x = cc.x0 + tx, y = cc.y0 + ty;
     const bool active = (compute || premask) && x < B.n[0] && y < B.n[1];
-    // this thread's cell in each of the 2G+1 planes z-G..z+G of the ring
+    // the 2G+1 planes z-G..z+G of the ring (plb: tile origin, pl: this thread's cell)
+    const T* plb[2 * G + 1];
     const T* pl[2 * G + 1];
 #pragma unroll
     for (int k = 0; k <= 2 * G; ++k) {
       int sl = slot - 2 * G + k;
       if (sl < 0) sl += RPSI;
+      plb[k] = reinterpret_cast<const T*>(psi_base) + sl * PSI_T + G * SXL + 4;
       pl[k] = reinterpret_cast<const T*>(psi_base) + sl * PSI_T + thread_off;
     }
     auto S = [&](int c, int dx, int dy, int dz) -> T { return pl[dz + G][c * PLANE + dy * SXL + dx]; };
@@ -388,40 +387,58 @@ __global__ void __launch_bounds__(TX* TY, 1) stage_kernel(const StageArgs<T> A) 
       }
     }
     if (DIAG) {
-      // Plaquette windings.  Edge terms are antisymmetric (delta(b,a) =
-      // -delta(a,b)), so the three plaquettes owned by a cell follow from the
-      // 9 edges leaving it and its +x, +y, +z neighbours; each cell publishes
-      // its 3-bit "winding != 0" mask for plane z in shared memory, and its
-      // tag is the OR over the 12 plaquettes it is a corner of (owners c,
-      // c-u, c-v, c-u-v), read back from the masks of planes z and z-1.
-      __shared__ unsigned char mk[2][TY + 1][TX + 1];
-      auto E = [&](int ax, int ay, int az, int bx, int by, int bz) -> int {
-        return edge_delta(S(0, ax, ay, az), S(1, ax, ay, az), S(0, bx, by, bz), S(1, bx, by, bz));
-      };
-      auto mask_at = [&](int ox, int oy) -> unsigned {
-        const int ex_c = E(ox, oy, 0, ox + 1, oy, 0), ey_c = E(ox, oy, 0, ox, oy + 1, 0);
-        const int ez_c = E(ox, oy, 0, ox, oy, 1);
-        const int ey_cx = E(ox + 1, oy, 0, ox + 1, oy + 1, 0), ex_cy = E(ox, oy + 1, 0, ox + 1, oy + 1, 0);
-        const int ez_cy = E(ox, oy + 1, 0, ox, oy + 1, 1), ey_cz = E(ox, oy, 1, ox, oy + 1, 1);
-        const int ex_cz = E(ox, oy, 1, ox + 1, oy, 1), ez_cx = E(ox + 1, oy, 0, ox + 1, oy, 1);
-        const int wxy = ex_c + ey_cx - ex_cy - ey_c;   // normal z: c, c+x, c+x+y, c+y
-        const int wyz = ey_c + ez_cy - ey_cz - ez_c;   // normal x: c, c+y, c+y+z, c+z
-        const int wzx = ez_c + ex_cz - ez_cx - ex_c;   // normal y: c, c+z, c+z+x, c+x
-        return (wxy != 0 ? 1u : 0u) | (wyz != 0 ? 2u : 0u) | (wzx != 0 ? 4u : 0u);
-      };
+      // Plaquette windings.  The edge term is antisymmetric (delta(b,a) =
+      // -delta(a,b)), so a plaquette's winding is the signed sum of the edges
+      // leaving its corners along +x, +y, +z.  Per plane: (1) every edge of
+      // the tile grown by one cell is evaluated once, spread evenly over the
+      // CTA; (2) the 3-bit "winding != 0" mask of each cell of the tile and of
+      // its low halo follows from those edges; (3) a cell's tag is the OR over
+      // the 12 plaquettes it is a corner of (owners c, c-u, c-v, c-u-v), read
+      // from the masks of planes z and z-1.
+      constexpr int EXW = TX + 2, EXH = TY + 2, NE = EXW * EXH;
+      constexpr int MW = TX + 1, MH = TY + 1, NM = MW * MH;
+      __shared__ signed char ed[5][EXH][EXW];     // e_x, e_y, e_z of plane z; e_x, e_y of plane z+1
+      __shared__ unsigned char mk[2][MH][MW];
+      const bool doit = compute || premask;      // uniform over the CTA
       const int pz = z & 1;
-      unsigned own = 0;
-      if (active) {
-        own = mask_at(0, 0);
-        mk[pz][ty + 1][tx + 1] = (unsigned char)own;
-        if (tx == 0) mk[pz][ty + 1][0] = (unsigned char)mask_at(-1, 0);
-        if (ty == 0) mk[pz][0][tx + 1] = (unsigned char)mask_at(0, -1);
-        if (tx == 0 && ty == 0) mk[pz][0][0] = (unsigned char)mask_at(-1, -1);
+      auto SA = [&](int c, int ax, int ay, int dz) -> T { return plb[dz + G][c * PLANE + ay * SXL + ax]; };
+      if (doit) {
+        for (int j = tid; j < NE; j += TXY) {
+          const int ex = j % EXW - 1, ey = j / EXW - 1;
+          const T r0 = SA(0, ex, ey, 0), i0 = SA(1, ex, ey, 0);
+          const T rx = SA(0, ex + 1, ey, 0), ix = SA(1, ex + 1, ey, 0);
+          const T rz = SA(0, ex, ey, 1), iz = SA(1, ex, ey, 1);
+          const T rzx = SA(0, ex + 1, ey, 1), izx = SA(1, ex + 1, ey, 1);
+          ed[0][ey + 1][ex + 1] = (signed char)edge_delta(r0, i0, rx, ix);
+          ed[2][ey + 1][ex + 1] = (signed char)edge_delta(r0, i0, rz, iz);
+          ed[3][ey + 1][ex + 1] = (signed char)edge_delta(rz, iz, rzx, izx);
+          if (ey < TY) {
+            const T ry = SA(0, ex, ey + 1, 0), iy = SA(1, ex, ey + 1, 0);
+            const T rzy = SA(0, ex, ey + 1, 1), izy = SA(1, ex, ey + 1, 1);
+            ed[1][ey + 1][ex + 1] = (signed char)edge_delta(r0, i0, ry, iy);
+            ed[4][ey + 1][ex + 1] = (signed char)edge_delta(rz, iz, rzy, izy);
+          }
+        }
+      }
+      __syncthreads();
+      if (doit) {
+        for (int j = tid; j < NM; j += TXY) {
+          const int mx = j % MW, my = j / MW;   // cell offset (mx-1, my-1) from (x0, y0)
+          const int ex_c = ed[0][my][mx], ey_c = ed[1][my][mx], ez_c = ed[2][my][mx];
+          const int ey_cx = ed[1][my][mx + 1], ez_cx = ed[2][my][mx + 1];
+          const int ex_cy = ed[0][my + 1][mx], ez_cy = ed[2][my + 1][mx];
+          const int ex_cz = ed[3][my][mx], ey_cz = ed[4][my][mx];
+          const int wxy = ex_c + ey_cx - ex_cy - ey_c;   // normal z: c, c+x, c+x+y, c+y
+          const int wyz = ey_c + ez_cy - ey_cz - ez_c;   // normal x: c, c+y, c+y+z, c+z
+          const int wzx = ez_c + ex_cz - ez_cx - ex_c;   // normal y: c, c+z, c+z+x, c+x
+          mk[pz][my][mx] = (unsigned char)((wxy != 0 ? 1 : 0) | (wyz != 0 ? 2 : 0) | (wzx != 0 ? 4 : 0));
+        }
       }
       __syncthreads();
       if (compute && active) {
         const int pm = pz ^ 1;
-        const unsigned m00 = own, m0x = mk[pz][ty + 1][tx], m0y = mk[pz][ty][tx + 1], m0xy = mk[pz][ty][tx];
+        const unsigned m00 = mk[pz][ty + 1][tx + 1], m0x = mk[pz][ty + 1][tx], m0y = mk[pz][ty][tx + 1],
+                       m0xy = mk[pz][ty][tx];
         const unsigned q00 = mk[pm][ty + 1][tx + 1], q0y = mk[pm][ty][tx + 1], q0x = mk[pm][ty + 1][tx];
         const unsigned tg = ((m00 | m0x | m0y | m0xy) & 1u) | ((m00 | m0y | q00 | q0y) & 2u) |
                             ((m00 | q00 | m0x | q0x) & 4u);
@@ -442,7 +459,7 @@ __global__ void __launch_bounds__(TX* TY, 1) stage_kernel(const StageArgs<T> A) 
             i_kin += (T)0.5 * (P1 * P1 + P2 * P2);
             i_grad += (T)(-0.5) * (p1 * l1 + p2 * l2);
             i_pot += ((T)0.25 * c_pot) * (dd * dd) + ((T)0.5 * a_c) * r2;
-            n_pierced += __popc(own);
+            n_pierced += __popc(m00);
           }
         }
       }
