@@ -256,8 +256,9 @@ slh_status slh_reduce_energy(slh_ctx* ctx, const slh_eom_params* p, int32_t mode
 slh_status slh_set_tile(slh_ctx* ctx, int32_t lev, int32_t variant);
 
 /* Autotuner: time every tile variant on level lev's own boxes (reps
- * launches of a stage that reads the state and writes only the scratch
- * buffers SLH_BUF_YA and SLH_BUF_D), keep the fastest.  *chosen receives its
+ * launches of an RK stage that reads the state, SLH_BUF_YA and SLH_BUF_D and
+ * writes only the scratch buffers SLH_BUF_YA and SLH_BUF_D), keep the
+ * fastest.  *chosen receives its
  * index, ms_out (may be NULL, one entry per variant) the mean milliseconds.
  * Call between steps, outside stream capture.  Synchronises.
  * Errors: INVALID_ARG, STATE, CUDA. */

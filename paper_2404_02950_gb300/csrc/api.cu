@@ -829,11 +829,12 @@ slh_status slh_autotune(slh_ctx* c, int32_t lev, const slh_eom_params* p, int32_
   float best_ms = 0.f;
   for (int v = 0; v < nv; ++v) {
     if ((st = set_tile(c, L, vs[v])) != SLH_OK) break;
-    // a stage-2 launch that reads the state and writes only scratch buffers
+    // a stage-2 launch with the traffic of a real one (three distinct input
+    // buffers) that writes only the scratch buffers YA and D
     StageLaunch sl;
     memset(&sl, 0, sizeof(sl));
     sl.stage = 2;
-    sl.in_buf = L.role_y;
+    sl.in_buf = SLH_BUF_YA;
     sl.yn_buf = L.role_y;
     sl.d_buf = SLH_BUF_D;
     sl.out_buf = SLH_BUF_YA;
