@@ -265,6 +265,30 @@ slh_status slh_set_tile(slh_ctx* ctx, int32_t lev, int32_t variant);
 slh_status slh_autotune(slh_ctx* ctx, int32_t lev, const slh_eom_params* p, int32_t reps, int32_t* chosen,
                         double* ms_out);
 
+/* Allocation-free energy reduction (the paper has no counterpart: this is a
+ * service for embedders).  For callers that cannot call cudaMalloc -- code
+ * running inside another library's stream-ordered section or a host callback
+ * where allocating would synchronise or is forbidden, or an embedder whose
+ * memory budget is handed out by its own allocator.  Computes the same five
+ * numbers as slh_reduce_energy for one periodic box, here for a dense
+ * lattice the caller owns: fields_dev holds psi1, psi2, Pi1, Pi2 as four
+ * consecutive n^3 arrays (x fastest), FP64 (prec SLH_F64) or FP32
+ * (SLH_F32_KAHAN); dx the spacing, eta the conformal time of the
+ * coefficients, p the Laplacian order and potential; out_dev receives the
+ * five doubles on the device, asynchronously on stream (a cudaStream_t).
+ * Nothing is allocated: the per-plane partial sums live in one fixed
+ * 128 KiB array in device global memory that is part of the library image
+ * (every GPU that loads the library holds it until the process exits),
+ * which limits the lattice side to n <= 4096 (larger n: SLH_ERR_OUT_OF_RANGE).
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  Every call overwrites the scratch rows it uses before
+ * reading them, so nothing needs clearing, but calls that overlap on the GPU
+ * (other streams, other threads) share the array and race.
+ * Errors: INVALID_ARG, OUT_OF_RANGE, CUDA. */
+slh_status slh_energy_noalloc(const void* fields_dev, int32_t n, int32_t prec, double dx, double eta,
+                              const slh_eom_params* p, double* out_dev, void* stream);
+
 /* Wait for the stream and return any latched device error (then clear it). */
 slh_status slh_sync(slh_ctx* ctx);
 

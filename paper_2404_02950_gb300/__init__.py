@@ -44,6 +44,7 @@ ABI_SYMBOLS = (
     "slh_set_state", "slh_get_state", "slh_set_eta", "slh_get_eta", "slh_rk_step",
     "slh_advance", "slh_fill_ghosts", "slh_tag", "slh_tag_blocks", "slh_regrid_boxes",
     "slh_reduce_energy", "slh_sync", "slh_profile", "slh_profile_read", "slh_set_tile", "slh_autotune",
+    "slh_energy_noalloc",
 )
 
 
@@ -115,6 +116,7 @@ def lib():
         "slh_profile_read": (i32, [vp, i32, P(dbl), P(i64), P(dbl)]),
         "slh_set_tile": (i32, [vp, i32, i32]),
         "slh_autotune": (i32, [vp, i32, P(slh_eom_params), i32, P(i32), P(dbl)]),
+        "slh_energy_noalloc": (i32, [vp, i32, i32, dbl, dbl, P(slh_eom_params), vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -170,6 +172,22 @@ def slh_regrid_boxes(tags, blocking_factor, n_error_buf, max_box, parent=None):
             continue
         _check(st)
         return [(tuple(out[i].lo), tuple(out[i].hi)) for i in range(nout.value)]
+
+
+def slh_energy_noalloc(fields_dev, n, dx, eta, params: EOMParams, out_dev, stream=None):
+    """Energy and string length of a dense periodic lattice without any
+    device allocation (for callers that cannot allocate; the library keeps
+    the reduction scratch in a fixed device array, lattice side <= 4096).
+    fields_dev: CUDA tensor (4, n, n, n) float64 or float32; out_dev: CUDA
+    float64 tensor of 5 elements, written asynchronously on ``stream``
+    (default: the current torch stream)."""
+    import torch
+    prec = SLH_F64 if fields_dev.dtype == torch.float64 else SLH_F32_KAHAN
+    st = torch.cuda.current_stream(fields_dev.device) if stream is None else stream
+    p = params.c()
+    _check(lib().slh_energy_noalloc(ctypes.c_void_p(fields_dev.data_ptr()), int(n), prec, float(dx), float(eta),
+                                    ctypes.byref(p), ctypes.c_void_p(out_dev.data_ptr()),
+                                    ctypes.c_void_p(st.cuda_stream)))
 
 
 def dense_from_boxes(fields, boxes):
