@@ -158,6 +158,23 @@ slh_status slh_level_layout(int32_t nghost, const slh_box* boxes, int32_t nboxes
 slh_status slh_init_level(slh_ctx* ctx, int32_t lev, const slh_box* boxes, int32_t nboxes,
                           void* const* bufs, uint8_t* tags_dev);
 
+/* Global regrid of a live level (Sec. 2.3): give level lev (1 <= lev <=
+ * number of levels; lev equal to it creates a new finest level) the boxes
+ * boxes[nboxes] with caller-owned buffers bufs[SLH_NBUF] laid out as for
+ * slh_init_level.  Every valid cell of the new boxes takes the old level's
+ * value where an old box covers it, otherwise the ratio-2 prolongation
+ * (interp_type 0/2/4) of level lev-1's current state, all four fields; the
+ * Kahan compensation is carried over where covered and zero elsewhere.  The
+ * new level's previous state equals its state and its eta that of lev-1.
+ * nboxes == 0 removes level lev and every finer level.  Finer levels keep
+ * their data but must be regridded (from the new lev) before the next
+ * slh_rk_step / slh_advance (SLH_ERR_STATE otherwise).  Regrid coarse to
+ * fine, at a synchronised time (after slh_advance).  The old buffers of lev
+ * are no longer referenced when the call returns (it synchronises).
+ * Errors: INVALID_ARG, OUT_OF_RANGE (nesting), STATE, NOMEM, CUDA. */
+slh_status slh_regrid_level(slh_ctx* ctx, int32_t lev, const slh_box* boxes, int32_t nboxes,
+                            void* const* bufs, uint8_t* tags_dev, int32_t interp_type);
+
 /* Copy the four fields of level lev from / to a dense valid-cell array
  * ([box][comp][z][y][x], context precision).  src/dst on the host
  * (is_host = 1, ideally pinned) or the device.  slh_set_state also sets the

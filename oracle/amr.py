@@ -311,3 +311,39 @@ def prolong_level_from_coarse(fine: Level, coarse: Level, interp_type: int, comp
         vals = interp.prolong_points(coarse_at, (kz, ky, kx), interp_type)
         for ci, c in enumerate(comps):
             fine.data[b][c][v[1:]] = vals[ci]
+
+
+def regrid_level(h: Hierarchy, lev: int, new_boxes):
+    """Give level ``lev`` (>= 1) the boxes ``new_boxes`` (Sec. 2.3 global
+    regrid): every valid cell of the new boxes takes the old level's value
+    where an old box of that level covers it, otherwise the prolongation of
+    the coarser level's current state (all four fields, the hierarchy's
+    interpolation type).  With no boxes the level and every finer one are
+    removed; ``lev == len(h.levels)`` creates a new finest level."""
+    C = h.levels[lev - 1]
+    old = h.levels[lev] if lev < len(h.levels) else None
+    if not new_boxes:
+        del h.levels[lev:]
+        return
+    L = Level(lev, new_boxes, C.n * 2, C.dx / 2, C.dt / 2, C.g, C.bf)
+    L.eta = C.eta
+    prolong_level_from_coarse(L, C, h.interp_type)
+    if old is not None:
+        g = L.g
+        for b, (lo, hi) in enumerate(L.boxes):
+            kz, ky, kx = np.indices(tuple(hi[d] - lo[d] + 1 for d in (2, 1, 0)))
+            kz, ky, kx = kz + lo[2], ky + lo[1], kx + lo[0]
+            own = old.owners_of(kz, ky, kx)
+            for s_ in range(len(old.boxes)):
+                sel = own == s_
+                if not sel.any():
+                    continue
+                olo = old.boxes[s_][0]
+                for c in range(4):
+                    L.data[b][c][kz[sel] - lo[2] + g, ky[sel] - lo[1] + g, kx[sel] - lo[0] + g] = \
+                        old.data[s_][c][kz[sel] - olo[2] + g, ky[sel] - olo[1] + g, kx[sel] - olo[0] + g]
+    if old is None:
+        h.levels.append(L)
+    else:
+        h.levels[lev] = L
+

@@ -44,7 +44,7 @@ ABI_SYMBOLS = (
     "slh_set_state", "slh_get_state", "slh_set_eta", "slh_get_eta", "slh_rk_step",
     "slh_advance", "slh_fill_ghosts", "slh_tag", "slh_tag_blocks", "slh_regrid_boxes",
     "slh_reduce_energy", "slh_sync", "slh_profile", "slh_profile_read", "slh_set_tile", "slh_autotune",
-    "slh_energy_noalloc",
+    "slh_energy_noalloc", "slh_regrid_level",
 )
 
 
@@ -117,6 +117,7 @@ def lib():
         "slh_set_tile": (i32, [vp, i32, i32]),
         "slh_autotune": (i32, [vp, i32, P(slh_eom_params), i32, P(i32), P(dbl)]),
         "slh_energy_noalloc": (i32, [vp, i32, i32, dbl, dbl, P(slh_eom_params), vp, vp]),
+        "slh_regrid_level": (i32, [vp, i32, P(slh_box), i32, P(vp), vp, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -270,6 +271,57 @@ class Hierarchy:
         and previous-state buffers swap roles after every RK step)."""
         info = self.levels[lev]
         return info["bufs"][SLH_BUF_Y if info["steps"] % 2 == 0 else SLH_BUF_YB]
+
+    def _alloc_level(self, boxes, fused_tags):
+        torch = self.torch
+        _, geom, total, nvalid = slh_level_layout(self.nghost, boxes)
+        bufs = [None if (i == SLH_BUF_C and self.prec == SLH_F64)
+                else torch.empty(int(total), dtype=self.dtype, device=self.device) for i in range(SLH_NBUF)]
+        tags = torch.zeros(int(nvalid), dtype=torch.uint8, device=self.device) if fused_tags else None
+        return bufs, tags, int(total), int(nvalid)
+
+    def regrid_level(self, lev, boxes, interp_type=4, fused_tags=None):
+        """Give level ``lev`` new boxes (copy where the old level covers,
+        prolong elsewhere); empty ``boxes`` removes it and every finer level."""
+        if not boxes:
+            _check(lib().slh_regrid_level(self.h, lev, None, 0, None, None, interp_type))
+            for l in list(self.levels):
+                if l >= lev:
+                    del self.levels[l]
+            return None
+        old = self.levels.get(lev)
+        if fused_tags is None:
+            fused_tags = old is not None and old["tags"] is not None
+        bufs, tags, total, nvalid = self._alloc_level(boxes, fused_tags)
+        ptrs = (ctypes.c_void_p * SLH_NBUF)(*[b.data_ptr() if b is not None else None for b in bufs])
+        _check(lib().slh_regrid_level(self.h, lev, _boxes(boxes), len(boxes), ptrs,
+                                      ctypes.c_void_p(tags.data_ptr()) if tags is not None else None, interp_type))
+        self.levels[lev] = dict(boxes=list(boxes), bufs=bufs, tags=tags, nvalid=nvalid, total=total, steps=0)
+        return self.levels[lev]
+
+    def regrid(self, max_levels, n_error_buf, max_box, interp_type=4):
+        """Global regrid of every level from level 0 upwards (Sec. 2.2-2.3):
+        tags of level l grown by n_error_buf and coarsened to blocks on the
+        device (slh_tag_blocks), clustered on the host (slh_regrid_boxes, in
+        block units), then slh_regrid_level(l + 1).  Returns the box lists."""
+        r = self.bf // 2
+        out = []
+        for l in range(0, max_levels - 1):
+            if l not in self.levels:
+                break
+            mask = self.tag_blocks(l, n_error_buf)
+            parent = None
+            if l > 0:
+                parent = [(tuple(v // r for v in lo), tuple((v + 1) // r - 1 for v in hi))
+                          for lo, hi in self.levels[l]["boxes"]]
+            # in block units: blocking factor 2 (one block per mask cell), no further growth
+            blocks = slh_regrid_boxes(mask, 2, 0, 2 * (max_box // self.bf), parent=parent)
+            boxes = [(tuple(v * r for v in lo), tuple((v + 1) * r - 1 for v in hi)) for lo, hi in blocks]
+            self.regrid_level(l + 1, boxes, interp_type)
+            out.append(boxes)
+            if not boxes:
+                break
+        return out
 
     def set_state(self, lev, dense):
         """dense: host numpy array (or CUDA tensor) in the dense valid-cell

@@ -240,81 +240,80 @@ void slh_destroy(slh_ctx* c) {
   delete c;
 }
 
-slh_status slh_init_level(slh_ctx* c, int32_t lev, const slh_box* boxes, int32_t nboxes, void* const* bufs,
-                          uint8_t* tags_dev) {
-  if (!c || !boxes || !bufs || nboxes < 1) return fail(SLH_ERR_INVALID_ARG, "init_level: null argument or no boxes");
-  if (lev < 0 || lev >= c->max_levels) return fail(SLH_ERR_OUT_OF_RANGE, "init_level: level %d outside [0,%d)", lev, c->max_levels);
-  if (lev > c->nlevels) return fail(SLH_ERR_STATE, "init_level: level %d defined before level %d", lev, c->nlevels);
+}  // extern "C"
+
+namespace slh {
+
+// Validate a level's boxes (alignment, overlap, level-0 coverage, nesting in
+// lev-1) and build its block owner map.
+static slh_status validate_boxes(slh_ctx* c, int lev, const slh_box* boxes, int nboxes, void* const* bufs,
+                                 std::vector<int>* bmap_out, const char* who) {
   for (int i = 0; i < SLH_NBUF; ++i) {
     const bool need = (i != SLH_BUF_C) || c->prec == SLH_F32_KAHAN;
-    if (need && !bufs[i]) return fail(SLH_ERR_INVALID_ARG, "init_level: buffer %d is null", i);
+    if (need && !bufs[i]) return fail(SLH_ERR_INVALID_ARG, "%s: buffer %d is null", who, i);
   }
   const int ndom = c->n0 << lev;
   const int bf = c->bf;
   const int nbd = ndom / bf;
-  std::vector<int> bmap((size_t)nbd * nbd * nbd, -1);
+  std::vector<int>& bmap = *bmap_out;
+  bmap.assign((size_t)nbd * nbd * nbd, -1);
   for (int b = 0; b < nboxes; ++b) {
     const slh_box& B = boxes[b];
     for (int d = 0; d < 3; ++d) {
       if (B.lo[d] < 0 || B.hi[d] >= ndom || B.hi[d] < B.lo[d])
-        return fail(SLH_ERR_OUT_OF_RANGE, "init_level: box %d outside the level domain [0,%d)", b, ndom);
+        return fail(SLH_ERR_OUT_OF_RANGE, "%s: box %d outside the level domain [0,%d)", who, b, ndom);
       if (B.lo[d] % bf || (B.hi[d] + 1) % bf)
-        return fail(SLH_ERR_INVALID_ARG, "init_level: box %d not aligned to the blocking factor %d", b, bf);
+        return fail(SLH_ERR_INVALID_ARG, "%s: box %d not aligned to the blocking factor %d", who, b, bf);
     }
     for (int z = B.lo[2] / bf; z <= B.hi[2] / bf; ++z)
       for (int y = B.lo[1] / bf; y <= B.hi[1] / bf; ++y)
         for (int x = B.lo[0] / bf; x <= B.hi[0] / bf; ++x) {
           int& o = bmap[((size_t)z * nbd + y) * nbd + x];
-          if (o >= 0) return fail(SLH_ERR_INVALID_ARG, "init_level: boxes %d and %d overlap", o, b);
+          if (o >= 0) return fail(SLH_ERR_INVALID_ARG, "%s: boxes %d and %d overlap", who, o, b);
           o = b;
         }
   }
   if (lev == 0) {
     for (int v : bmap)
-      if (v < 0) return fail(SLH_ERR_INVALID_ARG, "init_level: level 0 must cover the periodic domain");
-  } else {
-    // nesting: the coarse projection grown by one block of bf/2 coarse cells
-    // must lie inside level lev-1 (periodic).  A block of bf/2 coarse cells
-    // lies inside a coarse box iff its enclosing block of bf cells does
-    // (coarse boxes are aligned to bf).
-    Level& C = c->lev[lev - 1];
-    const int r = bf / 2;
-    const int nbc = C.n_dom / r;
-    for (int b = 0; b < nboxes; ++b) {
-      int lo[3], hi[3];
-      for (int d = 0; d < 3; ++d) {
-        lo[d] = (boxes[b].lo[d] / 2) / r - 1;
-        hi[d] = ((boxes[b].hi[d] + 1) / 2) / r;
-      }
-      for (int z = lo[2]; z <= hi[2]; ++z)
-        for (int y = lo[1]; y <= hi[1]; ++y)
-          for (int x = lo[0]; x <= hi[0]; ++x) {
-            const int wx = ((x % nbc) + nbc) % nbc, wy = ((y % nbc) + nbc) % nbc, wz = ((z % nbc) + nbc) % nbc;
-            const int own = C.h_bmap[((size_t)(wz / 2) * C.nb_dom + wy / 2) * C.nb_dom + wx / 2];
-            if (own < 0)
-              return fail(SLH_ERR_OUT_OF_RANGE,
-                          "init_level: box %d of level %d is not nested in level %d with a gap of %d coarse cells", b,
-                          lev, lev - 1, r);
-          }
+      if (v < 0) return fail(SLH_ERR_INVALID_ARG, "%s: level 0 must cover the periodic domain", who);
+    return SLH_OK;
+  }
+  // nesting: the coarse projection grown by one block of bf/2 coarse cells
+  // must lie inside level lev-1 (periodic).  A block of bf/2 coarse cells
+  // lies inside a coarse box iff its enclosing block of bf cells does
+  // (coarse boxes are aligned to bf).
+  Level& C = c->lev[lev - 1];
+  const int r = bf / 2;
+  const int nbc = C.n_dom / r;
+  for (int b = 0; b < nboxes; ++b) {
+    int lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = (boxes[b].lo[d] / 2) / r - 1;
+      hi[d] = ((boxes[b].hi[d] + 1) / 2) / r;
     }
+    for (int z = lo[2]; z <= hi[2]; ++z)
+      for (int y = lo[1]; y <= hi[1]; ++y)
+        for (int x = lo[0]; x <= hi[0]; ++x) {
+          const int wx = ((x % nbc) + nbc) % nbc, wy = ((y % nbc) + nbc) % nbc, wz = ((z % nbc) + nbc) % nbc;
+          const int own = C.h_bmap[((size_t)(wz / 2) * C.nb_dom + wy / 2) * C.nb_dom + wx / 2];
+          if (own < 0)
+            return fail(SLH_ERR_OUT_OF_RANGE,
+                        "%s: box %d of level %d is not nested in level %d with a gap of %d coarse cells", who, b, lev,
+                        lev - 1, r);
+        }
   }
-  // drop this level and every finer one
-  cudaStreamSynchronize(c->stream);
-  drop_graphs(c);
-  for (int l = lev; l < MAX_LEVELS; ++l) free_level(c->lev[l]);
-  if (lev > 0) {
-    cudaFree(c->lev[lev - 1].d_covered);
-    c->lev[lev - 1].d_covered = nullptr;
-  }
-  c->nlevels = lev;
+  return SLH_OK;
+}
 
-  Level& L = c->lev[lev];
-  L.n_dom = ndom;
-  L.nb_dom = nbd;
+// Fill the metadata of level lev (boxes already validated) into L.
+static slh_status build_level(slh_ctx* c, int lev, Level& L, const slh_box* boxes, int nboxes, void* const* bufs,
+                              uint8_t* tags_dev, const std::vector<int>& bmap) {
+  L.n_dom = c->n0 << lev;
+  L.nb_dom = L.n_dom / c->bf;
   L.dx = c->dx0 / (double)(1 << lev);
   L.boxes.assign(boxes, boxes + nboxes);
   std::string why;
-  if (!make_layout(c->g, boxes, nboxes, &L.lay, &why)) return fail(SLH_ERR_INVALID_ARG, "init_level: %s", why.c_str());
+  if (!make_layout(c->g, boxes, nboxes, &L.lay, &why)) return fail(SLH_ERR_INVALID_ARG, "level %d: %s", lev, why.c_str());
   for (int i = 0; i < SLH_NBUF; ++i) L.buf[i] = bufs[i];
   if (c->prec != SLH_F32_KAHAN) L.buf[SLH_BUF_C] = nullptr;
   L.tags_dev = tags_dev;
@@ -341,10 +340,10 @@ slh_status slh_init_level(slh_ctx* c, int32_t lev, const slh_box* boxes, int32_t
         {b, {-g, 0, 0}, {g, n1, n2}},
         {b, {n0, 0, 0}, {g, n1, n2}},
     };
-    for (auto& s : s6) {
-      slabs.push_back(s);
+    for (auto& sl : s6) {
+      slabs.push_back(sl);
       soff.push_back(tot);
-      tot += (long long)s.e[0] * s.e[1] * s.e[2];
+      tot += (long long)sl.e[0] * sl.e[1] * sl.e[2];
     }
   }
   L.nslabs = (int)slabs.size();
@@ -381,15 +380,99 @@ slh_status slh_init_level(slh_ctx* c, int32_t lev, const slh_box* boxes, int32_t
   L.epart_cap = c->num_sms * 32;
   {
     cudaError_t e = cudaMalloc(&L.d_epart, sizeof(double) * 4 * L.epart_cap);
-    if (e != cudaSuccess) return fail(SLH_ERR_NOMEM, "init_level: energy partials: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(SLH_ERR_NOMEM, "level %d: energy partials: %s", lev, cudaGetErrorString(e));
   }
   L.defined = true;
+  return SLH_OK;
+}
+
+}  // namespace slh
+
+extern "C" {
+
+slh_status slh_init_level(slh_ctx* c, int32_t lev, const slh_box* boxes, int32_t nboxes, void* const* bufs,
+                          uint8_t* tags_dev) {
+  if (!c || !boxes || !bufs || nboxes < 1) return fail(SLH_ERR_INVALID_ARG, "init_level: null argument or no boxes");
+  if (lev < 0 || lev >= c->max_levels) return fail(SLH_ERR_OUT_OF_RANGE, "init_level: level %d outside [0,%d)", lev, c->max_levels);
+  if (lev > c->nlevels) return fail(SLH_ERR_STATE, "init_level: level %d defined before level %d", lev, c->nlevels);
+  std::vector<int> bmap;
+  slh_status st = validate_boxes(c, lev, boxes, nboxes, bufs, &bmap, "init_level");
+  if (st != SLH_OK) return st;
+  // drop this level and every finer one
+  cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
+  for (int l = lev; l < MAX_LEVELS; ++l) free_level(c->lev[l]);
+  if (lev > 0) {
+    cudaFree(c->lev[lev - 1].d_covered);
+    c->lev[lev - 1].d_covered = nullptr;
+  }
+  c->nlevels = lev;
+  c->stale_from = MAX_LEVELS;
+  Level& L = c->lev[lev];
+  if ((st = build_level(c, lev, L, boxes, nboxes, bufs, tags_dev, bmap)) != SLH_OK) return st;
   c->nlevels = lev + 1;
   if (lev > 0 && (st = build_covered(c, lev)) != SLH_OK) return st;
-
   const size_t bytes = (size_t)L.lay.total * elem_size(c);
   for (int i = 0; i < SLH_NBUF; ++i)
     if (L.buf[i]) SLH_CUDA(cudaMemsetAsync(L.buf[i], 0, bytes, c->stream));
+  return SLH_OK;
+}
+
+slh_status slh_regrid_level(slh_ctx* c, int32_t lev, const slh_box* boxes, int32_t nboxes, void* const* bufs,
+                            uint8_t* tags_dev, int32_t interp_type) {
+  if (!c) return fail(SLH_ERR_INVALID_ARG, "regrid_level: null ctx");
+  if (lev < 1 || lev >= c->max_levels) return fail(SLH_ERR_OUT_OF_RANGE, "regrid_level: level %d outside [1,%d)", lev, c->max_levels);
+  if (lev > c->nlevels) return fail(SLH_ERR_STATE, "regrid_level: level %d below it is not defined", lev - 1);
+  if (lev - 1 >= c->stale_from) return fail(SLH_ERR_STATE, "regrid_level: regrid level %d first", c->stale_from);
+  if (interp_type != 0 && interp_type != 2 && interp_type != 4)
+    return fail(SLH_ERR_INVALID_ARG, "regrid_level: interp_type must be 0, 2 or 4");
+  SLH_CUDA(cudaStreamSynchronize(c->stream));
+  drop_graphs(c);
+  if (nboxes <= 0) {
+    // the level disappears, and every finer one with it
+    for (int l = lev; l < MAX_LEVELS; ++l) free_level(c->lev[l]);
+    cudaFree(c->lev[lev - 1].d_covered);
+    c->lev[lev - 1].d_covered = nullptr;
+    c->nlevels = lev;
+    c->stale_from = MAX_LEVELS;
+    return SLH_OK;
+  }
+  if (!boxes || !bufs) return fail(SLH_ERR_INVALID_ARG, "regrid_level: null argument");
+  std::vector<int> bmap;
+  slh_status st = validate_boxes(c, lev, boxes, nboxes, bufs, &bmap, "regrid_level");
+  if (st != SLH_OK) return st;
+  Level fresh;
+  if ((st = build_level(c, lev, fresh, boxes, nboxes, bufs, tags_dev, bmap)) != SLH_OK) {
+    free_level(fresh);
+    return st;
+  }
+  const size_t bytes = (size_t)fresh.lay.total * elem_size(c);
+  for (int i = 0; i < SLH_NBUF; ++i)
+    if (fresh.buf[i]) SLH_CUDA(cudaMemsetAsync(fresh.buf[i], 0, bytes, c->stream));
+  Level* old = lev < c->nlevels ? &c->lev[lev] : nullptr;
+  c->regrid_itype = interp_type;
+  if ((st = launch_regrid_fill(c, lev, fresh, old)) != SLH_OK) {
+    free_level(fresh);
+    return st;
+  }
+  SLH_CUDA(cudaMemcpyAsync(fresh.buf[fresh.role_prev], fresh.buf[fresh.role_y], bytes, cudaMemcpyDeviceToDevice,
+                           c->stream));
+  // the new level starts at its coarser level's (synchronised) time
+  SLH_CUDA(cudaMemcpyAsync(c->d_time + 2 * lev, c->d_time + 2 * (lev - 1), 2 * sizeof(double),
+                           cudaMemcpyDeviceToDevice, c->stream));
+  st = slh_sync(c);
+  if (old) free_level(*old);
+  c->lev[lev] = fresh;
+  fresh = Level();   // ownership moved (avoid freeing twice)
+  if (st != SLH_OK) return st;
+  if (lev + 1 > c->nlevels) c->nlevels = lev + 1;
+  if ((st = build_covered(c, lev)) != SLH_OK) return st;
+  if (lev + 1 < c->nlevels) {
+    c->stale_from = lev + 1;
+    if ((st = build_covered(c, lev + 1)) != SLH_OK) return st;
+  } else {
+    c->stale_from = MAX_LEVELS;
+  }
   return SLH_OK;
 }
 
@@ -544,6 +627,7 @@ slh_status slh_rk_step(slh_ctx* c, int32_t lev, int32_t sub, double dt0, const s
   slh_status st = check_params(p);
   if (st != SLH_OK) return st;
   if (lev < 0 || lev >= c->nlevels) return fail(SLH_ERR_STATE, "rk_step: level %d not defined", lev);
+  if (lev >= c->stale_from) return fail(SLH_ERR_STATE, "rk_step: level %d must be regridded first", c->stale_from);
   if (sub != 0 && sub != 1) return fail(SLH_ERR_INVALID_ARG, "rk_step: sub must be 0 or 1");
   if (!(dt0 > 0.0)) return fail(SLH_ERR_INVALID_ARG, "rk_step: dt0 must be positive");
   return rk_step_impl(c, lev, sub, dt0, *p, flags);
@@ -599,6 +683,7 @@ slh_status slh_advance(slh_ctx* c, double dt0, const slh_eom_params* p, uint32_t
   slh_status st = check_params(p);
   if (st != SLH_OK) return st;
   if (c->nlevels < 1) return fail(SLH_ERR_STATE, "advance: no level defined");
+  if (c->stale_from < c->nlevels) return fail(SLH_ERR_STATE, "advance: level %d must be regridded first", c->stale_from);
   if (!(dt0 > 0.0)) return fail(SLH_ERR_INVALID_ARG, "advance: dt0 must be positive");
   if (!(flags & SLH_USE_GRAPH) || c->prof) return advance_rec(c, 0, 0, dt0, *p, flags);
 

@@ -301,3 +301,146 @@ slh_status launch_time_begin(slh_ctx* c, int lev, int sub, double dt_l) {
 }
 
 }  // namespace slh
+
+namespace slh {
+
+// ---------------------------------------------------------------------------
+// regrid fill (Sec. 2.3): each valid cell of a level's new boxes takes the
+// old level's value where an old box covers it, else the prolongation of the
+// coarser level's current state (all four fields); the Kahan compensation is
+// carried over where covered and zero elsewhere.
+
+template <typename T>
+struct RegridFillArgs {
+  const BoxDev* nboxes;
+  int nnb;
+  long long nvalid;
+  T* ny;
+  T* nc;                 // new Kahan buffer or null
+  const BoxDev* oboxes;  // old level (null: none)
+  const T* oy;
+  const T* oc;
+  const int* obmap;
+  int nbd;               // blocks per axis of the level domain (old and new)
+  const BoxDev* cboxes;  // coarser level
+  const T* cy;
+  const int* cbmap;
+  int cnbd, cndom;
+  int bshift;
+  int gl;
+  int itype;
+  int* err;
+};
+
+template <typename T>
+__global__ void regrid_fill_kernel(const RegridFillArgs<T> A) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < A.nvalid; t += stride) {
+    int lo = 0, hi = A.nnb - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (A.nboxes[mid].voff <= t) lo = mid; else hi = mid - 1;
+    }
+    const BoxDev B = A.nboxes[lo];
+    const long long loc = t - B.voff;
+    const int rx = (int)(loc % B.n[0]);
+    const int ry = (int)((loc / B.n[0]) % B.n[1]);
+    const int rz = (int)(loc / ((long long)B.n[0] * B.n[1]));
+    const int gx = B.lo[0] + rx, gy = B.lo[1] + ry, gz = B.lo[2] + rz;
+    const long long dst = cell_index(B, A.gl, rx, ry, rz);
+    if (A.oboxes != nullptr) {
+      const int own = A.obmap[((long long)(gz >> A.bshift) * A.nbd + (gy >> A.bshift)) * A.nbd + (gx >> A.bshift)];
+      if (own >= 0) {
+        const BoxDev O = A.oboxes[own];
+        const long long src = cell_index(O, A.gl, gx - O.lo[0], gy - O.lo[1], gz - O.lo[2]);
+#pragma unroll
+        for (int c = 0; c < NCOMP; ++c) {
+          A.ny[dst + c * B.cs] = A.oy[src + c * O.cs];
+          if (A.nc) A.nc[dst + c * B.cs] = A.oc ? A.oc[src + c * O.cs] : (T)0;
+        }
+        continue;
+      }
+    }
+    const int Px = gx >> 1, Py = gy >> 1, Pz = gz >> 1;
+    const int cx = gx & 1, cy = gy & 1, cz = gz & 1;
+    const int rad = A.itype == 4 ? 2 : (A.itype == 2 ? 1 : 0);
+    double acc[NCOMP] = {0.0, 0.0, 0.0, 0.0};
+    bool bad = false;
+    for (int oz = -rad; oz <= rad; ++oz) {
+      const double wzv = pw(A.itype, cz, oz);
+      const int qz = wrapi(Pz + oz, A.cndom);
+      for (int oy = -rad; oy <= rad; ++oy) {
+        const double wyv = pw(A.itype, cy, oy);
+        const int qy = wrapi(Py + oy, A.cndom);
+        for (int ox = -rad; ox <= rad; ++ox) {
+          const double wxv = pw(A.itype, cx, ox);
+          const int qx = wrapi(Px + ox, A.cndom);
+          const int cown = A.cbmap[((long long)(qz >> A.bshift) * A.cnbd + (qy >> A.bshift)) * A.cnbd + (qx >> A.bshift)];
+          if (cown < 0) {
+            bad = true;
+            continue;
+          }
+          const BoxDev C = A.cboxes[cown];
+          const long long ci = cell_index(C, A.gl, qx - C.lo[0], qy - C.lo[1], qz - C.lo[2]);
+          const double wgt = wzv * wyv * wxv;
+#pragma unroll
+          for (int c = 0; c < NCOMP; ++c) acc[c] += wgt * (double)A.cy[ci + c * C.cs];
+        }
+      }
+    }
+    if (bad) atomicCAS(A.err, 0, DERR_NESTING);
+#pragma unroll
+    for (int c = 0; c < NCOMP; ++c) {
+      A.ny[dst + c * B.cs] = (T)acc[c];
+      if (A.nc) A.nc[dst + c * B.cs] = (T)0;
+    }
+  }
+}
+
+template <typename T>
+static slh_status regrid_fill_t(slh_ctx* c, int lev, Level& N, Level* O) {
+  Level& C = c->lev[lev - 1];
+  RegridFillArgs<T> A;
+  A.nboxes = N.d_boxes;
+  A.nnb = (int)N.boxes.size();
+  A.nvalid = N.lay.nvalid;
+  A.ny = static_cast<T*>(N.buf[N.role_y]);
+  A.nc = static_cast<T*>(N.buf[SLH_BUF_C]);
+  if (O != nullptr && O->defined) {
+    A.oboxes = O->d_boxes;
+    A.oy = static_cast<const T*>(O->buf[O->role_y]);
+    A.oc = static_cast<const T*>(O->buf[SLH_BUF_C]);
+    A.obmap = O->d_bmap;
+  } else {
+    A.oboxes = nullptr;
+    A.oy = nullptr;
+    A.oc = nullptr;
+    A.obmap = nullptr;
+  }
+  A.nbd = N.nb_dom;
+  A.cboxes = C.d_boxes;
+  A.cy = static_cast<const T*>(C.buf[C.role_y]);
+  A.cbmap = C.d_bmap;
+  A.cnbd = C.nb_dom;
+  A.cndom = C.n_dom;
+  int sh = 0;
+  while ((1 << sh) < c->bf) ++sh;
+  A.bshift = sh;
+  A.gl = c->g;
+  A.itype = c->regrid_itype;
+  A.err = c->d_err;
+  const int threads = 256;
+  long long blocks = (A.nvalid + threads - 1) / threads;
+  const long long cap = (long long)c->num_sms * 16;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  regrid_fill_kernel<T><<<(int)blocks, threads, 0, c->stream>>>(A);
+  SLH_CUDA(cudaGetLastError());
+  return SLH_OK;
+}
+
+slh_status launch_regrid_fill(slh_ctx* c, int lev, Level& fresh, Level* old) {
+  return c->prec == SLH_F64 ? regrid_fill_t<double>(c, lev, fresh, old) : regrid_fill_t<float>(c, lev, fresh, old);
+}
+
+}  // namespace slh

@@ -134,6 +134,8 @@ struct slh_ctx {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   unsigned long long graph_key = 0;
   int graph_parity = 0;
+  int stale_from = slh::MAX_LEVELS;   // levels >= this must be regridded before stepping
+  int regrid_itype = 4;
 };
 
 namespace slh {
@@ -179,6 +181,7 @@ slh_status launch_energy_final(slh_ctx* c, const double* epart, int n, double* o
 slh_status launch_tag_blocks(slh_ctx* c, Level& L, const uint8_t* tags, int nbuf, int r,
                              uint8_t* mask, int nb);
 slh_status launch_time_begin(slh_ctx* c, int lev, int sub, double dt_l);
+slh_status launch_regrid_fill(slh_ctx* c, int lev, Level& fresh, Level* old);
 
 // profiling helpers
 void prof_begin(slh_ctx* c, int kind, double bytes);

@@ -391,32 +391,34 @@ __global__ void __launch_bounds__(TX* TY, 1) stage_kernel(const StageArgs<T> A) 
       // -delta(a,b)), so a plaquette's winding is the signed sum of the edges
       // leaving its corners along +x, +y, +z.  Per plane: (1) every edge of
       // the tile grown by one cell is evaluated once, spread evenly over the
-      // CTA; (2) the 3-bit "winding != 0" mask of each cell of the tile and of
-      // its low halo follows from those edges; (3) a cell's tag is the OR over
-      // the 12 plaquettes it is a corner of (owners c, c-u, c-v, c-u-v), read
-      // from the masks of planes z and z-1.
+      // CTA (in-plane edges are reused for the next plane); (2) the 3-bit
+      // "winding != 0" mask of each cell of the tile and of its low halo
+      // follows from those edges; (3) a cell's tag is the OR over the 12
+      // plaquettes it is a corner of (owners c, c-u, c-v, c-u-v), read from
+      // the masks of planes z and z-1.
       constexpr int EXW = TX + 2, EXH = TY + 2, NE = EXW * EXH;
       constexpr int MW = TX + 1, MH = TY + 1, NM = MW * MH;
-      __shared__ signed char ed[5][EXH][EXW];     // e_x, e_y, e_z of plane z; e_x, e_y of plane z+1
+      // in-plane edges (e_x, e_y) of planes z and z+1 by plane parity, and
+      // the vertical edges e_z of plane z; an item's planes run consecutively
+      // from its premask plane z0-1, so plane z's in-plane edges are the ones
+      // computed as "plane z+1" one iteration earlier
+      __shared__ signed char exy[2][2][EXH][EXW];
+      __shared__ signed char ezv[EXH][EXW];
       __shared__ unsigned char mk[2][MH][MW];
       const bool doit = compute || premask;      // uniform over the CTA
-      const int pz = z & 1;
+      const int pz = z & 1, pn = pz ^ 1;
       auto SA = [&](int c, int ax, int ay, int dz) -> T { return plb[dz + G][c * PLANE + ay * SXL + ax]; };
       if (doit) {
         for (int j = tid; j < NE; j += TXY) {
           const int ex = j % EXW - 1, ey = j / EXW - 1;
           const T r0 = SA(0, ex, ey, 0), i0 = SA(1, ex, ey, 0);
-          const T rx = SA(0, ex + 1, ey, 0), ix = SA(1, ex + 1, ey, 0);
           const T rz = SA(0, ex, ey, 1), iz = SA(1, ex, ey, 1);
-          const T rzx = SA(0, ex + 1, ey, 1), izx = SA(1, ex + 1, ey, 1);
-          ed[0][ey + 1][ex + 1] = (signed char)edge_delta(r0, i0, rx, ix);
-          ed[2][ey + 1][ex + 1] = (signed char)edge_delta(r0, i0, rz, iz);
-          ed[3][ey + 1][ex + 1] = (signed char)edge_delta(rz, iz, rzx, izx);
-          if (ey < TY) {
-            const T ry = SA(0, ex, ey + 1, 0), iy = SA(1, ex, ey + 1, 0);
-            const T rzy = SA(0, ex, ey + 1, 1), izy = SA(1, ex, ey + 1, 1);
-            ed[1][ey + 1][ex + 1] = (signed char)edge_delta(r0, i0, ry, iy);
-            ed[4][ey + 1][ex + 1] = (signed char)edge_delta(rz, iz, rzy, izy);
+          ezv[ey + 1][ex + 1] = (signed char)edge_delta(r0, i0, rz, iz);
+          exy[pn][0][ey + 1][ex + 1] = (signed char)edge_delta(rz, iz, SA(0, ex + 1, ey, 1), SA(1, ex + 1, ey, 1));
+          if (ey < TY) exy[pn][1][ey + 1][ex + 1] = (signed char)edge_delta(rz, iz, SA(0, ex, ey + 1, 1), SA(1, ex, ey + 1, 1));
+          if (premask) {
+            exy[pz][0][ey + 1][ex + 1] = (signed char)edge_delta(r0, i0, SA(0, ex + 1, ey, 0), SA(1, ex + 1, ey, 0));
+            if (ey < TY) exy[pz][1][ey + 1][ex + 1] = (signed char)edge_delta(r0, i0, SA(0, ex, ey + 1, 0), SA(1, ex, ey + 1, 0));
           }
         }
       }
@@ -424,10 +426,10 @@ __global__ void __launch_bounds__(TX* TY, 1) stage_kernel(const StageArgs<T> A) 
       if (doit) {
         for (int j = tid; j < NM; j += TXY) {
           const int mx = j % MW, my = j / MW;   // cell offset (mx-1, my-1) from (x0, y0)
-          const int ex_c = ed[0][my][mx], ey_c = ed[1][my][mx], ez_c = ed[2][my][mx];
-          const int ey_cx = ed[1][my][mx + 1], ez_cx = ed[2][my][mx + 1];
-          const int ex_cy = ed[0][my + 1][mx], ez_cy = ed[2][my + 1][mx];
-          const int ex_cz = ed[3][my][mx], ey_cz = ed[4][my][mx];
+          const int ex_c = exy[pz][0][my][mx], ey_c = exy[pz][1][my][mx], ez_c = ezv[my][mx];
+          const int ey_cx = exy[pz][1][my][mx + 1], ez_cx = ezv[my][mx + 1];
+          const int ex_cy = exy[pz][0][my + 1][mx], ez_cy = ezv[my + 1][mx];
+          const int ex_cz = exy[pn][0][my][mx], ey_cz = exy[pn][1][my][mx];
           const int wxy = ex_c + ey_cx - ex_cy - ey_c;   // normal z: c, c+x, c+x+y, c+y
           const int wyz = ey_c + ez_cy - ey_cz - ez_c;   // normal x: c, c+y, c+y+z, c+z
           const int wzx = ez_c + ex_cz - ez_cx - ex_c;   // normal y: c, c+z, c+z+x, c+x

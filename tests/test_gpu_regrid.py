@@ -1,0 +1,123 @@
+"""Dynamic AMR on the GPU vs the oracle (Sec. 2.2-2.3): device tags grown and
+coarsened to blocks, host clustering in block units, live-level regrid
+(copy where the old level covers, prolongation elsewhere), and subcycled
+steps across regrids.  Box lists bit-exact; FP64 fields within 1e-12
+relative L2 of the oracle."""
+import numpy as np
+import pytest
+
+import paper_2404_02950_gb300 as slh
+from oracle import amr as oamr
+from oracle import regrid as oregrid
+from paper_2404_02950_gb300 import inputs
+from tests.helpers import oparams, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+N0, DX0, DT0, ETA0, G, BF = 32, 0.5, 0.125, 1.0, 3, 8
+NBUF, MAX_BOX, MAXLEV = 2, 32, 3
+
+
+def _dense_tags(oh, lev):
+    L = oh.levels[lev]
+    t = np.zeros((L.n, L.n, L.n), dtype=np.uint8)
+    for (lo, hi), tb in zip(L.boxes, oh.tags(lev)):
+        t[lo[2]:hi[2] + 1, lo[1]:hi[1] + 1, lo[0]:hi[0] + 1] = tb
+    return t
+
+
+def _oracle_regrid(oh):
+    out = []
+    for l in range(MAXLEV - 1):
+        if l >= len(oh.levels):
+            break
+        parent = None if l == 0 else oh.levels[l].boxes
+        boxes = oregrid.regrid_boxes(_dense_tags(oh, l), BF, NBUF, MAX_BOX, parent_boxes=parent)
+        oamr.regrid_level(oh, l + 1, boxes)
+        out.append(boxes)
+        if not boxes:
+            break
+    return out
+
+
+def _dense(level):
+    parts = []
+    for b in range(len(level.boxes)):
+        v = level.data[b][level.valid(b)]
+        for c in range(4):
+            parts.append(v[c].ravel())
+    return np.concatenate(parts)
+
+
+def _compare(h, oh, tol):
+    assert sorted(h.levels) == list(range(len(oh.levels)))
+    for l, L in enumerate(oh.levels):
+        assert [tuple(map(tuple, b)) for b in h.levels[l]["boxes"]] == L.boxes, l
+        got = slh.boxes_from_dense(h.get_state(l), L.boxes)
+        for b in range(len(L.boxes)):
+            exp = L.data[b][L.valid(b)]
+            for c in range(4):
+                e = rel_l2(got[b][c], exp[c])
+                assert e <= tol, (l, b, c, e)
+
+
+def test_regrid_then_subcycle_matches_oracle():
+    p = slh.EOMParams(order=4, interp_type=4)
+    y0 = inputs.string_loop(N0, 4.0, 2.0, DX0)
+    oh = oamr.make_hierarchy(N0, DX0, DT0, G, BF, [[((0, 0, 0), (N0 - 1, N0 - 1, N0 - 1))]], oparams(p),
+                             interp_type=4, eta0=ETA0)
+    oh.levels[0].set_dense(y0)
+    h = slh.Hierarchy(N0, DX0, nghost=G, bf=BF, prec="f64", max_levels=MAXLEV)
+    h.init_level(0, [((0, 0, 0), (N0 - 1, N0 - 1, N0 - 1))])
+    h.set_state(0, _dense(oh.levels[0]))
+    h.set_eta(ETA0)
+    # first regrid creates levels 1 and 2 by prolongation
+    ob = _oracle_regrid(oh)
+    gb = h.regrid(MAXLEV, NBUF, MAX_BOX)
+    assert gb == ob and len(ob) == 2 and all(len(b) > 0 for b in ob)
+    _compare(h, oh, 1e-13)
+    for _ in range(2):
+        oh.step()
+        h.advance(DT0, p)
+    _compare(h, oh, 1e-12)
+    # second regrid: copies from the old levels where they overlap
+    ob = _oracle_regrid(oh)
+    gb = h.regrid(MAXLEV, NBUF, MAX_BOX)
+    assert gb == ob
+    _compare(h, oh, 1e-12)
+    oh.step()
+    h.advance(DT0, p)
+    _compare(h, oh, 1e-12)
+
+
+def test_tag_blocks_equal_grown_coarsened_oracle_tags():
+    p = slh.EOMParams(order=4)
+    y0 = inputs.string_loop(N0, 4.0, 2.0, DX0)
+    h = slh.Hierarchy(N0, DX0, nghost=G, bf=BF, prec="f64", max_levels=1)
+    boxes = [((0, 0, 0), (15, 31, 31)), ((16, 0, 0), (31, 31, 31))]
+    h.init_level(0, boxes)
+    h.set_state(0, slh.dense_from_boxes(y0, boxes))
+    h.set_eta(ETA0)
+    from oracle import winding
+    tags = winding.cell_tags_periodic(y0[0], y0[1])
+    for nbuf in (0, 1, 3):
+        got = h.tag_blocks(0, nbuf)
+        exp = oregrid.coarsen_any(oregrid.dilate_periodic(tags != 0, nbuf), BF // 2)
+        assert np.array_equal(got.astype(bool), exp), nbuf
+
+
+def test_regrid_errors_and_removal():
+    h = slh.Hierarchy(N0, DX0, nghost=G, bf=BF, prec="f64", max_levels=3)
+    h.init_level(0, [((0, 0, 0), (N0 - 1, N0 - 1, N0 - 1))])
+    with pytest.raises(slh.SlhError) as e:
+        h.regrid_level(2, [((48, 48, 48), (63, 63, 63))])     # level 1 missing
+    assert e.value.code == -7
+    h.regrid_level(1, [((16, 16, 16), (47, 47, 47))])
+    h.regrid_level(2, [((48, 48, 48), (79, 79, 79))])
+    h.regrid_level(1, [((16, 16, 16), (47, 47, 31))])        # level 2 now stale
+    with pytest.raises(slh.SlhError) as e:
+        h.advance(DT0, slh.EOMParams(order=4))
+    assert e.value.code == -7
+    h.regrid_level(2, [])                                     # remove it
+    h.advance(DT0, slh.EOMParams(order=4))
+    assert sorted(h.levels) == [0, 1]
