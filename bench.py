@@ -215,6 +215,45 @@ def _time_form(slh, torch, prec, y0_dense, n, K, W, dist, flags):
     return h, out
 
 
+AMR_N, AMR_LEVELS, AMR_NBUF, AMR_BF, AMR_MAXBOX, AMR_RELAX, AMR_EVERY = 256, 3, 4, 16, 128, 100, 4
+AMR_WORKLOAD = ("dynamic AMR: 256^3 base + 2 ratio-2 levels, c0-style Gaussian init (k_max=pi/(4dx)) relaxed "
+                "100 coarse steps on the base level, then regridded every 4 coarse steps from string tags "
+                "(buffer 4, blocking factor 16, max box 128), 4th-order Laplacian, quartic prolongation, "
+                "subcycled RK4; regrid time included")
+
+
+def _amr_form(slh, torch, prec, y0_dense, K):
+    """Dynamic-AMR timing: coarse steps with global regrids every AMR_EVERY
+    steps.  Returns (cell-updates/s, details)."""
+    n = AMR_N
+    h = slh.Hierarchy(n, DX, nghost=3, bf=AMR_BF, prec=prec, max_levels=AMR_LEVELS)
+    h.init_level(0, [((0, 0, 0), (n - 1, n - 1, n - 1))])
+    h.set_state(0, y0_dense.astype(h.np_dtype))
+    h.set_eta(ETA0)
+    p = slh.EOMParams(order=4, interp_type=4)
+    for _ in range(AMR_RELAX):
+        h.advance(DT, p)
+    h.sync()
+    h.regrid(AMR_LEVELS, AMR_NBUF, AMR_MAXBOX)
+    for lev in sorted(h.levels):
+        h.autotune(lev, p, reps=2)
+    h.sync()
+    updates = 0
+    t0 = time.perf_counter()
+    for k in range(K):
+        if k and k % AMR_EVERY == 0:
+            h.regrid(AMR_LEVELS, AMR_NBUF, AMR_MAXBOX)
+        updates += sum(info["nvalid"] * 2 ** lev for lev, info in h.levels.items())
+        h.advance(DT, p)
+    h.sync()
+    el = time.perf_counter() - t0
+    det = {"levels": {str(l): {"boxes": len(info["boxes"]), "cells": info["nvalid"]} for l, info in h.levels.items()},
+           "coarse_steps": K, "seconds": el, "cell_updates": updates,
+           "eta_end": h.get_eta(0)}
+    h.close()
+    return updates / el, det
+
+
 def run_ours(args, rank, world, local_rank, dist):
     import torch
     import paper_2404_02950_gb300 as slh
@@ -268,6 +307,19 @@ def run_ours(args, rank, world, local_rank, dist):
     del h64
     torch.cuda.empty_cache()
 
+    # dynamic AMR (config 3 workload), FP32 batched and FP64 plain
+    amr = None
+    if not args.no_amr:
+        ya = inputs.gaussian_field(AMR_N, AMR_N / 8.0, seed=rank)
+        yad = slh.dense_from_boxes(ya, [((0, 0, 0), (AMR_N - 1,) * 3)])
+        del ya
+        v32, d32 = _amr_form(slh, torch, "f32", yad, 12)
+        torch.cuda.empty_cache()
+        v64, d64 = _amr_form(slh, torch, "f64", yad, 4)
+        torch.cuda.empty_cache()
+        amr = {"workload": AMR_WORKLOAD, "unit": "cell-updates/s",
+               "f32": {"value": world * v32, **d32}, "f64": {"value": world * v64, **d64}}
+
     ms = r32["ms"]
     e2e_ms = e2e_s * 1e3
     if dist is not None:
@@ -305,6 +357,7 @@ def run_ours(args, rank, world, local_rank, dist):
         "energy_f32": r32["energy"], "energy_f64": r64["energy"],
         "e2e": {"value": world * cells * K / (e2e_ms / 1e3), "unit": "cell-updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4 * 8},
+        "amr": amr,
         "gpu_launches": launches,
         "clocks": clocks,
     }
@@ -320,6 +373,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cells", type=int, default=N_CELLS, help="lattice cells per axis (default 512)")
+    ap.add_argument("--no-amr", action="store_true", help="skip the dynamic-AMR line")
     ap.add_argument("--profile-only", action="store_true",
                     help="time only the FP32 form and print nothing (for ncu captures of a small case)")
     args = ap.parse_args()

@@ -306,6 +306,13 @@ slh_status slh_autotune(slh_ctx* ctx, int32_t lev, const slh_eom_params* p, int3
 slh_status slh_energy_noalloc(const void* fields_dev, int32_t n, int32_t prec, double dx, double eta,
                               const slh_eom_params* p, double* out_dev, void* stream);
 
+/* Self-test of the bounded-wait path: launches one CTA that waits, for at
+ * most `polls` polls (1..2^22), on an mbarrier phase that never completes
+ * and latches the timeout exactly as the stage kernel's waits do.  The next
+ * slh_sync returns SLH_ERR_TIMEOUT and clears it; the context stays usable.
+ * Errors: INVALID_ARG, CUDA. */
+slh_status slh_selftest_wait_timeout(slh_ctx* ctx, int64_t polls);
+
 /* Wait for the stream and return any latched device error (then clear it). */
 slh_status slh_sync(slh_ctx* ctx);
 

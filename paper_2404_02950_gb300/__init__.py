@@ -44,7 +44,7 @@ ABI_SYMBOLS = (
     "slh_set_state", "slh_get_state", "slh_set_eta", "slh_get_eta", "slh_rk_step",
     "slh_advance", "slh_fill_ghosts", "slh_tag", "slh_tag_blocks", "slh_regrid_boxes",
     "slh_reduce_energy", "slh_sync", "slh_profile", "slh_profile_read", "slh_set_tile", "slh_autotune",
-    "slh_energy_noalloc", "slh_regrid_level",
+    "slh_energy_noalloc", "slh_regrid_level", "slh_selftest_wait_timeout",
 )
 
 
@@ -118,6 +118,7 @@ def lib():
         "slh_autotune": (i32, [vp, i32, P(slh_eom_params), i32, P(i32), P(dbl)]),
         "slh_energy_noalloc": (i32, [vp, i32, i32, dbl, dbl, P(slh_eom_params), vp, vp]),
         "slh_regrid_level": (i32, [vp, i32, P(slh_box), i32, P(vp), vp, i32]),
+        "slh_selftest_wait_timeout": (i32, [vp, i64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

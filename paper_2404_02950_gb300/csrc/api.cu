@@ -752,6 +752,12 @@ slh_status slh_fill_ghosts(slh_ctx* c, int32_t lev, double alpha, int32_t itype,
   return fill_impl(c, lev, alpha, itype, mode);
 }
 
+slh_status slh_selftest_wait_timeout(slh_ctx* c, int64_t polls) {
+  if (!c) return fail(SLH_ERR_INVALID_ARG, "selftest: null ctx");
+  if (polls < 1 || polls > (1ll << 22)) return fail(SLH_ERR_INVALID_ARG, "selftest: polls must be in [1, 2^22]");
+  return launch_expired_wait(c, polls);
+}
+
 slh_status slh_sync(slh_ctx* c) {
   if (!c) return fail(SLH_ERR_INVALID_ARG, "sync: null ctx");
   SLH_CUDA(cudaStreamSynchronize(c->stream));

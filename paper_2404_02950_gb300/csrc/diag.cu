@@ -96,4 +96,40 @@ slh_status launch_tag_blocks(slh_ctx* c, Level& L, const uint8_t* tags, int nbuf
   return SLH_OK;
 }
 
+// A wait nothing completes: one CTA initialises an mbarrier expecting two
+// arrivals, arrives once and polls the phase with a bounded loop like the
+// stage kernel's waits (here limited to `polls`); on expiry it latches
+// DERR_TIMEOUT exactly as the stage kernel does, so the host sees
+// SLH_ERR_TIMEOUT at its next synchronising call and the context stays usable.
+__global__ void expired_wait_kernel(int* err, long long polls) {
+  __shared__ unsigned long long bar;
+  const unsigned addr = static_cast<unsigned>(__cvta_generic_to_shared(&bar));
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(addr), "r"(2) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(addr) : "memory");
+    bool done = false;
+    for (long long i = 0; i < polls && !done; ++i) {
+      unsigned ok;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(ok)
+          : "r"(addr), "r"(0u)
+          : "memory");
+      done = ok != 0;
+    }
+    if (!done) atomicCAS(err, 0, DERR_TIMEOUT);
+  }
+  __syncthreads();
+}
+
+slh_status launch_expired_wait(slh_ctx* c, long long polls) {
+  expired_wait_kernel<<<1, 32, 0, c->stream>>>(c->d_err, polls);
+  SLH_CUDA(cudaGetLastError());
+  return SLH_OK;
+}
+
 }  // namespace slh

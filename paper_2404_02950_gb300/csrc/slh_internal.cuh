@@ -174,6 +174,7 @@ slh_status launch_stage(slh_ctx* c, Level& L, const slh_eom_params& p, const Sta
                         int* ctas_used);
 const TileVariant* tile_variants(int prec, int* n);
 void free_tmaps(Level& L);
+slh_status launch_expired_wait(slh_ctx* c, long long polls);
 
 slh_status launch_ghosts(slh_ctx* c, int lev, int role, double alpha, int itype);
 slh_status launch_restrict(slh_ctx* c, int fine_lev);

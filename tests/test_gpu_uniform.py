@@ -246,3 +246,23 @@ def test_autotune_keeps_state_and_picks_a_variant():
     assert 0 <= chosen < len(ms) and len(ms) == 4 and all(m > 0 for m in ms)
     assert ms[chosen] == min(ms)
     assert np.array_equal(before, h.get_state(0))
+
+
+def test_bounded_wait_expiry_is_reported_and_context_survives():
+    """A device wait that nothing completes gives up after its poll limit,
+    the host reads SLH_ERR_TIMEOUT, and the context keeps working."""
+    n, dx = 32, 0.25
+    p = slh.EOMParams(order=4)
+    y0 = inputs.gaussian_field(n, 4.0, seed=12)
+    h, boxes = uniform_hierarchy(n, dx, prec="f32")
+    upload(h, 0, y0, boxes)
+    h.set_eta(0.5)
+    slh._check(slh.lib().slh_selftest_wait_timeout(h.h, 1000))
+    with pytest.raises(slh.SlhError) as e:
+        h.sync()
+    assert e.value.code == -4
+    h.sync()                                   # cleared
+    h.rk_step(0, 0.05, p)
+    ref = ork4.rk4_step_periodic(y0, 0.5, 0.05, dx, oparams(p))
+    g = download_domain(h, 0, boxes, n)
+    assert max(rel_l2(g[c], ref[c]) for c in range(4)) <= 1e-5
