@@ -238,18 +238,27 @@ def _amr_form(slh, torch, prec, y0_dense, K):
     for lev in sorted(h.levels):
         h.autotune(lev, p, reps=2)
     h.sync()
+    h.profile(True, True)
     updates = 0
+    regrid_s = 0.0
     t0 = time.perf_counter()
     for k in range(K):
         if k and k % AMR_EVERY == 0:
+            h.sync()
+            tr = time.perf_counter()
             h.regrid(AMR_LEVELS, AMR_NBUF, AMR_MAXBOX)
+            regrid_s += time.perf_counter() - tr
         updates += sum(info["nvalid"] * 2 ** lev for lev, info in h.levels.items())
         h.advance(DT, p)
     h.sync()
     el = time.perf_counter() - t0
+    kinds = {"stage": slh.SLH_PROF_STAGE, "ghost": slh.SLH_PROF_GHOST, "restrict": slh.SLH_PROF_RESTRICT,
+             "diag": slh.SLH_PROF_DIAG, "time": slh.SLH_PROF_TIME}
+    prof = {k: round(h.profile_read(v)[0], 3) for k, v in kinds.items()}
+    h.profile(False, True)
     det = {"levels": {str(l): {"boxes": len(info["boxes"]), "cells": info["nvalid"]} for l, info in h.levels.items()},
-           "coarse_steps": K, "seconds": el, "cell_updates": updates,
-           "eta_end": h.get_eta(0)}
+           "coarse_steps": K, "seconds": el, "regrid_seconds": regrid_s, "device_ms": prof,
+           "cell_updates": updates, "eta_end": h.get_eta(0)}
     h.close()
     return updates / el, det
 

@@ -107,12 +107,13 @@ __device__ __forceinline__ int edge_delta(double ar, double ai, double br, doubl
   return (int)(ua && X > 0.0) - (int)(ub && X < 0.0);
 }
 
-// FP32 inputs: the sign of X from the rounded products whenever their
-// difference exceeds the worst-case rounding error (each product is within
-// 2^-24 of its value, the difference within 2^-24 more); otherwise the
-// products, exact in FP64, are formed in FP64.  Same sign as the FP64 form.
-// The near-tie fallback is kept out of line so that FP64 work is never
-// if-converted into the common, branch-free path.
+// FP32 inputs: q = fl(Im a * Re b), s = fma(Re a, Im b, -q) = fl(X + dq)
+// with |dq| <= 2^-24 |q| the rounding error of q.  Round-to-nearest keeps
+// the sign of a nonzero value, so whenever |s| > 2^-23 |q| (> 2 |dq|) the
+// sign of s is the sign of X.  Otherwise (near ties, or q tiny enough for
+// underflow to spoil the bound) the products, exact in FP64, are formed in
+// FP64.  The near-tie fallback is kept out of line so that FP64 work is
+// never if-converted into the common, branch-free path.
 __device__ __noinline__ float exact_cross_sign(float ar, float ai, float br, float bi) {
   const double X = __dsub_rn(__dmul_rn((double)ar, (double)bi), __dmul_rn((double)ai, (double)br));
   return X > 0.0 ? 1.0f : (X < 0.0 ? -1.0f : 0.0f);
@@ -120,10 +121,11 @@ __device__ __noinline__ float exact_cross_sign(float ar, float ai, float br, flo
 
 __device__ __forceinline__ int edge_delta(float ar, float ai, float br, float bi) {
   const bool ua = ai >= 0.0f, ub = bi >= 0.0f;
-  const float p = __fmul_rn(ar, bi), q = __fmul_rn(ai, br);
-  float s = __fsub_rn(p, q);
-  const float bound = __fmul_rn(__fadd_rn(fabsf(p), fabsf(q)), 4.76837158203125e-07f);  // 2^-21
-  if (ua != ub && !(fabsf(s) > bound && bound > 1e-30f)) s = exact_cross_sign(ar, ai, br, bi);
+  const float q = __fmul_rn(ai, br);
+  float s = __fmaf_rn(ar, bi, -q);
+  const float aq = fabsf(q);
+  if (ua != ub && !(fabsf(s) > aq * 1.1920928955078125e-07f && (aq > 1e-30f || fabsf(s) > 1e-30f)))
+    s = exact_cross_sign(ar, ai, br, bi);
   return (int)(ua && !ub && s > 0.0f) - (int)(!ua && ub && s < 0.0f);
 }
 
@@ -264,6 +266,26 @@ __global__ void __launch_bounds__(TX* TY, 1) stage_kernel(const StageArgs<T> A) 
   bool aborted = false;
   const int thread_off = (ty + G) * SXL + 4 + tx;
   constexpr int PSI_T = GE::PSI_STRIDE / (int)sizeof(T);
+
+  // fixed per-thread assignment of the diagnostics work: extended-tile cells
+  // (edges) and mask cells, with their shared-memory offsets
+  constexpr int NEK = ((TX + 2) * (TY + 2) + TXY - 1) / TXY;
+  constexpr int NMK = ((TX + 1) * (TY + 1) + TXY - 1) / TXY;
+  int e_x[NEK], e_y[NEK], e_off[NEK], m_x[NMK], m_y[NMK];
+#pragma unroll
+  for (int k = 0; k < NEK; ++k) {
+    const int j = k * TXY + tid;
+    e_x[k] = j % (TX + 2) - 1;
+    e_y[k] = j / (TX + 2) - 1;
+    e_off[k] = e_y[k] * SXL + e_x[k];
+  }
+#pragma unroll
+  for (int k = 0; k < NMK; ++k) {
+    const int j = k * TXY + tid;
+    m_x[k] = j % (TX + 1);
+    m_y[k] = j / (TX + 1);
+  }
+  (void)e_x; (void)e_y; (void)e_off; (void)m_x; (void)m_y;
 
   int t = 0, slot = 0, pslot = 0;
   unsigned parity = 0;
@@ -407,25 +429,29 @@ __global__ void __launch_bounds__(TX* TY, 1) stage_kernel(const StageArgs<T> A) 
       __shared__ unsigned char mk[2][MH][MW];
       const bool doit = compute || premask;      // uniform over the CTA
       const int pz = z & 1, pn = pz ^ 1;
-      auto SA = [&](int c, int ax, int ay, int dz) -> T { return plb[dz + G][c * PLANE + ay * SXL + ax]; };
       if (doit) {
-        for (int j = tid; j < NE; j += TXY) {
-          const int ex = j % EXW - 1, ey = j / EXW - 1;
-          const T r0 = SA(0, ex, ey, 0), i0 = SA(1, ex, ey, 0);
-          const T rz = SA(0, ex, ey, 1), iz = SA(1, ex, ey, 1);
+#pragma unroll
+        for (int k = 0; k < NEK; ++k) {
+          if (k * TXY + tid >= NE) break;
+          const int ex = e_x[k], ey = e_y[k];
+          auto SE = [&](int c, int dx, int dy, int dz) -> T { return plb[dz + G][c * PLANE + e_off[k] + dy * SXL + dx]; };
+          const T r0 = SE(0, 0, 0, 0), i0 = SE(1, 0, 0, 0);
+          const T rz = SE(0, 0, 0, 1), iz = SE(1, 0, 0, 1);
           ezv[ey + 1][ex + 1] = (signed char)edge_delta(r0, i0, rz, iz);
-          exy[pn][0][ey + 1][ex + 1] = (signed char)edge_delta(rz, iz, SA(0, ex + 1, ey, 1), SA(1, ex + 1, ey, 1));
-          if (ey < TY) exy[pn][1][ey + 1][ex + 1] = (signed char)edge_delta(rz, iz, SA(0, ex, ey + 1, 1), SA(1, ex, ey + 1, 1));
+          exy[pn][0][ey + 1][ex + 1] = (signed char)edge_delta(rz, iz, SE(0, 1, 0, 1), SE(1, 1, 0, 1));
+          if (ey < TY) exy[pn][1][ey + 1][ex + 1] = (signed char)edge_delta(rz, iz, SE(0, 0, 1, 1), SE(1, 0, 1, 1));
           if (premask) {
-            exy[pz][0][ey + 1][ex + 1] = (signed char)edge_delta(r0, i0, SA(0, ex + 1, ey, 0), SA(1, ex + 1, ey, 0));
-            if (ey < TY) exy[pz][1][ey + 1][ex + 1] = (signed char)edge_delta(r0, i0, SA(0, ex, ey + 1, 0), SA(1, ex, ey + 1, 0));
+            exy[pz][0][ey + 1][ex + 1] = (signed char)edge_delta(r0, i0, SE(0, 1, 0, 0), SE(1, 1, 0, 0));
+            if (ey < TY) exy[pz][1][ey + 1][ex + 1] = (signed char)edge_delta(r0, i0, SE(0, 0, 1, 0), SE(1, 0, 1, 0));
           }
         }
       }
       __syncthreads();
       if (doit) {
-        for (int j = tid; j < NM; j += TXY) {
-          const int mx = j % MW, my = j / MW;   // cell offset (mx-1, my-1) from (x0, y0)
+#pragma unroll
+        for (int k = 0; k < NMK; ++k) {
+          if (k * TXY + tid >= NM) break;
+          const int mx = m_x[k], my = m_y[k];   // cell offset (mx-1, my-1) from (x0, y0)
           const int ex_c = exy[pz][0][my][mx], ey_c = exy[pz][1][my][mx], ez_c = ezv[my][mx];
           const int ey_cx = exy[pz][1][my][mx + 1], ez_cx = ezv[my][mx + 1];
           const int ex_cy = exy[pz][0][my + 1][mx], ez_cy = ezv[my + 1][mx];
