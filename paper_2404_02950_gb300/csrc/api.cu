@@ -82,8 +82,7 @@ static void free_level(Level& L) {
   cudaFree(L.tile.d_items);
   cudaFree(L.d_boxes);
   cudaFree(L.d_bmap);
-  cudaFree(L.d_slabs);
-  cudaFree(L.d_slab_off);
+  cudaFree(L.d_gregions);
   cudaFree(L.d_covered);
   cudaFree(L.d_ritems);
   cudaFree(L.d_roff);
@@ -305,6 +304,93 @@ static slh_status validate_boxes(slh_ctx* c, int lev, const slh_box* boxes, int 
   return SLH_OK;
 }
 
+// Split [a, b] (inclusive) at multiples of `step` relative to `base` and at
+// the domain boundaries 0 and n (so that one periodic image applies).
+static void split_axis(int a, int b, int base, int step, int n, std::vector<std::pair<int, int>>* out) {
+  out->clear();
+  int s0 = a;
+  while (s0 <= b) {
+    int e = b;
+    const int nextb = base + ((s0 - base) / step + 1) * step;   // next chunk boundary above s0 (s0 >= base)
+    if (s0 >= base && nextb - 1 < e) e = nextb - 1;
+    if (s0 < base && base - 1 < e) e = base - 1;
+    if (s0 < 0 && -1 < e) e = -1;
+    if (s0 < n && n - 1 < e) e = n - 1;
+    out->push_back({s0, e});
+    s0 = e + 1;
+  }
+}
+
+// Ghost regions of every box: each of the six ghost slabs is cut at the box
+// bounds, every GHOST_CHUNK cells and at the domain boundaries; each piece is
+// classified from the host block map (blocks of bf >= g cells, so a piece
+// meets few blocks).
+static slh_status plan_ghost_regions(slh_ctx* c, Level& L, std::vector<GhostRegion>* out, long long* total) {
+  const int g = c->g, bf = c->bf, n = L.n_dom, nbd = L.nb_dom;
+  out->clear();
+  *total = 0;
+  std::vector<std::pair<int, int>> sx, sy, sz;
+  for (size_t b = 0; b < L.lay.boxes.size(); ++b) {
+    const BoxDev& B = L.lay.boxes[b];
+    const int nn[3] = {B.n[0], B.n[1], B.n[2]};
+    // six slabs: (lo, hi) valid-relative, inclusive
+    int slabs[6][2][3] = {
+        {{-g, -g, -g}, {nn[0] + g - 1, nn[1] + g - 1, -1}},
+        {{-g, -g, nn[2]}, {nn[0] + g - 1, nn[1] + g - 1, nn[2] + g - 1}},
+        {{-g, -g, 0}, {nn[0] + g - 1, -1, nn[2] - 1}},
+        {{-g, nn[1], 0}, {nn[0] + g - 1, nn[1] + g - 1, nn[2] - 1}},
+        {{-g, 0, 0}, {-1, nn[1] - 1, nn[2] - 1}},
+        {{nn[0], 0, 0}, {nn[0] + g - 1, nn[1] - 1, nn[2] - 1}},
+    };
+    for (auto& sl : slabs) {
+      // split in global coordinates so domain boundaries are seen
+      split_axis(B.lo[0] + sl[0][0], B.lo[0] + sl[1][0], B.lo[0], GHOST_CHUNK, n, &sx);
+      split_axis(B.lo[1] + sl[0][1], B.lo[1] + sl[1][1], B.lo[1], GHOST_CHUNK, n, &sy);
+      split_axis(B.lo[2] + sl[0][2], B.lo[2] + sl[1][2], B.lo[2], GHOST_CHUNK, n, &sz);
+      for (auto& zz : sz)
+        for (auto& yy : sy)
+          for (auto& xx : sx) {
+            GhostRegion R;
+            R.box = (int)b;
+            const int glo[3] = {xx.first, yy.first, zz.first}, ghi[3] = {xx.second, yy.second, zz.second};
+            int wl[3], k[3];
+            for (int d = 0; d < 3; ++d) {
+              R.lo[d] = glo[d] - B.lo[d];
+              R.ext[d] = ghi[d] - glo[d] + 1;
+              k[d] = glo[d] < 0 ? -1 : (glo[d] >= n ? 1 : 0);   // one periodic image per piece
+              wl[d] = glo[d] - k[d] * n;
+            }
+            // classify by the blocks the piece meets
+            int own = -2;
+            bool same = true, any_cov = false, any_unc = false;
+            for (int bz = wl[2] / bf; bz <= (wl[2] + R.ext[2] - 1) / bf; ++bz)
+              for (int by = wl[1] / bf; by <= (wl[1] + R.ext[1] - 1) / bf; ++by)
+                for (int bx = wl[0] / bf; bx <= (wl[0] + R.ext[0] - 1) / bf; ++bx) {
+                  const int o = L.h_bmap[((size_t)bz * nbd + by) * nbd + bx];
+                  if (o >= 0) any_cov = true; else any_unc = true;
+                  if (own == -2) own = o;
+                  else if (o != own) same = false;
+                }
+            R.src = -1;
+            R.d[0] = R.d[1] = R.d[2] = 0;
+            if (!any_cov) {
+              R.kind = GHOST_PROLONG;
+            } else if (!any_unc && same) {
+              R.kind = GHOST_COPY;
+              R.src = own;
+              const BoxDev& S = L.lay.boxes[own];
+              for (int d = 0; d < 3; ++d) R.d[d] = B.lo[d] - k[d] * n - S.lo[d];
+            } else {
+              R.kind = GHOST_MIXED;
+            }
+            out->push_back(R);
+            *total += (long long)R.ext[0] * R.ext[1] * R.ext[2];
+          }
+    }
+  }
+  return SLH_OK;
+}
+
 // Fill the metadata of level lev (boxes already validated) into L.
 static slh_status build_level(slh_ctx* c, int lev, Level& L, const slh_box* boxes, int nboxes, void* const* bufs,
                               uint8_t* tags_dev, const std::vector<int>& bmap) {
@@ -324,32 +410,15 @@ static slh_status build_level(slh_ctx* c, int lev, Level& L, const slh_box* boxe
   if ((st = upload(&L.d_bmap, bmap)) != SLH_OK) return st;
   L.h_bmap = bmap;
 
-  // ghost shell slabs
-  const int g = c->g;
-  std::vector<GhostSlab> slabs;
-  std::vector<long long> soff;
-  long long tot = 0;
-  for (int b = 0; b < nboxes; ++b) {
-    const BoxDev& B = L.lay.boxes[b];
-    const int n0 = B.n[0], n1 = B.n[1], n2 = B.n[2];
-    GhostSlab s6[6] = {
-        {b, {-g, -g, -g}, {n0 + 2 * g, n1 + 2 * g, g}},
-        {b, {-g, -g, n2}, {n0 + 2 * g, n1 + 2 * g, g}},
-        {b, {-g, -g, 0}, {n0 + 2 * g, g, n2}},
-        {b, {-g, n1, 0}, {n0 + 2 * g, g, n2}},
-        {b, {-g, 0, 0}, {g, n1, n2}},
-        {b, {n0, 0, 0}, {g, n1, n2}},
-    };
-    for (auto& sl : s6) {
-      slabs.push_back(sl);
-      soff.push_back(tot);
-      tot += (long long)sl.e[0] * sl.e[1] * sl.e[2];
-    }
+  // ghost shell regions, classified from the block map
+  {
+    std::vector<GhostRegion> regs;
+    long long tot = 0;
+    if ((st = plan_ghost_regions(c, L, &regs, &tot)) != SLH_OK) return st;
+    L.ngregions = (int)regs.size();
+    L.nghost_cells = tot;
+    if ((st = upload(&L.d_gregions, regs)) != SLH_OK) return st;
   }
-  L.nslabs = (int)slabs.size();
-  L.nghost_cells = tot;
-  if ((st = upload(&L.d_slabs, slabs)) != SLH_OK) return st;
-  if ((st = upload(&L.d_slab_off, soff)) != SLH_OK) return st;
 
   {
     int nv = 0;

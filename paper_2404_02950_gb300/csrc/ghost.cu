@@ -7,28 +7,6 @@
 
 namespace slh {
 
-template <typename T>
-struct GhostArgs {
-  const BoxDev* boxes;
-  const GhostSlab* slabs;
-  const long long* slab_off;
-  int nslabs;
-  long long total;
-  T* y;
-  int gl;
-  const int* bmap;
-  int bshift, nbd, ndom;
-  // coarser level
-  const BoxDev* cboxes;
-  const T* cold;
-  const T* cnew;
-  const int* cbmap;
-  int cbshift, cnbd, cndom;
-  double alpha;
-  int itype;
-  int* err;
-};
-
 __device__ __forceinline__ int wrapi(int v, int n) {
   v %= n;
   return v < 0 ? v + n : v;
@@ -66,84 +44,138 @@ __device__ __forceinline__ double pw(int itype, int child, int off) {
   return off == 0 ? 1.0 : 0.0;
 }
 
+// Ghost fill by regions (see GhostRegion): copy regions are plain strided
+// copies; prolongation regions first gather the coarser level's cells under
+// the region's stencil footprint, time-interpolated, into shared memory (one
+// box lookup per coarse cell instead of one per stencil point), then every
+// fine ghost cell sums its (2r+1)^3 tensor-product stencil from shared memory
+// in the order z (outer), y, x (inner); mixed regions decide cell by cell.
+constexpr int PATCH_MAX = 21 * 21 * 7;   // coarse cells under a 32 x 32 x g region (r <= 2, g <= 4)
+
 template <typename T>
-__global__ void ghost_kernel(const GhostArgs<T> A) {
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < A.total; t += stride) {
-    // slab lookup (binary search over prefix offsets)
-    int lo = 0, hi = A.nslabs - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (A.slab_off[mid] <= t) lo = mid; else hi = mid - 1;
+struct GhostArgs {
+  const BoxDev* boxes;
+  const GhostRegion* regions;
+  int nregions;
+  T* y;
+  int gl;
+  const int* bmap;
+  int bshift, nbd, ndom;
+  // coarser level
+  const BoxDev* cboxes;
+  const T* cold;
+  const T* cnew;
+  const int* cbmap;
+  int cnbd, cndom;
+  double alpha;
+  int itype;
+  int* err;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) ghost_region_kernel(const GhostArgs<T> A) {
+  extern __shared__ __align__(16) double patch[];   // [2][pz][py][px], time-interpolated psi1, psi2
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int rad = A.itype == 4 ? 2 : (A.itype == 2 ? 1 : 0);
+  const double al = A.alpha, bl = 1.0 - A.alpha;
+  for (int r = blockIdx.x; r < A.nregions; r += gridDim.x) {
+    const GhostRegion R = A.regions[r];
+    const BoxDev B = A.boxes[R.box];
+    const int ncell = R.ext[0] * R.ext[1] * R.ext[2];
+    if (R.kind == GHOST_COPY) {
+      const BoxDev S = A.boxes[R.src];
+      for (int t = tid; t < ncell; t += nt) {
+        const int i = t % R.ext[0], j = (t / R.ext[0]) % R.ext[1], k = t / (R.ext[0] * R.ext[1]);
+        const int rx = R.lo[0] + i, ry = R.lo[1] + j, rz = R.lo[2] + k;
+        const long long dst = cell_index(B, A.gl, rx, ry, rz);
+        const long long src = cell_index(S, A.gl, rx + R.d[0], ry + R.d[1], rz + R.d[2]);
+        A.y[dst] = A.y[src];
+        A.y[dst + B.cs] = A.y[src + S.cs];
+      }
+      continue;   // uniform over the CTA: no shared memory used
     }
-    const GhostSlab S = A.slabs[lo];
-    const long long loc = t - A.slab_off[lo];
-    const int i = (int)(loc % S.e[0]);
-    const int j = (int)((loc / S.e[0]) % S.e[1]);
-    const int k = (int)(loc / ((long long)S.e[0] * S.e[1]));
-    const BoxDev B = A.boxes[S.box];
-    const int rx = S.s[0] + i, ry = S.s[1] + j, rz = S.s[2] + k;
-    const int wx = wrapi(B.lo[0] + rx, A.ndom), wy = wrapi(B.lo[1] + ry, A.ndom), wz = wrapi(B.lo[2] + rz, A.ndom);
-    const long long dst = cell_index(B, A.gl, rx, ry, rz);
-    const int own = A.bmap[((long long)(wz >> A.bshift) * A.nbd + (wy >> A.bshift)) * A.nbd + (wx >> A.bshift)];
-    if (own >= 0) {
-      const BoxDev Sb = A.boxes[own];
-      const long long src = cell_index(Sb, A.gl, wx - Sb.lo[0], wy - Sb.lo[1], wz - Sb.lo[2]);
-      A.y[dst] = A.y[src];
-      A.y[dst + B.cs] = A.y[src + Sb.cs];
-      continue;
+    // coarse footprint of the region's stencils (unwrapped coarse coordinates)
+    int plo[3], pn[3];
+    for (int d = 0; d < 3; ++d) {
+      const int flo = B.lo[d] + R.lo[d], fhi = flo + R.ext[d] - 1;
+      plo[d] = (flo >> 1) - rad;
+      pn[d] = (fhi >> 1) + rad - plo[d] + 1;
     }
-    if (A.cboxes == nullptr) {
-      atomicCAS(A.err, 0, DERR_NESTING);
-      continue;
-    }
-    // prolongation from the coarser level at time fraction alpha
-    const int Px = wx >> 1, Py = wy >> 1, Pz = wz >> 1;
-    const int cx = wx & 1, cy = wy & 1, cz = wz & 1;
-    const int rad = A.itype == 4 ? 2 : (A.itype == 2 ? 1 : 0);
-    const double al = A.alpha, bl = 1.0 - A.alpha;
-    double acc0 = 0.0, acc1 = 0.0;
-    bool bad = false;
-    for (int oz = -rad; oz <= rad; ++oz) {
-      const double wzv = pw(A.itype, cz, oz);
-      const int qz = wrapi(Pz + oz, A.cndom);
-      for (int oy = -rad; oy <= rad; ++oy) {
-        const double wyv = pw(A.itype, cy, oy);
-        const int qy = wrapi(Py + oy, A.cndom);
-        for (int ox = -rad; ox <= rad; ++ox) {
-          const double wxv = pw(A.itype, cx, ox);
-          const int qx = wrapi(Px + ox, A.cndom);
-          const int cown = A.cbmap[((long long)(qz >> A.cbshift) * A.cnbd + (qy >> A.cbshift)) * A.cnbd + (qx >> A.cbshift)];
-          if (cown < 0) {
-            bad = true;
-            continue;
-          }
+    const int np = pn[0] * pn[1] * pn[2];
+    const bool have_coarse = A.cboxes != nullptr && np <= PATCH_MAX;
+    if (have_coarse) {
+      for (int t = tid; t < np; t += nt) {
+        const int i = t % pn[0], j = (t / pn[0]) % pn[1], k = t / (pn[0] * pn[1]);
+        const int qx = wrapi(plo[0] + i, A.cndom), qy = wrapi(plo[1] + j, A.cndom), qz = wrapi(plo[2] + k, A.cndom);
+        const int cown = A.cbmap[((long long)(qz >> A.bshift) * A.cnbd + (qy >> A.bshift)) * A.cnbd + (qx >> A.bshift)];
+        double v0 = __longlong_as_double(0x7ff8000000000000ll), v1 = v0;   // NaN: not covered
+        if (cown >= 0) {
           const BoxDev C = A.cboxes[cown];
           const long long ci = cell_index(C, A.gl, qx - C.lo[0], qy - C.lo[1], qz - C.lo[2]);
-          const double v0 = bl * (double)A.cold[ci] + al * (double)A.cnew[ci];
-          const double v1 = bl * (double)A.cold[ci + C.cs] + al * (double)A.cnew[ci + C.cs];
-          const double wgt = wzv * wyv * wxv;
-          acc0 += wgt * v0;
-          acc1 += wgt * v1;
+          v0 = bl * (double)A.cold[ci] + al * (double)A.cnew[ci];
+          v1 = bl * (double)A.cold[ci + C.cs] + al * (double)A.cnew[ci + C.cs];
         }
+        patch[t] = v0;
+        patch[np + t] = v1;
       }
     }
-    if (bad) atomicCAS(A.err, 0, DERR_NESTING);
-    A.y[dst] = (T)acc0;
-    A.y[dst + B.cs] = (T)acc1;
+    __syncthreads();
+    for (int t = tid; t < ncell; t += nt) {
+      const int i = t % R.ext[0], j = (t / R.ext[0]) % R.ext[1], k = t / (R.ext[0] * R.ext[1]);
+      const int rx = R.lo[0] + i, ry = R.lo[1] + j, rz = R.lo[2] + k;
+      const long long dst = cell_index(B, A.gl, rx, ry, rz);
+      const int gx = B.lo[0] + rx, gy = B.lo[1] + ry, gz = B.lo[2] + rz;   // unwrapped fine coordinates
+      if (R.kind == GHOST_MIXED) {
+        const int wx = wrapi(gx, A.ndom), wy = wrapi(gy, A.ndom), wz = wrapi(gz, A.ndom);
+        const int own = A.bmap[((long long)(wz >> A.bshift) * A.nbd + (wy >> A.bshift)) * A.nbd + (wx >> A.bshift)];
+        if (own >= 0) {
+          const BoxDev Sb = A.boxes[own];
+          const long long src = cell_index(Sb, A.gl, wx - Sb.lo[0], wy - Sb.lo[1], wz - Sb.lo[2]);
+          A.y[dst] = A.y[src];
+          A.y[dst + B.cs] = A.y[src + Sb.cs];
+          continue;
+        }
+      }
+      if (!have_coarse) {
+        atomicCAS(A.err, 0, DERR_NESTING);
+        continue;
+      }
+      const int Px = gx >> 1, Py = gy >> 1, Pz = gz >> 1;
+      const int cx = gx & 1, cy = gy & 1, cz = gz & 1;
+      double acc0 = 0.0, acc1 = 0.0;
+      bool bad = false;
+      for (int oz = -rad; oz <= rad; ++oz) {
+        const double wzv = pw(A.itype, cz, oz);
+        for (int oy = -rad; oy <= rad; ++oy) {
+          const double wyv = pw(A.itype, cy, oy);
+          const int rowb = ((Pz + oz - plo[2]) * pn[1] + (Py + oy - plo[1])) * pn[0] - plo[0];
+          for (int ox = -rad; ox <= rad; ++ox) {
+            const double wxv = pw(A.itype, cx, ox);
+            const int pi = rowb + Px + ox;
+            const double v0 = patch[pi], v1 = patch[np + pi];
+            if (v0 != v0) bad = true;
+            const double wgt = wzv * wyv * wxv;
+            acc0 += wgt * v0;
+            acc1 += wgt * v1;
+          }
+        }
+      }
+      if (bad) atomicCAS(A.err, 0, DERR_NESTING);
+      A.y[dst] = (T)acc0;
+      A.y[dst + B.cs] = (T)acc1;
+    }
+    __syncthreads();   // the patch is reused by the next region
   }
 }
 
 template <typename T>
 static slh_status ghosts_t(slh_ctx* c, int lev, int role, double alpha, int itype) {
   Level& L = c->lev[lev];
-  if (L.nghost_cells == 0) return SLH_OK;
+  if (L.ngregions == 0) return SLH_OK;
   GhostArgs<T> A;
   A.boxes = L.d_boxes;
-  A.slabs = L.d_slabs;
-  A.slab_off = L.d_slab_off;
-  A.nslabs = L.nslabs;
-  A.total = L.nghost_cells;
+  A.regions = L.d_gregions;
+  A.nregions = L.ngregions;
   A.y = static_cast<T*>(L.buf[role]);
   A.gl = c->g;
   A.bmap = L.d_bmap;
@@ -158,24 +190,27 @@ static slh_status ghosts_t(slh_ctx* c, int lev, int role, double alpha, int ityp
     A.cold = static_cast<const T*>(C.buf[C.role_prev]);
     A.cnew = static_cast<const T*>(C.buf[C.role_y]);
     A.cbmap = C.d_bmap;
-    A.cbshift = sh;
     A.cnbd = C.nb_dom;
     A.cndom = C.n_dom;
   } else {
     A.cboxes = nullptr;
     A.cold = A.cnew = nullptr;
     A.cbmap = nullptr;
-    A.cbshift = 0;
     A.cnbd = A.cndom = 0;
   }
   A.alpha = alpha;
   A.itype = itype;
   A.err = c->d_err;
-  const int threads = 256;
-  long long blocks = (L.nghost_cells + threads - 1) / threads;
-  const long long cap = (long long)c->num_sms * 8;
+  const int smem = 2 * PATCH_MAX * (int)sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(ghost_region_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
+  long long blocks = L.ngregions;
+  const long long cap = (long long)c->num_sms * 4;
   if (blocks > cap) blocks = cap;
-  ghost_kernel<T><<<(int)blocks, threads, 0, c->stream>>>(A);
+  ghost_region_kernel<T><<<(int)blocks, 256, smem, c->stream>>>(A);
   SLH_CUDA(cudaGetLastError());
   return SLH_OK;
 }

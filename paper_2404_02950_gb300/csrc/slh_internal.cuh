@@ -30,12 +30,24 @@ struct BoxDev {
   long long voff;   // offset of the box's first valid cell in dense valid-cell arrays
 };
 
-// One rectangular piece of a box's ghost shell: cells start..start+ext-1 in
-// valid-relative coordinates (-g .. n+g-1).
-struct GhostSlab {
+// A rectangular piece of a box's ghost shell (at most 32 cells along its two
+// long axes): cells lo..lo+ext-1 in valid-relative coordinates (-g .. n+g-1),
+// classified on the host from the level's block map:
+//   GHOST_COPY     every cell lies in box `src` of the same level under one
+//                  periodic image: source valid-relative = cell + d
+//   GHOST_PROLONG  no cell lies in a box of the same level
+//   GHOST_MIXED    anything else (per-cell lookup)
+constexpr int GHOST_COPY = 0;
+constexpr int GHOST_PROLONG = 1;
+constexpr int GHOST_MIXED = 2;
+constexpr int GHOST_CHUNK = 32;
+struct GhostRegion {
   int box;
-  int s[3];
-  int e[3];
+  int lo[3];
+  int ext[3];
+  int kind;
+  int src;
+  int d[3];
 };
 
 // Restriction work: one fine box, its coarse region.
@@ -80,9 +92,8 @@ struct Level {
   int* d_bmap = nullptr;         // block owner map, blocks of bf cells
   std::vector<int> h_bmap;       // host mirror of the block owner map
   int nb_dom = 0;
-  GhostSlab* d_slabs = nullptr;
-  long long* d_slab_off = nullptr;
-  int nslabs = 0;
+  GhostRegion* d_gregions = nullptr;
+  int ngregions = 0;
   long long nghost_cells = 0;
   Tile tile;                     // stage work items for the chosen tile variant
   std::map<unsigned long long, void*> tmaps;   // device tensor maps per (G, TX, TY)
