@@ -72,11 +72,11 @@ struct GhostArgs {
   int* err;
 };
 
-template <typename T>
+template <typename T, int RAD>
 __global__ void __launch_bounds__(256) ghost_region_kernel(const GhostArgs<T> A) {
   extern __shared__ __align__(16) double patch[];   // [2][pz][py][px], time-interpolated psi1, psi2
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int rad = A.itype == 4 ? 2 : (A.itype == 2 ? 1 : 0);
+  constexpr int rad = RAD;
   const double al = A.alpha, bl = 1.0 - A.alpha;
   for (int r = blockIdx.x; r < A.nregions; r += gridDim.x) {
     const GhostRegion R = A.regions[r];
@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(256) ghost_region_kernel(const GhostArgs<T> A)
     const int np = pn[0] * pn[1] * pn[2];
     const bool have_coarse = A.cboxes != nullptr && np <= PATCH_MAX;
     if (have_coarse) {
+#pragma unroll 4
       for (int t = tid; t < np; t += nt) {
         const int i = t % pn[0], j = (t / pn[0]) % pn[1], k = t / (pn[0] * pn[1]);
         const int qx = wrapi(plo[0] + i, A.cndom), qy = wrapi(plo[1] + j, A.cndom), qz = wrapi(plo[2] + k, A.cndom);
@@ -142,19 +143,27 @@ __global__ void __launch_bounds__(256) ghost_region_kernel(const GhostArgs<T> A)
       }
       const int Px = gx >> 1, Py = gy >> 1, Pz = gz >> 1;
       const int cx = gx & 1, cy = gy & 1, cz = gz & 1;
+      double wx[2 * RAD + 1], wy[2 * RAD + 1], wz[2 * RAD + 1];
+#pragma unroll
+      for (int o = -RAD; o <= RAD; ++o) {
+        wx[o + RAD] = pw(A.itype, cx, o);
+        wy[o + RAD] = pw(A.itype, cy, o);
+        wz[o + RAD] = pw(A.itype, cz, o);
+      }
       double acc0 = 0.0, acc1 = 0.0;
       bool bad = false;
-      for (int oz = -rad; oz <= rad; ++oz) {
-        const double wzv = pw(A.itype, cz, oz);
-        for (int oy = -rad; oy <= rad; ++oy) {
-          const double wyv = pw(A.itype, cy, oy);
-          const int rowb = ((Pz + oz - plo[2]) * pn[1] + (Py + oy - plo[1])) * pn[0] - plo[0];
-          for (int ox = -rad; ox <= rad; ++ox) {
-            const double wxv = pw(A.itype, cx, ox);
-            const int pi = rowb + Px + ox;
-            const double v0 = patch[pi], v1 = patch[np + pi];
-            if (v0 != v0) bad = true;
-            const double wgt = wzv * wyv * wxv;
+      const int base = ((Pz - RAD - plo[2]) * pn[1] + (Py - RAD - plo[1])) * pn[0] + (Px - RAD - plo[0]);
+#pragma unroll
+      for (int oz = 0; oz <= 2 * RAD; ++oz) {
+#pragma unroll
+        for (int oy = 0; oy <= 2 * RAD; ++oy) {
+          const double wzy = wz[oz] * wy[oy];
+          const int rowb = base + (oz * pn[1] + oy) * pn[0];
+#pragma unroll
+          for (int ox = 0; ox <= 2 * RAD; ++ox) {
+            const double v0 = patch[rowb + ox], v1 = patch[np + rowb + ox];
+            bad |= (v0 != v0);
+            const double wgt = wzy * wx[ox];
             acc0 += wgt * v0;
             acc1 += wgt * v1;
           }
@@ -204,13 +213,17 @@ static slh_status ghosts_t(slh_ctx* c, int lev, int role, double alpha, int ityp
   const int smem = 2 * PATCH_MAX * (int)sizeof(double);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(ghost_region_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(ghost_region_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(ghost_region_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(ghost_region_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     attr = true;
   }
   long long blocks = L.ngregions;
   const long long cap = (long long)c->num_sms * 4;
   if (blocks > cap) blocks = cap;
-  ghost_region_kernel<T><<<(int)blocks, 256, smem, c->stream>>>(A);
+  if (itype == 4) ghost_region_kernel<T, 2><<<(int)blocks, 256, smem, c->stream>>>(A);
+  else if (itype == 2) ghost_region_kernel<T, 1><<<(int)blocks, 256, smem, c->stream>>>(A);
+  else ghost_region_kernel<T, 0><<<(int)blocks, 256, smem, c->stream>>>(A);
   SLH_CUDA(cudaGetLastError());
   return SLH_OK;
 }
