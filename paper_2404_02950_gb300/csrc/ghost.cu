@@ -74,10 +74,13 @@ struct GhostArgs {
 
 template <typename T, int RAD>
 __global__ void __launch_bounds__(256) ghost_region_kernel(const GhostArgs<T> A) {
-  extern __shared__ __align__(16) double patch[];   // [2][pz][py][px], time-interpolated psi1, psi2
+  // [2][pz][py][px]: time-interpolated psi1, psi2 in the field precision
+  // (the stencil weights are dyadic rationals, exact in FP32 and FP64)
+  extern __shared__ __align__(16) unsigned char patch_raw[];
+  T* patch = reinterpret_cast<T*>(patch_raw);
   const int tid = threadIdx.x, nt = blockDim.x;
   constexpr int rad = RAD;
-  const double al = A.alpha, bl = 1.0 - A.alpha;
+  const T al = (T)A.alpha, bl = (T)1 - (T)A.alpha;
   for (int r = blockIdx.x; r < A.nregions; r += gridDim.x) {
     const GhostRegion R = A.regions[r];
     const BoxDev B = A.boxes[R.box];
@@ -109,12 +112,12 @@ __global__ void __launch_bounds__(256) ghost_region_kernel(const GhostArgs<T> A)
         const int i = t % pn[0], j = (t / pn[0]) % pn[1], k = t / (pn[0] * pn[1]);
         const int qx = wrapi(plo[0] + i, A.cndom), qy = wrapi(plo[1] + j, A.cndom), qz = wrapi(plo[2] + k, A.cndom);
         const int cown = A.cbmap[((long long)(qz >> A.bshift) * A.cnbd + (qy >> A.bshift)) * A.cnbd + (qx >> A.bshift)];
-        double v0 = __longlong_as_double(0x7ff8000000000000ll), v1 = v0;   // NaN: not covered
+        T v0 = (T)__longlong_as_double(0x7ff8000000000000ll), v1 = v0;   // NaN: not covered
         if (cown >= 0) {
           const BoxDev C = A.cboxes[cown];
           const long long ci = cell_index(C, A.gl, qx - C.lo[0], qy - C.lo[1], qz - C.lo[2]);
-          v0 = bl * (double)A.cold[ci] + al * (double)A.cnew[ci];
-          v1 = bl * (double)A.cold[ci + C.cs] + al * (double)A.cnew[ci + C.cs];
+          v0 = bl * A.cold[ci] + al * A.cnew[ci];
+          v1 = bl * A.cold[ci + C.cs] + al * A.cnew[ci + C.cs];
         }
         patch[t] = v0;
         patch[np + t] = v1;
@@ -143,35 +146,35 @@ __global__ void __launch_bounds__(256) ghost_region_kernel(const GhostArgs<T> A)
       }
       const int Px = gx >> 1, Py = gy >> 1, Pz = gz >> 1;
       const int cx = gx & 1, cy = gy & 1, cz = gz & 1;
-      double wx[2 * RAD + 1], wy[2 * RAD + 1], wz[2 * RAD + 1];
+      T wx[2 * RAD + 1], wy[2 * RAD + 1], wz[2 * RAD + 1];
 #pragma unroll
       for (int o = -RAD; o <= RAD; ++o) {
-        wx[o + RAD] = pw(A.itype, cx, o);
-        wy[o + RAD] = pw(A.itype, cy, o);
-        wz[o + RAD] = pw(A.itype, cz, o);
+        wx[o + RAD] = (T)pw(A.itype, cx, o);
+        wy[o + RAD] = (T)pw(A.itype, cy, o);
+        wz[o + RAD] = (T)pw(A.itype, cz, o);
       }
-      double acc0 = 0.0, acc1 = 0.0;
+      T acc0 = 0, acc1 = 0;
       bool bad = false;
       const int base = ((Pz - RAD - plo[2]) * pn[1] + (Py - RAD - plo[1])) * pn[0] + (Px - RAD - plo[0]);
 #pragma unroll
       for (int oz = 0; oz <= 2 * RAD; ++oz) {
 #pragma unroll
         for (int oy = 0; oy <= 2 * RAD; ++oy) {
-          const double wzy = wz[oz] * wy[oy];
+          const T wzy = wz[oz] * wy[oy];
           const int rowb = base + (oz * pn[1] + oy) * pn[0];
 #pragma unroll
           for (int ox = 0; ox <= 2 * RAD; ++ox) {
-            const double v0 = patch[rowb + ox], v1 = patch[np + rowb + ox];
+            const T v0 = patch[rowb + ox], v1 = patch[np + rowb + ox];
             bad |= (v0 != v0);
-            const double wgt = wzy * wx[ox];
+            const T wgt = wzy * wx[ox];
             acc0 += wgt * v0;
             acc1 += wgt * v1;
           }
         }
       }
       if (bad) atomicCAS(A.err, 0, DERR_NESTING);
-      A.y[dst] = (T)acc0;
-      A.y[dst + B.cs] = (T)acc1;
+      A.y[dst] = acc0;
+      A.y[dst + B.cs] = acc1;
     }
     __syncthreads();   // the patch is reused by the next region
   }
@@ -210,7 +213,7 @@ static slh_status ghosts_t(slh_ctx* c, int lev, int role, double alpha, int ityp
   A.alpha = alpha;
   A.itype = itype;
   A.err = c->d_err;
-  const int smem = 2 * PATCH_MAX * (int)sizeof(double);
+  const int smem = 2 * PATCH_MAX * (int)sizeof(T);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(ghost_region_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
