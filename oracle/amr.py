@@ -30,6 +30,7 @@ from __future__ import annotations
 
 import numpy as np
 
+from . import gw as ogw
 from . import interp, winding
 from .eom import EOMParams, rhs
 from .energy import energy_box
@@ -40,8 +41,9 @@ A_RK = (0.0, 0.5, 0.5, 1.0)
 
 
 class Level:
-    def __init__(self, lev, boxes, n, dx, dt, g, bf):
+    def __init__(self, lev, boxes, n, dx, dt, g, bf, ncomp=4):
         self.lev, self.n, self.dx, self.dt, self.g, self.bf = lev, n, dx, dt, g, bf
+        self.ncomp = ncomp
         self.boxes = [(tuple(int(v) for v in lo), tuple(int(v) for v in hi)) for lo, hi in boxes]
         if n % bf:
             raise ValueError("domain not a multiple of the blocking factor")
@@ -56,7 +58,7 @@ class Level:
             if (blk >= 0).any():
                 raise ValueError("boxes overlap")
             blk[...] = b
-        self.data = [np.zeros((4,) + self.padded_shape(b)) for b in range(len(self.boxes))]
+        self.data = [np.zeros((ncomp,) + self.padded_shape(b)) for b in range(len(self.boxes))]
         self.old = None
         self.eta = None
 
@@ -105,10 +107,10 @@ class Level:
         return out
 
     def set_dense(self, fields):
-        """Fill valid cells from four dense arrays over the level domain."""
+        """Fill valid cells from dense arrays (one per field) over the level domain."""
         for b, (lo, hi) in enumerate(self.boxes):
             v = self.valid(b)
-            for c in range(4):
+            for c in range(len(fields)):
                 self.data[b][c][v[1:]] = fields[c][lo[2]:hi[2] + 1, lo[1]:hi[1] + 1, lo[0]:hi[0] + 1]
 
     def covered_mask(self, b, finer):
@@ -180,12 +182,16 @@ def rhs_box(arr, g, dx, eta, p: EOMParams):
 
 
 class Hierarchy:
-    """Levels 0..L-1 with fixed (or externally regridded) boxes."""
+    """Levels 0..L-1 with fixed (or externally regridded) boxes.  With
+    ``gw`` the state carries the 12 gravitational-wave fields of oracle.gw
+    (16 fields; ghosts of psi and u are filled)."""
 
-    def __init__(self, levels, params: EOMParams, interp_type: int = 4):
+    def __init__(self, levels, params: EOMParams, interp_type: int = 4, gw: bool = False):
         self.levels = levels
         self.p = params
         self.interp_type = interp_type
+        self.gw = gw
+        self.ghost_comps = (0, 1, 4, 5, 6, 7, 8, 9) if gw else (0, 1)
         self.tag_log = []          # optional (lev, eta, [tags per box]) at stage 1
         self.record_tags = False
 
@@ -205,13 +211,19 @@ class Hierarchy:
                 for b in range(len(Y)):
                     v = L.valid(b)
                     Y[b][v] = y0[b][v] + (A_RK[s] * dt) * ks[s - 1][b]
-            fill_ghosts(L, Y, C, alpha, self.interp_type)
+            fill_ghosts(L, Y, C, alpha, self.interp_type, comps=self.ghost_comps)
             if s == 0 and self.record_tags:
                 self.tag_log.append((lev, eta, [winding.cell_tags_padded(a[0], a[1], g) for a in Y]))
-            ks.append([rhs_box(Y[b], g, L.dx, eta + C_RK[s] * dt, self.p) for b in range(len(Y))])
+            ks.append([self._rhs(Y[b], g, L.dx, eta + C_RK[s] * dt) for b in range(len(Y))])
         for b in range(len(Y)):
             v = L.valid(b)
             L.data[b][v] = y0[b][v] + (dt / 6.0) * (ks[0][b] + 2.0 * ks[1][b] + 2.0 * ks[2][b] + ks[3][b])
+
+    def _rhs(self, arr, g, dx, eta):
+        k = rhs_box(arr, g, dx, eta, self.p)
+        if not self.gw:
+            return k
+        return np.concatenate([k, np.stack(ogw.rhs_box_gw(arr, g, dx, eta, self.p))])
 
     def restrict(self, fine_lev):
         F = self.levels[fine_lev]
@@ -219,7 +231,7 @@ class Hierarchy:
         gc = Cl.g
         for b, (flo, fhi) in enumerate(F.boxes):
             fv = F.data[b][F.valid(b)]
-            red = np.stack([interp.restrict_block(fv[c]) for c in range(4)])
+            red = np.stack([interp.restrict_block(fv[c]) for c in range(F.ncomp)])
             clo = [flo[d] // 2 for d in range(3)]
             nz, ny, nx = red.shape[1:]
             kz, ky, kx = np.indices((nz, ny, nx))
@@ -230,7 +242,7 @@ class Hierarchy:
             for s in np.unique(own):
                 sel = own == s
                 slo = Cl.boxes[s][0]
-                for c in range(4):
+                for c in range(F.ncomp):
                     Cl.data[s][c][kz[sel] - slo[2] + gc, ky[sel] - slo[1] + gc,
                                   kx[sel] - slo[0] + gc] = red[c][sel]
 
@@ -258,7 +270,7 @@ class Hierarchy:
         C = self.coarse_of(lev)
         if C is not None and C.old is None:
             C.old = [a.copy() for a in C.data]
-        fill_ghosts(L, arrs, C, 1.0, self.interp_type)
+        fill_ghosts(L, arrs, C, 1.0, self.interp_type, comps=self.ghost_comps)
         return arrs
 
     def tags(self, lev):
@@ -284,23 +296,24 @@ class Hierarchy:
         return np.array([K, G, P, K + G + P, S])
 
 
-def make_hierarchy(n0, dx0, dt0, g, bf, level_boxes, params: EOMParams, interp_type=4, eta0=0.1):
+def make_hierarchy(n0, dx0, dt0, g, bf, level_boxes, params: EOMParams, interp_type=4, eta0=0.1, gw=False):
     """level_boxes[l] = list of (lo, hi) for level l (level 0 usually the one
     box covering the domain)."""
     levels = []
     for l, boxes in enumerate(level_boxes):
-        L = Level(l, boxes, n0 * 2 ** l, dx0 / 2 ** l, dt0 / 2 ** l, g, bf)
+        L = Level(l, boxes, n0 * 2 ** l, dx0 / 2 ** l, dt0 / 2 ** l, g, bf, ncomp=16 if gw else 4)
         L.eta = eta0
         levels.append(L)
-    return Hierarchy(levels, params, interp_type)
+    return Hierarchy(levels, params, interp_type, gw=gw)
 
 
-def prolong_level_from_coarse(fine: Level, coarse: Level, interp_type: int, comps=(0, 1, 2, 3)):
+def prolong_level_from_coarse(fine: Level, coarse: Level, interp_type: int, comps=None):
     """Initialise every valid cell of ``fine`` by prolongation of the coarse
     level's current state (used to create refined levels from a coarse
     initial state)."""
     if coarse.old is None:
         coarse.old = [a.copy() for a in coarse.data]
+    comps = tuple(range(fine.ncomp)) if comps is None else comps
     nc = coarse.n
     for b, (lo, hi) in enumerate(fine.boxes):
         kz, ky, kx = np.indices(tuple(hi[d] - lo[d] + 1 for d in (2, 1, 0)))
@@ -325,7 +338,7 @@ def regrid_level(h: Hierarchy, lev: int, new_boxes):
     if not new_boxes:
         del h.levels[lev:]
         return
-    L = Level(lev, new_boxes, C.n * 2, C.dx / 2, C.dt / 2, C.g, C.bf)
+    L = Level(lev, new_boxes, C.n * 2, C.dx / 2, C.dt / 2, C.g, C.bf, ncomp=C.ncomp)
     L.eta = C.eta
     prolong_level_from_coarse(L, C, h.interp_type)
     if old is not None:
@@ -339,7 +352,7 @@ def regrid_level(h: Hierarchy, lev: int, new_boxes):
                 if not sel.any():
                     continue
                 olo = old.boxes[s_][0]
-                for c in range(4):
+                for c in range(L.ncomp):
                     L.data[b][c][kz[sel] - lo[2] + g, ky[sel] - lo[1] + g, kx[sel] - lo[0] + g] = \
                         old.data[s_][c][kz[sel] - olo[2] + g, ky[sel] - olo[1] + g, kx[sel] - olo[0] + g]
     if old is None:
