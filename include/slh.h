@@ -9,7 +9,13 @@
  * synchronisation (Sec. 2.1, Fig. 2), classic RK4 (integrator type 4 of the
  * "integrator" table), string-winding refinement tags (the problem-specific
  * tagging hook of Sec. 4.2) and Berger-Rigoutsos style regridding
- * (Sec. 2.2-2.3).
+ * (Sec. 2.2-2.3).  Optionally (nfields = 16) it also evolves the auxiliary
+ * gravitational-wave tensor of Sec. 5: six components u_ij (xx, yy, zz, xy,
+ * xz, yz) and their conformal-time derivatives v_ij, with
+ *   u_ij' = v_ij
+ *   v_ij' = -c_fric v_ij + lap u_ij + 2 (d_i psi1 d_j psi1 + d_i psi2 d_j psi2)
+ * (the string-network source of Eq. GWEOM in conformal time; the gradients
+ * are the central differences of accuracy lap_order, App. A).
  *
  * Conventions shared by every call
  * --------------------------------
@@ -31,7 +37,8 @@
  *    inclusive lo/hi cell indices in its level's index space; boxes of a
  *    level are disjoint, multiples of and aligned to the blocking factor.
  *    In device buffers each box is stored component by component
- *    (psi1, psi2, Pi1, Pi2) with nghost ghost layers in y and z and a
+ *    (psi1, psi2, Pi1, Pi2, then with 16 fields u_xx, u_yy, u_zz, u_xy, u_xz,
+ *    u_yz, v_xx, ..., v_yz) with nghost ghost layers in y and z and a
  *    16-byte aligned x padding; slh_level_layout reports the offsets.
  *    "Dense" host/device arrays (slh_set_state / slh_get_state, tags) hold
  *    only valid cells: [box][component][z][y][x] with boxes in list order.
@@ -76,10 +83,10 @@ typedef int32_t slh_status;
 #define SLH_USE_GRAPH 4u    /* slh_advance: replay a captured CUDA graph */
 
 /* slh_fill_ghosts modes */
-#define SLH_GHOSTS 0     /* fill psi ghosts of the level's state */
+#define SLH_GHOSTS 0     /* fill the psi (and u_ij) ghosts of the level's state */
 #define SLH_RESTRICT 1   /* average the level onto the next coarser one
-                            (covered cells, all four fields), then refill
-                            this level's psi ghosts */
+                            (covered cells, every field), then refill
+                            this level's psi (and u_ij) ghosts */
 
 /* Profiling counters (slh_profile_read kinds) */
 #define SLH_PROF_STAGE 0     /* all four RK stages (sum of SLH_PROF_S1..S4) */
@@ -91,7 +98,8 @@ typedef int32_t slh_status;
 #define SLH_PROF_S2 6
 #define SLH_PROF_S3 7
 #define SLH_PROF_S4 8
-#define SLH_PROF_NKINDS 9
+#define SLH_PROF_GW 9        /* the gravitational-wave stage kernel (16 fields) */
+#define SLH_PROF_NKINDS 10
 
 typedef struct {
   int32_t lo[3];
@@ -123,18 +131,19 @@ const char* slh_last_error(void);
 /* Create a hierarchy whose level 0 spans n0^3 cells of spacing dx0 on a
  * periodic domain.  nghost in [1,4] ghost layers (>= lap_order/2, and >= 2
  * for quartic prolongation), blocking_factor a power of two >= 2 dividing
- * n0, prec SLH_F64 or SLH_F32_KAHAN, max_levels in [1,8], stream a
- * cudaStream_t (NULL = legacy default stream).  Allocates metadata only.
- * Errors: INVALID_ARG, NOMEM, CUDA. */
+ * n0, prec SLH_F64 or SLH_F32_KAHAN, max_levels in [1,8], nfields 4 (the
+ * scalar field and momenta) or 16 (plus the gravitational-wave tensor u_ij,
+ * v_ij), stream a cudaStream_t (NULL = legacy default stream).  Allocates
+ * metadata only.  Errors: INVALID_ARG, NOMEM, CUDA. */
 slh_status slh_create(slh_ctx** ctx, int32_t n0, double dx0, int32_t nghost,
                       int32_t blocking_factor, int32_t prec, int32_t max_levels,
-                      void* stream);
+                      int32_t nfields, void* stream);
 
 /* Release the metadata of ctx (field buffers stay with the caller). */
 void slh_destroy(slh_ctx* ctx);
 
-/* Element counts of one level buffer for the given boxes, without a
- * context.  box_offsets (nboxes entries, may be NULL) receives each box's
+/* Element counts of one level buffer of nfields (4 or 16) fields for the
+ * given boxes, without a context.  box_offsets (nboxes entries, may be NULL) receives each box's
  * element offset; box_geom (4*nboxes, may be NULL) receives pitch (x row
  * length incl. padding), padded ny, padded nz and the component stride in
  * elements.  The valid cell (x,y,z) of box b, component c, sits at
@@ -142,7 +151,7 @@ void slh_destroy(slh_ctx* ctx);
  *         + (x-lo_x+4).
  * *total_elems receives the buffer length in elements; *nvalid the number
  * of valid cells over all boxes.  Errors: INVALID_ARG. */
-slh_status slh_level_layout(int32_t nghost, const slh_box* boxes, int32_t nboxes,
+slh_status slh_level_layout(int32_t nghost, int32_t nfields, const slh_box* boxes, int32_t nboxes,
                             int64_t* box_offsets, int64_t* box_geom,
                             int64_t* total_elems, int64_t* nvalid);
 
@@ -163,7 +172,7 @@ slh_status slh_init_level(slh_ctx* ctx, int32_t lev, const slh_box* boxes, int32
  * boxes[nboxes] with caller-owned buffers bufs[SLH_NBUF] laid out as for
  * slh_init_level.  Every valid cell of the new boxes takes the old level's
  * value where an old box covers it, otherwise the ratio-2 prolongation
- * (interp_type 0/2/4) of level lev-1's current state, all four fields; the
+ * (interp_type 0/2/4) of level lev-1's current state, every field; the
  * Kahan compensation is carried over where covered and zero elsewhere.  The
  * new level's previous state equals its state and its eta that of lev-1.
  * nboxes == 0 removes level lev and every finer level.  Finer levels keep
@@ -175,7 +184,7 @@ slh_status slh_init_level(slh_ctx* ctx, int32_t lev, const slh_box* boxes, int32
 slh_status slh_regrid_level(slh_ctx* ctx, int32_t lev, const slh_box* boxes, int32_t nboxes,
                             void* const* bufs, uint8_t* tags_dev, int32_t interp_type);
 
-/* Copy the four fields of level lev from / to a dense valid-cell array
+/* Copy the fields (4 or 16) of level lev from / to a dense valid-cell array
  * ([box][comp][z][y][x], context precision).  src/dst on the host
  * (is_host = 1, ideally pinned) or the device.  slh_set_state also sets the
  * level's previous state equal to it and zeroes the Kahan compensation.
@@ -191,10 +200,11 @@ slh_status slh_get_eta(slh_ctx* ctx, int32_t lev, double* eta);
 /* One classic RK4 step (Tab. "integrator", type 4) of level lev by
  * dt_lev = dt0 / 2^lev.  For lev > 0, sub in {0,1} is the sub-step within
  * the coarser level's step: the level starts at eta_coarse_start +
- * sub*dt_lev and each stage fills psi ghosts from the coarser level at time
+ * sub*dt_lev and each stage fills psi (and u_ij) ghosts from the coarser level at time
  * fraction (sub + c_s)/2, c = (0, 1/2, 1/2, 1) (Sec. 2.1).  Before each
  * stage the ghost fill of level lev runs; the four fused stage kernels then
- * compute the RHS of Sec. 3.1 with the stage-time coefficients.  flags:
+ * compute the RHS of Sec. 3.1 with the stage-time coefficients (with 16
+ * fields a second kernel per stage advances u_ij, v_ij the same way).  flags:
  * SLH_FUSE_TAG (tags of y_n into the level's tags_dev), SLH_FUSE_ENERGY
  * (energy partials of y_n, read with slh_reduce_energy mode 1).
  * Errors: INVALID_ARG, STATE, CUDA. */
@@ -210,7 +220,7 @@ slh_status slh_rk_step(slh_ctx* ctx, int32_t lev, int32_t sub, double dt0,
 slh_status slh_advance(slh_ctx* ctx, double dt0, const slh_eom_params* p, uint32_t flags);
 
 /* Ghost fill / synchronisation of level lev (Sec. 2.1).  mode SLH_GHOSTS:
- * psi ghosts of the level's state from its own boxes (periodic wrap) and,
+ * psi (and u_ij) ghosts of the level's state from its own boxes (periodic wrap) and,
  * where uncovered, by ratio-2 prolongation (interp_type 0/2/4) of the
  * coarser level interpolated in time at fraction alpha in [0,1] between its
  * previous and current state.  mode SLH_RESTRICT (lev >= 1): every cell of

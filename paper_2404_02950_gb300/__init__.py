@@ -33,7 +33,8 @@ SLH_USE_GRAPH = 4
 SLH_GHOSTS = 0
 SLH_RESTRICT = 1
 (SLH_PROF_STAGE, SLH_PROF_GHOST, SLH_PROF_RESTRICT, SLH_PROF_DIAG, SLH_PROF_TIME,
- SLH_PROF_S1, SLH_PROF_S2, SLH_PROF_S3, SLH_PROF_S4) = range(9)
+ SLH_PROF_S1, SLH_PROF_S2, SLH_PROF_S3, SLH_PROF_S4, SLH_PROF_GW) = range(10)
+NFIELDS, NFIELDS_GW = 4, 16   # psi1, psi2, Pi1, Pi2 (+ u_xx..u_yz, v_xx..v_yz)
 
 ERRORS = {-1: "INVALID_ARG", -2: "OUT_OF_RANGE", -3: "CUDA", -4: "TIMEOUT", -5: "NOMEM",
           -6: "DEVICE", -7: "STATE"}
@@ -96,9 +97,9 @@ def lib():
     P = ctypes.POINTER
     sig = {
         "slh_last_error": (ctypes.c_char_p, []),
-        "slh_create": (i32, [P(vp), i32, dbl, i32, i32, i32, i32, vp]),
+        "slh_create": (i32, [P(vp), i32, dbl, i32, i32, i32, i32, i32, vp]),
         "slh_destroy": (None, [vp]),
-        "slh_level_layout": (i32, [i32, P(slh_box), i32, P(i64), P(i64), P(i64), P(i64)]),
+        "slh_level_layout": (i32, [i32, i32, P(slh_box), i32, P(i64), P(i64), P(i64), P(i64)]),
         "slh_init_level": (i32, [vp, i32, P(slh_box), i32, P(vp), vp]),
         "slh_set_state": (i32, [vp, i32, vp, i32]),
         "slh_get_state": (i32, [vp, i32, vp, i32]),
@@ -145,13 +146,14 @@ def _boxes(boxes):
 # ---------------------------------------------------------------------------
 # ABI-named wrappers
 
-def slh_level_layout(nghost, boxes):
+def slh_level_layout(nghost, boxes, nfields=NFIELDS):
     """(box_offsets, box_geom (n,4), total_elems, nvalid) of a level layout."""
     n = len(boxes)
     offs = (ctypes.c_int64 * max(1, n))()
     geom = (ctypes.c_int64 * max(1, 4 * n))()
     tot, nv = ctypes.c_int64(), ctypes.c_int64()
-    _check(lib().slh_level_layout(nghost, _boxes(boxes), n, offs, geom, ctypes.byref(tot), ctypes.byref(nv)))
+    _check(lib().slh_level_layout(nghost, nfields, _boxes(boxes), n, offs, geom, ctypes.byref(tot),
+                                  ctypes.byref(nv)))
     return (np.array(offs[:n], dtype=np.int64), np.array(geom[:4 * n], dtype=np.int64).reshape(n, 4),
             tot.value, nv.value)
 
@@ -193,23 +195,23 @@ def slh_energy_noalloc(fields_dev, n, dx, eta, params: EOMParams, out_dev, strea
 
 
 def dense_from_boxes(fields, boxes):
-    """Pack four [z, y, x] domain arrays into the dense valid-cell layout
-    [box][comp][z][y][x] (host numpy)."""
+    """Pack the [z, y, x] domain arrays of the fields (4 or 16) into the
+    dense valid-cell layout [box][comp][z][y][x] (host numpy)."""
     parts = []
     for lo, hi in boxes:
-        for c in range(4):
+        for c in range(len(fields)):
             parts.append(np.asarray(fields[c])[lo[2]:hi[2] + 1, lo[1]:hi[1] + 1, lo[0]:hi[0] + 1].ravel())
     return np.concatenate(parts)
 
 
-def boxes_from_dense(dense, boxes):
-    """Split a dense valid-cell array into per-box (4, nz, ny, nx) arrays."""
+def boxes_from_dense(dense, boxes, nfields=NFIELDS):
+    """Split a dense valid-cell array into per-box (nfields, nz, ny, nx) arrays."""
     out, off = [], 0
     for lo, hi in boxes:
         n = [hi[d] - lo[d] + 1 for d in range(3)]
         vol = n[0] * n[1] * n[2]
-        out.append(np.asarray(dense[off:off + 4 * vol]).reshape(4, n[2], n[1], n[0]))
-        off += 4 * vol
+        out.append(np.asarray(dense[off:off + nfields * vol]).reshape(nfields, n[2], n[1], n[0]))
+        off += nfields * vol
     return out
 
 
@@ -217,9 +219,11 @@ class Hierarchy:
     """A context plus the torch-allocated buffers of its levels.
 
     n0: level-0 cells per axis; dx0: level-0 spacing; nghost: ghost layers;
-    bf: blocking factor; prec: 'f64' or 'f32' (FP32 + Kahan)."""
+    bf: blocking factor; prec: 'f64' or 'f32' (FP32 + Kahan); gw: also evolve
+    the gravitational-wave tensor (16 fields per cell instead of 4)."""
 
-    def __init__(self, n0, dx0, nghost=3, bf=8, prec="f64", max_levels=1, device="cuda:0", stream=None):
+    def __init__(self, n0, dx0, nghost=3, bf=8, prec="f64", max_levels=1, device="cuda:0", stream=None,
+                 gw=False):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -229,9 +233,10 @@ class Hierarchy:
         # a stream of its own: CUDA graphs cannot capture the legacy default stream
         self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
         self.nghost, self.bf, self.n0, self.dx0 = nghost, bf, n0, dx0
+        self.ncomp = NFIELDS_GW if gw else NFIELDS
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            _check(lib().slh_create(ctypes.byref(h), n0, dx0, nghost, bf, self.prec, max_levels,
+            _check(lib().slh_create(ctypes.byref(h), n0, dx0, nghost, bf, self.prec, max_levels, self.ncomp,
                                     ctypes.c_void_p(self.stream.cuda_stream)))
         self.h = h
         self.levels = {}
@@ -249,7 +254,7 @@ class Hierarchy:
 
     def init_level(self, lev, boxes, fused_tags=False):
         torch = self.torch
-        _, geom, total, nvalid = slh_level_layout(self.nghost, boxes)
+        _, geom, total, nvalid = slh_level_layout(self.nghost, boxes, self.ncomp)
         bufs = []
         for i in range(SLH_NBUF):
             if i == SLH_BUF_C and self.prec == SLH_F64:
@@ -275,7 +280,7 @@ class Hierarchy:
 
     def _alloc_level(self, boxes, fused_tags):
         torch = self.torch
-        _, geom, total, nvalid = slh_level_layout(self.nghost, boxes)
+        _, geom, total, nvalid = slh_level_layout(self.nghost, boxes, self.ncomp)
         bufs = [None if (i == SLH_BUF_C and self.prec == SLH_F64)
                 else torch.empty(int(total), dtype=self.dtype, device=self.device) for i in range(SLH_NBUF)]
         tags = torch.zeros(int(nvalid), dtype=torch.uint8, device=self.device) if fused_tags else None
@@ -340,7 +345,7 @@ class Hierarchy:
             self.sync()
 
     def get_state(self, lev):
-        n = 4 * self.levels[lev]["nvalid"]
+        n = self.ncomp * self.levels[lev]["nvalid"]
         out = np.empty(n, dtype=self.np_dtype)
         _check(lib().slh_get_state(self.h, lev, ctypes.c_void_p(out.ctypes.data), 1))
         return out

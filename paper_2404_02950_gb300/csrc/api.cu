@@ -31,7 +31,7 @@ slh_status cuda_fail(cudaError_t e, const char* what) {
 
 static long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 
-bool make_layout(int g, const slh_box* boxes, int nboxes, Layout* out, std::string* why) {
+bool make_layout(int g, int ncomp, const slh_box* boxes, int nboxes, Layout* out, std::string* why) {
   out->boxes.clear();
   long long off = 0, voff = 0;
   for (int b = 0; b < nboxes; ++b) {
@@ -51,7 +51,7 @@ bool make_layout(int g, const slh_box* boxes, int nboxes, Layout* out, std::stri
     B.cs = round_up((long long)B.pitch * B.pny * B.pnz, 32);
     off = round_up(off, 64);
     B.off = off;
-    off += NCOMP * B.cs;
+    off += ncomp * B.cs;
     B.voff = voff;
     voff += (long long)B.n[0] * B.n[1] * B.n[2];
     out->boxes.push_back(B);
@@ -80,6 +80,7 @@ void prof_end(slh_ctx* c) {
 static void free_level(Level& L) {
   free_tmaps(L);
   cudaFree(L.tile.d_items);
+  cudaFree(L.d_gw_items);
   cudaFree(L.d_boxes);
   cudaFree(L.d_bmap);
   cudaFree(L.d_gregions);
@@ -118,6 +119,9 @@ static int ilog2(int v) {
 }
 
 static size_t elem_size(const slh_ctx* c) { return c->prec == SLH_F64 ? 8 : 4; }
+
+// fields whose ghost cells are filled: psi1, psi2 (+ the six u_ij)
+static int ghost_fields(const slh_ctx* c) { return c->ncomp == NCOMP_GW ? 8 : 2; }
 
 // mark, for the coarser level lev-1, the blocks of bf/2 cells covered by lev
 static slh_status build_covered(slh_ctx* c, int lev) {
@@ -167,12 +171,14 @@ extern "C" {
 
 const char* slh_last_error(void) { return g_last_error.c_str(); }
 
-slh_status slh_level_layout(int32_t nghost, const slh_box* boxes, int32_t nboxes, int64_t* box_offsets,
-                            int64_t* box_geom, int64_t* total_elems, int64_t* nvalid) {
+slh_status slh_level_layout(int32_t nghost, int32_t nfields, const slh_box* boxes, int32_t nboxes,
+                            int64_t* box_offsets, int64_t* box_geom, int64_t* total_elems, int64_t* nvalid) {
   if (!boxes || nboxes < 0 || nghost < 1 || nghost > 4) return fail(SLH_ERR_INVALID_ARG, "layout: bad arguments");
+  if (nfields != NCOMP && nfields != NCOMP_GW) return fail(SLH_ERR_INVALID_ARG, "layout: nfields must be 4 or 16");
   Layout lay;
   std::string why;
-  if (!make_layout(nghost, boxes, nboxes, &lay, &why)) return fail(SLH_ERR_INVALID_ARG, "layout: %s", why.c_str());
+  if (!make_layout(nghost, nfields, boxes, nboxes, &lay, &why))
+    return fail(SLH_ERR_INVALID_ARG, "layout: %s", why.c_str());
   for (int b = 0; b < nboxes; ++b) {
     if (box_offsets) box_offsets[b] = lay.boxes[b].off;
     if (box_geom) {
@@ -188,7 +194,7 @@ slh_status slh_level_layout(int32_t nghost, const slh_box* boxes, int32_t nboxes
 }
 
 slh_status slh_create(slh_ctx** out, int32_t n0, double dx0, int32_t nghost, int32_t bf, int32_t prec,
-                      int32_t max_levels, void* stream) {
+                      int32_t max_levels, int32_t nfields, void* stream) {
   if (!out) return fail(SLH_ERR_INVALID_ARG, "create: ctx pointer is null");
   *out = nullptr;
   if (nghost < 1 || nghost > 4) return fail(SLH_ERR_INVALID_ARG, "create: nghost must be in [1,4]");
@@ -197,6 +203,7 @@ slh_status slh_create(slh_ctx** out, int32_t n0, double dx0, int32_t nghost, int
   if (prec != SLH_F64 && prec != SLH_F32_KAHAN) return fail(SLH_ERR_INVALID_ARG, "create: unknown precision %d", prec);
   if (max_levels < 1 || max_levels > MAX_LEVELS) return fail(SLH_ERR_INVALID_ARG, "create: max_levels must be in [1,8]");
   if (!(dx0 > 0.0)) return fail(SLH_ERR_INVALID_ARG, "create: dx0 must be positive");
+  if (nfields != NCOMP && nfields != NCOMP_GW) return fail(SLH_ERR_INVALID_ARG, "create: nfields must be 4 or 16");
   slh_ctx* c = new (std::nothrow) slh_ctx();
   if (!c) return fail(SLH_ERR_NOMEM, "create: out of host memory");
   c->n0 = n0;
@@ -204,6 +211,7 @@ slh_status slh_create(slh_ctx** out, int32_t n0, double dx0, int32_t nghost, int
   c->g = nghost;
   c->bf = bf;
   c->prec = prec;
+  c->ncomp = nfields;
   c->max_levels = max_levels;
   c->stream = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaGetDevice(&c->device);
@@ -399,7 +407,8 @@ static slh_status build_level(slh_ctx* c, int lev, Level& L, const slh_box* boxe
   L.dx = c->dx0 / (double)(1 << lev);
   L.boxes.assign(boxes, boxes + nboxes);
   std::string why;
-  if (!make_layout(c->g, boxes, nboxes, &L.lay, &why)) return fail(SLH_ERR_INVALID_ARG, "level %d: %s", lev, why.c_str());
+  if (!make_layout(c->g, c->ncomp, boxes, nboxes, &L.lay, &why))
+    return fail(SLH_ERR_INVALID_ARG, "level %d: %s", lev, why.c_str());
   for (int i = 0; i < SLH_NBUF; ++i) L.buf[i] = bufs[i];
   if (c->prec != SLH_F32_KAHAN) L.buf[SLH_BUF_C] = nullptr;
   L.tags_dev = tags_dev;
@@ -424,6 +433,17 @@ static slh_status build_level(slh_ctx* c, int lev, Level& L, const slh_box* boxe
     int nv = 0;
     const TileVariant* vs = tile_variants(c->prec, &nv);
     if ((st = set_tile(c, L, vs[0])) != SLH_OK) return st;
+  }
+  if (c->ncomp == NCOMP_GW) {
+    std::vector<int4> items;
+    for (size_t b = 0; b < L.lay.boxes.size(); ++b) {
+      const BoxDev& B = L.lay.boxes[b];
+      for (int z0 = 0; z0 < B.n[2]; z0 += GW_ZLEN)
+        for (int y0 = 0; y0 < B.n[1]; y0 += GW_TY)
+          for (int x0 = 0; x0 < B.n[0]; x0 += GW_TX) items.push_back(make_int4((int)b, x0, y0, z0));
+    }
+    if ((st = upload(&L.d_gw_items, items)) != SLH_OK) return st;
+    L.ngw_items = (int)items.size();
   }
 
   // restriction items onto lev-1
@@ -553,10 +573,11 @@ static slh_status copy_state(slh_ctx* c, int lev, void* host_or_dev, bool to_dev
   for (size_t b = 0; b < L.lay.boxes.size(); ++b) {
     const BoxDev& B = L.lay.boxes[b];
     const long long vol = (long long)B.n[0] * B.n[1] * B.n[2];
-    for (int comp = 0; comp < NCOMP; ++comp) {
+    for (int comp = 0; comp < c->ncomp; ++comp) {
       cudaMemcpy3DParms p;
       memset(&p, 0, sizeof(p));
-      cudaPitchedPtr dptr = make_cudaPitchedPtr(dense + (size_t)(NCOMP * B.voff + comp * vol) * s, B.n[0] * s, B.n[0], B.n[1]);
+      cudaPitchedPtr dptr =
+          make_cudaPitchedPtr(dense + (size_t)(c->ncomp * B.voff + comp * vol) * s, B.n[0] * s, B.n[0], B.n[1]);
       cudaPitchedPtr bptr = make_cudaPitchedPtr(buf + (size_t)(B.off + comp * B.cs) * s, (size_t)B.pitch * s, B.pitch, B.pny);
       if (to_device) {
         p.srcPtr = dptr;
@@ -651,7 +672,7 @@ static slh_status rk_step_impl(slh_ctx* c, int lev, int sub, double dt0, const s
   const double vals[4] = {12.0, 20.0, 20.0, c->prec == SLH_F32_KAHAN ? 24.0 : 16.0};
   for (int k = 0; k < 4; ++k) {
     const double alpha = lev > 0 ? (sub + cRK[k]) / 2.0 : 1.0;
-    prof_begin(c, SLH_PROF_GHOST, (double)L.nghost_cells * 2 * 2 * s);
+    prof_begin(c, SLH_PROF_GHOST, (double)L.nghost_cells * ghost_fields(c) * 2 * s);
     st = launch_ghosts(c, lev, in_role[k], alpha, p.interp_type);
     prof_end(c);
     if (st != SLH_OK) return st;
@@ -685,6 +706,15 @@ static slh_status rk_step_impl(slh_ctx* c, int lev, int sub, double dt0, const s
     prof_end(c);
     if (st != SLH_OK) return st;
     if (k == 0 && (flags & SLH_FUSE_ENERGY)) L.fused_energy_ctas = used;
+    if (c->ncomp == NCOMP_GW) {
+      // the 12 tensor fields: reads psi (2) + u, v (12) of the stage input,
+      // and as the scalar stage y_n, D, C of its 12 fields
+      const double gvals[4] = {38.0, 62.0, 62.0, c->prec == SLH_F32_KAHAN ? 74.0 : 50.0};
+      prof_begin(c, SLH_PROF_GW, V * gvals[k] * s);
+      st = launch_gw_stage(c, L, p, sl);
+      prof_end(c);
+      if (st != SLH_OK) return st;
+    }
   }
   L.role_y = nbuf;
   L.role_prev = ybuf;
@@ -706,13 +736,13 @@ static slh_status fill_impl(slh_ctx* c, int lev, double alpha, int itype, int mo
   Level& L = c->lev[lev];
   const size_t s = elem_size(c);
   if (mode == SLH_RESTRICT) {
-    prof_begin(c, SLH_PROF_RESTRICT, (double)L.nrcells * NCOMP * 9 * s);
+    prof_begin(c, SLH_PROF_RESTRICT, (double)L.nrcells * c->ncomp * 9 * s);
     slh_status st = launch_restrict(c, lev);
     prof_end(c);
     if (st != SLH_OK) return st;
     alpha = 1.0;
   }
-  prof_begin(c, SLH_PROF_GHOST, (double)L.nghost_cells * 2 * 2 * s);
+  prof_begin(c, SLH_PROF_GHOST, (double)L.nghost_cells * ghost_fields(c) * 2 * s);
   slh_status st = launch_ghosts(c, lev, L.role_y, alpha, itype);
   prof_end(c);
   return st;

@@ -1,5 +1,5 @@
 // Inter-level transfer (Sec. 2.1): ghost fill of a level's psi components
-// from its own boxes (periodic wrap) or, where no box of the level covers a
+// (and, with the gravitational-wave tensor, the six u_ij) from its own boxes (periodic wrap) or, where no box of the level covers a
 // ghost cell, by ratio-2 prolongation of the coarser level interpolated in
 // time; restriction of a fine level onto the covered coarse cells; and the
 // small kernel that advances the per-level conformal time.
@@ -69,8 +69,12 @@ struct GhostArgs {
   int cnbd, cndom;
   double alpha;
   int itype;
+  int npairs;   // field pairs filled: (psi1, psi2) and with 16 fields (u_xx, u_yy), (u_zz, u_xy), (u_xz, u_yz)
   int* err;
 };
+
+// first component of field pair q
+__device__ __forceinline__ int pair_comp(int q) { return q == 0 ? 0 : GW_U0 + 2 * (q - 1); }
 
 template <typename T, int RAD>
 __global__ void __launch_bounds__(256) ghost_region_kernel(const GhostArgs<T> A) {
@@ -92,8 +96,11 @@ __global__ void __launch_bounds__(256) ghost_region_kernel(const GhostArgs<T> A)
         const int rx = R.lo[0] + i, ry = R.lo[1] + j, rz = R.lo[2] + k;
         const long long dst = cell_index(B, A.gl, rx, ry, rz);
         const long long src = cell_index(S, A.gl, rx + R.d[0], ry + R.d[1], rz + R.d[2]);
-        A.y[dst] = A.y[src];
-        A.y[dst + B.cs] = A.y[src + S.cs];
+        for (int q = 0; q < A.npairs; ++q) {
+          const int c0 = pair_comp(q);
+          A.y[dst + c0 * B.cs] = A.y[src + c0 * S.cs];
+          A.y[dst + (c0 + 1) * B.cs] = A.y[src + (c0 + 1) * S.cs];
+        }
       }
       continue;   // uniform over the CTA: no shared memory used
     }
@@ -106,77 +113,80 @@ __global__ void __launch_bounds__(256) ghost_region_kernel(const GhostArgs<T> A)
     }
     const int np = pn[0] * pn[1] * pn[2];
     const bool have_coarse = A.cboxes != nullptr && np <= PATCH_MAX;
-    if (have_coarse) {
+    for (int q = 0; q < A.npairs; ++q) {
+      const int c0 = pair_comp(q);
+      if (have_coarse) {
 #pragma unroll 4
-      for (int t = tid; t < np; t += nt) {
-        const int i = t % pn[0], j = (t / pn[0]) % pn[1], k = t / (pn[0] * pn[1]);
-        const int qx = wrapi(plo[0] + i, A.cndom), qy = wrapi(plo[1] + j, A.cndom), qz = wrapi(plo[2] + k, A.cndom);
-        const int cown = A.cbmap[((long long)(qz >> A.bshift) * A.cnbd + (qy >> A.bshift)) * A.cnbd + (qx >> A.bshift)];
-        T v0 = (T)__longlong_as_double(0x7ff8000000000000ll), v1 = v0;   // NaN: not covered
-        if (cown >= 0) {
-          const BoxDev C = A.cboxes[cown];
-          const long long ci = cell_index(C, A.gl, qx - C.lo[0], qy - C.lo[1], qz - C.lo[2]);
-          v0 = bl * A.cold[ci] + al * A.cnew[ci];
-          v1 = bl * A.cold[ci + C.cs] + al * A.cnew[ci + C.cs];
-        }
-        patch[t] = v0;
-        patch[np + t] = v1;
-      }
-    }
-    __syncthreads();
-    for (int t = tid; t < ncell; t += nt) {
-      const int i = t % R.ext[0], j = (t / R.ext[0]) % R.ext[1], k = t / (R.ext[0] * R.ext[1]);
-      const int rx = R.lo[0] + i, ry = R.lo[1] + j, rz = R.lo[2] + k;
-      const long long dst = cell_index(B, A.gl, rx, ry, rz);
-      const int gx = B.lo[0] + rx, gy = B.lo[1] + ry, gz = B.lo[2] + rz;   // unwrapped fine coordinates
-      if (R.kind == GHOST_MIXED) {
-        const int wx = wrapi(gx, A.ndom), wy = wrapi(gy, A.ndom), wz = wrapi(gz, A.ndom);
-        const int own = A.bmap[((long long)(wz >> A.bshift) * A.nbd + (wy >> A.bshift)) * A.nbd + (wx >> A.bshift)];
-        if (own >= 0) {
-          const BoxDev Sb = A.boxes[own];
-          const long long src = cell_index(Sb, A.gl, wx - Sb.lo[0], wy - Sb.lo[1], wz - Sb.lo[2]);
-          A.y[dst] = A.y[src];
-          A.y[dst + B.cs] = A.y[src + Sb.cs];
-          continue;
+        for (int t = tid; t < np; t += nt) {
+          const int i = t % pn[0], j = (t / pn[0]) % pn[1], k = t / (pn[0] * pn[1]);
+          const int qx = wrapi(plo[0] + i, A.cndom), qy = wrapi(plo[1] + j, A.cndom), qz = wrapi(plo[2] + k, A.cndom);
+          const int cown = A.cbmap[((long long)(qz >> A.bshift) * A.cnbd + (qy >> A.bshift)) * A.cnbd + (qx >> A.bshift)];
+          T v0 = (T)__longlong_as_double(0x7ff8000000000000ll), v1 = v0;   // NaN: not covered
+          if (cown >= 0) {
+            const BoxDev C = A.cboxes[cown];
+            const long long ci = cell_index(C, A.gl, qx - C.lo[0], qy - C.lo[1], qz - C.lo[2]) + c0 * C.cs;
+            v0 = bl * A.cold[ci] + al * A.cnew[ci];
+            v1 = bl * A.cold[ci + C.cs] + al * A.cnew[ci + C.cs];
+          }
+          patch[t] = v0;
+          patch[np + t] = v1;
         }
       }
-      if (!have_coarse) {
-        atomicCAS(A.err, 0, DERR_NESTING);
-        continue;
-      }
-      const int Px = gx >> 1, Py = gy >> 1, Pz = gz >> 1;
-      const int cx = gx & 1, cy = gy & 1, cz = gz & 1;
-      T wx[2 * RAD + 1], wy[2 * RAD + 1], wz[2 * RAD + 1];
-#pragma unroll
-      for (int o = -RAD; o <= RAD; ++o) {
-        wx[o + RAD] = (T)pw(A.itype, cx, o);
-        wy[o + RAD] = (T)pw(A.itype, cy, o);
-        wz[o + RAD] = (T)pw(A.itype, cz, o);
-      }
-      T acc0 = 0, acc1 = 0;
-      bool bad = false;
-      const int base = ((Pz - RAD - plo[2]) * pn[1] + (Py - RAD - plo[1])) * pn[0] + (Px - RAD - plo[0]);
-#pragma unroll
-      for (int oz = 0; oz <= 2 * RAD; ++oz) {
-#pragma unroll
-        for (int oy = 0; oy <= 2 * RAD; ++oy) {
-          const T wzy = wz[oz] * wy[oy];
-          const int rowb = base + (oz * pn[1] + oy) * pn[0];
-#pragma unroll
-          for (int ox = 0; ox <= 2 * RAD; ++ox) {
-            const T v0 = patch[rowb + ox], v1 = patch[np + rowb + ox];
-            bad |= (v0 != v0);
-            const T wgt = wzy * wx[ox];
-            acc0 += wgt * v0;
-            acc1 += wgt * v1;
+      __syncthreads();
+      for (int t = tid; t < ncell; t += nt) {
+        const int i = t % R.ext[0], j = (t / R.ext[0]) % R.ext[1], k = t / (R.ext[0] * R.ext[1]);
+        const int rx = R.lo[0] + i, ry = R.lo[1] + j, rz = R.lo[2] + k;
+        const long long dst = cell_index(B, A.gl, rx, ry, rz) + c0 * B.cs;
+        const int gx = B.lo[0] + rx, gy = B.lo[1] + ry, gz = B.lo[2] + rz;   // unwrapped fine coordinates
+        if (R.kind == GHOST_MIXED) {
+          const int wx = wrapi(gx, A.ndom), wy = wrapi(gy, A.ndom), wz = wrapi(gz, A.ndom);
+          const int own = A.bmap[((long long)(wz >> A.bshift) * A.nbd + (wy >> A.bshift)) * A.nbd + (wx >> A.bshift)];
+          if (own >= 0) {
+            const BoxDev Sb = A.boxes[own];
+            const long long src = cell_index(Sb, A.gl, wx - Sb.lo[0], wy - Sb.lo[1], wz - Sb.lo[2]) + c0 * Sb.cs;
+            A.y[dst] = A.y[src];
+            A.y[dst + B.cs] = A.y[src + Sb.cs];
+            continue;
           }
         }
+        if (!have_coarse) {
+          atomicCAS(A.err, 0, DERR_NESTING);
+          continue;
+        }
+        const int Px = gx >> 1, Py = gy >> 1, Pz = gz >> 1;
+        const int cx = gx & 1, cy = gy & 1, cz = gz & 1;
+        T wx[2 * RAD + 1], wy[2 * RAD + 1], wz[2 * RAD + 1];
+#pragma unroll
+        for (int o = -RAD; o <= RAD; ++o) {
+          wx[o + RAD] = (T)pw(A.itype, cx, o);
+          wy[o + RAD] = (T)pw(A.itype, cy, o);
+          wz[o + RAD] = (T)pw(A.itype, cz, o);
+        }
+        T acc0 = 0, acc1 = 0;
+        bool bad = false;
+        const int base = ((Pz - RAD - plo[2]) * pn[1] + (Py - RAD - plo[1])) * pn[0] + (Px - RAD - plo[0]);
+#pragma unroll
+        for (int oz = 0; oz <= 2 * RAD; ++oz) {
+#pragma unroll
+          for (int oy = 0; oy <= 2 * RAD; ++oy) {
+            const T wzy = wz[oz] * wy[oy];
+            const int rowb = base + (oz * pn[1] + oy) * pn[0];
+#pragma unroll
+            for (int ox = 0; ox <= 2 * RAD; ++ox) {
+              const T v0 = patch[rowb + ox], v1 = patch[np + rowb + ox];
+              bad |= (v0 != v0);
+              const T wgt = wzy * wx[ox];
+              acc0 += wgt * v0;
+              acc1 += wgt * v1;
+            }
+          }
+        }
+        if (bad) atomicCAS(A.err, 0, DERR_NESTING);
+        A.y[dst] = acc0;
+        A.y[dst + B.cs] = acc1;
       }
-      if (bad) atomicCAS(A.err, 0, DERR_NESTING);
-      A.y[dst] = acc0;
-      A.y[dst + B.cs] = acc1;
+      __syncthreads();   // the patch is reused by the next pair or region
     }
-    __syncthreads();   // the patch is reused by the next region
   }
 }
 
@@ -212,6 +222,7 @@ static slh_status ghosts_t(slh_ctx* c, int lev, int role, double alpha, int ityp
   }
   A.alpha = alpha;
   A.itype = itype;
+  A.npairs = c->ncomp == NCOMP_GW ? 4 : 1;
   A.err = c->d_err;
   const int smem = 2 * PATCH_MAX * (int)sizeof(T);
   static bool attr = false;
@@ -254,6 +265,7 @@ struct RestrictArgs {
   const int* cbmap;
   int cbshift, cnbd;
   int gl;
+  int ncomp;
   int* err;
 };
 
@@ -282,8 +294,7 @@ __global__ void restrict_kernel(const RestrictArgs<T> A) {
     const long long dsti = cell_index(C, A.gl, gx - C.lo[0], gy - C.lo[1], gz - C.lo[2]);
     const long long f000 = cell_index(F, A.gl, 2 * i, 2 * j, 2 * k);
     const long long sy = F.pitch, sz = (long long)F.pny * F.pitch;
-#pragma unroll
-    for (int c = 0; c < NCOMP; ++c) {
+    for (int c = 0; c < A.ncomp; ++c) {
       const T* f = A.fy + f000 + c * F.cs;
       double s = (double)f[0];
       s += (double)f[1];
@@ -318,6 +329,7 @@ static slh_status restrict_t(slh_ctx* c, int fl) {
   A.cbshift = sh;
   A.cnbd = C.nb_dom;
   A.gl = c->g;
+  A.ncomp = c->ncomp;
   A.err = c->d_err;
   const int threads = 256;
   long long blocks = (F.nrcells + threads - 1) / threads;
@@ -358,7 +370,7 @@ namespace slh {
 // ---------------------------------------------------------------------------
 // regrid fill (Sec. 2.3): each valid cell of a level's new boxes takes the
 // old level's value where an old box covers it, else the prolongation of the
-// coarser level's current state (all four fields); the Kahan compensation is
+// coarser level's current state (every field); the Kahan compensation is
 // carried over where covered and zero elsewhere.
 
 template <typename T>
@@ -380,6 +392,7 @@ struct RegridFillArgs {
   int bshift;
   int gl;
   int itype;
+  int ncomp;
   int* err;
 };
 
@@ -404,8 +417,7 @@ __global__ void regrid_fill_kernel(const RegridFillArgs<T> A) {
       if (own >= 0) {
         const BoxDev O = A.oboxes[own];
         const long long src = cell_index(O, A.gl, gx - O.lo[0], gy - O.lo[1], gz - O.lo[2]);
-#pragma unroll
-        for (int c = 0; c < NCOMP; ++c) {
+        for (int c = 0; c < A.ncomp; ++c) {
           A.ny[dst + c * B.cs] = A.oy[src + c * O.cs];
           if (A.nc) A.nc[dst + c * B.cs] = A.oc ? A.oc[src + c * O.cs] : (T)0;
         }
@@ -415,36 +427,39 @@ __global__ void regrid_fill_kernel(const RegridFillArgs<T> A) {
     const int Px = gx >> 1, Py = gy >> 1, Pz = gz >> 1;
     const int cx = gx & 1, cy = gy & 1, cz = gz & 1;
     const int rad = A.itype == 4 ? 2 : (A.itype == 2 ? 1 : 0);
-    double acc[NCOMP] = {0.0, 0.0, 0.0, 0.0};
     bool bad = false;
-    for (int oz = -rad; oz <= rad; ++oz) {
-      const double wzv = pw(A.itype, cz, oz);
-      const int qz = wrapi(Pz + oz, A.cndom);
-      for (int oy = -rad; oy <= rad; ++oy) {
-        const double wyv = pw(A.itype, cy, oy);
-        const int qy = wrapi(Py + oy, A.cndom);
-        for (int ox = -rad; ox <= rad; ++ox) {
-          const double wxv = pw(A.itype, cx, ox);
-          const int qx = wrapi(Px + ox, A.cndom);
-          const int cown = A.cbmap[((long long)(qz >> A.bshift) * A.cnbd + (qy >> A.bshift)) * A.cnbd + (qx >> A.bshift)];
-          if (cown < 0) {
-            bad = true;
-            continue;
-          }
-          const BoxDev C = A.cboxes[cown];
-          const long long ci = cell_index(C, A.gl, qx - C.lo[0], qy - C.lo[1], qz - C.lo[2]);
-          const double wgt = wzv * wyv * wxv;
+    // fields in groups of four (one stencil walk per group)
+    for (int c0 = 0; c0 < A.ncomp; c0 += NCOMP) {
+      double acc[NCOMP] = {0.0, 0.0, 0.0, 0.0};
+      for (int oz = -rad; oz <= rad; ++oz) {
+        const double wzv = pw(A.itype, cz, oz);
+        const int qz = wrapi(Pz + oz, A.cndom);
+        for (int oy = -rad; oy <= rad; ++oy) {
+          const double wyv = pw(A.itype, cy, oy);
+          const int qy = wrapi(Py + oy, A.cndom);
+          for (int ox = -rad; ox <= rad; ++ox) {
+            const double wxv = pw(A.itype, cx, ox);
+            const int qx = wrapi(Px + ox, A.cndom);
+            const int cown = A.cbmap[((long long)(qz >> A.bshift) * A.cnbd + (qy >> A.bshift)) * A.cnbd + (qx >> A.bshift)];
+            if (cown < 0) {
+              bad = true;
+              continue;
+            }
+            const BoxDev C = A.cboxes[cown];
+            const long long ci = cell_index(C, A.gl, qx - C.lo[0], qy - C.lo[1], qz - C.lo[2]) + c0 * C.cs;
+            const double wgt = wzv * wyv * wxv;
 #pragma unroll
-          for (int c = 0; c < NCOMP; ++c) acc[c] += wgt * (double)A.cy[ci + c * C.cs];
+            for (int c = 0; c < NCOMP; ++c) acc[c] += wgt * (double)A.cy[ci + c * C.cs];
+          }
         }
+      }
+#pragma unroll
+      for (int c = 0; c < NCOMP; ++c) {
+        A.ny[dst + (c0 + c) * B.cs] = (T)acc[c];
+        if (A.nc) A.nc[dst + (c0 + c) * B.cs] = (T)0;
       }
     }
     if (bad) atomicCAS(A.err, 0, DERR_NESTING);
-#pragma unroll
-    for (int c = 0; c < NCOMP; ++c) {
-      A.ny[dst + c * B.cs] = (T)acc[c];
-      if (A.nc) A.nc[dst + c * B.cs] = (T)0;
-    }
   }
 }
 
@@ -479,6 +494,7 @@ static slh_status regrid_fill_t(slh_ctx* c, int lev, Level& N, Level* O) {
   A.bshift = sh;
   A.gl = c->g;
   A.itype = c->regrid_itype;
+  A.ncomp = c->ncomp;
   A.err = c->d_err;
   const int threads = 256;
   long long blocks = (A.nvalid + threads - 1) / threads;

@@ -1,0 +1,169 @@
+// Gravitational-wave tensor stage kernel (Sec. 5).  With 16 fields per cell
+// the state carries, besides psi and Pi, six tensor components u_ij (ij =
+// xx, yy, zz, xy, xz, yz) and their conformal-time derivatives v_ij, evolved
+// by the string-network form of Eq. GWEOM in conformal time:
+//   u_ij' = v_ij
+//   v_ij' = -c_fric v_ij + lap u_ij + 2 (d_i psi1 d_j psi1 + d_i psi2 d_j psi2)
+// with the same Laplacian as the scalar field and central first differences
+// of the same accuracy for the source (App. A).  One launch per RK4 stage,
+// after the scalar stage kernel and with the same buffer roles, so that the
+// two together advance all 16 fields by classic RK4.
+//
+// Work decomposition: one CTA of GW_TX x GW_TY threads per (box, x0, y0, z0)
+// item, each thread a cell column marching up to GW_ZLEN planes in z.  The
+// stencil operands are plain global loads: x and y neighbours come from the
+// lines the CTA's own rows bring into L1, z neighbours from planes read a few
+// iterations earlier (L1/L2), so DRAM sees each value about once.
+#include "slh_internal.cuh"
+#include "stencil.cuh"
+
+namespace slh {
+
+template <typename T>
+struct GwArgs {
+  const BoxDev* boxes;
+  const int4* items;
+  int gl;
+  const T* in;              // stage input (psi and u ghosts filled)
+  const T* yn;              // y_n
+  T* d;                     // increment accumulator
+  T* out;                   // next stage input, or y_{n+1} at stage 4
+  T* cc;                    // Kahan compensation (stage 4, FP32 form) or null
+  int stage;                // 1..4
+  const double* eta_start;  // device eta at the start of the step
+  double c_stage;           // c_s * dt
+  int friction;
+  double inv_dx, inv_dx2;
+  double ha, hb;            // a_{s+1} dt, b_s dt
+};
+
+// (i, j) direction pairs of the six tensor components
+__device__ __forceinline__ constexpr int pair_i(int k) { return k < 3 ? k : (k == 5 ? 1 : 0); }
+__device__ __forceinline__ constexpr int pair_j(int k) { return k < 3 ? k : (k == 3 ? 1 : 2); }
+
+template <typename T, int G>
+__global__ void __launch_bounds__(GW_TX * GW_TY) gw_stage_kernel(const GwArgs<T> A) {
+  const int4 it = A.items[blockIdx.x];
+  const BoxDev B = A.boxes[it.x];
+  const int x = it.y + threadIdx.x, y = it.z + threadIdx.y;
+  if (x >= B.n[0] || y >= B.n[1]) return;
+  const int z1 = min(it.w + GW_ZLEN, B.n[2]);
+  const double eta = *A.eta_start + A.c_stage;
+  const T c_fric = (T)(A.friction ? 2.0 / eta : 0.0);
+  const T ha = (T)A.ha, hb = (T)A.hb, idx = (T)A.inv_dx, idx2 = (T)A.inv_dx2;
+  const long long sy = B.pitch, sz = (long long)B.pitch * B.pny, cs = B.cs;
+  const long long st[3] = {1, sy, sz};
+  const T* __restrict__ in = A.in;
+  long long e = B.off + ((long long)(it.w + A.gl) * B.pny + (y + A.gl)) * B.pitch + x + XPAD;
+  for (int z = it.w; z < z1; ++z, e += sz) {
+    // gradients of psi1, psi2
+    T g1[3], g2[3];
+#pragma unroll
+    for (int dir = 0; dir < 3; ++dir) {
+      T a1 = 0, a2 = 0;
+#pragma unroll
+      for (int m = 1; m <= G; ++m) {
+        const T w = (T)grad_w<G>(m);
+        const long long o = m * st[dir];
+        a1 += w * (__ldg(in + e + o) - __ldg(in + e - o));
+        a2 += w * (__ldg(in + e + cs + o) - __ldg(in + e + cs - o));
+      }
+      g1[dir] = a1 * idx;
+      g2[dir] = a2 * idx;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const long long eu = e + (GW_U0 + k) * cs, ev = e + (GW_V0 + k) * cs;
+      const T* f = in + eu;
+      const T u0 = __ldg(f);
+      T lap;
+      if (sizeof(T) == 8) {
+        // textbook form, as the scalar FP64 stage
+        T a = (T)(3.0 * lap_w<G>(0)) * u0;
+#pragma unroll
+        for (int m = 1; m <= G; ++m) {
+          const T w = (T)lap_w<G>(m);
+          a += w * (((__ldg(f + m) + __ldg(f - m)) + (__ldg(f + m * sy) + __ldg(f - m * sy))) +
+                    (__ldg(f + m * sz) + __ldg(f - m * sz)));
+        }
+        lap = a * idx2;
+      } else {
+        // difference form, as the scalar FP32 stage
+        T a = 0;
+#pragma unroll
+        for (int m = 1; m <= G; ++m) {
+          const T w = (T)lap_w<G>(m);
+          a += w * ((((__ldg(f + m) - u0) + (__ldg(f - m) - u0)) + ((__ldg(f + m * sy) - u0) + (__ldg(f - m * sy) - u0))) +
+                    ((__ldg(f + m * sz) - u0) + (__ldg(f - m * sz) - u0)));
+        }
+        lap = a * idx2;
+      }
+      const int i = pair_i(k), j = pair_j(k);
+      const T src = (T)2 * (g1[i] * g1[j] + g2[i] * g2[j]);
+      const T v = __ldg(in + ev);
+      const T ku = v;
+      const T kv = ((-c_fric) * v + lap) + src;
+      if (A.stage == 1) {
+        A.out[eu] = u0 + ha * ku;
+        A.out[ev] = v + ha * kv;
+        A.d[eu] = hb * ku;
+        A.d[ev] = hb * kv;
+      } else if (A.stage == 2 || A.stage == 3) {
+        A.out[eu] = __ldg(A.yn + eu) + ha * ku;
+        A.out[ev] = __ldg(A.yn + ev) + ha * kv;
+        A.d[eu] = A.d[eu] + hb * ku;
+        A.d[ev] = A.d[ev] + hb * kv;
+      } else {
+        const T yu = __ldg(A.yn + eu), yv = __ldg(A.yn + ev);
+        const T iu = A.d[eu] + hb * ku, iv = A.d[ev] + hb * kv;
+        if (A.cc) {
+          // compensated sum y + inc, the rounding error carried in C
+          T w, sm;
+          w = iu - A.cc[eu]; sm = yu + w; A.cc[eu] = (sm - yu) - w; A.out[eu] = sm;
+          w = iv - A.cc[ev]; sm = yv + w; A.cc[ev] = (sm - yv) - w; A.out[ev] = sm;
+        } else {
+          A.out[eu] = yu + iu;
+          A.out[ev] = yv + iv;
+        }
+      }
+    }
+  }
+}
+
+template <typename T>
+static slh_status gw_stage_t(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s) {
+  if (L.ngw_items == 0) return SLH_OK;
+  GwArgs<T> A;
+  A.boxes = L.d_boxes;
+  A.items = L.d_gw_items;
+  A.gl = c->g;
+  A.in = static_cast<const T*>(L.buf[s.in_buf]);
+  A.yn = static_cast<const T*>(L.buf[s.yn_buf]);
+  A.d = static_cast<T*>(L.buf[s.d_buf]);
+  A.out = static_cast<T*>(L.buf[s.out_buf]);
+  A.cc = s.c_buf >= 0 ? static_cast<T*>(L.buf[s.c_buf]) : nullptr;
+  A.stage = s.stage;
+  A.eta_start = c->d_time + 2 * s.lev + 1;
+  A.c_stage = s.c_stage;
+  A.friction = p.friction;
+  A.inv_dx = 1.0 / L.dx;
+  A.inv_dx2 = 1.0 / (L.dx * L.dx);
+  A.ha = s.ha;
+  A.hb = s.hb;
+  const dim3 block(GW_TX, GW_TY);
+  switch (p.lap_order) {
+    case 2: gw_stage_kernel<T, 1><<<L.ngw_items, block, 0, c->stream>>>(A); break;
+    case 4: gw_stage_kernel<T, 2><<<L.ngw_items, block, 0, c->stream>>>(A); break;
+    case 6: gw_stage_kernel<T, 3><<<L.ngw_items, block, 0, c->stream>>>(A); break;
+    default: return fail(SLH_ERR_INVALID_ARG, "lap_order must be 2, 4 or 6 (got %d)", p.lap_order);
+  }
+  SLH_CUDA(cudaGetLastError());
+  return SLH_OK;
+}
+
+slh_status launch_gw_stage(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s) {
+  if (s.stage < 1 || s.stage > 4) return fail(SLH_ERR_INVALID_ARG, "gw stage %d outside 1..4", s.stage);
+  return c->prec == SLH_F64 ? gw_stage_t<double>(c, L, p, s) : gw_stage_t<float>(c, L, p, s);
+}
+
+}  // namespace slh

@@ -15,7 +15,9 @@ namespace slh {
 // x padding in front of the first valid cell of every row: keeps the first
 // valid cell 16-byte aligned for FP32 and FP64 and is >= every ghost width.
 constexpr int XPAD = 4;
-constexpr int NCOMP = 4;
+constexpr int NCOMP = 4;        // psi1, psi2, Pi1, Pi2
+constexpr int NCOMP_GW = 16;    // + u_xx..u_yz (4..9), v_xx..v_yz (10..15)
+constexpr int GW_U0 = 4, GW_V0 = 10;
 constexpr int MAX_LEVELS = 8;
 
 // Per-box geometry as the kernels see it.
@@ -75,7 +77,7 @@ struct Layout {
   long long nvalid = 0;
 };
 
-bool make_layout(int g, const slh_box* boxes, int nboxes, Layout* out, std::string* why);
+bool make_layout(int g, int ncomp, const slh_box* boxes, int nboxes, Layout* out, std::string* why);
 
 struct Level {
   bool defined = false;
@@ -96,6 +98,8 @@ struct Level {
   int ngregions = 0;
   long long nghost_cells = 0;
   Tile tile;                     // stage work items for the chosen tile variant
+  int4* d_gw_items = nullptr;    // GW stage work items (box, x0, y0, z0)
+  int ngw_items = 0;
   std::map<unsigned long long, void*> tmaps;   // device tensor maps per (G, TX, TY)
   uint8_t* d_covered = nullptr;  // covered by the finer level, blocks of bf/2 cells
   int ncov = 0;
@@ -123,6 +127,7 @@ struct slh_ctx {
   int g = 0;
   int bf = 0;
   int prec = SLH_F64;
+  int ncomp = slh::NCOMP;        // fields per cell: 4, or 16 with the GW tensor
   int max_levels = 1;
   int nlevels = 0;
   cudaStream_t stream = nullptr;
@@ -186,6 +191,9 @@ slh_status launch_stage(slh_ctx* c, Level& L, const slh_eom_params& p, const Sta
 const TileVariant* tile_variants(int prec, int* n);
 void free_tmaps(Level& L);
 slh_status launch_expired_wait(slh_ctx* c, long long polls);
+
+slh_status launch_gw_stage(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s);
+constexpr int GW_TX = 32, GW_TY = 8, GW_ZLEN = 32;
 
 slh_status launch_ghosts(slh_ctx* c, int lev, int role, double alpha, int itype);
 slh_status launch_restrict(slh_ctx* c, int fine_lev);

@@ -26,6 +26,7 @@
 #include <mutex>
 
 #include "slh_internal.cuh"
+#include "stencil.cuh"
 
 namespace slh {
 
@@ -127,18 +128,6 @@ __device__ __forceinline__ int edge_delta(float ar, float ai, float br, float bi
   if (ua != ub && !(fabsf(s) > aq * 1.1920928955078125e-07f && (aq > 1e-30f || fabsf(s) > 1e-30f)))
     s = exact_cross_sign(ar, ai, br, bi);
   return (int)(ua && !ub && s > 0.0f) - (int)(!ua && ub && s < 0.0f);
-}
-
-// Central second-difference weights w_m, m = 0..G (w_0 the centre weight).
-template <int G>
-__device__ __forceinline__ double lap_w(int m);
-template <>
-__device__ __forceinline__ double lap_w<1>(int m) { return m == 0 ? -2.0 : 1.0; }
-template <>
-__device__ __forceinline__ double lap_w<2>(int m) { return m == 0 ? -2.5 : (m == 1 ? 4.0 / 3.0 : -1.0 / 12.0); }
-template <>
-__device__ __forceinline__ double lap_w<3>(int m) {
-  return m == 0 ? -49.0 / 18.0 : (m == 1 ? 1.5 : (m == 2 ? -0.15 : 1.0 / 90.0));
 }
 
 // shared-memory geometry of one kernel variant

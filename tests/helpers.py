@@ -50,14 +50,15 @@ def tags_domain(tags_dense, boxes, n):
 
 
 def box_padded_views(h, lev, role=None):
-    """Per-box padded (4, pnz, pny, pitch) torch views of a level buffer."""
+    """Per-box padded (ncomp, pnz, pny, pitch) torch views of a level buffer."""
     info = h.levels[lev]
-    offs, geom, _, _ = slh.slh_level_layout(h.nghost, info["boxes"])
+    nc = h.ncomp
+    offs, geom, _, _ = slh.slh_level_layout(h.nghost, info["boxes"], nc)
     buf = h.state_buffer(lev) if role is None else info["bufs"][role]
     views = []
     for b in range(len(info["boxes"])):
         pitch, pny, pnz, cs = (int(v) for v in geom[b])
         o = int(offs[b])
-        v = buf[o:o + 4 * cs].view(4, cs)[:, :pitch * pny * pnz].view(4, pnz, pny, pitch)
+        v = buf[o:o + nc * cs].view(nc, cs)[:, :pitch * pny * pnz].view(nc, pnz, pny, pitch)
         views.append(v)
     return views

@@ -120,3 +120,24 @@ def test_layout_rejects_bad_boxes():
         slh.slh_level_layout(3, [((0, 0, 0), (-1, 7, 7))])
     with pytest.raises(slh.SlhError):
         slh.slh_level_layout(0, [((0, 0, 0), (7, 7, 7))])
+    with pytest.raises(slh.SlhError) as e:
+        slh.slh_level_layout(3, [((0, 0, 0), (7, 7, 7))], nfields=5)
+    assert e.value.code == -1 and "nfields" in str(e.value)
+
+
+def test_layout_with_tensor_fields():
+    """16 fields (psi, Pi, u_ij, v_ij): the same box geometry, 16 component
+    strides per box instead of 4."""
+    boxes = [((0, 0, 0), (15, 31, 47)), ((16, 0, 0), (47, 15, 15))]
+    o4, g4, t4, n4 = slh.slh_level_layout(3, boxes, 4)
+    o16, g16, t16, n16 = slh.slh_level_layout(3, boxes, 16)
+    assert n4 == n16 and (g4 == g16).all()
+    assert o16[0] == 0 and o16[1] >= 16 * g16[0][3] and t16 >= o16[1] + 16 * g16[1][3]
+    assert t16 > 3.9 * t4
+
+
+def test_create_rejects_bad_field_count():
+    import ctypes
+    h = ctypes.c_void_p()
+    st = slh.lib().slh_create(ctypes.byref(h), 32, 0.5, 3, 8, slh.SLH_F64, 1, 5, None)
+    assert st == -1 and b"nfields" in slh.lib().slh_last_error()
