@@ -31,6 +31,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import gw as ogw
+from . import tee
 from . import interp, winding
 from .eom import EOMParams, rhs
 from .energy import energy_box
@@ -194,6 +195,8 @@ class Hierarchy:
         self.ghost_comps = (0, 1, 4, 5, 6, 7, 8, 9) if gw else (0, 1)
         self.tag_log = []          # optional (lev, eta, [tags per box]) at stage 1
         self.record_tags = False
+        self.te_eps = None         # TEE thresholds of (psi1, psi2, Pi1, Pi2): self-shadow tags at sync
+        self.te_tags = {}          # lev -> [tags per box] from the last synchronisation of lev
 
     def coarse_of(self, lev):
         return self.levels[lev - 1] if lev > 0 else None
@@ -239,6 +242,11 @@ class Hierarchy:
             own = Cl.owners_of(kz, ky, kx)
             if (own < 0).any():
                 raise ValueError("fine level not covered by the coarse level")
+            if self.te_eps is not None:
+                # self-shadow TEE (Sec. 2.2): the coarse values before they are replaced
+                cval = Cl.gather([Cl.data], range(tee.NSCALAR), kz, ky, kx)[0]
+                te = tee.te_on_coarse(cval, fv[:tee.NSCALAR])
+                self.te_tags.setdefault(fine_lev, [None] * len(F.boxes))[b] = tee.tags_from_te(te, self.te_eps)
             for s in np.unique(own):
                 sel = own == s
                 slo = Cl.boxes[s][0]
