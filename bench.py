@@ -175,14 +175,14 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def _time_form(slh, torch, prec, y0_dense, n, K, W, dist, flags):
+def _time_form(slh, torch, prec, y0_dense, n, K, W, dist, flags, gw=False, order=ORDER):
     """Warm up, then time K steps of one precision; returns a dict."""
-    h = slh.Hierarchy(n, DX, nghost=3, bf=16, prec=prec, max_levels=1)
+    h = slh.Hierarchy(n, DX, nghost=3, bf=16, prec=prec, max_levels=1, gw=gw)
     boxes = [((0, 0, 0), (n - 1, n - 1, n - 1))]
     h.init_level(0, boxes, fused_tags=True)
     h.set_state(0, y0_dense.astype(h.np_dtype))
     h.set_eta(ETA0)
-    p = slh.EOMParams(order=ORDER)
+    p = slh.EOMParams(order=order)
     chosen, tune_ms = h.autotune(0, p, reps=3)
     for _ in range(W):
         h.advance(DT, p, flags=flags)
@@ -207,12 +207,47 @@ def _time_form(slh, torch, prec, y0_dense, n, K, W, dist, flags):
     stage = h.profile_read(slh.SLH_PROF_STAGE)
     ghost = h.profile_read(slh.SLH_PROF_GHOST)
     tim = h.profile_read(slh.SLH_PROF_TIME)
+    gwk = h.profile_read(slh.SLH_PROF_GW)
     h.profile(False, True)
     E = h.reduce_energy(p, mode=1)
     out = dict(ms=ms, stage_ms=stage[0], stage_launches=stage[1], stage_bytes=stage[2],
                ghost_ms=ghost[0], ghost_launches=ghost[1], time_launches=tim[1], energy=E.tolist(),
-               per_stage_ms=[m / K for m in per_stage], tile_variant=chosen, tune_ms=tune_ms)
+               per_stage_ms=[m / K for m in per_stage], tile_variant=chosen, tune_ms=tune_ms,
+               gw_ms=gwk[0], gw_launches=gwk[1], gw_bytes=gwk[2],
+               buffer_bytes=sum(b.numel() * b.element_size() for b in h.levels[0]["bufs"] if b is not None))
     return h, out
+
+
+GW_N, GW_ORDER, GW_K = 512, 4, 5
+GW_WORKLOAD = ("gravitational-wave tensor (16 fields: psi, Pi, u_ij, v_ij): uniform 512^3 periodic lattice, "
+               "4th-order Laplacian and gradients, classic RK4, FP32 + Kahan, Gaussian psi init "
+               "k_max=pi/(4dx), u = v = 0, dx=1/8, dt=dx/4, eta0=0.1, tags+energy fused in stage 1")
+GW_VALUES = 236            # tensor-field values moved per cell-update by the GW kernel (FP32 + Kahan)
+
+
+def _gw_form(slh, torch, n, dist, peak, K=GW_K):
+    """Uniform 16-field lattice: whole-step throughput and the GW stage
+    kernel's achieved HBM bandwidth."""
+    from paper_2404_02950_gb300 import inputs
+    y = [a.astype(np.float32) for a in inputs.gaussian_field(n, n / 8.0, seed=7)]
+    zero = np.zeros_like(y[0])
+    dense = slh.dense_from_boxes(y + [zero] * 12, [((0, 0, 0), (n - 1,) * 3)])
+    del y, zero
+    flags = slh.SLH_FUSE_TAG | slh.SLH_FUSE_ENERGY
+    h, r = _time_form(slh, torch, "f32", dense, n, K, 3, dist, flags, gw=True, order=GW_ORDER)
+    h.close()
+    del h, dense
+    torch.cuda.empty_cache()
+    ach = r["gw_bytes"] / (r["gw_ms"] / 1e3) / 1e9
+    return {"workload": GW_WORKLOAD, "unit": "cell-updates/s",
+            "value": float(n) ** 3 * K / (r["ms"] / 1e3), "ms_per_step": r["ms"] / K,
+            "gw_kernel": {"achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                          "ms_per_step": r["gw_ms"] / K, "launches": r["gw_launches"],
+                          "alg_bytes_per_cell_update": GW_VALUES * 4},
+            "scalar_stage_ms_per_step": r["stage_ms"] / K, "ghost_ms_per_step": r["ghost_ms"] / K,
+            "hbm_footprint_gb": r["buffer_bytes"] / 1e9,
+            "footprint_note": ("5 level buffers x 16 FP32 fields = 320 B per cell: 1024^3 would need 344 GB "
+                               "(over the 288 GB of HBM); the largest lattice under 150 GB is 768^3")}
 
 
 AMR_N, AMR_LEVELS, AMR_NBUF, AMR_BF, AMR_MAXBOX, AMR_RELAX, AMR_EVERY = 256, 3, 4, 16, 128, 100, 4
@@ -222,10 +257,9 @@ AMR_WORKLOAD = ("dynamic AMR: 256^3 base + 2 ratio-2 levels, c0-style Gaussian i
                 "subcycled RK4; regrid time included")
 
 
-def _amr_form(slh, torch, prec, y0_dense, K):
+def _amr_form(slh, torch, prec, y0_dense, K, n=AMR_N):
     """Dynamic-AMR timing: coarse steps with global regrids every AMR_EVERY
     steps.  Returns (cell-updates/s, details)."""
-    n = AMR_N
     h = slh.Hierarchy(n, DX, nghost=3, bf=AMR_BF, prec=prec, max_levels=AMR_LEVELS)
     h.init_level(0, [((0, 0, 0), (n - 1, n - 1, n - 1))])
     h.set_state(0, y0_dense.astype(h.np_dtype))
@@ -272,12 +306,20 @@ def run_ours(args, rank, world, local_rank, dist):
         build.build()
     torch.cuda.set_device(local_rank)
     n, K, W = args.cells, args.steps, args.warmup
+    peak, peak_kind = _peaks()
+    if args.profile_only == "amr":
+        # short dynamic-AMR run for profilers (base n^3, K coarse steps)
+        ya = inputs.gaussian_field(n, n / 8.0, seed=rank)
+        _amr_form(slh, torch, "f32", slh.dense_from_boxes(ya, [((0, 0, 0), (n - 1,) * 3)]), K, n=n)
+        return
+    if args.profile_only == "gw":
+        _gw_form(slh, torch, n, dist, peak, K=K)
+        return
     y0 = inputs.gaussian_field(n, n / 16.0, seed=rank)
     boxes = [((0, 0, 0), (n - 1, n - 1, n - 1))]
     dense = slh.dense_from_boxes(y0, boxes)
     del y0
     flags = slh.SLH_FUSE_TAG | slh.SLH_FUSE_ENERGY
-    peak, peak_kind = _peaks()
 
     # FP32 + Kahan (headline), with clock sampling over its timed region
     with ClockSampler(_gpu_index(local_rank)) as clk:
@@ -329,6 +371,12 @@ def run_ours(args, rank, world, local_rank, dist):
         amr = {"workload": AMR_WORKLOAD, "unit": "cell-updates/s",
                "f32": {"value": world * v32, **d32}, "f64": {"value": world * v64, **d64}}
 
+    # gravitational-wave tensor fields
+    gw = None
+    if not args.no_gw:
+        gw = _gw_form(slh, torch, GW_N, dist, peak)
+        gw["value"] *= world
+
     ms = r32["ms"]
     e2e_ms = e2e_s * 1e3
     if dist is not None:
@@ -367,6 +415,7 @@ def run_ours(args, rank, world, local_rank, dist):
         "e2e": {"value": world * cells * K / (e2e_ms / 1e3), "unit": "cell-updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4 * 8},
         "amr": amr,
+        "gw": gw,
         "gpu_launches": launches,
         "clocks": clocks,
     }
@@ -383,8 +432,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cells", type=int, default=N_CELLS, help="lattice cells per axis (default 512)")
     ap.add_argument("--no-amr", action="store_true", help="skip the dynamic-AMR line")
-    ap.add_argument("--profile-only", action="store_true",
-                    help="time only the FP32 form and print nothing (for ncu captures of a small case)")
+    ap.add_argument("--no-gw", action="store_true", help="skip the gravitational-wave tensor line")
+    ap.add_argument("--profile-only", nargs="?", const="uniform", default=None, choices=["uniform", "amr", "gw"],
+                    help="short run for ncu captures of a small case, printing nothing: the FP32 uniform form "
+                         "(default), the dynamic-AMR form (base --cells^3, --steps coarse steps) or the "
+                         "16-field lattice")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

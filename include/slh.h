@@ -82,6 +82,11 @@ typedef int32_t slh_status;
 #define SLH_FUSE_ENERGY 2u  /* stage 1 also accumulates the energy of y_n */
 #define SLH_USE_GRAPH 4u    /* slh_advance: replay a captured CUDA graph */
 
+/* Refinement criteria (slh_set_tagging); the block mask of slh_tag_blocks
+ * is the union of the enabled ones */
+#define SLH_TAG_WINDING 1u  /* string winding (the problem-specific hook of Sec. 4.2) */
+#define SLH_TAG_TEE 2u      /* truncation-error estimate (Sec. 2.2) */
+
 /* slh_fill_ghosts modes */
 #define SLH_GHOSTS 0     /* fill the psi (and u_ij) ghosts of the level's state */
 #define SLH_RESTRICT 1   /* average the level onto the next coarser one
@@ -239,12 +244,47 @@ slh_status slh_fill_ghosts(slh_ctx* ctx, int32_t lev, double alpha, int32_t inte
  * Errors: INVALID_ARG, STATE, CUDA, and latched device errors. */
 slh_status slh_tag(slh_ctx* ctx, int32_t lev, uint8_t* tags_dev, int64_t* n_tagged_host);
 
-/* Block mask for regridding from level lev: the tags of lev, grown by
- * n_error_buf cells (cube, periodic, across boxes), coarsened to blocks of
- * blocking_factor/2 cells: mask_host[(bz*nb + by)*nb + bx] = 1 when the
- * grown tag set meets block (bx,by,bz), nb = (n0*2^lev)/(blocking_factor/2).
+/* Block mask for regridding from level lev: the tags of lev (the union of
+ * the criteria enabled by slh_set_tagging: winding tags computed now, and
+ * the level's last TEE tags), grown by n_error_buf cells (cube, periodic,
+ * across boxes), coarsened to blocks of blocking_factor/2 cells:
+ * mask_host[(bz*nb + by)*nb + bx] = 1 when the grown tag set meets block
+ * (bx,by,bz), nb = (n0*2^lev)/(blocking_factor/2).
  * Synchronises.  Errors: INVALID_ARG, STATE, CUDA. */
 slh_status slh_tag_blocks(slh_ctx* ctx, int32_t lev, int32_t n_error_buf, uint8_t* mask_host);
+
+/* Refinement criteria (Sec. 2.2): criteria is a nonzero combination of
+ * SLH_TAG_WINDING and SLH_TAG_TEE (default: SLH_TAG_WINDING).  With
+ * SLH_TAG_TEE, te_crit[4] are the thresholds eps of (psi1, psi2, Pi1, Pi2)
+ * (a threshold <= 0 leaves its component out); the library keeps one tag
+ * byte per valid cell of every level (allocated here and whenever a level
+ * is defined) and fills it with the truncation-error estimate
+ *   Delta phi_cf = |phi_coarse - phi_fine|:
+ *  - level l >= 1, at every synchronisation of l with l-1 (SLH_RESTRICT,
+ *    including the ones inside slh_advance): the coarse values of l-1 just
+ *    before they are replaced against the mean of their 8 children (the
+ *    self-shadow method; FP64 comparison);
+ *  - level 0, from a shadow context: slh_shadow_init / slh_shadow_compare.
+ * A fine cell is tagged when its parent's estimate exceeds eps for some
+ * component.  Synchronises.  Errors: INVALID_ARG, NOMEM, CUDA. */
+slh_status slh_set_tagging(slh_ctx* ctx, uint32_t criteria, const double* te_crit);
+
+/* Shadow level of level 0 (Sec. 2.2): shadow is a context of the same
+ * precision and field count with n0/2 cells of spacing 2 dx0 and its level
+ * 0 defined.  slh_shadow_init writes the 2^3 mean of ctx's level 0 (every
+ * field) into the shadow's state (its previous state too, Kahan zeroed) and
+ * gives it ctx's eta.  Advance the shadow by one step of 2 dt0
+ * (slh_rk_step) while ctx advances two coarse steps, then slh_shadow_compare
+ * writes level 0's TEE tags from |shadow - mean of children|.  Both order
+ * the work of the two streams with events.
+ * Errors: INVALID_ARG, STATE, CUDA. */
+slh_status slh_shadow_init(slh_ctx* ctx, slh_ctx* shadow);
+slh_status slh_shadow_compare(slh_ctx* ctx, slh_ctx* shadow);
+
+/* Copy level lev's TEE tags (nvalid bytes, dense valid-cell layout) to dst
+ * (host if dst_is_host, which synchronises, else device).
+ * Errors: INVALID_ARG, STATE (TEE not enabled), CUDA. */
+slh_status slh_tee_tags(slh_ctx* ctx, int32_t lev, uint8_t* dst, int32_t dst_is_host);
 
 /* Host-only, deterministic regrid: dense tags over a level's whole index
  * domain dims[3] (x,y,z; uint8, x fastest) -> boxes of the next finer level

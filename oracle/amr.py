@@ -197,6 +197,7 @@ class Hierarchy:
         self.record_tags = False
         self.te_eps = None         # TEE thresholds of (psi1, psi2, Pi1, Pi2): self-shadow tags at sync
         self.te_tags = {}          # lev -> [tags per box] from the last synchronisation of lev
+        self.te_vals = {}          # lev -> [(4, nz, ny, nx) estimates on the parent cells, per box]
 
     def coarse_of(self, lev):
         return self.levels[lev - 1] if lev > 0 else None
@@ -247,6 +248,7 @@ class Hierarchy:
                 cval = Cl.gather([Cl.data], range(tee.NSCALAR), kz, ky, kx)[0]
                 te = tee.te_on_coarse(cval, fv[:tee.NSCALAR])
                 self.te_tags.setdefault(fine_lev, [None] * len(F.boxes))[b] = tee.tags_from_te(te, self.te_eps)
+                self.te_vals.setdefault(fine_lev, [None] * len(F.boxes))[b] = te
             for s in np.unique(own):
                 sel = own == s
                 slo = Cl.boxes[s][0]

@@ -32,6 +32,7 @@ SLH_FUSE_ENERGY = 2
 SLH_USE_GRAPH = 4
 SLH_GHOSTS = 0
 SLH_RESTRICT = 1
+SLH_TAG_WINDING, SLH_TAG_TEE = 1, 2
 (SLH_PROF_STAGE, SLH_PROF_GHOST, SLH_PROF_RESTRICT, SLH_PROF_DIAG, SLH_PROF_TIME,
  SLH_PROF_S1, SLH_PROF_S2, SLH_PROF_S3, SLH_PROF_S4, SLH_PROF_GW) = range(10)
 NFIELDS, NFIELDS_GW = 4, 16   # psi1, psi2, Pi1, Pi2 (+ u_xx..u_yz, v_xx..v_yz)
@@ -46,6 +47,7 @@ ABI_SYMBOLS = (
     "slh_advance", "slh_fill_ghosts", "slh_tag", "slh_tag_blocks", "slh_regrid_boxes",
     "slh_reduce_energy", "slh_sync", "slh_profile", "slh_profile_read", "slh_set_tile", "slh_autotune",
     "slh_energy_noalloc", "slh_regrid_level", "slh_selftest_wait_timeout",
+    "slh_set_tagging", "slh_shadow_init", "slh_shadow_compare", "slh_tee_tags",
 )
 
 
@@ -120,6 +122,10 @@ def lib():
         "slh_energy_noalloc": (i32, [vp, i32, i32, dbl, dbl, P(slh_eom_params), vp, vp]),
         "slh_regrid_level": (i32, [vp, i32, P(slh_box), i32, P(vp), vp, i32]),
         "slh_selftest_wait_timeout": (i32, [vp, i64]),
+        "slh_set_tagging": (i32, [vp, ctypes.c_uint32, P(dbl)]),
+        "slh_shadow_init": (i32, [vp, vp]),
+        "slh_shadow_compare": (i32, [vp, vp]),
+        "slh_tee_tags": (i32, [vp, i32, vp, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -409,6 +415,37 @@ class Hierarchy:
         """Host copy of the tags written by the last SLH_FUSE_TAG stage 1."""
         self.sync()
         return self.levels[lev]["tags"].cpu().numpy()
+
+    def set_tagging(self, winding=True, te_crit=None):
+        """Refinement criteria of slh_tag_blocks / regrid: the string winding
+        and/or the truncation-error estimate with thresholds te_crit of
+        (psi1, psi2, Pi1, Pi2) (Sec. 2.2)."""
+        crit = (SLH_TAG_WINDING if winding else 0) | (SLH_TAG_TEE if te_crit is not None else 0)
+        eps = (ctypes.c_double * 4)(*[float(v) for v in te_crit]) if te_crit is not None else None
+        _check(lib().slh_set_tagging(self.h, crit, eps))
+
+    def make_shadow(self):
+        """The shadow context of level 0 (n0/2 cells of spacing 2 dx0, one
+        box), for the level-0 truncation-error estimate."""
+        n = self.n0 // 2
+        bf = self.bf if n % self.bf == 0 else max(2, self.bf // 2)
+        sh = Hierarchy(n, 2.0 * self.dx0, nghost=self.nghost, bf=bf,
+                       prec="f64" if self.prec == SLH_F64 else "f32", max_levels=1, device=self.device,
+                       gw=self.ncomp == NFIELDS_GW)
+        sh.init_level(0, [((0, 0, 0), (self.n0 // 2 - 1,) * 3)])
+        return sh
+
+    def shadow_init(self, shadow):
+        _check(lib().slh_shadow_init(self.h, shadow.h))
+
+    def shadow_compare(self, shadow):
+        _check(lib().slh_shadow_compare(self.h, shadow.h))
+
+    def tee_tags(self, lev):
+        """Host copy of level lev's truncation-error-estimate tags (dense)."""
+        out = np.empty(self.levels[lev]["nvalid"], dtype=np.uint8)
+        _check(lib().slh_tee_tags(self.h, lev, ctypes.c_void_p(out.ctypes.data), 1))
+        return out
 
     def profile(self, enable=True, reset=True):
         _check(lib().slh_profile(self.h, int(enable), int(reset)))

@@ -21,7 +21,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libslh.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SRCS = ["api.cu", "stage.cu", "gw.cu", "ghost.cu", "diag.cu", "noalloc.cu"]
+CUDA_SRCS = ["api.cu", "stage.cu", "gw.cu", "ghost.cu", "tee.cu", "diag.cu", "noalloc.cu"]
 CXX_SRCS = ["regrid.cpp"]
 
 

@@ -2,6 +2,7 @@
 // the RK4 step of one level (Tab. "integrator", type 4), the subcycled
 // coarse step (Sec. 2.1, Fig. 2) with optional CUDA-graph replay, and the
 // synchronising diagnostics (tags, energy, regrid block mask).
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -84,11 +85,13 @@ static void free_level(Level& L) {
   cudaFree(L.d_boxes);
   cudaFree(L.d_bmap);
   cudaFree(L.d_gregions);
+  cudaFree(L.d_pieces);
   cudaFree(L.d_covered);
   cudaFree(L.d_ritems);
   cudaFree(L.d_roff);
   cudaFree(L.d_epart);
   cudaFree(L.d_tagtmp);
+  cudaFree(L.d_tee);
   L = Level();
 }
 
@@ -329,13 +332,80 @@ static void split_axis(int a, int b, int base, int step, int n, std::vector<std:
   }
 }
 
+// Pieces of the coarse patch of a prolongation region (fine cells flo..fhi
+// inclusive, unwrapped): the radius-PROLONG_RAD_MAX footprint [plo, plo+pn)
+// split at the coarse domain boundaries into periodic images, each image
+// intersected with the coarse boxes it meets (found from the coarse block
+// map).  Returns whether the pieces tile the whole footprint.
+static bool plan_patch(const Level& C, int bf, const int flo[3], const int fhi[3], std::vector<PatchPiece>* pieces) {
+  int plo[3], pn[3];
+  for (int d = 0; d < 3; ++d) {
+    plo[d] = (flo[d] >> 1) - PROLONG_RAD_MAX;
+    pn[d] = (fhi[d] >> 1) + PROLONG_RAD_MAX - plo[d] + 1;
+  }
+  const int nc = C.n_dom, nbd = C.nb_dom;
+  long long got = 0;
+  // per axis: up to three segments [a, b] of the footprint, each under one image
+  std::vector<std::pair<int, int>> seg[3];
+  for (int d = 0; d < 3; ++d) {
+    int a = plo[d];
+    const int e = plo[d] + pn[d] - 1;
+    while (a <= e) {
+      const int img = a >= 0 ? a / nc : -((-a + nc - 1) / nc);   // floor(a / nc)
+      const int b = std::min(e, (img + 1) * nc - 1);
+      seg[d].push_back({a, b});
+      a = b + 1;
+    }
+  }
+  std::vector<int> owners;
+  for (auto& sz : seg[2])
+    for (auto& sy : seg[1])
+      for (auto& sx : seg[0]) {
+        const int lo[3] = {sx.first, sy.first, sz.first}, hi[3] = {sx.second, sy.second, sz.second};
+        int wlo[3], shift[3];
+        for (int d = 0; d < 3; ++d) {
+          const int img = lo[d] >= 0 ? lo[d] / nc : -((-lo[d] + nc - 1) / nc);
+          shift[d] = img * nc;
+          wlo[d] = lo[d] - shift[d];
+        }
+        owners.clear();
+        for (int bz = wlo[2] / bf; bz <= (hi[2] - shift[2]) / bf; ++bz)
+          for (int by = wlo[1] / bf; by <= (hi[1] - shift[1]) / bf; ++by)
+            for (int bx = wlo[0] / bf; bx <= (hi[0] - shift[0]) / bf; ++bx) {
+              const int o = C.h_bmap[((size_t)bz * nbd + by) * nbd + bx];
+              if (o >= 0 && std::find(owners.begin(), owners.end(), o) == owners.end()) owners.push_back(o);
+            }
+        std::sort(owners.begin(), owners.end());
+        for (int o : owners) {
+          const slh_box& cb = C.boxes[o];
+          PatchPiece P;
+          P.cbox = o;
+          bool empty = false;
+          for (int d = 0; d < 3; ++d) {
+            const int a = std::max(wlo[d], cb.lo[d]), b = std::min(hi[d] - shift[d], cb.hi[d]);
+            if (a > b) empty = true;
+            P.src[d] = a - cb.lo[d];
+            P.dst[d] = a + shift[d] - plo[d];
+            P.ext[d] = b - a + 1;
+          }
+          if (empty) continue;
+          got += (long long)P.ext[0] * P.ext[1] * P.ext[2];
+          pieces->push_back(P);
+        }
+      }
+  return got == (long long)pn[0] * pn[1] * pn[2];
+}
+
 // Ghost regions of every box: each of the six ghost slabs is cut at the box
 // bounds, every GHOST_CHUNK cells and at the domain boundaries; each piece is
 // classified from the host block map (blocks of bf >= g cells, so a piece
-// meets few blocks).
-static slh_status plan_ghost_regions(slh_ctx* c, Level& L, std::vector<GhostRegion>* out, long long* total) {
+// meets few blocks).  For a level > 0, regions that prolong get the pieces
+// of their coarse patch.
+static slh_status plan_ghost_regions(slh_ctx* c, int lev, Level& L, std::vector<GhostRegion>* out,
+                                     std::vector<PatchPiece>* pieces, long long* total) {
   const int g = c->g, bf = c->bf, n = L.n_dom, nbd = L.nb_dom;
   out->clear();
+  pieces->clear();
   *total = 0;
   std::vector<std::pair<int, int>> sx, sy, sz;
   for (size_t b = 0; b < L.lay.boxes.size(); ++b) {
@@ -391,6 +461,18 @@ static slh_status plan_ghost_regions(slh_ctx* c, Level& L, std::vector<GhostRegi
             } else {
               R.kind = GHOST_MIXED;
             }
+            R.p0 = (int)pieces->size();
+            R.np = 0;
+            R.covered = 0;
+            if (lev > 0 && R.kind != GHOST_COPY) {
+              int flo[3], fhi[3];
+              for (int d = 0; d < 3; ++d) {
+                flo[d] = glo[d];
+                fhi[d] = ghi[d];
+              }
+              R.covered = plan_patch(c->lev[lev - 1], bf, flo, fhi, pieces) ? 1 : 0;
+              R.np = (int)pieces->size() - R.p0;
+            }
             out->push_back(R);
             *total += (long long)R.ext[0] * R.ext[1] * R.ext[2];
           }
@@ -422,11 +504,14 @@ static slh_status build_level(slh_ctx* c, int lev, Level& L, const slh_box* boxe
   // ghost shell regions, classified from the block map
   {
     std::vector<GhostRegion> regs;
+    std::vector<PatchPiece> pcs;
     long long tot = 0;
-    if ((st = plan_ghost_regions(c, L, &regs, &tot)) != SLH_OK) return st;
+    if ((st = plan_ghost_regions(c, lev, L, &regs, &pcs, &tot)) != SLH_OK) return st;
     L.ngregions = (int)regs.size();
     L.nghost_cells = tot;
+    L.npieces = (int)pcs.size();
     if ((st = upload(&L.d_gregions, regs)) != SLH_OK) return st;
+    if ((st = upload(&L.d_pieces, pcs)) != SLH_OK) return st;
   }
 
   {
@@ -463,6 +548,13 @@ static slh_status build_level(slh_ctx* c, int lev, Level& L, const slh_box* boxe
     L.nrcells = rt;
     if ((st = upload(&L.d_ritems, ri)) != SLH_OK) return st;
     if ((st = upload(&L.d_roff, roff)) != SLH_OK) return st;
+  }
+
+  // truncation-error-estimate tags
+  if (c->tag_criteria & SLH_TAG_TEE) {
+    cudaError_t e = cudaMalloc(&L.d_tee, (size_t)std::max<long long>(1, L.lay.nvalid));
+    if (e != cudaSuccess) return fail(SLH_ERR_NOMEM, "level %d: TEE tags: %s", lev, cudaGetErrorString(e));
+    SLH_CUDA(cudaMemsetAsync(L.d_tee, 0, (size_t)std::max<long long>(1, L.lay.nvalid), c->stream));
   }
 
   // energy partials
@@ -768,6 +860,8 @@ static unsigned long long graph_key(slh_ctx* c, double dt0, const slh_eom_params
   mix(&dt0, sizeof(dt0));
   mix(&p, sizeof(p));
   mix(&flags, sizeof(flags));
+  mix(&c->tag_criteria, sizeof(c->tag_criteria));
+  mix(c->te_crit, sizeof(c->te_crit));
   mix(&c->nlevels, sizeof(int));
   for (int l = 0; l < c->nlevels; ++l) {
     mix(&c->lev[l].d_boxes, sizeof(void*));
@@ -844,6 +938,7 @@ slh_status slh_advance(slh_ctx* c, double dt0, const slh_eom_params* p, uint32_t
 slh_status slh_fill_ghosts(slh_ctx* c, int32_t lev, double alpha, int32_t itype, int32_t mode) {
   if (!c) return fail(SLH_ERR_INVALID_ARG, "fill_ghosts: null ctx");
   if (lev < 0 || lev >= c->nlevels) return fail(SLH_ERR_STATE, "fill_ghosts: level %d not defined", lev);
+  if (lev >= c->stale_from) return fail(SLH_ERR_STATE, "fill_ghosts: level %d must be regridded first", c->stale_from);
   if (mode != SLH_GHOSTS && mode != SLH_RESTRICT) return fail(SLH_ERR_INVALID_ARG, "fill_ghosts: bad mode");
   if (mode == SLH_RESTRICT && lev == 0) return fail(SLH_ERR_INVALID_ARG, "fill_ghosts: level 0 has no coarser level");
   if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(SLH_ERR_INVALID_ARG, "fill_ghosts: alpha outside [0,1]");
@@ -907,6 +1002,7 @@ static slh_status diag_pass(slh_ctx* c, int lev, const slh_eom_params& p, uint8_
 slh_status slh_tag(slh_ctx* c, int32_t lev, uint8_t* tags_dev, int64_t* n_tagged) {
   if (!c || !tags_dev) return fail(SLH_ERR_INVALID_ARG, "tag: null argument");
   if (lev < 0 || lev >= c->nlevels) return fail(SLH_ERR_STATE, "tag: level %d not defined", lev);
+  if (lev >= c->stale_from) return fail(SLH_ERR_STATE, "tag: level %d must be regridded first", c->stale_from);
   // the winding tags read psi only; the cheapest stencil variant runs them
   const slh_eom_params p = {1.0, 0.0, 1, 2, 2, 4};
   int used = 0;
@@ -925,14 +1021,20 @@ slh_status slh_tag(slh_ctx* c, int32_t lev, uint8_t* tags_dev, int64_t* n_tagged
 slh_status slh_tag_blocks(slh_ctx* c, int32_t lev, int32_t nbuf, uint8_t* mask_host) {
   if (!c || !mask_host) return fail(SLH_ERR_INVALID_ARG, "tag_blocks: null argument");
   if (lev < 0 || lev >= c->nlevels) return fail(SLH_ERR_STATE, "tag_blocks: level %d not defined", lev);
+  if (lev >= c->stale_from) return fail(SLH_ERR_STATE, "tag_blocks: level %d must be regridded first", c->stale_from);
   if (nbuf < 0) return fail(SLH_ERR_INVALID_ARG, "tag_blocks: n_error_buf < 0");
   Level& L = c->lev[lev];
-  if (!L.d_tagtmp) {
-    cudaError_t e = cudaMalloc(&L.d_tagtmp, (size_t)L.lay.nvalid);
-    if (e != cudaSuccess) return fail(SLH_ERR_NOMEM, "tag_blocks: %s", cudaGetErrorString(e));
+  slh_status st;
+  const uint8_t* winding = nullptr;
+  if (c->tag_criteria & SLH_TAG_WINDING) {
+    if (!L.d_tagtmp) {
+      cudaError_t e = cudaMalloc(&L.d_tagtmp, (size_t)L.lay.nvalid);
+      if (e != cudaSuccess) return fail(SLH_ERR_NOMEM, "tag_blocks: %s", cudaGetErrorString(e));
+    }
+    if ((st = slh_tag(c, lev, L.d_tagtmp, nullptr)) != SLH_OK) return st;
+    winding = L.d_tagtmp;
   }
-  slh_status st = slh_tag(c, lev, L.d_tagtmp, nullptr);
-  if (st != SLH_OK) return st;
+  const uint8_t* tee = (c->tag_criteria & SLH_TAG_TEE) ? L.d_tee : nullptr;
   const int r = c->bf / 2;
   const int nb = L.n_dom / r;
   const size_t nmask = (size_t)nb * nb * nb;
@@ -944,9 +1046,90 @@ slh_status slh_tag_blocks(slh_ctx* c, int32_t lev, int32_t nbuf, uint8_t* mask_h
     c->blockmask_cap = nmask;
   }
   SLH_CUDA(cudaMemsetAsync(c->d_blockmask, 0, nmask, c->stream));
-  if ((st = launch_tag_blocks(c, L, L.d_tagtmp, nbuf, r, c->d_blockmask, nb)) != SLH_OK) return st;
+  if ((st = launch_tag_blocks(c, L, winding, tee, nbuf, r, c->d_blockmask, nb)) != SLH_OK) return st;
   SLH_CUDA(cudaMemcpyAsync(mask_host, c->d_blockmask, nmask, cudaMemcpyDeviceToHost, c->stream));
   return slh_sync(c);
+}
+
+slh_status slh_set_tagging(slh_ctx* c, uint32_t criteria, const double* te_crit) {
+  if (!c) return fail(SLH_ERR_INVALID_ARG, "set_tagging: null ctx");
+  if (criteria == 0 || (criteria & ~(SLH_TAG_WINDING | SLH_TAG_TEE)))
+    return fail(SLH_ERR_INVALID_ARG, "set_tagging: criteria must be a nonzero combination of SLH_TAG_WINDING and SLH_TAG_TEE");
+  if ((criteria & SLH_TAG_TEE) && !te_crit) return fail(SLH_ERR_INVALID_ARG, "set_tagging: SLH_TAG_TEE needs te_crit[4]");
+  SLH_CUDA(cudaStreamSynchronize(c->stream));
+  drop_graphs(c);   // the restriction's arguments change
+  c->tag_criteria = criteria;
+  for (int q = 0; q < 4; ++q) c->te_crit[q] = (criteria & SLH_TAG_TEE) ? te_crit[q] : 0.0;
+  if (criteria & SLH_TAG_TEE) {
+    for (int l = 0; l < c->nlevels; ++l) {
+      Level& L = c->lev[l];
+      if (L.d_tee) continue;
+      const size_t nb = (size_t)std::max<long long>(1, L.lay.nvalid);
+      cudaError_t e = cudaMalloc(&L.d_tee, nb);
+      if (e != cudaSuccess) return fail(SLH_ERR_NOMEM, "set_tagging: TEE tags: %s", cudaGetErrorString(e));
+      SLH_CUDA(cudaMemsetAsync(L.d_tee, 0, nb, c->stream));
+    }
+  }
+  return SLH_OK;
+}
+
+slh_status slh_tee_tags(slh_ctx* c, int32_t lev, uint8_t* dst, int32_t dst_is_host) {
+  if (!c || !dst) return fail(SLH_ERR_INVALID_ARG, "tee_tags: null argument");
+  if (lev < 0 || lev >= c->nlevels) return fail(SLH_ERR_STATE, "tee_tags: level %d not defined", lev);
+  Level& L = c->lev[lev];
+  if (!(c->tag_criteria & SLH_TAG_TEE) || !L.d_tee) return fail(SLH_ERR_STATE, "tee_tags: SLH_TAG_TEE is not enabled");
+  SLH_CUDA(cudaMemcpyAsync(dst, L.d_tee, (size_t)L.lay.nvalid, cudaMemcpyDefault, c->stream));
+  if (dst_is_host) return slh_sync(c);
+  return SLH_OK;
+}
+
+// shadow checks shared by init and compare
+static slh_status check_shadow(slh_ctx* c, slh_ctx* s, const char* who) {
+  if (!c || !s || c == s) return fail(SLH_ERR_INVALID_ARG, "%s: need two distinct contexts", who);
+  if (s->prec != c->prec || s->ncomp != c->ncomp)
+    return fail(SLH_ERR_INVALID_ARG, "%s: shadow precision / field count differ", who);
+  if (2 * s->n0 != c->n0 || s->dx0 != 2.0 * c->dx0)
+    return fail(SLH_ERR_INVALID_ARG, "%s: shadow must have n0/2 cells of spacing 2 dx0", who);
+  if (s->device != c->device) return fail(SLH_ERR_INVALID_ARG, "%s: shadow on another device", who);
+  if (c->nlevels < 1 || s->nlevels < 1) return fail(SLH_ERR_STATE, "%s: level 0 not defined", who);
+  return SLH_OK;
+}
+
+// make `later` wait for the work queued so far on `earlier`
+static slh_status stream_after(cudaStream_t later, cudaStream_t earlier) {
+  if (later == earlier) return SLH_OK;
+  cudaEvent_t e;
+  SLH_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaError_t r = cudaEventRecord(e, earlier);
+  if (r == cudaSuccess) r = cudaStreamWaitEvent(later, e, 0);
+  cudaEventDestroy(e);
+  SLH_CUDA(r);
+  return SLH_OK;
+}
+
+slh_status slh_shadow_init(slh_ctx* c, slh_ctx* s) {
+  slh_status st = check_shadow(c, s, "shadow_init");
+  if (st != SLH_OK) return st;
+  if ((st = stream_after(c->stream, s->stream)) != SLH_OK) return st;
+  if ((st = launch_shadow(c, s, false)) != SLH_OK) return st;
+  Level& S = s->lev[0];
+  const size_t bytes = (size_t)S.lay.total * elem_size(s);
+  SLH_CUDA(cudaMemcpyAsync(S.buf[S.role_prev], S.buf[S.role_y], bytes, cudaMemcpyDeviceToDevice, c->stream));
+  if (S.buf[SLH_BUF_C]) SLH_CUDA(cudaMemsetAsync(S.buf[SLH_BUF_C], 0, bytes, c->stream));
+  // the shadow starts at level 0's (synchronised) time
+  SLH_CUDA(cudaMemcpyAsync(s->d_time, c->d_time, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  SLH_CUDA(cudaMemcpyAsync(s->d_time + 1, c->d_time, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  return stream_after(s->stream, c->stream);
+}
+
+slh_status slh_shadow_compare(slh_ctx* c, slh_ctx* s) {
+  slh_status st = check_shadow(c, s, "shadow_compare");
+  if (st != SLH_OK) return st;
+  if (!(c->tag_criteria & SLH_TAG_TEE) || !c->lev[0].d_tee)
+    return fail(SLH_ERR_STATE, "shadow_compare: SLH_TAG_TEE is not enabled");
+  if ((st = stream_after(c->stream, s->stream)) != SLH_OK) return st;
+  if ((st = launch_shadow(c, s, true)) != SLH_OK) return st;
+  return stream_after(s->stream, c->stream);
 }
 
 slh_status slh_reduce_energy(slh_ctx* c, const slh_eom_params* p, int32_t mode, double out[5]) {
@@ -954,6 +1137,8 @@ slh_status slh_reduce_energy(slh_ctx* c, const slh_eom_params* p, int32_t mode, 
   slh_status st = check_params(p);
   if (st != SLH_OK) return st;
   if (c->nlevels < 1) return fail(SLH_ERR_STATE, "reduce_energy: no level defined");
+  if (c->stale_from < c->nlevels)
+    return fail(SLH_ERR_STATE, "reduce_energy: level %d must be regridded first", c->stale_from);
   double sums[MAX_LEVELS][4];
   int nl = c->nlevels;
   if (mode == 1) {

@@ -37,7 +37,8 @@ slh_status launch_energy_final(slh_ctx* c, const double* epart, int n, double* o
 struct TagBlockArgs {
   const BoxDev* boxes;
   int nboxes;
-  const uint8_t* tags;
+  const uint8_t* tags;    // either may be null: a cell is tagged if either tags it
+  const uint8_t* tags2;
   long long nvalid;
   int nbuf, r, nb, ndom;
   uint8_t* mask;
@@ -48,7 +49,7 @@ struct TagBlockArgs {
 __global__ void tag_blocks_kernel(const TagBlockArgs A) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < A.nvalid; t += stride) {
-    if (!A.tags[t]) continue;
+    if (!((A.tags != nullptr && A.tags[t]) || (A.tags2 != nullptr && A.tags2[t]))) continue;
     int lo = 0, hi = A.nboxes - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
@@ -74,12 +75,13 @@ __global__ void tag_blocks_kernel(const TagBlockArgs A) {
   }
 }
 
-slh_status launch_tag_blocks(slh_ctx* c, Level& L, const uint8_t* tags, int nbuf, int r,
+slh_status launch_tag_blocks(slh_ctx* c, Level& L, const uint8_t* tags, const uint8_t* tags2, int nbuf, int r,
                              uint8_t* mask, int nb) {
   TagBlockArgs A;
   A.boxes = L.d_boxes;
   A.nboxes = (int)L.boxes.size();
   A.tags = tags;
+  A.tags2 = tags2;
   A.nvalid = L.lay.nvalid;
   A.nbuf = nbuf;
   A.r = r;

@@ -12,6 +12,22 @@ __device__ __forceinline__ int wrapi(int v, int n) {
   return v < 0 ? v + n : v;
 }
 
+// (i, j, k) of the flat index t in an e0 x e1 x ... box with quotients by
+// float reciprocals: t = q d + r gives (t + 1/2)/d in [q + 1/(2d), q + 1 -
+// 1/(2d)], and the rounding of the product stays below 1/(2d) while t d <
+// 2^22, which region, piece and patch indexes (<= 32*32*4) satisfy.
+struct Split3 {
+  int e0, e01;
+  float r0, r01;
+  __device__ __forceinline__ Split3(int a, int b) : e0(a), e01(a * b), r0(1.0f / (float)a), r01(1.0f / (float)(a * b)) {}
+  __device__ __forceinline__ void operator()(int t, int& i, int& j, int& k) const {
+    k = (int)(((float)t + 0.5f) * r01);
+    const int rem = t - k * e01;
+    j = (int)(((float)rem + 0.5f) * r0);
+    i = rem - j * e0;
+  }
+};
+
 __device__ __forceinline__ long long cell_index(const BoxDev& B, int gl, int x, int y, int z) {
   // valid-relative (x, y, z), may lie in the ghost shell
   return B.off + ((long long)(z + gl) * B.pny + (y + gl)) * B.pitch + (x + XPAD);
@@ -47,9 +63,11 @@ __device__ __forceinline__ double pw(int itype, int child, int off) {
 // Ghost fill by regions (see GhostRegion): copy regions are plain strided
 // copies; prolongation regions first gather the coarser level's cells under
 // the region's stencil footprint, time-interpolated, into shared memory (one
-// box lookup per coarse cell instead of one per stencil point), then every
-// fine ghost cell sums its (2r+1)^3 tensor-product stencil from shared memory
-// in the order z (outer), y, x (inner); mixed regions decide cell by cell.
+// box lookup per coarse cell instead of one per stencil point), then one
+// thread per coarse cell under the region evaluates the (2r+1)^3
+// tensor-product stencil of its 8 children at once, as separable partial
+// sums along x, then y, then z (each patch value read once per coarse cell
+// instead of once per child); mixed regions decide cell by cell.
 constexpr int PATCH_MAX = 21 * 21 * 7;   // coarse cells under a 32 x 32 x g region (r <= 2, g <= 4)
 
 template <typename T>
@@ -57,6 +75,7 @@ struct GhostArgs {
   const BoxDev* boxes;
   const GhostRegion* regions;
   int nregions;
+  const PatchPiece* pieces;
   T* y;
   int gl;
   const int* bmap;
@@ -77,13 +96,12 @@ struct GhostArgs {
 __device__ __forceinline__ int pair_comp(int q) { return q == 0 ? 0 : GW_U0 + 2 * (q - 1); }
 
 template <typename T, int RAD>
-__global__ void __launch_bounds__(256) ghost_region_kernel(const GhostArgs<T> A) {
+__global__ void __launch_bounds__(256, 3) ghost_region_kernel(const GhostArgs<T> A) {
   // [2][pz][py][px]: time-interpolated psi1, psi2 in the field precision
   // (the stencil weights are dyadic rationals, exact in FP32 and FP64)
   extern __shared__ __align__(16) unsigned char patch_raw[];
   T* patch = reinterpret_cast<T*>(patch_raw);
   const int tid = threadIdx.x, nt = blockDim.x;
-  constexpr int rad = RAD;
   const T al = (T)A.alpha, bl = (T)1 - (T)A.alpha;
   for (int r = blockIdx.x; r < A.nregions; r += gridDim.x) {
     const GhostRegion R = A.regions[r];
@@ -91,8 +109,10 @@ __global__ void __launch_bounds__(256) ghost_region_kernel(const GhostArgs<T> A)
     const int ncell = R.ext[0] * R.ext[1] * R.ext[2];
     if (R.kind == GHOST_COPY) {
       const BoxDev S = A.boxes[R.src];
+      const Split3 sp(R.ext[0], R.ext[1]);
       for (int t = tid; t < ncell; t += nt) {
-        const int i = t % R.ext[0], j = (t / R.ext[0]) % R.ext[1], k = t / (R.ext[0] * R.ext[1]);
+        int i, j, k;
+        sp(t, i, j, k);
         const int rx = R.lo[0] + i, ry = R.lo[1] + j, rz = R.lo[2] + k;
         const long long dst = cell_index(B, A.gl, rx, ry, rz);
         const long long src = cell_index(S, A.gl, rx + R.d[0], ry + R.d[1], rz + R.d[2]);
@@ -104,21 +124,42 @@ __global__ void __launch_bounds__(256) ghost_region_kernel(const GhostArgs<T> A)
       }
       continue;   // uniform over the CTA: no shared memory used
     }
-    // coarse footprint of the region's stencils (unwrapped coarse coordinates)
+    // coarse footprint of the widest stencil (unwrapped coarse coordinates);
+    // narrower stencils use part of it
     int plo[3], pn[3];
     for (int d = 0; d < 3; ++d) {
       const int flo = B.lo[d] + R.lo[d], fhi = flo + R.ext[d] - 1;
-      plo[d] = (flo >> 1) - rad;
-      pn[d] = (fhi >> 1) + rad - plo[d] + 1;
+      plo[d] = (flo >> 1) - PROLONG_RAD_MAX;
+      pn[d] = (fhi >> 1) + PROLONG_RAD_MAX - plo[d] + 1;
     }
     const int np = pn[0] * pn[1] * pn[2];
     const bool have_coarse = A.cboxes != nullptr && np <= PATCH_MAX;
     for (int q = 0; q < A.npairs; ++q) {
       const int c0 = pair_comp(q);
-      if (have_coarse) {
+      if (have_coarse && R.covered) {
+        // planned gather: strided copies of the pieces, no lookups
+        for (int pi = R.p0; pi < R.p0 + R.np; ++pi) {
+          const PatchPiece P = A.pieces[pi];
+          const BoxDev C = A.cboxes[P.cbox];
+          const int ne = P.ext[0] * P.ext[1] * P.ext[2];
+          const Split3 sp(P.ext[0], P.ext[1]);
+          for (int t = tid; t < ne; t += nt) {
+            int i, j, k;
+            sp(t, i, j, k);
+            const long long ci = cell_index(C, A.gl, P.src[0] + i, P.src[1] + j, P.src[2] + k) + c0 * C.cs;
+            const int pt = ((P.dst[2] + k) * pn[1] + (P.dst[1] + j)) * pn[0] + (P.dst[0] + i);
+            patch[pt] = bl * A.cold[ci] + al * A.cnew[ci];
+            patch[np + pt] = bl * A.cold[ci + C.cs] + al * A.cnew[ci + C.cs];
+          }
+        }
+      } else if (have_coarse) {
+        // footprint not tiled by the coarse level (a nesting violation, or a
+        // level built without a plan): per-cell lookup, NaN where uncovered
+        const Split3 sp(pn[0], pn[1]);
 #pragma unroll 4
         for (int t = tid; t < np; t += nt) {
-          const int i = t % pn[0], j = (t / pn[0]) % pn[1], k = t / (pn[0] * pn[1]);
+          int i, j, k;
+          sp(t, i, j, k);
           const int qx = wrapi(plo[0] + i, A.cndom), qy = wrapi(plo[1] + j, A.cndom), qz = wrapi(plo[2] + k, A.cndom);
           const int cown = A.cbmap[((long long)(qz >> A.bshift) * A.cnbd + (qy >> A.bshift)) * A.cnbd + (qx >> A.bshift)];
           T v0 = (T)__longlong_as_double(0x7ff8000000000000ll), v1 = v0;   // NaN: not covered
@@ -133,57 +174,91 @@ __global__ void __launch_bounds__(256) ghost_region_kernel(const GhostArgs<T> A)
         }
       }
       __syncthreads();
-      for (int t = tid; t < ncell; t += nt) {
-        const int i = t % R.ext[0], j = (t / R.ext[0]) % R.ext[1], k = t / (R.ext[0] * R.ext[1]);
-        const int rx = R.lo[0] + i, ry = R.lo[1] + j, rz = R.lo[2] + k;
-        const long long dst = cell_index(B, A.gl, rx, ry, rz) + c0 * B.cs;
-        const int gx = B.lo[0] + rx, gy = B.lo[1] + ry, gz = B.lo[2] + rz;   // unwrapped fine coordinates
-        if (R.kind == GHOST_MIXED) {
-          const int wx = wrapi(gx, A.ndom), wy = wrapi(gy, A.ndom), wz = wrapi(gz, A.ndom);
-          const int own = A.bmap[((long long)(wz >> A.bshift) * A.nbd + (wy >> A.bshift)) * A.nbd + (wx >> A.bshift)];
-          if (own >= 0) {
-            const BoxDev Sb = A.boxes[own];
-            const long long src = cell_index(Sb, A.gl, wx - Sb.lo[0], wy - Sb.lo[1], wz - Sb.lo[2]) + c0 * Sb.cs;
-            A.y[dst] = A.y[src];
-            A.y[dst + B.cs] = A.y[src + Sb.cs];
-            continue;
+      // one task per coarse cell under the region: its stencil is read from
+      // the patch once and all 8 children follow by separable partial sums
+      // (x, then y, then z); children outside the region are not stored
+      int clo[3], cn[3], flo[3], fhi[3];
+      for (int d = 0; d < 3; ++d) {
+        flo[d] = B.lo[d] + R.lo[d];
+        fhi[d] = flo[d] + R.ext[d] - 1;
+        clo[d] = flo[d] >> 1;
+        cn[d] = (fhi[d] >> 1) - clo[d] + 1;
+      }
+      const int ntask = cn[0] * cn[1] * cn[2];
+      const Split3 sp(cn[0], cn[1]);
+      T w[2][2 * RAD + 1];   // 1D weights of child 0 and child 1
+#pragma unroll
+      for (int o = -RAD; o <= RAD; ++o) {
+        w[0][o + RAD] = (T)pw(A.itype, 0, o);
+        w[1][o + RAD] = (T)pw(A.itype, 1, o);
+      }
+      for (int t = tid; t < ntask; t += nt) {
+        int ti, tj, tk;
+        sp(t, ti, tj, tk);
+        const int Px = clo[0] + ti, Py = clo[1] + tj, Pz = clo[2] + tk;
+        T out[2][2][2][2];   // [field][cz][cy][cx]
+        if (have_coarse) {
+#pragma unroll
+          for (int f = 0; f < 2; ++f)
+#pragma unroll
+            for (int a = 0; a < 8; ++a) out[f][a >> 2][(a >> 1) & 1][a & 1] = 0;
+          const int base = ((Pz - RAD - plo[2]) * pn[1] + (Py - RAD - plo[1])) * pn[0] + (Px - RAD - plo[0]);
+#pragma unroll
+          for (int oz = 0; oz <= 2 * RAD; ++oz) {
+            T ay[2][2][2] = {};   // [field][cy][cx]
+#pragma unroll
+            for (int oy = 0; oy <= 2 * RAD; ++oy) {
+              const int rowb = base + (oz * pn[1] + oy) * pn[0];
+              T sx[2][2] = {};    // [field][cx]
+#pragma unroll
+              for (int ox = 0; ox <= 2 * RAD; ++ox) {
+                const T v0 = patch[rowb + ox], v1 = patch[np + rowb + ox];
+                sx[0][0] += w[0][ox] * v0;
+                sx[0][1] += w[1][ox] * v0;
+                sx[1][0] += w[0][ox] * v1;
+                sx[1][1] += w[1][ox] * v1;
+              }
+#pragma unroll
+              for (int f = 0; f < 2; ++f)
+#pragma unroll
+                for (int cy = 0; cy < 2; ++cy) {
+                  ay[f][cy][0] += w[cy][oy] * sx[f][0];
+                  ay[f][cy][1] += w[cy][oy] * sx[f][1];
+                }
+            }
+#pragma unroll
+            for (int f = 0; f < 2; ++f)
+#pragma unroll
+              for (int a = 0; a < 8; ++a)
+                out[f][a >> 2][(a >> 1) & 1][a & 1] += w[a >> 2][oz] * ay[f][(a >> 1) & 1][a & 1];
           }
         }
-        if (!have_coarse) {
-          atomicCAS(A.err, 0, DERR_NESTING);
-          continue;
-        }
-        const int Px = gx >> 1, Py = gy >> 1, Pz = gz >> 1;
-        const int cx = gx & 1, cy = gy & 1, cz = gz & 1;
-        T wx[2 * RAD + 1], wy[2 * RAD + 1], wz[2 * RAD + 1];
 #pragma unroll
-        for (int o = -RAD; o <= RAD; ++o) {
-          wx[o + RAD] = (T)pw(A.itype, cx, o);
-          wy[o + RAD] = (T)pw(A.itype, cy, o);
-          wz[o + RAD] = (T)pw(A.itype, cz, o);
-        }
-        T acc0 = 0, acc1 = 0;
-        bool bad = false;
-        const int base = ((Pz - RAD - plo[2]) * pn[1] + (Py - RAD - plo[1])) * pn[0] + (Px - RAD - plo[0]);
-#pragma unroll
-        for (int oz = 0; oz <= 2 * RAD; ++oz) {
-#pragma unroll
-          for (int oy = 0; oy <= 2 * RAD; ++oy) {
-            const T wzy = wz[oz] * wy[oy];
-            const int rowb = base + (oz * pn[1] + oy) * pn[0];
-#pragma unroll
-            for (int ox = 0; ox <= 2 * RAD; ++ox) {
-              const T v0 = patch[rowb + ox], v1 = patch[np + rowb + ox];
-              bad |= (v0 != v0);
-              const T wgt = wzy * wx[ox];
-              acc0 += wgt * v0;
-              acc1 += wgt * v1;
+        for (int a = 0; a < 8; ++a) {
+          const int cz = a >> 2, cy = (a >> 1) & 1, cx = a & 1;
+          const int gx = 2 * Px + cx, gy = 2 * Py + cy, gz = 2 * Pz + cz;   // unwrapped fine coordinates
+          if (gx < flo[0] || gx > fhi[0] || gy < flo[1] || gy > fhi[1] || gz < flo[2] || gz > fhi[2]) continue;
+          const long long dst = cell_index(B, A.gl, gx - B.lo[0], gy - B.lo[1], gz - B.lo[2]) + c0 * B.cs;
+          if (R.kind == GHOST_MIXED) {
+            const int wx = wrapi(gx, A.ndom), wy = wrapi(gy, A.ndom), wz = wrapi(gz, A.ndom);
+            const int own = A.bmap[((long long)(wz >> A.bshift) * A.nbd + (wy >> A.bshift)) * A.nbd + (wx >> A.bshift)];
+            if (own >= 0) {
+              const BoxDev Sb = A.boxes[own];
+              const long long src = cell_index(Sb, A.gl, wx - Sb.lo[0], wy - Sb.lo[1], wz - Sb.lo[2]) + c0 * Sb.cs;
+              A.y[dst] = A.y[src];
+              A.y[dst + B.cs] = A.y[src + Sb.cs];
+              continue;
             }
           }
+          if (!have_coarse) {
+            atomicCAS(A.err, 0, DERR_NESTING);
+            continue;
+          }
+          const T v0 = out[0][cz][cy][cx], v1 = out[1][cz][cy][cx];
+          if (v0 != v0) atomicCAS(A.err, 0, DERR_NESTING);   // the stencil met an uncovered (NaN) coarse cell
+          A.y[dst] = v0;
+          A.y[dst + B.cs] = v1;
         }
-        if (bad) atomicCAS(A.err, 0, DERR_NESTING);
-        A.y[dst] = acc0;
-        A.y[dst + B.cs] = acc1;
       }
       __syncthreads();   // the patch is reused by the next pair or region
     }
@@ -198,6 +273,7 @@ static slh_status ghosts_t(slh_ctx* c, int lev, int role, double alpha, int ityp
   A.boxes = L.d_boxes;
   A.regions = L.d_gregions;
   A.nregions = L.ngregions;
+  A.pieces = L.d_pieces;
   A.y = static_cast<T*>(L.buf[role]);
   A.gl = c->g;
   A.bmap = L.d_bmap;
@@ -232,8 +308,10 @@ static slh_status ghosts_t(slh_ctx* c, int lev, int role, double alpha, int ityp
     cudaFuncSetAttribute(ghost_region_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     attr = true;
   }
+  // many more CTAs than resident slots: prolongation and copy regions cost
+  // very different amounts, and the block scheduler evens them out
   long long blocks = L.ngregions;
-  const long long cap = (long long)c->num_sms * 4;
+  const long long cap = (long long)c->num_sms * 16;
   if (blocks > cap) blocks = cap;
   if (itype == 4) ghost_region_kernel<T, 2><<<(int)blocks, 256, smem, c->stream>>>(A);
   else if (itype == 2) ghost_region_kernel<T, 1><<<(int)blocks, 256, smem, c->stream>>>(A);
@@ -250,7 +328,10 @@ slh_status launch_ghosts(slh_ctx* c, int lev, int role, double alpha, int itype)
 }
 
 // ---------------------------------------------------------------------------
-// restriction: coarse cell = mean of its 8 children (FP64 sum, order x, y, z)
+// restriction: coarse cell = mean of its 8 children (FP64 sum, order x, y, z);
+// with the truncation-error estimate enabled (Sec. 2.2, self-shadow), the
+// coarse scalar values just before they are replaced are compared with the
+// means and the 8 children's TEE tags written
 
 template <typename T>
 struct RestrictArgs {
@@ -266,6 +347,8 @@ struct RestrictArgs {
   int cbshift, cnbd;
   int gl;
   int ncomp;
+  uint8_t* tee;      // fine level's TEE tags (null: no estimate)
+  double eps[4];     // thresholds of psi1, psi2, Pi1, Pi2 (<= 0: left out)
   int* err;
 };
 
@@ -294,6 +377,7 @@ __global__ void restrict_kernel(const RestrictArgs<T> A) {
     const long long dsti = cell_index(C, A.gl, gx - C.lo[0], gy - C.lo[1], gz - C.lo[2]);
     const long long f000 = cell_index(F, A.gl, 2 * i, 2 * j, 2 * k);
     const long long sy = F.pitch, sz = (long long)F.pny * F.pitch;
+    bool hit = false;
     for (int c = 0; c < A.ncomp; ++c) {
       const T* f = A.fy + f000 + c * F.cs;
       double s = (double)f[0];
@@ -304,7 +388,17 @@ __global__ void restrict_kernel(const RestrictArgs<T> A) {
       s += (double)f[sz + 1];
       s += (double)f[sz + sy];
       s += (double)f[sz + sy + 1];
-      A.cy[dsti + c * C.cs] = (T)(s * 0.125);
+      s *= 0.125;
+      if (A.tee != nullptr && c < 4 && A.eps[c] > 0.0) hit |= fabs((double)A.cy[dsti + c * C.cs] - s) > A.eps[c];
+      A.cy[dsti + c * C.cs] = (T)s;
+    }
+    if (A.tee != nullptr) {
+      const uint8_t tv = hit ? 1 : 0;
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int fx = 2 * i + (a & 1), fy = 2 * j + ((a >> 1) & 1), fz = 2 * k + (a >> 2);
+        A.tee[F.voff + ((long long)fz * F.n[1] + fy) * F.n[0] + fx] = tv;
+      }
     }
   }
 }
@@ -330,6 +424,8 @@ static slh_status restrict_t(slh_ctx* c, int fl) {
   A.cnbd = C.nb_dom;
   A.gl = c->g;
   A.ncomp = c->ncomp;
+  A.tee = (c->tag_criteria & SLH_TAG_TEE) ? F.d_tee : nullptr;
+  for (int q = 0; q < 4; ++q) A.eps[q] = c->te_crit[q];
   A.err = c->d_err;
   const int threads = 256;
   long long blocks = (F.nrcells + threads - 1) / threads;

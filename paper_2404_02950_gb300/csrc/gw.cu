@@ -42,7 +42,7 @@ __device__ __forceinline__ constexpr int pair_i(int k) { return k < 3 ? k : (k =
 __device__ __forceinline__ constexpr int pair_j(int k) { return k < 3 ? k : (k == 3 ? 1 : 2); }
 
 template <typename T, int G>
-__global__ void __launch_bounds__(GW_TX * GW_TY) gw_stage_kernel(const GwArgs<T> A) {
+__global__ void __launch_bounds__(GW_TX * GW_TY, sizeof(T) == 4 ? 4 : 3) gw_stage_kernel(const GwArgs<T> A) {
   const int4 it = A.items[blockIdx.x];
   const BoxDev B = A.boxes[it.x];
   const int x = it.y + threadIdx.x, y = it.z + threadIdx.y;
@@ -53,10 +53,29 @@ __global__ void __launch_bounds__(GW_TX * GW_TY) gw_stage_kernel(const GwArgs<T>
   const T ha = (T)A.ha, hb = (T)A.hb, idx = (T)A.inv_dx, idx2 = (T)A.inv_dx2;
   const long long sy = B.pitch, sz = (long long)B.pitch * B.pny, cs = B.cs;
   const long long st[3] = {1, sy, sz};
+  // the buffers of one launch never overlap: every pointer is restricted so
+  // that the loads of later components may be issued before earlier stores
   const T* __restrict__ in = A.in;
+  const T* __restrict__ yn = A.yn;
+  T* __restrict__ dd = A.d;
+  T* __restrict__ out = A.out;
+  T* __restrict__ cc = A.cc;
+  const int stage = A.stage;
   long long e = B.off + ((long long)(it.w + A.gl) * B.pny + (y + A.gl)) * B.pitch + x + XPAD;
+#pragma unroll 1
   for (int z = it.w; z < z1; ++z, e += sz) {
-    // gradients of psi1, psi2
+    // gradients of psi1, psi2: all 12 G operands loaded first
+    T n1[3][2 * G], n2[3][2 * G];
+#pragma unroll
+    for (int dir = 0; dir < 3; ++dir)
+#pragma unroll
+      for (int m = 1; m <= G; ++m) {
+        const long long o = m * st[dir];
+        n1[dir][2 * m - 2] = __ldg(in + e + o);
+        n1[dir][2 * m - 1] = __ldg(in + e - o);
+        n2[dir][2 * m - 2] = __ldg(in + e + cs + o);
+        n2[dir][2 * m - 1] = __ldg(in + e + cs - o);
+      }
     T g1[3], g2[3];
 #pragma unroll
     for (int dir = 0; dir < 3; ++dir) {
@@ -64,18 +83,40 @@ __global__ void __launch_bounds__(GW_TX * GW_TY) gw_stage_kernel(const GwArgs<T>
 #pragma unroll
       for (int m = 1; m <= G; ++m) {
         const T w = (T)grad_w<G>(m);
-        const long long o = m * st[dir];
-        a1 += w * (__ldg(in + e + o) - __ldg(in + e - o));
-        a2 += w * (__ldg(in + e + cs + o) - __ldg(in + e + cs - o));
+        a1 += w * (n1[dir][2 * m - 2] - n1[dir][2 * m - 1]);
+        a2 += w * (n2[dir][2 * m - 2] - n2[dir][2 * m - 1]);
       }
       g1[dir] = a1 * idx;
       g2[dir] = a2 * idx;
     }
-#pragma unroll
+    // one component at a time for the 7-point stencil (unrolled, its loads
+    // would all be hoisted and overflow the register budget)
+#pragma unroll (G == 1 ? 1 : 6)
     for (int k = 0; k < 6; ++k) {
       const long long eu = e + (GW_U0 + k) * cs, ev = e + (GW_V0 + k) * cs;
       const T* f = in + eu;
+      // operands of this component
+      T nb[3][2 * G];
+#pragma unroll
+      for (int dir = 0; dir < 3; ++dir)
+#pragma unroll
+        for (int m = 1; m <= G; ++m) {
+          nb[dir][2 * m - 2] = __ldg(f + m * st[dir]);
+          nb[dir][2 * m - 1] = __ldg(f - m * st[dir]);
+        }
       const T u0 = __ldg(f);
+      const T v = __ldg(in + ev);
+      T yu = 0, yv = 0, du = 0, dv = 0, cu = 0, cv = 0;
+      if (stage >= 2) {
+        yu = __ldg(yn + eu);
+        yv = __ldg(yn + ev);
+        du = dd[eu];
+        dv = dd[ev];
+      }
+      if (stage == 4 && cc != nullptr) {
+        cu = cc[eu];
+        cv = cc[ev];
+      }
       T lap;
       if (sizeof(T) == 8) {
         // textbook form, as the scalar FP64 stage
@@ -83,8 +124,8 @@ __global__ void __launch_bounds__(GW_TX * GW_TY) gw_stage_kernel(const GwArgs<T>
 #pragma unroll
         for (int m = 1; m <= G; ++m) {
           const T w = (T)lap_w<G>(m);
-          a += w * (((__ldg(f + m) + __ldg(f - m)) + (__ldg(f + m * sy) + __ldg(f - m * sy))) +
-                    (__ldg(f + m * sz) + __ldg(f - m * sz)));
+          a += w * (((nb[0][2 * m - 2] + nb[0][2 * m - 1]) + (nb[1][2 * m - 2] + nb[1][2 * m - 1])) +
+                    (nb[2][2 * m - 2] + nb[2][2 * m - 1]));
         }
         lap = a * idx2;
       } else {
@@ -93,37 +134,38 @@ __global__ void __launch_bounds__(GW_TX * GW_TY) gw_stage_kernel(const GwArgs<T>
 #pragma unroll
         for (int m = 1; m <= G; ++m) {
           const T w = (T)lap_w<G>(m);
-          a += w * ((((__ldg(f + m) - u0) + (__ldg(f - m) - u0)) + ((__ldg(f + m * sy) - u0) + (__ldg(f - m * sy) - u0))) +
-                    ((__ldg(f + m * sz) - u0) + (__ldg(f - m * sz) - u0)));
+          a += w * ((((nb[0][2 * m - 2] - u0) + (nb[0][2 * m - 1] - u0)) +
+                     ((nb[1][2 * m - 2] - u0) + (nb[1][2 * m - 1] - u0))) +
+                    ((nb[2][2 * m - 2] - u0) + (nb[2][2 * m - 1] - u0)));
         }
         lap = a * idx2;
       }
       const int i = pair_i(k), j = pair_j(k);
-      const T src = (T)2 * (g1[i] * g1[j] + g2[i] * g2[j]);
-      const T v = __ldg(in + ev);
+      const T g1i = i == 0 ? g1[0] : (i == 1 ? g1[1] : g1[2]), g1j = j == 0 ? g1[0] : (j == 1 ? g1[1] : g1[2]);
+      const T g2i = i == 0 ? g2[0] : (i == 1 ? g2[1] : g2[2]), g2j = j == 0 ? g2[0] : (j == 1 ? g2[1] : g2[2]);
+      const T src = (T)2 * (g1i * g1j + g2i * g2j);
       const T ku = v;
       const T kv = ((-c_fric) * v + lap) + src;
-      if (A.stage == 1) {
-        A.out[eu] = u0 + ha * ku;
-        A.out[ev] = v + ha * kv;
-        A.d[eu] = hb * ku;
-        A.d[ev] = hb * kv;
-      } else if (A.stage == 2 || A.stage == 3) {
-        A.out[eu] = __ldg(A.yn + eu) + ha * ku;
-        A.out[ev] = __ldg(A.yn + ev) + ha * kv;
-        A.d[eu] = A.d[eu] + hb * ku;
-        A.d[ev] = A.d[ev] + hb * kv;
+      if (stage == 1) {
+        out[eu] = u0 + ha * ku;
+        out[ev] = v + ha * kv;
+        dd[eu] = hb * ku;
+        dd[ev] = hb * kv;
+      } else if (stage == 2 || stage == 3) {
+        out[eu] = yu + ha * ku;
+        out[ev] = yv + ha * kv;
+        dd[eu] = du + hb * ku;
+        dd[ev] = dv + hb * kv;
       } else {
-        const T yu = __ldg(A.yn + eu), yv = __ldg(A.yn + ev);
-        const T iu = A.d[eu] + hb * ku, iv = A.d[ev] + hb * kv;
-        if (A.cc) {
+        const T iu = du + hb * ku, iv = dv + hb * kv;
+        if (cc != nullptr) {
           // compensated sum y + inc, the rounding error carried in C
           T w, sm;
-          w = iu - A.cc[eu]; sm = yu + w; A.cc[eu] = (sm - yu) - w; A.out[eu] = sm;
-          w = iv - A.cc[ev]; sm = yv + w; A.cc[ev] = (sm - yv) - w; A.out[ev] = sm;
+          w = iu - cu; sm = yu + w; cc[eu] = (sm - yu) - w; out[eu] = sm;
+          w = iv - cv; sm = yv + w; cc[ev] = (sm - yv) - w; out[ev] = sm;
         } else {
-          A.out[eu] = yu + iu;
-          A.out[ev] = yv + iv;
+          out[eu] = yu + iu;
+          out[ev] = yv + iv;
         }
       }
     }

@@ -43,6 +43,7 @@ constexpr int GHOST_COPY = 0;
 constexpr int GHOST_PROLONG = 1;
 constexpr int GHOST_MIXED = 2;
 constexpr int GHOST_CHUNK = 32;
+constexpr int PROLONG_RAD_MAX = 2;   // widest prolongation stencil (type 4)
 struct GhostRegion {
   int box;
   int lo[3];
@@ -50,6 +51,19 @@ struct GhostRegion {
   int kind;
   int src;
   int d[3];
+  // prolongation / mixed regions of a level > 0: the coarse patch (the
+  // radius-2 stencil footprint of the region) as pieces [p0, p0+np), each in
+  // one coarse box under one periodic image; covered = 1 iff they tile it
+  int p0, np, covered;
+};
+
+// One rectangular piece of a region's coarse patch: ext cells starting at
+// valid-relative cell src of coarse box cbox go to patch cell dst.
+struct PatchPiece {
+  int cbox;
+  int src[3];
+  int dst[3];
+  int ext[3];
 };
 
 // Restriction work: one fine box, its coarse region.
@@ -96,6 +110,8 @@ struct Level {
   int nb_dom = 0;
   GhostRegion* d_gregions = nullptr;
   int ngregions = 0;
+  PatchPiece* d_pieces = nullptr;
+  int npieces = 0;
   long long nghost_cells = 0;
   Tile tile;                     // stage work items for the chosen tile variant
   int4* d_gw_items = nullptr;    // GW stage work items (box, x0, y0, z0)
@@ -111,6 +127,7 @@ struct Level {
   int epart_cap = 0;
   int fused_energy_ctas = 0;     // CTAs of the last fused-energy stage 1
   uint8_t* d_tagtmp = nullptr;   // internal tags for slh_tag_blocks
+  uint8_t* d_tee = nullptr;      // truncation-error-estimate tags (per valid cell)
 };
 
 struct ProfRec {
@@ -152,6 +169,8 @@ struct slh_ctx {
   int graph_parity = 0;
   int stale_from = slh::MAX_LEVELS;   // levels >= this must be regridded before stepping
   int regrid_itype = 4;
+  uint32_t tag_criteria = SLH_TAG_WINDING;
+  double te_crit[4] = {0.0, 0.0, 0.0, 0.0};
 };
 
 namespace slh {
@@ -198,8 +217,9 @@ constexpr int GW_TX = 32, GW_TY = 8, GW_ZLEN = 32;
 slh_status launch_ghosts(slh_ctx* c, int lev, int role, double alpha, int itype);
 slh_status launch_restrict(slh_ctx* c, int fine_lev);
 slh_status launch_energy_final(slh_ctx* c, const double* epart, int n, double* out4);
-slh_status launch_tag_blocks(slh_ctx* c, Level& L, const uint8_t* tags, int nbuf, int r,
+slh_status launch_tag_blocks(slh_ctx* c, Level& L, const uint8_t* tags, const uint8_t* tags2, int nbuf, int r,
                              uint8_t* mask, int nb);
+slh_status launch_shadow(slh_ctx* c, slh_ctx* shadow, bool compare);
 slh_status launch_time_begin(slh_ctx* c, int lev, int sub, double dt_l);
 slh_status launch_regrid_fill(slh_ctx* c, int lev, Level& fresh, Level* old);
 

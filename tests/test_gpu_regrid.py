@@ -118,6 +118,12 @@ def test_regrid_errors_and_removal():
     with pytest.raises(slh.SlhError) as e:
         h.advance(DT0, slh.EOMParams(order=4))
     assert e.value.code == -7
+    # its ghost plan refers to the old level-1 boxes: no ghost-filling call runs
+    for call in (lambda: h.fill_ghosts(2), lambda: h.tag(2), lambda: h.tag_blocks(2, 1),
+                 lambda: h.reduce_energy(slh.EOMParams(order=4))):
+        with pytest.raises(slh.SlhError) as e:
+            call()
+        assert e.value.code == -7
     h.regrid_level(2, [])                                     # remove it
     h.advance(DT0, slh.EOMParams(order=4))
     assert sorted(h.levels) == [0, 1]

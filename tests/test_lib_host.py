@@ -141,3 +141,21 @@ def test_create_rejects_bad_field_count():
     h = ctypes.c_void_p()
     st = slh.lib().slh_create(ctypes.byref(h), 32, 0.5, 3, 8, slh.SLH_F64, 1, 5, None)
     assert st == -1 and b"nfields" in slh.lib().slh_last_error()
+
+
+def test_float_reciprocal_index_split_is_exact():
+    """The ghost kernel splits flat indexes t into (i, j, k) of an e0 x e1 x e2
+    box with float32 reciprocals (k = trunc((t + 1/2) * fl(1/(e0 e1))), then
+    j likewise from the remainder).  IEEE float32 arithmetic, as on the GPU,
+    gives the exact quotients for every extent up to 34 per axis (regions,
+    pieces and patches stay below 32 x 32 x 4 and 21 x 21 x 7)."""
+    f32 = np.float32
+    for e0 in range(1, 35):
+        for e1 in range(1, 35):
+            e01 = e0 * e1
+            t = np.arange(e01 * 34, dtype=np.int64)
+            k = ((t.astype(f32) + f32(0.5)) * (f32(1.0) / f32(e01))).astype(np.int64)
+            rem = t - k * e01
+            j = ((rem.astype(f32) + f32(0.5)) * (f32(1.0) / f32(e0))).astype(np.int64)
+            i = rem - j * e0
+            assert np.array_equal(k, t // e01) and np.array_equal(j, (t // e0) % e1) and np.array_equal(i, t % e0), (e0, e1)
