@@ -130,8 +130,9 @@ __device__ __forceinline__ int edge_delta(float ar, float ai, float br, float bi
   return (int)(ua && !ub && s > 0.0f) - (int)(!ua && ub && s < 0.0f);
 }
 
-// shared-memory geometry of one kernel variant
-template <typename T, int G, int TX, int TY, int P>
+// shared-memory geometry of one kernel variant (the diagnostics variant runs
+// stage 0 or 1 only, whose pointwise ring holds just the momenta)
+template <typename T, int G, int TX, int TY, int P, bool DIAG>
 struct Geo {
   static constexpr int SXL = TX + 8;
   static constexpr int SY = TY + 2 * G;
@@ -140,7 +141,7 @@ struct Geo {
   static constexpr int PSI_BYTES = 2 * SY * SXL * (int)sizeof(T);
   static constexpr int PSI_STRIDE = (PSI_BYTES + 127) / 128 * 128;
   static constexpr int PW2 = 2 * TY * TX * (int)sizeof(T);
-  static constexpr int NPW = sizeof(T) == 4 ? NPW_MAX : NPW_MAX - 2;
+  static constexpr int NPW = DIAG ? 1 : (sizeof(T) == 4 ? NPW_MAX : NPW_MAX - 2);
   static constexpr int PW_STRIDE = (NPW * PW2 + 127) / 128 * 128;
   static constexpr int BAR_BYTES = 128;
   static constexpr int SMEM = BAR_BYTES + RPSI * PSI_STRIDE + RPW * PW_STRIDE;
@@ -172,8 +173,8 @@ __device__ __forceinline__ void cursor_next(Cursor& c, const int4* items, const 
 }
 
 template <typename T, int G, int TX, int TY, int P, bool DIAG>
-__global__ void __launch_bounds__(TX* TY, 1) stage_kernel(const StageArgs<T> A) {
-  using GE = Geo<T, G, TX, TY, P>;
+__global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stage_kernel(const StageArgs<T> A) {
+  using GE = Geo<T, G, TX, TY, P, DIAG>;
   constexpr int SXL = GE::SXL, SY = GE::SY, RPSI = GE::RPSI, RPW = GE::RPW;
   constexpr int PLANE = SY * SXL;   // elements of one psi component plane
   constexpr int TXY = TX * TY;
@@ -300,17 +301,18 @@ __global__ void __launch_bounds__(TX* TY, 1) stage_kernel(const StageArgs<T> A) 
     }
     const int x = cc.x0 + tx, y = cc.y0 + ty;
     const bool active = (compute || premask) && x < B.n[0] && y < B.n[1];
-    // the 2G+1 planes z-G..z+G of the ring (plb: tile origin, pl: this thread's cell)
-    const T* plb[2 * G + 1];
-    const T* pl[2 * G + 1];
+    // the 2G+1 planes z-G..z+G of the ring as 32-bit element offsets into
+    // the shared array (plb: tile origin, plane + thread_off: this thread's cell)
+    const T* psi = reinterpret_cast<const T*>(psi_base);
+    int plb[2 * G + 1];
 #pragma unroll
     for (int k = 0; k <= 2 * G; ++k) {
       int sl = slot - 2 * G + k;
       if (sl < 0) sl += RPSI;
-      plb[k] = reinterpret_cast<const T*>(psi_base) + sl * PSI_T + G * SXL + 4;
-      pl[k] = reinterpret_cast<const T*>(psi_base) + sl * PSI_T + thread_off;
+      plb[k] = sl * PSI_T + G * SXL + 4;
     }
-    auto S = [&](int c, int dx, int dy, int dz) -> T { return pl[dz + G][c * PLANE + dy * SXL + dx]; };
+    const int tcell = thread_off - (G * SXL + 4);
+    auto S = [&](int c, int dx, int dy, int dz) -> T { return psi[plb[dz + G] + tcell + c * PLANE + dy * SXL + dx]; };
     T p1 = 0, p2 = 0, l1 = 0, l2 = 0, P1 = 0, P2 = 0, r2 = 0;
     if (compute && active) {
       const T* pwp = reinterpret_cast<const T*>(pw_base + pslot * GE::PW_STRIDE);
@@ -423,7 +425,7 @@ __global__ void __launch_bounds__(TX* TY, 1) stage_kernel(const StageArgs<T> A) 
         for (int k = 0; k < NEK; ++k) {
           if (k * TXY + tid >= NE) break;
           const int ex = e_x[k], ey = e_y[k];
-          auto SE = [&](int c, int dx, int dy, int dz) -> T { return plb[dz + G][c * PLANE + e_off[k] + dy * SXL + dx]; };
+          auto SE = [&](int c, int dx, int dy, int dz) -> T { return psi[plb[dz + G] + c * PLANE + e_off[k] + dy * SXL + dx]; };
           const T r0 = SE(0, 0, 0, 0), i0 = SE(1, 0, 0, 0);
           const T rz = SE(0, 0, 0, 1), iz = SE(1, 0, 0, 1);
           ezv[ey + 1][ex + 1] = (signed char)edge_delta(r0, i0, rz, iz);
@@ -622,7 +624,8 @@ static slh_status build_tmaps(slh_ctx* c, Level& L, int G, int TX, int TY, CUten
 
 template <typename T, int G, int TX, int TY, int P, bool DIAG>
 static slh_status launch_v(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s, int* ctas_used) {
-  using GE = Geo<T, G, TX, TY, P>;
+  using GE = Geo<T, G, TX, TY, P, DIAG>;
+  if (DIAG && s.stage >= 2) return fail(SLH_ERR_INVALID_ARG, "diagnostics variant launched for stage %d", s.stage);
   static int occ = -1;
   if (occ < 0) {
     cudaFuncSetAttribute(stage_kernel<T, G, TX, TY, P, DIAG>, cudaFuncAttributeMaxDynamicSharedMemorySize, GE::SMEM);
