@@ -31,7 +31,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import gw as ogw
-from . import tee
+from . import ssprk3, tee
 from . import interp, winding
 from .eom import EOMParams, rhs
 from .energy import energy_box
@@ -187,10 +187,13 @@ class Hierarchy:
     ``gw`` the state carries the 12 gravitational-wave fields of oracle.gw
     (16 fields; ghosts of psi and u are filled)."""
 
-    def __init__(self, levels, params: EOMParams, interp_type: int = 4, gw: bool = False):
+    def __init__(self, levels, params: EOMParams, interp_type: int = 4, gw: bool = False, integrator: int = 4):
         self.levels = levels
         self.p = params
         self.interp_type = interp_type
+        if integrator not in (4, 10):
+            raise ValueError("integrator must be 4 (classic RK4) or 10 (low-storage SSPRK3)")
+        self.integrator = integrator
         self.gw = gw
         self.ghost_comps = (0, 1, 4, 5, 6, 7, 8, 9) if gw else (0, 1)
         self.tag_log = []          # optional (lev, eta, [tags per box]) at stage 1
@@ -222,6 +225,28 @@ class Hierarchy:
         for b in range(len(Y)):
             v = L.valid(b)
             L.data[b][v] = y0[b][v] + (dt / 6.0) * (ks[0][b] + 2.0 * ks[1][b] + 2.0 * ks[2][b] + ks[3][b])
+
+    def ssprk3_level(self, lev, sub):
+        """One low-storage SSPRK3 step of level ``lev`` (oracle/ssprk3.py): stage
+        s evaluates at eta + c_s dt, c = (0, 1, 1/2), with ghosts at time
+        fraction (sub + c_s)/2 of the coarser step."""
+        L = self.levels[lev]
+        C = self.coarse_of(lev)
+        g, dt, eta = L.g, L.dt, L.eta
+        y0 = [a.copy() for a in L.data]
+        U = [a.copy() for a in y0]
+        for s in range(3):
+            alpha = (sub + ssprk3.C[s]) / 2.0
+            fill_ghosts(L, U, C, alpha, self.interp_type, comps=self.ghost_comps)
+            if s == 0 and self.record_tags:
+                self.tag_log.append((lev, eta, [winding.cell_tags_padded(a[0], a[1], g) for a in U]))
+            k = [self._rhs(U[b], g, L.dx, eta + ssprk3.C[s] * dt) for b in range(len(U))]
+            for b in range(len(U)):
+                v = L.valid(b)
+                U[b][v] = ssprk3.A[s] * y0[b][v] + ssprk3.B[s] * (U[b][v] + dt * k[b])
+        for b in range(len(U)):
+            v = L.valid(b)
+            L.data[b][v] = U[b][v]
 
     def _rhs(self, arr, g, dx, eta):
         k = rhs_box(arr, g, dx, eta, self.p)
@@ -262,7 +287,10 @@ class Hierarchy:
             L.eta = parent_eta + sub * L.dt
         eta_start = L.eta
         L.old = [a.copy() for a in L.data]
-        self.rk4_level(lev, sub)
+        if self.integrator == 4:
+            self.rk4_level(lev, sub)
+        else:
+            self.ssprk3_level(lev, sub)
         L.eta = eta_start + L.dt
         if lev + 1 < len(self.levels):
             for i in (0, 1):
@@ -306,7 +334,8 @@ class Hierarchy:
         return np.array([K, G, P, K + G + P, S])
 
 
-def make_hierarchy(n0, dx0, dt0, g, bf, level_boxes, params: EOMParams, interp_type=4, eta0=0.1, gw=False):
+def make_hierarchy(n0, dx0, dt0, g, bf, level_boxes, params: EOMParams, interp_type=4, eta0=0.1, gw=False,
+                   integrator=4):
     """level_boxes[l] = list of (lo, hi) for level l (level 0 usually the one
     box covering the domain)."""
     levels = []
@@ -314,7 +343,7 @@ def make_hierarchy(n0, dx0, dt0, g, bf, level_boxes, params: EOMParams, interp_t
         L = Level(l, boxes, n0 * 2 ** l, dx0 / 2 ** l, dt0 / 2 ** l, g, bf, ncomp=16 if gw else 4)
         L.eta = eta0
         levels.append(L)
-    return Hierarchy(levels, params, interp_type, gw=gw)
+    return Hierarchy(levels, params, interp_type, gw=gw, integrator=integrator)
 
 
 def prolong_level_from_coarse(fine: Level, coarse: Level, interp_type: int, comps=None):

@@ -5,13 +5,13 @@ polynomial coarse field must equal its exact fine cell averages."""
 import numpy as np
 import pytest
 
-from oracle import amr, interp, rk4
+from oracle import amr, interp, rk4, ssprk3
 from oracle.eom import EOMParams
 from paper_2404_02950_gb300 import inputs
 
 
-@pytest.mark.parametrize("order", [2, 4])
-def test_full_cover_fine_level_equals_uniform_fine_run(order):
+@pytest.mark.parametrize("order,integrator", [(2, 4), (4, 4), (4, 10)])
+def test_full_cover_fine_level_equals_uniform_fine_run(order, integrator):
     n0, dx0, dt0, g, bf = 8, 0.25, 1.0 / 16, 3, 4
     p = EOMParams(order=order)
     eta0 = 0.5                       # dyadic times keep eta sums exact
@@ -21,13 +21,19 @@ def test_full_cover_fine_level_equals_uniform_fine_run(order):
                            [[((0, 0, 0), (7, 7, 7))],
                             [((0, 0, 0), (7, 15, 15)), ((8, 0, 0), (15, 7, 15)),
                              ((8, 8, 0), (15, 15, 15))]],
-                           p, interp_type=4, eta0=eta0)
+                           p, interp_type=4, eta0=eta0, integrator=integrator)
     h.levels[0].set_dense(coarse0)
     h.levels[1].set_dense(fine0)
     nsteps = 2
     for _ in range(nsteps):
         h.step()
-    ref, _ = rk4.evolve_periodic(fine0, eta0, dt0 / 2, dx0 / 2, 2 * nsteps, p)
+    if integrator == 4:
+        ref, _ = rk4.evolve_periodic(fine0, eta0, dt0 / 2, dx0 / 2, 2 * nsteps, p)
+    else:
+        ref, eta = fine0, eta0
+        for _ in range(2 * nsteps):
+            ref = ssprk3.ssprk3_step_periodic(ref, eta, dt0 / 2, dx0 / 2, p)
+            eta += dt0 / 2
     L1 = h.levels[1]
     for b, (lo, hi) in enumerate(L1.boxes):
         got = L1.data[b][L1.valid(b)]
