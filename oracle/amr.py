@@ -31,7 +31,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import gw as ogw
-from . import ssprk3, tee
+from . import ko, ssprk3, tee
 from . import interp, winding
 from .eom import EOMParams, rhs
 from .energy import energy_box
@@ -179,7 +179,11 @@ def rhs_box(arr, g, dx, eta, p: EOMParams):
     v = (slice(g, arr.shape[1] - g), slice(g, arr.shape[2] - g), slice(g, arr.shape[3] - g))
     lap1 = laplacian_padded(arr[0], g, dx, p.order)
     lap2 = laplacian_padded(arr[1], g, dx, p.order)
-    return np.stack(rhs(arr[0][v], arr[1][v], arr[2][v], arr[3][v], lap1, lap2, eta, p))
+    d = rhs(arr[0][v], arr[1][v], arr[2][v], arr[3][v], lap1, lap2, eta, p)
+    if p.ko_order:
+        # Kreiss-Oliger dissipation of every scalar component (Sec. 2.4)
+        d = [dc + ko.ko_padded(arr[c], g, dx, p.ko_order, p.ko_eps) for c, dc in enumerate(d)]
+    return np.stack(d)
 
 
 class Hierarchy:
@@ -195,7 +199,8 @@ class Hierarchy:
             raise ValueError("integrator must be 4 (classic RK4) or 10 (low-storage SSPRK3)")
         self.integrator = integrator
         self.gw = gw
-        self.ghost_comps = (0, 1, 4, 5, 6, 7, 8, 9) if gw else (0, 1)
+        # ghosts of psi (stencil), of Pi under dissipation, and of u_ij
+        self.ghost_comps = (0, 1) + ((2, 3) if params.ko_order else ()) + ((4, 5, 6, 7, 8, 9) if gw else ())
         self.tag_log = []          # optional (lev, eta, [tags per box]) at stage 1
         self.record_tags = False
         self.te_eps = None         # TEE thresholds of (psi1, psi2, Pi1, Pi2): self-shadow tags at sync

@@ -37,6 +37,8 @@ class EOMParams:
     friction: bool = True
     eta_power: int = 2
     order: int = 2          # Laplacian accuracy order: 2, 4 or 6
+    ko_order: int = 0       # Kreiss-Oliger dissipation order p (odd; 0: off), oracle/ko.py
+    ko_eps: float = 0.0     # its strength
 
 
 def coefficients(eta: float, p: EOMParams):

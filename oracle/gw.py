@@ -25,7 +25,8 @@ from __future__ import annotations
 
 import numpy as np
 
-from .eom import EOMParams, coefficients, rhs
+from .eom import EOMParams, coefficients
+from .rk4 import f_periodic as scalar_f_periodic
 from .stencil import gradient_padded, gradient_periodic, laplacian_padded, laplacian_periodic
 
 # (i, j) direction pairs of the six components
@@ -55,9 +56,7 @@ def f_periodic(y, eta, dx, p: EOMParams):
     """Time derivative of the 16-field state on a periodic lattice."""
     psi1, psi2, pi1, pi2 = y[:4]
     u, v = list(y[4:10]), list(y[10:16])
-    lap1 = laplacian_periodic(psi1, dx, p.order)
-    lap2 = laplacian_periodic(psi2, dx, p.order)
-    ds = rhs(psi1, psi2, pi1, pi2, lap1, lap2, eta, p)
+    ds = scalar_f_periodic((psi1, psi2, pi1, pi2), eta, dx, p)
     lap_u = [laplacian_periodic(uk, dx, p.order) for uk in u]
     du, dv = rhs_gw(u, v, lap_u, source(psi1, psi2, dx, p.order), eta, p)
     return tuple(ds) + tuple(du) + tuple(dv)

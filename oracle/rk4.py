@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import numpy as np
 
+from . import ko
 from .eom import EOMParams, rhs
 from .stencil import laplacian_periodic
 
@@ -29,7 +30,11 @@ def f_periodic(y, eta, dx, p: EOMParams):
     psi1, psi2, pi1, pi2 = y
     lap1 = laplacian_periodic(psi1, dx, p.order)
     lap2 = laplacian_periodic(psi2, dx, p.order)
-    return rhs(psi1, psi2, pi1, pi2, lap1, lap2, eta, p)
+    d = rhs(psi1, psi2, pi1, pi2, lap1, lap2, eta, p)
+    if p.ko_order:
+        # Kreiss-Oliger dissipation of every scalar component (Sec. 2.4)
+        d = tuple(dc + ko.ko_periodic(f, dx, p.ko_order, p.ko_eps) for dc, f in zip(d, y))
+    return d
 
 
 def rk4_step_periodic(y, eta: float, dt: float, dx: float, p: EOMParams):

@@ -10,10 +10,10 @@ from oracle.eom import EOMParams
 from paper_2404_02950_gb300 import inputs
 
 
-@pytest.mark.parametrize("order,integrator", [(2, 4), (4, 4), (4, 10)])
-def test_full_cover_fine_level_equals_uniform_fine_run(order, integrator):
+@pytest.mark.parametrize("order,integrator,ko_order", [(2, 4, 0), (4, 4, 0), (4, 10, 0), (4, 4, 5)])
+def test_full_cover_fine_level_equals_uniform_fine_run(order, integrator, ko_order):
     n0, dx0, dt0, g, bf = 8, 0.25, 1.0 / 16, 3, 4
-    p = EOMParams(order=order)
+    p = EOMParams(order=order, ko_order=ko_order, ko_eps=0.05 if ko_order else 0.0)
     eta0 = 0.5                       # dyadic times keep eta sums exact
     fine0 = inputs.random_snapshot(16, seed=4, amp=0.8)
     coarse0 = [interp.restrict_block(f) for f in fine0]
