@@ -175,14 +175,14 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def _time_form(slh, torch, prec, y0_dense, n, K, W, dist, flags, gw=False, order=ORDER):
+def _time_form(slh, torch, prec, y0_dense, n, K, W, dist, flags, gw=False, order=ORDER, integrator=4):
     """Warm up, then time K steps of one precision; returns a dict."""
     h = slh.Hierarchy(n, DX, nghost=3, bf=16, prec=prec, max_levels=1, gw=gw)
     boxes = [((0, 0, 0), (n - 1, n - 1, n - 1))]
     h.init_level(0, boxes, fused_tags=True)
     h.set_state(0, y0_dense.astype(h.np_dtype))
     h.set_eta(ETA0)
-    p = slh.EOMParams(order=order)
+    p = slh.EOMParams(order=order, integrator=integrator)
     chosen, tune_ms = h.autotune(0, p, reps=3)
     for _ in range(W):
         h.advance(DT, p, flags=flags)
@@ -371,6 +371,20 @@ def run_ours(args, rank, world, local_rank, dist):
         amr = {"workload": AMR_WORKLOAD, "unit": "cell-updates/s",
                "f32": {"value": world * v32, **d32}, "f64": {"value": world * v64, **d64}}
 
+    # the same workload with the low-storage SSPRK3 integrator (type 10)
+    ssp = None
+    if not args.no_ssp:
+        hs, rs = _time_form(slh, torch, "f32", dense, n, K, W, dist, flags, integrator=10)
+        hs.close()
+        del hs
+        torch.cuda.empty_cache()
+        ach_s = rs["stage_bytes"] / (rs["stage_ms"] / 1e3) / 1e9
+        ssp = {"workload": WORKLOAD.replace("classic RK4", "low-storage SSPRK3 (integrator type 10)"),
+               "unit": "cell-updates/s", "value": world * float(n) ** 3 * K / (rs["ms"] / 1e3),
+               "ms_per_step": rs["ms"] / K, "per_stage_ms": rs["per_stage_ms"][:3],
+               "stage_achieved_gbs": ach_s, "hbm_frac": ach_s / peak, "alg_bytes_per_cell_update": 32 * 4,
+               "precision": "FP32 (no compensation)"}
+
     # gravitational-wave tensor fields
     gw = None
     if not args.no_gw:
@@ -415,6 +429,7 @@ def run_ours(args, rank, world, local_rank, dist):
         "e2e": {"value": world * cells * K / (e2e_ms / 1e3), "unit": "cell-updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4 * 8},
         "amr": amr,
+        "ssprk3": ssp,
         "gw": gw,
         "gpu_launches": launches,
         "clocks": clocks,
@@ -433,6 +448,7 @@ def main():
     ap.add_argument("--cells", type=int, default=N_CELLS, help="lattice cells per axis (default 512)")
     ap.add_argument("--no-amr", action="store_true", help="skip the dynamic-AMR line")
     ap.add_argument("--no-gw", action="store_true", help="skip the gravitational-wave tensor line")
+    ap.add_argument("--no-ssp", action="store_true", help="skip the SSPRK3 line")
     ap.add_argument("--profile-only", nargs="?", const="uniform", default=None, choices=["uniform", "amr", "gw"],
                     help="short run for ncu captures of a small case, printing nothing: the FP32 uniform form "
                          "(default), the dynamic-AMR form (base --cells^3, --steps coarse steps) or the "

@@ -104,7 +104,8 @@ typedef int32_t slh_status;
 #define SLH_PROF_S3 7
 #define SLH_PROF_S4 8
 #define SLH_PROF_GW 9        /* the gravitational-wave stage kernel (16 fields) */
-#define SLH_PROF_NKINDS 10
+#define SLH_PROF_KO 10       /* the dissipation kernel */
+#define SLH_PROF_NKINDS 11
 
 typedef struct {
   int32_t lo[3];
@@ -126,6 +127,17 @@ typedef struct {
   int32_t eta_power;
   int32_t lap_order;
   int32_t interp_type;
+  int32_t integrator;   /* Tab. "integrator" type: 4 = classic RK4; 10 (or 3) =
+                           low-storage SSPRK3, Shu-Osher form: stages at
+                           c = (0, 1, 1/2), out = a_s y_n + b_s (Y_s + dt k_s),
+                           (a, b) = (0, 1), (3/4, 1/4), (1/3, 2/3) */
+  int32_t pad_;
+  double ko_eps;        /* Kreiss-Oliger dissipation (Sec. 2.4) added to the
+                           evolution of psi1, psi2, Pi1, Pi2:
+                           (-1)^((p+3)/2) eps dx^p / 2^(p+1) sum_d d^(p+1)/dx_d^(p+1)
+                           with the central (p+2)-point difference; strength eps */
+  int32_t ko_order;     /* p in {1, 3, 5}, 0 = off; needs nghost >= (p+1)/2 */
+  int32_t pad2_;
 } slh_eom_params;
 
 typedef struct slh_ctx slh_ctx;
@@ -280,6 +292,23 @@ slh_status slh_set_tagging(slh_ctx* ctx, uint32_t criteria, const double* te_cri
  * Errors: INVALID_ARG, STATE, CUDA. */
 slh_status slh_shadow_init(slh_ctx* ctx, slh_ctx* shadow);
 slh_status slh_shadow_compare(slh_ctx* ctx, slh_ctx* shadow);
+
+/* Gravitational-wave spectrum of level 0 (Sec. 7.4, Eq. gw_spectrum; needs
+ * nfields 16): G(n^2) = N^-6 sum over the modes k with |n(k)|^2 = n^2 of
+ * Lambda_ij,lm(k) v~_ij(k) v~*_lm(k), v~ the unnormalised DFT of v_ij = u_ij'
+ * over the N^3 cells of level 0, n(k) the signed integer frequencies,
+ * Lambda_ij,lm = P_il P_jm - P_ij P_lm / 2 with P = 1 - khat khat (Sec. 5,
+ * Eq. Lambda_ijlm) and khat the unit effective lattice momentum of
+ * projection type ptype: 1, k_eff = sin(theta)/dx (second-order gradients),
+ * or 2, k_eff = (8 sin(theta) - sin(2 theta))/(6 dx) (fourth order), theta =
+ * 2 pi n/N per axis; khat = 0 where k_eff vanishes.  Writes the distinct n^2
+ * values that occur, ascending, to n2_out and the spectrum to g_out (host
+ * arrays of capacity cap); *nout receives the number of entries (with
+ * OUT_OF_RANGE if cap is smaller).  Uses cuFFT, loaded on first use, and
+ * device scratch of about 12 N^3 field values for the call.  Synchronises.
+ * Errors: INVALID_ARG, STATE, OUT_OF_RANGE, NOMEM, CUDA. */
+slh_status slh_gw_spectrum(slh_ctx* ctx, int32_t ptype, int64_t* n2_out, double* g_out, int32_t cap,
+                           int32_t* nout);
 
 /* Copy level lev's TEE tags (nvalid bytes, dense valid-cell layout) to dst
  * (host if dst_is_host, which synchronises, else device).

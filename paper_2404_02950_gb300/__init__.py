@@ -34,7 +34,7 @@ SLH_GHOSTS = 0
 SLH_RESTRICT = 1
 SLH_TAG_WINDING, SLH_TAG_TEE = 1, 2
 (SLH_PROF_STAGE, SLH_PROF_GHOST, SLH_PROF_RESTRICT, SLH_PROF_DIAG, SLH_PROF_TIME,
- SLH_PROF_S1, SLH_PROF_S2, SLH_PROF_S3, SLH_PROF_S4, SLH_PROF_GW) = range(10)
+ SLH_PROF_S1, SLH_PROF_S2, SLH_PROF_S3, SLH_PROF_S4, SLH_PROF_GW, SLH_PROF_KO) = range(11)
 NFIELDS, NFIELDS_GW = 4, 16   # psi1, psi2, Pi1, Pi2 (+ u_xx..u_yz, v_xx..v_yz)
 
 ERRORS = {-1: "INVALID_ARG", -2: "OUT_OF_RANGE", -3: "CUDA", -4: "TIMEOUT", -5: "NOMEM",
@@ -47,7 +47,7 @@ ABI_SYMBOLS = (
     "slh_advance", "slh_fill_ghosts", "slh_tag", "slh_tag_blocks", "slh_regrid_boxes",
     "slh_reduce_energy", "slh_sync", "slh_profile", "slh_profile_read", "slh_set_tile", "slh_autotune",
     "slh_energy_noalloc", "slh_regrid_level", "slh_selftest_wait_timeout",
-    "slh_set_tagging", "slh_shadow_init", "slh_shadow_compare", "slh_tee_tags",
+    "slh_set_tagging", "slh_shadow_init", "slh_shadow_compare", "slh_tee_tags", "slh_gw_spectrum",
 )
 
 
@@ -64,23 +64,29 @@ class slh_box(ctypes.Structure):
 class slh_eom_params(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_double), ("a", ctypes.c_double), ("friction", ctypes.c_int32),
                 ("eta_power", ctypes.c_int32), ("lap_order", ctypes.c_int32),
-                ("interp_type", ctypes.c_int32)]
+                ("interp_type", ctypes.c_int32), ("integrator", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("ko_eps", ctypes.c_double), ("ko_order", ctypes.c_int32), ("pad2_", ctypes.c_int32)]
 
 
 @dataclass(frozen=True)
 class EOMParams:
     """Coefficients of Sec. 3.1: lambda, a, friction on/off, eta power of the
-    potential coefficient, Laplacian accuracy order and ghost interpolation."""
+    potential coefficient, Laplacian accuracy order, ghost interpolation,
+    the integrator type (4 classic RK4, 10 low-storage SSPRK3) and the
+    Kreiss-Oliger dissipation order (0 off, 1/3/5) and strength (Sec. 2.4)."""
     lam: float = 1.0
     a: float = 0.0
     friction: bool = True
     eta_power: int = 2
     order: int = 2
     interp_type: int = 4
+    integrator: int = 4
+    ko_order: int = 0
+    ko_eps: float = 0.0
 
     def c(self):
         return slh_eom_params(self.lam, self.a, int(self.friction), self.eta_power, self.order,
-                              self.interp_type)
+                              self.interp_type, self.integrator, 0, self.ko_eps, self.ko_order, 0)
 
 
 _lib = None
@@ -126,6 +132,7 @@ def lib():
         "slh_shadow_init": (i32, [vp, vp]),
         "slh_shadow_compare": (i32, [vp, vp]),
         "slh_tee_tags": (i32, [vp, i32, vp, i32]),
+        "slh_gw_spectrum": (i32, [vp, i32, P(i64), P(dbl), i32, P(i32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -446,6 +453,17 @@ class Hierarchy:
         out = np.empty(self.levels[lev]["nvalid"], dtype=np.uint8)
         _check(lib().slh_tee_tags(self.h, lev, ctypes.c_void_p(out.ctypes.data), 1))
         return out
+
+    def gw_spectrum(self, ptype=2):
+        """(n2, G): the unbinned gravitational-wave spectrum of level 0
+        (Sec. 7.4) for projection type 1 or 2."""
+        cap = 3 * (self.n0 // 2) ** 2 + 1
+        n2 = np.empty(cap, dtype=np.int64)
+        g = np.empty(cap, dtype=np.float64)
+        nout = ctypes.c_int32()
+        _check(lib().slh_gw_spectrum(self.h, ptype, n2.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                     g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), cap, ctypes.byref(nout)))
+        return n2[:nout.value].copy(), g[:nout.value].copy()
 
     def profile(self, enable=True, reset=True):
         _check(lib().slh_profile(self.h, int(enable), int(reset)))

@@ -21,7 +21,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libslh.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SRCS = ["api.cu", "stage.cu", "gw.cu", "ghost.cu", "tee.cu", "diag.cu", "noalloc.cu"]
+CUDA_SRCS = ["api.cu", "stage.cu", "gw.cu", "ghost.cu", "tee.cu", "spectrum.cu", "ko.cu", "diag.cu", "noalloc.cu"]
 CXX_SRCS = ["regrid.cpp"]
 
 
@@ -59,7 +59,7 @@ def build(verbose: bool = False, extra_flags=None) -> str:
             logs.append(out)
     objs = [j[-1] for j in jobs]
     tmp = LIB + ".tmp"
-    logs.append(_run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]))
+    logs.append(_run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-ldl"]))
     os.replace(tmp, LIB)
     if verbose:
         print("\n".join(l for l in logs if l.strip()))

@@ -81,7 +81,7 @@ void prof_end(slh_ctx* c) {
 static void free_level(Level& L) {
   free_tmaps(L);
   cudaFree(L.tile.d_items);
-  cudaFree(L.d_gw_items);
+  cudaFree(L.d_col_items);
   cudaFree(L.d_boxes);
   cudaFree(L.d_bmap);
   cudaFree(L.d_gregions);
@@ -519,16 +519,16 @@ static slh_status build_level(slh_ctx* c, int lev, Level& L, const slh_box* boxe
     const TileVariant* vs = tile_variants(c->prec, &nv);
     if ((st = set_tile(c, L, vs[0])) != SLH_OK) return st;
   }
-  if (c->ncomp == NCOMP_GW) {
+  {   // column items of the GW and dissipation kernels
     std::vector<int4> items;
     for (size_t b = 0; b < L.lay.boxes.size(); ++b) {
       const BoxDev& B = L.lay.boxes[b];
-      for (int z0 = 0; z0 < B.n[2]; z0 += GW_ZLEN)
-        for (int y0 = 0; y0 < B.n[1]; y0 += GW_TY)
-          for (int x0 = 0; x0 < B.n[0]; x0 += GW_TX) items.push_back(make_int4((int)b, x0, y0, z0));
+      for (int z0 = 0; z0 < B.n[2]; z0 += COL_ZLEN)
+        for (int y0 = 0; y0 < B.n[1]; y0 += COL_TY)
+          for (int x0 = 0; x0 < B.n[0]; x0 += COL_TX) items.push_back(make_int4((int)b, x0, y0, z0));
     }
-    if ((st = upload(&L.d_gw_items, items)) != SLH_OK) return st;
-    L.ngw_items = (int)items.size();
+    if ((st = upload(&L.d_col_items, items)) != SLH_OK) return st;
+    L.ncol_items = (int)items.size();
   }
 
   // restriction items onto lev-1
@@ -741,12 +741,20 @@ static slh_status check_params(const slh_eom_params* p) {
   if (p->eta_power != 0 && p->eta_power != 2) return fail(SLH_ERR_INVALID_ARG, "eta_power must be 0 or 2");
   if (p->interp_type != 0 && p->interp_type != 2 && p->interp_type != 4)
     return fail(SLH_ERR_INVALID_ARG, "interp_type must be 0, 2 or 4");
+  if (p->integrator != 4 && p->integrator != 10 && p->integrator != 3)
+    return fail(SLH_ERR_INVALID_ARG, "integrator must be 4 (classic RK4) or 10 / 3 (SSPRK3), got %d", p->integrator);
+  if (p->ko_order != 0 && p->ko_order != 1 && p->ko_order != 3 && p->ko_order != 5)
+    return fail(SLH_ERR_INVALID_ARG, "ko_order must be 0 (off), 1, 3 or 5 (got %d)", p->ko_order);
+  if (!(p->ko_eps >= 0.0) || p->ko_eps > 1e30) return fail(SLH_ERR_INVALID_ARG, "ko_eps must be finite and >= 0");
   return SLH_OK;
 }
 
 static slh_status rk_step_impl(slh_ctx* c, int lev, int sub, double dt0, const slh_eom_params& p, uint32_t flags) {
   Level& L = c->lev[lev];
   if (c->g < p.lap_order / 2) return fail(SLH_ERR_INVALID_ARG, "nghost %d < Laplacian half width %d", c->g, p.lap_order / 2);
+  if (p.ko_order > 0 && c->g < (p.ko_order + 1) / 2)
+    return fail(SLH_ERR_INVALID_ARG, "nghost %d < dissipation half width %d", c->g, (p.ko_order + 1) / 2);
+  const bool ko = p.ko_order > 0 && p.ko_eps > 0.0;
   const double dt = std::ldexp(dt0, -lev);
   const double cRK[4] = {0.0, 0.5, 0.5, 1.0};
   const double aRK[4] = {0.5, 0.5, 1.0, 0.0};
@@ -759,13 +767,20 @@ static slh_status rk_step_impl(slh_ctx* c, int lev, int sub, double dt0, const s
   prof_end(c);
   if (st != SLH_OK) return st;
   const int ybuf = L.role_y, nbuf = L.role_prev;
-  const int in_role[4] = {ybuf, SLH_BUF_YA, nbuf, SLH_BUF_YA};
-  const int out_role[4] = {SLH_BUF_YA, nbuf, SLH_BUF_YA, nbuf};
-  const double vals[4] = {12.0, 20.0, 20.0, c->prec == SLH_F32_KAHAN ? 24.0 : 16.0};
-  for (int k = 0; k < 4; ++k) {
-    const double alpha = lev > 0 ? (sub + cRK[k]) / 2.0 : 1.0;
+  const bool ssp = p.integrator != 4;
+  // classic RK4: Y -> YA -> prev -> YA -> prev with the increment in D;
+  // SSPRK3: Y -> YA -> D -> prev (D holds the second stage value)
+  const int in_role[4] = {ybuf, SLH_BUF_YA, ssp ? SLH_BUF_D : nbuf, SLH_BUF_YA};
+  const int out_role[4] = {SLH_BUF_YA, ssp ? SLH_BUF_D : nbuf, ssp ? nbuf : SLH_BUF_YA, nbuf};
+  const double vals[4] = {ssp ? 8.0 : 12.0, ssp ? 12.0 : 20.0, ssp ? 12.0 : 20.0,
+                          c->prec == SLH_F32_KAHAN ? 24.0 : 16.0};
+  const double cSSP[3] = {0.0, 1.0, 0.5}, aSSP[3] = {0.0, 0.75, 1.0 / 3.0}, bSSP[3] = {1.0, 0.25, 2.0 / 3.0};
+  const int nstage = ssp ? 3 : 4;
+  for (int k = 0; k < nstage; ++k) {
+    const double cs = ssp ? cSSP[k] : cRK[k];
+    const double alpha = lev > 0 ? (sub + cs) / 2.0 : 1.0;
     prof_begin(c, SLH_PROF_GHOST, (double)L.nghost_cells * ghost_fields(c) * 2 * s);
-    st = launch_ghosts(c, lev, in_role[k], alpha, p.interp_type);
+    st = launch_ghosts(c, lev, in_role[k], alpha, p.interp_type, ko);
     prof_end(c);
     if (st != SLH_OK) return st;
     StageLaunch sl;
@@ -775,10 +790,13 @@ static slh_status rk_step_impl(slh_ctx* c, int lev, int sub, double dt0, const s
     sl.yn_buf = ybuf;
     sl.d_buf = SLH_BUF_D;
     sl.out_buf = out_role[k];
-    sl.c_buf = (k == 3 && L.buf[SLH_BUF_C]) ? SLH_BUF_C : -1;
-    sl.c_stage = cRK[k] * dt;
-    sl.ha = aRK[k] * dt;
-    sl.hb = bRK[k] * dt;
+    sl.c_buf = (!ssp && k == 3 && L.buf[SLH_BUF_C]) ? SLH_BUF_C : -1;
+    sl.c_stage = cs * dt;
+    sl.ha = ssp ? dt : aRK[k] * dt;
+    sl.hb = ssp ? 0.0 : bRK[k] * dt;
+    sl.ssp = ssp ? 1 : 0;
+    sl.sa = ssp ? aSSP[k] : 0.0;
+    sl.sb = ssp ? bSSP[k] : 0.0;
     sl.lev = lev;
     double extra = 0.0;
     if (k == 0 && (flags & SLH_FUSE_TAG)) {
@@ -792,16 +810,33 @@ static slh_status rk_step_impl(slh_ctx* c, int lev, int sub, double dt0, const s
       sl.cov_shift = ilog2(c->bf / 2);
       sl.cov_nb = L.ncov;
     }
+    if (ko && !ssp && k == 3) {
+      // the last RK4 stage's share goes into the increment before the
+      // compensated final sum: D += b_4 dt Q(Y_4)
+      prof_begin(c, SLH_PROF_KO, V * 12.0 * s);
+      st = launch_ko(c, L, p, in_role[k], out_role[k], SLH_BUF_D, 0.0, bRK[k] * dt);
+      prof_end(c);
+      if (st != SLH_OK) return st;
+    }
     prof_begin(c, SLH_PROF_S1 + k, V * (vals[k] * s + extra));
     int used = 0;
     st = launch_stage(c, L, p, sl, &used);
     prof_end(c);
     if (st != SLH_OK) return st;
+    if (ko && (ssp || k < 3)) {
+      // out += a dt Q(Y_s), D += b dt Q(Y_s) (classic RK4); out += b_s dt Q(Y_s) (SSPRK3)
+      prof_begin(c, SLH_PROF_KO, V * (ssp ? 12.0 : 20.0) * s);
+      st = ssp ? launch_ko(c, L, p, in_role[k], out_role[k], -1, bSSP[k] * dt, 0.0)
+               : launch_ko(c, L, p, in_role[k], out_role[k], SLH_BUF_D, aRK[k] * dt, bRK[k] * dt);
+      prof_end(c);
+      if (st != SLH_OK) return st;
+    }
     if (k == 0 && (flags & SLH_FUSE_ENERGY)) L.fused_energy_ctas = used;
     if (c->ncomp == NCOMP_GW) {
       // the 12 tensor fields: reads psi (2) + u, v (12) of the stage input,
       // and as the scalar stage y_n, D, C of its 12 fields
-      const double gvals[4] = {38.0, 62.0, 62.0, c->prec == SLH_F32_KAHAN ? 74.0 : 50.0};
+      const double gvals[4] = {ssp ? 26.0 : 38.0, ssp ? 38.0 : 62.0, ssp ? 38.0 : 62.0,
+                               c->prec == SLH_F32_KAHAN ? 74.0 : 50.0};
       prof_begin(c, SLH_PROF_GW, V * gvals[k] * s);
       st = launch_gw_stage(c, L, p, sl);
       prof_end(c);
@@ -1004,7 +1039,7 @@ slh_status slh_tag(slh_ctx* c, int32_t lev, uint8_t* tags_dev, int64_t* n_tagged
   if (lev < 0 || lev >= c->nlevels) return fail(SLH_ERR_STATE, "tag: level %d not defined", lev);
   if (lev >= c->stale_from) return fail(SLH_ERR_STATE, "tag: level %d must be regridded first", c->stale_from);
   // the winding tags read psi only; the cheapest stencil variant runs them
-  const slh_eom_params p = {1.0, 0.0, 1, 2, 2, 4};
+  const slh_eom_params p = {1.0, 0.0, 1, 2, 2, 4, 4, 0, 0.0, 0, 0};
   int used = 0;
   slh_status st = diag_pass(c, lev, p, tags_dev, false, &used);
   if (st != SLH_OK) return st;
@@ -1130,6 +1165,32 @@ slh_status slh_shadow_compare(slh_ctx* c, slh_ctx* s) {
   if ((st = stream_after(c->stream, s->stream)) != SLH_OK) return st;
   if ((st = launch_shadow(c, s, true)) != SLH_OK) return st;
   return stream_after(s->stream, c->stream);
+}
+
+slh_status slh_gw_spectrum(slh_ctx* c, int32_t ptype, int64_t* n2_out, double* g_out, int32_t cap, int32_t* nout) {
+  if (!c || !nout) return fail(SLH_ERR_INVALID_ARG, "gw_spectrum: null argument");
+  if (ptype != 1 && ptype != 2) return fail(SLH_ERR_INVALID_ARG, "gw_spectrum: projection type must be 1 or 2");
+  if (c->ncomp != NCOMP_GW) return fail(SLH_ERR_STATE, "gw_spectrum: the context carries no gravitational-wave fields");
+  if (c->nlevels < 1) return fail(SLH_ERR_STATE, "gw_spectrum: level 0 not defined");
+  std::vector<double> bins;
+  std::vector<unsigned long long> counts;
+  slh_status st = gw_spectrum_impl(c, ptype, &bins, &counts);
+  if (st != SLH_OK) return st;
+  int need = 0;
+  for (unsigned long long k : counts) need += k ? 1 : 0;
+  *nout = need;
+  if (cap < need || (need > 0 && (!n2_out || !g_out)))
+    return fail(SLH_ERR_OUT_OF_RANGE, "gw_spectrum: capacity %d < %d entries", cap, need);
+  const double n = (double)c->lev[0].n_dom;
+  const double norm = 1.0 / (n * n * n * n * n * n);
+  int o = 0;
+  for (size_t k = 0; k < counts.size(); ++k)
+    if (counts[k]) {
+      n2_out[o] = (int64_t)k;
+      g_out[o] = bins[k] * norm;
+      ++o;
+    }
+  return slh_sync(c);
 }
 
 slh_status slh_reduce_energy(slh_ctx* c, const slh_eom_params* p, int32_t mode, double out[5]) {

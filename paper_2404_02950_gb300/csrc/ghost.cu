@@ -63,12 +63,15 @@ __device__ __forceinline__ double pw(int itype, int child, int off) {
 // Ghost fill by regions (see GhostRegion): copy regions are plain strided
 // copies; prolongation regions first gather the coarser level's cells under
 // the region's stencil footprint, time-interpolated, into shared memory (one
-// box lookup per coarse cell instead of one per stencil point), then one
-// thread per coarse cell under the region evaluates the (2r+1)^3
-// tensor-product stencil of its 8 children at once, as separable partial
-// sums along x, then y, then z (each patch value read once per coarse cell
-// instead of once per child); mixed regions decide cell by cell.
+// box lookup per coarse cell instead of one per stencil point), field by
+// field, then apply the tensor-product stencil as three separable 1D passes
+// (coarse -> fine along one axis per pass, thinnest region extent first, so
+// the intermediate arrays stay small and no coarse cell's stencil is
+// evaluated for children outside the region); mixed regions decide cell by
+// cell in the last pass.
 constexpr int PATCH_MAX = 21 * 21 * 7;   // coarse cells under a 32 x 32 x g region (r <= 2, g <= 4)
+constexpr int PASS1_MAX = 4 * 21 * 21;   // after the pass along the thinnest axis (<= g = 4 fine cells)
+constexpr int PASS2_MAX = 4 * 32 * 21;   // after the second pass
 
 template <typename T>
 struct GhostArgs {
@@ -88,21 +91,144 @@ struct GhostArgs {
   int cnbd, cndom;
   double alpha;
   int itype;
-  int npairs;   // field pairs filled: (psi1, psi2) and with 16 fields (u_xx, u_yy), (u_zz, u_xy), (u_xz, u_yz)
+  int npairs;   // field pairs filled: (psi1, psi2), (Pi1, Pi2) under dissipation, and with 16
+                // fields (u_xx, u_yy), (u_zz, u_xy), (u_xz, u_yz)
+  int pc[5];    // first component of each pair
   int* err;
 };
 
-// first component of field pair q
-__device__ __forceinline__ int pair_comp(int q) { return q == 0 ? 0 : GW_U0 + 2 * (q - 1); }
+
+// geometry of a region's separable prolongation passes: the region's first
+// fine cell (unwrapped), the coarse patch origin and the fine extents
+struct PassGeo {
+  int flo[3];
+  int plo[3];
+  int ext[3];
+};
+
+template <int AX>
+__device__ __forceinline__ int pick(int a, int b, int c) { return AX == 0 ? a : (AX == 1 ? b : c); }
+
+// One coarse -> fine pass along axis AX over NF fields in shared memory
+// (field f at src + f * sstr): input extents d (x, y, z), output extent
+// geo.ext[AX] along AX; d is updated to the output extents.
+template <typename T, int RAD, int AX, int NF>
+__device__ __forceinline__ void smem_pass(const T* __restrict__ src, int sstr, T* __restrict__ dst, int dstr,
+                                          int (&d)[3], const PassGeo& geo, const T (&w0)[2 * RAD + 1],
+                                          const T (&w1)[2 * RAD + 1]) {
+  const int o0 = AX == 0 ? geo.ext[0] : d[0], o1 = AX == 1 ? geo.ext[1] : d[1], o2 = AX == 2 ? geo.ext[2] : d[2];
+  const int sa = AX == 0 ? 1 : (AX == 1 ? d[0] : d[0] * d[1]);
+  const int fa = geo.flo[AX], pa = geo.plo[AX];
+  const int nout = o0 * o1 * o2;
+  const Split3 sp(o0, o1);
+  for (int t = threadIdx.x; t < nout; t += blockDim.x) {
+    int i0, i1, i2;
+    sp(t, i0, i1, i2);
+    const int g = fa + pick<AX>(i0, i1, i2);       // unwrapped fine coordinate along AX
+    const int pc = (g >> 1) - pa - RAD;             // first stencil cell of the input along AX
+    const bool ch = (g & 1) != 0;
+    const int base = (pick<AX>(i2, i2, pc) * d[1] + pick<AX>(i1, pc, i1)) * d[0] + pick<AX>(pc, i0, i0);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      T acc = 0;
+#pragma unroll
+      for (int o = 0; o <= 2 * RAD; ++o) acc += (ch ? w1[o] : w0[o]) * src[f * sstr + base + o * sa];
+      dst[f * dstr + t] = acc;
+    }
+  }
+  d[0] = o0;
+  d[1] = o1;
+  d[2] = o2;
+}
+
+template <typename T, int RAD, int NF>
+__device__ __forceinline__ void smem_pass_any(int ax, const T* src, int sstr, T* dst, int dstr, int (&d)[3],
+                                              const PassGeo& geo, const T (&w0)[2 * RAD + 1],
+                                              const T (&w1)[2 * RAD + 1]) {
+  if (ax == 0) smem_pass<T, RAD, 0, NF>(src, sstr, dst, dstr, d, geo, w0, w1);
+  else if (ax == 1) smem_pass<T, RAD, 1, NF>(src, sstr, dst, dstr, d, geo, w0, w1);
+  else smem_pass<T, RAD, 2, NF>(src, sstr, dst, dstr, d, geo, w0, w1);
+}
+
+// The last pass, along axis AX: writes the region's ghost cells of fields
+// f0 .. f0+NF-1 (mixed regions copy the cells a same-level box covers).
+template <typename T, int RAD, int AX, int NF>
+__device__ __forceinline__ void final_pass(const T* __restrict__ src, int sstr, const int (&d)[3], const PassGeo& geo,
+                                           const T (&w0)[2 * RAD + 1], const T (&w1)[2 * RAD + 1],
+                                           const GhostArgs<T>& A, const GhostRegion& R, const BoxDev& B, int f0,
+                                           bool have_coarse) {
+  const int o0 = AX == 0 ? geo.ext[0] : d[0], o1 = AX == 1 ? geo.ext[1] : d[1], o2 = AX == 2 ? geo.ext[2] : d[2];
+  const int sa = AX == 0 ? 1 : (AX == 1 ? d[0] : d[0] * d[1]);
+  const int fa = geo.flo[AX], pa = geo.plo[AX];
+  const int nout = o0 * o1 * o2;
+  const Split3 sp(o0, o1);
+  for (int t = threadIdx.x; t < nout; t += blockDim.x) {
+    int i0, i1, i2;
+    sp(t, i0, i1, i2);
+    const int rx = R.lo[0] + i0, ry = R.lo[1] + i1, rz = R.lo[2] + i2;
+    const long long dg = cell_index(B, A.gl, rx, ry, rz);
+    if (R.kind == GHOST_MIXED) {
+      const int gx = B.lo[0] + rx, gy = B.lo[1] + ry, gz = B.lo[2] + rz;
+      const int wx = wrapi(gx, A.ndom), wy = wrapi(gy, A.ndom), wz = wrapi(gz, A.ndom);
+      const int own = A.bmap[((long long)(wz >> A.bshift) * A.nbd + (wy >> A.bshift)) * A.nbd + (wx >> A.bshift)];
+      if (own >= 0) {
+        const BoxDev Sb = A.boxes[own];
+        const long long sg = cell_index(Sb, A.gl, wx - Sb.lo[0], wy - Sb.lo[1], wz - Sb.lo[2]);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          const int comp = A.pc[(f0 + f) >> 1] + ((f0 + f) & 1);
+          A.y[dg + comp * B.cs] = A.y[sg + comp * Sb.cs];
+        }
+        continue;
+      }
+    }
+    if (!have_coarse) {
+      atomicCAS(A.err, 0, DERR_NESTING);
+      continue;
+    }
+    const int g = fa + pick<AX>(i0, i1, i2);
+    const int pc = (g >> 1) - pa - RAD;
+    const bool ch = (g & 1) != 0;
+    const int base = (pick<AX>(i2, i2, pc) * d[1] + pick<AX>(i1, pc, i1)) * d[0] + pick<AX>(pc, i0, i0);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      T acc = 0;
+#pragma unroll
+      for (int o = 0; o <= 2 * RAD; ++o) acc += (ch ? w1[o] : w0[o]) * src[f * sstr + base + o * sa];
+      if (acc != acc) atomicCAS(A.err, 0, DERR_NESTING);   // the stencil met an uncovered (NaN) coarse cell
+      const int comp = A.pc[(f0 + f) >> 1] + ((f0 + f) & 1);
+      A.y[dg + comp * B.cs] = acc;
+    }
+  }
+}
+
+template <typename T, int RAD, int NF>
+__device__ __forceinline__ void final_pass_any(int ax, const T* src, int sstr, const int (&d)[3], const PassGeo& geo,
+                                               const T (&w0)[2 * RAD + 1], const T (&w1)[2 * RAD + 1],
+                                               const GhostArgs<T>& A, const GhostRegion& R, const BoxDev& B, int f0,
+                                               bool have_coarse) {
+  if (ax == 0) final_pass<T, RAD, 0, NF>(src, sstr, d, geo, w0, w1, A, R, B, f0, have_coarse);
+  else if (ax == 1) final_pass<T, RAD, 1, NF>(src, sstr, d, geo, w0, w1, A, R, B, f0, have_coarse);
+  else final_pass<T, RAD, 2, NF>(src, sstr, d, geo, w0, w1, A, R, B, f0, have_coarse);
+}
 
 template <typename T, int RAD>
 __global__ void __launch_bounds__(256, 3) ghost_region_kernel(const GhostArgs<T> A) {
   // [2][pz][py][px]: time-interpolated psi1, psi2 in the field precision
   // (the stencil weights are dyadic rationals, exact in FP32 and FP64)
   extern __shared__ __align__(16) unsigned char patch_raw[];
+  constexpr int NF = sizeof(T) == 4 ? 2 : 1;   // fields per pass (shared memory ~60 KB either way)
   T* patch = reinterpret_cast<T*>(patch_raw);
+  T* buf1 = patch + NF * PATCH_MAX;
+  T* buf2 = buf1 + NF * PASS1_MAX;
   const int tid = threadIdx.x, nt = blockDim.x;
   const T al = (T)A.alpha, bl = (T)1 - (T)A.alpha;
+  T w0[2 * RAD + 1], w1[2 * RAD + 1];   // 1D weights of child 0 and child 1
+#pragma unroll
+  for (int o = -RAD; o <= RAD; ++o) {
+    w0[o + RAD] = (T)pw(A.itype, 0, o);
+    w1[o + RAD] = (T)pw(A.itype, 1, o);
+  }
   for (int r = blockIdx.x; r < A.nregions; r += gridDim.x) {
     const GhostRegion R = A.regions[r];
     const BoxDev B = A.boxes[R.box];
@@ -117,7 +243,7 @@ __global__ void __launch_bounds__(256, 3) ghost_region_kernel(const GhostArgs<T>
         const long long dst = cell_index(B, A.gl, rx, ry, rz);
         const long long src = cell_index(S, A.gl, rx + R.d[0], ry + R.d[1], rz + R.d[2]);
         for (int q = 0; q < A.npairs; ++q) {
-          const int c0 = pair_comp(q);
+          const int c0 = A.pc[q];
           A.y[dst + c0 * B.cs] = A.y[src + c0 * S.cs];
           A.y[dst + (c0 + 1) * B.cs] = A.y[src + (c0 + 1) * S.cs];
         }
@@ -126,147 +252,85 @@ __global__ void __launch_bounds__(256, 3) ghost_region_kernel(const GhostArgs<T>
     }
     // coarse footprint of the widest stencil (unwrapped coarse coordinates);
     // narrower stencils use part of it
-    int plo[3], pn[3];
+    int flo[3], plo[3], pn[3];
     for (int d = 0; d < 3; ++d) {
-      const int flo = B.lo[d] + R.lo[d], fhi = flo + R.ext[d] - 1;
-      plo[d] = (flo >> 1) - PROLONG_RAD_MAX;
+      flo[d] = B.lo[d] + R.lo[d];
+      const int fhi = flo[d] + R.ext[d] - 1;
+      plo[d] = (flo[d] >> 1) - PROLONG_RAD_MAX;
       pn[d] = (fhi >> 1) + PROLONG_RAD_MAX - plo[d] + 1;
     }
     const int np = pn[0] * pn[1] * pn[2];
     const bool have_coarse = A.cboxes != nullptr && np <= PATCH_MAX;
-    for (int q = 0; q < A.npairs; ++q) {
-      const int c0 = pair_comp(q);
-      if (have_coarse && R.covered) {
-        // planned gather: strided copies of the pieces, no lookups
-        for (int pi = R.p0; pi < R.p0 + R.np; ++pi) {
-          const PatchPiece P = A.pieces[pi];
-          const BoxDev C = A.cboxes[P.cbox];
-          const int ne = P.ext[0] * P.ext[1] * P.ext[2];
-          const Split3 sp(P.ext[0], P.ext[1]);
-          for (int t = tid; t < ne; t += nt) {
+    // the three separable passes go thinnest fine extent first, so that the
+    // intermediate arrays stay small (a slab is at most g <= 4 cells thick)
+    const int ex0 = R.ext[0], ex1 = R.ext[1], ex2 = R.ext[2];
+    auto ext_of = [&](int a) { return a == 0 ? ex0 : (a == 1 ? ex1 : ex2); };
+    int a0 = 0, a1 = 1, a2 = 2;
+    if (ext_of(a1) < ext_of(a0)) { const int s_ = a0; a0 = a1; a1 = s_; }
+    if (ext_of(a2) < ext_of(a1)) { const int s_ = a1; a1 = a2; a2 = s_; }
+    if (ext_of(a1) < ext_of(a0)) { const int s_ = a0; a0 = a1; a1 = s_; }
+    const PassGeo geo{{flo[0], flo[1], flo[2]}, {plo[0], plo[1], plo[2]}, {ex0, ex1, ex2}};
+    for (int f0 = 0; f0 < 2 * A.npairs; f0 += NF) {
+      // gather NF fields into the patch (field f of the region's pair list)
+      for (int f = 0; f < NF; ++f) {
+        const int comp = A.pc[(f0 + f) >> 1] + ((f0 + f) & 1);
+        T* pf = patch + f * PATCH_MAX;
+        if (have_coarse && R.covered) {
+          // planned gather: strided copies of the pieces, no lookups
+          for (int pi = R.p0; pi < R.p0 + R.np; ++pi) {
+            const PatchPiece P = A.pieces[pi];
+            const BoxDev C = A.cboxes[P.cbox];
+            const int ne = P.ext[0] * P.ext[1] * P.ext[2];
+            const Split3 sp(P.ext[0], P.ext[1]);
+            for (int t = tid; t < ne; t += nt) {
+              int i, j, k;
+              sp(t, i, j, k);
+              const long long ci = cell_index(C, A.gl, P.src[0] + i, P.src[1] + j, P.src[2] + k) + comp * C.cs;
+              pf[((P.dst[2] + k) * pn[1] + (P.dst[1] + j)) * pn[0] + (P.dst[0] + i)] = bl * A.cold[ci] + al * A.cnew[ci];
+            }
+          }
+        } else if (have_coarse) {
+          // footprint not tiled by the coarse level (a nesting violation, or a
+          // level built without a plan): per-cell lookup, NaN where uncovered
+          const Split3 sp(pn[0], pn[1]);
+#pragma unroll 4
+          for (int t = tid; t < np; t += nt) {
             int i, j, k;
             sp(t, i, j, k);
-            const long long ci = cell_index(C, A.gl, P.src[0] + i, P.src[1] + j, P.src[2] + k) + c0 * C.cs;
-            const int pt = ((P.dst[2] + k) * pn[1] + (P.dst[1] + j)) * pn[0] + (P.dst[0] + i);
-            patch[pt] = bl * A.cold[ci] + al * A.cnew[ci];
-            patch[np + pt] = bl * A.cold[ci + C.cs] + al * A.cnew[ci + C.cs];
+            const int qx = wrapi(plo[0] + i, A.cndom), qy = wrapi(plo[1] + j, A.cndom), qz = wrapi(plo[2] + k, A.cndom);
+            const int cown = A.cbmap[((long long)(qz >> A.bshift) * A.cnbd + (qy >> A.bshift)) * A.cnbd + (qx >> A.bshift)];
+            T v = (T)__longlong_as_double(0x7ff8000000000000ll);   // NaN: not covered
+            if (cown >= 0) {
+              const BoxDev C = A.cboxes[cown];
+              const long long ci = cell_index(C, A.gl, qx - C.lo[0], qy - C.lo[1], qz - C.lo[2]) + comp * C.cs;
+              v = bl * A.cold[ci] + al * A.cnew[ci];
+            }
+            pf[t] = v;
           }
-        }
-      } else if (have_coarse) {
-        // footprint not tiled by the coarse level (a nesting violation, or a
-        // level built without a plan): per-cell lookup, NaN where uncovered
-        const Split3 sp(pn[0], pn[1]);
-#pragma unroll 4
-        for (int t = tid; t < np; t += nt) {
-          int i, j, k;
-          sp(t, i, j, k);
-          const int qx = wrapi(plo[0] + i, A.cndom), qy = wrapi(plo[1] + j, A.cndom), qz = wrapi(plo[2] + k, A.cndom);
-          const int cown = A.cbmap[((long long)(qz >> A.bshift) * A.cnbd + (qy >> A.bshift)) * A.cnbd + (qx >> A.bshift)];
-          T v0 = (T)__longlong_as_double(0x7ff8000000000000ll), v1 = v0;   // NaN: not covered
-          if (cown >= 0) {
-            const BoxDev C = A.cboxes[cown];
-            const long long ci = cell_index(C, A.gl, qx - C.lo[0], qy - C.lo[1], qz - C.lo[2]) + c0 * C.cs;
-            v0 = bl * A.cold[ci] + al * A.cnew[ci];
-            v1 = bl * A.cold[ci + C.cs] + al * A.cnew[ci + C.cs];
-          }
-          patch[t] = v0;
-          patch[np + t] = v1;
         }
       }
       __syncthreads();
-      // one task per coarse cell under the region: its stencil is read from
-      // the patch once and all 8 children follow by separable partial sums
-      // (x, then y, then z); children outside the region are not stored
-      int clo[3], cn[3], flo[3], fhi[3];
-      for (int d = 0; d < 3; ++d) {
-        flo[d] = B.lo[d] + R.lo[d];
-        fhi[d] = flo[d] + R.ext[d] - 1;
-        clo[d] = flo[d] >> 1;
-        cn[d] = (fhi[d] >> 1) - clo[d] + 1;
+      // passes: coarse -> fine along a0 (patch -> buf1), a1 (buf1 -> buf2),
+      // a2 (buf2 -> the ghost cells)
+      int d[3] = {pn[0], pn[1], pn[2]};
+      if (have_coarse) {
+        smem_pass_any<T, RAD, NF>(a0, patch, PATCH_MAX, buf1, PASS1_MAX, d, geo, w0, w1);
+        __syncthreads();
+        smem_pass_any<T, RAD, NF>(a1, buf1, PASS1_MAX, buf2, PASS2_MAX, d, geo, w0, w1);
+        __syncthreads();
+      } else {
+        d[0] = ex0;   // no coarse data: the last pass only copies or flags
+        d[1] = ex1;
+        d[2] = ex2;
       }
-      const int ntask = cn[0] * cn[1] * cn[2];
-      const Split3 sp(cn[0], cn[1]);
-      T w[2][2 * RAD + 1];   // 1D weights of child 0 and child 1
-#pragma unroll
-      for (int o = -RAD; o <= RAD; ++o) {
-        w[0][o + RAD] = (T)pw(A.itype, 0, o);
-        w[1][o + RAD] = (T)pw(A.itype, 1, o);
-      }
-      for (int t = tid; t < ntask; t += nt) {
-        int ti, tj, tk;
-        sp(t, ti, tj, tk);
-        const int Px = clo[0] + ti, Py = clo[1] + tj, Pz = clo[2] + tk;
-        T out[2][2][2][2];   // [field][cz][cy][cx]
-        if (have_coarse) {
-#pragma unroll
-          for (int f = 0; f < 2; ++f)
-#pragma unroll
-            for (int a = 0; a < 8; ++a) out[f][a >> 2][(a >> 1) & 1][a & 1] = 0;
-          const int base = ((Pz - RAD - plo[2]) * pn[1] + (Py - RAD - plo[1])) * pn[0] + (Px - RAD - plo[0]);
-#pragma unroll
-          for (int oz = 0; oz <= 2 * RAD; ++oz) {
-            T ay[2][2][2] = {};   // [field][cy][cx]
-#pragma unroll
-            for (int oy = 0; oy <= 2 * RAD; ++oy) {
-              const int rowb = base + (oz * pn[1] + oy) * pn[0];
-              T sx[2][2] = {};    // [field][cx]
-#pragma unroll
-              for (int ox = 0; ox <= 2 * RAD; ++ox) {
-                const T v0 = patch[rowb + ox], v1 = patch[np + rowb + ox];
-                sx[0][0] += w[0][ox] * v0;
-                sx[0][1] += w[1][ox] * v0;
-                sx[1][0] += w[0][ox] * v1;
-                sx[1][1] += w[1][ox] * v1;
-              }
-#pragma unroll
-              for (int f = 0; f < 2; ++f)
-#pragma unroll
-                for (int cy = 0; cy < 2; ++cy) {
-                  ay[f][cy][0] += w[cy][oy] * sx[f][0];
-                  ay[f][cy][1] += w[cy][oy] * sx[f][1];
-                }
-            }
-#pragma unroll
-            for (int f = 0; f < 2; ++f)
-#pragma unroll
-              for (int a = 0; a < 8; ++a)
-                out[f][a >> 2][(a >> 1) & 1][a & 1] += w[a >> 2][oz] * ay[f][(a >> 1) & 1][a & 1];
-          }
-        }
-#pragma unroll
-        for (int a = 0; a < 8; ++a) {
-          const int cz = a >> 2, cy = (a >> 1) & 1, cx = a & 1;
-          const int gx = 2 * Px + cx, gy = 2 * Py + cy, gz = 2 * Pz + cz;   // unwrapped fine coordinates
-          if (gx < flo[0] || gx > fhi[0] || gy < flo[1] || gy > fhi[1] || gz < flo[2] || gz > fhi[2]) continue;
-          const long long dst = cell_index(B, A.gl, gx - B.lo[0], gy - B.lo[1], gz - B.lo[2]) + c0 * B.cs;
-          if (R.kind == GHOST_MIXED) {
-            const int wx = wrapi(gx, A.ndom), wy = wrapi(gy, A.ndom), wz = wrapi(gz, A.ndom);
-            const int own = A.bmap[((long long)(wz >> A.bshift) * A.nbd + (wy >> A.bshift)) * A.nbd + (wx >> A.bshift)];
-            if (own >= 0) {
-              const BoxDev Sb = A.boxes[own];
-              const long long src = cell_index(Sb, A.gl, wx - Sb.lo[0], wy - Sb.lo[1], wz - Sb.lo[2]) + c0 * Sb.cs;
-              A.y[dst] = A.y[src];
-              A.y[dst + B.cs] = A.y[src + Sb.cs];
-              continue;
-            }
-          }
-          if (!have_coarse) {
-            atomicCAS(A.err, 0, DERR_NESTING);
-            continue;
-          }
-          const T v0 = out[0][cz][cy][cx], v1 = out[1][cz][cy][cx];
-          if (v0 != v0) atomicCAS(A.err, 0, DERR_NESTING);   // the stencil met an uncovered (NaN) coarse cell
-          A.y[dst] = v0;
-          A.y[dst + B.cs] = v1;
-        }
-      }
-      __syncthreads();   // the patch is reused by the next pair or region
+      final_pass_any<T, RAD, NF>(a2, buf2, PASS2_MAX, d, geo, w0, w1, A, R, B, f0, have_coarse);
+      __syncthreads();   // the buffers are reused by the next fields or region
     }
   }
 }
 
 template <typename T>
-static slh_status ghosts_t(slh_ctx* c, int lev, int role, double alpha, int itype) {
+static slh_status ghosts_t(slh_ctx* c, int lev, int role, double alpha, int itype, bool with_pi) {
   Level& L = c->lev[lev];
   if (L.ngregions == 0) return SLH_OK;
   GhostArgs<T> A;
@@ -298,9 +362,13 @@ static slh_status ghosts_t(slh_ctx* c, int lev, int role, double alpha, int ityp
   }
   A.alpha = alpha;
   A.itype = itype;
-  A.npairs = c->ncomp == NCOMP_GW ? 4 : 1;
+  A.npairs = 0;
+  A.pc[A.npairs++] = 0;
+  if (with_pi) A.pc[A.npairs++] = 2;
+  if (c->ncomp == NCOMP_GW)
+    for (int q = 0; q < 3; ++q) A.pc[A.npairs++] = GW_U0 + 2 * q;
   A.err = c->d_err;
-  const int smem = 2 * PATCH_MAX * (int)sizeof(T);
+  const int smem = (sizeof(T) == 4 ? 2 : 1) * (PATCH_MAX + PASS1_MAX + PASS2_MAX) * (int)sizeof(T);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(ghost_region_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -320,11 +388,11 @@ static slh_status ghosts_t(slh_ctx* c, int lev, int role, double alpha, int ityp
   return SLH_OK;
 }
 
-slh_status launch_ghosts(slh_ctx* c, int lev, int role, double alpha, int itype) {
+slh_status launch_ghosts(slh_ctx* c, int lev, int role, double alpha, int itype, bool with_pi) {
   if (itype != 0 && itype != 2 && itype != 4)
     return fail(SLH_ERR_INVALID_ARG, "interp_type must be 0, 2 or 4 (got %d)", itype);
-  return c->prec == SLH_F64 ? ghosts_t<double>(c, lev, role, alpha, itype)
-                            : ghosts_t<float>(c, lev, role, alpha, itype);
+  return c->prec == SLH_F64 ? ghosts_t<double>(c, lev, role, alpha, itype, with_pi)
+                            : ghosts_t<float>(c, lev, role, alpha, itype, with_pi);
 }
 
 // ---------------------------------------------------------------------------

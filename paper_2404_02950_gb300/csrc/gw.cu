@@ -9,8 +9,8 @@
 // after the scalar stage kernel and with the same buffer roles, so that the
 // two together advance all 16 fields by classic RK4.
 //
-// Work decomposition: one CTA of GW_TX x GW_TY threads per (box, x0, y0, z0)
-// item, each thread a cell column marching up to GW_ZLEN planes in z.  The
+// Work decomposition: one CTA of COL_TX x COL_TY threads per (box, x0, y0, z0)
+// item, each thread a cell column marching up to COL_ZLEN planes in z.  The
 // stencil operands are plain global loads: x and y neighbours come from the
 // lines the CTA's own rows bring into L1, z neighbours from planes read a few
 // iterations earlier (L1/L2), so DRAM sees each value about once.
@@ -29,7 +29,9 @@ struct GwArgs {
   T* d;                     // increment accumulator
   T* out;                   // next stage input, or y_{n+1} at stage 4
   T* cc;                    // Kahan compensation (stage 4, FP32 form) or null
-  int stage;                // 1..4
+  int stage;                // 1..4 (classic RK4) or 1..3 (SSPRK3)
+  int ssp;                  // 1: low-storage SSPRK3 combine sa y_n + sb (Y + ha k)
+  double sa, sb;
   const double* eta_start;  // device eta at the start of the step
   double c_stage;           // c_s * dt
   int friction;
@@ -42,12 +44,12 @@ __device__ __forceinline__ constexpr int pair_i(int k) { return k < 3 ? k : (k =
 __device__ __forceinline__ constexpr int pair_j(int k) { return k < 3 ? k : (k == 3 ? 1 : 2); }
 
 template <typename T, int G>
-__global__ void __launch_bounds__(GW_TX * GW_TY, sizeof(T) == 4 ? 4 : 3) gw_stage_kernel(const GwArgs<T> A) {
+__global__ void __launch_bounds__(COL_TX * COL_TY, sizeof(T) == 4 ? 4 : 3) gw_stage_kernel(const GwArgs<T> A) {
   const int4 it = A.items[blockIdx.x];
   const BoxDev B = A.boxes[it.x];
   const int x = it.y + threadIdx.x, y = it.z + threadIdx.y;
   if (x >= B.n[0] || y >= B.n[1]) return;
-  const int z1 = min(it.w + GW_ZLEN, B.n[2]);
+  const int z1 = min(it.w + COL_ZLEN, B.n[2]);
   const double eta = *A.eta_start + A.c_stage;
   const T c_fric = (T)(A.friction ? 2.0 / eta : 0.0);
   const T ha = (T)A.ha, hb = (T)A.hb, idx = (T)A.inv_dx, idx2 = (T)A.inv_dx2;
@@ -61,6 +63,8 @@ __global__ void __launch_bounds__(GW_TX * GW_TY, sizeof(T) == 4 ? 4 : 3) gw_stag
   T* __restrict__ out = A.out;
   T* __restrict__ cc = A.cc;
   const int stage = A.stage;
+  const bool ssp = A.ssp != 0;
+  const T sa = (T)A.sa, sb = (T)A.sb;
   long long e = B.off + ((long long)(it.w + A.gl) * B.pny + (y + A.gl)) * B.pitch + x + XPAD;
 #pragma unroll 1
   for (int z = it.w; z < z1; ++z, e += sz) {
@@ -110,8 +114,10 @@ __global__ void __launch_bounds__(GW_TX * GW_TY, sizeof(T) == 4 ? 4 : 3) gw_stag
       if (stage >= 2) {
         yu = __ldg(yn + eu);
         yv = __ldg(yn + ev);
-        du = dd[eu];
-        dv = dd[ev];
+        if (!ssp) {
+          du = dd[eu];
+          dv = dd[ev];
+        }
       }
       if (stage == 4 && cc != nullptr) {
         cu = cc[eu];
@@ -146,7 +152,16 @@ __global__ void __launch_bounds__(GW_TX * GW_TY, sizeof(T) == 4 ? 4 : 3) gw_stag
       const T src = (T)2 * (g1i * g1j + g2i * g2j);
       const T ku = v;
       const T kv = ((-c_fric) * v + lap) + src;
-      if (stage == 1) {
+      if (ssp) {
+        const T fu = u0 + ha * ku, fv = v + ha * kv;
+        if (stage == 1) {
+          out[eu] = fu;
+          out[ev] = fv;
+        } else {
+          out[eu] = sa * yu + sb * fu;
+          out[ev] = sa * yv + sb * fv;
+        }
+      } else if (stage == 1) {
         out[eu] = u0 + ha * ku;
         out[ev] = v + ha * kv;
         dd[eu] = hb * ku;
@@ -174,10 +189,10 @@ __global__ void __launch_bounds__(GW_TX * GW_TY, sizeof(T) == 4 ? 4 : 3) gw_stag
 
 template <typename T>
 static slh_status gw_stage_t(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s) {
-  if (L.ngw_items == 0) return SLH_OK;
+  if (L.ncol_items == 0) return SLH_OK;
   GwArgs<T> A;
   A.boxes = L.d_boxes;
-  A.items = L.d_gw_items;
+  A.items = L.d_col_items;
   A.gl = c->g;
   A.in = static_cast<const T*>(L.buf[s.in_buf]);
   A.yn = static_cast<const T*>(L.buf[s.yn_buf]);
@@ -192,11 +207,14 @@ static slh_status gw_stage_t(slh_ctx* c, Level& L, const slh_eom_params& p, cons
   A.inv_dx2 = 1.0 / (L.dx * L.dx);
   A.ha = s.ha;
   A.hb = s.hb;
-  const dim3 block(GW_TX, GW_TY);
+  A.ssp = s.ssp;
+  A.sa = s.sa;
+  A.sb = s.sb;
+  const dim3 block(COL_TX, COL_TY);
   switch (p.lap_order) {
-    case 2: gw_stage_kernel<T, 1><<<L.ngw_items, block, 0, c->stream>>>(A); break;
-    case 4: gw_stage_kernel<T, 2><<<L.ngw_items, block, 0, c->stream>>>(A); break;
-    case 6: gw_stage_kernel<T, 3><<<L.ngw_items, block, 0, c->stream>>>(A); break;
+    case 2: gw_stage_kernel<T, 1><<<L.ncol_items, block, 0, c->stream>>>(A); break;
+    case 4: gw_stage_kernel<T, 2><<<L.ncol_items, block, 0, c->stream>>>(A); break;
+    case 6: gw_stage_kernel<T, 3><<<L.ncol_items, block, 0, c->stream>>>(A); break;
     default: return fail(SLH_ERR_INVALID_ARG, "lap_order must be 2, 4 or 6 (got %d)", p.lap_order);
   }
   SLH_CUDA(cudaGetLastError());

@@ -114,8 +114,8 @@ struct Level {
   int npieces = 0;
   long long nghost_cells = 0;
   Tile tile;                     // stage work items for the chosen tile variant
-  int4* d_gw_items = nullptr;    // GW stage work items (box, x0, y0, z0)
-  int ngw_items = 0;
+  int4* d_col_items = nullptr;   // column work items (box, x0, y0, z0) of the GW and dissipation kernels
+  int ncol_items = 0;
   std::map<unsigned long long, void*> tmaps;   // device tensor maps per (G, TX, TY)
   uint8_t* d_covered = nullptr;  // covered by the finer level, blocks of bf/2 cells
   int ncov = 0;
@@ -195,7 +195,9 @@ struct StageLaunch {
   int stage;            // 0 = diagnostics only, 1..4
   int in_buf, yn_buf, d_buf, out_buf, c_buf;   // physical buffer indices (-1: unused)
   double c_stage;       // c_s * dt
-  double ha, hb;        // a_{s+1} dt, b_s dt
+  double ha, hb;        // a_{s+1} dt, b_s dt (classic RK4); dt (SSPRK3)
+  int ssp;              // 1: low-storage SSPRK3 stage, out = sa y_n + sb (Y + ha k)
+  double sa, sb;
   uint8_t* tags;
   double* epart;        // per CTA x 4 (kin, grad, pot, pierced count)
   unsigned long long* tagcount;
@@ -212,14 +214,18 @@ void free_tmaps(Level& L);
 slh_status launch_expired_wait(slh_ctx* c, long long polls);
 
 slh_status launch_gw_stage(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s);
-constexpr int GW_TX = 32, GW_TY = 8, GW_ZLEN = 32;
+// Kreiss-Oliger dissipation of the stage input in_buf: out += cout Q, D += cd Q (psi, Pi)
+slh_status launch_ko(slh_ctx* c, Level& L, const slh_eom_params& p, int in_buf, int out_buf, int d_buf, double cout,
+                     double cd);
+constexpr int COL_TX = 32, COL_TY = 8, COL_ZLEN = 32;
 
-slh_status launch_ghosts(slh_ctx* c, int lev, int role, double alpha, int itype);
+slh_status launch_ghosts(slh_ctx* c, int lev, int role, double alpha, int itype, bool with_pi = false);
 slh_status launch_restrict(slh_ctx* c, int fine_lev);
 slh_status launch_energy_final(slh_ctx* c, const double* epart, int n, double* out4);
 slh_status launch_tag_blocks(slh_ctx* c, Level& L, const uint8_t* tags, const uint8_t* tags2, int nbuf, int r,
                              uint8_t* mask, int nb);
 slh_status launch_shadow(slh_ctx* c, slh_ctx* shadow, bool compare);
+slh_status gw_spectrum_impl(slh_ctx* c, int ptype, std::vector<double>* bins, std::vector<unsigned long long>* counts);
 slh_status launch_time_begin(slh_ctx* c, int lev, int sub, double dt_l);
 slh_status launch_regrid_fill(slh_ctx* c, int lev, Level& fresh, Level* old);
 

@@ -43,7 +43,9 @@ struct StageArgs {
   const CUtensorMap* tmaps; // [box][buffer][kind 0 = halo'd psi, 1 = pointwise]
   int in_buf, yn_buf, d_buf, out_buf, c_buf;   // physical buffer indices (-1: none)
   T* bufs[SLH_NBUF];
-  int stage;                // 0 = diagnostics only, 1..4
+  int stage;                // 0 = diagnostics only, 1..4 (classic RK4) or 1..3 (SSPRK3)
+  int ssp;                  // 1: low-storage SSPRK3 combine a y_n + b (Y + h k)
+  double sa, sb;            // its a_s, b_s (h is ha)
   const double* eta_start;  // device eta at the start of the step (or current eta)
   double c_stage;           // c_s * dt
   double lambda, a;
@@ -195,7 +197,8 @@ __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stag
   const int stage = A.stage;
   const bool has_c = A.c_buf >= 0;
   // pointwise boxes this stage needs: Pi always; y_n and D from stage 2; C in stage 4
-  const int npw = stage >= 2 ? ((stage == 4 && has_c) ? 7 : 5) : 1;
+  const bool ssp = A.ssp != 0;
+  const int npw = stage >= 2 ? (ssp ? 3 : ((stage == 4 && has_c) ? 7 : 5)) : 1;
   const unsigned step_bytes_pw = (unsigned)(npw * GE::PW2);
 
   if (tid == 0) {
@@ -225,6 +228,8 @@ __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stag
       if (stage >= 2) {
         tma_load4(smem_u32(dst + 1 * GE::PW2), mb + 2 * A.yn_buf + 1, xp, yp, zp, 0, bar);
         tma_load4(smem_u32(dst + 2 * GE::PW2), mb + 2 * A.yn_buf + 1, xp, yp, zp, 2, bar);
+      }
+      if (stage >= 2 && !ssp) {
         tma_load4(smem_u32(dst + 3 * GE::PW2), mb + 2 * A.d_buf + 1, xp, yp, zp, 0, bar);
         tma_load4(smem_u32(dst + 4 * GE::PW2), mb + 2 * A.d_buf + 1, xp, yp, zp, 2, bar);
         if (stage == 4 && has_c) {
@@ -356,7 +361,23 @@ __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stag
       const T kP2 = (-c_fric) * P2 + l2 - p2 * pot;
       const long long e0 = B.off + (long long)(z + gl) * B.pny * B.pitch + (long long)(y + gl) * B.pitch + x + XPAD;
       const long long cs = B.cs;
-      if (stage == 1) {
+      if (ssp) {
+        // low-storage SSPRK3: out = a_s y_n + b_s (Y + h k), Y + h k alone at stage 1
+        T* yo = A.bufs[A.out_buf];
+        const T f0 = p1 + ha * P1, f1 = p2 + ha * P2, f2 = P1 + ha * kP1, f3 = P2 + ha * kP2;
+        if (stage == 1) {
+          yo[e0] = f0;
+          yo[e0 + cs] = f1;
+          yo[e0 + 2 * cs] = f2;
+          yo[e0 + 3 * cs] = f3;
+        } else {
+          const T sa = (T)A.sa, sb = (T)A.sb;
+          yo[e0] = sa * PWv(1, 0) + sb * f0;
+          yo[e0 + cs] = sa * PWv(1, 1) + sb * f1;
+          yo[e0 + 2 * cs] = sa * PWv(2, 0) + sb * f2;
+          yo[e0 + 3 * cs] = sa * PWv(2, 1) + sb * f3;
+        }
+      } else if (stage == 1) {
         T* yo = A.bufs[A.out_buf];
         T* dd = A.bufs[A.d_buf];
         yo[e0] = p1 + ha * P1;
@@ -660,6 +681,9 @@ static slh_status launch_v(slh_ctx* c, Level& L, const slh_eom_params& p, const 
   A.eta_power = p.eta_power;
   A.inv_dx2 = 1.0 / (L.dx * L.dx);
   A.ha = s.ha;
+  A.ssp = s.ssp;
+  A.sa = s.sa;
+  A.sb = s.sb;
   A.hb = s.hb;
   A.tags = s.tags;
   A.epart = s.epart;

@@ -6,7 +6,8 @@ from oracle.eom import EOMParams as OParams
 
 
 def oparams(p: slh.EOMParams) -> OParams:
-    return OParams(lam=p.lam, a=p.a, friction=p.friction, eta_power=p.eta_power, order=p.order)
+    return OParams(lam=p.lam, a=p.a, friction=p.friction, eta_power=p.eta_power, order=p.order,
+                   ko_order=p.ko_order, ko_eps=p.ko_eps)
 
 
 def rel_l2(a, b):

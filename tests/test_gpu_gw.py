@@ -1,14 +1,16 @@
 """Gravitational-wave tensor on the GPU vs the oracle (Sec. 5, oracle/gw.py):
 the 16-field classic RK4 step on a periodic level (FP64 within 1e-12 relative
 L2 per field after 5 steps for Laplacian orders 2/4/6; FP32 + Kahan within
-1e-4), and the 16-field hierarchy (ghost fill of psi and u by copy and
-prolongation, restriction and regrid of every field)."""
+1e-4), the 16-field hierarchy (ghost fill of psi and u by copy and
+prolongation, restriction and regrid of every field), and the spectrum of
+Sec. 7.4 (oracle/gw_spectrum.py)."""
 import numpy as np
 import pytest
 
 import paper_2404_02950_gb300 as slh
 from oracle import amr as oamr
 from oracle import gw as ogw
+from oracle import gw_spectrum as ogs
 from paper_2404_02950_gb300 import inputs
 from tests.helpers import oparams, rel_l2
 
@@ -146,3 +148,52 @@ def test_hierarchy_subcycled_step_and_regrid_match_oracle():
     oh.step()
     h.advance(DT, p)
     _compare(h, oh, 1e-12)
+
+
+# ---------------------------------------------------------------------------
+# spectrum (Sec. 7.4)
+
+
+@pytest.mark.parametrize("ptype", [1, 2])
+@pytest.mark.parametrize("boxes", [FULL, [((0, 0, 0), (15, 31, 31)), ((16, 0, 0), (31, 31, 31))]])
+def test_spectrum_matches_oracle_f64(ptype, boxes):
+    y = _initial()
+    h = slh.Hierarchy(N, DX, nghost=G, bf=BF, prec="f64", max_levels=1, gw=True)
+    h.init_level(0, boxes)
+    h.set_state(0, slh.dense_from_boxes(y, boxes))
+    n2, g = h.gw_spectrum(ptype)
+    en2, eg = ogs.spectrum(y[10:16], DX, ptype)
+    assert np.array_equal(n2, en2)
+    assert np.max(np.abs(g - eg)) <= 1e-12 * np.max(np.abs(eg))
+
+
+def test_spectrum_f32_and_tt_wave():
+    """FP32 storage: within 1e-5 of the FP64 oracle's largest bin; a
+    transverse-traceless wave lands in its own bin with G = e:e / 2."""
+    y = _initial()
+    h = slh.Hierarchy(N, DX, nghost=G, bf=BF, prec="f32", max_levels=1, gw=True)
+    h.init_level(0, FULL)
+    h.set_state(0, slh.dense_from_boxes([a.astype(np.float32) for a in y], FULL))
+    n2, g = h.gw_spectrum(2)
+    en2, eg = ogs.spectrum(y[10:16], DX, 2)
+    assert np.array_equal(n2, en2) and np.max(np.abs(g - eg)) <= 1e-5 * np.max(np.abs(eg))
+    ax = np.arange(N)
+    Z, Y, X = np.meshgrid(ax, ax, ax, indexing="ij")
+    c = np.cos(2 * np.pi * 3 * X / N)
+    e = {(1, 1): 0.3, (2, 2): -0.3, (1, 2): 0.2}
+    v = [e.get((i, j), 0.0) * c for i, j in ogs.PAIRS]
+    z = np.zeros_like(c)
+    h2 = slh.Hierarchy(N, DX, nghost=G, bf=BF, prec="f64", max_levels=1, gw=True)
+    h2.init_level(0, FULL)
+    h2.set_state(0, slh.dense_from_boxes([z, z, z, z] + [z] * 6 + v, FULL))
+    n2, g = h2.gw_spectrum(2)
+    assert np.isclose(g[n2 == 9][0], 0.5 * (0.09 + 0.09 + 2 * 0.04), rtol=1e-12)
+    assert np.max(np.abs(g[n2 != 9])) < 1e-15
+
+
+def test_spectrum_needs_tensor_fields():
+    h = slh.Hierarchy(N, DX, nghost=G, bf=BF, prec="f64", max_levels=1)
+    h.init_level(0, FULL)
+    with pytest.raises(slh.SlhError) as e:
+        h.gw_spectrum(2)
+    assert e.value.code == -7
