@@ -1,0 +1,82 @@
+"""Pins of the oracle's local regrid (Sec. 2.3, oracle/local_regrid.py):
+properties the paper fixes, checked cell by cell on random hierarchies."""
+import numpy as np
+import pytest
+
+from oracle import local_regrid as olr
+
+
+def _cells(boxes, n):
+    m = np.zeros((n, n, n), dtype=np.int32)
+    for lo, hi in boxes:
+        m[lo[2]:hi[2] + 1, lo[1]:hi[1] + 1, lo[0]:hi[0] + 1] += 1
+    return m
+
+
+def _nested(fine_boxes, coarse_boxes, nc, r):
+    """Every fine box's coarse footprint grown by r coarse cells (periodic)
+    lies in the coarse level: checked cell by cell."""
+    cov = _cells(coarse_boxes, nc) > 0
+    for lo, hi in fine_boxes:
+        for z in range(lo[2] // 2 - r, (hi[2] + 1) // 2 + r):
+            for y in range(lo[1] // 2 - r, (hi[1] + 1) // 2 + r):
+                for x in range(lo[0] // 2 - r, (hi[0] + 1) // 2 + r):
+                    if not cov[z % nc, y % nc, x % nc]:
+                        return False
+    return True
+
+
+def _random_case(seed, n0=16, bf=4):
+    rng = np.random.default_rng(seed)
+    r = bf // 2
+    L = 3
+    boxes = [[((0, 0, 0), (n0 - 1,) * 3)]]
+    # level 1: a few bf-aligned boxes well inside level 0; level 2 nested in level 1
+    lo1 = rng.integers(1, 3, size=3) * bf
+    boxes.append([(tuple(int(v) for v in lo1), tuple(int(v + 2 * bf - 1) for v in lo1))])
+    c = [(lo1[d] + bf) * 2 for d in range(3)]   # inside level 1, away from its edge
+    boxes.append([(tuple(c), tuple(v + bf - 1 for v in c))])
+    assert _nested(boxes[1], boxes[0], n0, r) and _nested(boxes[2], boxes[1], 2 * n0, r)
+    masks = []
+    for l in range(L - 1):
+        nb = (n0 << l) // r
+        masks.append(rng.random((nb, nb, nb)) < 0.03)
+    return boxes, masks, n0, bf
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_grows_covers_and_nests(seed):
+    boxes, masks, n0, bf = _random_case(seed)
+    r = bf // 2
+    out = olr.local_regrid(boxes, n0, bf, masks)
+    for l in range(len(boxes)):
+        n = n0 << l
+        assert out[l][:len(boxes[l])] == boxes[l]                 # old boxes kept as they are
+        cov = _cells(out[l], n)
+        assert cov.max() <= 1                                      # no overlap
+        assert np.all(cov[_cells(boxes[l], n) > 0] == 1)           # only grows
+        for lo, hi in out[l][len(boxes[l]):]:
+            assert all(lo[d] % bf == 0 and (hi[d] + 1) % bf == 0 for d in range(3))
+    for l in range(len(boxes) - 1):
+        fine = _cells(out[l + 1], n0 << (l + 1)) > 0
+        nb = masks[l].shape[0]
+        for bz, by, bx in zip(*np.nonzero(masks[l])):
+            # the r-block of level l = a bf-block of level l+1
+            blk = fine[bz * bf:(bz + 1) * bf, by * bf:(by + 1) * bf, bx * bf:(bx + 1) * bf]
+            assert blk.all(), (l, bz, by, bx)
+        assert nb == (n0 << l) // r
+    for l in range(1, len(boxes)):
+        assert _nested(out[l], out[l - 1], n0 << (l - 1), r), l
+
+
+def test_no_change_when_covered_and_idempotent():
+    boxes, masks, n0, bf = _random_case(7)
+    none = [np.zeros_like(m) for m in masks]
+    assert olr.local_regrid(boxes, n0, bf, none) == boxes
+    out = olr.local_regrid(boxes, n0, bf, masks)
+    assert olr.local_regrid(out, n0, bf, masks) == out
+    # tags inside the already refined region change nothing
+    inner = [np.zeros_like(m) for m in masks]
+    lo, hi = boxes[1][0]
+    inner[0][lo[2] // bf, lo[1] // bf, lo[0] // bf] = True      # level-1 cell c lies in level-0 block c // bf
+    assert olr.local_regrid(boxes, n0, bf, inner) == boxes
