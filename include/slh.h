@@ -332,6 +332,25 @@ slh_status slh_regrid_boxes(const uint8_t* tags_host, const int32_t dims[3],
                             const slh_box* parent, int32_t nparent, slh_box* out, int32_t cap,
                             int32_t* nout);
 
+/* Host-only local regrid (Sec. 2.3): keep every level's boxes and only add.
+ * boxes: the current boxes of levels 0..nlevels-1, concatenated (nboxes[l]
+ * per level; level 0 covers the domain of n0 cells); masks[l] (l < nlevels-1,
+ * NULL = no tags): the block mask of level l as slh_tag_blocks returns it
+ * (grown tags in blocks of blocking_factor/2 cells of l, x fastest).
+ * Steps: a block of masks[l] not covered by level l+1 becomes a new block of
+ * blocking_factor cells of level l+1; then, finest level first, every block
+ * of level j needs the 3x3x3 blocks of blocking_factor/2 cells of level j-1
+ * around it (periodic) inside level j-1, and the missing blocks of
+ * blocking_factor cells are added to level j-1 (level 0 never changes).
+ * out receives each level's old boxes in their order followed by its new
+ * blocks merged into x-runs (ordered by z, y, x), levels concatenated;
+ * out_nboxes[l] the count per level.  cap = capacity of out (entries).
+ * Errors: INVALID_ARG, OUT_OF_RANGE (cap too small; out_nboxes filled). */
+slh_status slh_local_regrid_boxes(int32_t nlevels, int32_t n0, int32_t blocking_factor,
+                                  const uint8_t* const* masks, const slh_box* boxes,
+                                  const int32_t* nboxes, slh_box* out, int32_t cap,
+                                  int32_t* out_nboxes);
+
 /* Energy and string length of the hierarchy over the cells not covered by
  * a finer level, each level at its own eta:
  *   out[0] = sum 1/2 (Pi1^2 + Pi2^2) dx^3

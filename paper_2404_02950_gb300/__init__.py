@@ -48,6 +48,7 @@ ABI_SYMBOLS = (
     "slh_reduce_energy", "slh_sync", "slh_profile", "slh_profile_read", "slh_set_tile", "slh_autotune",
     "slh_energy_noalloc", "slh_regrid_level", "slh_selftest_wait_timeout",
     "slh_set_tagging", "slh_shadow_init", "slh_shadow_compare", "slh_tee_tags", "slh_gw_spectrum",
+    "slh_local_regrid_boxes",
 )
 
 
@@ -133,6 +134,7 @@ def lib():
         "slh_shadow_compare": (i32, [vp, vp]),
         "slh_tee_tags": (i32, [vp, i32, vp, i32]),
         "slh_gw_spectrum": (i32, [vp, i32, P(i64), P(dbl), i32, P(i32)]),
+        "slh_local_regrid_boxes": (i32, [i32, i32, i32, P(vp), P(slh_box), P(i32), P(slh_box), i32, P(i32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -189,6 +191,33 @@ def slh_regrid_boxes(tags, blocking_factor, n_error_buf, max_box, parent=None):
             continue
         _check(st)
         return [(tuple(out[i].lo), tuple(out[i].hi)) for i in range(nout.value)]
+
+
+def slh_local_regrid_boxes(level_boxes, n0, blocking_factor, masks):
+    """Local regrid (Sec. 2.3), host only: every level's boxes kept, new blocks
+    of level l+1 where the block mask of level l (grown tags in blocks of
+    blocking_factor/2 cells, as from slh_tag_blocks) is not covered by level
+    l+1, coarser levels grown where nesting needs it.  Returns the new box
+    lists (old boxes first)."""
+    L = len(level_boxes)
+    flat = [b for lb in level_boxes for b in lb]
+    nb = (ctypes.c_int32 * L)(*[len(lb) for lb in level_boxes])
+    keep = [np.ascontiguousarray(np.asarray(m, dtype=np.uint8)) for m in masks]
+    mp = (ctypes.c_void_p * max(1, L))(*([m.ctypes.data for m in keep] + [None] * (max(1, L) - len(keep))))
+    cap = max(64, 4 * len(flat))
+    counts = (ctypes.c_int32 * L)()
+    while True:
+        out = (slh_box * cap)()
+        st = lib().slh_local_regrid_boxes(L, n0, blocking_factor, mp, _boxes(flat), nb, out, cap, counts)
+        if st == -2 and sum(counts) > cap:
+            cap = sum(counts)
+            continue
+        _check(st)
+        res, o = [], 0
+        for l in range(L):
+            res.append([(tuple(out[o + i].lo), tuple(out[o + i].hi)) for i in range(counts[l])])
+            o += counts[l]
+        return res
 
 
 def slh_energy_noalloc(fields_dev, n, dx, eta, params: EOMParams, out_dev, stream=None):
@@ -318,14 +347,14 @@ class Hierarchy:
         self.levels[lev] = dict(boxes=list(boxes), bufs=bufs, tags=tags, nvalid=nvalid, total=total, steps=0)
         return self.levels[lev]
 
-    def regrid(self, max_levels, n_error_buf, max_box, interp_type=4):
-        """Global regrid of every level from level 0 upwards (Sec. 2.2-2.3):
+    def regrid(self, max_levels, n_error_buf, max_box, interp_type=4, start=0):
+        """Global regrid of every level above ``start`` (Sec. 2.2-2.3):
         tags of level l grown by n_error_buf and coarsened to blocks on the
         device (slh_tag_blocks), clustered on the host (slh_regrid_boxes, in
         block units), then slh_regrid_level(l + 1).  Returns the box lists."""
         r = self.bf // 2
         out = []
-        for l in range(0, max_levels - 1):
+        for l in range(start, max_levels - 1):
             if l not in self.levels:
                 break
             mask = self.tag_blocks(l, n_error_buf)
@@ -341,6 +370,54 @@ class Hierarchy:
             if not boxes:
                 break
         return out
+
+    def regrid_local(self, n_error_buf, interp_type=4):
+        """Local regrid of every level (Sec. 2.3): the block masks of the
+        current levels (slh_tag_blocks), the added blocks from
+        slh_local_regrid_boxes, then slh_regrid_level from the lowest changed
+        level up (copy where the old boxes cover, prolong elsewhere).
+        Returns the cells added per level."""
+        L = len(self.levels)
+        if L < 2:
+            return [0] * L
+        cur = [list(self.levels[l]["boxes"]) for l in range(L)]
+        masks = [self.tag_blocks(l, n_error_buf) for l in range(L - 1)]
+        new = slh_local_regrid_boxes(cur, self.n0, self.bf, masks)
+        vol = lambda bl: sum((hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1) for lo, hi in bl)
+        added = [vol(new[l]) - vol(cur[l]) for l in range(L)]
+        first = next((l for l in range(1, L) if added[l] > 0), None)
+        if first is not None:
+            for l in range(first, L):
+                self.regrid_level(l, new[l], interp_type)
+        return added
+
+    def regrid_auto(self, max_levels, n_error_buf, max_box, interp_type=4, eps_strong=0.1, eps_weak=0.05,
+                    max_local=None):
+        """Local regrids with the paper's fallback (Sec. 2.3): the volume each
+        level gained by local regrids since the last global regrid, as a
+        fraction of its volume then, is tracked; once some level reaches
+        eps_strong (or after max_local local regrids) the next regrid is a
+        global one, from the lowest level whose fraction reached eps_weak.
+        Returns ("global" | "local", per-level info)."""
+        st = getattr(self, "_auto", None)
+        L = len(self.levels)
+        if st is None or len(st["base"]) != L:
+            st = self._auto = {"base": [max(1, self.levels[l]["nvalid"]) for l in range(L)], "added": [0] * L,
+                               "count": 0, "pending": None}
+        if st["pending"] is not None or L < max_levels:
+            start = st["pending"] if st["pending"] is not None else 0
+            boxes = self.regrid(max_levels, n_error_buf, max_box, interp_type, start=start)
+            self._auto = None
+            return "global", boxes
+        added = self.regrid_local(n_error_buf, interp_type)
+        st["count"] += 1
+        for l in range(L):
+            st["added"][l] += added[l]
+        frac = [st["added"][l] / st["base"][l] for l in range(L)]
+        if any(f >= eps_strong for f in frac) or (max_local is not None and st["count"] >= max_local):
+            weak = [l for l in range(1, L) if frac[l] >= eps_weak]
+            st["pending"] = (min(weak) - 1) if weak else 0
+        return "local", frac
 
     def set_state(self, lev, dense):
         """dense: host numpy array (or CUDA tensor) in the dense valid-cell

@@ -277,3 +277,137 @@ extern "C" slh_status slh_regrid_boxes(const uint8_t* tags_host, const int32_t d
   for (size_t i = 0; i < boxes.size(); ++i) out[i] = boxes[i];
   return SLH_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Local regrid (Sec. 2.3): keep every level's boxes, add blocks of the finer
+// level where the grown tags are not yet covered by it, add blocks to the
+// coarser levels where nesting needs them, never remove any.
+
+namespace slh {
+
+namespace {
+
+struct BlockGrid {
+  int n = 0;
+  std::vector<uint8_t> v;
+  explicit BlockGrid(int nn) : n(nn), v((size_t)nn * nn * nn, 0) {}
+  uint8_t& at(int x, int y, int z) { return v[((size_t)z * n + y) * n + x]; }
+  uint8_t at(int x, int y, int z) const { return v[((size_t)z * n + y) * n + x]; }
+};
+
+// blocks of `unit` cells inside the boxes (boxes given in cells of the grid's level)
+slh_status cover(const slh_box* b, int nb, int unit, int shift, BlockGrid* g, const char* what) {
+  for (int i = 0; i < nb; ++i) {
+    int lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = b[i].lo[d] >> shift;
+      hi[d] = ((b[i].hi[d] + 1) >> shift) - 1;
+      if (lo[d] % unit || (hi[d] + 1) % unit || lo[d] < 0 || hi[d] >= g->n * unit || hi[d] < lo[d])
+        return fail(SLH_ERR_INVALID_ARG, "local_regrid: %s box %d not aligned or outside the domain", what, i);
+    }
+    for (int z = lo[2] / unit; z <= hi[2] / unit; ++z)
+      for (int y = lo[1] / unit; y <= hi[1] / unit; ++y)
+        for (int x = lo[0] / unit; x <= hi[0] / unit; ++x) g->at(x, y, z) = 1;
+  }
+  return SLH_OK;
+}
+
+}  // namespace
+
+slh_status local_regrid_impl(int L, int n0, int bf, const uint8_t* const* masks, const slh_box* boxes,
+                             const int32_t* nboxes, std::vector<std::vector<slh_box>>* out) {
+  const int r = bf / 2;
+  std::vector<BlockGrid> have, add;
+  std::vector<int> off(L + 1, 0);
+  for (int l = 0; l < L; ++l) {
+    if (nboxes[l] < 0) return fail(SLH_ERR_INVALID_ARG, "local_regrid: negative box count");
+    off[l + 1] = off[l] + nboxes[l];
+    const int n = n0 << l;
+    have.emplace_back(n / bf);
+    add.emplace_back(n / bf);
+    slh_status st = cover(boxes + off[l], nboxes[l], bf, 0, &have[l], "level");
+    if (st != SLH_OK) return st;
+  }
+  // 1-3: uncovered grown tags -> new blocks of the finer level
+  for (int l = 0; l + 1 < L; ++l) {
+    const int nr = (n0 << l) / r;   // r-blocks of l = bf-blocks of l+1
+    BlockGrid C(nr);
+    slh_status st = cover(boxes + off[l + 1], nboxes[l + 1], r, 1, &C, "finer");
+    if (st != SLH_OK) return st;
+    if (!masks || !masks[l]) continue;
+    for (size_t i = 0; i < C.v.size(); ++i)
+      if (masks[l][i] && !C.v[i]) add[l + 1].v[i] = 1;
+  }
+  // 4: nesting closure, finest first
+  for (int j = L - 1; j >= 1; --j) {
+    const int nr = have[j].n;       // bf-blocks of j = r-blocks of j-1
+    for (int z = 0; z < nr; ++z)
+      for (int y = 0; y < nr; ++y)
+        for (int x = 0; x < nr; ++x) {
+          if (!have[j].at(x, y, z) && !add[j].at(x, y, z)) continue;
+          for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+              for (int dx = -1; dx <= 1; ++dx) {
+                const int wx = ((x + dx) % nr + nr) % nr, wy = ((y + dy) % nr + nr) % nr, wz = ((z + dz) % nr + nr) % nr;
+                const int cx = wx / 2, cy = wy / 2, cz = wz / 2;   // bf-block of level j-1
+                if (!have[j - 1].at(cx, cy, cz)) add[j - 1].at(cx, cy, cz) = 1;
+              }
+        }
+  }
+  std::fill(add[0].v.begin(), add[0].v.end(), 0);
+  // 5: old boxes, then x-runs of the new blocks ordered by (z, y, x)
+  out->assign(L, {});
+  for (int l = 0; l < L; ++l) {
+    std::vector<slh_box>& o = (*out)[l];
+    o.assign(boxes + off[l], boxes + off[l + 1]);
+    const int nb = add[l].n;
+    for (int z = 0; z < nb; ++z)
+      for (int y = 0; y < nb; ++y) {
+        int x = 0;
+        while (x < nb) {
+          if (!add[l].at(x, y, z) || have[l].at(x, y, z)) {
+            ++x;
+            continue;
+          }
+          const int x0 = x;
+          while (x < nb && add[l].at(x, y, z) && !have[l].at(x, y, z)) ++x;
+          slh_box b;
+          b.lo[0] = x0 * bf;
+          b.lo[1] = y * bf;
+          b.lo[2] = z * bf;
+          b.hi[0] = x * bf - 1;
+          b.hi[1] = (y + 1) * bf - 1;
+          b.hi[2] = (z + 1) * bf - 1;
+          o.push_back(b);
+        }
+      }
+  }
+  return SLH_OK;
+}
+
+}  // namespace slh
+
+extern "C" slh_status slh_local_regrid_boxes(int32_t nlevels, int32_t n0, int32_t blocking_factor,
+                                             const uint8_t* const* masks, const slh_box* boxes,
+                                             const int32_t* nboxes, slh_box* out, int32_t cap,
+                                             int32_t* out_nboxes) {
+  if (nlevels < 1 || nlevels > 8 || !boxes || !nboxes || !out_nboxes)
+    return slh::fail(SLH_ERR_INVALID_ARG, "local_regrid: bad arguments");
+  if (blocking_factor < 2 || (blocking_factor & (blocking_factor - 1)))
+    return slh::fail(SLH_ERR_INVALID_ARG, "local_regrid: blocking factor must be a power of two >= 2");
+  if (n0 < blocking_factor || n0 % blocking_factor)
+    return slh::fail(SLH_ERR_INVALID_ARG, "local_regrid: n0 must be a positive multiple of the blocking factor");
+  std::vector<std::vector<slh_box>> res;
+  slh_status st = slh::local_regrid_impl(nlevels, n0, blocking_factor, masks, boxes, nboxes, &res);
+  if (st != SLH_OK) return st;
+  int total = 0;
+  for (int l = 0; l < nlevels; ++l) {
+    out_nboxes[l] = (int32_t)res[l].size();
+    total += (int)res[l].size();
+  }
+  if (total > cap || !out) return slh::fail(SLH_ERR_OUT_OF_RANGE, "local_regrid: %d boxes exceed capacity %d", total, cap);
+  int o = 0;
+  for (int l = 0; l < nlevels; ++l)
+    for (const slh_box& b : res[l]) out[o++] = b;
+  return SLH_OK;
+}

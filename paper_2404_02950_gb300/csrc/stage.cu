@@ -253,9 +253,17 @@ __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stag
     }
   }
 
-  double s_kin = 0.0, s_grad = 0.0, s_pot = 0.0;
+  // per-thread energy partials in the field precision with a compensation
+  // term each (Kahan), so that no FP64 work remains inside the plane loop
+  // (FP64 runs at 1/64 of the FP32 rate here); FP64 from the block reduction on
   unsigned long long n_pierced = 0, n_tagged = 0;
-  T i_kin = 0, i_grad = 0, i_pot = 0;
+  T i_kin = 0, i_grad = 0, i_pot = 0, c_kin = 0, c_grad = 0, c_pot_ = 0;
+  auto kahan = [](T& sum, T& comp, T v) {
+    const T y_ = v - comp;
+    const T t_ = sum + y_;
+    comp = (t_ - sum) - y_;
+    sum = t_;
+  };
   int cur_box = -1;
   BoxDev B;
   bool aborted = false;
@@ -319,6 +327,7 @@ __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stag
     const int tcell = thread_off - (G * SXL + 4);
     auto S = [&](int c, int dx, int dy, int dz) -> T { return psi[plb[dz + G] + tcell + c * PLANE + dy * SXL + dx]; };
     T p1 = 0, p2 = 0, l1 = 0, l2 = 0, P1 = 0, P2 = 0, r2 = 0;
+    bool cell_cov = false;   // this cell is covered by a finer level (no energy, no string length)
     if (compute && active) {
       const T* pwp = reinterpret_cast<const T*>(pw_base + pslot * GE::PW_STRIDE);
       auto PWv = [&](int box, int comp) -> T { return pwp[box * 2 * TXY + comp * TXY + ty * TX + tx]; };
@@ -359,6 +368,25 @@ __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stag
       const T pot = c_pot * (r2 - (T)1) + a_c;
       const T kP1 = (-c_fric) * P1 + l1 - p1 * pot;
       const T kP2 = (-c_fric) * P2 + l2 - p2 * pot;
+      if (DIAG && A.epart != nullptr) {
+        // energy of the stage input, accumulated where its terms are formed
+        // (keeping them live across the winding phases below costs more than
+        // the winding itself); the pierced-plaquette count follows the masks
+        bool cov = false;
+        if (A.covered != nullptr) {
+          const int gx = (B.lo[0] + x) >> A.cov_shift, gy = (B.lo[1] + y) >> A.cov_shift,
+                    gz = (B.lo[2] + z) >> A.cov_shift;
+          cov = A.covered[((long long)gz * A.cov_nb + gy) * A.cov_nb + gx] != 0;
+        }
+        if (!cov) {
+          const T dd = r2 - (T)1;
+          kahan(i_kin, c_kin, (T)0.5 * (P1 * P1 + P2 * P2));
+          kahan(i_grad, c_grad, (T)(-0.5) * (p1 * l1 + p2 * l2));
+          kahan(i_pot, c_pot_, ((T)0.25 * c_pot) * (dd * dd) + ((T)0.5 * a_c) * r2);
+        } else {
+          cell_cov = true;
+        }
+      }
       const long long e0 = B.off + (long long)(z + gl) * B.pny * B.pitch + (long long)(y + gl) * B.pitch + x + XPAD;
       const long long cs = B.cs;
       if (ssp) {
@@ -487,29 +515,8 @@ __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stag
           A.tags[B.voff + ((long long)z * B.n[1] + y) * B.n[0] + x] = tagged ? 1 : 0;
           n_tagged += tagged ? 1 : 0;
         }
-        if (A.epart != nullptr) {
-          bool cov = false;
-          if (A.covered != nullptr) {
-            const int gx = (B.lo[0] + x) >> A.cov_shift, gy = (B.lo[1] + y) >> A.cov_shift,
-                      gz = (B.lo[2] + z) >> A.cov_shift;
-            cov = A.covered[((long long)gz * A.cov_nb + gy) * A.cov_nb + gx] != 0;
-          }
-          if (!cov) {
-            const T dd = r2 - (T)1;
-            i_kin += (T)0.5 * (P1 * P1 + P2 * P2);
-            i_grad += (T)(-0.5) * (p1 * l1 + p2 * l2);
-            i_pot += ((T)0.25 * c_pot) * (dd * dd) + ((T)0.5 * a_c) * r2;
-            n_pierced += __popc(m00);
-          }
-        }
+        if (A.epart != nullptr && !cell_cov) n_pierced += __popc(m00);
       }
-    }
-    const bool last_of_item = (cc.q == cc.z1 + G - 1);
-    if (DIAG && last_of_item) {
-      s_kin += (double)i_kin;
-      s_grad += (double)i_grad;
-      s_pot += (double)i_pot;
-      i_kin = i_grad = i_pot = 0;
     }
     if (__syncthreads_or(!ok)) {
       aborted = true;
@@ -538,7 +545,8 @@ __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stag
     constexpr int NW = TXY / 32;
     __shared__ double red[4][NW];
     __shared__ unsigned long long redt[NW];
-    double v0 = s_kin, v1 = s_grad, v2 = s_pot, v3 = (double)n_pierced;
+    double v0 = (double)i_kin - (double)c_kin, v1 = (double)i_grad - (double)c_grad,
+           v2 = (double)i_pot - (double)c_pot_, v3 = (double)n_pierced;
     unsigned long long vt = n_tagged;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

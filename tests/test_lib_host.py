@@ -159,3 +159,17 @@ def test_float_reciprocal_index_split_is_exact():
             j = ((rem.astype(f32) + f32(0.5)) * (f32(1.0) / f32(e0))).astype(np.int64)
             i = rem - j * e0
             assert np.array_equal(k, t // e01) and np.array_equal(j, (t // e0) % e1) and np.array_equal(i, t % e0), (e0, e1)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_local_regrid_matches_oracle(seed):
+    """C++ local regrid (slh_local_regrid_boxes) vs the oracle: identical box
+    lists on random three-level hierarchies and random block masks."""
+    from oracle import local_regrid as olr
+    from tests.test_oracle_local_regrid import _random_case
+    boxes, masks, n0, bf = _random_case(seed)
+    exp = olr.local_regrid(boxes, n0, bf, masks)
+    got = slh.slh_local_regrid_boxes(boxes, n0, bf, masks)
+    norm = lambda L: [[(tuple(int(v) for v in lo), tuple(int(v) for v in hi)) for lo, hi in lb] for lb in L]
+    assert norm(got) == norm(exp)
+    assert any(len(g) > len(b) for g, b in zip(got, boxes)) or not any(m.any() for m in masks)
