@@ -127,3 +127,51 @@ def test_regrid_errors_and_removal():
     h.regrid_level(2, [])                                     # remove it
     h.advance(DT0, slh.EOMParams(order=4))
     assert sorted(h.levels) == [0, 1]
+
+
+def test_local_regrid_matches_oracle():
+    """Local regrid (Sec. 2.3) on the GPU hierarchy: the block masks of the
+    device tags, the host box update (slh_local_regrid_boxes) and the level
+    rebuild, against the oracle's local regrid and data transfer."""
+    from oracle import local_regrid as olr
+    p = slh.EOMParams(order=4, interp_type=4)
+    y0 = inputs.string_loop(N0, 4.0, 2.0, DX0)
+    oh = oamr.make_hierarchy(N0, DX0, DT0, G, BF, [[((0, 0, 0), (N0 - 1, N0 - 1, N0 - 1))]], oparams(p),
+                             interp_type=4, eta0=ETA0)
+    oh.levels[0].set_dense(y0)
+    h = slh.Hierarchy(N0, DX0, nghost=G, bf=BF, prec="f64", max_levels=MAXLEV)
+    h.init_level(0, [((0, 0, 0), (N0 - 1, N0 - 1, N0 - 1))])
+    h.set_state(0, _dense(oh.levels[0]))
+    h.set_eta(ETA0)
+    # a global regrid with a small buffer, then the string moves and local regrids follow
+    _oracle_regrid_nbuf(oh, 1)
+    h.regrid(MAXLEV, 1, MAX_BOX)
+    for _ in range(3):
+        oh.step()
+        h.advance(DT0, p)
+    masks = [oregrid.coarsen_any(oregrid.dilate_periodic(_dense_tags(oh, l) != 0, NBUF), BF // 2)
+             for l in range(len(oh.levels) - 1)]
+    exp = olr.local_regrid([L.boxes for L in oh.levels], N0, BF, masks)
+    cur = [list(L.boxes) for L in oh.levels]
+    added = h.regrid_local(NBUF)
+    got = [[tuple(map(tuple, b)) for b in h.levels[l]["boxes"]] for l in sorted(h.levels)]
+    assert got == [[(tuple(int(v) for v in lo), tuple(int(v) for v in hi)) for lo, hi in lb] for lb in exp]
+    assert any(a > 0 for a in added)
+    first = next(l for l in range(1, len(exp)) if exp[l] != cur[l])
+    for l in range(first, len(exp)):
+        oamr.regrid_level(oh, l, exp[l])
+    _compare(h, oh, 1e-12)
+    oh.step()
+    h.advance(DT0, p)
+    _compare(h, oh, 1e-12)
+
+
+def _oracle_regrid_nbuf(oh, nbuf):
+    for l in range(MAXLEV - 1):
+        if l >= len(oh.levels):
+            break
+        parent = None if l == 0 else oh.levels[l].boxes
+        boxes = oregrid.regrid_boxes(_dense_tags(oh, l), BF, nbuf, MAX_BOX, parent_boxes=parent)
+        oamr.regrid_level(oh, l + 1, boxes)
+        if not boxes:
+            break
