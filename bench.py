@@ -129,6 +129,23 @@ def _gpu_index(local_rank):
     return local_rank
 
 
+def max_over_ranks(dist, values, device):
+    """Each value's maximum over the ranks of the job (the slowest replica
+    sets the time); the values themselves on a single rank."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_value(world, cells, steps, ms):
+    """Whole-job throughput: every rank advances its own replica of ``cells``
+    cells ``steps`` times; the job takes the slowest rank's ``ms``."""
+    return world * float(cells) * steps / (ms / 1e3)
+
+
 def cpu_oracle_sample(budget_s=12.0, n=96):
     """Time the FP64 oracle (as it stands) on a bounded sample of the workload:
     an n^3 periodic lattice with the same dx, dt, order and init recipe."""
@@ -398,14 +415,9 @@ def run_ours(args, rank, world, local_rank, dist):
 
     ms = r32["ms"]
     e2e_ms = e2e_s * 1e3
-    if dist is not None:
-        t = torch.tensor([ms, e2e_ms, r64["ms"]], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_ms, ms64 = (float(v) for v in t.tolist())
-    else:
-        ms64 = r64["ms"]
+    ms, e2e_ms, ms64 = max_over_ranks(dist, [ms, e2e_ms, r64["ms"]], "cuda")
     cells = float(n) ** 3
-    value = world * cells * K / (ms / 1e3)
+    value = job_value(world, cells, K, ms)
     launches = r32["stage_launches"] + r32["ghost_launches"] + r32["time_launches"]
     achieved = r32["stage_bytes"] / (r32["stage_ms"] / 1e3) / 1e9
     ach64 = r64["stage_bytes"] / (r64["stage_ms"] / 1e3) / 1e9
@@ -423,7 +435,7 @@ def run_ours(args, rank, world, local_rank, dist):
                      "frac": achieved / peak, "traffic": _stage_traffic(),
                      "kernel": "stage_kernel<float,3,32,16>", "peak_kind": peak_kind,
                      "alg_bytes_per_cell_update": KAHAN_VALUES * 4},
-        "fp64_plain": {"value": world * cells * K / (ms64 / 1e3), "unit": "cell-updates/s",
+        "fp64_plain": {"value": job_value(world, cells, K, ms64), "unit": "cell-updates/s",
                        "ms_per_step": ms64 / K, "stage_achieved_gbs": ach64,
                        "hbm_frac": ach64 / peak, "alg_bytes_per_cell_update": F64_VALUES * 8},
         "stage_share": r32["stage_ms"] / ms,
@@ -431,7 +443,7 @@ def run_ours(args, rank, world, local_rank, dist):
         "autotune": {"f32": {"chosen": r32["tile_variant"], "ms": r32["tune_ms"]},
                      "f64": {"chosen": r64["tile_variant"], "ms": r64["tune_ms"]}},
         "energy_f32": r32["energy"], "energy_f64": r64["energy"],
-        "e2e": {"value": world * cells * K / (e2e_ms / 1e3), "unit": "cell-updates/s",
+        "e2e": {"value": job_value(world, cells, K, e2e_ms), "unit": "cell-updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4 * 8},
         "amr": amr,
         "ssprk3": ssp,
