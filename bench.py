@@ -202,9 +202,10 @@ def _time_form(slh, torch, prec, y0_dense, n, K, W, dist, flags, gw=False, order
     p = slh.EOMParams(order=order, integrator=integrator)
     if tile is None:
         chosen, tune_ms = h.autotune(0, p, reps=3)
+        chosen_d, tune_d_ms = h.autotune(0, p, reps=3, diag=True) if flags else (chosen, [])
     else:
         h.set_tile(0, tile)
-        chosen, tune_ms = tile, []
+        chosen, tune_ms, chosen_d, tune_d_ms = tile, [], tile, []
     for _ in range(W):
         h.advance(DT, p, flags=flags)
     h.sync()
@@ -234,6 +235,7 @@ def _time_form(slh, torch, prec, y0_dense, n, K, W, dist, flags, gw=False, order
     out = dict(ms=ms, stage_ms=stage[0], stage_launches=stage[1], stage_bytes=stage[2],
                ghost_ms=ghost[0], ghost_launches=ghost[1], time_launches=tim[1], energy=E.tolist(),
                per_stage_ms=[m / K for m in per_stage], tile_variant=chosen, tune_ms=tune_ms,
+               diag_tile_variant=chosen_d, diag_tune_ms=tune_d_ms,
                gw_ms=gwk[0], gw_launches=gwk[1], gw_bytes=gwk[2],
                buffer_bytes=sum(b.numel() * b.element_size() for b in h.levels[0]["bufs"] if b is not None))
     return h, out
@@ -440,8 +442,10 @@ def run_ours(args, rank, world, local_rank, dist):
                        "hbm_frac": ach64 / peak, "alg_bytes_per_cell_update": F64_VALUES * 8},
         "stage_share": r32["stage_ms"] / ms,
         "per_stage_ms": {"f32": r32["per_stage_ms"], "f64": r64["per_stage_ms"]},
-        "autotune": {"f32": {"chosen": r32["tile_variant"], "ms": r32["tune_ms"]},
-                     "f64": {"chosen": r64["tile_variant"], "ms": r64["tune_ms"]}},
+        "autotune": {"f32": {"chosen": r32["tile_variant"], "ms": r32["tune_ms"],
+                             "diag_chosen": r32["diag_tile_variant"], "diag_ms": r32["diag_tune_ms"]},
+                     "f64": {"chosen": r64["tile_variant"], "ms": r64["tune_ms"],
+                             "diag_chosen": r64["diag_tile_variant"], "diag_ms": r64["diag_tune_ms"]}},
         "energy_f32": r32["energy"], "energy_f64": r64["energy"],
         "e2e": {"value": job_value(world, cells, K, e2e_ms), "unit": "cell-updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4 * 8},

@@ -367,8 +367,17 @@ slh_status slh_reduce_energy(slh_ctx* ctx, const slh_eom_params* p, int32_t mode
 
 /* Stage-kernel tile shape of level lev: variant indexes a fixed table of
  * (x extent, y extent, TMA pipeline depth, z-march length) shapes; 0 is the
- * default.  Synchronises.  Errors: INVALID_ARG, STATE, OUT_OF_RANGE. */
+ * default.  Sets the tile of every stage, the diagnostics stage 1 (fused
+ * tags and energy) included.  Synchronises.
+ * Errors: INVALID_ARG, STATE, OUT_OF_RANGE. */
 slh_status slh_set_tile(slh_ctx* ctx, int32_t lev, int32_t variant);
+
+/* As slh_set_tile, for the diagnostics stage only: the stage-1 launch that
+ * fuses the winding tags and/or the energy partials (SLH_FUSE_TAG,
+ * SLH_FUSE_ENERGY) and the diagnostics pass of slh_tag and of
+ * slh_reduce_energy mode 0.  The other stages keep their tile.
+ * Synchronises.  Errors: INVALID_ARG, STATE, OUT_OF_RANGE. */
+slh_status slh_set_diag_tile(slh_ctx* ctx, int32_t lev, int32_t variant);
 
 /* Autotuner: time every tile variant on level lev's own boxes (reps
  * launches of an RK stage that reads the state, SLH_BUF_YA and SLH_BUF_D and
@@ -379,6 +388,16 @@ slh_status slh_set_tile(slh_ctx* ctx, int32_t lev, int32_t variant);
  * Errors: INVALID_ARG, STATE, CUDA. */
 slh_status slh_autotune(slh_ctx* ctx, int32_t lev, const slh_eom_params* p, int32_t reps, int32_t* chosen,
                         double* ms_out);
+
+/* Autotuner of the diagnostics stage 1: as slh_autotune, timing reps
+ * launches of stage 1 with the fused winding and energy partials (reads the
+ * state, writes SLH_BUF_YA, SLH_BUF_D and the level's energy partials), and
+ * keeps the fastest variant as the level's diagnostics tile
+ * (slh_set_diag_tile).  Discards the partials of the last fused stage 1, so a
+ * following slh_reduce_energy mode 1 fails with STATE until the next fused
+ * step.  Synchronises.  Errors: INVALID_ARG, STATE, CUDA. */
+slh_status slh_autotune_diag(slh_ctx* ctx, int32_t lev, const slh_eom_params* p, int32_t reps, int32_t* chosen,
+                             double* ms_out);
 
 /* Allocation-free energy reduction (the paper has no counterpart: this is a
  * service for embedders).  For callers that cannot call cudaMalloc -- code

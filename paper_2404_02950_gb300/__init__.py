@@ -45,7 +45,8 @@ ABI_SYMBOLS = (
     "slh_last_error", "slh_create", "slh_destroy", "slh_level_layout", "slh_init_level",
     "slh_set_state", "slh_get_state", "slh_set_eta", "slh_get_eta", "slh_rk_step",
     "slh_advance", "slh_fill_ghosts", "slh_tag", "slh_tag_blocks", "slh_regrid_boxes",
-    "slh_reduce_energy", "slh_sync", "slh_profile", "slh_profile_read", "slh_set_tile", "slh_autotune",
+    "slh_reduce_energy", "slh_sync", "slh_profile", "slh_profile_read", "slh_set_tile", "slh_set_diag_tile",
+    "slh_autotune", "slh_autotune_diag",
     "slh_energy_noalloc", "slh_regrid_level", "slh_selftest_wait_timeout",
     "slh_set_tagging", "slh_shadow_init", "slh_shadow_compare", "slh_tee_tags", "slh_gw_spectrum",
     "slh_local_regrid_boxes",
@@ -126,6 +127,8 @@ def lib():
         "slh_profile_read": (i32, [vp, i32, P(dbl), P(i64), P(dbl)]),
         "slh_set_tile": (i32, [vp, i32, i32]),
         "slh_autotune": (i32, [vp, i32, P(slh_eom_params), i32, P(i32), P(dbl)]),
+        "slh_set_diag_tile": (i32, [vp, i32, i32]),
+        "slh_autotune_diag": (i32, [vp, i32, P(slh_eom_params), i32, P(i32), P(dbl)]),
         "slh_energy_noalloc": (i32, [vp, i32, i32, dbl, dbl, P(slh_eom_params), vp, vp]),
         "slh_regrid_level": (i32, [vp, i32, P(slh_box), i32, P(vp), vp, i32]),
         "slh_selftest_wait_timeout": (i32, [vp, i64]),
@@ -486,13 +489,18 @@ class Hierarchy:
     def set_tile(self, lev, variant):
         _check(lib().slh_set_tile(self.h, lev, variant))
 
-    def autotune(self, lev, params: EOMParams, reps=3, nvariants=8):
+    def set_diag_tile(self, lev, variant):
+        _check(lib().slh_set_diag_tile(self.h, lev, variant))
+
+    def autotune(self, lev, params: EOMParams, reps=3, nvariants=8, diag=False):
         """Time every stage-kernel tile variant on this level; keep the fastest.
-        Returns (chosen index, [ms per variant])."""
+        diag: tune the diagnostics stage 1 (fused tags and energy) instead of
+        the plain stages.  Returns (chosen index, [ms per variant])."""
         p = params.c()
         ch = ctypes.c_int32()
         ms = (ctypes.c_double * nvariants)(*([-1.0] * nvariants))
-        _check(lib().slh_autotune(self.h, lev, ctypes.byref(p), reps, ctypes.byref(ch), ms))
+        fn = lib().slh_autotune_diag if diag else lib().slh_autotune
+        _check(fn(self.h, lev, ctypes.byref(p), reps, ctypes.byref(ch), ms))
         return ch.value, [v for v in ms[:] if v >= 0]
 
     def fused_tags(self, lev):

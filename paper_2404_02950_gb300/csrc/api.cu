@@ -81,6 +81,7 @@ void prof_end(slh_ctx* c) {
 static void free_level(Level& L) {
   free_tmaps(L);
   cudaFree(L.tile.d_items);
+  cudaFree(L.dtile.d_items);
   cudaFree(L.d_col_items);
   cudaFree(L.d_boxes);
   cudaFree(L.d_bmap);
@@ -148,8 +149,9 @@ static slh_status build_covered(slh_ctx* c, int lev) {
 }
 
 // Stage work items of a tile variant: box by box, z chunk outer, then y,
-// then x tiles (consecutive CTAs share halo planes in L2).
-static slh_status set_tile(slh_ctx* c, Level& L, const TileVariant& v) {
+// then x tiles (consecutive CTAs share halo planes in L2).  which: 1 the
+// plain stages, 2 the diagnostics stage, 3 both.
+static slh_status set_tile(slh_ctx* c, Level& L, const TileVariant& v, int which = 3) {
   (void)c;
   std::vector<int4> items;
   for (size_t b = 0; b < L.lay.boxes.size(); ++b) {
@@ -158,11 +160,15 @@ static slh_status set_tile(slh_ctx* c, Level& L, const TileVariant& v) {
       for (int y0 = 0; y0 < B.n[1]; y0 += v.ty)
         for (int x0 = 0; x0 < B.n[0]; x0 += v.tx) items.push_back(make_int4((int)b, x0, y0, z0));
   }
-  slh_status st = upload(&L.tile.d_items, items);
-  if (st != SLH_OK) return st;
-  L.tile.v = v;
-  L.tile.nitems = (int)items.size();
-  L.tile.zlen = v.zlen;
+  for (int k = 0; k < 2; ++k) {
+    if (!(which & (1 << k))) continue;
+    Tile& t = k == 0 ? L.tile : L.dtile;
+    slh_status st = upload(&t.d_items, items);
+    if (st != SLH_OK) return st;
+    t.v = v;
+    t.nitems = (int)items.size();
+    t.zlen = v.zlen;
+  }
   return SLH_OK;
 }
 
@@ -1235,25 +1241,39 @@ slh_status slh_reduce_energy(slh_ctx* c, const slh_eom_params* p, int32_t mode, 
   return SLH_OK;
 }
 
-slh_status slh_set_tile(slh_ctx* c, int32_t lev, int32_t variant) {
-  if (!c) return fail(SLH_ERR_INVALID_ARG, "set_tile: null ctx");
-  if (lev < 0 || lev >= c->nlevels) return fail(SLH_ERR_STATE, "set_tile: level %d not defined", lev);
+static slh_status set_tile_api(slh_ctx* c, int32_t lev, int32_t variant, int which, const char* what) {
+  if (!c) return fail(SLH_ERR_INVALID_ARG, "%s: null ctx", what);
+  if (lev < 0 || lev >= c->nlevels) return fail(SLH_ERR_STATE, "%s: level %d not defined", what, lev);
   int nv = 0;
   const TileVariant* vs = tile_variants(c->prec, &nv);
-  if (variant < 0 || variant >= nv) return fail(SLH_ERR_OUT_OF_RANGE, "set_tile: variant %d outside [0,%d)", variant, nv);
+  if (variant < 0 || variant >= nv) return fail(SLH_ERR_OUT_OF_RANGE, "%s: variant %d outside [0,%d)", what, variant, nv);
   SLH_CUDA(cudaStreamSynchronize(c->stream));
   drop_graphs(c);
-  return set_tile(c, c->lev[lev], vs[variant]);
+  return set_tile(c, c->lev[lev], vs[variant], which);
 }
 
-slh_status slh_autotune(slh_ctx* c, int32_t lev, const slh_eom_params* p, int32_t reps, int32_t* chosen,
-                        double* ms_out) {
-  if (!c) return fail(SLH_ERR_INVALID_ARG, "autotune: null ctx");
+slh_status slh_set_tile(slh_ctx* c, int32_t lev, int32_t variant) {
+  return set_tile_api(c, lev, variant, 3, "set_tile");
+}
+
+slh_status slh_set_diag_tile(slh_ctx* c, int32_t lev, int32_t variant) {
+  return set_tile_api(c, lev, variant, 2, "set_diag_tile");
+}
+
+// Time every tile variant of the plain stage (diag = false: a stage-2 launch
+// with the traffic of a real one, three distinct input buffers, writing only
+// the scratch buffers YA and D) or of the diagnostics stage 1 (reads the
+// state, writes YA, D and the energy partials), keep the fastest.
+static slh_status autotune_impl(slh_ctx* c, int32_t lev, const slh_eom_params* p, int32_t reps, int32_t* chosen,
+                                double* ms_out, bool diag) {
+  const char* what = diag ? "autotune_diag" : "autotune";
+  if (!c) return fail(SLH_ERR_INVALID_ARG, "%s: null ctx", what);
   slh_status st = check_params(p);
   if (st != SLH_OK) return st;
-  if (lev < 0 || lev >= c->nlevels) return fail(SLH_ERR_STATE, "autotune: level %d not defined", lev);
+  if (lev < 0 || lev >= c->nlevels) return fail(SLH_ERR_STATE, "%s: level %d not defined", what, lev);
   if (reps < 1) reps = 3;
   Level& L = c->lev[lev];
+  const int which = diag ? 2 : 1;
   int nv = 0;
   const TileVariant* vs = tile_variants(c->prec, &nv);
   const bool was_prof = c->prof;
@@ -1264,14 +1284,19 @@ slh_status slh_autotune(slh_ctx* c, int32_t lev, const slh_eom_params* p, int32_
   int best = 0;
   float best_ms = 0.f;
   for (int v = 0; v < nv; ++v) {
-    if ((st = set_tile(c, L, vs[v])) != SLH_OK) break;
-    // a stage-2 launch with the traffic of a real one (three distinct input
-    // buffers) that writes only the scratch buffers YA and D
+    if ((st = set_tile(c, L, vs[v], which)) != SLH_OK) break;
     StageLaunch sl;
     memset(&sl, 0, sizeof(sl));
-    sl.stage = 2;
-    sl.in_buf = SLH_BUF_YA;
-    sl.yn_buf = L.role_y;
+    if (diag) {
+      sl.stage = 1;
+      sl.in_buf = L.role_y;
+      sl.yn_buf = L.role_y;
+      sl.epart = L.d_epart;
+    } else {
+      sl.stage = 2;
+      sl.in_buf = SLH_BUF_YA;
+      sl.yn_buf = L.role_y;
+    }
     sl.d_buf = SLH_BUF_D;
     sl.out_buf = SLH_BUF_YA;
     sl.c_buf = -1;
@@ -1297,9 +1322,20 @@ slh_status slh_autotune(slh_ctx* c, int32_t lev, const slh_eom_params* p, int32_
   c->prof = was_prof;
   if (st != SLH_OK) return st;
   drop_graphs(c);
-  if ((st = set_tile(c, L, vs[best])) != SLH_OK) return st;
+  if (diag) L.fused_energy_ctas = 0;   // the partials now hold a timing launch's sums
+  if ((st = set_tile(c, L, vs[best], which)) != SLH_OK) return st;
   if (chosen) *chosen = best;
   return slh_sync(c);
+}
+
+slh_status slh_autotune(slh_ctx* c, int32_t lev, const slh_eom_params* p, int32_t reps, int32_t* chosen,
+                        double* ms_out) {
+  return autotune_impl(c, lev, p, reps, chosen, ms_out, false);
+}
+
+slh_status slh_autotune_diag(slh_ctx* c, int32_t lev, const slh_eom_params* p, int32_t reps, int32_t* chosen,
+                             double* ms_out) {
+  return autotune_impl(c, lev, p, reps, chosen, ms_out, true);
 }
 
 slh_status slh_profile(slh_ctx* c, int32_t enable, int32_t reset) {

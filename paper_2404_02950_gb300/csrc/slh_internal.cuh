@@ -114,6 +114,7 @@ struct Level {
   int npieces = 0;
   long long nghost_cells = 0;
   Tile tile;                     // stage work items for the chosen tile variant
+  Tile dtile;                    // the same for the diagnostics stage 1 (tags, energy)
   int4* d_col_items = nullptr;   // column work items (box, x0, y0, z0) of the GW and dissipation kernels
   int ncol_items = 0;
   std::map<unsigned long long, void*> tmaps;   // device tensor maps per (G, TX, TY)

@@ -101,35 +101,63 @@ __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier
 // ---------------------------------------------------------------------------
 // Winding contribution of the edge a -> b: +1 when it leaves the upper half
 // plane (Im >= 0) turning counter-clockwise, -1 when it enters it turning
-// clockwise, by the exact sign of X = Re a Im b - Im a Re b.
+// clockwise, by the exact sign of X = Re a Im b - Im a Re b.  edge_terms
+// gives delta + 1 (0..2) for N edges at once.
 
-__device__ __forceinline__ int edge_delta(double ar, double ai, double br, double bi) {
-  const bool ua = ai >= 0.0, ub = bi >= 0.0;
-  if (ua == ub) return 0;
-  const double X = __dsub_rn(__dmul_rn(ar, bi), __dmul_rn(ai, br));
-  return (int)(ua && X > 0.0) - (int)(ub && X < 0.0);
+// FP64 inputs: X from two correctly rounded products and one correctly
+// rounded difference, the form the oracle uses.
+template <int N>
+__device__ __forceinline__ void edge_terms(const double (&ar)[N], const double (&ai)[N], const double (&br)[N],
+                                           const double (&bi)[N], unsigned (&out)[N]) {
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const bool ua = ai[k] >= 0.0, ub = bi[k] >= 0.0;
+    const double X = __dsub_rn(__dmul_rn(ar[k], bi[k]), __dmul_rn(ai[k], br[k]));
+    out[k] = 1u + (unsigned)(ua && !ub && X > 0.0) - (unsigned)(!ua && ub && X < 0.0);
+  }
 }
 
-// FP32 inputs: q = fl(Im a * Re b), s = fma(Re a, Im b, -q) = fl(X + dq)
-// with |dq| <= 2^-24 |q| the rounding error of q.  Round-to-nearest keeps
-// the sign of a nonzero value, so whenever |s| > 2^-23 |q| (> 2 |dq|) the
-// sign of s is the sign of X.  Otherwise (near ties, or q tiny enough for
-// underflow to spoil the bound) the products, exact in FP64, are formed in
-// FP64.  The near-tie fallback is kept out of line so that FP64 work is
-// never if-converted into the common, branch-free path.
-__device__ __noinline__ float exact_cross_sign(float ar, float ai, float br, float bi) {
+// FP32 near-tie fallback: the products, exact in FP64, formed in FP64.  Kept
+// out of line so that FP64 work is never if-converted into the common path.
+__device__ __noinline__ unsigned exact_edge_term(float ar, float ai, float br, float bi) {
   const double X = __dsub_rn(__dmul_rn((double)ar, (double)bi), __dmul_rn((double)ai, (double)br));
-  return X > 0.0 ? 1.0f : (X < 0.0 ? -1.0f : 0.0f);
+  const bool ua = ai >= 0.0f, ub = bi >= 0.0f;
+  return 1u + (unsigned)(ua && !ub && X > 0.0) - (unsigned)(!ua && ub && X < 0.0);
 }
 
-__device__ __forceinline__ int edge_delta(float ar, float ai, float br, float bi) {
-  const bool ua = ai >= 0.0f, ub = bi >= 0.0f;
-  const float q = __fmul_rn(ai, br);
-  float s = __fmaf_rn(ar, bi, -q);
-  const float aq = fabsf(q);
-  if (ua != ub && !(fabsf(s) > aq * 1.1920928955078125e-07f && (aq > 1e-30f || fabsf(s) > 1e-30f)))
-    s = exact_cross_sign(ar, ai, br, bi);
-  return (int)(ua && !ub && s > 0.0f) - (int)(!ua && ub && s < 0.0f);
+// FP32 inputs, in integer arithmetic on the bit patterns (no predicates, of
+// which a thread has few).  Half-plane flags: bit 31 of fl(v + 0) is set iff
+// v < 0 (the sum maps -0 to +0).  q = fl(Im a Re b), s = fma(Re a, Im b, -q)
+// = fl(X + dq) with |dq| <= max(2^-24 |q|, 2^-150) the rounding error of q.
+// When |s| > max(2^-23 |q|, 2^-126), s is normal (so |X + dq| >=
+// |s| / (1 + 2^-24)) and exceeds |dq| with room to spare, so X has the sign
+// of s.  The bound's bit pattern is max(bits|q| - 23 * 2^23, bits 2^-126)
+// (scaling a normal number by 2^-23 subtracts 23 from its exponent field;
+// where that leaves the normal range the 2^-126 term wins), and for
+// non-negative floats the order of bit patterns is the numeric order.  An
+// edge that crosses the real axis without such a certificate takes the
+// exact fallback; with one, the sign bit of s is the sign of X.
+template <int N>
+__device__ __forceinline__ void edge_terms(const float (&ar)[N], const float (&ai)[N], const float (&br)[N],
+                                           const float (&bi)[N], unsigned (&out)[N]) {
+  unsigned need[N], any = 0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const unsigned na = __float_as_uint(__fadd_rn(ai[k], 0.0f)), nb = __float_as_uint(__fadd_rn(bi[k], 0.0f));
+    const float q = __fmul_rn(ai[k], br[k]);
+    const unsigned ns = __float_as_uint(__fmaf_rn(ar[k], bi[k], -q));
+    const int bound = max((int)(__float_as_uint(q) & 0x7FFFFFFFu) - 0x0B800000, 0x00800000);
+    const unsigned cert = (unsigned)(bound - (int)(ns & 0x7FFFFFFFu));   // bit 31: |s| above the bound
+    const unsigned pos = ~na & nb & ~ns, neg = na & ~nb & ns;
+    out[k] = 1u + (pos >> 31) - (neg >> 31);
+    need[k] = (na ^ nb) & ~cert;
+    any |= need[k];
+  }
+  if ((int)any < 0) {
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+      if ((int)need[k] < 0) out[k] = exact_edge_term(ar[k], ai[k], br[k], bi[k]);
+  }
 }
 
 // shared-memory geometry of one kernel variant (the diagnostics variant runs
@@ -256,7 +284,9 @@ __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stag
   // per-thread energy partials in the field precision with a compensation
   // term each (Kahan), so that no FP64 work remains inside the plane loop
   // (FP64 runs at 1/64 of the FP32 rate here); FP64 from the block reduction on
-  unsigned long long n_pierced = 0, n_tagged = 0;
+  // per-thread counts stay far below 2^32: at most 3 per cell a thread visits,
+  // and a persistent CTA visits (cells of the level) / (CTAs) of them
+  unsigned n_pierced = 0, n_tagged = 0;
   T i_kin = 0, i_grad = 0, i_pot = 0, c_kin = 0, c_grad = 0, c_pot_ = 0;
   auto kahan = [](T& sum, T& comp, T v) {
     const T y_ = v - comp;
@@ -271,24 +301,50 @@ __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stag
   constexpr int PSI_T = GE::PSI_STRIDE / (int)sizeof(T);
 
   // fixed per-thread assignment of the diagnostics work: extended-tile cells
-  // (edges) and mask cells, with their shared-memory offsets
+  // (edges) and mask cells, with their shared-memory offsets.  Interior
+  // columns first, TX consecutive items per row, so that a warp reads and
+  // writes whole rows (no bank conflicts); the side columns after them.
   constexpr int NEK = ((TX + 2) * (TY + 2) + TXY - 1) / TXY;
   constexpr int NMK = ((TX + 1) * (TY + 1) + TXY - 1) / TXY;
   int e_x[NEK], e_y[NEK], e_off[NEK], m_x[NMK], m_y[NMK];
 #pragma unroll
   for (int k = 0; k < NEK; ++k) {
     const int j = k * TXY + tid;
-    e_x[k] = j % (TX + 2) - 1;
-    e_y[k] = j / (TX + 2) - 1;
+    if (j < (TY + 2) * TX) {
+      e_x[k] = j % TX;
+      e_y[k] = j / TX - 1;
+    } else {
+      const int r = j - (TY + 2) * TX;
+      e_x[k] = (r & 1) ? TX : -1;
+      e_y[k] = r / 2 - 1;
+    }
     e_off[k] = e_y[k] * SXL + e_x[k];
   }
 #pragma unroll
   for (int k = 0; k < NMK; ++k) {
     const int j = k * TXY + tid;
-    m_x[k] = j % (TX + 1);
-    m_y[k] = j / (TX + 1);
+    if (j < (TY + 1) * TX) {
+      m_x[k] = j % TX + 1;
+      m_y[k] = j / TX;
+    } else {
+      m_x[k] = 0;
+      m_y[k] = j - (TY + 1) * TX;
+    }
   }
-  (void)e_x; (void)e_y; (void)e_off; (void)m_x; (void)m_y;
+  // values carried from one plane to the next (diagnostics): corner values
+  // of plane z and biased in-plane edge terms of each edge cell, the masks
+  // of plane z-1 of each mask cell
+  T c_r[NEK], c_i[NEK];
+  unsigned e_pl[NEK], m_pl[NMK];
+#pragma unroll
+  for (int k = 0; k < NEK; ++k) {
+    c_r[k] = 0;
+    c_i[k] = 0;
+    e_pl[k] = 0x0101u;
+  }
+#pragma unroll
+  for (int k = 0; k < NMK; ++k) m_pl[k] = 0;
+  (void)e_x; (void)e_y; (void)e_off; (void)m_x; (void)m_y; (void)c_r; (void)c_i; (void)e_pl; (void)m_pl;
 
   int t = 0, slot = 0, pslot = 0;
   unsigned parity = 0;
@@ -327,7 +383,6 @@ __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stag
     const int tcell = thread_off - (G * SXL + 4);
     auto S = [&](int c, int dx, int dy, int dz) -> T { return psi[plb[dz + G] + tcell + c * PLANE + dy * SXL + dx]; };
     T p1 = 0, p2 = 0, l1 = 0, l2 = 0, P1 = 0, P2 = 0, r2 = 0;
-    bool cell_cov = false;   // this cell is covered by a finer level (no energy, no string length)
     if (compute && active) {
       const T* pwp = reinterpret_cast<const T*>(pw_base + pslot * GE::PW_STRIDE);
       auto PWv = [&](int box, int comp) -> T { return pwp[box * 2 * TXY + comp * TXY + ty * TX + tx]; };
@@ -369,9 +424,8 @@ __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stag
       const T kP1 = (-c_fric) * P1 + l1 - p1 * pot;
       const T kP2 = (-c_fric) * P2 + l2 - p2 * pot;
       if (DIAG && A.epart != nullptr) {
-        // energy of the stage input, accumulated where its terms are formed
-        // (keeping them live across the winding phases below costs more than
-        // the winding itself); the pierced-plaquette count follows the masks
+        // energy of the stage input, accumulated where its terms are formed;
+        // the pierced-plaquette count follows the tags (three planes later)
         bool cov = false;
         if (A.covered != nullptr) {
           const int gx = (B.lo[0] + x) >> A.cov_shift, gy = (B.lo[1] + y) >> A.cov_shift,
@@ -383,8 +437,6 @@ __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stag
           kahan(i_kin, c_kin, (T)0.5 * (P1 * P1 + P2 * P2));
           kahan(i_grad, c_grad, (T)(-0.5) * (p1 * l1 + p2 * l2));
           kahan(i_pot, c_pot_, ((T)0.25 * c_pot) * (dd * dd) + ((T)0.5 * a_c) * r2);
-        } else {
-          cell_cov = true;
         }
       }
       const long long e0 = B.off + (long long)(z + gl) * B.pny * B.pitch + (long long)(y + gl) * B.pitch + x + XPAD;
@@ -451,71 +503,122 @@ __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stag
     if (DIAG) {
       // Plaquette windings.  The edge term is antisymmetric (delta(b,a) =
       // -delta(a,b)), so a plaquette's winding is the signed sum of the edges
-      // leaving its corners along +x, +y, +z.  Per plane: (1) every edge of
-      // the tile grown by one cell is evaluated once, spread evenly over the
-      // CTA (in-plane edges are reused for the next plane); (2) the 3-bit
-      // "winding != 0" mask of each cell of the tile and of its low halo
-      // follows from those edges; (3) a cell's tag is the OR over the 12
-      // plaquettes it is a corner of (owners c, c-u, c-v, c-u-v), read from
-      // the masks of planes z and z-1.
+      // leaving its corners along +x, +y, +z.  Three steps, software-pipelined
+      // over the planes of an item so that one CTA barrier per plane (the
+      // ring barrier below) separates them:
+      //  edges(z):   every edge of the tile grown by one cell is evaluated
+      //              once, spread over the CTA, and stored biased (delta + 1)
+      //              as bytes 0-2 (e_x, e_y, e_z) of one word per cell: the
+      //              vertical edges of plane z and the in-plane edges of
+      //              plane z+1 (plane z0-1's own in-plane edges in the
+      //              premask step);
+      //  masks(z-2): the 3-bit "winding != 0" mask of each cell of the tile
+      //              and of its low halo, from four words by byte-wise sums;
+      //  tags(z-3):  a cell's tag is the OR over the 12 plaquettes it is a
+      //              corner of (owners c, c-u, c-v, c-u-v), from the masks
+      //              of two planes, which share one byte.
+      // After an item's last plane the pipeline drains in three more
+      // barrier-separated steps.  Each thread keeps the same edge and mask
+      // cells on every plane, so the corner values of plane z, its in-plane
+      // edge terms and the masks of the plane below stay in registers.
       constexpr int EXW = TX + 2, EXH = TY + 2, NE = EXW * EXH;
       constexpr int MW = TX + 1, MH = TY + 1, NM = MW * MH;
-      // in-plane edges (e_x, e_y) of planes z and z+1 by plane parity, and
-      // the vertical edges e_z of plane z; an item's planes run consecutively
-      // from its premask plane z0-1, so plane z's in-plane edges are the ones
-      // computed as "plane z+1" one iteration earlier
-      __shared__ signed char exy[2][2][EXH][EXW];
-      __shared__ signed char ezv[EXH][EXW];
-      __shared__ unsigned char mk[2][MH][MW];
-      const bool doit = compute || premask;      // uniform over the CTA
-      const int pz = z & 1, pn = pz ^ 1;
-      if (doit) {
-#pragma unroll
-        for (int k = 0; k < NEK; ++k) {
-          if (k * TXY + tid >= NE) break;
-          const int ex = e_x[k], ey = e_y[k];
-          auto SE = [&](int c, int dx, int dy, int dz) -> T { return psi[plb[dz + G] + c * PLANE + e_off[k] + dy * SXL + dx]; };
-          const T r0 = SE(0, 0, 0, 0), i0 = SE(1, 0, 0, 0);
-          const T rz = SE(0, 0, 0, 1), iz = SE(1, 0, 0, 1);
-          ezv[ey + 1][ex + 1] = (signed char)edge_delta(r0, i0, rz, iz);
-          exy[pn][0][ey + 1][ex + 1] = (signed char)edge_delta(rz, iz, SE(0, 1, 0, 1), SE(1, 1, 0, 1));
-          if (ey < TY) exy[pn][1][ey + 1][ex + 1] = (signed char)edge_delta(rz, iz, SE(0, 0, 1, 1), SE(1, 0, 1, 1));
-          if (premask) {
-            exy[pz][0][ey + 1][ex + 1] = (signed char)edge_delta(r0, i0, SE(0, 1, 0, 0), SE(1, 1, 0, 0));
-            if (ey < TY) exy[pz][1][ey + 1][ex + 1] = (signed char)edge_delta(r0, i0, SE(0, 0, 1, 0), SE(1, 0, 1, 0));
-          }
-        }
-      }
-      __syncthreads();
-      if (doit) {
+      __shared__ unsigned ew[4][EXH][EXW];     // edge words of planes z-2..z+1 (plane & 3)
+      __shared__ unsigned char mk[2][MH][MW];  // by plane parity; bits 0-2: plane p, 3-5: plane p-1
+      const bool in_box = x < B.n[0] && y < B.n[1];
+      auto masks = [&](int pm) {
+        const int s0 = pm & 3, s1 = (pm + 1) & 3, mo = pm & 1;
 #pragma unroll
         for (int k = 0; k < NMK; ++k) {
           if (k * TXY + tid >= NM) break;
           const int mx = m_x[k], my = m_y[k];   // cell offset (mx-1, my-1) from (x0, y0)
-          const int ex_c = exy[pz][0][my][mx], ey_c = exy[pz][1][my][mx], ez_c = ezv[my][mx];
-          const int ey_cx = exy[pz][1][my][mx + 1], ez_cx = ezv[my][mx + 1];
-          const int ex_cy = exy[pz][0][my + 1][mx], ez_cy = ezv[my + 1][mx];
-          const int ex_cz = exy[pn][0][my][mx], ey_cz = exy[pn][1][my][mx];
-          const int wxy = ex_c + ey_cx - ex_cy - ey_c;   // normal z: c, c+x, c+x+y, c+y
-          const int wyz = ey_c + ez_cy - ey_cz - ez_c;   // normal x: c, c+y, c+y+z, c+z
-          const int wzx = ez_c + ex_cz - ez_cx - ex_c;   // normal y: c, c+z, c+z+x, c+x
-          mk[pz][my][mx] = (unsigned char)((wxy != 0 ? 1 : 0) | (wyz != 0 ? 2 : 0) | (wzx != 0 ? 4 : 0));
+          // windings in bytes 0, 1, 2 (normals z, x, y):
+          //   xy: C.ex + X.ey - Y.ex - C.ey   (c, c+x, c+x+y, c+y)
+          //   yz: C.ey + Y.ez - Z.ey - C.ez   (c, c+y, c+y+z, c+z)
+          //   zx: C.ez + Z.ex - X.ez - C.ex   (c, c+z, c+z+x, c+x)
+          // each term in 0..2, so every byte of s = W + 4 lies in 0..8 and no
+          // carry or borrow crosses a byte
+          const unsigned C = ew[s0][my][mx], X = ew[s0][my][mx + 1], Y = ew[s0][my + 1][mx], Z = ew[s1][my][mx];
+          const unsigned plus = __byte_perm(__byte_perm(X, Y, 0x0061u), Z, 0x0410u);    // X.ey, Y.ez, Z.ex
+          const unsigned minus = __byte_perm(__byte_perm(Y, Z, 0x0050u), X, 0x0610u);   // Y.ex, Z.ey, X.ez
+          const unsigned rot = __byte_perm(C, 0u, 0x0021u);                              // C.ey, C.ez, C.ex
+          const unsigned sw = (C + plus + 0x00040404u) - (minus + rot);
+          const unsigned nz = ((sw ^ 0x00040404u) + 0x007F7F7Fu) & 0x00808080u;         // bit 7: W != 0
+          const unsigned m = ((nz >> 7) & 1u) | ((nz >> 14) & 2u) | ((nz >> 21) & 4u);
+          mk[mo][my][mx] = (unsigned char)(m | (m_pl[k] << 3));
+          m_pl[k] = m;
         }
-      }
-      __syncthreads();
-      if (compute && active) {
-        const int pm = pz ^ 1;
-        const unsigned m00 = mk[pz][ty + 1][tx + 1], m0x = mk[pz][ty + 1][tx], m0y = mk[pz][ty][tx + 1],
-                       m0xy = mk[pz][ty][tx];
-        const unsigned q00 = mk[pm][ty + 1][tx + 1], q0y = mk[pm][ty][tx + 1], q0x = mk[pm][ty + 1][tx];
-        const unsigned tg = ((m00 | m0x | m0y | m0xy) & 1u) | ((m00 | m0y | q00 | q0y) & 2u) |
-                            ((m00 | q00 | m0x | q0x) & 4u);
+      };
+      auto tags = [&](int pt) {
+        if (!in_box) return;
+        const int mo = pt & 1;
+        const unsigned a00 = mk[mo][ty + 1][tx + 1], a0x = mk[mo][ty + 1][tx], a0y = mk[mo][ty][tx + 1],
+                       a0xy = mk[mo][ty][tx];
+        const unsigned u = a00 | a0y, v = a00 | a0x;
+        const unsigned tg = ((u | a0x | a0xy) & 1u) | ((u | (u >> 3)) & 2u) | ((v | (v >> 3)) & 4u);
         const bool tagged = tg != 0;
         if (A.tags != nullptr) {
-          A.tags[B.voff + ((long long)z * B.n[1] + y) * B.n[0] + x] = tagged ? 1 : 0;
-          n_tagged += tagged ? 1 : 0;
+          A.tags[B.voff + ((long long)pt * B.n[1] + y) * B.n[0] + x] = tagged ? 1 : 0;
+          n_tagged += tagged ? 1u : 0u;
         }
-        if (A.epart != nullptr && !cell_cov) n_pierced += __popc(m00);
+        if (A.epart != nullptr) {
+          bool cov = false;
+          if (A.covered != nullptr) {
+            const int gx = (B.lo[0] + x) >> A.cov_shift, gy = (B.lo[1] + y) >> A.cov_shift,
+                      gz = (B.lo[2] + pt) >> A.cov_shift;
+            cov = A.covered[((long long)gz * A.cov_nb + gy) * A.cov_nb + gx] != 0;
+          }
+          if (!cov) n_pierced += __popc(a00 & 7u);
+        }
+      };
+      if (compute || premask) {
+#pragma unroll
+        for (int k = 0; k < NEK; ++k) {
+          if (k * TXY + tid >= NE) break;
+          const int ey = e_y[k];
+          auto SE = [&](int c, int dx, int dy, int dz) -> T { return psi[plb[dz + G] + c * PLANE + e_off[k] + dy * SXL + dx]; };
+          T r0, i0;
+          if (premask) {
+            // plane z0-1: its corner values and in-plane edges from the ring
+            r0 = SE(0, 0, 0, 0);
+            i0 = SE(1, 0, 0, 0);
+            const T xr = SE(0, 1, 0, 0), xi = SE(1, 1, 0, 0);
+            const T yr = ey < TY ? SE(0, 0, 1, 0) : r0, yi = ey < TY ? SE(1, 0, 1, 0) : i0;
+            const T ar2[2] = {r0, r0}, ai2[2] = {i0, i0}, br2[2] = {xr, yr}, bi2[2] = {xi, yi};
+            unsigned b2[2];
+            edge_terms<2>(ar2, ai2, br2, bi2, b2);
+            e_pl[k] = b2[0] | (b2[1] << 8);
+          } else {
+            r0 = c_r[k];
+            i0 = c_i[k];
+          }
+          const T rz = SE(0, 0, 0, 1), iz = SE(1, 0, 0, 1);
+          const T xr = SE(0, 1, 0, 1), xi = SE(1, 1, 0, 1);
+          const T yr = ey < TY ? SE(0, 0, 1, 1) : rz, yi = ey < TY ? SE(1, 0, 1, 1) : iz;
+          // e_z of plane z, e_x and e_y of plane z+1
+          const T ar3[3] = {r0, rz, rz}, ai3[3] = {i0, iz, iz}, br3[3] = {rz, xr, yr}, bi3[3] = {iz, xi, yi};
+          unsigned b3[3];
+          edge_terms<3>(ar3, ai3, br3, bi3, b3);
+          const unsigned nxt = b3[1] | (b3[2] << 8);
+          ew[z & 3][ey + 1][e_x[k] + 1] = e_pl[k] | (b3[0] << 16);
+          ew[(z + 1) & 3][ey + 1][e_x[k] + 1] = nxt | (1u << 16);
+          c_r[k] = rz;
+          c_i[k] = iz;
+          e_pl[k] = nxt;
+        }
+      }
+      // planes z-2 and z-3: their inputs were written before the last barrier
+      if (compute && z - 2 >= cc.z0 - 1) masks(z - 2);
+      if (compute && z - 3 >= cc.z0) tags(z - 3);
+      if (cc.valid && z == cc.z1 - 1) {   // the item's last plane: drain (uniform over the CTA)
+        __syncthreads();
+        if (z - 1 >= cc.z0 - 1) masks(z - 1);
+        if (z - 2 >= cc.z0) tags(z - 2);
+        __syncthreads();
+        masks(z);
+        if (z - 1 >= cc.z0) tags(z - 1);
+        __syncthreads();
+        tags(z);
       }
     }
     if (__syncthreads_or(!ok)) {
@@ -547,7 +650,7 @@ __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stag
     __shared__ unsigned long long redt[NW];
     double v0 = (double)i_kin - (double)c_kin, v1 = (double)i_grad - (double)c_grad,
            v2 = (double)i_pot - (double)c_pot_, v3 = (double)n_pierced;
-    unsigned long long vt = n_tagged;
+    unsigned long long vt = (unsigned long long)n_tagged;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       v0 += __shfl_down_sync(0xffffffffu, v0, o);
@@ -666,7 +769,7 @@ static slh_status launch_v(slh_ctx* c, Level& L, const slh_eom_params& p, const 
   slh_status st = build_tmaps(c, L, G, TX, TY, &maps);
   if (st != SLH_OK) return st;
   if (s.dry) return SLH_OK;   // preparation only (before stream capture)
-  const Tile& tile = L.tile;
+  const Tile& tile = DIAG ? L.dtile : L.tile;
   StageArgs<T> A;
   A.boxes = L.d_boxes;
   A.items = tile.d_items;
@@ -721,12 +824,6 @@ static slh_status by_order(slh_ctx* c, Level& L, const slh_eom_params& p, const 
   }
 }
 
-template <typename T, int TX, int TY, int P>
-static slh_status by_diag(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s, int* u) {
-  const bool diag = s.tags != nullptr || s.epart != nullptr;
-  return diag ? by_order<T, TX, TY, P, true>(c, L, p, s, u) : by_order<T, TX, TY, P, false>(c, L, p, s, u);
-}
-
 // Tile variants (x extent, y extent, pipeline depth) the autotuner chooses
 // among; variant 0 is the default.
 const TileVariant* tile_variants(int prec, int* n) {
@@ -740,19 +837,27 @@ const TileVariant* tile_variants(int prec, int* n) {
   return f32;
 }
 
-slh_status launch_stage(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s, int* ctas_used) {
-  const TileVariant& v = L.tile.v;
+template <bool DIAG>
+static slh_status launch_tile(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s, int* u) {
+  const TileVariant& v = DIAG ? L.dtile.v : L.tile.v;
   if (c->prec == SLH_F64) {
-    if (v.tx == 32 && v.ty == 8 && v.p == 2) return by_diag<double, 32, 8, 2>(c, L, p, s, ctas_used);
-    if (v.tx == 32 && v.ty == 4 && v.p == 3) return by_diag<double, 32, 4, 3>(c, L, p, s, ctas_used);
-    if (v.tx == 16 && v.ty == 8 && v.p == 2) return by_diag<double, 16, 8, 2>(c, L, p, s, ctas_used);
+    if (v.tx == 32 && v.ty == 8 && v.p == 2) return by_order<double, 32, 8, 2, DIAG>(c, L, p, s, u);
+    if (v.tx == 32 && v.ty == 4 && v.p == 3) return by_order<double, 32, 4, 3, DIAG>(c, L, p, s, u);
+    if (v.tx == 16 && v.ty == 8 && v.p == 2) return by_order<double, 16, 8, 2, DIAG>(c, L, p, s, u);
   } else {
-    if (v.tx == 32 && v.ty == 16 && v.p == 2) return by_diag<float, 32, 16, 2>(c, L, p, s, ctas_used);
-    if (v.tx == 32 && v.ty == 8 && v.p == 3) return by_diag<float, 32, 8, 3>(c, L, p, s, ctas_used);
-    if (v.tx == 32 && v.ty == 16 && v.p == 3) return by_diag<float, 32, 16, 3>(c, L, p, s, ctas_used);
-    if (v.tx == 16 && v.ty == 16 && v.p == 2) return by_diag<float, 16, 16, 2>(c, L, p, s, ctas_used);
+    if (v.tx == 32 && v.ty == 16 && v.p == 2) return by_order<float, 32, 16, 2, DIAG>(c, L, p, s, u);
+    if (v.tx == 32 && v.ty == 8 && v.p == 3) return by_order<float, 32, 8, 3, DIAG>(c, L, p, s, u);
+    if (v.tx == 32 && v.ty == 16 && v.p == 3) return by_order<float, 32, 16, 3, DIAG>(c, L, p, s, u);
+    if (v.tx == 16 && v.ty == 16 && v.p == 2) return by_order<float, 16, 16, 2, DIAG>(c, L, p, s, u);
   }
   return fail(SLH_ERR_STATE, "no stage kernel for tile %dx%d depth %d", v.tx, v.ty, v.p);
+}
+
+// the diagnostics variant (tags and/or energy partials) runs on the level's
+// diagnostics tile, every other stage on its plain tile
+slh_status launch_stage(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s, int* ctas_used) {
+  const bool diag = s.tags != nullptr || s.epart != nullptr;
+  return diag ? launch_tile<true>(c, L, p, s, ctas_used) : launch_tile<false>(c, L, p, s, ctas_used);
 }
 
 void free_tmaps(Level& L) {

@@ -201,10 +201,13 @@ def test_full_size_512_order6_sampled(prec):
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("which", ["both", "diag_only"])
 @pytest.mark.parametrize("prec,nvar", [("f64", 3), ("f32", 4)])
-def test_every_tile_variant_matches_oracle(prec, nvar):
+def test_every_tile_variant_matches_oracle(prec, nvar, which):
     """Each stage-kernel tile shape the autotuner may pick gives the oracle's
-    result (ragged 40-cell boxes, 6th order, fused tags in stage 1)."""
+    result (ragged 40-cell boxes, 6th order, fused tags in stage 1), set for
+    every stage or for the diagnostics stage 1 alone (plain stages on
+    variant 0)."""
     n, dx = 40, 0.125
     p = slh.EOMParams(order=6)
     y0 = inputs.gaussian_field(n, 5.0, seed=4)
@@ -217,7 +220,10 @@ def test_every_tile_variant_matches_oracle(prec, nvar):
     tol = 1e-12 if prec == "f64" else 1e-5
     for v in range(nvar):
         h, _ = uniform_hierarchy(n, dx, prec=prec, nghost=3, bf=4, boxes=boxes, fused_tags=True)
-        h.set_tile(0, v)
+        if which == "both":
+            h.set_tile(0, v)
+        else:
+            h.set_diag_tile(0, v)
         upload(h, 0, y0, boxes)
         h.set_eta(0.5)
         snap = download_domain(h, 0, boxes, n)
@@ -246,6 +252,18 @@ def test_autotune_keeps_state_and_picks_a_variant():
     assert 0 <= chosen < len(ms) and len(ms) == 4 and all(m > 0 for m in ms)
     assert ms[chosen] == min(ms)
     assert np.array_equal(before, h.get_state(0))
+    # the diagnostics stage is tuned on its own; the fused partials it
+    # overwrites are no longer reported
+    h.rk_step(0, 0.02, p, flags=slh.SLH_FUSE_ENERGY)
+    h.reduce_energy(p, mode=1)
+    before = h.get_state(0)
+    chosen_d, ms_d = h.autotune(0, p, reps=2, diag=True)
+    assert 0 <= chosen_d < len(ms_d) and len(ms_d) == 4 and all(m > 0 for m in ms_d)
+    assert ms_d[chosen_d] == min(ms_d)
+    assert np.array_equal(before, h.get_state(0))
+    with pytest.raises(slh.SlhError) as e:
+        h.reduce_energy(p, mode=1)
+    assert e.value.code == -7          # STATE
 
 
 def test_bounded_wait_expiry_is_reported_and_context_survives():
