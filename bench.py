@@ -192,7 +192,8 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def _time_form(slh, torch, prec, y0_dense, n, K, W, dist, flags, gw=False, order=ORDER, integrator=4, tile=None):
+def _time_form(slh, torch, prec, y0_dense, n, K, W, dist, flags, gw=False, order=ORDER, integrator=4, tile=None,
+               diag_tile=None):
     """Warm up, then time K steps of one precision; returns a dict."""
     h = slh.Hierarchy(n, DX, nghost=3, bf=16, prec=prec, max_levels=1, gw=gw)
     boxes = [((0, 0, 0), (n - 1, n - 1, n - 1))]
@@ -206,6 +207,9 @@ def _time_form(slh, torch, prec, y0_dense, n, K, W, dist, flags, gw=False, order
     else:
         h.set_tile(0, tile)
         chosen, tune_ms, chosen_d, tune_d_ms = tile, [], tile, []
+        if diag_tile is not None:
+            h.set_diag_tile(0, diag_tile)
+            chosen_d = diag_tile
     for _ in range(W):
         h.advance(DT, p, flags=flags)
     h.sync()
@@ -347,7 +351,8 @@ def run_ours(args, rank, world, local_rank, dist):
     # FP32 + Kahan (headline), with clock sampling over its timed region
     with ClockSampler(_gpu_index(local_rank)) as clk:
         h32, r32 = _time_form(slh, torch, "f32", dense, n, K, W, dist, flags,
-                              tile=args.tile if args.profile_only else None)
+                              tile=args.tile if args.profile_only else None,
+                              diag_tile=args.diag_tile if args.profile_only else None)
     clocks = clk.summary()
     if args.profile_only:
         # short run for profilers: no e2e leg, no FP64 form, no JSON line
@@ -472,6 +477,8 @@ def main():
     ap.add_argument("--no-ssp", action="store_true", help="skip the SSPRK3 line")
     ap.add_argument("--tile", type=int, default=None,
                     help="with --profile-only: use this stage-kernel tile variant instead of autotuning")
+    ap.add_argument("--diag-tile", type=int, default=None,
+                    help="with --profile-only --tile: the diagnostics stage-1 tile variant (default: --tile)")
     ap.add_argument("--profile-only", nargs="?", const="uniform", default=None, choices=["uniform", "amr", "gw"],
                     help="short run for ncu captures of a small case, printing nothing: the FP32 uniform form "
                          "(default), the dynamic-AMR form (base --cells^3, --steps coarse steps) or the "

@@ -393,7 +393,9 @@ slh_status slh_autotune(slh_ctx* ctx, int32_t lev, const slh_eom_params* p, int3
  * launches of stage 1 with the fused winding and energy partials (reads the
  * state, writes SLH_BUF_YA, SLH_BUF_D and the level's energy partials), and
  * keeps the fastest variant as the level's diagnostics tile
- * (slh_set_diag_tile).  Discards the partials of the last fused stage 1, so a
+ * (slh_set_diag_tile).  Fills the level's ghost cells first (alpha = 1, as
+ * slh_fill_ghosts), since the winding's cost depends on the values it reads.
+ * Discards the partials of the last fused stage 1, so a
  * following slh_reduce_energy mode 1 fails with STATE until the next fused
  * step.  Synchronises.  Errors: INVALID_ARG, STATE, CUDA. */
 slh_status slh_autotune_diag(slh_ctx* ctx, int32_t lev, const slh_eom_params* p, int32_t reps, int32_t* chosen,

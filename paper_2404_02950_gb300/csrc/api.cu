@@ -1278,6 +1278,12 @@ static slh_status autotune_impl(slh_ctx* c, int32_t lev, const slh_eom_params* p
   const TileVariant* vs = tile_variants(c->prec, &nv);
   const bool was_prof = c->prof;
   c->prof = false;
+  // the winding's near-tie fallback depends on the values it reads, so the
+  // diagnostics stage is timed on the state with its ghosts filled, as in a step
+  if (diag && (st = fill_impl(c, lev, 1.0, p->interp_type, SLH_GHOSTS)) != SLH_OK) {
+    c->prof = was_prof;
+    return st;
+  }
   cudaEvent_t e0, e1;
   SLH_CUDA(cudaEventCreate(&e0));
   SLH_CUDA(cudaEventCreate(&e1));
