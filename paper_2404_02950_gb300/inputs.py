@@ -63,6 +63,23 @@ def gaussian_field(n: int, m_max: float, seed: int):
     return p1, p2, z, z.copy()
 
 
+def _loop_center(n: int):
+    return (n / 2.0 - 0.5 + 0.25, n / 2.0 - 0.5 + 0.125, n / 2.0 - 0.5 + 0.0625)
+
+
+def _loop_fields(i, j, k, radius, eta0, dx, c):
+    rho = np.hypot(i - c[0], j - c[1])
+    dz = k - c[2]
+    dr = rho - radius
+    d = np.hypot(dr, dz)
+    theta = np.arctan2(dz, dr) - np.arctan2(dz, rho + radius)
+    amp = np.tanh(eta0 * d * dx / np.sqrt(2.0))
+    p1 = np.ascontiguousarray(amp * np.cos(theta))
+    p2 = np.ascontiguousarray(amp * np.sin(theta))
+    z = np.zeros_like(p1)
+    return p1, p2, z, z.copy()
+
+
 def string_loop(n: int, radius: float, eta0: float, dx: float, center=None):
     """A circular string loop of ``radius`` lattice cells in the plane z = n/2.
 
@@ -74,21 +91,27 @@ def string_loop(n: int, radius: float, eta0: float, dx: float, center=None):
     to zero far from the loop, so the periodic wrap adds no spurious string.
     psi = tanh(eta0 d dx / sqrt 2) e^{i theta}.
     """
-    c = (n / 2.0 - 0.5 + 0.25, n / 2.0 - 0.5 + 0.125, n / 2.0 - 0.5 + 0.0625) \
-        if center is None else center
+    c = _loop_center(n) if center is None else center
     k, j, i = np.meshgrid(np.arange(n, dtype=np.float64),
                           np.arange(n, dtype=np.float64),
                           np.arange(n, dtype=np.float64), indexing="ij")
-    rho = np.hypot(i - c[0], j - c[1])
-    dz = k - c[2]
-    dr = rho - radius
-    d = np.hypot(dr, dz)
-    theta = np.arctan2(dz, dr) - np.arctan2(dz, rho + radius)
-    amp = np.tanh(eta0 * d * dx / np.sqrt(2.0))
-    p1 = np.ascontiguousarray(amp * np.cos(theta))
-    p2 = np.ascontiguousarray(amp * np.sin(theta))
-    z = np.zeros_like(p1)
-    return p1, p2, z, z.copy()
+    return _loop_fields(i, j, k, radius, eta0, dx, c)
+
+
+def string_loop_boxes(n0: int, level: int, boxes, radius: float, eta0: float, dx0: float):
+    """The loop of ``string_loop(n0, radius, eta0, dx0)`` sampled at the cell
+    centres of refinement level ``level`` (ratio 2 per level) inside
+    ``boxes`` (inclusive (lo, hi) in that level's index space).  A level-l cell
+    i sits at (i + 1/2) / 2^l - 1/2 in level-0 lattice units.  Returns one
+    (4, nz, ny, nx) float64 array per box."""
+    c = _loop_center(n0)
+    r = float(1 << level)
+    out = []
+    for lo, hi in boxes:
+        ax = [(np.arange(lo[d], hi[d] + 1, dtype=np.float64) + 0.5) / r - 0.5 for d in range(3)]
+        k, j, i = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+        out.append(np.stack(_loop_fields(i, j, k, radius, eta0, dx0, c)))
+    return out
 
 
 def plane_wave_vector():
