@@ -195,7 +195,8 @@ def run_reference(args, rank, world):
 def _time_form(slh, torch, prec, y0_dense, n, K, W, dist, flags, gw=False, order=ORDER, integrator=4, tile=None,
                diag_tile=None):
     """Warm up, then time K steps of one precision; returns a dict."""
-    h = slh.Hierarchy(n, DX, nghost=3, bf=16, prec=prec, max_levels=1, gw=gw)
+    # ghost layers = the Laplacian's stencil radius (the paper's "order")
+    h = slh.Hierarchy(n, DX, nghost=order // 2, bf=16, prec=prec, max_levels=1, gw=gw)
     boxes = [((0, 0, 0), (n - 1, n - 1, n - 1))]
     h.init_level(0, boxes, fused_tags=True)
     h.set_state(0, y0_dense.astype(h.np_dtype))
@@ -278,6 +279,7 @@ def _gw_form(slh, torch, n, dist, peak, K=GW_K):
 
 
 AMR_N, AMR_LEVELS, AMR_NBUF, AMR_BF, AMR_MAXBOX, AMR_RELAX, AMR_EVERY = 256, 3, 4, 16, 128, 100, 4
+AMR_ORDER = 4
 AMR_WORKLOAD = ("dynamic AMR: 256^3 base + 2 ratio-2 levels, c0-style Gaussian init (k_max=pi/(4dx)) relaxed "
                 "100 coarse steps on the base level, then regridded every 4 coarse steps from string tags "
                 "(buffer 4, blocking factor 16, max box 128), 4th-order Laplacian, quartic prolongation, "
@@ -287,11 +289,11 @@ AMR_WORKLOAD = ("dynamic AMR: 256^3 base + 2 ratio-2 levels, c0-style Gaussian i
 def _amr_form(slh, torch, prec, y0_dense, K, n=AMR_N):
     """Dynamic-AMR timing: coarse steps with global regrids every AMR_EVERY
     steps.  Returns (cell-updates/s, details)."""
-    h = slh.Hierarchy(n, DX, nghost=3, bf=AMR_BF, prec=prec, max_levels=AMR_LEVELS)
+    h = slh.Hierarchy(n, DX, nghost=AMR_ORDER // 2, bf=AMR_BF, prec=prec, max_levels=AMR_LEVELS)
     h.init_level(0, [((0, 0, 0), (n - 1, n - 1, n - 1))])
     h.set_state(0, y0_dense.astype(h.np_dtype))
     h.set_eta(ETA0)
-    p = slh.EOMParams(order=4, interp_type=4)
+    p = slh.EOMParams(order=AMR_ORDER, interp_type=4)
     for _ in range(AMR_RELAX):
         h.advance(DT, p)
     h.sync()

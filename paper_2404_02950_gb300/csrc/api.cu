@@ -405,15 +405,76 @@ static bool plan_patch(const Level& C, int bf, const int flo[3], const int fhi[3
 // Ghost regions of every box: each of the six ghost slabs is cut at the box
 // bounds, every GHOST_CHUNK cells and at the domain boundaries; each piece is
 // classified from the host block map (blocks of bf >= g cells, so a piece
-// meets few blocks).  For a level > 0, regions that prolong get the pieces
-// of their coarse patch.
+// meets few blocks).  A piece that meets several owners (or owners and
+// uncovered blocks) is cut further at the block boundaries, where ownership
+// is constant, and neighbouring cuts of one kind and source merged again, so
+// that every region is a pure copy or a pure prolongation.  For a level > 0,
+// regions that prolong get the pieces of their coarse patch.  Copy regions
+// come first in the list (a kernel of their own fills them).
 static slh_status plan_ghost_regions(slh_ctx* c, int lev, Level& L, std::vector<GhostRegion>* out,
-                                     std::vector<PatchPiece>* pieces, long long* total) {
+                                     std::vector<PatchPiece>* pieces, long long* total, int* ncopy) {
   const int g = c->g, bf = c->bf, n = L.n_dom, nbd = L.nb_dom;
   out->clear();
   pieces->clear();
   *total = 0;
-  std::vector<std::pair<int, int>> sx, sy, sz;
+  std::vector<GhostRegion> copies, others;
+  // classification of cells glo..ghi (unwrapped, inclusive, one periodic image)
+  auto classify = [&](const BoxDev& B, int b, const int glo[3], const int ghi[3], GhostRegion* R) {
+    int wl[3], k[3];
+    R->box = b;
+    for (int d = 0; d < 3; ++d) {
+      R->lo[d] = glo[d] - B.lo[d];
+      R->ext[d] = ghi[d] - glo[d] + 1;
+      k[d] = glo[d] < 0 ? -1 : (glo[d] >= n ? 1 : 0);
+      wl[d] = glo[d] - k[d] * n;
+    }
+    int own = -2;
+    bool same = true, any_cov = false, any_unc = false;
+    for (int bz = wl[2] / bf; bz <= (wl[2] + R->ext[2] - 1) / bf; ++bz)
+      for (int by = wl[1] / bf; by <= (wl[1] + R->ext[1] - 1) / bf; ++by)
+        for (int bx = wl[0] / bf; bx <= (wl[0] + R->ext[0] - 1) / bf; ++bx) {
+          const int o = L.h_bmap[((size_t)bz * nbd + by) * nbd + bx];
+          if (o >= 0) any_cov = true; else any_unc = true;
+          if (own == -2) own = o;
+          else if (o != own) same = false;
+        }
+    R->src = -1;
+    R->d[0] = R->d[1] = R->d[2] = 0;
+    if (!any_cov) {
+      R->kind = GHOST_PROLONG;
+    } else if (!any_unc && same) {
+      R->kind = GHOST_COPY;
+      R->src = own;
+      const BoxDev& S = L.lay.boxes[own];
+      for (int d = 0; d < 3; ++d) R->d[d] = B.lo[d] - k[d] * n - S.lo[d];
+    } else {
+      R->kind = GHOST_MIXED;
+    }
+  };
+  auto emit = [&](const BoxDev& B, int b, const int glo[3], const int ghi[3]) {
+    GhostRegion R;
+    classify(B, b, glo, ghi, &R);
+    R.p0 = (int)pieces->size();
+    R.np = 0;
+    R.covered = 0;
+    if (lev > 0 && R.kind != GHOST_COPY) {
+      int flo[3], fhi[3];
+      for (int d = 0; d < 3; ++d) {
+        flo[d] = glo[d];
+        fhi[d] = ghi[d];
+      }
+      R.covered = plan_patch(c->lev[lev - 1], bf, flo, fhi, pieces) ? 1 : 0;
+      R.np = (int)pieces->size() - R.p0;
+    }
+    (R.kind == GHOST_COPY ? copies : others).push_back(R);
+    *total += (long long)R.ext[0] * R.ext[1] * R.ext[2];
+  };
+  auto same_key = [](const GhostRegion& a, const GhostRegion& b) {
+    return a.kind == b.kind && a.kind != GHOST_MIXED && a.src == b.src && a.d[0] == b.d[0] && a.d[1] == b.d[1] &&
+           a.d[2] == b.d[2];
+  };
+  std::vector<std::pair<int, int>> sx, sy, sz, cut[3];
+  std::vector<GhostRegion> sub;
   for (size_t b = 0; b < L.lay.boxes.size(); ++b) {
     const BoxDev& B = L.lay.boxes[b];
     const int nn[3] = {B.n[0], B.n[1], B.n[2]};
@@ -434,56 +495,73 @@ static slh_status plan_ghost_regions(slh_ctx* c, int lev, Level& L, std::vector<
       for (auto& zz : sz)
         for (auto& yy : sy)
           for (auto& xx : sx) {
-            GhostRegion R;
-            R.box = (int)b;
             const int glo[3] = {xx.first, yy.first, zz.first}, ghi[3] = {xx.second, yy.second, zz.second};
-            int wl[3], k[3];
+            GhostRegion R;
+            classify(B, (int)b, glo, ghi, &R);
+            if (R.kind != GHOST_MIXED) {
+              emit(B, (int)b, glo, ghi);
+              continue;
+            }
+            // cut at the block boundaries (of the wrapped coordinates)
             for (int d = 0; d < 3; ++d) {
-              R.lo[d] = glo[d] - B.lo[d];
-              R.ext[d] = ghi[d] - glo[d] + 1;
-              k[d] = glo[d] < 0 ? -1 : (glo[d] >= n ? 1 : 0);   // one periodic image per piece
-              wl[d] = glo[d] - k[d] * n;
-            }
-            // classify by the blocks the piece meets
-            int own = -2;
-            bool same = true, any_cov = false, any_unc = false;
-            for (int bz = wl[2] / bf; bz <= (wl[2] + R.ext[2] - 1) / bf; ++bz)
-              for (int by = wl[1] / bf; by <= (wl[1] + R.ext[1] - 1) / bf; ++by)
-                for (int bx = wl[0] / bf; bx <= (wl[0] + R.ext[0] - 1) / bf; ++bx) {
-                  const int o = L.h_bmap[((size_t)bz * nbd + by) * nbd + bx];
-                  if (o >= 0) any_cov = true; else any_unc = true;
-                  if (own == -2) own = o;
-                  else if (o != own) same = false;
-                }
-            R.src = -1;
-            R.d[0] = R.d[1] = R.d[2] = 0;
-            if (!any_cov) {
-              R.kind = GHOST_PROLONG;
-            } else if (!any_unc && same) {
-              R.kind = GHOST_COPY;
-              R.src = own;
-              const BoxDev& S = L.lay.boxes[own];
-              for (int d = 0; d < 3; ++d) R.d[d] = B.lo[d] - k[d] * n - S.lo[d];
-            } else {
-              R.kind = GHOST_MIXED;
-            }
-            R.p0 = (int)pieces->size();
-            R.np = 0;
-            R.covered = 0;
-            if (lev > 0 && R.kind != GHOST_COPY) {
-              int flo[3], fhi[3];
-              for (int d = 0; d < 3; ++d) {
-                flo[d] = glo[d];
-                fhi[d] = ghi[d];
+              cut[d].clear();
+              const int k = glo[d] < 0 ? -1 : (glo[d] >= n ? 1 : 0);
+              int a = glo[d];
+              while (a <= ghi[d]) {
+                const int w = a - k * n;
+                const int e = std::min(ghi[d], a + (bf - w % bf) - 1);
+                cut[d].push_back({a, e});
+                a = e + 1;
               }
-              R.covered = plan_patch(c->lev[lev - 1], bf, flo, fhi, pieces) ? 1 : 0;
-              R.np = (int)pieces->size() - R.p0;
             }
-            out->push_back(R);
-            *total += (long long)R.ext[0] * R.ext[1] * R.ext[2];
+            const int nx = (int)cut[0].size(), ny = (int)cut[1].size(), nz = (int)cut[2].size();
+            sub.assign((size_t)nx * ny * nz, GhostRegion());
+            for (int iz = 0; iz < nz; ++iz)
+              for (int iy = 0; iy < ny; ++iy)
+                for (int ix = 0; ix < nx; ++ix) {
+                  const int l[3] = {cut[0][ix].first, cut[1][iy].first, cut[2][iz].first};
+                  const int h[3] = {cut[0][ix].second, cut[1][iy].second, cut[2][iz].second};
+                  classify(B, (int)b, l, h, &sub[((size_t)iz * ny + iy) * nx + ix]);
+                }
+            // merge runs along x of one key, then rows along y with the same
+            // runs; z (the slab's thickness, or a 32-cell chunk) stays cut
+            for (int iz = 0; iz < nz; ++iz) {
+              int iy = 0;
+              while (iy < ny) {
+                // runs of row iy
+                std::vector<std::pair<int, int>> runs;
+                for (int ix = 0; ix < nx;) {
+                  int jx = ix;
+                  while (jx + 1 < nx && same_key(sub[((size_t)iz * ny + iy) * nx + ix], sub[((size_t)iz * ny + iy) * nx + jx + 1])) ++jx;
+                  runs.push_back({ix, jx});
+                  ix = jx + 1;
+                }
+                // extend every run along y while the next row holds its key
+                // over the run's whole width (each rectangle stays uniform)
+                int jy = iy;
+                while (jy + 1 < ny) {
+                  bool ok = true;
+                  for (auto& r : runs)
+                    for (int q = r.first; q <= r.second && ok; ++q)
+                      ok = same_key(sub[((size_t)iz * ny + iy) * nx + r.first], sub[((size_t)iz * ny + jy + 1) * nx + q]);
+                  if (!ok) break;
+                  ++jy;
+                }
+                for (auto& r : runs) {
+                  const int l[3] = {cut[0][r.first].first, cut[1][iy].first, cut[2][iz].first};
+                  const int h[3] = {cut[0][r.second].second, cut[1][jy].second, cut[2][iz].second};
+                  emit(B, (int)b, l, h);
+                }
+                iy = jy + 1;
+              }
+            }
           }
     }
   }
+  *ncopy = (int)copies.size();
+  out->reserve(copies.size() + others.size());
+  out->insert(out->end(), copies.begin(), copies.end());
+  out->insert(out->end(), others.begin(), others.end());
   return SLH_OK;
 }
 
@@ -512,8 +590,10 @@ static slh_status build_level(slh_ctx* c, int lev, Level& L, const slh_box* boxe
     std::vector<GhostRegion> regs;
     std::vector<PatchPiece> pcs;
     long long tot = 0;
-    if ((st = plan_ghost_regions(c, lev, L, &regs, &pcs, &tot)) != SLH_OK) return st;
+    int ncopy = 0;
+    if ((st = plan_ghost_regions(c, lev, L, &regs, &pcs, &tot, &ncopy)) != SLH_OK) return st;
     L.ngregions = (int)regs.size();
+    L.ncopyregions = ncopy;
     L.nghost_cells = tot;
     L.npieces = (int)pcs.size();
     if ((st = upload(&L.d_gregions, regs)) != SLH_OK) return st;

@@ -77,7 +77,7 @@ template <typename T>
 struct GhostArgs {
   const BoxDev* boxes;
   const GhostRegion* regions;
-  int nregions;
+  int r0, nregions;   // the region kernel takes regions [r0, nregions), the copy kernel [0, r0)
   const PatchPiece* pieces;
   T* y;
   int gl;
@@ -212,6 +212,53 @@ __device__ __forceinline__ void final_pass_any(int ax, const T* src, int sstr, c
   else final_pass<T, RAD, 2, NF>(src, sstr, d, geo, w0, w1, A, R, B, f0, have_coarse);
 }
 
+// Same-level copy regions [0, r0): no shared memory, so many CTAs per SM
+// keep loads in flight; each thread reads CU cells of every field pair
+// before writing them (source and destination cells never overlap: the
+// source is valid cells of a box, the destination ghost cells).
+template <typename T>
+__global__ void __launch_bounds__(256) ghost_copy_kernel(const GhostArgs<T> A) {
+  constexpr int CU = 4;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int r = blockIdx.x; r < A.r0; r += gridDim.x) {
+    const GhostRegion R = A.regions[r];
+    const BoxDev B = A.boxes[R.box];
+    const BoxDev S = A.boxes[R.src];
+    const int ncell = R.ext[0] * R.ext[1] * R.ext[2];
+    const Split3 sp(R.ext[0], R.ext[1]);
+    for (int t0 = tid; t0 < ncell; t0 += CU * nt) {
+      long long dst[CU], src[CU];
+      bool ok[CU];
+#pragma unroll
+      for (int u = 0; u < CU; ++u) {
+        const int t = t0 + u * nt;
+        ok[u] = t < ncell;
+        int i = 0, j = 0, k = 0;
+        if (ok[u]) sp(t, i, j, k);
+        const int rx = R.lo[0] + i, ry = R.lo[1] + j, rz = R.lo[2] + k;
+        dst[u] = cell_index(B, A.gl, rx, ry, rz);
+        src[u] = cell_index(S, A.gl, rx + R.d[0], ry + R.d[1], rz + R.d[2]);
+      }
+      for (int q = 0; q < A.npairs; ++q) {
+        const int c0 = A.pc[q];
+        T v0[CU], v1[CU];
+#pragma unroll
+        for (int u = 0; u < CU; ++u)
+          if (ok[u]) {
+            v0[u] = A.y[src[u] + c0 * S.cs];
+            v1[u] = A.y[src[u] + (c0 + 1) * S.cs];
+          }
+#pragma unroll
+        for (int u = 0; u < CU; ++u)
+          if (ok[u]) {
+            A.y[dst[u] + c0 * B.cs] = v0[u];
+            A.y[dst[u] + (c0 + 1) * B.cs] = v1[u];
+          }
+      }
+    }
+  }
+}
+
 template <typename T, int RAD>
 __global__ void __launch_bounds__(256, 3) ghost_region_kernel(const GhostArgs<T> A) {
   // [2][pz][py][px]: time-interpolated psi1, psi2 in the field precision
@@ -229,7 +276,7 @@ __global__ void __launch_bounds__(256, 3) ghost_region_kernel(const GhostArgs<T>
     w0[o + RAD] = (T)pw(A.itype, 0, o);
     w1[o + RAD] = (T)pw(A.itype, 1, o);
   }
-  for (int r = blockIdx.x; r < A.nregions; r += gridDim.x) {
+  for (int r = A.r0 + blockIdx.x; r < A.nregions; r += gridDim.x) {
     const GhostRegion R = A.regions[r];
     const BoxDev B = A.boxes[R.box];
     const int ncell = R.ext[0] * R.ext[1] * R.ext[2];
@@ -336,6 +383,7 @@ static slh_status ghosts_t(slh_ctx* c, int lev, int role, double alpha, int ityp
   GhostArgs<T> A;
   A.boxes = L.d_boxes;
   A.regions = L.d_gregions;
+  A.r0 = L.ncopyregions;
   A.nregions = L.ngregions;
   A.pieces = L.d_pieces;
   A.y = static_cast<T*>(L.buf[role]);
@@ -376,15 +424,21 @@ static slh_status ghosts_t(slh_ctx* c, int lev, int role, double alpha, int ityp
     cudaFuncSetAttribute(ghost_region_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     attr = true;
   }
-  // many more CTAs than resident slots: prolongation and copy regions cost
-  // very different amounts, and the block scheduler evens them out
-  long long blocks = L.ngregions;
+  // many more CTAs than resident slots: regions cost very different
+  // amounts, and the block scheduler evens them out
   const long long cap = (long long)c->num_sms * 16;
-  if (blocks > cap) blocks = cap;
-  if (itype == 4) ghost_region_kernel<T, 2><<<(int)blocks, 256, smem, c->stream>>>(A);
-  else if (itype == 2) ghost_region_kernel<T, 1><<<(int)blocks, 256, smem, c->stream>>>(A);
-  else ghost_region_kernel<T, 0><<<(int)blocks, 256, smem, c->stream>>>(A);
-  SLH_CUDA(cudaGetLastError());
+  if (A.r0 > 0) {
+    const long long blocks = std::min<long long>(A.r0, cap);
+    ghost_copy_kernel<T><<<(int)blocks, 256, 0, c->stream>>>(A);
+    SLH_CUDA(cudaGetLastError());
+  }
+  if (A.nregions > A.r0) {
+    const long long blocks = std::min<long long>(A.nregions - A.r0, cap);
+    if (itype == 4) ghost_region_kernel<T, 2><<<(int)blocks, 256, smem, c->stream>>>(A);
+    else if (itype == 2) ghost_region_kernel<T, 1><<<(int)blocks, 256, smem, c->stream>>>(A);
+    else ghost_region_kernel<T, 0><<<(int)blocks, 256, smem, c->stream>>>(A);
+    SLH_CUDA(cudaGetLastError());
+  }
   return SLH_OK;
 }
 

@@ -110,6 +110,7 @@ struct Level {
   int nb_dom = 0;
   GhostRegion* d_gregions = nullptr;
   int ngregions = 0;
+  int ncopyregions = 0;          // regions [0, ncopyregions) are copies
   PatchPiece* d_pieces = nullptr;
   int npieces = 0;
   long long nghost_cells = 0;

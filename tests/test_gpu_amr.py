@@ -32,8 +32,8 @@ def _dense(level):
     return np.concatenate(parts)
 
 
-def _oracle_hierarchy(p, nlev=3, itype=4):
-    h = oamr.make_hierarchy(N0, DX0, DT0, G, BF, LEVEL_BOXES[:nlev], oparams(p), interp_type=itype, eta0=ETA0)
+def _oracle_hierarchy(p, nlev=3, itype=4, g=G):
+    h = oamr.make_hierarchy(N0, DX0, DT0, g, BF, LEVEL_BOXES[:nlev], oparams(p), interp_type=itype, eta0=ETA0)
     y = inputs.string_loop(N0, 3.0, 2.0, DX0)
     h.levels[0].set_dense(y)
     for l in range(1, nlev):
@@ -44,7 +44,7 @@ def _oracle_hierarchy(p, nlev=3, itype=4):
 
 def _gpu_hierarchy(oh, prec="f64", fused_tags=False):
     nlev = len(oh.levels)
-    h = slh.Hierarchy(N0, DX0, nghost=G, bf=BF, prec=prec, max_levels=nlev)
+    h = slh.Hierarchy(N0, DX0, nghost=oh.levels[0].g, bf=BF, prec=prec, max_levels=nlev)
     for l in range(nlev):
         h.init_level(l, LEVEL_BOXES[l], fused_tags=fused_tags)
         h.set_state(l, _dense(oh.levels[l]))
@@ -67,10 +67,11 @@ def _ghosted(h, lev, g=G):
     return out
 
 
-@pytest.mark.parametrize("nlev", [2, 3])
-def test_subcycled_hierarchy_f64_matches_oracle(nlev):
+@pytest.mark.parametrize("nlev,g", [(2, 3), (3, 3), (3, 2)])
+def test_subcycled_hierarchy_f64_matches_oracle(nlev, g):
+    """g = 2: ghost layers equal to the 4th-order stencil's radius."""
     p = slh.EOMParams(order=4, interp_type=4)
-    oh = _oracle_hierarchy(p, nlev)
+    oh = _oracle_hierarchy(p, nlev, g=g)
     h = _gpu_hierarchy(oh)
     for _ in range(2):
         oh.step()
