@@ -236,9 +236,10 @@ def _time_form(slh, torch, prec, y0_dense, n, K, W, dist, flags, gw=False, order
     tim = h.profile_read(slh.SLH_PROF_TIME)
     gwk = h.profile_read(slh.SLH_PROF_GW)
     h.profile(False, True)
-    E = h.reduce_energy(p, mode=1)
+    E = h.reduce_energy(p, mode=1) if flags & slh.SLH_FUSE_ENERGY else None
     out = dict(ms=ms, stage_ms=stage[0], stage_launches=stage[1], stage_bytes=stage[2],
-               ghost_ms=ghost[0], ghost_launches=ghost[1], time_launches=tim[1], energy=E.tolist(),
+               ghost_ms=ghost[0], ghost_launches=ghost[1], time_launches=tim[1],
+               energy=None if E is None else E.tolist(),
                per_stage_ms=[m / K for m in per_stage], tile_variant=chosen, tune_ms=tune_ms,
                diag_tile_variant=chosen_d, diag_tune_ms=tune_d_ms,
                gw_ms=gwk[0], gw_launches=gwk[1], gw_bytes=gwk[2],
@@ -416,6 +417,21 @@ def run_ours(args, rank, world, local_rank, dist):
                "stage_achieved_gbs": ach_s, "hbm_frac": ach_s / peak, "alg_bytes_per_cell_update": 32 * 4,
                "precision": "FP32 (no compensation)"}
 
+    # the same RK4 steps without the fused tags and energy (the paper tags at
+    # regrid time only): what the diagnostics cost, and the stencil stages'
+    # own share of the HBM roofline
+    plain = None
+    if not args.no_plain:
+        hp, rp = _time_form(slh, torch, "f32", dense, n, K, W, dist, 0)
+        hp.close()
+        del hp
+        torch.cuda.empty_cache()
+        ach_p = rp["stage_bytes"] / (rp["stage_ms"] / 1e3) / 1e9
+        plain = {"workload": WORKLOAD.replace(", tags+energy fused in stage 1", ", no fused tags or energy"),
+                 "unit": "cell-updates/s", "value": world * float(n) ** 3 * K / (rp["ms"] / 1e3),
+                 "ms_per_step": rp["ms"] / K, "per_stage_ms": rp["per_stage_ms"],
+                 "stage_achieved_gbs": ach_p, "hbm_frac": ach_p / peak}
+
     # gravitational-wave tensor fields
     gw = None
     if not args.no_gw:
@@ -442,7 +458,8 @@ def run_ours(args, rank, world, local_rank, dist):
                    "l2": "inputs larger than L2 (10.9 GB of level buffers)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": _stage_traffic(),
-                     "kernel": "stage_kernel<float,3,32,16>", "peak_kind": peak_kind,
+                     "kernel": "stage_kernel<float,3> (4 RK4 stages; tags + energy fused in stage 1)",
+                     "peak_kind": peak_kind,
                      "alg_bytes_per_cell_update": KAHAN_VALUES * 4},
         "fp64_plain": {"value": job_value(world, cells, K, ms64), "unit": "cell-updates/s",
                        "ms_per_step": ms64 / K, "stage_achieved_gbs": ach64,
@@ -458,6 +475,7 @@ def run_ours(args, rank, world, local_rank, dist):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4 * 8},
         "amr": amr,
         "ssprk3": ssp,
+        "plain_step": plain,
         "gw": gw,
         "gpu_launches": launches,
         "clocks": clocks,
@@ -477,6 +495,7 @@ def main():
     ap.add_argument("--no-amr", action="store_true", help="skip the dynamic-AMR line")
     ap.add_argument("--no-gw", action="store_true", help="skip the gravitational-wave tensor line")
     ap.add_argument("--no-ssp", action="store_true", help="skip the SSPRK3 line")
+    ap.add_argument("--no-plain", action="store_true", help="skip the line without fused diagnostics")
     ap.add_argument("--tile", type=int, default=None,
                     help="with --profile-only: use this stage-kernel tile variant instead of autotuning")
     ap.add_argument("--diag-tile", type=int, default=None,

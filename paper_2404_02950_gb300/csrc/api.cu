@@ -1029,6 +1029,15 @@ slh_status slh_advance(slh_ctx* c, double dt0, const slh_eom_params* p, uint32_t
         if (diag) sl.tags = reinterpret_cast<uint8_t*>(1);
         if ((st = launch_stage(c, c->lev[l], *p, sl, nullptr)) != SLH_OK) return st;
       }
+      if (c->ncomp == NCOMP_GW) {
+        StageLaunch sl;
+        memset(&sl, 0, sizeof(sl));
+        sl.dry = true;
+        sl.stage = 1;
+        sl.lev = l;
+        sl.c_buf = -1;
+        if ((st = launch_gw_stage(c, c->lev[l], *p, sl)) != SLH_OK) return st;
+      }
     }
     int saved[MAX_LEVELS][2];
     for (int l = 0; l < c->nlevels; ++l) {

@@ -14,8 +14,11 @@
 // stencil operands are plain global loads: x and y neighbours come from the
 // lines the CTA's own rows bring into L1, z neighbours from planes read a few
 // iterations earlier (L1/L2), so DRAM sees each value about once.
+#include <cuda.h>
+
 #include "slh_internal.cuh"
 #include "stencil.cuh"
+#include "tma.cuh"
 
 namespace slh {
 
@@ -37,6 +40,9 @@ struct GwArgs {
   int friction;
   double inv_dx, inv_dx2;
   double ha, hb;            // a_{s+1} dt, b_s dt
+  const CUtensorMap* tmaps; // TMA form: [box][buffer] maps of the 16-field view
+  int in_buf;               // TMA form: physical index of the stage input buffer
+  int* err;
 };
 
 // (i, j) direction pairs of the six tensor components
@@ -187,6 +193,221 @@ __global__ void __launch_bounds__(COL_TX * COL_TY, sizeof(T) == 4 ? 4 : 3) gw_st
   }
 }
 
+// TMA-fed form (FP32, Laplacian radius G <= 2).  The same items, threads and
+// arithmetic as gw_stage_kernel, but the stencil operands -- psi1, psi2 and
+// the six u_ij of every plane of the column with its x/y halo -- stream into
+// a shared-memory ring of 2G+1+P planes by tensor copies (four 2-component
+// boxes of (32+8) x (8+2G) cells per plane, 16-byte aligned in x), issued P
+// planes ahead by one thread and tracked by mbarrier transaction counts.
+// Only the pointwise operands (v_ij of the input, y_n, D, C) are read from
+// global memory, coalesced, each value once.  Every wait is bounded; on
+// expiry the CTA latches DERR_TIMEOUT, drains its copies (bounded) and leaves.
+constexpr int GWT_P = 2;
+
+template <int G>
+struct GwTmaGeo {
+  static constexpr int SXL = COL_TX + 8;        // x halo of 4 cells each side (G <= 4)
+  static constexpr int SY = COL_TY + 2 * G;
+  static constexpr int RU = 2 * G + 1 + GWT_P;  // ring planes
+  static constexpr int PLANE = SY * SXL;        // floats of one component plane
+  static constexpr int PAIR = 2 * PLANE;        // one tensor copy (2 components)
+  static constexpr int SLOT = 4 * PAIR;         // psi pair + three u pairs
+  static constexpr int BAR_BYTES = 128;
+  static constexpr int SMEM = BAR_BYTES + RU * SLOT * 4;
+  static_assert((PAIR * 4) % 128 == 0, "tensor copy destinations must stay 128-byte aligned");
+};
+
+template <int G>
+__global__ void __launch_bounds__(COL_TX * COL_TY, 2) gw_tma_kernel(const GwArgs<float> A) {
+  using GE = GwTmaGeo<G>;
+  using T = float;
+  constexpr int SXL = GE::SXL, PLANE = GE::PLANE, RU = GE::RU;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem);
+  T* ring = reinterpret_cast<T*>(smem + GE::BAR_BYTES);
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * COL_TX + tx;
+  const int4 it = A.items[blockIdx.x];
+  const BoxDev B = A.boxes[it.x];
+  const int x = it.y + tx, y = it.z + ty;
+  const bool active = x < B.n[0] && y < B.n[1];
+  const int z0 = it.w, z1 = min(it.w + COL_ZLEN, B.n[2]);
+  const int nplanes = (z1 - z0) + 2 * G;
+  const CUtensorMap* map = A.tmaps + (size_t)it.x * SLH_NBUF + A.in_buf;
+
+  if (tid == 0) {
+    for (int i = 0; i < RU; ++i) mbar_init(smem_u32(&bars[i]), 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  // plane z0 - G + t of the input into slot t % RU (one thread)
+  auto issue = [&](int t) {
+    const int slot = t % RU;
+    const unsigned bar = smem_u32(&bars[slot]);
+    mbar_expect_tx(bar, (unsigned)(GE::SLOT * 4));
+    T* dst = ring + slot * GE::SLOT;
+    const int cy = it.z - G + A.gl, cz = z0 - G + t + A.gl;
+    tma_load4(smem_u32(dst), map, it.y, cy, cz, 0, bar);
+    tma_load4(smem_u32(dst + GE::PAIR), map, it.y, cy, cz, GW_U0, bar);
+    tma_load4(smem_u32(dst + 2 * GE::PAIR), map, it.y, cy, cz, GW_U0 + 2, bar);
+    tma_load4(smem_u32(dst + 3 * GE::PAIR), map, it.y, cy, cz, GW_U0 + 4, bar);
+  };
+  int issued = 0;
+  if (tid == 0)
+    for (; issued < GWT_P && issued < nplanes; ++issued) issue(issued);
+
+  const double eta = *A.eta_start + A.c_stage;
+  const T c_fric = (T)(A.friction ? 2.0 / eta : 0.0);
+  const T ha = (T)A.ha, hb = (T)A.hb, idx = (T)A.inv_dx, idx2 = (T)A.inv_dx2;
+  const long long cs = B.cs, sz = (long long)B.pitch * B.pny;
+  const T* __restrict__ in = A.in;
+  const T* __restrict__ yn = A.yn;
+  T* __restrict__ dd = A.d;
+  T* __restrict__ out = A.out;
+  T* __restrict__ cc = A.cc;
+  const int stage = A.stage;
+  const bool ssp = A.ssp != 0;
+  const T sa = (T)A.sa, sb = (T)A.sb;
+  const int cell = (ty + G) * SXL + 4 + tx;   // this thread's cell in a component plane
+  long long e = B.off + ((long long)(z0 + A.gl) * B.pny + (y + A.gl)) * B.pitch + x + XPAD;
+
+  int t = 0;
+  bool aborted = false;
+  for (; t < nplanes; ++t) {
+    if (tid == 0 && issued < nplanes) {
+      fence_proxy_async();
+      issue(issued);
+      ++issued;
+    }
+    const bool ok = mbar_wait(smem_u32(&bars[t % RU]), (unsigned)((t / RU) & 1));
+    const int z = z0 - 2 * G + t;
+    if (ok && active && z >= z0) {
+      // ring slots of planes z-G .. z+G
+      int sb_[2 * G + 1];
+#pragma unroll
+      for (int k = 0; k <= 2 * G; ++k) sb_[k] = ((t - 2 * G + k) % RU) * GE::SLOT + cell;
+      auto S = [&](int comp, int dx, int dy, int dz) -> T { return ring[sb_[dz + G] + comp * PLANE + dy * SXL + dx]; };
+      // pointwise operands of the six components, all issued first
+      T v[6], yu[6], yv[6], du[6], dv[6], cu[6], cv[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const long long eu = e + (GW_U0 + k) * cs, ev = e + (GW_V0 + k) * cs;
+        v[k] = __ldg(in + ev);
+        yu[k] = yv[k] = du[k] = dv[k] = cu[k] = cv[k] = 0;
+        if (stage >= 2) {
+          yu[k] = __ldg(yn + eu);
+          yv[k] = __ldg(yn + ev);
+          if (!ssp) {
+            du[k] = dd[eu];
+            dv[k] = dd[ev];
+          }
+        }
+        if (stage == 4 && cc != nullptr) {
+          cu[k] = cc[eu];
+          cv[k] = cc[ev];
+        }
+      }
+      // gradients of psi1, psi2
+      T g1[3], g2[3];
+#pragma unroll
+      for (int dir = 0; dir < 3; ++dir) {
+        T a1 = 0, a2 = 0;
+#pragma unroll
+        for (int m = 1; m <= G; ++m) {
+          const T w = (T)grad_w<G>(m);
+          const int dx = dir == 0 ? m : 0, dy = dir == 1 ? m : 0, dz = dir == 2 ? m : 0;
+          a1 += w * (S(0, dx, dy, dz) - S(0, -dx, -dy, -dz));
+          a2 += w * (S(1, dx, dy, dz) - S(1, -dx, -dy, -dz));
+        }
+        g1[dir] = a1 * idx;
+        g2[dir] = a2 * idx;
+      }
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const long long eu = e + (GW_U0 + k) * cs, ev = e + (GW_V0 + k) * cs;
+        const int c = 2 + k;
+        const T u0 = S(c, 0, 0, 0);
+        // difference form, as the scalar FP32 stage
+        T a = 0;
+#pragma unroll
+        for (int m = 1; m <= G; ++m) {
+          const T w = (T)lap_w<G>(m);
+          a += w * ((((S(c, m, 0, 0) - u0) + (S(c, -m, 0, 0) - u0)) + ((S(c, 0, m, 0) - u0) + (S(c, 0, -m, 0) - u0))) +
+                    ((S(c, 0, 0, m) - u0) + (S(c, 0, 0, -m) - u0)));
+        }
+        const T lap = a * idx2;
+        const int i = pair_i(k), j = pair_j(k);
+        const T g1i = i == 0 ? g1[0] : (i == 1 ? g1[1] : g1[2]), g1j = j == 0 ? g1[0] : (j == 1 ? g1[1] : g1[2]);
+        const T g2i = i == 0 ? g2[0] : (i == 1 ? g2[1] : g2[2]), g2j = j == 0 ? g2[0] : (j == 1 ? g2[1] : g2[2]);
+        const T src = (T)2 * (g1i * g1j + g2i * g2j);
+        const T ku = v[k];
+        const T kv = ((-c_fric) * v[k] + lap) + src;
+        if (ssp) {
+          const T fu = u0 + ha * ku, fv = v[k] + ha * kv;
+          if (stage == 1) {
+            out[eu] = fu;
+            out[ev] = fv;
+          } else {
+            out[eu] = sa * yu[k] + sb * fu;
+            out[ev] = sa * yv[k] + sb * fv;
+          }
+        } else if (stage == 1) {
+          out[eu] = u0 + ha * ku;
+          out[ev] = v[k] + ha * kv;
+          dd[eu] = hb * ku;
+          dd[ev] = hb * kv;
+        } else if (stage == 2 || stage == 3) {
+          out[eu] = yu[k] + ha * ku;
+          out[ev] = yv[k] + ha * kv;
+          dd[eu] = du[k] + hb * ku;
+          dd[ev] = dv[k] + hb * kv;
+        } else {
+          const T iu = du[k] + hb * ku, iv = dv[k] + hb * kv;
+          if (cc != nullptr) {
+            // compensated sum y + inc, the rounding error carried in C
+            T w, sm;
+            w = iu - cu[k]; sm = yu[k] + w; cc[eu] = (sm - yu[k]) - w; out[eu] = sm;
+            w = iv - cv[k]; sm = yv[k] + w; cc[ev] = (sm - yv[k]) - w; out[ev] = sm;
+          } else {
+            out[eu] = yu[k] + iu;
+            out[ev] = yv[k] + iv;
+          }
+        }
+      }
+    }
+    if (z >= z0) e += sz;
+    if (__syncthreads_or(!ok)) {
+      aborted = true;
+      break;
+    }
+  }
+  if (aborted) {
+    // latch the error and drain every copy still in flight (bounded)
+    if (tid == 0) {
+      atomicCAS(A.err, 0, DERR_TIMEOUT);
+      for (int u = t; u < issued; ++u) mbar_wait(smem_u32(&bars[u % RU]), (unsigned)((u / RU) & 1));
+    }
+    __syncthreads();
+  }
+}
+
+template <int G>
+static slh_status gw_tma_launch(slh_ctx* c, Level& L, const StageLaunch& s, GwArgs<float>& A) {
+  CUtensorMap* maps = nullptr;
+  slh_status st = build_gw_tmaps(c, L, G, COL_TX, COL_TY, &maps);
+  if (st != SLH_OK) return st;
+  static bool attr = false;
+  if (!attr) {
+    SLH_CUDA(cudaFuncSetAttribute(gw_tma_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, GwTmaGeo<G>::SMEM));
+    attr = true;
+  }
+  if (s.dry) return SLH_OK;   // preparation only (before stream capture)
+  A.tmaps = maps;
+  A.in_buf = s.in_buf;
+  gw_tma_kernel<G><<<L.ncol_items, dim3(COL_TX, COL_TY), GwTmaGeo<G>::SMEM, c->stream>>>(A);
+  SLH_CUDA(cudaGetLastError());
+  return SLH_OK;
+}
+
 template <typename T>
 static slh_status gw_stage_t(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s) {
   if (L.ncol_items == 0) return SLH_OK;
@@ -210,6 +431,15 @@ static slh_status gw_stage_t(slh_ctx* c, Level& L, const slh_eom_params& p, cons
   A.ssp = s.ssp;
   A.sa = s.sa;
   A.sb = s.sb;
+  A.tmaps = nullptr;
+  A.in_buf = s.in_buf;
+  A.err = c->d_err;
+  if constexpr (sizeof(T) == 4) {
+    // FP32, Laplacian radius <= 2: the TMA-fed form
+    if (p.lap_order == 2) return gw_tma_launch<1>(c, L, s, A);
+    if (p.lap_order == 4) return gw_tma_launch<2>(c, L, s, A);
+  }
+  if (s.dry) return SLH_OK;
   const dim3 block(COL_TX, COL_TY);
   switch (p.lap_order) {
     case 2: gw_stage_kernel<T, 1><<<L.ncol_items, block, 0, c->stream>>>(A); break;

@@ -27,11 +27,11 @@
 
 #include "slh_internal.cuh"
 #include "stencil.cuh"
+#include "tma.cuh"
 
 namespace slh {
 
 constexpr int NPW_MAX = 7;   // pointwise boxes: Pi | y_n(0,1) y_n(2,3) | D(0,1) D(2,3) | C(0,1) C(2,3)
-constexpr long long WAIT_LIMIT = 1ll << 22;
 
 template <typename T>
 struct StageArgs {
@@ -60,43 +60,6 @@ struct StageArgs {
   int* err;
 };
 
-// ---------------------------------------------------------------------------
-// PTX helpers (TMA, mbarrier)
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
-  unsigned done;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(done)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-// bounded wait on a phase of an mbarrier; false if the limit expired
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-  for (long long i = 0; i < WAIT_LIMIT; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-__device__ __forceinline__ void tma_load4(unsigned dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                          unsigned bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(
-          dst),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
-      : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
 // Winding contribution of the edge a -> b: +1 when it leaves the upper half
@@ -748,6 +711,53 @@ static slh_status build_tmaps(slh_ctx* c, Level& L, int G, int TX, int TY, CUten
   if (e != cudaSuccess) {
     cudaFree(d);
     return cuda_fail(e, "tensor maps upload");
+  }
+  L.tmaps[key] = d;
+  *out = d;
+  return SLH_OK;
+}
+
+// Tensor maps of the TMA-fed gravitational-wave stage: per (box, buffer)
+// one map of the 4D view {pitch, pny, pnz, 16 components} of the box with
+// the halo'd 2-component box {TX+8, TY+2G, 1, 2}; psi and the three pairs of
+// u_ij are four copies of it per plane.  FP32 levels only.
+slh_status build_gw_tmaps(slh_ctx* c, Level& L, int G, int TX, int TY, CUtensorMap** out) {
+  const unsigned long long key = (1ull << 63) | ((unsigned long long)G << 32) | ((unsigned long long)TX << 16) | (unsigned)TY;
+  auto it = L.tmaps.find(key);
+  if (it != L.tmaps.end()) {
+    *out = static_cast<CUtensorMap*>(it->second);
+    return SLH_OK;
+  }
+  if (c->prec == SLH_F64 || c->ncomp != NCOMP_GW) return fail(SLH_ERR_STATE, "gw tensor maps: FP32 16-field levels only");
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return fail(SLH_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const size_t es = 4;
+  const int nb = (int)L.lay.boxes.size();
+  std::vector<CUtensorMap> maps((size_t)nb * SLH_NBUF);
+  for (int b = 0; b < nb; ++b) {
+    const BoxDev& B = L.lay.boxes[b];
+    for (int k = 0; k < SLH_NBUF; ++k) {
+      CUtensorMap& m = maps[(size_t)b * SLH_NBUF + k];
+      memset(&m, 0, sizeof(m));
+      if (!L.buf[k]) continue;
+      void* base = static_cast<char*>(L.buf[k]) + (size_t)B.off * es;
+      cuuint64_t dims[4] = {(cuuint64_t)B.pitch, (cuuint64_t)B.pny, (cuuint64_t)B.pnz, (cuuint64_t)NCOMP_GW};
+      cuuint64_t strides[3] = {(cuuint64_t)B.pitch * es, (cuuint64_t)B.pitch * B.pny * es, (cuuint64_t)B.cs * es};
+      cuuint32_t box[4] = {(cuuint32_t)(TX + 8), (cuuint32_t)(TY + 2 * G), 1, 2};
+      cuuint32_t estr[4] = {1, 1, 1, 1};
+      CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return fail(SLH_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for gw box %d buffer %d", (int)r, b, k);
+    }
+  }
+  CUtensorMap* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(CUtensorMap) * maps.size());
+  if (e != cudaSuccess) return fail(SLH_ERR_NOMEM, "gw tensor maps: %s", cudaGetErrorString(e));
+  e = cudaMemcpy(d, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    return cuda_fail(e, "gw tensor maps upload");
   }
   L.tmaps[key] = d;
   *out = d;

@@ -11,6 +11,7 @@ import paper_2404_02950_gb300 as slh
 from oracle import amr as oamr
 from oracle import gw as ogw
 from oracle import gw_spectrum as ogs
+from oracle import ssprk3 as ossp
 from paper_2404_02950_gb300 import inputs
 from tests.helpers import oparams, rel_l2
 
@@ -65,14 +66,24 @@ def test_uniform_f64_matches_oracle(order):
     assert rel_l2(exp[4], y[4]) > 1e-3
 
 
-def test_uniform_f32_kahan_within_bound():
-    p = slh.EOMParams(order=4)
+@pytest.mark.parametrize("order,integrator", [(2, 4), (4, 4), (6, 4), (2, 10), (4, 10)])
+def test_uniform_f32_within_bound(order, integrator):
+    """FP32 (Kahan at RK4's last stage) for every Laplacian order and both
+    integrators: orders 2 and 4 run the TMA-fed GW kernel, order 6 the
+    column kernel."""
+    p = slh.EOMParams(order=order, integrator=integrator)
     y = _initial()
-    exp = _oracle(y, p, 5)
+    if integrator == 4:
+        exp = _oracle(y, p, 5)
+    else:
+        exp, eta = tuple(np.asarray(a, dtype=np.float64) for a in y), ETA0
+        for _ in range(5):
+            exp = ossp.ssprk3_step_periodic(exp, eta, DT, DX, oparams(p), f=ogw.f_periodic)
+            eta += DT
     got = _gpu([a.astype(np.float32) for a in y], p, "f32", 5)
     for c in range(16):
         e = rel_l2(got[c].astype(np.float64), exp[c])
-        assert e <= 1e-4, (c, e)
+        assert e <= 1e-4, (order, integrator, c, e)
 
 
 def test_no_source_without_gradients_and_free_mode():
@@ -197,3 +208,25 @@ def test_spectrum_needs_tensor_fields():
     with pytest.raises(slh.SlhError) as e:
         h.gw_spectrum(2)
     assert e.value.code == -7
+
+
+def test_f32_graph_replay_matches_direct_steps():
+    """The TMA-fed GW kernel inside the captured coarse-step graph (tensor
+    maps prepared before capture) gives the direct launches' result bit for
+    bit."""
+    p = slh.EOMParams(order=4)
+    y = [a.astype(np.float32) for a in _initial()]
+    outs = []
+    for use_graph in (False, True):
+        h = slh.Hierarchy(N, DX, nghost=G, bf=BF, prec="f32", max_levels=1, gw=True)
+        h.init_level(0, FULL)
+        h.set_state(0, slh.dense_from_boxes(y, FULL))
+        h.set_eta(ETA0)
+        for _ in range(3):
+            if use_graph:
+                h.advance(DT, p)
+            else:
+                h.rk_step(0, DT, p)
+        outs.append(h.get_state(0))
+        h.close()
+    assert np.array_equal(outs[0], outs[1])
