@@ -244,18 +244,27 @@ __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stag
     }
   }
 
-  // per-thread energy partials in the field precision with a compensation
-  // term each (Kahan), so that no FP64 work remains inside the plane loop
-  // (FP64 runs at 1/64 of the FP32 rate here); FP64 from the block reduction on
+  // per-thread energy partials in the field precision, FP32 ones with a
+  // compensation term each (Kahan), so that no FP64 work remains inside the
+  // plane loop of the FP32 form (FP64 runs at 1/64 of the FP32 rate here);
+  // FP64 from the block reduction on
   // per-thread counts stay far below 2^32: at most 3 per cell a thread visits,
   // and a persistent CTA visits (cells of the level) / (CTAs) of them
   unsigned n_pierced = 0, n_tagged = 0;
   T i_kin = 0, i_grad = 0, i_pot = 0, c_kin = 0, c_grad = 0, c_pot_ = 0;
+  // (FP64 partials need no compensation: a thread sums some thousands of
+  // terms, whose rounding stays near 1e-13 relative, and every FP64 add
+  // costs as much as 64 FP32 ones here)
   auto kahan = [](T& sum, T& comp, T v) {
-    const T y_ = v - comp;
-    const T t_ = sum + y_;
-    comp = (t_ - sum) - y_;
-    sum = t_;
+    if constexpr (sizeof(T) == 8) {
+      (void)comp;
+      sum += v;
+    } else {
+      const T y_ = v - comp;
+      const T t_ = sum + y_;
+      comp = (t_ - sum) - y_;
+      sum = t_;
+    }
   };
   int cur_box = -1;
   BoxDev B;
