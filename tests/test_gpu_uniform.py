@@ -14,7 +14,8 @@ from oracle import energy as oenergy
 from oracle import rk4 as ork4
 from oracle import winding as owinding
 from paper_2404_02950_gb300 import inputs
-from tests.helpers import download_domain, oparams, rel_l2, tags_domain, uniform_hierarchy, upload
+from tests.helpers import (box_padded_views, download_domain, oparams, rel_l2, tags_domain, uniform_hierarchy,
+                           upload)
 
 pytestmark = pytest.mark.gpu
 
@@ -172,32 +173,97 @@ def _local_rk4_center(y, idx, half, eta, dt, dx, op):
     return np.array([o[half, half, half] for o in out])
 
 
+def _local_tag(y, idx):
+    """The oracle's winding tag of one cell from a periodic 5^3 patch."""
+    k, j, i = idx
+    n = y[0].shape[0]
+    r = [np.arange(c - 2, c + 3) % n for c in (k, j, i)]
+    t = owinding.cell_tags_padded(y[0][np.ix_(*r)], y[1][np.ix_(*r)], 2)
+    return int(t[0, 0, 0])
+
+
+def _check_sampled(get, y0, n_field, idx, dt, dx, p, prec, tags=None):
+    """Sampled cells of one RK4 step (and their tags) against the oracle;
+    ``get(c3)`` returns the 4 GPU values at lattice cell c3 and the snapshot
+    is periodic with period n_field."""
+    half = 4 * 3 + 1
+    tol = 1e-12 if prec == "f64" else 1e-5
+    for c3 in idx:
+        cm = tuple(v % n_field for v in c3)
+        exp = _local_rk4_center(y0, cm, half, ETA0, dt, dx, oparams(p))
+        got = get(c3)
+        scale = max(1.0, float(np.max(np.abs(exp))))
+        assert np.max(np.abs(got - exp)) <= tol * scale, (c3, got, exp)
+        if tags is not None:
+            assert tags(c3) == _local_tag(y0, cm), c3
+
+
+def _bench_launch(h, p):
+    """The launch configuration of the benchmark: both autotuners, then one
+    RK4 step with the winding tags and energy fused in stage 1."""
+    h.autotune(0, p, reps=2)
+    h.autotune(0, p, reps=2, diag=True)
+    h.rk_step(0, DX_FULL / 4, p, flags=slh.SLH_FUSE_TAG | slh.SLH_FUSE_ENERGY)
+
+
+DX_FULL = 0.125
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_full_size_512_order6_sampled(prec):
     """512^3, 6th-order Laplacian, one RK4 step in the benchmark's launch
-    configuration; 48 sampled cells computed one by one by the oracle."""
+    configuration (autotuned tiles, tags and energy fused in stage 1); 48
+    sampled cells computed one by one by the oracle, their tags too."""
     import torch
-    n, dx = 512, 0.125
+    n, dx = 512, DX_FULL
     p = slh.EOMParams(order=6)
     y0 = inputs.gaussian_field(n, n / 16.0, seed=0)
-    h, boxes = uniform_hierarchy(n, dx, prec=prec, nghost=3, bf=16)
+    h, boxes = uniform_hierarchy(n, dx, prec=prec, nghost=3, bf=16, fused_tags=True)
     upload(h, 0, y0, boxes)
     h.set_eta(ETA0)
-    dt = dx / 4
-    h.rk_step(0, dt, p)
+    _bench_launch(h, p)
     g = h.get_state(0).reshape(4, n, n, n)
+    tg = h.fused_tags(0).reshape(n, n, n)
     rng = np.random.default_rng(5)
     idx = [tuple(int(v) for v in rng.integers(0, n, size=3)) for _ in range(44)]
     idx += [(0, 0, 0), (n - 1, n - 1, n - 1), (0, n - 1, 5), (n - 1, 3, 0)]
-    half = 4 * 3 + 1
-    tol = 1e-12 if prec == "f64" else 1e-5
-    for c3 in idx:
-        exp = _local_rk4_center(y0, c3, half, ETA0, dt, dx, oparams(p))
-        got = g[:, c3[0], c3[1], c3[2]].astype(np.float64)
-        scale = max(1.0, float(np.max(np.abs(exp))))
-        assert np.max(np.abs(got - exp)) <= tol * scale, (c3, got, exp)
+    _check_sampled(lambda c3: g[:, c3[0], c3[1], c3[2]].astype(np.float64), y0, n, idx, dx / 4, dx, p, prec,
+                   tags=lambda c3: int(tg[c3]))
     del h
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.slow
+def test_max_size_1024_f32_sampled():
+    """1024^3 FP32 + Kahan, the largest uniform scalar lattice one GPU holds
+    in this form (5 level buffers, 86 GB): the 512^3 Gaussian field tiled
+    twice per axis (periodic, so the oracle's patches come from the 512^3
+    arrays), written into the level on the device; one RK4 step in the
+    benchmark's launch configuration; 24 sampled cells and their tags against
+    the oracle, read back one by one."""
+    import torch
+    n, m, dx = 1024, 512, DX_FULL
+    p = slh.EOMParams(order=6)
+    y0 = inputs.gaussian_field(m, m / 16.0, seed=2)
+    h, boxes = uniform_hierarchy(n, dx, prec="f32", nghost=3, bf=16, fused_tags=True)
+    v = box_padded_views(h, 0)[0]
+    for c in range(4):
+        t = torch.from_numpy(y0[c].astype(np.float32)).to(v.device)
+        v[c, 3:3 + n, 3:3 + n, 4:4 + n] = t.repeat(2, 2, 2)
+        del t
+    torch.cuda.synchronize()
+    h.set_eta(ETA0)
+    _bench_launch(h, p)
+    h.sync()
+    out = box_padded_views(h, 0)[0]
+    tg = h.fused_tags(0).reshape(n, n, n)
+    rng = np.random.default_rng(9)
+    idx = [tuple(int(v) for v in rng.integers(0, n, size=3)) for _ in range(20)]
+    idx += [(0, 0, 0), (n - 1, n - 1, n - 1), (511, 512, 1023), (1023, 0, 512)]
+    _check_sampled(lambda c3: out[:, 3 + c3[0], 3 + c3[1], 4 + c3[2]].double().cpu().numpy(), y0, m, idx,
+                   dx / 4, dx, p, "f32", tags=lambda c3: int(tg[c3]))
+    del out, v, h
     torch.cuda.empty_cache()
 
 
