@@ -350,3 +350,47 @@ def test_bounded_wait_expiry_is_reported_and_context_survives():
     ref = ork4.rk4_step_periodic(y0, 0.5, 0.05, dx, oparams(p))
     g = download_domain(h, 0, boxes, n)
     assert max(rel_l2(g[c], ref[c]) for c in range(4)) <= 1e-5
+
+
+@pytest.mark.parametrize("prec,nvar", [("f32", 4), ("f64", 3)])
+def test_tags_bit_exact_on_ties_signed_zeros_and_near_ties(prec, nvar):
+    """Winding tags where the method meets its degenerate cases: values from a
+    small set with signed zeros (Im = +-0 counts as upper, X = 0 on many
+    edges), neighbours that are exact multiples of each other (X = 0 across
+    crossing edges) and near ties (X tiny but nonzero, the FP32 form's exact
+    fallback).  Fused in stage 1 and standalone, on every diagnostics tile,
+    bit-exact with the oracle on the same snapshot; ragged boxes."""
+    n, dx = 24, 0.125
+    rng = np.random.default_rng(11)
+    vals = np.array([-2.0, -1.0, -0.5, -0.0, 0.0, 0.5, 1.0, 2.0])
+    p1 = rng.choice(vals, size=(n, n, n))
+    p2 = rng.choice(vals, size=(n, n, n))
+    sh1, sh2 = np.roll(p1, 1, axis=2), np.roll(p2, 1, axis=2)
+    m = rng.random((n, n, n)) < 0.25
+    s = rng.choice([-1.0, 2.0, 0.5, -0.5], size=(n, n, n))
+    p1, p2 = np.where(m, s * sh1, p1), np.where(m, s * sh2, p2)
+    q = rng.random((n, n, n)) < 0.15
+    p1 = np.where(q, np.roll(p1, 1, axis=1) * (1.0 + 2.0 ** -20), p1)
+    p2 = np.where(q, np.roll(p2, 1, axis=1), p2)
+    z = np.zeros((n, n, n))
+    y0 = [p1, p2, z, z.copy()]
+    boxes = [((0, 0, 0), (23, 11, 23)), ((0, 12, 0), (11, 23, 23)), ((12, 12, 0), (23, 23, 15)),
+             ((12, 12, 16), (23, 23, 23))]
+    p = slh.EOMParams(order=4)
+    for v in range(nvar):
+        h, _ = uniform_hierarchy(n, dx, prec=prec, nghost=3, bf=4, boxes=boxes, fused_tags=True)
+        h.set_diag_tile(0, v)
+        upload(h, 0, y0, boxes)
+        h.set_eta(0.5)
+        snap = download_domain(h, 0, boxes, n)       # the values as stored (FP32: rounded)
+        exp = owinding.cell_tags_periodic(snap[0], snap[1])
+        assert 0 < int(exp.sum()) < exp.size
+        h.rk_step(0, 0.02, p, flags=slh.SLH_FUSE_TAG)
+        assert np.array_equal(tags_domain(h.fused_tags(0), boxes, n), exp), v
+        # standalone tags of the stepped state
+        snap2 = download_domain(h, 0, boxes, n)
+        t, cnt = h.tag(0)
+        exp2 = owinding.cell_tags_periodic(snap2[0], snap2[1])
+        assert np.array_equal(tags_domain(t.cpu().numpy(), boxes, n), exp2), v
+        assert cnt == int(exp2.sum())
+        h.close()
