@@ -11,10 +11,10 @@
   the spatial weights of ``interp`` applied to coarse values interpolated in
   time between the coarse states at the start and end of the coarse step
   (fraction alpha of that step).
-* One RK4 step of level l fills ghosts before every stage at the stage time:
+* One step of level l (classic RK4, SSPRK3 or RKN4) fills ghosts before every stage at the stage time:
   the fine sub-step i in {0, 1} of the coarse step has stage fractions
   alpha = (i + c_s) / 2, c = (0, 1/2, 1/2, 1).
-* advance(l): keep the level's state as "old", take one RK4 step; if a finer
+* advance(l): keep the level's state as "old", take one step; if a finer
   level exists, advance it twice, then synchronise: every coarse cell covered
   by the finer level becomes the mean of its 8 children (all four fields).
 * eta: level 0 advances by repeated addition of dt_0; the finer level's
@@ -31,7 +31,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import gw as ogw
-from . import ko, ssprk3, tee
+from . import ko, rkn4, ssprk3, tee
 from . import interp, winding
 from .eom import EOMParams, rhs
 from .energy import energy_box
@@ -195,8 +195,10 @@ class Hierarchy:
         self.levels = levels
         self.p = params
         self.interp_type = interp_type
-        if integrator not in (4, 10):
-            raise ValueError("integrator must be 4 (classic RK4) or 10 (low-storage SSPRK3)")
+        if integrator not in (4, 10, 21):
+            raise ValueError("integrator must be 4 (classic RK4), 10 (low-storage SSPRK3) or 21 (RKN4)")
+        if integrator == 21 and params.ko_order:
+            raise ValueError("RKN4 needs x' = v: no Kreiss-Oliger term")
         self.integrator = integrator
         self.gw = gw
         # ghosts of psi (stencil), of Pi under dissipation, and of u_ij
@@ -253,6 +255,44 @@ class Hierarchy:
             v = L.valid(b)
             L.data[b][v] = U[b][v]
 
+    def rkn4_level(self, lev, sub):
+        """One RKN4 step of level ``lev`` (oracle/rkn4.py): stage s from the
+        positions and velocities the previous stages' accelerations give,
+        ghosts at time fraction (sub + c_s)/2 of the coarser step."""
+        L = self.levels[lev]
+        C = self.coarse_of(lev)
+        g, dt, eta = L.g, L.dt, L.eta
+        pos, vel = (rkn4.POS_GW, rkn4.VEL_GW) if self.gw else (rkn4.POS, rkn4.VEL)
+        y0 = [a.copy() for a in L.data]
+        Y = [a.copy() for a in y0]
+        acc = []                              # per stage: per box, the accelerations (len(vel), nz, ny, nx)
+        for s in range(4):
+            alpha = (sub + rkn4.C[s]) / 2.0
+            if s > 0:
+                for b in range(len(Y)):
+                    v = L.valid(b)
+                    x0 = [y0[b][i][v[1:]] for i in pos]
+                    v0 = [y0[b][i][v[1:]] for i in vel]
+                    xs, vs = rkn4.stage_states(x0, v0, dt, [a[b] for a in acc], s)
+                    for i, a in zip(pos, xs):
+                        Y[b][i][v[1:]] = a
+                    for i, a in zip(vel, vs):
+                        Y[b][i][v[1:]] = a
+            fill_ghosts(L, Y, C, alpha, self.interp_type, comps=self.ghost_comps)
+            if s == 0 and self.record_tags:
+                self.tag_log.append((lev, eta, [winding.cell_tags_padded(a[0], a[1], g) for a in Y]))
+            acc.append([[k[i] for i in vel] for k in
+                        (self._rhs(Y[b], g, L.dx, eta + rkn4.C[s] * dt) for b in range(len(Y)))])
+        for b in range(len(Y)):
+            v = L.valid(b)
+            x0 = [y0[b][i][v[1:]] for i in pos]
+            v0 = [y0[b][i][v[1:]] for i in vel]
+            xn, vn = rkn4.final_state(x0, v0, dt, [a[b] for a in acc])
+            for i, a in zip(pos, xn):
+                L.data[b][i][v[1:]] = a
+            for i, a in zip(vel, vn):
+                L.data[b][i][v[1:]] = a
+
     def _rhs(self, arr, g, dx, eta):
         k = rhs_box(arr, g, dx, eta, self.p)
         if not self.gw:
@@ -294,6 +334,8 @@ class Hierarchy:
         L.old = [a.copy() for a in L.data]
         if self.integrator == 4:
             self.rk4_level(lev, sub)
+        elif self.integrator == 21:
+            self.rkn4_level(lev, sub)
         else:
             self.ssprk3_level(lev, sub)
         L.eta = eta_start + L.dt

@@ -5,12 +5,12 @@ polynomial coarse field must equal its exact fine cell averages."""
 import numpy as np
 import pytest
 
-from oracle import amr, interp, rk4, ssprk3
+from oracle import amr, interp, rk4, rkn4, ssprk3
 from oracle.eom import EOMParams
 from paper_2404_02950_gb300 import inputs
 
 
-@pytest.mark.parametrize("order,integrator,ko_order", [(2, 4, 0), (4, 4, 0), (4, 10, 0), (4, 4, 5)])
+@pytest.mark.parametrize("order,integrator,ko_order", [(2, 4, 0), (4, 4, 0), (4, 10, 0), (4, 4, 5), (4, 21, 0)])
 def test_full_cover_fine_level_equals_uniform_fine_run(order, integrator, ko_order):
     n0, dx0, dt0, g, bf = 8, 0.25, 1.0 / 16, 3, 4
     p = EOMParams(order=order, ko_order=ko_order, ko_eps=0.05 if ko_order else 0.0)
@@ -30,9 +30,10 @@ def test_full_cover_fine_level_equals_uniform_fine_run(order, integrator, ko_ord
     if integrator == 4:
         ref, _ = rk4.evolve_periodic(fine0, eta0, dt0 / 2, dx0 / 2, 2 * nsteps, p)
     else:
+        step = rkn4.rkn4_step_periodic if integrator == 21 else ssprk3.ssprk3_step_periodic
         ref, eta = fine0, eta0
         for _ in range(2 * nsteps):
-            ref = ssprk3.ssprk3_step_periodic(ref, eta, dt0 / 2, dx0 / 2, p)
+            ref = step(ref, eta, dt0 / 2, dx0 / 2, p)
             eta += dt0 / 2
     L1 = h.levels[1]
     for b, (lo, hi) in enumerate(L1.boxes):
