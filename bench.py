@@ -417,6 +417,20 @@ def run_ours(args, rank, world, local_rank, dist):
                "stage_achieved_gbs": ach_s, "hbm_frac": ach_s / peak, "alg_bytes_per_cell_update": 32 * 4,
                "precision": "FP32 (no compensation)"}
 
+    # the same workload with RKN4 (integrator type 21)
+    rkn = None
+    if not args.no_rkn:
+        hr, rr = _time_form(slh, torch, "f32", dense, n, K, W, dist, flags, integrator=21)
+        hr.close()
+        del hr
+        torch.cuda.empty_cache()
+        ach_r = rr["stage_bytes"] / (rr["stage_ms"] / 1e3) / 1e9
+        rkn = {"workload": WORKLOAD.replace("classic RK4", "RKN4 (integrator type 21)"),
+               "unit": "cell-updates/s", "value": world * float(n) ** 3 * K / (rr["ms"] / 1e3),
+               "ms_per_step": rr["ms"] / K, "per_stage_ms": rr["per_stage_ms"],
+               "stage_achieved_gbs": ach_r, "hbm_frac": ach_r / peak, "alg_bytes_per_cell_update": 72 * 4,
+               "precision": "FP32 + Kahan"}
+
     # the same RK4 steps without the fused tags and energy (the paper tags at
     # regrid time only): what the diagnostics cost, and the stencil stages'
     # own share of the HBM roofline
@@ -475,6 +489,7 @@ def run_ours(args, rank, world, local_rank, dist):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4 * 8},
         "amr": amr,
         "ssprk3": ssp,
+        "rkn4": rkn,
         "plain_step": plain,
         "gw": gw,
         "gpu_launches": launches,
@@ -496,6 +511,7 @@ def main():
     ap.add_argument("--no-gw", action="store_true", help="skip the gravitational-wave tensor line")
     ap.add_argument("--no-ssp", action="store_true", help="skip the SSPRK3 line")
     ap.add_argument("--no-plain", action="store_true", help="skip the line without fused diagnostics")
+    ap.add_argument("--no-rkn", action="store_true", help="skip the RKN4 line")
     ap.add_argument("--tile", type=int, default=None,
                     help="with --profile-only: use this stage-kernel tile variant instead of autotuning")
     ap.add_argument("--diag-tile", type=int, default=None,

@@ -130,7 +130,15 @@ typedef struct {
   int32_t integrator;   /* Tab. "integrator" type: 4 = classic RK4; 10 (or 3) =
                            low-storage SSPRK3, Shu-Osher form: stages at
                            c = (0, 1, 1/2), out = a_s y_n + b_s (Y_s + dt k_s),
-                           (a, b) = (0, 1), (3/4, 1/4), (1/3, 2/3) */
+                           (a, b) = (0, 1), (3/4, 1/4), (1/3, 2/3); 21 = RKN4,
+                           Nystrom's fourth-order method for x'' = a(t, x, x')
+                           with positions psi (u_ij), velocities Pi (v_ij):
+                           a1 at (x, v); a2 at (x + dt/2 v + dt^2/8 a1,
+                           v + dt/2 a1); a3 at (same x, v + dt/2 a2); a4 at
+                           (x + dt v + dt^2/2 a3, v + dt a3), stages at
+                           c = (0, 1/2, 1/2, 1); x' = x + dt v + dt^2/6 (a1 +
+                           a2 + a3), v' = v + dt/6 (a1 + 2 a2 + 2 a3 + a4).
+                           RKN4 takes no Kreiss-Oliger term (it needs x' = v) */
   int32_t pad_;
   double ko_eps;        /* Kreiss-Oliger dissipation (Sec. 2.4) added to the
                            evolution of psi1, psi2, Pi1, Pi2:
@@ -214,7 +222,7 @@ slh_status slh_set_eta(slh_ctx* ctx, double eta);
 /* Read eta of level lev (synchronises). */
 slh_status slh_get_eta(slh_ctx* ctx, int32_t lev, double* eta);
 
-/* One classic RK4 step (Tab. "integrator", type 4) of level lev by
+/* One step of the integrator p->integrator (classic RK4, SSPRK3 or RKN4) of level lev by
  * dt_lev = dt0 / 2^lev.  For lev > 0, sub in {0,1} is the sub-step within
  * the coarser level's step: the level starts at eta_coarse_start +
  * sub*dt_lev and each stage fills psi (and u_ij) ghosts from the coarser level at time

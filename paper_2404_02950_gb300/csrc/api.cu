@@ -827,11 +827,14 @@ static slh_status check_params(const slh_eom_params* p) {
   if (p->eta_power != 0 && p->eta_power != 2) return fail(SLH_ERR_INVALID_ARG, "eta_power must be 0 or 2");
   if (p->interp_type != 0 && p->interp_type != 2 && p->interp_type != 4)
     return fail(SLH_ERR_INVALID_ARG, "interp_type must be 0, 2 or 4");
-  if (p->integrator != 4 && p->integrator != 10 && p->integrator != 3)
-    return fail(SLH_ERR_INVALID_ARG, "integrator must be 4 (classic RK4) or 10 / 3 (SSPRK3), got %d", p->integrator);
+  if (p->integrator != 4 && p->integrator != 10 && p->integrator != 3 && p->integrator != 21)
+    return fail(SLH_ERR_INVALID_ARG, "integrator must be 4 (classic RK4), 10 / 3 (SSPRK3) or 21 (RKN4), got %d",
+                p->integrator);
   if (p->ko_order != 0 && p->ko_order != 1 && p->ko_order != 3 && p->ko_order != 5)
     return fail(SLH_ERR_INVALID_ARG, "ko_order must be 0 (off), 1, 3 or 5 (got %d)", p->ko_order);
   if (!(p->ko_eps >= 0.0) || p->ko_eps > 1e30) return fail(SLH_ERR_INVALID_ARG, "ko_eps must be finite and >= 0");
+  if (p->integrator == 21 && p->ko_order > 0 && p->ko_eps > 0.0)
+    return fail(SLH_ERR_INVALID_ARG, "RKN4 takes no Kreiss-Oliger term (it needs psi' = Pi)");
   return SLH_OK;
 }
 
@@ -853,13 +856,31 @@ static slh_status rk_step_impl(slh_ctx* c, int lev, int sub, double dt0, const s
   prof_end(c);
   if (st != SLH_OK) return st;
   const int ybuf = L.role_y, nbuf = L.role_prev;
-  const bool ssp = p.integrator != 4;
+  const bool rkn = p.integrator == 21;
+  const bool ssp = p.integrator != 4 && !rkn;
   // classic RK4: Y -> YA -> prev -> YA -> prev with the increment in D;
-  // SSPRK3: Y -> YA -> D -> prev (D holds the second stage value)
-  const int in_role[4] = {ybuf, SLH_BUF_YA, ssp ? SLH_BUF_D : nbuf, SLH_BUF_YA};
-  const int out_role[4] = {SLH_BUF_YA, ssp ? SLH_BUF_D : nbuf, ssp ? nbuf : SLH_BUF_YA, nbuf};
-  const double vals[4] = {ssp ? 8.0 : 12.0, ssp ? 12.0 : 20.0, ssp ? 12.0 : 20.0,
-                          c->prec == SLH_F32_KAHAN ? 24.0 : 16.0};
+  // SSPRK3: Y -> YA -> D -> prev (D holds the second stage value);
+  // RKN4: Y -> prev -> prev (velocities only, in place: stages 2 and 3 share
+  // their positions) -> YA -> prev, the position and velocity sums in D
+  int in_role[4] = {ybuf, SLH_BUF_YA, ssp ? SLH_BUF_D : nbuf, SLH_BUF_YA};
+  int out_role[4] = {SLH_BUF_YA, ssp ? SLH_BUF_D : nbuf, ssp ? nbuf : SLH_BUF_YA, nbuf};
+  double vals[4] = {ssp ? 8.0 : 12.0, ssp ? 12.0 : 20.0, ssp ? 12.0 : 20.0, c->prec == SLH_F32_KAHAN ? 24.0 : 16.0};
+  if (rkn) {
+    const int ir[4] = {ybuf, nbuf, nbuf, SLH_BUF_YA}, orr[4] = {nbuf, nbuf, SLH_BUF_YA, nbuf};
+    const double vr[4] = {12.0, 16.0, 20.0, c->prec == SLH_F32_KAHAN ? 24.0 : 16.0};
+    for (int k = 0; k < 4; ++k) {
+      in_role[k] = ir[k];
+      out_role[k] = orr[k];
+      vals[k] = vr[k];
+    }
+  }
+  // RKN4 stage coefficients: (Pi_n in the positions, a in the positions,
+  // a in the velocities, a into the position sum, a into the velocity sum)
+  const double h = dt;
+  const double rknc[4][5] = {{0.5 * h, h * h / 8.0, 0.5 * h, h * h / 6.0, h / 6.0},
+                             {0.0, 0.0, 0.5 * h, h * h / 6.0, h / 3.0},
+                             {h, h * h / 2.0, h, h * h / 6.0, h / 3.0},
+                             {h, 0.0, 0.0, 0.0, h / 6.0}};
   const double cSSP[3] = {0.0, 1.0, 0.5}, aSSP[3] = {0.0, 0.75, 1.0 / 3.0}, bSSP[3] = {1.0, 0.25, 2.0 / 3.0};
   const int nstage = ssp ? 3 : 4;
   for (int k = 0; k < nstage; ++k) {
@@ -881,6 +902,14 @@ static slh_status rk_step_impl(slh_ctx* c, int lev, int sub, double dt0, const s
     sl.ha = ssp ? dt : aRK[k] * dt;
     sl.hb = ssp ? 0.0 : bRK[k] * dt;
     sl.ssp = ssp ? 1 : 0;
+    sl.rkn = rkn ? 1 : 0;
+    if (rkn) {
+      sl.ha = rknc[k][0];
+      sl.hb = rknc[k][1];
+      sl.hc = rknc[k][2];
+      sl.hd = rknc[k][3];
+      sl.he = rknc[k][4];
+    }
     sl.sa = ssp ? aSSP[k] : 0.0;
     sl.sb = ssp ? bSSP[k] : 0.0;
     sl.lev = lev;
@@ -921,8 +950,12 @@ static slh_status rk_step_impl(slh_ctx* c, int lev, int sub, double dt0, const s
     if (c->ncomp == NCOMP_GW) {
       // the 12 tensor fields: reads psi (2) + u, v (12) of the stage input,
       // and as the scalar stage y_n, D, C of its 12 fields
-      const double gvals[4] = {ssp ? 26.0 : 38.0, ssp ? 38.0 : 62.0, ssp ? 38.0 : 62.0,
-                               c->prec == SLH_F32_KAHAN ? 74.0 : 50.0};
+      double gvals[4] = {ssp ? 26.0 : 38.0, ssp ? 38.0 : 62.0, ssp ? 38.0 : 62.0,
+                         c->prec == SLH_F32_KAHAN ? 74.0 : 50.0};
+      if (rkn) {   // RKN4: stage 2 writes the velocities only (no y_n positions read)
+        gvals[1] = 50.0;
+        gvals[3] = c->prec == SLH_F32_KAHAN ? 74.0 : 50.0;
+      }
       prof_begin(c, SLH_PROF_GW, V * gvals[k] * s);
       st = launch_gw_stage(c, L, p, sl);
       prof_end(c);

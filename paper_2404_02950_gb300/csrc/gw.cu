@@ -35,6 +35,8 @@ struct GwArgs {
   int stage;                // 1..4 (classic RK4) or 1..3 (SSPRK3)
   int ssp;                  // 1: low-storage SSPRK3 combine sa y_n + sb (Y + ha k)
   double sa, sb;
+  int rkn;                  // 1: RKN4 stage, coefficients ha, hb, hc, hd, he (as the scalar stage)
+  double hc, hd, he;
   const double* eta_start;  // device eta at the start of the step
   double c_stage;           // c_s * dt
   int friction;
@@ -166,6 +168,30 @@ __global__ void __launch_bounds__(COL_TX * COL_TY, sizeof(T) == 4 ? 4 : 3) gw_st
         } else {
           out[eu] = sa * yu + sb * fu;
           out[ev] = sa * yv + sb * fv;
+        }
+      } else if (A.rkn) {
+        // RKN4 with positions u, velocities v (see the scalar stage kernel)
+        const T hc = (T)A.hc, hd = (T)A.hd, he = (T)A.he;
+        if (stage == 1) {
+          out[eu] = u0 + ha * v + hb * kv;
+          out[ev] = v + hc * kv;
+          dd[eu] = hd * kv;
+          dd[ev] = he * kv;
+        } else if (stage <= 3) {
+          if (stage == 3) out[eu] = yu + ha * yv + hb * kv;
+          out[ev] = yv + hc * kv;
+          dd[eu] = du + hd * kv;
+          dd[ev] = dv + he * kv;
+        } else {
+          const T iu = ha * yv + du, iv = dv + he * kv;
+          if (cc != nullptr) {
+            T w, sm;
+            w = iu - cu; sm = yu + w; cc[eu] = (sm - yu) - w; out[eu] = sm;
+            w = iv - cv; sm = yv + w; cc[ev] = (sm - yv) - w; out[ev] = sm;
+          } else {
+            out[eu] = yu + iu;
+            out[ev] = yv + iv;
+          }
         }
       } else if (stage == 1) {
         out[eu] = u0 + ha * ku;
@@ -350,6 +376,30 @@ __global__ void __launch_bounds__(COL_TX * COL_TY, 2) gw_tma_kernel(const GwArgs
             out[eu] = sa * yu[k] + sb * fu;
             out[ev] = sa * yv[k] + sb * fv;
           }
+        } else if (A.rkn) {
+          // RKN4 with positions u, velocities v (see the scalar stage kernel)
+          const T hc = (T)A.hc, hd = (T)A.hd, he = (T)A.he;
+          if (stage == 1) {
+            out[eu] = u0 + ha * v[k] + hb * kv;
+            out[ev] = v[k] + hc * kv;
+            dd[eu] = hd * kv;
+            dd[ev] = he * kv;
+          } else if (stage <= 3) {
+            if (stage == 3) out[eu] = yu[k] + ha * yv[k] + hb * kv;
+            out[ev] = yv[k] + hc * kv;
+            dd[eu] = du[k] + hd * kv;
+            dd[ev] = dv[k] + he * kv;
+          } else {
+            const T iu = ha * yv[k] + du[k], iv = dv[k] + he * kv;
+            if (cc != nullptr) {
+              T w, sm;
+              w = iu - cu[k]; sm = yu[k] + w; cc[eu] = (sm - yu[k]) - w; out[eu] = sm;
+              w = iv - cv[k]; sm = yv[k] + w; cc[ev] = (sm - yv[k]) - w; out[ev] = sm;
+            } else {
+              out[eu] = yu[k] + iu;
+              out[ev] = yv[k] + iv;
+            }
+          }
         } else if (stage == 1) {
           out[eu] = u0 + ha * ku;
           out[ev] = v[k] + ha * kv;
@@ -431,6 +481,10 @@ static slh_status gw_stage_t(slh_ctx* c, Level& L, const slh_eom_params& p, cons
   A.ssp = s.ssp;
   A.sa = s.sa;
   A.sb = s.sb;
+  A.rkn = s.rkn;
+  A.hc = s.hc;
+  A.hd = s.hd;
+  A.he = s.he;
   A.tmaps = nullptr;
   A.in_buf = s.in_buf;
   A.err = c->d_err;

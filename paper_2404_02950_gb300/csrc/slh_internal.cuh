@@ -202,6 +202,9 @@ struct StageLaunch {
   double ha, hb;        // a_{s+1} dt, b_s dt (classic RK4); dt (SSPRK3)
   int ssp;              // 1: low-storage SSPRK3 stage, out = sa y_n + sb (Y + ha k)
   double sa, sb;
+  int rkn;              // 1: RKN4 stage; ha, hb, hc, hd, he its coefficients of Pi_n in the
+  double hc, hd, he;    // positions, a in the positions, a in the velocities, a into the
+                        // position sum, a into the velocity sum (a = this stage's Pi')
   uint8_t* tags;
   double* epart;        // per CTA x 4 (kin, grad, pot, pierced count)
   unsigned long long* tagcount;

@@ -46,6 +46,8 @@ struct StageArgs {
   int stage;                // 0 = diagnostics only, 1..4 (classic RK4) or 1..3 (SSPRK3)
   int ssp;                  // 1: low-storage SSPRK3 combine a y_n + b (Y + h k)
   double sa, sb;            // its a_s, b_s (h is ha)
+  int rkn;                  // 1: RKN4 stage (coefficients ha, hb, hc, hd, he; see StageLaunch)
+  double hc, hd, he;
   const double* eta_start;  // device eta at the start of the step (or current eta)
   double c_stage;           // c_s * dt
   double lambda, a;
@@ -428,6 +430,54 @@ __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stag
           yo[e0 + cs] = sa * PWv(1, 1) + sb * f1;
           yo[e0 + 2 * cs] = sa * PWv(2, 0) + sb * f2;
           yo[e0 + 3 * cs] = sa * PWv(2, 1) + sb * f3;
+        }
+      } else if (A.rkn) {
+        // RKN4 (positions psi, velocities Pi, a = kP this stage's Pi'):
+        //   stage 1 (input y_n): psi + ha Pi + hb a, Pi + hc a; D = (hd a, he a)
+        //   stage 2: Pi_n + hc a over the input's own velocities (its positions
+        //            are stage 3's); D += (hd a, he a)
+        //   stage 3: psi_n + ha Pi_n + hb a, Pi_n + hc a; D += (hd a, he a)
+        //   stage 4: psi_n + (ha Pi_n + D_psi), Pi_n + (D_Pi + he a)
+        T* yo = A.bufs[A.out_buf];
+        T* dd = A.bufs[A.d_buf];
+        const T hc = (T)A.hc, hd = (T)A.hd, he = (T)A.he;
+        if (stage == 1) {
+          yo[e0] = p1 + ha * P1 + hb * kP1;
+          yo[e0 + cs] = p2 + ha * P2 + hb * kP2;
+          yo[e0 + 2 * cs] = P1 + hc * kP1;
+          yo[e0 + 3 * cs] = P2 + hc * kP2;
+          dd[e0] = hd * kP1;
+          dd[e0 + cs] = hd * kP2;
+          dd[e0 + 2 * cs] = he * kP1;
+          dd[e0 + 3 * cs] = he * kP2;
+        } else if (stage <= 3) {
+          if (stage == 3) {
+            yo[e0] = PWv(1, 0) + ha * PWv(2, 0) + hb * kP1;
+            yo[e0 + cs] = PWv(1, 1) + ha * PWv(2, 1) + hb * kP2;
+          }
+          yo[e0 + 2 * cs] = PWv(2, 0) + hc * kP1;
+          yo[e0 + 3 * cs] = PWv(2, 1) + hc * kP2;
+          dd[e0] = PWv(3, 0) + hd * kP1;
+          dd[e0 + cs] = PWv(3, 1) + hd * kP2;
+          dd[e0 + 2 * cs] = PWv(4, 0) + he * kP1;
+          dd[e0 + 3 * cs] = PWv(4, 1) + he * kP2;
+        } else {
+          const T y0v = PWv(1, 0), y1v = PWv(1, 1), y2v = PWv(2, 0), y3v = PWv(2, 1);
+          const T inc0 = ha * y2v + PWv(3, 0), inc1 = ha * y3v + PWv(3, 1);
+          const T inc2 = PWv(4, 0) + he * kP1, inc3 = PWv(4, 1) + he * kP2;
+          if (has_c) {
+            T* cc_ = A.bufs[A.c_buf];
+            T v, sm;
+            v = inc0 - PWv(5, 0); sm = y0v + v; cc_[e0] = (sm - y0v) - v; yo[e0] = sm;
+            v = inc1 - PWv(5, 1); sm = y1v + v; cc_[e0 + cs] = (sm - y1v) - v; yo[e0 + cs] = sm;
+            v = inc2 - PWv(6, 0); sm = y2v + v; cc_[e0 + 2 * cs] = (sm - y2v) - v; yo[e0 + 2 * cs] = sm;
+            v = inc3 - PWv(6, 1); sm = y3v + v; cc_[e0 + 3 * cs] = (sm - y3v) - v; yo[e0 + 3 * cs] = sm;
+          } else {
+            yo[e0] = y0v + inc0;
+            yo[e0 + cs] = y1v + inc1;
+            yo[e0 + 2 * cs] = y2v + inc2;
+            yo[e0 + 3 * cs] = y3v + inc3;
+          }
         }
       } else if (stage == 1) {
         T* yo = A.bufs[A.out_buf];
@@ -814,6 +864,10 @@ static slh_status launch_v(slh_ctx* c, Level& L, const slh_eom_params& p, const 
   A.ssp = s.ssp;
   A.sa = s.sa;
   A.sb = s.sb;
+  A.rkn = s.rkn;
+  A.hc = s.hc;
+  A.hd = s.hd;
+  A.he = s.he;
   A.hb = s.hb;
   A.tags = s.tags;
   A.epart = s.epart;
