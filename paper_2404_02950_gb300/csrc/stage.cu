@@ -167,6 +167,63 @@ __device__ __forceinline__ void cursor_next(Cursor& c, const int4* items, const 
   cursor_load<G>(c, items, boxes, nitems, zlen);
 }
 
+// RKN4 stage combine (positions psi, velocities Pi, a = kP this stage's Pi'),
+// out of line so that the other integrators' stage code keeps its registers:
+//   stage 1 (input y_n): psi + ha Pi + hb a, Pi + hc a; D = (hd a, he a)
+//   stage 2: Pi_n + hc a over the input's own velocities (its positions are
+//            stage 3's); D += (hd a, he a)
+//   stage 3: psi_n + ha Pi_n + hb a, Pi_n + hc a; D += (hd a, he a)
+//   stage 4: psi_n + (ha Pi_n + D_psi), Pi_n + (D_Pi + he a), compensated
+//            when the level carries a Kahan buffer
+// pw: this cell's value in pointwise box 0 (box b, component c at
+// pw[(2 b + c) * txy]).
+template <typename T>
+__device__ __noinline__ void rkn_combine(const StageArgs<T>& A, int stage, bool has_c, long long e0, long long cs, T p1,
+                                         T p2, T P1, T P2, T kP1, T kP2, const T* pw, int txy) {
+  auto PWv = [&](int box, int comp) -> T { return pw[(box * 2 + comp) * txy]; };
+  T* yo = A.bufs[A.out_buf];
+  T* dd = A.bufs[A.d_buf];
+  const T ha = (T)A.ha, hb = (T)A.hb, hc = (T)A.hc, hd = (T)A.hd, he = (T)A.he;
+  if (stage == 1) {
+    yo[e0] = p1 + ha * P1 + hb * kP1;
+    yo[e0 + cs] = p2 + ha * P2 + hb * kP2;
+    yo[e0 + 2 * cs] = P1 + hc * kP1;
+    yo[e0 + 3 * cs] = P2 + hc * kP2;
+    dd[e0] = hd * kP1;
+    dd[e0 + cs] = hd * kP2;
+    dd[e0 + 2 * cs] = he * kP1;
+    dd[e0 + 3 * cs] = he * kP2;
+  } else if (stage <= 3) {
+    if (stage == 3) {
+      yo[e0] = PWv(1, 0) + ha * PWv(2, 0) + hb * kP1;
+      yo[e0 + cs] = PWv(1, 1) + ha * PWv(2, 1) + hb * kP2;
+    }
+    yo[e0 + 2 * cs] = PWv(2, 0) + hc * kP1;
+    yo[e0 + 3 * cs] = PWv(2, 1) + hc * kP2;
+    dd[e0] = PWv(3, 0) + hd * kP1;
+    dd[e0 + cs] = PWv(3, 1) + hd * kP2;
+    dd[e0 + 2 * cs] = PWv(4, 0) + he * kP1;
+    dd[e0 + 3 * cs] = PWv(4, 1) + he * kP2;
+  } else {
+    const T y0v = PWv(1, 0), y1v = PWv(1, 1), y2v = PWv(2, 0), y3v = PWv(2, 1);
+    const T inc0 = ha * y2v + PWv(3, 0), inc1 = ha * y3v + PWv(3, 1);
+    const T inc2 = PWv(4, 0) + he * kP1, inc3 = PWv(4, 1) + he * kP2;
+    if (has_c) {
+      T* cc_ = A.bufs[A.c_buf];
+      T v, sm;
+      v = inc0 - PWv(5, 0); sm = y0v + v; cc_[e0] = (sm - y0v) - v; yo[e0] = sm;
+      v = inc1 - PWv(5, 1); sm = y1v + v; cc_[e0 + cs] = (sm - y1v) - v; yo[e0 + cs] = sm;
+      v = inc2 - PWv(6, 0); sm = y2v + v; cc_[e0 + 2 * cs] = (sm - y2v) - v; yo[e0 + 2 * cs] = sm;
+      v = inc3 - PWv(6, 1); sm = y3v + v; cc_[e0 + 3 * cs] = (sm - y3v) - v; yo[e0 + 3 * cs] = sm;
+    } else {
+      yo[e0] = y0v + inc0;
+      yo[e0 + cs] = y1v + inc1;
+      yo[e0 + 2 * cs] = y2v + inc2;
+      yo[e0 + 3 * cs] = y3v + inc3;
+    }
+  }
+}
+
 template <typename T, int G, int TX, int TY, int P, bool DIAG>
 __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stage_kernel(const StageArgs<T> A) {
   using GE = Geo<T, G, TX, TY, P, DIAG>;
@@ -432,53 +489,7 @@ __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stag
           yo[e0 + 3 * cs] = sa * PWv(2, 1) + sb * f3;
         }
       } else if (A.rkn) {
-        // RKN4 (positions psi, velocities Pi, a = kP this stage's Pi'):
-        //   stage 1 (input y_n): psi + ha Pi + hb a, Pi + hc a; D = (hd a, he a)
-        //   stage 2: Pi_n + hc a over the input's own velocities (its positions
-        //            are stage 3's); D += (hd a, he a)
-        //   stage 3: psi_n + ha Pi_n + hb a, Pi_n + hc a; D += (hd a, he a)
-        //   stage 4: psi_n + (ha Pi_n + D_psi), Pi_n + (D_Pi + he a)
-        T* yo = A.bufs[A.out_buf];
-        T* dd = A.bufs[A.d_buf];
-        const T hc = (T)A.hc, hd = (T)A.hd, he = (T)A.he;
-        if (stage == 1) {
-          yo[e0] = p1 + ha * P1 + hb * kP1;
-          yo[e0 + cs] = p2 + ha * P2 + hb * kP2;
-          yo[e0 + 2 * cs] = P1 + hc * kP1;
-          yo[e0 + 3 * cs] = P2 + hc * kP2;
-          dd[e0] = hd * kP1;
-          dd[e0 + cs] = hd * kP2;
-          dd[e0 + 2 * cs] = he * kP1;
-          dd[e0 + 3 * cs] = he * kP2;
-        } else if (stage <= 3) {
-          if (stage == 3) {
-            yo[e0] = PWv(1, 0) + ha * PWv(2, 0) + hb * kP1;
-            yo[e0 + cs] = PWv(1, 1) + ha * PWv(2, 1) + hb * kP2;
-          }
-          yo[e0 + 2 * cs] = PWv(2, 0) + hc * kP1;
-          yo[e0 + 3 * cs] = PWv(2, 1) + hc * kP2;
-          dd[e0] = PWv(3, 0) + hd * kP1;
-          dd[e0 + cs] = PWv(3, 1) + hd * kP2;
-          dd[e0 + 2 * cs] = PWv(4, 0) + he * kP1;
-          dd[e0 + 3 * cs] = PWv(4, 1) + he * kP2;
-        } else {
-          const T y0v = PWv(1, 0), y1v = PWv(1, 1), y2v = PWv(2, 0), y3v = PWv(2, 1);
-          const T inc0 = ha * y2v + PWv(3, 0), inc1 = ha * y3v + PWv(3, 1);
-          const T inc2 = PWv(4, 0) + he * kP1, inc3 = PWv(4, 1) + he * kP2;
-          if (has_c) {
-            T* cc_ = A.bufs[A.c_buf];
-            T v, sm;
-            v = inc0 - PWv(5, 0); sm = y0v + v; cc_[e0] = (sm - y0v) - v; yo[e0] = sm;
-            v = inc1 - PWv(5, 1); sm = y1v + v; cc_[e0 + cs] = (sm - y1v) - v; yo[e0 + cs] = sm;
-            v = inc2 - PWv(6, 0); sm = y2v + v; cc_[e0 + 2 * cs] = (sm - y2v) - v; yo[e0 + 2 * cs] = sm;
-            v = inc3 - PWv(6, 1); sm = y3v + v; cc_[e0 + 3 * cs] = (sm - y3v) - v; yo[e0 + 3 * cs] = sm;
-          } else {
-            yo[e0] = y0v + inc0;
-            yo[e0 + cs] = y1v + inc1;
-            yo[e0 + 2 * cs] = y2v + inc2;
-            yo[e0 + 3 * cs] = y3v + inc3;
-          }
-        }
+        rkn_combine<T>(A, stage, has_c, e0, cs, p1, p2, P1, P2, kP1, kP2, pwp + ty * TX + tx, TXY);
       } else if (stage == 1) {
         T* yo = A.bufs[A.out_buf];
         T* dd = A.bufs[A.d_buf];
