@@ -49,15 +49,23 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def _stage_source_sha():
+    """Hash of the stage kernel's source (the kernel header and its host side)."""
+    csrc = os.path.join(ROOT, "paper_2404_02950_gb300", "csrc")
+    m = hashlib.sha256()
+    for name in ("stage_kernel.cuh", "stage.cu"):
+        m.update(open(os.path.join(csrc, name), "rb").read())
+    return m.hexdigest()[:16]
+
+
 def _stage_traffic():
     """DRAM bytes per stage-kernel launch from the committed ncu summary, if
     it was taken on the current kernel source (else None)."""
-    src = os.path.join(ROOT, "paper_2404_02950_gb300", "csrc", "stage.cu")
     f = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(f):
         return None
     d = json.load(open(f))
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = _stage_source_sha()
     e = d.get("stage_kernel_f32_g3")
     if e and e.get("source_sha") == h:
         return e.get("bytes_per_launch")

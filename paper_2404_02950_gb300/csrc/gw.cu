@@ -35,8 +35,6 @@ struct GwArgs {
   int stage;                // 1..4 (classic RK4) or 1..3 (SSPRK3)
   int ssp;                  // 1: low-storage SSPRK3 combine sa y_n + sb (Y + ha k)
   double sa, sb;
-  int rkn;                  // 1: RKN4 stage, coefficients ha, hb, hc, hd, he (as the scalar stage)
-  double hc, hd, he;
   const double* eta_start;  // device eta at the start of the step
   double c_stage;           // c_s * dt
   int friction;
@@ -45,6 +43,8 @@ struct GwArgs {
   const CUtensorMap* tmaps; // TMA form: [box][buffer] maps of the 16-field view
   int in_buf;               // TMA form: physical index of the stage input buffer
   int* err;
+  int rkn;                  // 1: RKN4 stage, coefficients ha, hb, hc, hd, he (as the scalar stage)
+  double hc, hd, he;
 };
 
 // (i, j) direction pairs of the six tensor components
