@@ -200,6 +200,8 @@ slh_status slh_init_level(slh_ctx* ctx, int32_t lev, const slh_box* boxes, int32
  * (interp_type 0/2/4) of level lev-1's current state, every field; the
  * Kahan compensation is carried over where covered and zero elsewhere.  The
  * new level's previous state equals its state and its eta that of lev-1.
+ * A level that existed keeps its tile variants (slh_set_tile,
+ * slh_set_diag_tile, the autotuners); a new one starts on variant 0.
  * nboxes == 0 removes level lev and every finer level.  Finer levels keep
  * their data but must be regridded (from the new lev) before the next
  * slh_rk_step / slh_advance (SLH_ERR_STATE otherwise).  Regrid coarse to

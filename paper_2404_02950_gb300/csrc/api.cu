@@ -717,6 +717,13 @@ slh_status slh_regrid_level(slh_ctx* c, int32_t lev, const slh_box* boxes, int32
   for (int i = 0; i < SLH_NBUF; ++i)
     if (fresh.buf[i]) SLH_CUDA(cudaMemsetAsync(fresh.buf[i], 0, bytes, c->stream));
   Level* old = lev < c->nlevels ? &c->lev[lev] : nullptr;
+  if (old) {
+    // a level that is regridded keeps the tiles its autotuners chose
+    if ((st = set_tile(c, fresh, old->tile.v, 1)) != SLH_OK || (st = set_tile(c, fresh, old->dtile.v, 2)) != SLH_OK) {
+      free_level(fresh);
+      return st;
+    }
+  }
   c->regrid_itype = interp_type;
   if ((st = launch_regrid_fill(c, lev, fresh, old)) != SLH_OK) {
     free_level(fresh);

@@ -61,7 +61,10 @@ def _compare(h, oh, tol):
                 assert e <= tol, (l, b, c, e)
 
 
-def test_regrid_then_subcycle_matches_oracle():
+@pytest.mark.parametrize("tile", [0, 2])
+def test_regrid_then_subcycle_matches_oracle(tile):
+    """tile: the stage tile of every level before the second regrid, which
+    the regridded levels keep."""
     p = slh.EOMParams(order=4, interp_type=4)
     y0 = inputs.string_loop(N0, 4.0, 2.0, DX0)
     oh = oamr.make_hierarchy(N0, DX0, DT0, G, BF, [[((0, 0, 0), (N0 - 1, N0 - 1, N0 - 1))]], oparams(p),
@@ -80,6 +83,8 @@ def test_regrid_then_subcycle_matches_oracle():
         oh.step()
         h.advance(DT0, p)
     _compare(h, oh, 1e-12)
+    for l in sorted(h.levels):
+        h.set_tile(l, tile)
     # second regrid: copies from the old levels where they overlap
     ob = _oracle_regrid(oh)
     gb = h.regrid(MAXLEV, NBUF, MAX_BOX)
