@@ -69,9 +69,15 @@ __device__ __forceinline__ double pw(int itype, int child, int off) {
 // the intermediate arrays stay small and no coarse cell's stencil is
 // evaluated for children outside the region); mixed regions decide cell by
 // cell in the last pass.
-constexpr int PATCH_MAX = 21 * 21 * 7;   // coarse cells under a 32 x 32 x g region (r <= 2, g <= 4)
-constexpr int PASS1_MAX = 4 * 21 * 21;   // after the pass along the thinnest axis (<= g = 4 fine cells)
-constexpr int PASS2_MAX = 4 * 32 * 21;   // after the second pass
+// Shared-memory buffers of a prolongation region of at most 32 x 32 x g fine
+// cells (g <= 4): the coarse patch (radius-2 footprint: 21 coarse cells along
+// a 32-cell axis, (g >> 1) + 5 along the thin one), the result of the pass
+// along the thinnest axis (g fine x 21 x 21 coarse) and of the second pass
+// (g x 32 x 21).  Sized by the level's g at launch, so that thin ghost
+// shells leave room for more CTAs per SM.
+__host__ __device__ constexpr int patch_max(int g) { return 21 * 21 * ((g >> 1) + 5); }
+__host__ __device__ constexpr int pass1_max(int g) { return g * 21 * 21; }
+__host__ __device__ constexpr int pass2_max(int g) { return g * 32 * 21; }
 
 template <typename T>
 struct GhostArgs {
@@ -260,12 +266,13 @@ __global__ void __launch_bounds__(256) ghost_copy_kernel(const GhostArgs<T> A) {
 }
 
 template <typename T, int RAD>
-__global__ void __launch_bounds__(256, 3) ghost_region_kernel(const GhostArgs<T> A) {
+__global__ void __launch_bounds__(256, 5) ghost_region_kernel(const GhostArgs<T> A) {
   // [2][pz][py][px]: time-interpolated psi1, psi2 in the field precision
   // (the stencil weights are dyadic rationals, exact in FP32 and FP64)
   extern __shared__ __align__(16) unsigned char patch_raw[];
   constexpr int NF = sizeof(T) == 4 ? 2 : 1;   // fields per pass (shared memory ~60 KB either way)
   T* patch = reinterpret_cast<T*>(patch_raw);
+  const int PATCH_MAX = patch_max(A.gl), PASS1_MAX = pass1_max(A.gl), PASS2_MAX = pass2_max(A.gl);
   T* buf1 = patch + NF * PATCH_MAX;
   T* buf2 = buf1 + NF * PASS1_MAX;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -416,12 +423,13 @@ static slh_status ghosts_t(slh_ctx* c, int lev, int role, double alpha, int ityp
   if (c->ncomp == NCOMP_GW)
     for (int q = 0; q < 3; ++q) A.pc[A.npairs++] = GW_U0 + 2 * q;
   A.err = c->d_err;
-  const int smem = (sizeof(T) == 4 ? 2 : 1) * (PATCH_MAX + PASS1_MAX + PASS2_MAX) * (int)sizeof(T);
+  const int smem = (sizeof(T) == 4 ? 2 : 1) * (patch_max(c->g) + pass1_max(c->g) + pass2_max(c->g)) * (int)sizeof(T);
+  const int smem_max = (sizeof(T) == 4 ? 2 : 1) * (patch_max(4) + pass1_max(4) + pass2_max(4)) * (int)sizeof(T);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(ghost_region_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(ghost_region_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(ghost_region_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(ghost_region_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+    cudaFuncSetAttribute(ghost_region_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+    cudaFuncSetAttribute(ghost_region_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
     attr = true;
   }
   // many more CTAs than resident slots: regions cost very different
