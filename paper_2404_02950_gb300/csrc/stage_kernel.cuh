@@ -15,8 +15,14 @@
 //     input, y_n, the increment accumulator, the Kahan compensation),
 // into shared-memory rings whose completion is tracked by mbarrier
 // transaction counts.  Consumers read the 2G+1 psi planes of the stencil from
-// the ring and write outputs with coalesced stores.  Every waiting loop is
-// bounded; on expiry the CTA latches DERR_TIMEOUT, drains its copies with a
+// the ring and write outputs with coalesced stores.  In the plain variant the
+// copies come from a producer warp of their own, and each consumer warp
+// releases a load step on a "consumed" mbarrier when it is done with it, so
+// the warps run without a CTA barrier per plane (the producer reuses the ring
+// slots of step u - P - 1 for step u once all warps have released it); the
+// diagnostics variant exchanges its winding data through shared memory, keeps
+// thread 0 as the producer and one CTA barrier per plane.  Every waiting loop
+// is bounded; on expiry the CTA latches DERR_TIMEOUT, drains its copies with a
 // bounded wait and leaves.
 //
 // The kernel and its launch templates are shared by the translation units
@@ -141,7 +147,10 @@ struct Geo {
   static constexpr int PW2 = 2 * TY * TX * (int)sizeof(T);
   static constexpr int NPW = DIAG ? 1 : (sizeof(T) == 4 ? NPW_MAX : NPW_MAX - 2);
   static constexpr int PW_STRIDE = (NPW * PW2 + 127) / 128 * 128;
-  static constexpr int BAR_BYTES = 128;
+  static constexpr bool WS = !DIAG;     // producer warp + per-step release barriers
+  static constexpr int NTHREADS = TX * TY + (WS ? 32 : 0);
+  static constexpr int BAR_BYTES = 128;  // RPSI "loaded" + (P + 1) "consumed" mbarriers
+  static_assert(RPSI + P + 1 <= BAR_BYTES / 8, "mbarrier area too small");
   static constexpr int SMEM = BAR_BYTES + RPSI * PSI_STRIDE + RPW * PW_STRIDE;
 };
 
@@ -171,11 +180,16 @@ __device__ __forceinline__ void cursor_next(Cursor& c, const int4* items, const 
 }
 
 template <typename T, int G, int TX, int TY, int P, bool DIAG, bool RKN>
-__global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stage_kernel(const StageArgs<T> A) {
+__global__ void __launch_bounds__(Geo<T, G, TX, TY, P, DIAG>::NTHREADS, (DIAG && TX * TY <= 256) ? 2 : 1)
+    stage_kernel(const StageArgs<T> A) {
   using GE = Geo<T, G, TX, TY, P, DIAG>;
   constexpr int SXL = GE::SXL, SY = GE::SY, RPSI = GE::RPSI, RPW = GE::RPW;
   constexpr int PLANE = SY * SXL;   // elements of one psi component plane
   constexpr int TXY = TX * TY;
+  // producer warp (plain variant): consumer warps release each load step on
+  // an mbarrier instead of meeting at a CTA barrier per plane
+  constexpr bool WS = GE::WS;
+  constexpr int RD = P + 1;         // "step consumed" barriers
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem);
   unsigned char* psi_base = smem + GE::BAR_BYTES;
@@ -197,9 +211,15 @@ __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stag
   const int npw = stage >= 2 ? (ssp ? 3 : ((stage == 4 && has_c) ? 7 : 5)) : 1;
   const unsigned step_bytes_pw = (unsigned)(npw * GE::PW2);
 
+  unsigned long long* done_bars = bars + RPSI;
+  __shared__ int s_abort, s_issued;
   if (tid == 0) {
     for (int i = 0; i < RPSI; ++i) mbar_init(smem_u32(&bars[i]), 1);
+    if (WS)
+      for (int i = 0; i < RD; ++i) mbar_init(smem_u32(&done_bars[i]), TXY / 32);
     fence_mbar_init();
+    s_abort = 0;
+    s_issued = 0;
   }
   __syncthreads();
 
@@ -239,7 +259,35 @@ __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stag
   // ring positions are tracked incrementally in 32-bit registers:
   // consumer step t -> (slot, pslot, parity), producer step t+P -> (islot, ipslot)
   int issued = 0, islot = 0, ipslot = 0;
-  if (tid == 0) {
+  if (WS && tid >= TXY) {
+    // producer: load step u may overwrite the ring slots of step u - P - 1
+    // once every consumer warp has released that step
+    if (tid == TXY) {
+      int dslot = 0;
+      unsigned dpar = 0;
+      while (pc.valid) {
+        if (issued >= RD) {
+          if (!mbar_wait(smem_u32(&done_bars[dslot]), dpar) || *(volatile int*)&s_abort) {
+            atomicExch(&s_abort, 1);
+            break;
+          }
+          if (++dslot == RD) {
+            dslot = 0;
+            dpar ^= 1u;
+          }
+        }
+        fence_proxy_async();
+        issue(pc, islot, ipslot);
+        ++issued;
+        if (++islot == RPSI) islot = 0;
+        if (++ipslot == RPW) ipslot = 0;
+        cursor_next<G>(pc, A.items, A.boxes, A.nitems, A.zlen);
+      }
+      s_issued = issued;
+    }
+    cc.valid = false;   // the producer warp consumes nothing
+  }
+  if (!WS && tid == 0) {
     for (int i = 0; i < P && pc.valid; ++i) {
       issue(pc, islot, ipslot);
       ++issued;
@@ -325,8 +373,9 @@ __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stag
 
   int t = 0, slot = 0, pslot = 0;
   unsigned parity = 0;
+  int dslot = 0;
   for (; cc.valid; ++t) {
-    if (tid == 0 && pc.valid) {
+    if (!WS && tid == 0 && pc.valid) {
       fence_proxy_async();
       issue(pc, islot, ipslot);
       ++issued;
@@ -334,7 +383,16 @@ __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stag
       if (++ipslot == RPW) ipslot = 0;
       cursor_next<G>(pc, A.items, A.boxes, A.nitems, A.zlen);
     }
-    const bool ok = mbar_wait(smem_u32(&bars[slot]), parity);
+    bool ok = mbar_wait(smem_u32(&bars[slot]), parity);
+    if (WS) {
+      // warp-uniform: a warp leaves together, before its release
+      ok = __all_sync(0xffffffffu, ok) && !*(volatile int*)&s_abort;
+      if (!ok) {
+        atomicExch(&s_abort, 1);
+        aborted = true;
+        break;
+      }
+    }
 
     const int z = cc.q - G;
     const bool compute = ok && z >= cc.z0;
@@ -646,7 +704,12 @@ __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stag
         tags(z);
       }
     }
-    if (__syncthreads_or(!ok)) {
+    if (WS) {
+      // this warp is done with the step's ring slots
+      __syncwarp();
+      if ((tid & 31) == 0) mbar_arrive(smem_u32(&done_bars[dslot]));
+      if (++dslot == RD) dslot = 0;
+    } else if (__syncthreads_or(!ok)) {
       aborted = true;
       break;
     }
@@ -658,6 +721,22 @@ __global__ void __launch_bounds__(TX* TY, (DIAG && TX * TY <= 256) ? 2 : 1) stag
     cursor_next<G>(cc, A.items, A.boxes, A.nitems, A.zlen);
   }
 
+  if (WS) {
+    // every copy the producer issued has been waited for by the consumers,
+    // unless a wait gave up: then latch the error and drain (bounded) the
+    // last phase issued on each ring slot
+    __syncthreads();
+    if (s_abort) {
+      if (tid == TXY) {
+        atomicCAS(A.err, 0, DERR_TIMEOUT);
+        const int n = s_issued;
+        for (int u = n > RPSI ? n - RPSI : 0; u < n; ++u)
+          mbar_wait(smem_u32(&bars[u % RPSI]), (unsigned)((u / RPSI) & 1));
+      }
+      __syncthreads();
+    }
+    return;
+  }
   if (aborted) {
     // latch the error and drain every copy still in flight (bounded)
     if (tid == 0) {
@@ -725,7 +804,7 @@ static slh_status launch_v(slh_ctx* c, Level& L, const slh_eom_params& p, const 
   if (occ < 0) {
     cudaFuncSetAttribute(stage_kernel<T, G, TX, TY, P, DIAG, RKN>, cudaFuncAttributeMaxDynamicSharedMemorySize, GE::SMEM);
     int o = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, stage_kernel<T, G, TX, TY, P, DIAG, RKN>, TX * TY, GE::SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, stage_kernel<T, G, TX, TY, P, DIAG, RKN>, GE::NTHREADS, GE::SMEM);
     occ = o > 0 ? o : 1;
   }
   CUtensorMap* maps = nullptr;
@@ -775,7 +854,7 @@ static slh_status launch_v(slh_ctx* c, Level& L, const slh_eom_params& p, const 
   if (s.epart != nullptr && grid > L.epart_cap) grid = L.epart_cap;
   if (ctas_used) *ctas_used = grid;
   if (tile.nitems == 0) return SLH_OK;
-  stage_kernel<T, G, TX, TY, P, DIAG, RKN><<<grid, TX * TY, GE::SMEM, c->stream>>>(A);
+  stage_kernel<T, G, TX, TY, P, DIAG, RKN><<<grid, GE::NTHREADS, GE::SMEM, c->stream>>>(A);
   SLH_CUDA(cudaGetLastError());
   return SLH_OK;
 }
