@@ -390,9 +390,10 @@ slh_status slh_set_tile(slh_ctx* ctx, int32_t lev, int32_t variant);
 slh_status slh_set_diag_tile(slh_ctx* ctx, int32_t lev, int32_t variant);
 
 /* Autotuner: time every tile variant on level lev's own boxes (reps
- * launches of an RK stage that reads the state, SLH_BUF_YA and SLH_BUF_D and
- * writes only the scratch buffers SLH_BUF_YA and SLH_BUF_D), keep the
- * fastest.  *chosen receives its
+ * launches of a middle RK stage in the form p->integrator runs it -- stage 2
+ * of classic RK4 or SSPRK3, stage 3 of RKN4 -- that reads the state,
+ * SLH_BUF_YA and SLH_BUF_D and writes only the scratch buffers SLH_BUF_YA and
+ * SLH_BUF_D), keep the fastest.  *chosen receives its
  * index, ms_out (may be NULL, one entry per variant) the mean milliseconds.
  * Call between steps, outside stream capture.  Synchronises.
  * Errors: INVALID_ARG, STATE, CUDA. */

@@ -1428,9 +1428,15 @@ static slh_status autotune_impl(slh_ctx* c, int32_t lev, const slh_eom_params* p
       sl.yn_buf = L.role_y;
       sl.epart = L.d_epart;
     } else {
-      sl.stage = 2;
+      // a middle stage in the form the integrator runs it (its pointwise
+      // operands differ: 5 boxes for classic RK4 and RKN4, 3 for SSPRK3)
+      sl.stage = p->integrator == 21 ? 3 : 2;
       sl.in_buf = SLH_BUF_YA;
       sl.yn_buf = L.role_y;
+      sl.ssp = (p->integrator != 4 && p->integrator != 21) ? 1 : 0;
+      sl.rkn = p->integrator == 21 ? 1 : 0;
+      sl.sa = sl.ssp ? 0.75 : 0.0;
+      sl.sb = sl.ssp ? 0.25 : 0.0;
     }
     sl.d_buf = SLH_BUF_D;
     sl.out_buf = SLH_BUF_YA;
