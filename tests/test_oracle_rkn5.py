@@ -1,0 +1,191 @@
+"""Pins of the oracle's fifth-order Runge-Kutta-Nystrom step (integrator
+type 22, oracle/rkn5.py) against polynomial solutions, an independent ODE
+integrator on a nonlinear time-dependent system, the closed form of a
+friction-free lattice mode, and the App. B energy slopes the paper prints
+for RKN5 and RKN4."""
+from math import gcd
+
+import numpy as np
+import pytest
+
+from oracle import energy, rkn4, rkn5
+from oracle.eom import EOMParams
+from oracle.stencil import laplacian_periodic
+from paper_2404_02950_gb300 import inputs
+
+FLAT = dict(friction=False)
+
+
+def _ode(acc):
+    """x'' = acc(t, x) in the f(y, t, dx, p) form the step takes: y = (x, v)."""
+    return lambda y, t, dx, p: (y[1], acc(t, y[0]))
+
+
+def _poly_step(c, t0, dt):
+    x = np.polynomial.Polynomial(c)
+    a = x.deriv(2)
+    out = rkn5.rkn5_step((np.array(x(t0)), np.array(x.deriv(1)(t0))), t0, dt, 1.0, EOMParams(**FLAT),
+                         f=_ode(lambda t, xx: a(t) + 0.0 * xx), pos=(0,), vel=(1,))
+    return out, x
+
+
+@pytest.mark.parametrize("deg", [0, 1, 2, 3, 4, 5])
+def test_polynomial_solutions_are_exact(deg):
+    """The position update integrates x'' = a(t) exactly when a is a cubic
+    (x of degree <= 5), the velocity update when a is a quartic."""
+    c = np.array([0.7, -1.3, 0.4, 2.1, -0.9, 0.6])[:deg + 1]
+    t0, dt = 0.3, 0.37
+    out, x = _poly_step(c, t0, dt)
+    assert abs(out[0] - x(t0 + dt)) <= 1e-13 * max(1.0, abs(x(t0 + dt)))
+    assert abs(out[1] - x.deriv(1)(t0 + dt)) <= 1e-13 * max(1.0, abs(x.deriv(1)(t0 + dt)))
+
+
+def test_degree_six_is_not_exact():
+    """... and no further: x = t^6 leaves an O(dt^6) position error (~64 per
+    halving of dt), while the velocity (a quartic acceleration) stays exact."""
+    errs = []
+    for dt in (0.2, 0.1, 0.05):
+        out, x = _poly_step([0, 0, 0, 0, 0, 0, 1.0], 1.0, dt)
+        errs.append(abs(out[0] - x(1.0 + dt)))
+        assert abs(out[1] - x.deriv(1)(1.0 + dt)) <= 1e-12
+    assert errs[0] > 1e-8
+    for e0, e1 in zip(errs, errs[1:]):
+        assert 50 < e0 / e1 < 80, errs
+
+
+def test_homogeneous_field_matches_independent_integrator():
+    """A spatially constant field without friction obeys psi'' = -(lambda
+    eta^2 (|psi|^2 - 1) + a) psi, nonlinear and explicitly time-dependent
+    through the stage times; RKN5 approaches a DOP853 solution at fifth
+    order (~32 per halving of dt)."""
+    from scipy.integrate import solve_ivp
+    p = EOMParams(lam=1.0, a=0.3, friction=False, eta_power=2, order=4)
+    psi0, pi0 = np.array([0.6, -0.5]), np.array([0.2, 0.1])
+    eta0, T = 0.5, 1.5
+
+    def f(eta, s):
+        ps, pi = s[:2], s[2:]
+        pot = p.lam * eta ** 2 * (ps @ ps - 1.0) + p.a
+        return np.concatenate([pi, -ps * pot])
+
+    ref = solve_ivp(f, (eta0, eta0 + T), np.concatenate([psi0, pi0]), method="DOP853",
+                    rtol=3e-14, atol=1e-15).y[:, -1]
+    errs = []
+    for nst in (12, 24, 48):
+        dt = T / nst
+        y = tuple(np.full((4, 4, 4), v) for v in np.concatenate([psi0, pi0]))
+        eta = eta0
+        for _ in range(nst):
+            y = rkn5.rkn5_step_periodic(y, eta, dt, 1.0, p)
+            eta += dt
+        errs.append(max(abs(y[c][0, 0, 0] - ref[c]) for c in range(4)))
+    assert errs[-1] > 1e-12
+    for e0, e1 in zip(errs, errs[1:]):
+        assert 24 < e0 / e1 < 40, errs
+
+
+def test_lattice_mode_converges_at_fifth_order():
+    """Massless and friction-free, a lattice Fourier mode obeys psi'' = -w^2
+    psi with w^2 the symbol of the discrete Laplacian: psi = A cos(w t) +
+    (B / w) sin(w t).  Position and velocity errors at t = 4 fall ~32 per
+    halving of dt."""
+    n, dx = 8, 0.5
+    ax = np.arange(n)
+    Z, Y, X = np.meshgrid(ax, ax, ax, indexing="ij")
+    mode = np.cos(2 * np.pi * (1 * X - 2 * Y + 1 * Z) / n)
+    p = EOMParams(lam=0.0, a=0.0, friction=False, eta_power=0, order=6)
+    w = np.sqrt(-laplacian_periodic(mode, dx, 6)[0, 0, 0] / mode[0, 0, 0])
+    A, Bv, T = 1.0, 0.7, 4.0
+    exact_x = A * np.cos(w * T) + Bv / w * np.sin(w * T)
+    exact_v = -A * w * np.sin(w * T) + Bv * np.cos(w * T)
+    z = np.zeros((n, n, n))
+    errs = []
+    for nst in (40, 80, 160):
+        dt = T / nst
+        y = (A * mode, z, Bv * mode, z)
+        for s in range(nst):
+            y = rkn5.rkn5_step_periodic(y, 1.0 + s * dt, dt, dx, p)
+        errs.append(max(np.max(np.abs(y[0] - exact_x * mode)), np.max(np.abs(y[2] - exact_v * mode))))
+        assert np.max(np.abs(y[1])) == 0.0 and np.max(np.abs(y[3])) == 0.0
+    for e0, e1 in zip(errs, errs[1:]):
+        assert 26 < e0 / e1 < 38, errs
+
+
+def test_rejects_friction_and_dissipation():
+    y = [np.zeros((4, 4, 4))] * 4
+    with pytest.raises(ValueError):
+        rkn5.rkn5_step_periodic(y, 1.0, 0.1, 1.0, EOMParams(friction=True))
+    with pytest.raises(ValueError):
+        rkn5.rkn5_step_periodic(y, 1.0, 0.1, 1.0, EOMParams(friction=False, ko_order=3, ko_eps=0.1))
+
+
+def _app_b_dE(step, Ns):
+    """App. B: the wave with 8, 5, 6 wavelengths along x, y, z of a box of
+    side 10 sqrt 5, 4th-order Laplacian, dt = 0.32 dx, 100 periods (t = 200);
+    energy error against pi^2 / 2, and the part of it the Laplacian alone
+    makes (the semi-discrete system conserves the lattice energy, so that
+    part is the initial state's lattice energy minus pi^2 / 2).  The wave sees
+    only its phase increment per cell along each axis, so the one-step map of
+    the N^3 run is built on the smallest periodic lattice with the same
+    increments (N / gcd(N, m_d) cells along axis d); the evolution is that
+    map's power."""
+    m = (8, 5, 6)
+    dE, dE_space = [], []
+    for n in Ns:
+        _, _, dx = inputs.plane_wave(4)
+        dx = dx * 4 / n
+        k = inputs.plane_wave_vector()
+        shp = tuple(n // gcd(n, md) for md in m)
+        Z, Y, X = np.meshgrid(*(np.arange(c) * dx for c in shp[::-1]), indexing="ij")
+        ph = k[0] * X + k[1] * Y + k[2] * Z
+        cs, sn = np.cos(ph), np.sin(ph)
+        nc, ns = np.sum(cs * cs), np.sum(sn * sn)
+        p = EOMParams(lam=0.0, a=0.0, friction=False, eta_power=0, order=4)
+        dt = 0.32 * dx
+        zero = np.zeros_like(cs)
+        Mx = np.zeros((4, 4))
+        for j, (u0, v0) in enumerate([(cs, zero), (sn, zero), (zero, cs), (zero, sn)]):
+            y = step((u0, zero, v0, zero), 1.0, dt, dx, p)
+            for r, f in enumerate((y[0], y[2])):
+                a, b = np.sum(f * cs) / nc, np.sum(f * sn) / ns
+                Mx[2 * r, j], Mx[2 * r + 1, j] = a, b
+                assert np.max(np.abs(f - a * cs - b * sn)) < 1e-12
+        s = np.linalg.matrix_power(Mx, int(round(200.0 / dt))) @ np.array([1.0, 0.0, 0.0, -np.pi])
+        uu, vv = s[0] * cs + s[1] * sn, s[2] * cs + s[3] * sn
+        vol = cs.size * dx ** 3
+        dE.append(energy.energy_periodic((uu, zero, vv, zero), 1.0, dx, p)[3] / vol - np.pi ** 2 / 2)
+        dE_space.append(energy.energy_periodic((cs, zero, -np.pi * sn, zero), 1.0, dx, p)[3] / vol - np.pi ** 2 / 2)
+    return np.array(dE), np.array(dE_space)
+
+
+def _check_time_part(Ns, dE, dE_space):
+    """The integrator's share of the error falls like dt^5 (a fourth- or
+    fifth-order one-step map of a linear oscillator loses energy at
+    O((w dt)^6) per step)."""
+    t = dE - dE_space
+    for n0, n1, t0, t1 in zip(Ns, Ns[1:], t, t[1:]):
+        assert abs(t0 / t1 / (n1 / n0) ** 5 - 1.0) < 0.03, (Ns, t)
+
+
+@pytest.mark.slow
+def test_plane_wave_energy_convergence_app_b_rkn5():
+    """RKN5: the fitted power law of |dE| against N is the paper's printed
+    index -4.0 (held back by the 4th-order Laplacian) within 0.3, where the
+    Laplacian's share dominates (the integrator's share has the other sign
+    and makes |dE| dip near N = 96)."""
+    Ns = [480, 640, 720, 960]
+    dE, dE_space = _app_b_dE(rkn5.rkn5_step_periodic, Ns)
+    slope = np.polyfit(np.log(Ns), np.log(np.abs(dE)), 1)[0]
+    assert abs(slope + 4.0) < 0.3, (slope, dE)
+    _check_time_part(Ns, dE, dE_space)
+
+
+def test_plane_wave_energy_convergence_app_b_rkn4():
+    """RKN4: |dE| falls at least like N^-4 (the paper prints -4.3 and asks
+    for roughly -p or better at order p)."""
+    Ns = [96, 128, 192, 256]
+    dE, dE_space = _app_b_dE(rkn4.rkn4_step_periodic, Ns)
+    assert np.all(dE < 0) and abs(dE[-1]) < 0.05 * np.pi ** 2 / 2
+    slope = np.polyfit(np.log(Ns), np.log(np.abs(dE)), 1)[0]
+    assert -6.0 < slope < -3.8, (slope, dE)
+    _check_time_part(Ns, dE, dE_space)
