@@ -31,7 +31,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import gw as ogw
-from . import ko, rkn4, ssprk3, tee
+from . import ko, rkn4, rkn5, ssprk3, tee
 from . import interp, winding
 from .eom import EOMParams, rhs
 from .energy import energy_box
@@ -195,10 +195,13 @@ class Hierarchy:
         self.levels = levels
         self.p = params
         self.interp_type = interp_type
-        if integrator not in (4, 10, 21):
-            raise ValueError("integrator must be 4 (classic RK4), 10 (low-storage SSPRK3) or 21 (RKN4)")
-        if integrator == 21 and params.ko_order:
-            raise ValueError("RKN4 needs x' = v: no Kreiss-Oliger term")
+        if integrator not in (4, 10, 21, 22):
+            raise ValueError("integrator must be 4 (classic RK4), 10 (low-storage SSPRK3), 21 (RKN4) or 22 (RKN5)")
+        if integrator in (21, 22) and params.ko_order:
+            raise ValueError("RKN needs x' = v: no Kreiss-Oliger term")
+        if integrator == 22 and (params.friction or gw):
+            raise ValueError("RKN5 needs an acceleration independent of the velocities: "
+                             "friction off, scalar fields only")
         self.integrator = integrator
         self.gw = gw
         # ghosts of psi (stencil), of Pi under dissipation, and of u_ij
@@ -293,6 +296,40 @@ class Hierarchy:
             for i, a in zip(vel, vn):
                 L.data[b][i][v[1:]] = a
 
+    def rkn5_level(self, lev, sub):
+        """One RKN5 step of level ``lev`` (oracle/rkn5.py): stage s at the
+        positions x + c_s h v + h^2 sum_j abar_sj k_j (velocities left at the
+        step's start: the acceleration does not read them), ghosts at time
+        fraction (sub + c_s)/2 of the coarser step."""
+        L = self.levels[lev]
+        C = self.coarse_of(lev)
+        g, dt, eta = L.g, L.dt, L.eta
+        pos, vel = rkn5.POS, rkn5.VEL
+        y0 = [a.copy() for a in L.data]
+        Y = [a.copy() for a in y0]
+        acc = []                              # per stage: per box, the accelerations
+        for s in range(4):
+            if s > 0:
+                for b in range(len(Y)):
+                    v = L.valid(b)
+                    for n, i in enumerate(pos):
+                        xs = y0[b][i][v[1:]] + (rkn5.C[s] * dt) * y0[b][vel[n]][v[1:]]
+                        for j in range(s):
+                            xs = xs + (dt * dt * rkn5.ABAR[s][j]) * acc[j][b][n]
+                        Y[b][i][v[1:]] = xs
+            fill_ghosts(L, Y, C, (sub + rkn5.C[s]) / 2.0, self.interp_type, comps=self.ghost_comps)
+            if s == 0 and self.record_tags:
+                self.tag_log.append((lev, eta, [winding.cell_tags_padded(a[0], a[1], g) for a in Y]))
+            acc.append([[k[i] for i in vel] for k in
+                        (self._rhs(Y[b], g, L.dx, eta + rkn5.C[s] * dt) for b in range(len(Y)))])
+        for b in range(len(Y)):
+            v = L.valid(b)
+            for n, i in enumerate(pos):
+                L.data[b][i][v[1:]] = (y0[b][i][v[1:]] + dt * y0[b][vel[n]][v[1:]]
+                                       + (dt * dt) * sum(rkn5.BBAR[q] * acc[q][b][n] for q in range(4)))
+            for n, i in enumerate(vel):
+                L.data[b][i][v[1:]] = y0[b][i][v[1:]] + dt * sum(rkn5.B[q] * acc[q][b][n] for q in range(4))
+
     def _rhs(self, arr, g, dx, eta):
         k = rhs_box(arr, g, dx, eta, self.p)
         if not self.gw:
@@ -336,6 +373,8 @@ class Hierarchy:
             self.rk4_level(lev, sub)
         elif self.integrator == 21:
             self.rkn4_level(lev, sub)
+        elif self.integrator == 22:
+            self.rkn5_level(lev, sub)
         else:
             self.ssprk3_level(lev, sub)
         L.eta = eta_start + L.dt

@@ -5,15 +5,17 @@ polynomial coarse field must equal its exact fine cell averages."""
 import numpy as np
 import pytest
 
-from oracle import amr, interp, rk4, rkn4, ssprk3
+from oracle import amr, interp, rk4, rkn4, rkn5, ssprk3
 from oracle.eom import EOMParams
 from paper_2404_02950_gb300 import inputs
 
 
-@pytest.mark.parametrize("order,integrator,ko_order", [(2, 4, 0), (4, 4, 0), (4, 10, 0), (4, 4, 5), (4, 21, 0)])
+@pytest.mark.parametrize("order,integrator,ko_order", [(2, 4, 0), (4, 4, 0), (4, 10, 0), (4, 4, 5), (4, 21, 0),
+                                                           (4, 22, 0)])
 def test_full_cover_fine_level_equals_uniform_fine_run(order, integrator, ko_order):
     n0, dx0, dt0, g, bf = 8, 0.25, 1.0 / 16, 3, 4
-    p = EOMParams(order=order, ko_order=ko_order, ko_eps=0.05 if ko_order else 0.0)
+    p = EOMParams(order=order, ko_order=ko_order, ko_eps=0.05 if ko_order else 0.0,
+                  friction=integrator != 22)    # RKN5: velocity-independent acceleration
     eta0 = 0.5                       # dyadic times keep eta sums exact
     fine0 = inputs.random_snapshot(16, seed=4, amp=0.8)
     coarse0 = [interp.restrict_block(f) for f in fine0]
@@ -30,7 +32,7 @@ def test_full_cover_fine_level_equals_uniform_fine_run(order, integrator, ko_ord
     if integrator == 4:
         ref, _ = rk4.evolve_periodic(fine0, eta0, dt0 / 2, dx0 / 2, 2 * nsteps, p)
     else:
-        step = rkn4.rkn4_step_periodic if integrator == 21 else ssprk3.ssprk3_step_periodic
+        step = {21: rkn4.rkn4_step_periodic, 22: rkn5.rkn5_step_periodic}.get(integrator, ssprk3.ssprk3_step_periodic)
         ref, eta = fine0, eta0
         for _ in range(2 * nsteps):
             ref = step(ref, eta, dt0 / 2, dx0 / 2, p)
