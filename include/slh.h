@@ -138,7 +138,15 @@ typedef struct {
                            (x + dt v + dt^2/2 a3, v + dt a3), stages at
                            c = (0, 1/2, 1/2, 1); x' = x + dt v + dt^2/6 (a1 +
                            a2 + a3), v' = v + dt/6 (a1 + 2 a2 + 2 a3 + a4).
-                           RKN4 takes no Kreiss-Oliger term (it needs x' = v) */
+                           RKN4 takes no Kreiss-Oliger term (it needs x' = v).
+                           22 = RKN5, Nystrom's fifth-order method for
+                           x'' = a(t, x) (friction must be 0; scalar fields
+                           only): stages at c = (0, 1/5, 2/3, 1), a_s at
+                           x + c_s dt v + dt^2 sum_j abar_sj a_j with abar rows
+                           (1/50), (-1/27, 7/27), (3/10, -2/35, 9/35);
+                           x' = x + dt v + dt^2 (14 a1 + 100 a2 + 54 a3)/336,
+                           v' = v + dt (14 a1 + 125 a2 + 162 a3 + 35 a4)/336;
+                           no Kreiss-Oliger term either */
   int32_t pad_;
   double ko_eps;        /* Kreiss-Oliger dissipation (Sec. 2.4) added to the
                            evolution of psi1, psi2, Pi1, Pi2:
@@ -224,11 +232,11 @@ slh_status slh_set_eta(slh_ctx* ctx, double eta);
 /* Read eta of level lev (synchronises). */
 slh_status slh_get_eta(slh_ctx* ctx, int32_t lev, double* eta);
 
-/* One step of the integrator p->integrator (classic RK4, SSPRK3 or RKN4) of level lev by
+/* One step of the integrator p->integrator (classic RK4, SSPRK3, RKN4 or RKN5) of level lev by
  * dt_lev = dt0 / 2^lev.  For lev > 0, sub in {0,1} is the sub-step within
  * the coarser level's step: the level starts at eta_coarse_start +
  * sub*dt_lev and each stage fills psi (and u_ij) ghosts from the coarser level at time
- * fraction (sub + c_s)/2, c = (0, 1/2, 1/2, 1) (Sec. 2.1).  Before each
+ * fraction (sub + c_s)/2, with the integrator's stage times c (Sec. 2.1).  Before each
  * stage the ghost fill of level lev runs; the four fused stage kernels then
  * compute the RHS of Sec. 3.1 with the stage-time coefficients (with 16
  * fields a second kernel per stage advances u_ij, v_ij the same way).  flags:
@@ -391,7 +399,7 @@ slh_status slh_set_diag_tile(slh_ctx* ctx, int32_t lev, int32_t variant);
 
 /* Autotuner: time every tile variant on level lev's own boxes (reps
  * launches of a middle RK stage in the form p->integrator runs it -- stage 2
- * of classic RK4 or SSPRK3, stage 3 of RKN4 -- that reads the state,
+ * of classic RK4 or SSPRK3, stage 3 of RKN4 or RKN5 -- that reads the state,
  * SLH_BUF_YA and SLH_BUF_D and writes only the scratch buffers SLH_BUF_YA and
  * SLH_BUF_D), keep the fastest.  *chosen receives its
  * index, ms_out (may be NULL, one entry per variant) the mean milliseconds.

@@ -74,7 +74,8 @@ class slh_eom_params(ctypes.Structure):
 class EOMParams:
     """Coefficients of Sec. 3.1: lambda, a, friction on/off, eta power of the
     potential coefficient, Laplacian accuracy order, ghost interpolation,
-    the integrator type (4 classic RK4, 10 low-storage SSPRK3, 21 RKN4) and the
+    the integrator type (4 classic RK4, 10 low-storage SSPRK3, 21 RKN4, 22 RKN5
+    with friction off) and the
     Kreiss-Oliger dissipation order (0 off, 1/3/5) and strength (Sec. 2.4)."""
     lam: float = 1.0
     a: float = 0.0

@@ -834,19 +834,23 @@ static slh_status check_params(const slh_eom_params* p) {
   if (p->eta_power != 0 && p->eta_power != 2) return fail(SLH_ERR_INVALID_ARG, "eta_power must be 0 or 2");
   if (p->interp_type != 0 && p->interp_type != 2 && p->interp_type != 4)
     return fail(SLH_ERR_INVALID_ARG, "interp_type must be 0, 2 or 4");
-  if (p->integrator != 4 && p->integrator != 10 && p->integrator != 3 && p->integrator != 21)
-    return fail(SLH_ERR_INVALID_ARG, "integrator must be 4 (classic RK4), 10 / 3 (SSPRK3) or 21 (RKN4), got %d",
-                p->integrator);
+  if (p->integrator != 4 && p->integrator != 10 && p->integrator != 3 && p->integrator != 21 && p->integrator != 22)
+    return fail(SLH_ERR_INVALID_ARG,
+                "integrator must be 4 (classic RK4), 10 / 3 (SSPRK3), 21 (RKN4) or 22 (RKN5), got %d", p->integrator);
   if (p->ko_order != 0 && p->ko_order != 1 && p->ko_order != 3 && p->ko_order != 5)
     return fail(SLH_ERR_INVALID_ARG, "ko_order must be 0 (off), 1, 3 or 5 (got %d)", p->ko_order);
   if (!(p->ko_eps >= 0.0) || p->ko_eps > 1e30) return fail(SLH_ERR_INVALID_ARG, "ko_eps must be finite and >= 0");
-  if (p->integrator == 21 && p->ko_order > 0 && p->ko_eps > 0.0)
-    return fail(SLH_ERR_INVALID_ARG, "RKN4 takes no Kreiss-Oliger term (it needs psi' = Pi)");
+  if ((p->integrator == 21 || p->integrator == 22) && p->ko_order > 0 && p->ko_eps > 0.0)
+    return fail(SLH_ERR_INVALID_ARG, "RKN%d takes no Kreiss-Oliger term (it needs psi' = Pi)", p->integrator - 17);
+  if (p->integrator == 22 && p->friction)
+    return fail(SLH_ERR_INVALID_ARG, "RKN5 needs an acceleration independent of Pi: friction must be off");
   return SLH_OK;
 }
 
 static slh_status rk_step_impl(slh_ctx* c, int lev, int sub, double dt0, const slh_eom_params& p, uint32_t flags) {
   Level& L = c->lev[lev];
+  if (p.integrator == 22 && c->ncomp == NCOMP_GW)
+    return fail(SLH_ERR_INVALID_ARG, "RKN5 is built for the scalar fields only (not the tensor fields)");
   if (c->g < p.lap_order / 2) return fail(SLH_ERR_INVALID_ARG, "nghost %d < Laplacian half width %d", c->g, p.lap_order / 2);
   if (p.ko_order > 0 && c->g < (p.ko_order + 1) / 2)
     return fail(SLH_ERR_INVALID_ARG, "nghost %d < dissipation half width %d", c->g, (p.ko_order + 1) / 2);
@@ -863,7 +867,8 @@ static slh_status rk_step_impl(slh_ctx* c, int lev, int sub, double dt0, const s
   prof_end(c);
   if (st != SLH_OK) return st;
   const int ybuf = L.role_y, nbuf = L.role_prev;
-  const bool rkn = p.integrator == 21;
+  const bool rkn5 = p.integrator == 22;
+  const bool rkn = p.integrator == 21 || rkn5;
   const bool ssp = p.integrator != 4 && !rkn;
   // classic RK4: Y -> YA -> prev -> YA -> prev with the increment in D;
   // SSPRK3: Y -> YA -> D -> prev (D holds the second stage value);
@@ -872,7 +877,18 @@ static slh_status rk_step_impl(slh_ctx* c, int lev, int sub, double dt0, const s
   int in_role[4] = {ybuf, SLH_BUF_YA, ssp ? SLH_BUF_D : nbuf, SLH_BUF_YA};
   int out_role[4] = {SLH_BUF_YA, ssp ? SLH_BUF_D : nbuf, ssp ? nbuf : SLH_BUF_YA, nbuf};
   double vals[4] = {ssp ? 8.0 : 12.0, ssp ? 12.0 : 20.0, ssp ? 12.0 : 20.0, c->prec == SLH_F32_KAHAN ? 24.0 : 16.0};
-  if (rkn) {
+  // RKN5: Y -> YA (stage-2 positions, k1) -> prev (stage-3 positions, A4;
+  // D = position and velocity sums) -> YA (stage-4 positions; D = position
+  // increment, velocity sum) -> prev
+  if (rkn5) {
+    const int ir[4] = {ybuf, SLH_BUF_YA, nbuf, SLH_BUF_YA}, orr[4] = {SLH_BUF_YA, nbuf, SLH_BUF_YA, nbuf};
+    const double vr[4] = {8.0, 16.0, 18.0, c->prec == SLH_F32_KAHAN ? 24.0 : 16.0};
+    for (int k = 0; k < 4; ++k) {
+      in_role[k] = ir[k];
+      out_role[k] = orr[k];
+      vals[k] = vr[k];
+    }
+  } else if (rkn) {
     const int ir[4] = {ybuf, nbuf, nbuf, SLH_BUF_YA}, orr[4] = {nbuf, nbuf, SLH_BUF_YA, nbuf};
     const double vr[4] = {12.0, 16.0, 20.0, c->prec == SLH_F32_KAHAN ? 24.0 : 16.0};
     for (int k = 0; k < 4; ++k) {
@@ -888,10 +904,20 @@ static slh_status rk_step_impl(slh_ctx* c, int lev, int sub, double dt0, const s
                              {0.0, 0.0, 0.5 * h, h * h / 6.0, h / 3.0},
                              {h, h * h / 2.0, h, h * h / 6.0, h / 3.0},
                              {h, 0.0, 0.0, 0.0, h / 6.0}};
+  // RKN5 (Nystrom's fifth-order tableau: c, abar, bbar, b):
+  // per stage the coefficients the stage kernel's combine takes
+  const double c5[4] = {0.0, 1.0 / 5.0, 2.0 / 3.0, 1.0};
+  const double h2 = h * h;
+  const double rq5[4][9] = {
+      {h / 5.0, h2 / 50.0},
+      {2.0 * h / 3.0, -h2 / 27.0, 7.0 * h2 / 27.0, 3.0 * h2 / 10.0, -2.0 * h2 / 35.0, 14.0 * h2 / 336.0,
+       100.0 * h2 / 336.0, 14.0 * h / 336.0, 125.0 * h / 336.0},
+      {h, 9.0 * h2 / 35.0, 54.0 * h2 / 336.0, 162.0 * h / 336.0},
+      {35.0 * h / 336.0}};
   const double cSSP[3] = {0.0, 1.0, 0.5}, aSSP[3] = {0.0, 0.75, 1.0 / 3.0}, bSSP[3] = {1.0, 0.25, 2.0 / 3.0};
   const int nstage = ssp ? 3 : 4;
   for (int k = 0; k < nstage; ++k) {
-    const double cs = ssp ? cSSP[k] : cRK[k];
+    const double cs = ssp ? cSSP[k] : (rkn5 ? c5[k] : cRK[k]);
     const double alpha = lev > 0 ? (sub + cs) / 2.0 : 1.0;
     prof_begin(c, SLH_PROF_GHOST, (double)L.nghost_cells * ghost_fields(c) * 2 * s);
     st = launch_ghosts(c, lev, in_role[k], alpha, p.interp_type, ko);
@@ -910,7 +936,11 @@ static slh_status rk_step_impl(slh_ctx* c, int lev, int sub, double dt0, const s
     sl.hb = ssp ? 0.0 : bRK[k] * dt;
     sl.ssp = ssp ? 1 : 0;
     sl.rkn = rkn ? 1 : 0;
-    if (rkn) {
+    if (rkn5) {
+      sl.ha = sl.hb = 0.0;
+      sl.rkn5 = 1;
+      for (int q = 0; q < 9; ++q) sl.rq[q] = rq5[k][q];
+    } else if (rkn) {
       sl.ha = rknc[k][0];
       sl.hb = rknc[k][1];
       sl.hc = rknc[k][2];
@@ -1429,12 +1459,14 @@ static slh_status autotune_impl(slh_ctx* c, int32_t lev, const slh_eom_params* p
       sl.epart = L.d_epart;
     } else {
       // a middle stage in the form the integrator runs it (its pointwise
-      // operands differ: 5 boxes for classic RK4 and RKN4, 3 for SSPRK3)
-      sl.stage = p->integrator == 21 ? 3 : 2;
+      // operands differ: 5 boxes for classic RK4, RKN4 and RKN5, 3 for SSPRK3)
+      const bool rk_n = p->integrator == 21 || p->integrator == 22;
+      sl.stage = rk_n ? 3 : 2;
       sl.in_buf = SLH_BUF_YA;
       sl.yn_buf = L.role_y;
-      sl.ssp = (p->integrator != 4 && p->integrator != 21) ? 1 : 0;
-      sl.rkn = p->integrator == 21 ? 1 : 0;
+      sl.ssp = (p->integrator != 4 && !rk_n) ? 1 : 0;
+      sl.rkn = rk_n ? 1 : 0;
+      sl.rkn5 = p->integrator == 22 ? 1 : 0;
       sl.sa = sl.ssp ? 0.75 : 0.0;
       sl.sb = sl.ssp ? 0.25 : 0.0;
     }

@@ -213,6 +213,8 @@ struct StageLaunch {
   int lev;
   bool cur_eta;         // evaluate at eta[lev] (diagnostics) instead of eta_start[lev] + c_stage
   bool dry;             // set up tensor maps and kernel attributes only, launch nothing
+  int rkn5;             // 1 (with rkn): RKN5 stage, rq its coefficients (see stage_kernel.cuh)
+  double rq[9];
 };
 slh_status launch_stage(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s,
                         int* ctas_used);

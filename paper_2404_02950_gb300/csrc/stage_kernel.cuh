@@ -69,6 +69,8 @@ struct StageArgs {
   int cov_shift, cov_nb;
   int* err;
   double hc, hd, he;        // RKN4 coefficients (with ha, hb; see StageLaunch)
+  int rkn5;                 // RKN5 stage (RKN instantiations only), coefficients rq
+  double rq[9];
 };
 
 
@@ -208,7 +210,10 @@ __global__ void __launch_bounds__(Geo<T, G, TX, TY, P, DIAG>::NTHREADS, (DIAG &&
   const bool has_c = A.c_buf >= 0;
   // pointwise boxes this stage needs: Pi always; y_n and D from stage 2; C in stage 4
   const bool ssp = A.ssp != 0;
-  const int npw = stage >= 2 ? (ssp ? 3 : ((stage == 4 && has_c) ? 7 : 5)) : 1;
+  // RKN5's stage 2 writes D without reading it
+  const bool rkn5 = RKN && A.rkn5 != 0;
+  const bool read_d = !ssp && !(rkn5 && stage == 2);
+  const int npw = stage >= 2 ? (!read_d ? 3 : ((stage == 4 && has_c) ? 7 : 5)) : 1;
   const unsigned step_bytes_pw = (unsigned)(npw * GE::PW2);
 
   unsigned long long* done_bars = bars + RPSI;
@@ -245,7 +250,7 @@ __global__ void __launch_bounds__(Geo<T, G, TX, TY, P, DIAG>::NTHREADS, (DIAG &&
         tma_load4(smem_u32(dst + 1 * GE::PW2), mb + 2 * A.yn_buf + 1, xp, yp, zp, 0, bar);
         tma_load4(smem_u32(dst + 2 * GE::PW2), mb + 2 * A.yn_buf + 1, xp, yp, zp, 2, bar);
       }
-      if (stage >= 2 && !ssp) {
+      if (stage >= 2 && read_d) {
         tma_load4(smem_u32(dst + 3 * GE::PW2), mb + 2 * A.d_buf + 1, xp, yp, zp, 0, bar);
         tma_load4(smem_u32(dst + 4 * GE::PW2), mb + 2 * A.d_buf + 1, xp, yp, zp, 2, bar);
         if (stage == 4 && has_c) {
@@ -499,10 +504,45 @@ __global__ void __launch_bounds__(Geo<T, G, TX, TY, P, DIAG>::NTHREADS, (DIAG &&
         //            positions are stage 3's); D += (hd a, he a)
         //   stage 3: psi_n + ha Pi_n + hb a, Pi_n + hc a; D += (hd a, he a)
         //   stage 4: psi_n + (ha Pi_n + D_psi), Pi_n + (D_Pi + he a)
+        // RKN5 (a independent of Pi; q = rq, k = a; the input's velocity
+        // slots carry k1 into stage 2, the partial sum A4 into stage 3):
+        //   stage 1 (input y_n): psi_n + q0 Pi_n + q1 k | k1
+        //   stage 2: psi_n + q0 Pi_n + (q1 k1 + q2 k) | A4 = q3 k1 + q4 k;
+        //            D = (q5 k1 + q6 k, q7 k1 + q8 k)
+        //   stage 3: positions psi_n + q0 Pi_n + (A4 + q1 k);
+        //            D = (q0 Pi_n + (D_psi + q2 k), D_Pi + q3 k)
+        //   stage 4: psi_n + D_psi, Pi_n + (D_Pi + q0 k)
         T* yo = A.bufs[A.out_buf];
         T* dd = A.bufs[A.d_buf];
         const T hc = (T)A.hc, hd = (T)A.hd, he = (T)A.he;
-        if (stage == 1) {
+        if (rkn5 && stage < 4) {
+          const T q0 = (T)A.rq[0], q1 = (T)A.rq[1];
+          if (stage == 1) {
+            yo[e0] = p1 + q0 * P1 + q1 * kP1;
+            yo[e0 + cs] = p2 + q0 * P2 + q1 * kP2;
+            yo[e0 + 2 * cs] = kP1;
+            yo[e0 + 3 * cs] = kP2;
+          } else if (stage == 2) {
+            const T q2 = (T)A.rq[2], q3 = (T)A.rq[3], q4 = (T)A.rq[4], q5 = (T)A.rq[5], q6 = (T)A.rq[6],
+                    q7 = (T)A.rq[7], q8 = (T)A.rq[8];
+            yo[e0] = PWv(1, 0) + q0 * PWv(2, 0) + (q1 * P1 + q2 * kP1);
+            yo[e0 + cs] = PWv(1, 1) + q0 * PWv(2, 1) + (q1 * P2 + q2 * kP2);
+            yo[e0 + 2 * cs] = q3 * P1 + q4 * kP1;
+            yo[e0 + 3 * cs] = q3 * P2 + q4 * kP2;
+            dd[e0] = q5 * P1 + q6 * kP1;
+            dd[e0 + cs] = q5 * P2 + q6 * kP2;
+            dd[e0 + 2 * cs] = q7 * P1 + q8 * kP1;
+            dd[e0 + 3 * cs] = q7 * P2 + q8 * kP2;
+          } else {
+            const T q2 = (T)A.rq[2], q3 = (T)A.rq[3];
+            yo[e0] = PWv(1, 0) + q0 * PWv(2, 0) + (P1 + q1 * kP1);
+            yo[e0 + cs] = PWv(1, 1) + q0 * PWv(2, 1) + (P2 + q1 * kP2);
+            dd[e0] = q0 * PWv(2, 0) + (PWv(3, 0) + q2 * kP1);
+            dd[e0 + cs] = q0 * PWv(2, 1) + (PWv(3, 1) + q2 * kP2);
+            dd[e0 + 2 * cs] = PWv(4, 0) + q3 * kP1;
+            dd[e0 + 3 * cs] = PWv(4, 1) + q3 * kP2;
+          }
+        } else if (stage == 1) {
           yo[e0] = p1 + ha * P1 + hb * kP1;
           yo[e0 + cs] = p2 + ha * P2 + hb * kP2;
           yo[e0 + 2 * cs] = P1 + hc * kP1;
@@ -524,8 +564,9 @@ __global__ void __launch_bounds__(Geo<T, G, TX, TY, P, DIAG>::NTHREADS, (DIAG &&
           dd[e0 + 3 * cs] = PWv(4, 1) + he * kP2;
         } else {
           const T y0v = PWv(1, 0), y1v = PWv(1, 1), y2v = PWv(2, 0), y3v = PWv(2, 1);
-          const T inc0 = ha * y2v + PWv(3, 0), inc1 = ha * y3v + PWv(3, 1);
-          const T inc2 = PWv(4, 0) + he * kP1, inc3 = PWv(4, 1) + he * kP2;
+          const T ka = rkn5 ? (T)A.rq[0] : he;
+          const T inc0 = rkn5 ? PWv(3, 0) : ha * y2v + PWv(3, 0), inc1 = rkn5 ? PWv(3, 1) : ha * y3v + PWv(3, 1);
+          const T inc2 = PWv(4, 0) + ka * kP1, inc3 = PWv(4, 1) + ka * kP2;
           if (has_c) {
             T* cc_ = A.bufs[A.c_buf];
             T v, sm;
@@ -840,6 +881,8 @@ static slh_status launch_v(slh_ctx* c, Level& L, const slh_eom_params& p, const 
   A.hc = s.hc;
   A.hd = s.hd;
   A.he = s.he;
+  A.rkn5 = s.rkn5;
+  for (int q = 0; q < 9; ++q) A.rq[q] = s.rq[q];
   A.hb = s.hb;
   A.tags = s.tags;
   A.epart = s.epart;
