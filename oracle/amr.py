@@ -11,9 +11,9 @@
   the spatial weights of ``interp`` applied to coarse values interpolated in
   time between the coarse states at the start and end of the coarse step
   (fraction alpha of that step).
-* One step of level l (classic RK4, SSPRK3 or RKN4) fills ghosts before every stage at the stage time:
-  the fine sub-step i in {0, 1} of the coarse step has stage fractions
-  alpha = (i + c_s) / 2, c = (0, 1/2, 1/2, 1).
+* One step of level l (classic RK4, SSPRK3, RKN4 or RKN5) fills ghosts before every stage at the
+  stage time: the fine sub-step i in {0, 1} of the coarse step has stage fractions
+  alpha = (i + c_s) / 2 with the integrator's stage times c (c = (0, 1/2, 1/2, 1) for RK4).
 * advance(l): keep the level's state as "old", take one step; if a finer
   level exists, advance it twice, then synchronise: every coarse cell covered
   by the finer level becomes the mean of its 8 children (all four fields).
@@ -24,7 +24,9 @@ Parity: the ingredients are pinned individually (stencil, rk4, interp,
 winding); the hierarchy itself has no closed form.  Pins here: a fine level
 covering the whole domain reproduces a uniform fine-lattice run bit for bit
 and restricts onto the coarse level exactly; a polynomial coarse field is
-prolonged exactly into fine ghosts -- tests/test_oracle_amr.py.
+prolonged exactly into fine ghosts; a three-level run is invariant bit for
+bit under lattice translations by whole blocks and under the rotation
+(psi1, psi2) -> (-psi2, psi1) in field space -- tests/test_oracle_amr.py.
 """
 from __future__ import annotations
 

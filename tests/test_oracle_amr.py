@@ -109,3 +109,63 @@ def test_nesting_violation_raises():
     h.levels[0].old = h.levels[0].data
     with pytest.raises(ValueError):
         amr.fill_ghosts(h.levels[1], arrs, h.levels[0], 0.0, 4)
+
+
+# Exact symmetries of the subcycled hierarchy (no closed form exists for it):
+# a lattice translation of boxes and data by whole blocks, and the rotation
+# (psi1, psi2) -> (-psi2, psi1) in field space, under which the equations of
+# Sec. 3.1 are invariant.  Both commute with every rounding the scheme does
+# (relabelled cells; exact negation, commutative sums), so the shifted or
+# rotated run equals the shifted or rotated original bit for bit.
+SYM_BOXES = [[((0, 0, 0), (15, 15, 15))],
+             [((8, 8, 4), (19, 23, 23)), ((20, 8, 4), (23, 15, 23))],
+             [((24, 24, 20), (31, 39, 27))]]
+SYM_CASES = [(4, 0, True), (10, 0, True), (21, 0, True), (22, 0, False), (4, 3, True)]
+
+
+def _sym_run(boxes, fields, integrator, ko_order, friction, nsteps=2):
+    p = EOMParams(order=4, ko_order=ko_order, ko_eps=0.05 if ko_order else 0.0, friction=friction)
+    h = amr.make_hierarchy(16, 0.5, 0.125, 3, 4, boxes, p, interp_type=4, eta0=0.75, integrator=integrator)
+    for L, f in zip(h.levels, fields):
+        L.set_dense(f)
+    for _ in range(nsteps):
+        h.step()
+    return h
+
+
+def _sym_fields(seed):
+    return [inputs.random_snapshot(16 * 2 ** l, seed=seed + l, amp=0.8) for l in range(3)]
+
+
+@pytest.mark.parametrize("integrator,ko_order,friction", SYM_CASES)
+def test_hierarchy_translation_invariance(integrator, ko_order, friction):
+    s0 = (4, 4, 0)                                    # (x, y, z) coarse cells: whole blocks on every level
+    fields = _sym_fields(21)
+    ref = _sym_run(SYM_BOXES, fields, integrator, ko_order, friction)
+    boxes, moved = [], []
+    for l, (bl, fl) in enumerate(zip(SYM_BOXES, fields)):
+        s = [c * 2 ** l for c in s0]
+        boxes.append(bl if l == 0 else [(tuple(a + d for a, d in zip(lo, s)), tuple(a + d for a, d in zip(hi, s)))
+                                        for lo, hi in bl])
+        moved.append([np.roll(a, shift=(s[2], s[1], s[0]), axis=(0, 1, 2)) for a in fl])
+    got = _sym_run(boxes, moved, integrator, ko_order, friction)
+    for l, (Lr, Lg) in enumerate(zip(ref.levels, got.levels)):
+        s = [c * 2 ** l for c in s0]
+        for b in range(len(Lr.boxes)):
+            vr, vg = Lr.data[b][Lr.valid(b)], Lg.data[b][Lg.valid(b)]
+            if l == 0:                                # the one periodic box: compare rolled
+                vr = np.stack([np.roll(a, shift=(s[2], s[1], s[0]), axis=(0, 1, 2)) for a in vr])
+            assert np.array_equal(vr, vg), (l, b)
+
+
+@pytest.mark.parametrize("integrator,ko_order,friction", SYM_CASES)
+def test_hierarchy_field_rotation_invariance(integrator, ko_order, friction):
+    fields = _sym_fields(33)
+    ref = _sym_run(SYM_BOXES, fields, integrator, ko_order, friction)
+    rot = [(-f[1], f[0], -f[3], f[2]) for f in fields]
+    got = _sym_run(SYM_BOXES, rot, integrator, ko_order, friction)
+    for l, (Lr, Lg) in enumerate(zip(ref.levels, got.levels)):
+        for b in range(len(Lr.boxes)):
+            vr, vg = Lr.data[b][Lr.valid(b)], Lg.data[b][Lg.valid(b)]
+            for a, e in ((vg[0], -vr[1]), (vg[1], vr[0]), (vg[2], -vr[3]), (vg[3], vr[2])):
+                assert np.array_equal(a, e), (l, b)
