@@ -1,8 +1,17 @@
-"""Shared helpers of the GPU parity tests (inputs, oracle runs, comparisons)."""
+"""Shared helpers of the tests (inputs, oracle runs, comparisons, paper fixtures)."""
+import json
+import os
+
 import numpy as np
 
 import paper_2404_02950_gb300 as slh
 from oracle.eom import EOMParams as OParams
+
+
+def golden(name):
+    """A fixture of values the paper prints (tests/golden/; each file names its source)."""
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        return json.load(f)
 
 
 def oparams(p: slh.EOMParams) -> OParams:

@@ -3,15 +3,13 @@ type 22, oracle/rkn5.py) against polynomial solutions, an independent ODE
 integrator on a nonlinear time-dependent system, the closed form of a
 friction-free lattice mode, and the App. B energy slopes the paper prints
 for RKN5 and RKN4."""
-from math import gcd
-
 import numpy as np
 import pytest
 
-from oracle import energy, rkn4, rkn5
+from oracle import rkn4, rkn5
 from oracle.eom import EOMParams
 from oracle.stencil import laplacian_periodic
-from paper_2404_02950_gb300 import inputs
+from tests import app_b
 
 FLAT = dict(friction=False)
 
@@ -119,45 +117,6 @@ def test_rejects_friction_and_dissipation():
         rkn5.rkn5_step_periodic(y, 1.0, 0.1, 1.0, EOMParams(friction=False, ko_order=3, ko_eps=0.1))
 
 
-def _app_b_dE(step, Ns):
-    """App. B: the wave with 8, 5, 6 wavelengths along x, y, z of a box of
-    side 10 sqrt 5, 4th-order Laplacian, dt = 0.32 dx, 100 periods (t = 200);
-    energy error against pi^2 / 2, and the part of it the Laplacian alone
-    makes (the semi-discrete system conserves the lattice energy, so that
-    part is the initial state's lattice energy minus pi^2 / 2).  The wave sees
-    only its phase increment per cell along each axis, so the one-step map of
-    the N^3 run is built on the smallest periodic lattice with the same
-    increments (N / gcd(N, m_d) cells along axis d); the evolution is that
-    map's power."""
-    m = (8, 5, 6)
-    dE, dE_space = [], []
-    for n in Ns:
-        _, _, dx = inputs.plane_wave(4)
-        dx = dx * 4 / n
-        k = inputs.plane_wave_vector()
-        shp = tuple(n // gcd(n, md) for md in m)
-        Z, Y, X = np.meshgrid(*(np.arange(c) * dx for c in shp[::-1]), indexing="ij")
-        ph = k[0] * X + k[1] * Y + k[2] * Z
-        cs, sn = np.cos(ph), np.sin(ph)
-        nc, ns = np.sum(cs * cs), np.sum(sn * sn)
-        p = EOMParams(lam=0.0, a=0.0, friction=False, eta_power=0, order=4)
-        dt = 0.32 * dx
-        zero = np.zeros_like(cs)
-        Mx = np.zeros((4, 4))
-        for j, (u0, v0) in enumerate([(cs, zero), (sn, zero), (zero, cs), (zero, sn)]):
-            y = step((u0, zero, v0, zero), 1.0, dt, dx, p)
-            for r, f in enumerate((y[0], y[2])):
-                a, b = np.sum(f * cs) / nc, np.sum(f * sn) / ns
-                Mx[2 * r, j], Mx[2 * r + 1, j] = a, b
-                assert np.max(np.abs(f - a * cs - b * sn)) < 1e-12
-        s = np.linalg.matrix_power(Mx, int(round(200.0 / dt))) @ np.array([1.0, 0.0, 0.0, -np.pi])
-        uu, vv = s[0] * cs + s[1] * sn, s[2] * cs + s[3] * sn
-        vol = cs.size * dx ** 3
-        dE.append(energy.energy_periodic((uu, zero, vv, zero), 1.0, dx, p)[3] / vol - np.pi ** 2 / 2)
-        dE_space.append(energy.energy_periodic((cs, zero, -np.pi * sn, zero), 1.0, dx, p)[3] / vol - np.pi ** 2 / 2)
-    return np.array(dE), np.array(dE_space)
-
-
 def _check_time_part(Ns, dE, dE_space):
     """The integrator's share of the error falls like dt^5 (a fourth- or
     fifth-order one-step map of a linear oscillator loses energy at
@@ -169,23 +128,23 @@ def _check_time_part(Ns, dE, dE_space):
 
 @pytest.mark.slow
 def test_plane_wave_energy_convergence_app_b_rkn5():
-    """RKN5: the fitted power law of |dE| against N is the paper's printed
-    index -4.0 (held back by the 4th-order Laplacian) within 0.3, where the
-    Laplacian's share dominates (the integrator's share has the other sign
-    and makes |dE| dip near N = 96)."""
+    """RKN5 on App. B (tests/app_b.py): the fitted power law of |dE|
+    against N is the paper's printed index (held back by the 4th-order
+    Laplacian) within 0.3, where the Laplacian's share dominates (the
+    integrator's share has the other sign and makes |dE| dip near N = 96)."""
     Ns = [480, 640, 720, 960]
-    dE, dE_space = _app_b_dE(rkn5.rkn5_step_periodic, Ns)
-    slope = np.polyfit(np.log(Ns), np.log(np.abs(dE)), 1)[0]
-    assert abs(slope + 4.0) < 0.3, (slope, dE)
+    dE, dE_space = app_b.energy_errors(rkn5.rkn5_step_periodic, Ns)
+    sl = app_b.slope(Ns, dE)
+    assert abs(sl - app_b.APP_B["slopes"]["RKN5"]) < 0.3, (sl, dE)
     _check_time_part(Ns, dE, dE_space)
 
 
 def test_plane_wave_energy_convergence_app_b_rkn4():
-    """RKN4: |dE| falls at least like N^-4 (the paper prints -4.3 and asks
-    for roughly -p or better at order p)."""
+    """RKN4 on App. B: |dE| falls at least like N^-4 (the paper prints -4.3
+    and asks for roughly -p or better at order p)."""
     Ns = [96, 128, 192, 256]
-    dE, dE_space = _app_b_dE(rkn4.rkn4_step_periodic, Ns)
-    assert np.all(dE < 0) and abs(dE[-1]) < 0.05 * np.pi ** 2 / 2
-    slope = np.polyfit(np.log(Ns), np.log(np.abs(dE)), 1)[0]
-    assert -6.0 < slope < -3.8, (slope, dE)
+    dE, dE_space = app_b.energy_errors(rkn4.rkn4_step_periodic, Ns)
+    assert np.all(dE < 0) and abs(dE[-1]) < 0.05 * app_b.APP_B["E_exact"]
+    sl = app_b.slope(Ns, dE)
+    assert -6.0 < sl < -4.0 + 0.2, (sl, app_b.APP_B["slopes"]["RKN4"], dE)
     _check_time_part(Ns, dE, dE_space)
