@@ -12,6 +12,19 @@ prints no weights.  Readings used here, per axis, tensor product over x, y, z:
 * type 2: the fine value is the degree-2 polynomial through the three coarse
   cell-centre values I-1..I+1, evaluated at the fine cell centre (+-1/4).
 * type 0: the parent value.
+* type 1 (linear conservative): the parent value plus, per axis, a quarter of
+  a limited slope signed by the child's side, f = c + (s_x sx + s_y sy +
+  s_z sz) / 4 with s = +-1.  The slope along an axis is the monotonized
+  central one (van Leer) from the one-sided differences dm = c - c(-1),
+  dp = c(+1) - c: zero where dm dp <= 0 (an extremum), else
+  sign(dp) min(2|dm|, 2|dp|, |dm + dp| / 2).  Per-axis limiting alone lets a
+  corner child leave the range of its neighbours (three axis terms add up),
+  so the three slopes are then scaled by one factor alpha = min(1,
+  (M - c) / E, (c - m) / E), E = (|sx| + |sy| + |sz|) / 4 the largest excursion
+  of a child, M and m the largest and smallest of the parent and its six face
+  neighbours.  Conservative (the 8 children average to the parent), exact
+  for linear fields (alpha = 1 there), and no child leaves [m, M].  This is
+  not a fixed-weight stencil, so it has its own evaluation below.
 
 The 1D weights are derived below from those definitions with exact rational
 arithmetic (no table is typed in).  Coarse cell I spans [I-1/2, I+1/2] in
@@ -26,8 +39,9 @@ fine level becomes the mean of its 8 children, summed in the order
 x fastest, then y, then z, and multiplied by 1/8.
 
 Parity: pinned (exact fine averages of polynomials of per-axis degree <= 4,
-restriction(prolongation) = identity, constants and linear functions) --
-tests/test_oracle_interp.py.
+restriction(prolongation) = identity, constants and linear functions; for
+type 1 also the limiter's cases worked by hand, bounds on random data and a
+monotone step) -- tests/test_oracle_interp.py.
 """
 from __future__ import annotations
 
@@ -82,7 +96,41 @@ def weights_1d(interp_type: int):
             At = [[A[r][c] for r in range(3)] for c in range(3)]
             out[child] = (offs, tuple(_solve(At, m)))
         return out
-    raise ValueError("interpolation type must be 0, 2 or 4")
+    raise ValueError("interpolation type must be 0, 2 or 4 (type 1 has no fixed weights)")
+
+
+def mc_slope(dm, dp):
+    """Monotonized-central slope from the one-sided differences dm = c - c(-1)
+    and dp = c(+1) - c (type 1)."""
+    dm, dp = np.asarray(dm, dtype=np.float64), np.asarray(dp, dtype=np.float64)
+    mag = np.minimum(np.minimum(2.0 * np.abs(dm), 2.0 * np.abs(dp)), 0.5 * np.abs(dm + dp))
+    return np.where(dm * dp > 0.0, np.where(dp > 0.0, mag, -mag), 0.0)
+
+
+def _prolong_linear_limited(coarse_at, fine_idx):
+    """Type 1 at fine cells: parent value and its six face neighbours
+    gathered in one call, the three limited slopes and their common scale,
+    then the children's sum ((c + s_x sx / 4) + s_y sy / 4) + s_z sz / 4."""
+    fz, fy, fx = (np.asarray(a, dtype=np.int64).ravel() for a in fine_idx)
+    shape = np.shape(fine_idx[0])
+    P = (fz // 2, fy // 2, fx // 2)
+    sgn = [2.0 * (f - 2 * q) - 1.0 for f, q in zip((fz, fy, fx), P)]    # -1 lower child, +1 upper
+    # offsets (z, y, x): centre, then -x, +x, -y, +y, -z, +z
+    oz = np.array([0, 0, 0, 0, 0, -1, 1])
+    oy = np.array([0, 0, 0, -1, 1, 0, 0])
+    ox = np.array([0, -1, 1, 0, 0, 0, 0])
+    V = coarse_at(P[0][:, None] + oz[None, :], P[1][:, None] + oy[None, :], P[2][:, None] + ox[None, :])
+    c = V[..., 0]
+    sx = mc_slope(c - V[..., 1], V[..., 2] - c)
+    sy = mc_slope(c - V[..., 3], V[..., 4] - c)
+    sz = mc_slope(c - V[..., 5], V[..., 6] - c)
+    e = 0.25 * ((np.abs(sx) + np.abs(sy)) + np.abs(sz))
+    hi, lo = np.max(V, axis=-1), np.min(V, axis=-1)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        alpha = np.where(e > 0.0, np.minimum(1.0, np.minimum((hi - c) / e, (c - lo) / e)), 1.0)
+    sx, sy, sz = alpha * sx, alpha * sy, alpha * sz
+    out = ((c + 0.25 * (sgn[2] * sx)) + 0.25 * (sgn[1] * sy)) + 0.25 * (sgn[0] * sz)
+    return out.reshape(V.shape[:-2] + shape)
 
 
 def prolong_points(coarse_at, fine_idx, interp_type: int):
@@ -94,6 +142,8 @@ def prolong_points(coarse_at, fine_idx, interp_type: int):
     All stencil values are gathered in one call; the weighted sum then runs
     over offsets z (outer), y, x (inner) in increasing order.
     """
+    if interp_type == 1:
+        return _prolong_linear_limited(coarse_at, fine_idx)
     fz, fy, fx = (np.asarray(a, dtype=np.int64).ravel() for a in fine_idx)
     shape = np.shape(fine_idx[0])
     W = weights_1d(interp_type)

@@ -120,12 +120,13 @@ def test_nesting_violation_raises():
 SYM_BOXES = [[((0, 0, 0), (15, 15, 15))],
              [((8, 8, 4), (19, 23, 23)), ((20, 8, 4), (23, 15, 23))],
              [((24, 24, 20), (31, 39, 27))]]
-SYM_CASES = [(4, 0, True), (10, 0, True), (21, 0, True), (22, 0, False), (4, 3, True)]
+SYM_CASES = [(4, 0, True, 4), (10, 0, True, 4), (21, 0, True, 4), (22, 0, False, 4), (4, 3, True, 4),
+             (4, 0, True, 1)]
 
 
-def _sym_run(boxes, fields, integrator, ko_order, friction, nsteps=2):
+def _sym_run(boxes, fields, integrator, ko_order, friction, itype, nsteps=2):
     p = EOMParams(order=4, ko_order=ko_order, ko_eps=0.05 if ko_order else 0.0, friction=friction)
-    h = amr.make_hierarchy(16, 0.5, 0.125, 3, 4, boxes, p, interp_type=4, eta0=0.75, integrator=integrator)
+    h = amr.make_hierarchy(16, 0.5, 0.125, 3, 4, boxes, p, interp_type=itype, eta0=0.75, integrator=integrator)
     for L, f in zip(h.levels, fields):
         L.set_dense(f)
     for _ in range(nsteps):
@@ -137,18 +138,18 @@ def _sym_fields(seed):
     return [inputs.random_snapshot(16 * 2 ** l, seed=seed + l, amp=0.8) for l in range(3)]
 
 
-@pytest.mark.parametrize("integrator,ko_order,friction", SYM_CASES)
-def test_hierarchy_translation_invariance(integrator, ko_order, friction):
+@pytest.mark.parametrize("integrator,ko_order,friction,itype", SYM_CASES)
+def test_hierarchy_translation_invariance(integrator, ko_order, friction, itype):
     s0 = (4, 4, 0)                                    # (x, y, z) coarse cells: whole blocks on every level
     fields = _sym_fields(21)
-    ref = _sym_run(SYM_BOXES, fields, integrator, ko_order, friction)
+    ref = _sym_run(SYM_BOXES, fields, integrator, ko_order, friction, itype)
     boxes, moved = [], []
     for l, (bl, fl) in enumerate(zip(SYM_BOXES, fields)):
         s = [c * 2 ** l for c in s0]
         boxes.append(bl if l == 0 else [(tuple(a + d for a, d in zip(lo, s)), tuple(a + d for a, d in zip(hi, s)))
                                         for lo, hi in bl])
         moved.append([np.roll(a, shift=(s[2], s[1], s[0]), axis=(0, 1, 2)) for a in fl])
-    got = _sym_run(boxes, moved, integrator, ko_order, friction)
+    got = _sym_run(boxes, moved, integrator, ko_order, friction, itype)
     for l, (Lr, Lg) in enumerate(zip(ref.levels, got.levels)):
         s = [c * 2 ** l for c in s0]
         for b in range(len(Lr.boxes)):
@@ -158,12 +159,12 @@ def test_hierarchy_translation_invariance(integrator, ko_order, friction):
             assert np.array_equal(vr, vg), (l, b)
 
 
-@pytest.mark.parametrize("integrator,ko_order,friction", SYM_CASES)
-def test_hierarchy_field_rotation_invariance(integrator, ko_order, friction):
+@pytest.mark.parametrize("integrator,ko_order,friction,itype", SYM_CASES)
+def test_hierarchy_field_rotation_invariance(integrator, ko_order, friction, itype):
     fields = _sym_fields(33)
-    ref = _sym_run(SYM_BOXES, fields, integrator, ko_order, friction)
+    ref = _sym_run(SYM_BOXES, fields, integrator, ko_order, friction, itype)
     rot = [(-f[1], f[0], -f[3], f[2]) for f in fields]
-    got = _sym_run(SYM_BOXES, rot, integrator, ko_order, friction)
+    got = _sym_run(SYM_BOXES, rot, integrator, ko_order, friction, itype)
     for l, (Lr, Lg) in enumerate(zip(ref.levels, got.levels)):
         for b in range(len(Lr.boxes)):
             vr, vg = Lr.data[b][Lr.valid(b)], Lg.data[b][Lg.valid(b)]

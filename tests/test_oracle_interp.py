@@ -1,5 +1,6 @@
 """Pins of the oracle's prolongation and restriction (Sec. 2.1, Tab. "amr"
-interpolation types 2 and 4) against exact polynomial cell averages."""
+interpolation types 0, 1, 2 and 4) against exact polynomial cell averages,
+and of the limited type 1 against its worked cases, bounds and monotonicity."""
 from fractions import Fraction as Fr
 
 import numpy as np
@@ -92,7 +93,7 @@ def _avg_f(coef, lo, hi):
     return sum(c * (hi ** (p + 1) - lo ** (p + 1)) / ((p + 1) * (hi - lo)) for p, c in enumerate(coef))
 
 
-@pytest.mark.parametrize("itype", [0, 2, 4])
+@pytest.mark.parametrize("itype", [0, 1, 2, 4])
 def test_restrict_of_prolong_is_identity_and_constants_exact(itype):
     nc = 6
     C = np.random.default_rng(itype).standard_normal((nc, nc, nc))
@@ -124,3 +125,98 @@ def test_time_lerp_endpoints_exact():
     a, b = np.array([0.1, -3.7]), np.array([2.9, 1e-9])
     assert np.array_equal(interp.time_lerp(a, b, 0.0), a)
     assert np.array_equal(interp.time_lerp(a, b, 1.0), b)
+
+
+# -- type 1: linear conservative (limited slopes) ----------------------------
+
+@pytest.mark.parametrize("dm,dp,s", [(1.0, 3.0, 2.0), (1.0, 0.2, 0.4), (3.0, 1.0, 2.0), (2.0, 2.0, 2.0),
+                                     (-1.0, -3.0, -2.0), (1e-3, 1.0, 2e-3), (1.0, -1.0, 0.0), (0.0, 5.0, 0.0),
+                                     (-2.0, 0.5, 0.0)])
+def test_mc_slope_worked_cases(dm, dp, s):
+    """min(2|dm|, 2|dp|, |dm + dp| / 2) with the sign of the differences,
+    zero at an extremum or a flat side."""
+    assert interp.mc_slope(dm, dp) == pytest.approx(s, rel=1e-15, abs=0.0)
+
+
+def _neighbours_range(C, nc):
+    stack = [C] + [np.roll(C, sh, axis=ax) for ax in range(3) for sh in (1, -1)]
+    return np.max(stack, axis=0), np.min(stack, axis=0)
+
+
+def test_linear_conservative_bounds_and_conservation_on_random_data():
+    """Every child within [m, M] of its parent and the parent's face
+    neighbours, and the 8 children average to the parent."""
+    nc = 8
+    C = np.random.default_rng(4).standard_normal((nc, nc, nc))
+
+    def coarse_at(Kz, Ky, Kx):
+        return C[Kz % nc, Ky % nc, Kx % nc]
+
+    fz, fy, fx = np.meshgrid(*(np.arange(2 * nc),) * 3, indexing="ij")
+    Fv = interp.prolong_points(coarse_at, (fz, fy, fx), 1)
+    M, m = _neighbours_range(C, nc)
+    up = lambda a: np.repeat(np.repeat(np.repeat(a, 2, 0), 2, 1), 2, 2)
+    Mf, mf = up(M), up(m)
+    assert np.all(Fv <= Mf + 1e-15) and np.all(Fv >= mf - 1e-15)
+    assert np.max(np.abs(interp.restrict_block(Fv) - C)) < 1e-14
+    # on this data the per-axis slopes alone overshoot, so the joint scale is exercised
+    sgn = lambda f: 2.0 * (f % 2) - 1.0
+    c = up(C)
+    slope = lambda ax: up(interp.mc_slope(C - np.roll(C, 1, axis=ax), np.roll(C, -1, axis=ax) - C))
+    raw = c + 0.25 * (sgn(fx) * slope(2) + sgn(fy) * slope(1) + sgn(fz) * slope(0))
+    assert np.max(np.maximum(raw - Mf, mf - raw)) > 0.05
+
+
+def test_linear_conservative_exact_for_linear_fields():
+    """Coarse cell averages of a linear function (its values at cell
+    centres) give children equal to the fine cell averages."""
+    a = np.array([0.7, -1.3, 0.4])                         # (x, y, z)
+
+    def coarse_at(Kz, Ky, Kx):
+        return a[0] * Kx + a[1] * Ky + a[2] * Kz + 2.5      # no wrap: a linear field
+
+    fz, fy, fx = np.meshgrid(*(np.arange(4, 12),) * 3, indexing="ij")
+    Fv = interp.prolong_points(coarse_at, (fz, fy, fx), 1)
+    # fine cell f spans [f/2 - 1/2, f/2] in coarse units, centre f/2 - 1/4
+    exp = a[0] * (fx / 2 - 0.25) + a[1] * (fy / 2 - 0.25) + a[2] * (fz / 2 - 0.25) + 2.5
+    assert np.max(np.abs(Fv - exp)) < 1e-13
+
+
+def test_linear_conservative_joint_scale_worked_case():
+    """Parent 0 with neighbours -1 / +3 along every axis: each slope is 2,
+    the corner excursion E = 1.5 would reach -1.5 < m = -1, so alpha = 2/3:
+    the lowest child is exactly m and the highest +1."""
+    vals = {(0, 0, 0): 0.0}
+    for d in range(3):
+        e = [0, 0, 0]
+        e[d] = -1
+        vals[tuple(e)] = -1.0
+        e[d] = 1
+        vals[tuple(e)] = 3.0
+
+    def coarse_at(Kz, Ky, Kx):
+        out = np.empty(Kz.shape)
+        for idx in np.ndindex(Kz.shape):
+            out[idx] = vals[(int(Kz[idx]), int(Ky[idx]), int(Kx[idx]))]
+        return out
+
+    fz, fy, fx = np.meshgrid(*(np.arange(2),) * 3, indexing="ij")
+    Fv = interp.prolong_points(coarse_at, (fz, fy, fx), 1)
+    assert Fv[0, 0, 0] == pytest.approx(-1.0, abs=1e-15)
+    assert Fv[1, 1, 1] == pytest.approx(1.0, abs=1e-15)
+    assert np.mean(Fv) == pytest.approx(0.0, abs=1e-15)
+
+
+def test_linear_conservative_step_is_monotone():
+    """A coarse step along x: the children keep the step's values (slopes
+    vanish at the cells on either side of the jump), no over- or undershoot."""
+    nc = 8
+    C = np.zeros((nc, nc, nc))
+    C[:, :, nc // 2:] = 1.0
+
+    def coarse_at(Kz, Ky, Kx):
+        return C[Kz % nc, Ky % nc, Kx % nc]
+
+    fz, fy, fx = np.meshgrid(*(np.arange(2 * nc),) * 3, indexing="ij")
+    Fv = interp.prolong_points(coarse_at, (fz, fy, fx), 1)
+    assert np.array_equal(Fv, np.repeat(np.repeat(np.repeat(C, 2, 0), 2, 1), 2, 2))
