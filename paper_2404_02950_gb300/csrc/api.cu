@@ -10,9 +10,25 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "slh_internal.cuh"
 
 namespace slh {
+
+// NVTX range over a host-side phase (a level step, a ghost fill, a regrid):
+// a profiler that records NVTX can select one by name; without one the push
+// and pop are no-ops
+struct NvtxRange {
+  NvtxRange(const char* fmt, int a, int b = 0) {
+    char buf[64];
+    snprintf(buf, sizeof buf, fmt, a, b);
+    nvtxRangePushA(buf);
+  }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 static thread_local std::string g_last_error;
 
@@ -690,6 +706,7 @@ slh_status slh_regrid_level(slh_ctx* c, int32_t lev, const slh_box* boxes, int32
   if (!c) return fail(SLH_ERR_INVALID_ARG, "regrid_level: null ctx");
   if (lev < 1 || lev >= c->max_levels) return fail(SLH_ERR_OUT_OF_RANGE, "regrid_level: level %d outside [1,%d)", lev, c->max_levels);
   if (lev > c->nlevels) return fail(SLH_ERR_STATE, "regrid_level: level %d below it is not defined", lev - 1);
+  NvtxRange range("slh regrid level %d (%d boxes)", lev, nboxes);
   if (lev - 1 >= c->stale_from) return fail(SLH_ERR_STATE, "regrid_level: regrid level %d first", c->stale_from);
   if (interp_type != 0 && interp_type != 2 && interp_type != 4)
     return fail(SLH_ERR_INVALID_ARG, "regrid_level: interp_type must be 0, 2 or 4");
@@ -848,6 +865,7 @@ static slh_status check_params(const slh_eom_params* p) {
 }
 
 static slh_status rk_step_impl(slh_ctx* c, int lev, int sub, double dt0, const slh_eom_params& p, uint32_t flags) {
+  NvtxRange range("slh level %d step (sub %d)", lev, sub);
   Level& L = c->lev[lev];
   if (p.integrator == 22 && c->ncomp == NCOMP_GW)
     return fail(SLH_ERR_INVALID_ARG, "RKN5 is built for the scalar fields only (not the tensor fields)");
@@ -1016,6 +1034,7 @@ slh_status slh_rk_step(slh_ctx* c, int32_t lev, int32_t sub, double dt0, const s
 }
 
 static slh_status fill_impl(slh_ctx* c, int lev, double alpha, int itype, int mode) {
+  NvtxRange range(mode == SLH_RESTRICT ? "slh level %d restrict + ghost fill" : "slh level %d ghost fill", lev);
   Level& L = c->lev[lev];
   const size_t s = elem_size(c);
   if (mode == SLH_RESTRICT) {
@@ -1069,6 +1088,7 @@ slh_status slh_advance(slh_ctx* c, double dt0, const slh_eom_params* p, uint32_t
   if (c->nlevels < 1) return fail(SLH_ERR_STATE, "advance: no level defined");
   if (c->stale_from < c->nlevels) return fail(SLH_ERR_STATE, "advance: level %d must be regridded first", c->stale_from);
   if (!(dt0 > 0.0)) return fail(SLH_ERR_INVALID_ARG, "advance: dt0 must be positive");
+  NvtxRange range("slh coarse step (%d levels)", c->nlevels);
   if (!(flags & SLH_USE_GRAPH) || c->prof) return advance_rec(c, 0, 0, dt0, *p, flags);
 
   // graph replay: the graph depends on the rotation parity of level 0 only
@@ -1427,6 +1447,7 @@ static slh_status autotune_impl(slh_ctx* c, int32_t lev, const slh_eom_params* p
                                 double* ms_out, bool diag) {
   const char* what = diag ? "autotune_diag" : "autotune";
   if (!c) return fail(SLH_ERR_INVALID_ARG, "%s: null ctx", what);
+  NvtxRange range(diag ? "slh autotune (diagnostics) level %d" : "slh autotune level %d", lev);
   slh_status st = check_params(p);
   if (st != SLH_OK) return st;
   if (lev < 0 || lev >= c->nlevels) return fail(SLH_ERR_STATE, "%s: level %d not defined", what, lev);
