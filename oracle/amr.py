@@ -24,9 +24,11 @@ Parity: the ingredients are pinned individually (stencil, rk4, interp,
 winding); the hierarchy itself has no closed form.  Pins here: a fine level
 covering the whole domain reproduces a uniform fine-lattice run bit for bit
 and restricts onto the coarse level exactly; a polynomial coarse field is
-prolonged exactly into fine ghosts; a three-level run is invariant bit for
-bit under lattice translations by whole blocks and under the rotation
-(psi1, psi2) -> (-psi2, psi1) in field space -- tests/test_oracle_amr.py.
+prolonged exactly into fine ghosts; a field constant in space and linear in
+time stays exact through the subcycled steps (the stage-time fractions); a
+three-level run is invariant bit for bit under lattice translations by whole
+blocks and under the rotation (psi1, psi2) -> (-psi2, psi1) in field space --
+tests/test_oracle_amr.py.
 """
 from __future__ import annotations
 

@@ -170,3 +170,30 @@ def test_hierarchy_field_rotation_invariance(integrator, ko_order, friction, ity
             vr, vg = Lr.data[b][Lr.valid(b)], Lg.data[b][Lg.valid(b)]
             for a, e in ((vg[0], -vr[1]), (vg[1], vr[0]), (vg[2], -vr[3]), (vg[3], vr[2])):
                 assert np.array_equal(a, e), (l, b)
+
+
+@pytest.mark.parametrize("integrator", [4, 10, 21, 22])
+def test_linear_in_time_field_pins_the_stage_time_fractions(integrator):
+    """With lambda = a = 0 and no friction, psi = psi0 + v t (constant in
+    space) solves the equations, and prolongation of constants and linear
+    time interpolation are exact: every level of a three-level hierarchy
+    stays at psi0 + v t through the subcycled steps.  A fine ghost taken at
+    the wrong fraction of the coarse step differs from the interior by v
+    times the time error, which the Laplacian turns into a visible error."""
+    p = EOMParams(lam=0.0, a=0.0, friction=False, eta_power=0, order=4)
+    h = amr.make_hierarchy(16, 0.5, 0.125, 3, 4, SYM_BOXES, p, interp_type=4, eta0=0.75, integrator=integrator)
+    psi0, v = (0.3, -0.2), (1.25, 0.5)
+    for L in h.levels:
+        n = L.n
+        L.set_dense([np.full((n, n, n), psi0[0]), np.full((n, n, n), psi0[1]),
+                     np.full((n, n, n), v[0]), np.full((n, n, n), v[1])])
+    t = 0.0
+    for _ in range(2):
+        h.step()
+        t += 0.125
+    for L in h.levels:
+        for b in range(len(L.boxes)):
+            got = L.data[b][L.valid(b)]
+            for c in range(2):
+                assert np.max(np.abs(got[c] - (psi0[c] + v[c] * t))) < 1e-14, (L, b, c)
+                assert np.max(np.abs(got[2 + c] - v[c])) < 1e-14
