@@ -197,3 +197,46 @@ def test_linear_in_time_field_pins_the_stage_time_fractions(integrator):
             for c in range(2):
                 assert np.max(np.abs(got[c] - (psi0[c] + v[c] * t))) < 1e-14, (L, b, c)
                 assert np.max(np.abs(got[2 + c] - v[c])) < 1e-14
+
+
+def _set_level_fields(h, fn):
+    """Fields from fn(x, y, z) at the cell centres of each level, in level-0
+    lattice units (a level-l cell i sits at (i + 1/2) / 2^l - 1/2)."""
+    for lev, L in enumerate(h.levels):
+        r = float(1 << lev)
+        ax = (np.arange(L.n, dtype=np.float64) + 0.5) / r - 0.5
+        z, y, x = np.meshgrid(ax, ax, ax, indexing="ij")
+        L.set_dense(fn(x, y, z))
+
+
+def test_hierarchy_energy_of_a_constant_field_is_density_times_volume():
+    """Every cell of the domain counted once, whatever the box layout: the
+    energy of a constant state is the closed-form density times the domain
+    volume (the gradient part vanishes)."""
+    p = EOMParams(lam=1.0, a=0.3, friction=True, eta_power=2, order=4)
+    h = amr.make_hierarchy(16, 0.5, 0.125, 3, 4, SYM_BOXES, p, interp_type=4, eta0=0.75)
+    psi, pi = (0.6, -0.3), (0.2, 0.1)
+    _set_level_fields(h, lambda x, y, z: [np.full(x.shape, v) for v in psi + pi])
+    K, G, P, T, S = h.energy()
+    r2 = psi[0] ** 2 + psi[1] ** 2
+    vol = (16 * 0.5) ** 3
+    kin = 0.5 * (pi[0] ** 2 + pi[1] ** 2) * vol
+    pot = ((p.lam * 0.75 ** 2 / 4.0) * (r2 - 1.0) ** 2 + 0.5 * p.a * r2) * vol
+    assert abs(K - kin) < 1e-12 * kin and abs(P - pot) < 1e-12 * pot
+    assert abs(G) < 1e-12 and S == 0.0 and abs(T - (kin + pot)) < 1e-12 * (kin + pot)
+
+
+def test_hierarchy_string_length_of_straight_strings_is_exact():
+    """psi = sin(2 pi (x - x0) / 16) + i sin(2 pi (y - y0) / 16) has four
+    straight strings along z, one pierced plaquette per layer of whichever
+    level owns the region: one string runs through levels 1 and 2, three
+    through the coarse level only.  The string length is 4 x 16 dx_0 exactly
+    (a layer of level l counts dx_l, and level l has 2^l layers per coarse
+    one)."""
+    p = EOMParams(order=4)
+    h = amr.make_hierarchy(16, 0.5, 0.125, 3, 4, SYM_BOXES, p, interp_type=4, eta0=0.75)
+    x0, y0 = 7.1, 7.3
+    _set_level_fields(h, lambda x, y, z: [np.sin(2 * np.pi * (x - x0) / 16), np.sin(2 * np.pi * (y - y0) / 16),
+                                          np.zeros(x.shape), np.zeros(x.shape)])
+    S = h.energy()[4]
+    assert S == 4 * 16 * 0.5, S
