@@ -240,3 +240,54 @@ def test_hierarchy_string_length_of_straight_strings_is_exact():
                                           np.zeros(x.shape), np.zeros(x.shape)])
     S = h.energy()[4]
     assert S == 4 * 16 * 0.5, S
+
+
+def _level_cells(L):
+    """{(x, y, z): values of the four fields} over the valid cells of a level."""
+    out = {}
+    for b, (lo, hi) in enumerate(L.boxes):
+        v = L.data[b][L.valid(b)]
+        for k in range(hi[2] - lo[2] + 1):
+            for j in range(hi[1] - lo[1] + 1):
+                for i in range(hi[0] - lo[0] + 1):
+                    out[(lo[0] + i, lo[1] + j, lo[2] + k)] = tuple(v[:, k, j, i])
+    return out
+
+
+def test_regrid_level_copies_old_cells_and_prolongs_new_ones():
+    """Sec. 2.3's rebuild of a level: the same cells chopped into other boxes
+    keep their values bit for bit; a superset keeps the old cells bit for
+    bit and takes, in the new cells, the prolongation of the coarse level,
+    here the exact fine averages of the coarse level's quartic polynomial
+    (type 4 is exact for those); no boxes remove the level and every finer one."""
+    p = EOMParams(order=4)
+    boxes0 = [((0, 0, 0), (15, 15, 15))]
+    old1 = [((8, 8, 8), (15, 15, 15)), ((16, 8, 8), (23, 15, 15))]
+    h = amr.make_hierarchy(16, 0.5, 0.125, 3, 4, [boxes0, old1, [((20, 20, 20), (27, 27, 27))]], p, interp_type=4)
+    coef = [0.3, -0.2, 0.05, 0.01, -0.002]                  # quartic in x, constant in y and z
+
+    def avg(lo, hi):                                         # exact average over [lo, hi] (level-0 units)
+        return sum(c * (hi ** (q + 1) - lo ** (q + 1)) / ((q + 1) * (hi - lo)) for q, c in enumerate(coef))
+
+    xs = np.arange(16.0)
+    row = np.array([avg(x - 0.5, x + 0.5) for x in xs])
+    h.levels[0].set_dense([np.broadcast_to(row, (16, 16, 16)).copy()] * 4)
+    rng = np.random.default_rng(9)
+    h.levels[1].set_dense([rng.standard_normal((32, 32, 32)) for _ in range(4)])
+    before = _level_cells(h.levels[1])
+    # same cells, other boxes
+    amr.regrid_level(h, 1, [((8, 8, 8), (23, 11, 15)), ((8, 12, 8), (23, 15, 15))])
+    assert _level_cells(h.levels[1]) == before
+    # a superset: the old cells and new cells along x
+    amr.regrid_level(h, 1, [((4, 8, 8), (27, 15, 15))])
+    after = _level_cells(h.levels[1])
+    for key, val in after.items():
+        if key in before:
+            assert val == before[key], key
+        else:
+            x = key[0]                                       # fine cell x spans [x/2 - 1/2, x/2] in level-0 units
+            exp = avg(x / 2 - 0.5, x / 2)
+            assert all(abs(c - exp) < 1e-13 for c in val), (key, val, exp)
+    assert len(after) == 24 * 8 * 8 and len(h.levels) == 3
+    amr.regrid_level(h, 1, [])
+    assert len(h.levels) == 1
