@@ -291,3 +291,35 @@ def test_regrid_level_copies_old_cells_and_prolongs_new_ones():
     assert len(after) == 24 * 8 * 8 and len(h.levels) == 3
     amr.regrid_level(h, 1, [])
     assert len(h.levels) == 1
+
+
+def test_full_cover_with_tensor_fields_equals_uniform_fine_run():
+    """The 16-field state (Sec. 5): a fine level covering the whole domain
+    reproduces a uniform fine run of psi, Pi, u_ij, v_ij bit for bit and
+    restricts onto the coarse level exactly, all 16 fields."""
+    from oracle import gw as ogw
+    n0, dx0, dt0 = 8, 0.25, 1.0 / 16
+    p = EOMParams(order=4)
+    rng = np.random.default_rng(14)
+    fine0 = [rng.uniform(-0.8, 0.8, size=(16, 16, 16)) for _ in range(4)]
+    fine0 += [0.1 * rng.standard_normal((16, 16, 16)) for _ in range(12)]
+    h = amr.make_hierarchy(n0, dx0, dt0, 3, 4,
+                           [[((0, 0, 0), (7, 7, 7))],
+                            [((0, 0, 0), (7, 15, 15)), ((8, 0, 0), (15, 7, 15)), ((8, 8, 0), (15, 15, 15))]],
+                           p, interp_type=4, eta0=0.5, gw=True)
+    h.levels[0].set_dense([interp.restrict_block(f) for f in fine0])
+    h.levels[1].set_dense(fine0)
+    for _ in range(2):
+        h.step()
+    ref, eta = fine0, 0.5
+    for _ in range(4):
+        ref = ogw.rk4_step_periodic(ref, eta, dt0 / 2, dx0 / 2, p)
+        eta += dt0 / 2
+    L1 = h.levels[1]
+    for b, (lo, hi) in enumerate(L1.boxes):
+        got = L1.data[b][L1.valid(b)]
+        for c in range(16):
+            assert np.array_equal(got[c], ref[c][lo[2]:hi[2] + 1, lo[1]:hi[1] + 1, lo[0]:hi[0] + 1]), (b, c)
+    got0 = h.levels[0].data[0][h.levels[0].valid(0)]
+    for c in range(16):
+        assert np.array_equal(got0[c], interp.restrict_block(ref[c])), c
