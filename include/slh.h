@@ -119,7 +119,8 @@ typedef struct {
  * (eta_power 2 as in the paper, 0 freezes it), the Laplacian of accuracy
  * lap_order in {2,4,6} (the 7/13/19-point stencils of App. A, ghost width
  * lap_order/2), and ghost prolongation interp_type in {0,2,4} (the
- * "interpolation_type" entry of the "amr" table; 4 = quartic conservative). */
+ * "interpolation_type" entry of the "amr" table; 4 = quartic conservative;
+ * type 1, linear conservative, is not built and returns INVALID_ARG). */
 typedef struct {
   double lambda;
   double a;
