@@ -143,3 +143,17 @@ def test_quadratic_exact_on_polynomials():
     for order in (2, 4, 6):
         L = stencil.laplacian_padded(f, g, 0.5, order)
         assert np.max(np.abs(L - 4.0)) < 1e-9
+
+
+def test_stencil_sizes_are_the_printed_ones():
+    """App. A: order p (the ghost width) gives the 7/13/19-point Laplacian and
+    the 3/5/7-point gradient; the oracle's order-2p stencils have half width p
+    and those point counts."""
+    from tests.helpers import golden
+    G = golden("app_a_stencils.json")
+    for p in (1, 2, 3):
+        lap = stencil.LAPLACIAN_WEIGHTS[2 * p]
+        assert stencil.half_width(2 * p) == p and len(lap) == 2 * p + 1
+        assert all(w != 0 for w in lap)
+        assert 1 + 3 * (len(lap) - 1) == G["laplacian_points_3d"][str(p)]     # centre shared by the 3 axes
+        assert len(stencil.GRADIENT_WEIGHTS[2 * p]) == G["gradient_points_1d"][str(p)]
