@@ -22,7 +22,10 @@ structure of the global regrid (oracle/regrid.py), with r = bf/2:
 
 Parity: pinned (the refined region only grows; every block of M_l ends up
 covered by level l+1; nesting holds on every level afterwards; nothing changes
-when every grown tag is already covered) -- tests/test_oracle_local_regrid.py.
+when every grown tag is already covered; minimality: each level's region
+equals, cell for cell, the least region the tags and the nesting rule force,
+found by a cell-level fixed-point iteration, plus a worked case where one
+block too many fails) -- tests/test_oracle_local_regrid.py.
 """
 from __future__ import annotations
 

@@ -232,12 +232,29 @@ def slh_energy_noalloc(fields_dev, n, dx, eta, params: EOMParams, out_dev, strea
     float64 tensor of 5 elements, written asynchronously on ``stream``
     (default: the current torch stream)."""
     import torch
+    # the C call sees raw pointers only: every size and type is checked here
+    n = int(n)
+    if not (isinstance(fields_dev, torch.Tensor) and fields_dev.is_cuda):
+        raise ValueError("fields_dev must be a CUDA tensor")
+    if fields_dev.dtype not in (torch.float64, torch.float32):
+        raise ValueError(f"fields_dev must be float64 or float32, not {fields_dev.dtype}")
+    if not fields_dev.is_contiguous():
+        raise ValueError("fields_dev must be contiguous")
+    if n < 1 or fields_dev.numel() < 4 * n ** 3:
+        raise ValueError(f"fields_dev holds {fields_dev.numel()} values, fewer than 4 n^3 = {4 * n ** 3}")
+    if not (isinstance(out_dev, torch.Tensor) and out_dev.is_cuda and out_dev.dtype == torch.float64
+            and out_dev.is_contiguous() and out_dev.numel() >= 5):
+        raise ValueError("out_dev must be a contiguous CUDA float64 tensor of at least 5 values")
+    if out_dev.device != fields_dev.device:
+        raise ValueError("fields_dev and out_dev must be on the same device")
     prec = SLH_F64 if fields_dev.dtype == torch.float64 else SLH_F32_KAHAN
-    st = torch.cuda.current_stream(fields_dev.device) if stream is None else stream
     p = params.c()
-    _check(lib().slh_energy_noalloc(ctypes.c_void_p(fields_dev.data_ptr()), int(n), prec, float(dx), float(eta),
-                                    ctypes.byref(p), ctypes.c_void_p(out_dev.data_ptr()),
-                                    ctypes.c_void_p(st.cuda_stream)))
+    # the library looks up its scratch array on the current device
+    with torch.cuda.device(fields_dev.device):
+        st = torch.cuda.current_stream(fields_dev.device) if stream is None else stream
+        _check(lib().slh_energy_noalloc(ctypes.c_void_p(fields_dev.data_ptr()), n, prec, float(dx), float(eta),
+                                        ctypes.byref(p), ctypes.c_void_p(out_dev.data_ptr()),
+                                        ctypes.c_void_p(st.cuda_stream)))
 
 
 def dense_from_boxes(fields, boxes):

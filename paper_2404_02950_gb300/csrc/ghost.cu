@@ -110,7 +110,27 @@ struct PassGeo {
   int flo[3];
   int plo[3];
   int ext[3];
+  int pn[3];
 };
+
+// Coverage of the coarse patch where the planned pieces do not tile it: one
+// bit per patch cell, set where no coarse box holds the cell (its patch
+// value is then 0).  The widest patch (g = 4) has 21 x 21 x 7 cells.
+constexpr int UNC_WORDS = (21 * 21 * 7 + 31) / 32;
+
+// Whether the radius-RAD stencil of the fine cell (unwrapped fine
+// coordinates f) meets an uncovered patch cell.
+template <int RAD>
+__device__ __forceinline__ bool stencil_uncovered(const unsigned* unc, const PassGeo& geo, int fx, int fy, int fz) {
+  const int px = (fx >> 1) - geo.plo[0], py = (fy >> 1) - geo.plo[1], pz = (fz >> 1) - geo.plo[2];
+  for (int oz = -RAD; oz <= RAD; ++oz)
+    for (int oy = -RAD; oy <= RAD; ++oy)
+      for (int ox = -RAD; ox <= RAD; ++ox) {
+        const int q = ((pz + oz) * geo.pn[1] + (py + oy)) * geo.pn[0] + (px + ox);
+        if ((unc[q >> 5] >> (q & 31)) & 1u) return true;
+      }
+  return false;
+}
 
 template <int AX>
 __device__ __forceinline__ int pick(int a, int b, int c) { return AX == 0 ? a : (AX == 1 ? b : c); }
@@ -162,7 +182,7 @@ template <typename T, int RAD, int AX, int NF>
 __device__ __forceinline__ void final_pass(const T* __restrict__ src, int sstr, const int (&d)[3], const PassGeo& geo,
                                            const T (&w0)[2 * RAD + 1], const T (&w1)[2 * RAD + 1],
                                            const GhostArgs<T>& A, const GhostRegion& R, const BoxDev& B, int f0,
-                                           bool have_coarse) {
+                                           bool have_coarse, const unsigned* unc) {
   const int o0 = AX == 0 ? geo.ext[0] : d[0], o1 = AX == 1 ? geo.ext[1] : d[1], o2 = AX == 2 ? geo.ext[2] : d[2];
   const int sa = AX == 0 ? 1 : (AX == 1 ? d[0] : d[0] * d[1]);
   const int fa = geo.flo[AX], pa = geo.plo[AX];
@@ -192,6 +212,14 @@ __device__ __forceinline__ void final_pass(const T* __restrict__ src, int sstr, 
       atomicCAS(A.err, 0, DERR_NESTING);
       continue;
     }
+    // a stencil that reaches a coarse cell no coarse box holds (the patch
+    // was not tiled by the plan) is a nesting violation; field values, NaN
+    // or infinite ones included, are never inspected
+    if (unc != nullptr &&
+        stencil_uncovered<RAD>(unc, geo, geo.flo[0] + i0, geo.flo[1] + i1, geo.flo[2] + i2)) {
+      atomicCAS(A.err, 0, DERR_NESTING);
+      continue;
+    }
     const int g = fa + pick<AX>(i0, i1, i2);
     const int pc = (g >> 1) - pa - RAD;
     const bool ch = (g & 1) != 0;
@@ -201,7 +229,6 @@ __device__ __forceinline__ void final_pass(const T* __restrict__ src, int sstr, 
       T acc = 0;
 #pragma unroll
       for (int o = 0; o <= 2 * RAD; ++o) acc += (ch ? w1[o] : w0[o]) * src[f * sstr + base + o * sa];
-      if (acc != acc) atomicCAS(A.err, 0, DERR_NESTING);   // the stencil met an uncovered (NaN) coarse cell
       const int comp = A.pc[(f0 + f) >> 1] + ((f0 + f) & 1);
       A.y[dg + comp * B.cs] = acc;
     }
@@ -212,10 +239,10 @@ template <typename T, int RAD, int NF>
 __device__ __forceinline__ void final_pass_any(int ax, const T* src, int sstr, const int (&d)[3], const PassGeo& geo,
                                                const T (&w0)[2 * RAD + 1], const T (&w1)[2 * RAD + 1],
                                                const GhostArgs<T>& A, const GhostRegion& R, const BoxDev& B, int f0,
-                                               bool have_coarse) {
-  if (ax == 0) final_pass<T, RAD, 0, NF>(src, sstr, d, geo, w0, w1, A, R, B, f0, have_coarse);
-  else if (ax == 1) final_pass<T, RAD, 1, NF>(src, sstr, d, geo, w0, w1, A, R, B, f0, have_coarse);
-  else final_pass<T, RAD, 2, NF>(src, sstr, d, geo, w0, w1, A, R, B, f0, have_coarse);
+                                               bool have_coarse, const unsigned* unc) {
+  if (ax == 0) final_pass<T, RAD, 0, NF>(src, sstr, d, geo, w0, w1, A, R, B, f0, have_coarse, unc);
+  else if (ax == 1) final_pass<T, RAD, 1, NF>(src, sstr, d, geo, w0, w1, A, R, B, f0, have_coarse, unc);
+  else final_pass<T, RAD, 2, NF>(src, sstr, d, geo, w0, w1, A, R, B, f0, have_coarse, unc);
 }
 
 // Same-level copy regions [0, r0): no shared memory, so many CTAs per SM
@@ -275,6 +302,7 @@ __global__ void __launch_bounds__(256, 5) ghost_region_kernel(const GhostArgs<T>
   const int PATCH_MAX = patch_max(A.gl), PASS1_MAX = pass1_max(A.gl), PASS2_MAX = pass2_max(A.gl);
   T* buf1 = patch + NF * PATCH_MAX;
   T* buf2 = buf1 + NF * PASS1_MAX;
+  __shared__ unsigned s_unc[UNC_WORDS];
   const int tid = threadIdx.x, nt = blockDim.x;
   const T al = (T)A.alpha, bl = (T)1 - (T)A.alpha;
   T w0[2 * RAD + 1], w1[2 * RAD + 1];   // 1D weights of child 0 and child 1
@@ -323,7 +351,14 @@ __global__ void __launch_bounds__(256, 5) ghost_region_kernel(const GhostArgs<T>
     if (ext_of(a1) < ext_of(a0)) { const int s_ = a0; a0 = a1; a1 = s_; }
     if (ext_of(a2) < ext_of(a1)) { const int s_ = a1; a1 = a2; a2 = s_; }
     if (ext_of(a1) < ext_of(a0)) { const int s_ = a0; a0 = a1; a1 = s_; }
-    const PassGeo geo{{flo[0], flo[1], flo[2]}, {plo[0], plo[1], plo[2]}, {ex0, ex1, ex2}};
+    const PassGeo geo{{flo[0], flo[1], flo[2]}, {plo[0], plo[1], plo[2]}, {ex0, ex1, ex2}, {pn[0], pn[1], pn[2]}};
+    // patch not tiled by the planned pieces (uniform over the CTA): the
+    // gather looks every cell up and marks the uncovered ones
+    const bool lookup = have_coarse && !R.covered;
+    if (lookup) {
+      for (int w = tid; w < UNC_WORDS; w += nt) s_unc[w] = 0u;
+      __syncthreads();
+    }
     for (int f0 = 0; f0 < 2 * A.npairs; f0 += NF) {
       // gather NF fields into the patch (field f of the region's pair list)
       for (int f = 0; f < NF; ++f) {
@@ -345,7 +380,8 @@ __global__ void __launch_bounds__(256, 5) ghost_region_kernel(const GhostArgs<T>
           }
         } else if (have_coarse) {
           // footprint not tiled by the coarse level (a nesting violation, or a
-          // level built without a plan): per-cell lookup, NaN where uncovered
+          // level built without a plan): per-cell lookup; an uncovered cell
+          // reads 0 and is marked in s_unc
           const Split3 sp(pn[0], pn[1]);
 #pragma unroll 4
           for (int t = tid; t < np; t += nt) {
@@ -353,11 +389,13 @@ __global__ void __launch_bounds__(256, 5) ghost_region_kernel(const GhostArgs<T>
             sp(t, i, j, k);
             const int qx = wrapi(plo[0] + i, A.cndom), qy = wrapi(plo[1] + j, A.cndom), qz = wrapi(plo[2] + k, A.cndom);
             const int cown = A.cbmap[((long long)(qz >> A.bshift) * A.cnbd + (qy >> A.bshift)) * A.cnbd + (qx >> A.bshift)];
-            T v = (T)__longlong_as_double(0x7ff8000000000000ll);   // NaN: not covered
+            T v = 0;
             if (cown >= 0) {
               const BoxDev C = A.cboxes[cown];
               const long long ci = cell_index(C, A.gl, qx - C.lo[0], qy - C.lo[1], qz - C.lo[2]) + comp * C.cs;
               v = bl * A.cold[ci] + al * A.cnew[ci];
+            } else if (f == 0 && f0 == 0) {
+              atomicOr(&s_unc[t >> 5], 1u << (t & 31));
             }
             pf[t] = v;
           }
@@ -377,7 +415,8 @@ __global__ void __launch_bounds__(256, 5) ghost_region_kernel(const GhostArgs<T>
         d[1] = ex1;
         d[2] = ex2;
       }
-      final_pass_any<T, RAD, NF>(a2, buf2, PASS2_MAX, d, geo, w0, w1, A, R, B, f0, have_coarse);
+      final_pass_any<T, RAD, NF>(a2, buf2, PASS2_MAX, d, geo, w0, w1, A, R, B, f0, have_coarse,
+                                 lookup ? s_unc : nullptr);
       __syncthreads();   // the buffers are reused by the next fields or region
     }
   }

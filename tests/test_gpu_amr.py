@@ -169,6 +169,29 @@ def test_graph_replay_on_hierarchy_matches_direct():
         assert np.array_equal(ha.get_state(l), hb.get_state(l))
 
 
+def test_nonfinite_coarse_value_is_not_a_nesting_error():
+    """A NaN in a covered coarse cell is a field value, not a box-layout
+    error: the ghost fill returns OK and carries the NaN into the ghost cells
+    whose stencil reads it; every other ghost cell stays finite."""
+    import torch
+    p = slh.EOMParams(order=4, interp_type=4)
+    oh = _oracle_hierarchy(p, 2)
+    h = _gpu_hierarchy(oh)
+    h.sync()
+    # coarse cell (x, y, z) = (7, 12, 12): outside level 1's footprint
+    # (coarse 8..23) but under the quartic stencils of its lower-x ghost
+    # shell (level-1 x = 13..15 -> coarse parents 6..7, radius 2)
+    v = box_padded_views(h, 0)[0]
+    with torch.no_grad():
+        v[0, 12 + G, 12 + G, 7 + 4] = float("nan")
+    h.fill_ghosts(1, alpha=1.0, interp_type=4)
+    h.sync()   # no latched error
+    got = _ghosted(h, 1)
+    nan_cells = sum(int(np.isnan(a[0]).sum()) for a in got)
+    assert nan_cells > 0
+    assert all(np.isfinite(a[1]).all() for a in got)   # psi2's ghosts never read the NaN
+
+
 def test_nesting_violation_is_rejected_on_host():
     h = slh.Hierarchy(N0, DX0, nghost=G, bf=BF, prec="f64", max_levels=3)
     h.init_level(0, LEVEL_BOXES[0])

@@ -202,6 +202,22 @@ def test_spectrum_f32_and_tt_wave():
     assert np.max(np.abs(g[n2 != 9])) < 1e-15
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_spectrum_is_bit_reproducible(prec):
+    """The bins are summed in a fixed order (no atomics): two calls on the
+    same state agree bit for bit."""
+    y = _initial()
+    if prec == "f32":
+        y = [a.astype(np.float32) for a in y]
+    h = slh.Hierarchy(N, DX, nghost=G, bf=BF, prec=prec, max_levels=1, gw=True)
+    h.init_level(0, FULL)
+    h.set_state(0, slh.dense_from_boxes(y, FULL))
+    runs = [h.gw_spectrum(ptype) for ptype in (2, 2, 1, 1)]
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+    assert np.array_equal(runs[2][0], runs[3][0]) and np.array_equal(runs[2][1], runs[3][1])
+    h.close()
+
+
 def test_spectrum_needs_tensor_fields():
     h = slh.Hierarchy(N, DX, nghost=G, bf=BF, prec="f64", max_levels=1)
     h.init_level(0, FULL)

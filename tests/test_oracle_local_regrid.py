@@ -80,3 +80,64 @@ def test_no_change_when_covered_and_idempotent():
     lo, hi = boxes[1][0]
     inner[0][lo[2] // bf, lo[1] // bf, lo[0] // bf] = True      # level-1 cell c lies in level-0 block c // bf
     assert olr.local_regrid(boxes, n0, bf, inner) == boxes
+
+
+def _brute_force_cells(boxes, n0, bf, masks):
+    """The least refined region per level that keeps the old boxes, covers
+    every tagged block of M_l by level l+1 and nests every level in the one
+    below with a gap of r = bf/2 coarse cells, with additions in whole blocks
+    of bf cells: cell by cell, iterated to a fixed point (no block algebra)."""
+    L = len(boxes)
+    r = bf // 2
+    cells = [_cells(boxes[l], n0 << l) > 0 for l in range(L)]
+    for l in range(L - 1):
+        for bz, by, bx in zip(*np.nonzero(np.asarray(masks[l], dtype=bool))):
+            # r cells of level l along an axis = 2r = bf cells of level l+1
+            cells[l + 1][bz * bf:(bz + 1) * bf, by * bf:(by + 1) * bf, bx * bf:(bx + 1) * bf] = True
+    changed = True
+    while changed:
+        changed = False
+        for j in range(L - 1, 0, -1):
+            nc = n0 << (j - 1)
+            foot = cells[j].reshape(nc, 2, nc, 2, nc, 2).any(axis=(1, 3, 5))
+            req = np.zeros_like(foot)
+            for dz in range(-r, r + 1):
+                for dy in range(-r, r + 1):
+                    for dx in range(-r, r + 1):
+                        req |= np.roll(foot, (dz, dy, dx), axis=(0, 1, 2))
+            nb = nc // bf
+            blk = req.reshape(nb, bf, nb, bf, nb, bf).any(axis=(1, 3, 5))
+            req = np.repeat(np.repeat(np.repeat(blk, bf, 0), bf, 1), bf, 2)
+            if (req & ~cells[j - 1]).any():
+                cells[j - 1] |= req
+                changed = True
+    return cells
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_adds_exactly_the_required_blocks(seed):
+    """Minimality: the refined region of every level equals, cell for cell,
+    the least region the tags and the nesting rule force (a local regrid that
+    grows one block too many, or a nesting shell one block too wide, fails)."""
+    boxes, masks, n0, bf = _random_case(seed)
+    out = olr.local_regrid(boxes, n0, bf, masks)
+    want = _brute_force_cells(boxes, n0, bf, masks)
+    for l in range(len(boxes)):
+        assert np.array_equal(_cells(out[l], n0 << l) > 0, want[l]), l
+
+
+def test_worked_case_one_tag_block_at_the_fine_edge():
+    """Level 1 = [4, 11]^3 and level 2 = [12, 19]^3 (bf = 4, r = 2); one tagged
+    block of level 1 at cells (10..11, 8..9, 8..9), just outside level 2.
+    Level 2 gains exactly that block ([20, 23] x [16, 19]^2); its footprint
+    grown by 2 reaches level-1 x = 12..13, so level 1 gains exactly the four
+    blocks x in [12, 15], y and z in [4, 7] or [8, 11]; level 0 is unchanged."""
+    n0, bf = 16, 4
+    boxes = [[((0, 0, 0), (15, 15, 15))], [((4, 4, 4), (11, 11, 11))], [((12, 12, 12), (19, 19, 19))]]
+    masks = [np.zeros((8, 8, 8), dtype=bool), np.zeros((16, 16, 16), dtype=bool)]
+    masks[1][4, 4, 5] = True       # [z, y, x] r-block of level 1: cells x 10..11, y 8..9, z 8..9
+    out = olr.local_regrid(boxes, n0, bf, masks)
+    assert out[0] == boxes[0]
+    assert out[2] == boxes[2] + [((20, 16, 16), (23, 19, 19))]
+    assert out[1] == boxes[1] + [((12, 4, 4), (15, 7, 7)), ((12, 8, 4), (15, 11, 7)),
+                                 ((12, 4, 8), (15, 7, 11)), ((12, 8, 8), (15, 11, 11))]

@@ -1,6 +1,8 @@
 """The allocation-free energy entry point (for callers that cannot call
-cudaMalloc) against the regular context-based reduction of the same state,
-on two calls in a row; and its size limit."""
+cudaMalloc) against the regular context-based reduction of the same state
+and against the CPU oracle, on two calls in a row; that a warm call
+allocates no device memory; its size limit and the binding's argument
+checks."""
 import ctypes
 import os
 
@@ -8,7 +10,9 @@ import numpy as np
 import pytest
 
 import paper_2404_02950_gb300 as slh
+from oracle import energy as oenergy
 from paper_2404_02950_gb300 import inputs
+from tests.helpers import oparams
 
 pytestmark = pytest.mark.gpu
 
@@ -36,15 +40,46 @@ def test_noalloc_energy_matches_context_reduction_twice(prec, order, tol):
     ref = h.reduce_energy(p)
     dt = torch.float64 if prec == "f64" else torch.float32
     fields = torch.from_numpy(np.stack(y)).to(dt).cuda().contiguous()
+    # the oracle on the state as stored (FP32 values widened exactly)
+    orc = oenergy.energy_periodic([a.astype(np.float64) for a in fields.cpu().numpy()], eta, dx, oparams(p))
+    outs = [torch.full((5,), float("nan"), dtype=torch.float64, device="cuda") for _ in range(2)]
+    torch.cuda.synchronize()
     for call in range(2):
-        out = torch.full((5,), float("nan"), dtype=torch.float64, device="cuda")
-        slh.slh_energy_noalloc(fields, n, dx, eta, p, out)
+        if call == 1:
+            # a warm call allocates nothing: neither through torch nor on the device
+            alloc0 = torch.cuda.memory_allocated()
+            free0, _ = torch.cuda.mem_get_info()
+        slh.slh_energy_noalloc(fields, n, dx, eta, p, outs[call])
         torch.cuda.synchronize()
-        got = out.cpu().numpy()
+        if call == 1:
+            assert torch.cuda.memory_allocated() == alloc0
+            assert torch.cuda.mem_get_info()[0] == free0
+        got = outs[call].cpu().numpy()
         for k in range(4):
             assert abs(got[k] - ref[k]) <= tol * max(abs(ref[k]), 1.0), (call, k, got[k], ref[k])
+            assert abs(got[k] - orc[k]) <= tol * max(abs(orc[k]), 1.0), (call, k, got[k], orc[k])
         assert got[4] == ref[4], (call, got[4], ref[4])
+        assert got[4] == orc[4], (call, got[4], orc[4])
     h.close()
+
+
+def test_noalloc_binding_rejects_bad_buffers():
+    import torch
+    n = 8
+    p = slh.EOMParams()
+    good = torch.zeros(4 * n ** 3, dtype=torch.float64, device="cuda")
+    out = torch.zeros(5, dtype=torch.float64, device="cuda")
+    bad_calls = [
+        (good.cpu(), out),                                                  # host tensor
+        (good.to(torch.bfloat16), out),                                     # unsupported dtype
+        (good[: 4 * n ** 3 - 1], out),                                      # too short
+        (good.view(4, n ** 3).t(), out),                                    # not contiguous
+        (good, torch.zeros(5, dtype=torch.float32, device="cuda")),          # out not float64
+        (good, torch.zeros(4, dtype=torch.float64, device="cuda")),          # out too short
+    ]
+    for f, o in bad_calls:
+        with pytest.raises(ValueError):
+            slh.slh_energy_noalloc(f, n, 1.0, 1.0, p, o)
 
 
 def test_noalloc_rejects_lattice_beyond_scratch_limit():
