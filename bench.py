@@ -200,6 +200,22 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _error_vs_f64(st32, st64, cells, len32, len64, steps):
+    """Relative L2 error per field (psi1, psi2, Pi1, Pi2) and relative
+    string-length error of the FP32 + Kahan state against the FP64 state
+    after the same steps from the same field."""
+    import torch
+    out = {}
+    for c, name in enumerate(("psi1", "psi2", "Pi1", "Pi2")):
+        a = st32[c * cells:(c + 1) * cells].double()
+        b = st64[c * cells:(c + 1) * cells]
+        out[name] = float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+    out["string_length"] = abs(len32 - len64) / len64 if len64 > 0 else None
+    out["steps"] = steps
+    out["bound"] = "1e-4 relative L2 per field, 1 % string length (tests/test_gpu_precision.py checks 100 steps)"
+    return out
+
+
 def _time_form(slh, torch, prec, y0_dense, n, K, W, dist, flags, gw=False, order=ORDER, integrator=4, tile=None,
                diag_tile=None, friction=True):
     """Warm up, then time K steps of one precision; returns a dict."""
@@ -369,6 +385,11 @@ def run_ours(args, rank, world, local_rank, dist):
         # short run for profilers: no e2e leg, no FP64 form, no JSON line
         h32.close()
         return
+    # the FP32 state after the timed steps, kept on the device for the error
+    # against the FP64 form on the same field and step count
+    p6 = slh.EOMParams(order=ORDER)
+    st32 = h32.get_state_device(0)
+    len32 = float(h32.reduce_energy(p6, mode=0)[4])
 
     # end to end through the C ABI with host buffers: upload the step's input
     # from pinned memory, advance, read the step's energy back
@@ -394,8 +415,10 @@ def run_ours(args, rank, world, local_rank, dist):
 
     # FP64 plain on the same field
     h64, r64 = _time_form(slh, torch, "f64", dense, n, K, W, dist, flags)
+    err = _error_vs_f64(st32, h64.get_state_device(0), n ** 3, len32, float(h64.reduce_energy(p6, mode=0)[4]),
+                        W + K)
     h64.close()
-    del h64
+    del h64, st32
     torch.cuda.empty_cache()
 
     # dynamic AMR (config 3 workload), FP32 batched and FP64 plain
@@ -498,6 +521,7 @@ def run_ours(args, rank, world, local_rank, dist):
                      "kernel": "stage_kernel<float,3> (4 RK4 stages; tags + energy fused in stage 1)",
                      "peak_kind": peak_kind,
                      "alg_bytes_per_cell_update": KAHAN_VALUES * 4},
+        "error_vs_f64": err,
         "fp64_plain": {"value": job_value(world, cells, K, ms64), "unit": "cell-updates/s",
                        "ms_per_step": ms64 / K, "stage_achieved_gbs": ach64,
                        "hbm_frac": ach64 / peak, "alg_bytes_per_cell_update": F64_VALUES * 8},

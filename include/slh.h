@@ -105,7 +105,13 @@ typedef int32_t slh_status;
 #define SLH_PROF_S4 8
 #define SLH_PROF_GW 9        /* the gravitational-wave stage kernel (16 fields) */
 #define SLH_PROF_KO 10       /* the dissipation kernel */
-#define SLH_PROF_NKINDS 11
+/* host wall-clock phases, recorded whether or not profiling is enabled
+ * (cleared by slh_profile's reset): */
+#define SLH_PROF_REGRID_TAGS 11     /* slh_regrid: tags and block masks (device + copy back) */
+#define SLH_PROF_REGRID_CLUSTER 12  /* slh_regrid: host clustering (global or local) */
+#define SLH_PROF_REGRID_BUILD 13    /* slh_regrid: caller's allocator + level rebuild */
+#define SLH_PROF_GRAPH_CAPTURE 14   /* slh_advance: capture and instantiation of a graph */
+#define SLH_PROF_NKINDS 15
 
 typedef struct {
   int32_t lo[3];
@@ -370,6 +376,72 @@ slh_status slh_local_regrid_boxes(int32_t nlevels, int32_t n0, int32_t blocking_
                                   const int32_t* nboxes, slh_box* out, int32_t cap,
                                   int32_t* out_nboxes);
 
+/* slh_regrid modes */
+#define SLH_REGRID_GLOBAL 0  /* cluster the grown tags of every level anew */
+#define SLH_REGRID_LOCAL 1   /* keep every box, only add where needed */
+#define SLH_REGRID_AUTO 2    /* local, with the fallback rule below */
+
+/* Parameters of slh_regrid (Sec. 2.2-2.3 and the "amr" table of App. F). */
+typedef struct {
+  int32_t mode;          /* SLH_REGRID_GLOBAL, SLH_REGRID_LOCAL or SLH_REGRID_AUTO */
+  int32_t max_levels;    /* levels the hierarchy may hold afterwards, in [1, ctx max_levels] */
+  int32_t start;         /* global: levels <= start keep their boxes; the tags of level start
+                            give level start+1 (0: regrid every level above the base) */
+  int32_t n_error_buf;   /* cells the tags are grown by ("n_error_buf") */
+  int32_t max_box;       /* largest box side in cells of the new level, a multiple of the
+                            blocking factor */
+  int32_t interp_type;   /* prolongation of new cells: 0, 2 or 4 */
+  int32_t max_local;     /* auto: local regrids in a row after which a global one runs
+                            ("max_local_regrids", paper default 10; 0 = no cap) */
+  int32_t pad_;
+  double eps_strong;     /* auto: added-volume fraction that forces a global regrid
+                            ("volume_threshold_strong" - 1, paper default 0.1) */
+  double eps_weak;       /* auto: fraction from which a level is regridded with it
+                            ("volume_threshold_weak" - 1, paper default 0.05) */
+} slh_regrid_params;
+
+/* Caller's allocator for the levels slh_regrid rebuilds.  Called with the
+ * new boxes of level lev, the buffer length total_elems (elements of the
+ * context precision, as slh_level_layout) and nvalid; it stores SLH_NBUF
+ * device pointers in bufs (bufs[SLH_BUF_C] may stay NULL unless
+ * SLH_F32_KAHAN) and, optionally, a device buffer of nvalid bytes for fused
+ * tags in *tags_dev (left NULL: none).  The buffers must stay valid while
+ * the level exists; the level's previous buffers are no longer referenced
+ * once the rebuild of lev returns.  Called with nboxes = 0 (boxes, bufs,
+ * tags_dev NULL) after level lev and every finer level were removed.
+ * Returns 0 on success, nonzero to abort the regrid (SLH_ERR_NOMEM). */
+typedef int32_t (*slh_level_alloc_fn)(void* user, int32_t lev, const slh_box* boxes, int32_t nboxes,
+                                      int64_t total_elems, int64_t nvalid, void** bufs, uint8_t** tags_dev);
+
+/* Regrid the live hierarchy at a synchronised time (after slh_advance),
+ * Sec. 2.2-2.3.
+ *  - Global: for l = start, start+1, ...: the block mask of level l
+ *    (slh_tag_blocks: the enabled criteria, grown by n_error_buf, in blocks
+ *    of blocking_factor/2 cells), clustered as slh_regrid_boxes does inside
+ *    level l's boxes eroded by one block (l > 0), gives the boxes of level
+ *    l+1 (at most max_levels levels), which is rebuilt (slh_regrid_level)
+ *    before its own tags give level l+2; an empty list removes the level and
+ *    every finer one.
+ *  - Local: the block masks of every level but the finest, then
+ *    slh_local_regrid_boxes; the levels from the lowest one that gained
+ *    cells upward are rebuilt.
+ *  - Auto (the paper's fallback rule): the volume local regrids added to
+ *    each level since the last global regrid is tracked as a fraction dV_l
+ *    of the level's volume then.  The regrid is global when the hierarchy
+ *    has fewer than max_levels levels, or when the previous local regrid
+ *    left dV_l >= eps_strong on some level or was the max_local-th in a row:
+ *    it then starts from level l0 - 1, l0 the lowest level >= 1 with
+ *    dV_l >= eps_weak (level 0 if none).  Otherwise it is local.  A global
+ *    regrid restarts the counts from the new volumes.
+ * Levels are rebuilt with buffers from alloc(user, ...).  *kind (may be
+ * NULL) receives SLH_REGRID_GLOBAL or SLH_REGRID_LOCAL; frac (may be NULL,
+ * one entry per level before the call) receives dV_l after an auto local
+ * regrid, or the cells each level gained in mode local.  Synchronises.
+ * Errors: INVALID_ARG, STATE, NOMEM, CUDA; a failure part way leaves the
+ * levels rebuilt so far in place. */
+slh_status slh_regrid(slh_ctx* ctx, const slh_regrid_params* rp, slh_level_alloc_fn alloc, void* user,
+                      int32_t* kind, double* frac);
+
 /* Energy and string length of the hierarchy over the cells not covered by
  * a finer level, each level at its own eta:
  *   out[0] = sum 1/2 (Pi1^2 + Pi2^2) dx^3
@@ -459,7 +531,10 @@ slh_status slh_sync(slh_ctx* ctx);
  * time per kind (SLH_PROF_*) is accumulated; slh_profile_read synchronises
  * and returns the total milliseconds, the number of launches and the
  * algorithmic bytes those launches moved (field values read + written per
- * valid cell, ghost and halo re-reads excluded).  enable 0/1; reset clears. */
+ * valid cell, ghost and halo re-reads excluded).  enable 0/1; reset clears.
+ * While profiling is enabled slh_advance launches directly (no graph).
+ * The host-phase kinds (SLH_PROF_REGRID_*, SLH_PROF_GRAPH_CAPTURE) give host
+ * wall-clock milliseconds and the number of phases, always recorded. */
 slh_status slh_profile(slh_ctx* ctx, int32_t enable, int32_t reset);
 slh_status slh_profile_read(slh_ctx* ctx, int32_t kind, double* ms, int64_t* launches,
                             double* alg_bytes);

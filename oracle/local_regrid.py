@@ -20,12 +20,17 @@ structure of the global regrid (oracle/regrid.py), with r = bf/2:
    followed by its new blocks merged along x into runs (runs ordered by z,
    then y, then x; no run crosses the periodic boundary).
 
+RegridPolicy states the paper's rule for falling back from local to global
+regrids (the volume thresholds eps_s, eps_w and the cap on consecutive local
+regrids).
+
 Parity: pinned (the refined region only grows; every block of M_l ends up
 covered by level l+1; nesting holds on every level afterwards; nothing changes
 when every grown tag is already covered; minimality: each level's region
 equals, cell for cell, the least region the tags and the nesting rule force,
 found by a cell-level fixed-point iteration, plus a worked case where one
-block too many fails) -- tests/test_oracle_local_regrid.py.
+block too many fails; the policy by worked sequences of volumes) --
+tests/test_oracle_local_regrid.py.
 """
 from __future__ import annotations
 
@@ -87,3 +92,51 @@ def local_regrid(level_boxes, n0: int, bf: int, masks):
         new[j - 1] |= needc & ~have[j - 1]
     new[0][:] = False                        # level 0 covers the domain
     return [list(level_boxes[l]) + _runs(new[l] & ~have[l], bf) for l in range(L)]
+
+
+class RegridPolicy:
+    """When a local regrid gives way to a global one (Sec. 2.3): the volume
+    that local regrids added to each level since the last global regrid is
+    tracked as a fraction dV_l of the level's volume at that global regrid.
+    Once dV_l >= eps_strong on some level (or max_local local regrids have
+    run in a row), the next regrid is global, starting at the lowest level
+    l >= 1 with dV_l >= eps_weak (that level and the finer ones are rebuilt,
+    from the tags of level l - 1); with no such level it starts at level 1.
+    A hierarchy with fewer levels than it may have is regridded globally
+    (a local regrid never creates a level).  The paper's defaults are
+    eps_strong = 10 % and eps_weak = 5 % (its parameter table writes them as
+    the volume ratios 1.1 and 1.05) and at most 10 local regrids in a row.
+
+    next_regrid(volumes) -> ("global", l0) or ("local", None), where l0 is the
+    level whose tags the global regrid starts from; then after_local(added)
+    with the cells each level gained, or after_global()."""
+
+    def __init__(self, max_levels, eps_strong=0.1, eps_weak=0.05, max_local=10):
+        self.max_levels = max_levels
+        self.eps_strong, self.eps_weak, self.max_local = eps_strong, eps_weak, max_local
+        self.base = None
+
+    def next_regrid(self, volumes):
+        if self.base is None or len(self.base) != len(volumes):
+            self.base = [max(1, int(v)) for v in volumes]
+            self.added = [0] * len(volumes)
+            self.count = 0
+            self.pending = None
+        if self.pending is not None:
+            return "global", self.pending
+        if len(volumes) < self.max_levels:
+            return "global", 0
+        return "local", None
+
+    def after_local(self, added):
+        self.count += 1
+        self.added = [a + int(b) for a, b in zip(self.added, added)]
+        frac = [a / b for a, b in zip(self.added, self.base)]
+        if any(f >= self.eps_strong for f in frac) or (self.max_local and self.count >= self.max_local):
+            weak = [l for l in range(1, len(frac)) if frac[l] >= self.eps_weak]
+            self.pending = (min(weak) - 1) if weak else 0
+        return frac
+
+    def after_global(self):
+        self.base = None
+

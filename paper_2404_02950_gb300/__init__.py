@@ -33,8 +33,10 @@ SLH_USE_GRAPH = 4
 SLH_GHOSTS = 0
 SLH_RESTRICT = 1
 SLH_TAG_WINDING, SLH_TAG_TEE = 1, 2
+SLH_REGRID_GLOBAL, SLH_REGRID_LOCAL, SLH_REGRID_AUTO = 0, 1, 2
 (SLH_PROF_STAGE, SLH_PROF_GHOST, SLH_PROF_RESTRICT, SLH_PROF_DIAG, SLH_PROF_TIME,
- SLH_PROF_S1, SLH_PROF_S2, SLH_PROF_S3, SLH_PROF_S4, SLH_PROF_GW, SLH_PROF_KO) = range(11)
+ SLH_PROF_S1, SLH_PROF_S2, SLH_PROF_S3, SLH_PROF_S4, SLH_PROF_GW, SLH_PROF_KO,
+ SLH_PROF_REGRID_TAGS, SLH_PROF_REGRID_CLUSTER, SLH_PROF_REGRID_BUILD, SLH_PROF_GRAPH_CAPTURE) = range(15)
 NFIELDS, NFIELDS_GW = 4, 16   # psi1, psi2, Pi1, Pi2 (+ u_xx..u_yz, v_xx..v_yz)
 
 ERRORS = {-1: "INVALID_ARG", -2: "OUT_OF_RANGE", -3: "CUDA", -4: "TIMEOUT", -5: "NOMEM",
@@ -49,7 +51,7 @@ ABI_SYMBOLS = (
     "slh_autotune", "slh_autotune_diag",
     "slh_energy_noalloc", "slh_regrid_level", "slh_selftest_wait_timeout",
     "slh_set_tagging", "slh_shadow_init", "slh_shadow_compare", "slh_tee_tags", "slh_gw_spectrum",
-    "slh_local_regrid_boxes",
+    "slh_local_regrid_boxes", "slh_regrid",
 )
 
 
@@ -68,6 +70,19 @@ class slh_eom_params(ctypes.Structure):
                 ("eta_power", ctypes.c_int32), ("lap_order", ctypes.c_int32),
                 ("interp_type", ctypes.c_int32), ("integrator", ctypes.c_int32), ("pad_", ctypes.c_int32),
                 ("ko_eps", ctypes.c_double), ("ko_order", ctypes.c_int32), ("pad2_", ctypes.c_int32)]
+
+
+class slh_regrid_params(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("max_levels", ctypes.c_int32), ("start", ctypes.c_int32),
+                ("n_error_buf", ctypes.c_int32), ("max_box", ctypes.c_int32), ("interp_type", ctypes.c_int32),
+                ("max_local", ctypes.c_int32), ("pad_", ctypes.c_int32), ("eps_strong", ctypes.c_double),
+                ("eps_weak", ctypes.c_double)]
+
+
+# the caller's allocator slh_regrid calls for every level it rebuilds
+SLH_LEVEL_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(slh_box),
+                                      ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
+                                      ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p))
 
 
 @dataclass(frozen=True)
@@ -139,6 +154,7 @@ def lib():
         "slh_tee_tags": (i32, [vp, i32, vp, i32]),
         "slh_gw_spectrum": (i32, [vp, i32, P(i64), P(dbl), i32, P(i32)]),
         "slh_local_regrid_boxes": (i32, [i32, i32, i32, P(vp), P(slh_box), P(i32), P(slh_box), i32, P(i32)]),
+        "slh_regrid": (i32, [vp, P(slh_regrid_params), SLH_LEVEL_ALLOC_FN, vp, P(i32), P(dbl)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -368,76 +384,71 @@ class Hierarchy:
         self.levels[lev] = dict(boxes=list(boxes), bufs=bufs, tags=tags, nvalid=nvalid, total=total, steps=0)
         return self.levels[lev]
 
-    def regrid(self, max_levels, n_error_buf, max_box, interp_type=4, start=0):
-        """Global regrid of every level above ``start`` (Sec. 2.2-2.3):
-        tags of level l grown by n_error_buf and coarsened to blocks on the
-        device (slh_tag_blocks), clustered on the host (slh_regrid_boxes, in
-        block units), then slh_regrid_level(l + 1).  Returns the box lists."""
-        r = self.bf // 2
-        out = []
-        for l in range(start, max_levels - 1):
-            if l not in self.levels:
-                break
-            mask = self.tag_blocks(l, n_error_buf)
-            parent = None
-            if l > 0:
-                parent = [(tuple(v // r for v in lo), tuple((v + 1) // r - 1 for v in hi))
-                          for lo, hi in self.levels[l]["boxes"]]
-            # in block units: blocking factor 2 (one block per mask cell), no further growth
-            blocks = slh_regrid_boxes(mask, 2, 0, 2 * (max_box // self.bf), parent=parent)
-            boxes = [(tuple(v * r for v in lo), tuple((v + 1) * r - 1 for v in hi)) for lo, hi in blocks]
-            self.regrid_level(l + 1, boxes, interp_type)
-            out.append(boxes)
-            if not boxes:
-                break
-        return out
+    def _regrid(self, mode, max_levels, n_error_buf, max_box, interp_type=4, start=0, eps_strong=0.1,
+                eps_weak=0.05, max_local=10):
+        """One slh_regrid call; this side only allocates the buffers the
+        library asks for.  Returns (kind, [(level, boxes) rebuilt, in order],
+        per-level values of slh_regrid's frac output)."""
+        rp = slh_regrid_params(mode, max_levels, start, n_error_buf, max_box, interp_type,
+                               0 if max_local is None else max_local, 0, eps_strong, eps_weak)
+        done = []
 
-    def regrid_local(self, n_error_buf, interp_type=4):
-        """Local regrid of every level (Sec. 2.3): the block masks of the
-        current levels (slh_tag_blocks), the added blocks from
-        slh_local_regrid_boxes, then slh_regrid_level from the lowest changed
-        level up (copy where the old boxes cover, prolong elsewhere).
+        def alloc(user, lev, boxes, nboxes, total, nvalid, bufs, tags):
+            try:
+                if nboxes == 0:
+                    done.append((lev, None))
+                    return 0
+                bl = [(tuple(boxes[i].lo), tuple(boxes[i].hi)) for i in range(nboxes)]
+                old = self.levels.get(lev)
+                fused = old is not None and old["tags"] is not None
+                nb, nt, tot, nv = self._alloc_level(bl, fused)
+                assert tot == total and nv == nvalid
+                for i in range(SLH_NBUF):
+                    bufs[i] = nb[i].data_ptr() if nb[i] is not None else None
+                tags[0] = nt.data_ptr() if nt is not None else None
+                done.append((lev, dict(boxes=bl, bufs=nb, tags=nt, nvalid=nv, total=tot, steps=0)))
+                return 0
+            except Exception:   # the library reports SLH_ERR_NOMEM
+                return -5
+
+        cb = SLH_LEVEL_ALLOC_FN(alloc)
+        kind = ctypes.c_int32(-1)
+        nl = len(self.levels)
+        frac = (ctypes.c_double * max(1, nl))()
+        st = lib().slh_regrid(self.h, ctypes.byref(rp), cb, None, ctypes.byref(kind), frac)
+        # the levels rebuilt before a failure stay in place: keep their buffers
+        for lev, info in done:
+            if info is None:
+                for l in list(self.levels):
+                    if l >= lev:
+                        del self.levels[l]
+            else:
+                self.levels[lev] = info
+        _check(st)
+        return kind.value, [(lev, info["boxes"] if info else []) for lev, info in done], list(frac[:nl])
+
+    def regrid(self, max_levels, n_error_buf, max_box, interp_type=4, start=0):
+        """Global regrid of every level above ``start`` (Sec. 2.2-2.3, one
+        slh_regrid call).  Returns the new box lists in order."""
+        _, lists, _ = self._regrid(SLH_REGRID_GLOBAL, max_levels, n_error_buf, max_box, interp_type, start)
+        return [b for _, b in lists]
+
+    def regrid_local(self, n_error_buf, interp_type=4, max_box=None):
+        """Local regrid of every level (Sec. 2.3, one slh_regrid call).
         Returns the cells added per level."""
-        L = len(self.levels)
-        if L < 2:
-            return [0] * L
-        cur = [list(self.levels[l]["boxes"]) for l in range(L)]
-        masks = [self.tag_blocks(l, n_error_buf) for l in range(L - 1)]
-        new = slh_local_regrid_boxes(cur, self.n0, self.bf, masks)
-        vol = lambda bl: sum((hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1) for lo, hi in bl)
-        added = [vol(new[l]) - vol(cur[l]) for l in range(L)]
-        first = next((l for l in range(1, L) if added[l] > 0), None)
-        if first is not None:
-            for l in range(first, L):
-                self.regrid_level(l, new[l], interp_type)
-        return added
+        mb = max_box if max_box is not None else self.bf
+        _, _, added = self._regrid(SLH_REGRID_LOCAL, len(self.levels), n_error_buf, mb, interp_type)
+        return [int(a) for a in added]
 
     def regrid_auto(self, max_levels, n_error_buf, max_box, interp_type=4, eps_strong=0.1, eps_weak=0.05,
-                    max_local=None):
-        """Local regrids with the paper's fallback (Sec. 2.3): the volume each
-        level gained by local regrids since the last global regrid, as a
-        fraction of its volume then, is tracked; once some level reaches
-        eps_strong (or after max_local local regrids) the next regrid is a
-        global one, from the lowest level whose fraction reached eps_weak.
-        Returns ("global" | "local", per-level info)."""
-        st = getattr(self, "_auto", None)
-        L = len(self.levels)
-        if st is None or len(st["base"]) != L:
-            st = self._auto = {"base": [max(1, self.levels[l]["nvalid"]) for l in range(L)], "added": [0] * L,
-                               "count": 0, "pending": None}
-        if st["pending"] is not None or L < max_levels:
-            start = st["pending"] if st["pending"] is not None else 0
-            boxes = self.regrid(max_levels, n_error_buf, max_box, interp_type, start=start)
-            self._auto = None
-            return "global", boxes
-        added = self.regrid_local(n_error_buf, interp_type)
-        st["count"] += 1
-        for l in range(L):
-            st["added"][l] += added[l]
-        frac = [st["added"][l] / st["base"][l] for l in range(L)]
-        if any(f >= eps_strong for f in frac) or (max_local is not None and st["count"] >= max_local):
-            weak = [l for l in range(1, L) if frac[l] >= eps_weak]
-            st["pending"] = (min(weak) - 1) if weak else 0
+                    max_local=10):
+        """Local regrids with the paper's fallback to a global one (Sec. 2.3,
+        decided by the library).  Returns ("global", box lists) or ("local",
+        per-level added-volume fractions)."""
+        kind, lists, frac = self._regrid(SLH_REGRID_AUTO, max_levels, n_error_buf, max_box, interp_type,
+                                         eps_strong=eps_strong, eps_weak=eps_weak, max_local=max_local)
+        if kind == SLH_REGRID_GLOBAL:
+            return "global", [b for _, b in lists]
         return "local", frac
 
     def set_state(self, lev, dense):
@@ -459,6 +470,14 @@ class Hierarchy:
         n = self.ncomp * self.levels[lev]["nvalid"]
         out = np.empty(n, dtype=self.np_dtype)
         _check(lib().slh_get_state(self.h, lev, ctypes.c_void_p(out.ctypes.data), 1))
+        return out
+
+    def get_state_device(self, lev):
+        """The level's valid cells in the dense layout, as a CUDA tensor
+        (device-to-device copy on the library's stream)."""
+        out = self.torch.empty(self.ncomp * self.levels[lev]["nvalid"], dtype=self.dtype, device=self.device)
+        _check(lib().slh_get_state(self.h, lev, ctypes.c_void_p(out.data_ptr()), 0))
+        self.sync()
         return out
 
     def set_eta(self, eta):

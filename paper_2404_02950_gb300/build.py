@@ -22,7 +22,7 @@ LIB = os.path.join(OUT_DIR, "libslh.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_SRCS = ["api.cu", "stage.cu", "stage_rkn.cu", "gw.cu", "ghost.cu", "tee.cu", "spectrum.cu", "ko.cu", "diag.cu", "noalloc.cu"]
-CXX_SRCS = ["regrid.cpp"]
+CXX_SRCS = ["regrid.cpp", "regrid_policy.cpp"]
 
 
 def _nvcc():

@@ -3,6 +3,7 @@
 // coarse step (Sec. 2.1, Fig. 2) with optional CUDA-graph replay, and the
 // synchronising diagnostics (tags, energy, regrid block mask).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -92,6 +93,16 @@ void prof_begin(slh_ctx* c, int kind, double bytes) {
 void prof_end(slh_ctx* c) {
   if (!c->prof || c->prof_open.empty()) return;
   cudaEventRecord(c->prof_open.back().b, c->stream);
+}
+
+static double host_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+HostPhase::HostPhase(slh_ctx* cc, int k) : c(cc), kind(k), t0(host_ms()) {}
+HostPhase::~HostPhase() {
+  c->prof_ms[kind] += host_ms() - t0;
+  c->prof_n[kind] += 1;
 }
 
 static void free_level(Level& L) {
@@ -1106,6 +1117,7 @@ slh_status slh_advance(slh_ctx* c, double dt0, const slh_eom_params* p, uint32_t
     c->graph_key = key;
   }
   if (!c->graph[parity]) {
+    HostPhase phase(c, SLH_PROF_GRAPH_CAPTURE);   // preparation, capture and instantiation
     // everything a launch sets up lazily (tensor maps, kernel attributes) is
     // prepared before capture: allocations are not allowed while capturing
     for (int l = 0; l < c->nlevels; ++l) {

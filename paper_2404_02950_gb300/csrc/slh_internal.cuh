@@ -175,6 +175,14 @@ struct slh_ctx {
   int regrid_itype = 4;
   uint32_t tag_criteria = SLH_TAG_WINDING;
   double te_crit[4] = {0.0, 0.0, 0.0, 0.0};
+  // regrid policy (Sec. 2.3): each level's volume at the last global regrid
+  // and the volume local regrids added to it since
+  bool rp_valid = false;
+  int rp_nlev = 0;
+  double rp_base[slh::MAX_LEVELS] = {0};
+  double rp_added[slh::MAX_LEVELS] = {0};
+  int rp_count = 0;
+  int rp_pending = -1;
 };
 
 namespace slh {
@@ -244,9 +252,21 @@ slh_status launch_regrid_fill(slh_ctx* c, int lev, Level& fresh, Level* old);
 // profiling helpers
 void prof_begin(slh_ctx* c, int kind, double bytes);
 void prof_end(slh_ctx* c);
+// host wall-clock phase timer: adds its lifetime to kind (always recorded)
+struct HostPhase {
+  slh_ctx* c;
+  int kind;
+  double t0;
+  HostPhase(slh_ctx* cc, int k);
+  ~HostPhase();
+  HostPhase(const HostPhase&) = delete;
+  HostPhase& operator=(const HostPhase&) = delete;
+};
 
 // host regrid
 slh_status regrid_boxes_impl(const uint8_t* tags, const int dims[3], int bf, int nbuf, int max_box,
                              const slh_box* parent, int nparent, std::vector<slh_box>* out);
+slh_status local_regrid_impl(int L, int n0, int bf, const uint8_t* const* masks, const slh_box* boxes,
+                             const int32_t* nboxes, std::vector<std::vector<slh_box>>* out);
 
 }  // namespace slh

@@ -180,3 +180,74 @@ def _oracle_regrid_nbuf(oh, nbuf):
         oamr.regrid_level(oh, l + 1, boxes)
         if not boxes:
             break
+
+
+def _volume(boxes):
+    return sum((hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1) for lo, hi in boxes)
+
+
+def _loop_hierarchy(prec="f64"):
+    y0 = inputs.string_loop(N0, 4.0, 2.0, DX0)
+    h = slh.Hierarchy(N0, DX0, nghost=G, bf=BF, prec=prec, max_levels=MAXLEV)
+    full = [((0, 0, 0), (N0 - 1, N0 - 1, N0 - 1))]
+    h.init_level(0, full)
+    h.set_state(0, slh.dense_from_boxes(y0, full))
+    h.set_eta(ETA0)
+    return h
+
+
+def test_auto_regrid_follows_the_fallback_rule():
+    """slh_regrid in auto mode (the library decides, Sec. 2.3) against the
+    oracle's RegridPolicy fed with the hierarchy's own volumes: the same kind
+    of regrid every time, the same added-volume fractions after each local
+    one, and a global one that leaves the levels below its start level alone."""
+    from oracle import local_regrid as olr
+    p = slh.EOMParams(order=4, interp_type=4)
+    eps_s, eps_w, cap = 0.02, 0.01, 3
+    h = _loop_hierarchy()
+    pol = olr.RegridPolicy(MAXLEV, eps_strong=eps_s, eps_weak=eps_w, max_local=cap)
+    kinds = []
+    for _ in range(9):
+        before = [list(h.levels[l]["boxes"]) for l in sorted(h.levels)]
+        exp_kind, exp_start = pol.next_regrid([_volume(b) for b in before])
+        kind, res = h.regrid_auto(MAXLEV, NBUF, MAX_BOX, eps_strong=eps_s, eps_weak=eps_w, max_local=cap)
+        assert kind == exp_kind, (kinds, kind)
+        after = [list(h.levels[l]["boxes"]) for l in sorted(h.levels)]
+        if kind == "local":
+            assert len(after) == len(before)
+            frac = pol.after_local([_volume(a) - _volume(b) for a, b in zip(after, before)])
+            assert res == frac
+        else:
+            pol.after_global()
+            for l in range(exp_start + 1):
+                assert after[l] == before[l], l
+        kinds.append(kind)
+        for _ in range(2):
+            h.advance(DT0, p)
+    assert kinds.count("local") >= 3 and kinds.count("global") >= 2, kinds
+    h.close()
+
+
+def test_graph_replay_across_regrids_matches_direct():
+    """The coarse-step CUDA graph is captured again after every regrid (the
+    levels' boxes and buffers change): replayed steps across two global and
+    one local regrid equal the direct launches bit for bit."""
+    p = slh.EOMParams(order=4, interp_type=4)
+    ha, hb = _loop_hierarchy(), _loop_hierarchy()
+    for rnd in range(3):
+        if rnd < 2:
+            la = ha.regrid(MAXLEV, NBUF, MAX_BOX)
+            lb = hb.regrid(MAXLEV, NBUF, MAX_BOX)
+        else:
+            la = ha.regrid_local(NBUF)
+            lb = hb.regrid_local(NBUF)
+        assert la == lb
+        for _ in range(3):
+            ha.advance(DT0, p)
+            hb.advance(DT0, p, flags=slh.SLH_USE_GRAPH)
+        assert sorted(ha.levels) == sorted(hb.levels) and len(ha.levels) == MAXLEV
+        for l in sorted(ha.levels):
+            assert ha.levels[l]["boxes"] == hb.levels[l]["boxes"]
+            assert np.array_equal(ha.get_state(l), hb.get_state(l)), (rnd, l)
+    ha.close()
+    hb.close()

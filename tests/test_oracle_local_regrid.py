@@ -141,3 +141,37 @@ def test_worked_case_one_tag_block_at_the_fine_edge():
     assert out[2] == boxes[2] + [((20, 16, 16), (23, 19, 19))]
     assert out[1] == boxes[1] + [((12, 4, 4), (15, 7, 7)), ((12, 8, 4), (15, 11, 7)),
                                  ((12, 4, 8), (15, 7, 11)), ((12, 8, 8), (15, 11, 11))]
+
+
+def test_policy_worked_sequences():
+    """The fallback rule of Sec. 2.3 on hand-worked volume sequences."""
+    # a hierarchy short of its levels is regridded globally from level 0
+    pol = olr.RegridPolicy(3)
+    assert pol.next_regrid([4096, 1000]) == ("global", 0)
+    pol.after_global()
+    # local regrids accumulate dV_l against the volumes at the last global regrid
+    assert pol.next_regrid([4096, 1000, 2000]) == ("local", None)
+    assert pol.after_local([0, 40, 90]) == [0.0, 0.04, 0.045]
+    assert pol.next_regrid([4096, 1040, 2090]) == ("local", None)
+    frac = pol.after_local([0, 70, 10])          # level 1 reaches 11 % >= eps_s
+    assert frac == [0.0, 0.11, 0.05]
+    # both levels reach eps_w: the global regrid starts at level 1 (from level 0's tags)
+    assert pol.next_regrid([4096, 1110, 2100]) == ("global", 0)
+    pol.after_global()
+    # the counters start again from the new volumes
+    assert pol.next_regrid([4096, 1200, 2400]) == ("local", None)
+    frac = pol.after_local([0, 12, 250])          # only level 2 is above eps_w (and eps_s)
+    assert frac == [0.0, 0.01, 250 / 2400]
+    assert pol.next_regrid([4096, 1212, 2650]) == ("global", 1)
+    # the cap on consecutive local regrids, with every fraction small
+    pol = olr.RegridPolicy(2, max_local=3)
+    assert pol.next_regrid([4096, 1000]) == ("local", None)
+    for k in range(3):
+        assert pol.next_regrid([4096, 1000 + k]) == ("local", None)
+        pol.after_local([0, 1])
+    assert pol.next_regrid([4096, 1003]) == ("global", 0)
+    # eps_s is reached on a level while a finer one is below eps_w
+    pol = olr.RegridPolicy(3, eps_strong=0.2, eps_weak=0.1)
+    pol.next_regrid([100, 100, 100])
+    pol.after_local([0, 5, 25])
+    assert pol.next_regrid([100, 105, 125]) == ("global", 1)
