@@ -303,32 +303,39 @@ def _gw_form(slh, torch, n, dist, peak, K=GW_K):
                                "(over the 288 GB of HBM); the largest lattice under 150 GB is 768^3")}
 
 
-AMR_N, AMR_LEVELS, AMR_NBUF, AMR_BF, AMR_MAXBOX, AMR_RELAX, AMR_EVERY = 256, 3, 4, 16, 128, 100, 4
+AMR_N, AMR_LEVELS, AMR_NBUF, AMR_BF, AMR_MAXBOX, AMR_RELAX, AMR_EVERY = 256, 4, 4, 16, 128, 300, 4
 AMR_ORDER = 4
-AMR_WORKLOAD = ("dynamic AMR: 256^3 base + 2 ratio-2 levels, c0-style Gaussian init (k_max=pi/(4dx)) relaxed "
-                "100 coarse steps on the base level, then regridded every 4 coarse steps from string tags "
-                "(buffer 4, blocking factor 16, max box 128), 4th-order Laplacian, quartic prolongation, "
-                "subcycled RK4; regrid time included")
+AMR_K32, AMR_K64 = 16, 4   # coarse steps timed (FP32 batched, FP64 plain)
+AMR_WORKLOAD = ("dynamic AMR: 256^3 base + up to 3 ratio-2 levels, c0-style Gaussian init (k_max=pi/(4dx)) relaxed "
+                f"{AMR_RELAX} coarse steps on the base level, then global regrids every {AMR_EVERY} coarse steps from "
+                "string tags (buffer 4, blocking factor 16, max box 128), 4th-order Laplacian, quartic prolongation, "
+                "subcycled RK4 replayed as one CUDA graph per coarse step (captured again after every regrid); "
+                "regrid and capture time included")
 
 
-def _amr_form(slh, torch, prec, y0_dense, K, n=AMR_N):
-    """Dynamic-AMR timing: coarse steps with global regrids every AMR_EVERY
-    steps.  Returns (cell-updates/s, details)."""
+def _amr_form(slh, torch, prec, y0_dense, K, n=AMR_N, peak=None, relax=AMR_RELAX):
+    """Dynamic-AMR timing: K coarse steps with a global regrid every
+    AMR_EVERY steps, every coarse step replayed from its CUDA graph, then K
+    more steps launched directly with the per-kernel profile on.  Returns
+    (cell-updates/s of the graph pass, details)."""
     h = slh.Hierarchy(n, DX, nghost=AMR_ORDER // 2, bf=AMR_BF, prec=prec, max_levels=AMR_LEVELS)
     h.init_level(0, [((0, 0, 0), (n - 1, n - 1, n - 1))])
     h.set_state(0, y0_dense.astype(h.np_dtype))
     h.set_eta(ETA0)
     p = slh.EOMParams(order=AMR_ORDER, interp_type=4)
-    for _ in range(AMR_RELAX):
-        h.advance(DT, p)
+    for _ in range(relax):
+        h.advance(DT, p, flags=slh.SLH_USE_GRAPH)
     h.sync()
     h.regrid(AMR_LEVELS, AMR_NBUF, AMR_MAXBOX)
     for lev in sorted(h.levels):
         h.autotune(lev, p, reps=2)
+    h.advance(DT, p, flags=slh.SLH_USE_GRAPH)   # first capture outside the timed pass
     h.sync()
-    h.profile(True, True)
+    h.profile(False, True)                       # clears the host-phase counters
+    # pass 1: graph replay, regrids and re-captures included
     updates = 0
     regrid_s = 0.0
+    boxes_seen = []
     t0 = time.perf_counter()
     for k in range(K):
         if k and k % AMR_EVERY == 0:
@@ -336,16 +343,39 @@ def _amr_form(slh, torch, prec, y0_dense, K, n=AMR_N):
             tr = time.perf_counter()
             h.regrid(AMR_LEVELS, AMR_NBUF, AMR_MAXBOX)
             regrid_s += time.perf_counter() - tr
+            boxes_seen.append([len(info["boxes"]) for _, info in sorted(h.levels.items())])
         updates += sum(info["nvalid"] * 2 ** lev for lev, info in h.levels.items())
-        h.advance(DT, p)
+        h.advance(DT, p, flags=slh.SLH_USE_GRAPH)
     h.sync()
     el = time.perf_counter() - t0
+    phases = {name: h.profile_read(kind)[:2] for name, kind in
+              (("regrid_tags", slh.SLH_PROF_REGRID_TAGS), ("regrid_cluster", slh.SLH_PROF_REGRID_CLUSTER),
+               ("regrid_build", slh.SLH_PROF_REGRID_BUILD), ("graph_capture", slh.SLH_PROF_GRAPH_CAPTURE))}
+    cap_ms, ncap = phases["graph_capture"]
+    # pass 2: the same kind of steps launched directly, per-kernel device time
+    h.profile(True, True)
+    upd2 = 0
+    for k in range(K):
+        upd2 += sum(info["nvalid"] * 2 ** lev for lev, info in h.levels.items())
+        h.advance(DT, p)
+    h.sync()
     kinds = {"stage": slh.SLH_PROF_STAGE, "ghost": slh.SLH_PROF_GHOST, "restrict": slh.SLH_PROF_RESTRICT,
              "diag": slh.SLH_PROF_DIAG, "time": slh.SLH_PROF_TIME}
     prof = {k: round(h.profile_read(v)[0], 3) for k, v in kinds.items()}
+    st = h.profile_read(slh.SLH_PROF_STAGE)
     h.profile(False, True)
+    stage_gbs = st[2] / (st[0] / 1e3) / 1e9 if st[0] > 0 else None
     det = {"levels": {str(l): {"boxes": len(info["boxes"]), "cells": info["nvalid"]} for l, info in h.levels.items()},
-           "coarse_steps": K, "seconds": el, "regrid_seconds": regrid_s, "device_ms": prof,
+           "boxes_per_regrid": boxes_seen, "coarse_steps": K, "relax_coarse_steps": relax,
+           "horizon": f"{relax} relaxation + {K} timed + {K} profiled coarse steps (config 3 states 400)",
+           "seconds": el, "regrid_seconds": regrid_s,
+           "regrid_phases_ms": {k: round(v[0], 2) for k, v in phases.items() if k != "graph_capture"},
+           "graph": {"captures": ncap, "capture_ms_total": round(cap_ms, 2),
+                     "capture_ms_per_regrid": round(cap_ms / max(1, ncap), 2),
+                     "step_ms_excl_regrid_capture": round((el - regrid_s - cap_ms / 1e3) / K * 1e3, 3)},
+           "device_ms_direct": prof, "direct_pass_cell_updates": upd2,
+           "stage_kernels": {"achieved_gbs": stage_gbs, "frac": (stage_gbs / peak) if (stage_gbs and peak) else None,
+                             "peak": peak},
            "cell_updates": updates, "eta_end": h.get_eta(0)}
     h.close()
     return updates / el, det
@@ -364,7 +394,7 @@ def run_ours(args, rank, world, local_rank, dist):
     if args.profile_only == "amr":
         # short dynamic-AMR run for profilers (base n^3, K coarse steps)
         ya = inputs.gaussian_field(n, n / 8.0, seed=rank)
-        _amr_form(slh, torch, "f32", slh.dense_from_boxes(ya, [((0, 0, 0), (n - 1,) * 3)]), K, n=n)
+        _amr_form(slh, torch, "f32", slh.dense_from_boxes(ya, [((0, 0, 0), (n - 1,) * 3)]), K, n=n, peak=peak)
         return
     if args.profile_only == "gw":
         _gw_form(slh, torch, n, dist, peak, K=K)
@@ -427,9 +457,9 @@ def run_ours(args, rank, world, local_rank, dist):
         ya = inputs.gaussian_field(AMR_N, AMR_N / 8.0, seed=rank)
         yad = slh.dense_from_boxes(ya, [((0, 0, 0), (AMR_N - 1,) * 3)])
         del ya
-        v32, d32 = _amr_form(slh, torch, "f32", yad, 12)
+        v32, d32 = _amr_form(slh, torch, "f32", yad, AMR_K32, peak=peak)
         torch.cuda.empty_cache()
-        v64, d64 = _amr_form(slh, torch, "f64", yad, 4)
+        v64, d64 = _amr_form(slh, torch, "f64", yad, AMR_K64, peak=peak)
         torch.cuda.empty_cache()
         amr = {"workload": AMR_WORKLOAD, "unit": "cell-updates/s",
                "f32": {"value": world * v32, **d32}, "f64": {"value": world * v64, **d64}}

@@ -169,7 +169,10 @@ extern "C" slh_status slh_regrid(slh_ctx* c, const slh_regrid_params* rp, slh_le
   if (rp->mode == SLH_REGRID_AUTO && !(rp->eps_strong > 0.0 && rp->eps_weak >= 0.0 && rp->max_local >= 0))
     return fail(SLH_ERR_INVALID_ARG, "regrid: eps_strong must be > 0, eps_weak >= 0, max_local >= 0");
   if (c->nlevels < 1) return fail(SLH_ERR_STATE, "regrid: level 0 is not defined");
-  if (c->stale_from < c->nlevels) return fail(SLH_ERR_STATE, "regrid: level %d must be regridded first", c->stale_from);
+  // a global regrid from `start` rebuilds every level above it, so only the
+  // levels up to `start` must be current; the other modes read every level
+  const int need_fresh = rp->mode == SLH_REGRID_GLOBAL ? rp->start : c->nlevels - 1;
+  if (c->stale_from <= need_fresh) return fail(SLH_ERR_STATE, "regrid: level %d must be regridded first", c->stale_from);
   const int L = c->nlevels;
   int k = rp->mode == SLH_REGRID_LOCAL ? SLH_REGRID_LOCAL : SLH_REGRID_GLOBAL;
   slh_regrid_params g = *rp;

@@ -136,6 +136,47 @@ __device__ __forceinline__ void edge_terms(const float (&ar)[N], const float (&a
   }
 }
 
+// FP32 inputs, whether the winding term is nonzero (bit 31 of nz[k] set iff
+// delta != 0), from the sign classes s = bit 31 of fl(v + 0) (set iff v < 0):
+//  - the endpoints share the sign of Im: delta = 0;
+//  - the sign of Im changes and both Re < 0: the edge crosses the negative
+//    real axis (X = Re a Im b - Im a Re b is then > 0 on the way down and
+//    < 0 on the way up), delta != 0;
+//  - the sign of Im changes and both Re >= 0: X <= 0 on the way down and
+//    >= 0 on the way up, delta = 0;
+//  - the signs of Im and of Re both change: the sign of X decides (delta != 0
+//    iff X > 0 on the way down, X < 0 on the way up), by the certificate of
+//    edge_terms or, without one, exactly in FP64.  That last case is rare on
+//    a smooth field (a few per thousand edges), so it runs in a branch that is
+//    taken only by warps that need it.
+template <int N>
+__device__ __forceinline__ void edge_nonzero(const float (&ar)[N], const float (&ai)[N], const float (&br)[N],
+                                             const float (&bi)[N], unsigned (&nz)[N]) {
+  unsigned need[N], any = 0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const unsigned sra = __float_as_uint(__fadd_rn(ar[k], 0.0f)), sia = __float_as_uint(__fadd_rn(ai[k], 0.0f));
+    const unsigned srb = __float_as_uint(__fadd_rn(br[k], 0.0f)), sib = __float_as_uint(__fadd_rn(bi[k], 0.0f));
+    const unsigned dI = sia ^ sib;
+    nz[k] = dI & sra & srb;
+    need[k] = dI & (sra ^ srb);
+    any |= need[k];
+  }
+  if (__any_sync(0xffffffffu, (int)any < 0)) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      if ((int)need[k] >= 0) continue;
+      const unsigned nb = __float_as_uint(__fadd_rn(bi[k], 0.0f));   // set: the way down
+      const float q = __fmul_rn(ai[k], br[k]);
+      const unsigned ns = __float_as_uint(__fmaf_rn(ar[k], bi[k], -q));
+      const int bound = max((int)(__float_as_uint(q) & 0x7FFFFFFFu) - 0x0B800000, 0x00800000);
+      const bool cert = (int)(ns & 0x7FFFFFFFu) > bound;
+      if (cert) nz[k] = (nb & ~ns) | (~nb & ns);              // X > 0 down, X < 0 up
+      else nz[k] = exact_edge_term(ar[k], ai[k], br[k], bi[k]) != 1u ? 0x80000000u : 0u;
+    }
+  }
+}
+
 // shared-memory geometry of one kernel variant (the diagnostics variant runs
 // stage 0 or 1 only, whose pointwise ring holds just the momenta)
 template <typename T, int G, int TX, int TY, int P, bool DIAG>
@@ -191,6 +232,8 @@ __global__ void __launch_bounds__(Geo<T, G, TX, TY, P, DIAG>::NTHREADS, (DIAG &&
   // producer warp (plain variant): consumer warps release each load step on
   // an mbarrier instead of meeting at a CTA barrier per plane
   constexpr bool WS = GE::WS;
+  // diagnostics in bit-sliced form: FP32 fields, rows of 32 cells (one warp)
+  constexpr bool BITS = DIAG && sizeof(T) == 4 && TX == 32;
   constexpr int RD = P + 1;         // "step consumed" barriers
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem);
@@ -624,7 +667,179 @@ __global__ void __launch_bounds__(Geo<T, G, TX, TY, P, DIAG>::NTHREADS, (DIAG &&
         }
       }
     }
-    if (DIAG) {
+    if constexpr (BITS) {
+      // Plaquette windings, bit-sliced (FP32, 32-cell rows: one warp per row).
+      // A plaquette's winding W is the signed sum of its four edge terms, and
+      // a quadrilateral winds at most once around the origin: the angle each
+      // edge turns through is below pi in magnitude, and where the sign of X
+      // is exact (X in FP64 from FP32 values) the half-plane rule counts those
+      // turns (proof by contradiction: two crossings of one sign would chain
+      // the corners' angles into a < a).  So |W| <= 1, and W != 0 exactly
+      // when an odd number of its edges have a nonzero term: the masks are
+      // XORs of "edge nonzero" bits, 32 cells per operation.  Steps, one CTA
+      // barrier apart (software-pipelined over the planes of an item):
+      //  edges(z):      every edge cell of the tile grown by one cell
+      //                 evaluates its z edge of plane z and its x, y edges of
+      //                 plane z+1 (plane z0-1's own x, y edges in the
+      //                 premask step); a warp (one row of 32 cells) packs
+      //                 them with ballots, side columns into words of their
+      //                 own;
+      //  masks(z-2):    warp 0, one lane per owner row -1..TY-1, from the
+      //                 edge words of planes z-2 and z-1;
+      //  words(z-3):    warp 1, one lane per row, the tag word (OR of the 12
+      //                 plaquettes around each cell) from the masks of planes
+      //                 z-3 and z-4, with the pierced-plaquette and tag counts;
+      //  stores(z-4):   every thread stores its cell's tag byte.
+      // Words hold cell x at bit x+1 (x = -1 .. 32).
+      constexpr int NE = (TY + 2) * TX + 2 * (TY + 2);
+      constexpr int SIDEW = (2 * (TY + 2) + 31) / 32;
+      __shared__ unsigned bw[4][3][TY + 2];              // interior edge bits (plane & 3, x/y/z, row + 1)
+      __shared__ unsigned bs[4][3][SIDEW];               // side columns: bit 2 (row + 1) + (x == TX)
+      __shared__ unsigned long long mw[4][3][TY + 1];    // masks (plane & 3, normal z/x/y, owner row + 1)
+      __shared__ unsigned long long tw[2][TY];           // tag words (plane & 1, row)
+      const int lane = tid & 31, warp = tid >> 5;
+      auto row_word = [&](int slot, int dir, int rr) -> unsigned long long {
+        unsigned long long w = (unsigned long long)bw[slot][dir][rr] << 1;
+        const int sl = 2 * rr, sr = 2 * rr + 1;
+        w |= (unsigned long long)((bs[slot][dir][sl >> 5] >> (sl & 31)) & 1u);
+        w |= (unsigned long long)((bs[slot][dir][sr >> 5] >> (sr & 31)) & 1u) << 33;
+        return w;
+      };
+      auto masks = [&](int pm) {
+        if (warp != 0 || lane > TY) return;
+        const int s0 = pm & 3, s1 = (pm + 1) & 3, r = lane;   // owner row r - 1
+        const unsigned long long ex = row_word(s0, 0, r), ey = row_word(s0, 1, r), ez = row_word(s0, 2, r);
+        const unsigned long long exY = row_word(s0, 0, r + 1), ezY = row_word(s0, 2, r + 1);
+        const unsigned long long exZ = row_word(s1, 0, r), eyZ = row_word(s1, 1, r);
+        constexpr unsigned long long OWN = (1ull << (TX + 1)) - 1;   // owners x = -1 .. TX-1
+        // xy: C.ex X.ey Y.ex C.ey;  yz: C.ey Y.ez Z.ey C.ez;  zx: C.ez Z.ex X.ez C.ex
+        mw[pm & 3][0][r] = (ex ^ (ey >> 1) ^ exY ^ ey) & OWN;
+        mw[pm & 3][1][r] = (ey ^ ezY ^ eyZ ^ ez) & OWN;
+        mw[pm & 3][2][r] = (ez ^ exZ ^ (ez >> 1) ^ ex) & OWN;
+      };
+      auto words = [&](int pt) {
+        if (warp != 1 || lane >= TY) return;
+        const int a = pt & 3, b = (pt - 1) & 3, r = lane + 1, rm = lane;   // owner rows y and y-1
+        const unsigned long long xy0 = mw[a][0][r], xy1 = mw[a][0][rm], zx0 = mw[a][2][r], zx1 = mw[b][2][r];
+        const unsigned long long tg = xy0 | (xy0 << 1) | xy1 | (xy1 << 1) | mw[a][1][r] | mw[a][1][rm] | mw[b][1][r] |
+                                      mw[b][1][rm] | zx0 | (zx0 << 1) | zx1 | (zx1 << 1);
+        tw[pt & 1][lane] = tg;
+        const int yv = cc.y0 + lane;
+        if (yv >= B.n[1]) return;
+        const int nx = min(TX, B.n[0] - cc.x0);
+        unsigned long long valid = ((1ull << nx) - 1) << 1;
+        if (A.tags != nullptr) n_tagged += __popcll(tg & valid);
+        if (A.epart != nullptr) {
+          if (A.covered != nullptr) {
+            // owners in blocks covered by the finer level do not count
+            const int gy = (B.lo[1] + yv) >> A.cov_shift, gz = (B.lo[2] + pt) >> A.cov_shift;
+            const uint8_t* crow = A.covered + ((long long)gz * A.cov_nb + gy) * A.cov_nb;
+            for (int xx = 0; xx < nx;) {
+              const int gx = (B.lo[0] + cc.x0 + xx) >> A.cov_shift;
+              const int xe = min(nx, ((gx + 1) << A.cov_shift) - B.lo[0] - cc.x0);   // end of this block
+              if (crow[gx]) valid &= ~((((1ull << (xe - xx)) - 1)) << (xx + 1));
+              xx = xe;
+            }
+          }
+          n_pierced += __popcll(mw[a][0][r] & valid) + __popcll(mw[a][1][r] & valid) + __popcll(mw[a][2][r] & valid);
+        }
+      };
+      auto stores = [&](int ps) {
+        if (A.tags == nullptr || !(x < B.n[0] && y < B.n[1])) return;
+        A.tags[B.voff + ((long long)ps * B.n[1] + y) * B.n[0] + x] = (uint8_t)((tw[ps & 1][ty] >> (tx + 1)) & 1u);
+      };
+      if (compute || premask) {
+#pragma unroll
+        for (int k = 0; k < NEK; ++k) {
+          if (k * TXY >= NE) break;   // uniform over the CTA
+          const int j = k * TXY + tid;
+          const bool act = j < NE;
+          const int ey = e_y[k];
+          auto SE = [&](int c, int dx, int dy, int dz) -> T { return psi[plb[dz + G] + c * PLANE + e_off[k] + dy * SXL + dx]; };
+          // every lane runs the edge tests (they vote); lanes past the last
+          // edge cell read nothing and test zeros
+          T r0 = 0, i0 = 0, rz = 0, iz = 0, xr = 0, xi = 0, yr = 0, yi = 0;
+          if (act) {
+            r0 = premask ? SE(0, 0, 0, 0) : c_r[k];   // plane z0-1 from the ring in the premask step
+            i0 = premask ? SE(1, 0, 0, 0) : c_i[k];
+            rz = SE(0, 0, 0, 1);
+            iz = SE(1, 0, 0, 1);
+            xr = SE(0, 1, 0, 1);
+            xi = SE(1, 1, 0, 1);
+            yr = ey < TY ? SE(0, 0, 1, 1) : rz;
+            yi = ey < TY ? SE(1, 0, 1, 1) : iz;
+          }
+          unsigned px = 0, py = 0;
+          if (premask) {   // uniform over the CTA: the x and y edges of plane z0-1
+            T br2[2] = {0, 0}, bi2[2] = {0, 0};
+            if (act) {
+              br2[0] = SE(0, 1, 0, 0);
+              bi2[0] = SE(1, 1, 0, 0);
+              br2[1] = ey < TY ? SE(0, 0, 1, 0) : r0;
+              bi2[1] = ey < TY ? SE(1, 0, 1, 0) : i0;
+            }
+            const T ar2[2] = {r0, r0}, ai2[2] = {i0, i0};
+            unsigned nz2[2];
+            edge_nonzero<2>(ar2, ai2, br2, bi2, nz2);
+            px = __ballot_sync(0xffffffffu, act && (int)nz2[0] < 0);
+            py = __ballot_sync(0xffffffffu, act && (int)nz2[1] < 0);
+          }
+          // the z edge of plane z, the x and y edges of plane z+1
+          const T ar3[3] = {r0, rz, rz}, ai3[3] = {i0, iz, iz}, br3[3] = {rz, xr, yr}, bi3[3] = {iz, xi, yi};
+          unsigned nz3[3];
+          edge_nonzero<3>(ar3, ai3, br3, bi3, nz3);
+          const unsigned nzz = nz3[0], nzx = nz3[1], nzy = nz3[2];
+          c_r[k] = rz;
+          c_i[k] = iz;
+          const unsigned bz = __ballot_sync(0xffffffffu, act && (int)nzz < 0);
+          const unsigned bx = __ballot_sync(0xffffffffu, act && (int)nzx < 0);
+          const unsigned by = __ballot_sync(0xffffffffu, act && (int)nzy < 0);
+          if (lane == 0) {
+            if (k * TXY + (warp << 5) < (TY + 2) * TX) {
+              const int rr = ey + 1;   // one row per warp
+              if (premask) {
+                bw[z & 3][0][rr] = px;
+                bw[z & 3][1][rr] = py;
+              }
+              bw[z & 3][2][rr] = bz;
+              bw[(z + 1) & 3][0][rr] = bx;
+              bw[(z + 1) & 3][1][rr] = by;
+            } else {
+              const int sw = (k * TXY + (warp << 5) - (TY + 2) * TX) >> 5;
+              if (sw < SIDEW) {
+                if (premask) {
+                  bs[z & 3][0][sw] = px;
+                  bs[z & 3][1][sw] = py;
+                }
+                bs[z & 3][2][sw] = bz;
+                bs[(z + 1) & 3][0][sw] = bx;
+                bs[(z + 1) & 3][1][sw] = by;
+              }
+            }
+          }
+        }
+      }
+      // planes z-2, z-3, z-4: their inputs were written before the last barrier
+      if (compute && z - 2 >= cc.z0 - 1) masks(z - 2);
+      if (compute && z - 3 >= cc.z0) words(z - 3);
+      if (compute && z - 4 >= cc.z0) stores(z - 4);
+      if (cc.valid && z == cc.z1 - 1) {   // the item's last plane: drain (uniform over the CTA)
+        __syncthreads();
+        if (z - 1 >= cc.z0 - 1) masks(z - 1);
+        if (z - 2 >= cc.z0) words(z - 2);
+        if (z - 3 >= cc.z0) stores(z - 3);
+        __syncthreads();
+        masks(z);
+        if (z - 1 >= cc.z0) words(z - 1);
+        if (z - 2 >= cc.z0) stores(z - 2);
+        __syncthreads();
+        words(z);
+        if (z - 1 >= cc.z0) stores(z - 1);
+        __syncthreads();
+        stores(z);
+      }
+    }
+    if constexpr (DIAG && !BITS) {
       // Plaquette windings.  The edge term is antisymmetric (delta(b,a) =
       // -delta(a,b)), so a plaquette's winding is the signed sum of the edges
       // leaving its corners along +x, +y, +z.  Three steps, software-pipelined
