@@ -223,7 +223,7 @@ __device__ __forceinline__ void cursor_next(Cursor& c, const int4* items, const 
 }
 
 template <typename T, int G, int TX, int TY, int P, bool DIAG, bool RKN>
-__global__ void __launch_bounds__(Geo<T, G, TX, TY, P, DIAG>::NTHREADS, (DIAG && TX * TY <= 256) ? 2 : 1)
+__global__ void __launch_bounds__(Geo<T, G, TX, TY, P, DIAG>::NTHREADS, (DIAG && TX * TY <= 256) ? (sizeof(T) == 4 ? 3 : 2) : 1)
     stage_kernel(const StageArgs<T> A) {
   using GE = Geo<T, G, TX, TY, P, DIAG>;
   constexpr int SXL = GE::SXL, SY = GE::SY, RPSI = GE::RPSI, RPW = GE::RPW;
@@ -751,7 +751,8 @@ __global__ void __launch_bounds__(Geo<T, G, TX, TY, P, DIAG>::NTHREADS, (DIAG &&
       if (compute || premask) {
 #pragma unroll
         for (int k = 0; k < NEK; ++k) {
-          if (k * TXY >= NE) break;   // uniform over the CTA
+          if (k * TXY >= NE) break;                  // uniform over the CTA
+          if (k * TXY + (warp << 5) >= NE) continue;   // uniform over the warp: no edge cell left
           const int j = k * TXY + tid;
           const bool act = j < NE;
           const int ey = e_y[k];
