@@ -68,6 +68,17 @@ typedef int32_t slh_status;
 #define SLH_F32_KAHAN 2  /* FP32 fields and arithmetic, Kahan-compensated final
                             RK update; FP64 only for eta, its coefficients and
                             the reductions */
+#define SLH_F32_BF16 3   /* 16 fields: psi, Pi in FP32, the tensor fields u_ij,
+                            v_ij stored in BF16 (rounded to nearest even),
+                            FP32 arithmetic and accumulation; a cell holds 10
+                            slots of 4 bytes (SLH_SLOTS_BF16); three level
+                            buffers (SLH_BUF_Y, YA, YB; D and C stay NULL);
+                            integrator SSPRK3 (type 10 or 3) only */
+#define SLH_SLOTS_BF16 10 /* slots of an SLH_F32_BF16 cell: psi1, psi2, Pi1, Pi2
+                            in FP32, then the BF16 pairs (u_xx, u_yy),
+                            (u_zz, u_xy), (u_xz, u_yz), (v_xx, v_yy),
+                            (v_zz, v_xy), (v_xz, v_yz), the first of each pair
+                            in the low 16 bits */
 
 /* Buffers of one level (device pointers handed to slh_init_level). */
 #define SLH_BUF_Y 0      /* state y_n (rotates with SLH_BUF_YB every step) */
@@ -182,8 +193,9 @@ slh_status slh_create(slh_ctx** ctx, int32_t n0, double dx0, int32_t nghost,
 /* Release the metadata of ctx (field buffers stay with the caller). */
 void slh_destroy(slh_ctx* ctx);
 
-/* Element counts of one level buffer of nfields (4 or 16) fields for the
- * given boxes, without a context.  box_offsets (nboxes entries, may be NULL) receives each box's
+/* Element counts of one level buffer of nfields (4 or 16) fields, or of
+ * SLH_SLOTS_BF16 slots (a 16-field SLH_F32_BF16 level: elements of 4 bytes),
+ * for the given boxes, without a context.  box_offsets (nboxes entries, may be NULL) receives each box's
  * element offset; box_geom (4*nboxes, may be NULL) receives pitch (x row
  * length incl. padding), padded ny, padded nz and the component stride in
  * elements.  The valid cell (x,y,z) of box b, component c, sits at
@@ -227,12 +239,20 @@ slh_status slh_regrid_level(slh_ctx* ctx, int32_t lev, const slh_box* boxes, int
                             void* const* bufs, uint8_t* tags_dev, int32_t interp_type);
 
 /* Copy the fields (4 or 16) of level lev from / to a dense valid-cell array
- * ([box][comp][z][y][x], context precision).  src/dst on the host
+ * ([box][comp][z][y][x], context precision; for SLH_F32_BF16 the 10 slots
+ * of 4 bytes, [box][slot][z][y][x]).  src/dst on the host
  * (is_host = 1, ideally pinned) or the device.  slh_set_state also sets the
  * level's previous state equal to it and zeroes the Kahan compensation.
  * slh_get_state to host synchronises.  Errors: INVALID_ARG, STATE, CUDA. */
 slh_status slh_set_state(slh_ctx* ctx, int32_t lev, const void* src, int32_t src_is_host);
 slh_status slh_get_state(slh_ctx* ctx, int32_t lev, void* dst, int32_t dst_is_host);
+
+/* Which of the level's buffers (SLH_BUF_*) currently hold its state,
+ * its previous state and the stage scratch: roles[0..2].  Classic RK4 and
+ * the Nystrom methods swap the first two every step; SSPRK3 rotates all
+ * three (state <- scratch, previous <- state, scratch <- previous).
+ * Errors: INVALID_ARG, STATE. */
+slh_status slh_level_roles(slh_ctx* ctx, int32_t lev, int32_t roles[3]);
 
 /* Set the conformal time eta of every level (kept in FP64 on the device). */
 slh_status slh_set_eta(slh_ctx* ctx, double eta);

@@ -25,6 +25,8 @@ LIB_PATH = os.path.join(_HERE, "lib", "libslh.so")
 SLH_OK = 0
 SLH_F64 = 0
 SLH_F32_KAHAN = 2
+SLH_F32_BF16 = 3
+SLH_SLOTS_BF16 = 10   # 4 FP32 slots (psi, Pi) + 6 slots of BF16 pairs (u_ij, v_ij)
 SLH_NBUF = 5
 SLH_BUF_Y, SLH_BUF_YA, SLH_BUF_YB, SLH_BUF_D, SLH_BUF_C = range(5)
 SLH_FUSE_TAG = 1
@@ -51,7 +53,7 @@ ABI_SYMBOLS = (
     "slh_autotune", "slh_autotune_diag",
     "slh_energy_noalloc", "slh_regrid_level", "slh_selftest_wait_timeout",
     "slh_set_tagging", "slh_shadow_init", "slh_shadow_compare", "slh_tee_tags", "slh_gw_spectrum",
-    "slh_local_regrid_boxes", "slh_regrid",
+    "slh_local_regrid_boxes", "slh_regrid", "slh_level_roles",
 )
 
 
@@ -155,6 +157,7 @@ def lib():
         "slh_gw_spectrum": (i32, [vp, i32, P(i64), P(dbl), i32, P(i32)]),
         "slh_local_regrid_boxes": (i32, [i32, i32, i32, P(vp), P(slh_box), P(i32), P(slh_box), i32, P(i32)]),
         "slh_regrid": (i32, [vp, P(slh_regrid_params), SLH_LEVEL_ALLOC_FN, vp, P(i32), P(dbl)]),
+        "slh_level_roles": (i32, [vp, i32, P(i32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -273,6 +276,39 @@ def slh_energy_noalloc(fields_dev, n, dx, eta, params: EOMParams, out_dev, strea
                                         ctypes.c_void_p(st.cuda_stream)))
 
 
+def _bf16_bits(a):
+    """float32 -> BF16 bit patterns (uint32, low 16 bits), rounded to
+    nearest even (finite values)."""
+    u = np.ascontiguousarray(np.asarray(a, dtype=np.float32)).view(np.uint32).astype(np.uint64)
+    return ((u + 0x7FFF + ((u >> 16) & 1)) >> 16).astype(np.uint32)
+
+
+def pack_bf16_fields(fields):
+    """The 16 fields (psi1, psi2, Pi1, Pi2, u_xx..u_yz, v_xx..v_yz) as the
+    10 slots of an SLH_F32_BF16 level: the scalar fields in FP32, the tensor
+    fields rounded to BF16 and paired, (u_xx, u_yy), (u_zz, u_xy), (u_xz, u_yz),
+    (v_xx, v_yy), ... with the first field of a pair in the low half.  Returns
+    float32 arrays (the pairs as raw bit patterns)."""
+    assert len(fields) == 16
+    out = [np.asarray(f, dtype=np.float32) for f in fields[:4]]
+    for k in range(4, 16, 2):
+        w = _bf16_bits(fields[k]) | (_bf16_bits(fields[k + 1]) << 16)
+        out.append(w.astype(np.uint32).view(np.float32))
+    return out
+
+
+def unpack_bf16_fields(slots):
+    """Inverse of pack_bf16_fields: the 16 fields as float32 arrays (the
+    tensor fields widened exactly from BF16)."""
+    assert len(slots) == SLH_SLOTS_BF16
+    out = [np.asarray(s, dtype=np.float32) for s in slots[:4]]
+    for s in slots[4:]:
+        w = np.ascontiguousarray(np.asarray(s, dtype=np.float32)).view(np.uint32)
+        out.append((w << 16).astype(np.uint32).view(np.float32))
+        out.append((w & 0xFFFF0000).astype(np.uint32).view(np.float32))
+    return out
+
+
 def dense_from_boxes(fields, boxes):
     """Pack the [z, y, x] domain arrays of the fields (4 or 16) into the
     dense valid-cell layout [box][comp][z][y][x] (host numpy)."""
@@ -306,13 +342,17 @@ class Hierarchy:
         import torch
         self.torch = torch
         self.device = torch.device(device)
-        self.prec = SLH_F64 if prec == "f64" else SLH_F32_KAHAN
+        self.prec = {"f64": SLH_F64, "f32": SLH_F32_KAHAN, "f32bf16": SLH_F32_BF16}[prec]
+        if self.prec == SLH_F32_BF16 and not gw:
+            raise ValueError("BF16 storage is for the tensor fields: prec='f32bf16' needs gw=True")
         self.dtype = torch.float64 if self.prec == SLH_F64 else torch.float32
         self.np_dtype = np.float64 if self.prec == SLH_F64 else np.float32
         # a stream of its own: CUDA graphs cannot capture the legacy default stream
         self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
         self.nghost, self.bf, self.n0, self.dx0 = nghost, bf, n0, dx0
         self.ncomp = NFIELDS_GW if gw else NFIELDS
+        # storage slots per cell (elements of the buffers' dtype)
+        self.nslots = SLH_SLOTS_BF16 if self.prec == SLH_F32_BF16 else self.ncomp
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check(lib().slh_create(ctypes.byref(h), n0, dx0, nghost, bf, self.prec, max_levels, self.ncomp,
@@ -331,15 +371,18 @@ class Hierarchy:
         except Exception:
             pass
 
+    def _needs(self, i):
+        """Whether level buffer i is allocated: three for BF16 storage
+        (SSPRK3), no Kahan compensation in FP64."""
+        if self.prec == SLH_F32_BF16:
+            return i in (SLH_BUF_Y, SLH_BUF_YA, SLH_BUF_YB)
+        return not (i == SLH_BUF_C and self.prec == SLH_F64)
+
     def init_level(self, lev, boxes, fused_tags=False):
         torch = self.torch
-        _, geom, total, nvalid = slh_level_layout(self.nghost, boxes, self.ncomp)
-        bufs = []
-        for i in range(SLH_NBUF):
-            if i == SLH_BUF_C and self.prec == SLH_F64:
-                bufs.append(None)
-            else:
-                bufs.append(torch.empty(int(total), dtype=self.dtype, device=self.device))
+        _, geom, total, nvalid = slh_level_layout(self.nghost, boxes, self.nslots)
+        bufs = [torch.empty(int(total), dtype=self.dtype, device=self.device) if self._needs(i) else None
+                for i in range(SLH_NBUF)]
         tags = torch.zeros(int(nvalid), dtype=torch.uint8, device=self.device) if fused_tags else None
         ptrs = (ctypes.c_void_p * SLH_NBUF)(*[b.data_ptr() if b is not None else None for b in bufs])
         _check(lib().slh_init_level(self.h, lev, _boxes(boxes), len(boxes), ptrs,
@@ -351,17 +394,22 @@ class Hierarchy:
                                 steps=0)
         return self.levels[lev]
 
+    def roles(self, lev):
+        """(state, previous state, stage scratch) buffer indices of the level
+        (they rotate from step to step)."""
+        r = (ctypes.c_int32 * 3)()
+        _check(lib().slh_level_roles(self.h, lev, r))
+        return tuple(r)
+
     def state_buffer(self, lev):
-        """The torch buffer currently holding the level's state (the state
-        and previous-state buffers swap roles after every RK step)."""
-        info = self.levels[lev]
-        return info["bufs"][SLH_BUF_Y if info["steps"] % 2 == 0 else SLH_BUF_YB]
+        """The torch buffer currently holding the level's state."""
+        return self.levels[lev]["bufs"][self.roles(lev)[0]]
 
     def _alloc_level(self, boxes, fused_tags):
         torch = self.torch
-        _, geom, total, nvalid = slh_level_layout(self.nghost, boxes, self.ncomp)
-        bufs = [None if (i == SLH_BUF_C and self.prec == SLH_F64)
-                else torch.empty(int(total), dtype=self.dtype, device=self.device) for i in range(SLH_NBUF)]
+        _, geom, total, nvalid = slh_level_layout(self.nghost, boxes, self.nslots)
+        bufs = [torch.empty(int(total), dtype=self.dtype, device=self.device) if self._needs(i) else None
+                for i in range(SLH_NBUF)]
         tags = torch.zeros(int(nvalid), dtype=torch.uint8, device=self.device) if fused_tags else None
         return bufs, tags, int(total), int(nvalid)
 
@@ -467,7 +515,7 @@ class Hierarchy:
             self.sync()
 
     def get_state(self, lev):
-        n = self.ncomp * self.levels[lev]["nvalid"]
+        n = self.nslots * self.levels[lev]["nvalid"]
         out = np.empty(n, dtype=self.np_dtype)
         _check(lib().slh_get_state(self.h, lev, ctypes.c_void_p(out.ctypes.data), 1))
         return out
@@ -475,7 +523,7 @@ class Hierarchy:
     def get_state_device(self, lev):
         """The level's valid cells in the dense layout, as a CUDA tensor
         (device-to-device copy on the library's stream)."""
-        out = self.torch.empty(self.ncomp * self.levels[lev]["nvalid"], dtype=self.dtype, device=self.device)
+        out = self.torch.empty(self.nslots * self.levels[lev]["nvalid"], dtype=self.dtype, device=self.device)
         _check(lib().slh_get_state(self.h, lev, ctypes.c_void_p(out.data_ptr()), 0))
         self.sync()
         return out

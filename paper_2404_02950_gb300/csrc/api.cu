@@ -124,12 +124,8 @@ static void free_level(Level& L) {
 }
 
 static void drop_graphs(slh_ctx* c) {
-  for (int i = 0; i < 2; ++i)
-    if (c->graph[i]) {
-      cudaGraphExecDestroy(c->graph[i]);
-      c->graph[i] = nullptr;
-    }
-  c->graph_key = 0;
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
 }
 
 template <typename V>
@@ -150,6 +146,7 @@ static int ilog2(int v) {
 }
 
 static size_t elem_size(const slh_ctx* c) { return c->prec == SLH_F64 ? 8 : 4; }
+static bool bf16(const slh_ctx* c) { return c->prec == SLH_F32_BF16; }
 
 // fields whose ghost cells are filled: psi1, psi2 (+ the six u_ij)
 static int ghost_fields(const slh_ctx* c) { return c->ncomp == NCOMP_GW ? 8 : 2; }
@@ -210,7 +207,8 @@ const char* slh_last_error(void) { return g_last_error.c_str(); }
 slh_status slh_level_layout(int32_t nghost, int32_t nfields, const slh_box* boxes, int32_t nboxes,
                             int64_t* box_offsets, int64_t* box_geom, int64_t* total_elems, int64_t* nvalid) {
   if (!boxes || nboxes < 0 || nghost < 1 || nghost > 4) return fail(SLH_ERR_INVALID_ARG, "layout: bad arguments");
-  if (nfields != NCOMP && nfields != NCOMP_GW) return fail(SLH_ERR_INVALID_ARG, "layout: nfields must be 4 or 16");
+  if (nfields != NCOMP && nfields != NCOMP_GW && nfields != SLH_SLOTS_BF16)
+    return fail(SLH_ERR_INVALID_ARG, "layout: nfields must be 4, 16 or %d (BF16 tensor slots)", SLH_SLOTS_BF16);
   Layout lay;
   std::string why;
   if (!make_layout(nghost, nfields, boxes, nboxes, &lay, &why))
@@ -236,7 +234,10 @@ slh_status slh_create(slh_ctx** out, int32_t n0, double dx0, int32_t nghost, int
   if (nghost < 1 || nghost > 4) return fail(SLH_ERR_INVALID_ARG, "create: nghost must be in [1,4]");
   if (bf < 2 || (bf & (bf - 1))) return fail(SLH_ERR_INVALID_ARG, "create: blocking factor must be a power of two >= 2");
   if (n0 < bf || n0 % bf) return fail(SLH_ERR_INVALID_ARG, "create: n0 must be a positive multiple of the blocking factor");
-  if (prec != SLH_F64 && prec != SLH_F32_KAHAN) return fail(SLH_ERR_INVALID_ARG, "create: unknown precision %d", prec);
+  if (prec != SLH_F64 && prec != SLH_F32_KAHAN && prec != SLH_F32_BF16)
+    return fail(SLH_ERR_INVALID_ARG, "create: unknown precision %d", prec);
+  if (prec == SLH_F32_BF16 && nfields != NCOMP_GW)
+    return fail(SLH_ERR_INVALID_ARG, "create: SLH_F32_BF16 stores the 16-field state (nfields 16)");
   if (max_levels < 1 || max_levels > MAX_LEVELS) return fail(SLH_ERR_INVALID_ARG, "create: max_levels must be in [1,8]");
   if (!(dx0 > 0.0)) return fail(SLH_ERR_INVALID_ARG, "create: dx0 must be positive");
   if (nfields != NCOMP && nfields != NCOMP_GW) return fail(SLH_ERR_INVALID_ARG, "create: nfields must be 4 or 16");
@@ -248,6 +249,7 @@ slh_status slh_create(slh_ctx** out, int32_t n0, double dx0, int32_t nghost, int
   c->bf = bf;
   c->prec = prec;
   c->ncomp = nfields;
+  c->nslots = prec == SLH_F32_BF16 ? SLH_SLOTS_BF16 : nfields;
   c->max_levels = max_levels;
   c->stream = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaGetDevice(&c->device);
@@ -292,7 +294,10 @@ namespace slh {
 static slh_status validate_boxes(slh_ctx* c, int lev, const slh_box* boxes, int nboxes, void* const* bufs,
                                  std::vector<int>* bmap_out, const char* who) {
   for (int i = 0; i < SLH_NBUF; ++i) {
-    const bool need = (i != SLH_BUF_C) || c->prec == SLH_F32_KAHAN;
+    // SLH_F32_BF16 levels hold three buffers (SSPRK3); the others need D,
+    // and the Kahan compensation with SLH_F32_KAHAN
+    const bool need = bf16(c) ? (i == SLH_BUF_Y || i == SLH_BUF_YA || i == SLH_BUF_YB)
+                              : ((i != SLH_BUF_C) || c->prec == SLH_F32_KAHAN);
     if (need && !bufs[i]) return fail(SLH_ERR_INVALID_ARG, "%s: buffer %d is null", who, i);
   }
   const int ndom = c->n0 << lev;
@@ -600,13 +605,15 @@ static slh_status build_level(slh_ctx* c, int lev, Level& L, const slh_box* boxe
   L.dx = c->dx0 / (double)(1 << lev);
   L.boxes.assign(boxes, boxes + nboxes);
   std::string why;
-  if (!make_layout(c->g, c->ncomp, boxes, nboxes, &L.lay, &why))
+  if (!make_layout(c->g, c->nslots, boxes, nboxes, &L.lay, &why))
     return fail(SLH_ERR_INVALID_ARG, "level %d: %s", lev, why.c_str());
   for (int i = 0; i < SLH_NBUF; ++i) L.buf[i] = bufs[i];
   if (c->prec != SLH_F32_KAHAN) L.buf[SLH_BUF_C] = nullptr;
+  if (bf16(c)) L.buf[SLH_BUF_D] = nullptr;
   L.tags_dev = tags_dev;
   L.role_y = SLH_BUF_Y;
   L.role_prev = SLH_BUF_YB;
+  L.role_s = SLH_BUF_YA;
   slh_status st;
   if ((st = upload(&L.d_boxes, L.lay.boxes)) != SLH_OK) return st;
   if ((st = upload(&L.d_bmap, bmap)) != SLH_OK) return st;
@@ -786,11 +793,11 @@ static slh_status copy_state(slh_ctx* c, int lev, void* host_or_dev, bool to_dev
   for (size_t b = 0; b < L.lay.boxes.size(); ++b) {
     const BoxDev& B = L.lay.boxes[b];
     const long long vol = (long long)B.n[0] * B.n[1] * B.n[2];
-    for (int comp = 0; comp < c->ncomp; ++comp) {
+    for (int comp = 0; comp < c->nslots; ++comp) {
       cudaMemcpy3DParms p;
       memset(&p, 0, sizeof(p));
       cudaPitchedPtr dptr =
-          make_cudaPitchedPtr(dense + (size_t)(c->ncomp * B.voff + comp * vol) * s, B.n[0] * s, B.n[0], B.n[1]);
+          make_cudaPitchedPtr(dense + (size_t)(c->nslots * B.voff + comp * vol) * s, B.n[0] * s, B.n[0], B.n[1]);
       cudaPitchedPtr bptr = make_cudaPitchedPtr(buf + (size_t)(B.off + comp * B.cs) * s, (size_t)B.pitch * s, B.pitch, B.pny);
       if (to_device) {
         p.srcPtr = dptr;
@@ -847,6 +854,15 @@ slh_status slh_set_eta(slh_ctx* c, double eta) {
   return SLH_OK;
 }
 
+slh_status slh_level_roles(slh_ctx* c, int32_t lev, int32_t roles[3]) {
+  if (!c || !roles) return fail(SLH_ERR_INVALID_ARG, "level_roles: null argument");
+  if (lev < 0 || lev >= c->nlevels) return fail(SLH_ERR_STATE, "level_roles: level %d not defined", lev);
+  roles[0] = c->lev[lev].role_y;
+  roles[1] = c->lev[lev].role_prev;
+  roles[2] = c->lev[lev].role_s;
+  return SLH_OK;
+}
+
 slh_status slh_get_eta(slh_ctx* c, int32_t lev, double* eta) {
   if (!c || !eta) return fail(SLH_ERR_INVALID_ARG, "get_eta: null argument");
   if (lev < 0 || lev >= MAX_LEVELS) return fail(SLH_ERR_OUT_OF_RANGE, "get_eta: level %d", lev);
@@ -880,6 +896,8 @@ static slh_status rk_step_impl(slh_ctx* c, int lev, int sub, double dt0, const s
   Level& L = c->lev[lev];
   if (p.integrator == 22 && c->ncomp == NCOMP_GW)
     return fail(SLH_ERR_INVALID_ARG, "RKN5 is built for the scalar fields only (not the tensor fields)");
+  if (bf16(c) && p.integrator != 10 && p.integrator != 3)
+    return fail(SLH_ERR_INVALID_ARG, "SLH_F32_BF16 levels hold three buffers: integrator SSPRK3 (10 or 3) only");
   if (c->g < p.lap_order / 2) return fail(SLH_ERR_INVALID_ARG, "nghost %d < Laplacian half width %d", c->g, p.lap_order / 2);
   if (p.ko_order > 0 && c->g < (p.ko_order + 1) / 2)
     return fail(SLH_ERR_INVALID_ARG, "nghost %d < dissipation half width %d", c->g, (p.ko_order + 1) / 2);
@@ -895,22 +913,24 @@ static slh_status rk_step_impl(slh_ctx* c, int lev, int sub, double dt0, const s
   st = launch_time_begin(c, lev, sub, dt);
   prof_end(c);
   if (st != SLH_OK) return st;
-  const int ybuf = L.role_y, nbuf = L.role_prev;
+  const int ybuf = L.role_y, nbuf = L.role_prev, sbuf = L.role_s;
   const bool rkn5 = p.integrator == 22;
   const bool rkn = p.integrator == 21 || rkn5;
   const bool ssp = p.integrator != 4 && !rkn;
-  // classic RK4: Y -> YA -> prev -> YA -> prev with the increment in D;
-  // SSPRK3: Y -> YA -> D -> prev (D holds the second stage value);
+  // classic RK4: Y -> S -> prev -> S -> prev with the increment in D (state
+  // and previous state swap);
+  // SSPRK3: Y -> S -> prev -> S, three buffers (the new state in S, the old
+  // one the previous state, prev the next scratch);
   // RKN4: Y -> prev -> prev (velocities only, in place: stages 2 and 3 share
-  // their positions) -> YA -> prev, the position and velocity sums in D
-  int in_role[4] = {ybuf, SLH_BUF_YA, ssp ? SLH_BUF_D : nbuf, SLH_BUF_YA};
-  int out_role[4] = {SLH_BUF_YA, ssp ? SLH_BUF_D : nbuf, ssp ? nbuf : SLH_BUF_YA, nbuf};
+  // their positions) -> S -> prev, the position and velocity sums in D
+  int in_role[4] = {ybuf, sbuf, nbuf, sbuf};
+  int out_role[4] = {sbuf, nbuf, sbuf, nbuf};
   double vals[4] = {ssp ? 8.0 : 12.0, ssp ? 12.0 : 20.0, ssp ? 12.0 : 20.0, c->prec == SLH_F32_KAHAN ? 24.0 : 16.0};
   // RKN5: Y -> YA (stage-2 positions, k1) -> prev (stage-3 positions, A4;
   // D = position and velocity sums) -> YA (stage-4 positions; D = position
   // increment, velocity sum) -> prev
   if (rkn5) {
-    const int ir[4] = {ybuf, SLH_BUF_YA, nbuf, SLH_BUF_YA}, orr[4] = {SLH_BUF_YA, nbuf, SLH_BUF_YA, nbuf};
+    const int ir[4] = {ybuf, sbuf, nbuf, sbuf}, orr[4] = {sbuf, nbuf, sbuf, nbuf};
     const double vr[4] = {8.0, 16.0, 18.0, c->prec == SLH_F32_KAHAN ? 24.0 : 16.0};
     for (int k = 0; k < 4; ++k) {
       in_role[k] = ir[k];
@@ -918,7 +938,7 @@ static slh_status rk_step_impl(slh_ctx* c, int lev, int sub, double dt0, const s
       vals[k] = vr[k];
     }
   } else if (rkn) {
-    const int ir[4] = {ybuf, nbuf, nbuf, SLH_BUF_YA}, orr[4] = {nbuf, nbuf, SLH_BUF_YA, nbuf};
+    const int ir[4] = {ybuf, nbuf, nbuf, sbuf}, orr[4] = {nbuf, nbuf, sbuf, nbuf};
     const double vr[4] = {12.0, 16.0, 20.0, c->prec == SLH_F32_KAHAN ? 24.0 : 16.0};
     for (int k = 0; k < 4; ++k) {
       in_role[k] = ir[k];
@@ -1018,6 +1038,10 @@ static slh_status rk_step_impl(slh_ctx* c, int lev, int sub, double dt0, const s
       // and as the scalar stage y_n, D, C of its 12 fields
       double gvals[4] = {ssp ? 26.0 : 38.0, ssp ? 38.0 : 62.0, ssp ? 38.0 : 62.0,
                          c->prec == SLH_F32_KAHAN ? 74.0 : 50.0};
+      if (bf16(c)) {   // 4-byte slots: psi (2) + u, v pairs (6) in, u, v pairs (6) out, + y_n pairs (6)
+        gvals[0] = 14.0;
+        gvals[1] = gvals[2] = 20.0;
+      }
       if (rkn) {   // RKN4: stage 2 writes the velocities only (no y_n positions read)
         gvals[1] = 50.0;
         gvals[3] = c->prec == SLH_F32_KAHAN ? 74.0 : 50.0;
@@ -1028,8 +1052,14 @@ static slh_status rk_step_impl(slh_ctx* c, int lev, int sub, double dt0, const s
       if (st != SLH_OK) return st;
     }
   }
-  L.role_y = nbuf;
-  L.role_prev = ybuf;
+  if (ssp) {
+    L.role_y = sbuf;
+    L.role_prev = ybuf;
+    L.role_s = nbuf;
+  } else {
+    L.role_y = nbuf;
+    L.role_prev = ybuf;
+  }
   return SLH_OK;
 }
 
@@ -1049,7 +1079,7 @@ static slh_status fill_impl(slh_ctx* c, int lev, double alpha, int itype, int mo
   Level& L = c->lev[lev];
   const size_t s = elem_size(c);
   if (mode == SLH_RESTRICT) {
-    prof_begin(c, SLH_PROF_RESTRICT, (double)L.nrcells * c->ncomp * 9 * s);
+    prof_begin(c, SLH_PROF_RESTRICT, (double)L.nrcells * c->nslots * 9 * s);
     slh_status st = launch_restrict(c, lev);
     prof_end(c);
     if (st != SLH_OK) return st;
@@ -1088,6 +1118,8 @@ static unsigned long long graph_key(slh_ctx* c, double dt0, const slh_eom_params
     mix(&c->lev[l].d_boxes, sizeof(void*));
     mix(c->lev[l].buf, sizeof(c->lev[l].buf));
     mix(&c->lev[l].role_y, sizeof(int));
+    mix(&c->lev[l].role_prev, sizeof(int));
+    mix(&c->lev[l].role_s, sizeof(int));
   }
   return h | 1ull;
 }
@@ -1102,22 +1134,17 @@ slh_status slh_advance(slh_ctx* c, double dt0, const slh_eom_params* p, uint32_t
   NvtxRange range("slh coarse step (%d levels)", c->nlevels);
   if (!(flags & SLH_USE_GRAPH) || c->prof) return advance_rec(c, 0, 0, dt0, *p, flags);
 
-  // graph replay: the graph depends on the rotation parity of level 0 only
-  // (finer levels take an even number of steps per coarse step)
-  uint32_t f = flags & ~SLH_USE_GRAPH;
-  Level& L0 = c->lev[0];
-  const int parity = L0.role_y == SLH_BUF_Y ? 0 : 1;
-  // key of the configuration with level-0 rotation normalised
-  const int saved0 = L0.role_y, savedp0 = L0.role_prev;
-  L0.role_y = SLH_BUF_Y;
+  // graph replay: one graph per buffer-role configuration of the levels at
+  // the start of the step (the key covers them with the parameters, boxes
+  // and buffers); a replay leaves the roles the captured step left
+  const uint32_t f = flags & ~SLH_USE_GRAPH;
   const unsigned long long key = graph_key(c, dt0, *p, f);
-  L0.role_y = saved0;
-  if (key != c->graph_key) {
-    drop_graphs(c);
-    c->graph_key = key;
-  }
-  if (!c->graph[parity]) {
+  slh_ctx::Graph* hit = nullptr;
+  for (auto& g : c->graphs)
+    if (g.key == key) hit = &g;
+  if (!hit) {
     HostPhase phase(c, SLH_PROF_GRAPH_CAPTURE);   // preparation, capture and instantiation
+    if (c->graphs.size() >= 4) drop_graphs(c);      // parameters or levels changed: start afresh
     // everything a launch sets up lazily (tensor maps, kernel attributes) is
     // prepared before capture: allocations are not allowed while capturing
     for (int l = 0; l < c->nlevels; ++l) {
@@ -1141,29 +1168,44 @@ slh_status slh_advance(slh_ctx* c, double dt0, const slh_eom_params* p, uint32_t
         if ((st = launch_gw_stage(c, c->lev[l], *p, sl)) != SLH_OK) return st;
       }
     }
-    int saved[MAX_LEVELS][2];
+    int saved[MAX_LEVELS][3];
     for (int l = 0; l < c->nlevels; ++l) {
       saved[l][0] = c->lev[l].role_y;
       saved[l][1] = c->lev[l].role_prev;
+      saved[l][2] = c->lev[l].role_s;
     }
+    slh_ctx::Graph g;
+    memset(&g, 0, sizeof(g));
+    g.key = key;
     cudaGraph_t gr;
     SLH_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     slh_status cst = advance_rec(c, 0, 0, dt0, *p, f);
     cudaError_t e = cudaStreamEndCapture(c->stream, &gr);
     for (int l = 0; l < c->nlevels; ++l) {
+      g.roles_after[l][0] = c->lev[l].role_y;
+      g.roles_after[l][1] = c->lev[l].role_prev;
+      g.roles_after[l][2] = c->lev[l].role_s;
       c->lev[l].role_y = saved[l][0];
       c->lev[l].role_prev = saved[l][1];
+      c->lev[l].role_s = saved[l][2];
     }
-    if (cst != SLH_OK) return cst;
+    if (cst != SLH_OK) {
+      if (e == cudaSuccess) cudaGraphDestroy(gr);
+      return cst;
+    }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&c->graph[parity], gr, 0);
+    e = cudaGraphInstantiate(&g.exec, gr, 0);
     cudaGraphDestroy(gr);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    c->graphs.push_back(g);
+    hit = &c->graphs.back();
   }
-  SLH_CUDA(cudaGraphLaunch(c->graph[parity], c->stream));
-  (void)savedp0;
-  // apply the rotation the replayed step performed
-  std::swap(L0.role_y, L0.role_prev);
+  SLH_CUDA(cudaGraphLaunch(hit->exec, c->stream));
+  for (int l = 0; l < c->nlevels; ++l) {
+    c->lev[l].role_y = hit->roles_after[l][0];
+    c->lev[l].role_prev = hit->roles_after[l][1];
+    c->lev[l].role_s = hit->roles_after[l][2];
+  }
   return SLH_OK;
 }
 
@@ -1209,7 +1251,7 @@ static slh_status diag_pass(slh_ctx* c, int lev, const slh_eom_params& p, uint8_
   sl.in_buf = L.role_y;
   sl.yn_buf = L.role_y;
   sl.d_buf = SLH_BUF_D;
-  sl.out_buf = SLH_BUF_YA;
+  sl.out_buf = L.role_s;   // the diagnostics-only pass writes no field
   sl.c_buf = -1;
   sl.lev = lev;
   sl.c_stage = 0.0;
@@ -1320,6 +1362,7 @@ static slh_status check_shadow(slh_ctx* c, slh_ctx* s, const char* who) {
   if (!c || !s || c == s) return fail(SLH_ERR_INVALID_ARG, "%s: need two distinct contexts", who);
   if (s->prec != c->prec || s->ncomp != c->ncomp)
     return fail(SLH_ERR_INVALID_ARG, "%s: shadow precision / field count differ", who);
+  if (bf16(c)) return fail(SLH_ERR_INVALID_ARG, "%s: the shadow level is not built for BF16 tensor storage", who);
   if (2 * s->n0 != c->n0 || s->dx0 != 2.0 * c->dx0)
     return fail(SLH_ERR_INVALID_ARG, "%s: shadow must have n0/2 cells of spacing 2 dx0", who);
   if (s->device != c->device) return fail(SLH_ERR_INVALID_ARG, "%s: shadow on another device", who);
@@ -1495,7 +1538,7 @@ static slh_status autotune_impl(slh_ctx* c, int32_t lev, const slh_eom_params* p
       // operands differ: 5 boxes for classic RK4, RKN4 and RKN5, 3 for SSPRK3)
       const bool rk_n = p->integrator == 21 || p->integrator == 22;
       sl.stage = rk_n ? 3 : 2;
-      sl.in_buf = SLH_BUF_YA;
+      sl.in_buf = L.role_s;
       sl.yn_buf = L.role_y;
       sl.ssp = (p->integrator != 4 && !rk_n) ? 1 : 0;
       sl.rkn = rk_n ? 1 : 0;
@@ -1504,7 +1547,7 @@ static slh_status autotune_impl(slh_ctx* c, int32_t lev, const slh_eom_params* p
       sl.sb = sl.ssp ? 0.25 : 0.0;
     }
     sl.d_buf = SLH_BUF_D;
-    sl.out_buf = SLH_BUF_YA;
+    sl.out_buf = L.role_s;   // the level's scratch buffers only (S and D)
     sl.c_buf = -1;
     sl.ha = sl.hb = 0.0;
     sl.lev = lev;

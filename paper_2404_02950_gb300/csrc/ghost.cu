@@ -3,6 +3,8 @@
 // ghost cell, by ratio-2 prolongation of the coarser level interpolated in
 // time; restriction of a fine level onto the covered coarse cells; and the
 // small kernel that advances the per-level conformal time.
+#include <cuda_bf16.h>
+
 #include "slh_internal.cuh"
 
 namespace slh {
@@ -31,6 +33,18 @@ struct Split3 {
 __device__ __forceinline__ long long cell_index(const BoxDev& B, int gl, int x, int y, int z) {
   // valid-relative (x, y, z), may lie in the ghost shell
   return B.off + ((long long)(z + gl) * B.pny + (y + gl)) * B.pitch + (x + XPAD);
+}
+
+// SLH_F32_BF16 storage: two BF16 fields in one 4-byte slot (the first in
+// the low half).  Widening is exact; narrowing rounds to nearest even.
+__device__ __forceinline__ float bf16_half(float slot, int h) {
+  const unsigned w = __float_as_uint(slot);
+  return __uint_as_float(h ? (w & 0xFFFF0000u) : (w << 16));
+}
+__device__ __forceinline__ float bf16_pack(float lo, float hi) {
+  const unsigned a = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+  const unsigned b = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
+  return __uint_as_float(a | (b << 16));
 }
 
 // 1D prolongation weights for offsets -2..2 (type 4: fine-cell average of
@@ -99,7 +113,8 @@ struct GhostArgs {
   int itype;
   int npairs;   // field pairs filled: (psi1, psi2), (Pi1, Pi2) under dissipation, and with 16
                 // fields (u_xx, u_yy), (u_zz, u_xy), (u_xz, u_yz)
-  int pc[5];    // first component of each pair
+  int pc[5];    // first component of each pair (its slot, when packed)
+  int packed;   // bit q: pair q is one slot of two BF16 fields (SLH_F32_BF16)
   int* err;
 };
 
@@ -202,7 +217,10 @@ __device__ __forceinline__ void final_pass(const T* __restrict__ src, int sstr, 
         const long long sg = cell_index(Sb, A.gl, wx - Sb.lo[0], wy - Sb.lo[1], wz - Sb.lo[2]);
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-          const int comp = A.pc[(f0 + f) >> 1] + ((f0 + f) & 1);
+          const int q = (f0 + f) >> 1;
+          const bool pk = (A.packed >> q) & 1;
+          if (pk && ((f0 + f) & 1)) continue;   // a packed pair is one slot
+          const int comp = A.pc[q] + (pk ? 0 : ((f0 + f) & 1));
           A.y[dg + comp * B.cs] = A.y[sg + comp * Sb.cs];
         }
         continue;
@@ -224,13 +242,23 @@ __device__ __forceinline__ void final_pass(const T* __restrict__ src, int sstr, 
     const int pc = (g >> 1) - pa - RAD;
     const bool ch = (g & 1) != 0;
     const int base = (pick<AX>(i2, i2, pc) * d[1] + pick<AX>(i1, pc, i1)) * d[0] + pick<AX>(pc, i0, i0);
+    T acc[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-      T acc = 0;
+      acc[f] = 0;
 #pragma unroll
-      for (int o = 0; o <= 2 * RAD; ++o) acc += (ch ? w1[o] : w0[o]) * src[f * sstr + base + o * sa];
+      for (int o = 0; o <= 2 * RAD; ++o) acc[f] += (ch ? w1[o] : w0[o]) * src[f * sstr + base + o * sa];
+    }
+    if constexpr (NF == 2) {
+      if ((A.packed >> (f0 >> 1)) & 1) {   // both fields of a packed pair: one slot
+        A.y[dg + A.pc[f0 >> 1] * B.cs] = (T)bf16_pack((float)acc[0], (float)acc[1]);
+        continue;
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
       const int comp = A.pc[(f0 + f) >> 1] + ((f0 + f) & 1);
-      A.y[dg + comp * B.cs] = acc;
+      A.y[dg + comp * B.cs] = acc[f];
     }
   }
 }
@@ -274,18 +302,19 @@ __global__ void __launch_bounds__(256) ghost_copy_kernel(const GhostArgs<T> A) {
       }
       for (int q = 0; q < A.npairs; ++q) {
         const int c0 = A.pc[q];
+        const bool two = !((A.packed >> q) & 1);   // a packed pair is one slot
         T v0[CU], v1[CU];
 #pragma unroll
         for (int u = 0; u < CU; ++u)
           if (ok[u]) {
             v0[u] = A.y[src[u] + c0 * S.cs];
-            v1[u] = A.y[src[u] + (c0 + 1) * S.cs];
+            if (two) v1[u] = A.y[src[u] + (c0 + 1) * S.cs];
           }
 #pragma unroll
         for (int u = 0; u < CU; ++u)
           if (ok[u]) {
             A.y[dst[u] + c0 * B.cs] = v0[u];
-            A.y[dst[u] + (c0 + 1) * B.cs] = v1[u];
+            if (two) A.y[dst[u] + (c0 + 1) * B.cs] = v1[u];
           }
       }
     }
@@ -327,7 +356,7 @@ __global__ void __launch_bounds__(256, 5) ghost_region_kernel(const GhostArgs<T>
         for (int q = 0; q < A.npairs; ++q) {
           const int c0 = A.pc[q];
           A.y[dst + c0 * B.cs] = A.y[src + c0 * S.cs];
-          A.y[dst + (c0 + 1) * B.cs] = A.y[src + (c0 + 1) * S.cs];
+          if (!((A.packed >> q) & 1)) A.y[dst + (c0 + 1) * B.cs] = A.y[src + (c0 + 1) * S.cs];
         }
       }
       continue;   // uniform over the CTA: no shared memory used
@@ -362,7 +391,16 @@ __global__ void __launch_bounds__(256, 5) ghost_region_kernel(const GhostArgs<T>
     for (int f0 = 0; f0 < 2 * A.npairs; f0 += NF) {
       // gather NF fields into the patch (field f of the region's pair list)
       for (int f = 0; f < NF; ++f) {
-        const int comp = A.pc[(f0 + f) >> 1] + ((f0 + f) & 1);
+        const int q = (f0 + f) >> 1, half = (f0 + f) & 1;
+        const bool pk = sizeof(T) == 4 && ((A.packed >> q) & 1);
+        const int comp = A.pc[q] + (pk ? 0 : half);
+        // a field value of the coarse level, time-interpolated
+        auto cval = [&](long long ci) -> T {
+          if constexpr (sizeof(T) == 4) {
+            if (pk) return bl * (T)bf16_half((float)A.cold[ci], half) + al * (T)bf16_half((float)A.cnew[ci], half);
+          }
+          return bl * A.cold[ci] + al * A.cnew[ci];
+        };
         T* pf = patch + f * PATCH_MAX;
         if (have_coarse && R.covered) {
           // planned gather: strided copies of the pieces, no lookups
@@ -375,7 +413,7 @@ __global__ void __launch_bounds__(256, 5) ghost_region_kernel(const GhostArgs<T>
               int i, j, k;
               sp(t, i, j, k);
               const long long ci = cell_index(C, A.gl, P.src[0] + i, P.src[1] + j, P.src[2] + k) + comp * C.cs;
-              pf[((P.dst[2] + k) * pn[1] + (P.dst[1] + j)) * pn[0] + (P.dst[0] + i)] = bl * A.cold[ci] + al * A.cnew[ci];
+              pf[((P.dst[2] + k) * pn[1] + (P.dst[1] + j)) * pn[0] + (P.dst[0] + i)] = cval(ci);
             }
           }
         } else if (have_coarse) {
@@ -393,7 +431,7 @@ __global__ void __launch_bounds__(256, 5) ghost_region_kernel(const GhostArgs<T>
             if (cown >= 0) {
               const BoxDev C = A.cboxes[cown];
               const long long ci = cell_index(C, A.gl, qx - C.lo[0], qy - C.lo[1], qz - C.lo[2]) + comp * C.cs;
-              v = bl * A.cold[ci] + al * A.cnew[ci];
+              v = cval(ci);
             } else if (f == 0 && f0 == 0) {
               atomicOr(&s_unc[t >> 5], 1u << (t & 31));
             }
@@ -457,10 +495,15 @@ static slh_status ghosts_t(slh_ctx* c, int lev, int role, double alpha, int ityp
   A.alpha = alpha;
   A.itype = itype;
   A.npairs = 0;
+  A.packed = 0;
   A.pc[A.npairs++] = 0;
   if (with_pi) A.pc[A.npairs++] = 2;
   if (c->ncomp == NCOMP_GW)
-    for (int q = 0; q < 3; ++q) A.pc[A.npairs++] = GW_U0 + 2 * q;
+    for (int q = 0; q < 3; ++q) {
+      if (c->prec == SLH_F32_BF16) A.packed |= 1 << A.npairs;
+      A.pc[A.npairs] = c->prec == SLH_F32_BF16 ? SLOT_U0 + q : GW_U0 + 2 * q;
+      ++A.npairs;
+    }
   A.err = c->d_err;
   const int smem = (sizeof(T) == 4 ? 2 : 1) * (patch_max(c->g) + pass1_max(c->g) + pass2_max(c->g)) * (int)sizeof(T);
   const int smem_max = (sizeof(T) == 4 ? 2 : 1) * (patch_max(4) + pass1_max(4) + pass2_max(4)) * (int)sizeof(T);
@@ -515,7 +558,8 @@ struct RestrictArgs {
   const int* cbmap;
   int cbshift, cnbd;
   int gl;
-  int ncomp;
+  int ncomp;         // leading components of the field precision
+  int npacked;       // then slots of two BF16 fields each (SLH_F32_BF16)
   uint8_t* tee;      // fine level's TEE tags (null: no estimate)
   double eps[4];     // thresholds of psi1, psi2, Pi1, Pi2 (<= 0: left out)
   int* err;
@@ -561,6 +605,19 @@ __global__ void restrict_kernel(const RestrictArgs<T> A) {
       if (A.tee != nullptr && c < 4 && A.eps[c] > 0.0) hit |= fabs((double)A.cy[dsti + c * C.cs] - s) > A.eps[c];
       A.cy[dsti + c * C.cs] = (T)s;
     }
+    if constexpr (sizeof(T) == 4) {
+      for (int c = A.ncomp; c < A.ncomp + A.npacked; ++c) {
+        const T* f = A.fy + f000 + c * F.cs;
+        const long long off[8] = {0, 1, sy, sy + 1, sz, sz + 1, sz + sy, sz + sy + 1};
+        double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          s0 += (double)bf16_half(f[off[a]], 0);
+          s1 += (double)bf16_half(f[off[a]], 1);
+        }
+        A.cy[dsti + c * C.cs] = bf16_pack((float)(s0 * 0.125), (float)(s1 * 0.125));
+      }
+    }
     if (A.tee != nullptr) {
       const uint8_t tv = hit ? 1 : 0;
 #pragma unroll
@@ -592,7 +649,8 @@ static slh_status restrict_t(slh_ctx* c, int fl) {
   A.cbshift = sh;
   A.cnbd = C.nb_dom;
   A.gl = c->g;
-  A.ncomp = c->ncomp;
+  A.ncomp = c->prec == SLH_F32_BF16 ? NCOMP : c->ncomp;
+  A.npacked = c->prec == SLH_F32_BF16 ? c->nslots - NCOMP : 0;
   A.tee = (c->tag_criteria & SLH_TAG_TEE) ? F.d_tee : nullptr;
   for (int q = 0; q < 4; ++q) A.eps[q] = c->te_crit[q];
   A.err = c->d_err;
@@ -657,7 +715,9 @@ struct RegridFillArgs {
   int bshift;
   int gl;
   int itype;
-  int ncomp;
+  int ncomp;             // slots per cell (copied bit for bit)
+  int nscalar;           // of which the leading ones hold one field of the precision;
+                         // the rest (SLH_F32_BF16) two BF16 fields each
   int* err;
 };
 
@@ -693,8 +753,11 @@ __global__ void regrid_fill_kernel(const RegridFillArgs<T> A) {
     const int cx = gx & 1, cy = gy & 1, cz = gz & 1;
     const int rad = A.itype == 4 ? 2 : (A.itype == 2 ? 1 : 0);
     bool bad = false;
-    // fields in groups of four (one stencil walk per group)
-    for (int c0 = 0; c0 < A.ncomp; c0 += NCOMP) {
+    // fields in groups of four (one stencil walk per group): four slots of
+    // one field each, or two slots of two BF16 fields each
+    for (int c0 = 0; c0 < A.ncomp;) {
+      const bool pk = c0 >= A.nscalar;
+      const int nsl = pk ? min(2, A.ncomp - c0) : NCOMP;   // slots of this group
       double acc[NCOMP] = {0.0, 0.0, 0.0, 0.0};
       for (int oz = -rad; oz <= rad; ++oz) {
         const double wzv = pw(A.itype, cz, oz);
@@ -713,9 +776,26 @@ __global__ void regrid_fill_kernel(const RegridFillArgs<T> A) {
             const BoxDev C = A.cboxes[cown];
             const long long ci = cell_index(C, A.gl, qx - C.lo[0], qy - C.lo[1], qz - C.lo[2]) + c0 * C.cs;
             const double wgt = wzv * wyv * wxv;
+            if constexpr (sizeof(T) == 4) {
+              if (pk) {
+                for (int k = 0; k < nsl; ++k) {
+                  const float v = A.cy[ci + k * C.cs];
+                  acc[2 * k] += wgt * (double)bf16_half(v, 0);
+                  acc[2 * k + 1] += wgt * (double)bf16_half(v, 1);
+                }
+                continue;
+              }
+            }
 #pragma unroll
             for (int c = 0; c < NCOMP; ++c) acc[c] += wgt * (double)A.cy[ci + c * C.cs];
           }
+        }
+      }
+      if constexpr (sizeof(T) == 4) {
+        if (pk) {
+          for (int k = 0; k < nsl; ++k) A.ny[dst + (c0 + k) * B.cs] = bf16_pack((float)acc[2 * k], (float)acc[2 * k + 1]);
+          c0 += nsl;
+          continue;
         }
       }
 #pragma unroll
@@ -723,6 +803,7 @@ __global__ void regrid_fill_kernel(const RegridFillArgs<T> A) {
         A.ny[dst + (c0 + c) * B.cs] = (T)acc[c];
         if (A.nc) A.nc[dst + (c0 + c) * B.cs] = (T)0;
       }
+      c0 += NCOMP;
     }
     if (bad) atomicCAS(A.err, 0, DERR_NESTING);
   }
@@ -759,7 +840,8 @@ static slh_status regrid_fill_t(slh_ctx* c, int lev, Level& N, Level* O) {
   A.bshift = sh;
   A.gl = c->g;
   A.itype = c->regrid_itype;
-  A.ncomp = c->ncomp;
+  A.ncomp = c->nslots;
+  A.nscalar = c->prec == SLH_F32_BF16 ? NCOMP : c->nslots;
   A.err = c->d_err;
   const int threads = 256;
   long long blocks = (A.nvalid + threads - 1) / threads;

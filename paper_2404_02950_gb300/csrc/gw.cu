@@ -15,6 +15,7 @@
 // lines the CTA's own rows bring into L1, z neighbours from planes read a few
 // iterations earlier (L1/L2), so DRAM sees each value about once.
 #include <cuda.h>
+#include <cuda_bf16.h>
 
 #include "slh_internal.cuh"
 #include "stencil.cuh"
@@ -215,6 +216,105 @@ __global__ void __launch_bounds__(COL_TX * COL_TY, sizeof(T) == 4 ? 4 : 3) gw_st
           out[ev] = yv + iv;
         }
       }
+    }
+  }
+}
+
+// BF16 storage (SLH_F32_BF16): the SSPRK3 stage of the tensor fields with
+// u_ij and v_ij held as BF16 pairs, (u_xx, u_yy), (u_zz, u_xy), (u_xz, u_yz)
+// in slots SLOT_U0 .. SLOT_U0 + 2 and the v_ij likewise from SLOT_V0, the
+// first field of a pair in the low half.  Every value is widened to FP32
+// (exactly), the stage is computed and combined in FP32 as in
+// gw_stage_kernel, and the results are rounded to BF16 (to nearest even)
+// once, when stored.  Same items and threads as gw_stage_kernel.
+__device__ __forceinline__ float bf_lo(float w) { return __uint_as_float(__float_as_uint(w) << 16); }
+__device__ __forceinline__ float bf_hi(float w) { return __uint_as_float(__float_as_uint(w) & 0xFFFF0000u); }
+__device__ __forceinline__ float bf_pack(float lo, float hi) {
+  return __uint_as_float((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+                         ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16));
+}
+
+template <int G>
+__global__ void __launch_bounds__(COL_TX * COL_TY, 4) gw_bf16_kernel(const GwArgs<float> A) {
+  using T = float;
+  const int4 it = A.items[blockIdx.x];
+  const BoxDev B = A.boxes[it.x];
+  const int x = it.y + threadIdx.x, y = it.z + threadIdx.y;
+  if (x >= B.n[0] || y >= B.n[1]) return;
+  const int z1 = min(it.w + COL_ZLEN, B.n[2]);
+  const double eta = *A.eta_start + A.c_stage;
+  const T c_fric = (T)(A.friction ? 2.0 / eta : 0.0);
+  const T ha = (T)A.ha, idx = (T)A.inv_dx, idx2 = (T)A.inv_dx2;
+  const long long sy = B.pitch, sz = (long long)B.pitch * B.pny, cs = B.cs;
+  const long long st[3] = {1, sy, sz};
+  const T* __restrict__ in = A.in;
+  const T* __restrict__ yn = A.yn;
+  T* __restrict__ out = A.out;
+  const int stage = A.stage;
+  const T sa = (T)A.sa, sb = (T)A.sb;
+  long long e = B.off + ((long long)(it.w + A.gl) * B.pny + (y + A.gl)) * B.pitch + x + XPAD;
+#pragma unroll 1
+  for (int z = it.w; z < z1; ++z, e += sz) {
+    // gradients of psi1, psi2 (FP32 slots 0 and 1)
+    T g1[3], g2[3];
+#pragma unroll
+    for (int dir = 0; dir < 3; ++dir) {
+      T a1 = 0, a2 = 0;
+#pragma unroll
+      for (int m = 1; m <= G; ++m) {
+        const long long o = m * st[dir];
+        const T w = (T)grad_w<G>(m);
+        a1 += w * (__ldg(in + e + o) - __ldg(in + e - o));
+        a2 += w * (__ldg(in + e + cs + o) - __ldg(in + e + cs - o));
+      }
+      g1[dir] = a1 * idx;
+      g2[dir] = a2 * idx;
+    }
+#pragma unroll 1
+    for (int q = 0; q < 3; ++q) {
+      const long long eu = e + (SLOT_U0 + q) * cs, ev = e + (SLOT_V0 + q) * cs;
+      const T* f = in + eu;
+      const T uc = __ldg(f);
+      const T u0[2] = {bf_lo(uc), bf_hi(uc)};
+      // difference-form Laplacians of both fields of the pair
+      T acc[2] = {0, 0};
+#pragma unroll
+      for (int m = 1; m <= G; ++m) {
+        const T w = (T)lap_w<G>(m);
+        T sm[2] = {0, 0};
+#pragma unroll
+        for (int dir = 0; dir < 3; ++dir) {
+          const T pv = __ldg(f + m * st[dir]), mv = __ldg(f - m * st[dir]);
+          sm[0] += (bf_lo(pv) - u0[0]) + (bf_lo(mv) - u0[0]);
+          sm[1] += (bf_hi(pv) - u0[1]) + (bf_hi(mv) - u0[1]);
+        }
+        acc[0] += w * sm[0];
+        acc[1] += w * sm[1];
+      }
+      const T vc = __ldg(in + ev);
+      const T v[2] = {bf_lo(vc), bf_hi(vc)};
+      T yu[2] = {0, 0}, yv[2] = {0, 0};
+      if (stage >= 2) {
+        const T a = __ldg(yn + eu), b = __ldg(yn + ev);
+        yu[0] = bf_lo(a);
+        yu[1] = bf_hi(a);
+        yv[0] = bf_lo(b);
+        yv[1] = bf_hi(b);
+      }
+      T ou[2], ov[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = 2 * q + h, i = pair_i(k), j = pair_j(k);
+        const T g1i = i == 0 ? g1[0] : (i == 1 ? g1[1] : g1[2]), g1j = j == 0 ? g1[0] : (j == 1 ? g1[1] : g1[2]);
+        const T g2i = i == 0 ? g2[0] : (i == 1 ? g2[1] : g2[2]), g2j = j == 0 ? g2[0] : (j == 1 ? g2[1] : g2[2]);
+        const T src = (T)2 * (g1i * g1j + g2i * g2j);
+        const T kv = ((-c_fric) * v[h] + acc[h] * idx2) + src;
+        const T fu = u0[h] + ha * v[h], fv = v[h] + ha * kv;
+        ou[h] = stage == 1 ? fu : sa * yu[h] + sb * fu;
+        ov[h] = stage == 1 ? fv : sa * yv[h] + sb * fv;
+      }
+      out[eu] = bf_pack(ou[0], ou[1]);
+      out[ev] = bf_pack(ov[0], ov[1]);
     }
   }
 }
@@ -489,6 +589,20 @@ static slh_status gw_stage_t(slh_ctx* c, Level& L, const slh_eom_params& p, cons
   A.in_buf = s.in_buf;
   A.err = c->d_err;
   if constexpr (sizeof(T) == 4) {
+    if (c->prec == SLH_F32_BF16) {
+      // BF16 tensor storage: SSPRK3 only (three level buffers)
+      if (!s.ssp) return fail(SLH_ERR_INVALID_ARG, "BF16 tensor storage runs SSPRK3 only");
+      if (s.dry) return SLH_OK;
+      const dim3 block(COL_TX, COL_TY);
+      switch (p.lap_order) {
+        case 2: gw_bf16_kernel<1><<<L.ncol_items, block, 0, c->stream>>>(A); break;
+        case 4: gw_bf16_kernel<2><<<L.ncol_items, block, 0, c->stream>>>(A); break;
+        case 6: gw_bf16_kernel<3><<<L.ncol_items, block, 0, c->stream>>>(A); break;
+        default: return fail(SLH_ERR_INVALID_ARG, "lap_order must be 2, 4 or 6 (got %d)", p.lap_order);
+      }
+      SLH_CUDA(cudaGetLastError());
+      return SLH_OK;
+    }
     // FP32, Laplacian radius <= 2: the TMA-fed form
     if (p.lap_order == 2) return gw_tma_launch<1>(c, L, s, A);
     if (p.lap_order == 4) return gw_tma_launch<2>(c, L, s, A);

@@ -34,7 +34,7 @@ slh_status apply_level(slh_ctx* c, int lev, const std::vector<slh_box>& boxes, i
     return SLH_OK;
   }
   int64_t total = 0, nvalid = 0;
-  slh_status st = slh_level_layout(c->g, c->ncomp, boxes.data(), (int32_t)boxes.size(), nullptr, nullptr, &total,
+  slh_status st = slh_level_layout(c->g, c->nslots, boxes.data(), (int32_t)boxes.size(), nullptr, nullptr, &total,
                                    &nvalid);
   if (st != SLH_OK) return st;
   void* bufs[SLH_NBUF] = {nullptr, nullptr, nullptr, nullptr, nullptr};

@@ -20,6 +20,7 @@ constexpr int XPAD = 4;
 constexpr int NCOMP = 4;        // psi1, psi2, Pi1, Pi2
 constexpr int NCOMP_GW = 16;    // + u_xx..u_yz (4..9), v_xx..v_yz (10..15)
 constexpr int GW_U0 = 4, GW_V0 = 10;
+constexpr int SLOT_U0 = 4, SLOT_V0 = 7;   // SLH_F32_BF16: first slot of the u and v pairs
 constexpr int MAX_LEVELS = 8;
 
 // Per-box geometry as the kernels see it.
@@ -104,6 +105,7 @@ struct Level {
   void* buf[SLH_NBUF] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   int role_y = SLH_BUF_Y;        // buffer currently holding y_n
   int role_prev = SLH_BUF_YB;    // buffer holding the previous state
+  int role_s = SLH_BUF_YA;       // stage scratch (rotates with the other two under SSPRK3)
   uint8_t* tags_dev = nullptr;   // caller-owned (fused tags)
   // device metadata (owned)
   BoxDev* d_boxes = nullptr;
@@ -149,6 +151,7 @@ struct slh_ctx {
   int bf = 0;
   int prec = SLH_F64;
   int ncomp = slh::NCOMP;        // fields per cell: 4, or 16 with the GW tensor
+  int nslots = slh::NCOMP;       // storage slots per cell: ncomp, or 10 with BF16 tensor pairs
   int max_levels = 1;
   int nlevels = 0;
   cudaStream_t stream = nullptr;
@@ -167,10 +170,15 @@ struct slh_ctx {
   double prof_ms[SLH_PROF_NKINDS] = {0};
   long long prof_n[SLH_PROF_NKINDS] = {0};
   double prof_bytes[SLH_PROF_NKINDS] = {0};
-  // CUDA graph of one coarse step
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  unsigned long long graph_key = 0;
-  int graph_parity = 0;
+  // CUDA graphs of one coarse step, one per buffer-role configuration the
+  // levels start it in (two for the integrators that swap state and previous
+  // state, three for SSPRK3's rotation of three buffers)
+  struct Graph {
+    unsigned long long key;
+    cudaGraphExec_t exec;
+    int roles_after[slh::MAX_LEVELS][3];   // (y, prev, s) of every level after the step
+  };
+  std::vector<Graph> graphs;
   int stale_from = slh::MAX_LEVELS;   // levels >= this must be regridded before stepping
   int regrid_itype = 4;
   uint32_t tag_criteria = SLH_TAG_WINDING;

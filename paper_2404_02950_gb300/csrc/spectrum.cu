@@ -60,7 +60,7 @@ static const CufftApi& cufft_api() {
 // --- gather v_ij of a level into dense [6][N][N][N] arrays
 template <typename T>
 __global__ void gather_v_kernel(const BoxDev* boxes, int nboxes, long long nvalid, const T* y, int gl, int n,
-                                T* out) {
+                                T* out, int packed) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long n3 = (long long)n * n * n;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nvalid; t += stride) {
@@ -76,8 +76,17 @@ __global__ void gather_v_kernel(const BoxDev* boxes, int nboxes, long long nvali
     const int rz = (int)(loc / ((long long)B.n[0] * B.n[1]));
     const long long src = B.off + ((long long)(rz + gl) * B.pny + (ry + gl)) * B.pitch + (rx + XPAD);
     const long long dst = ((long long)(B.lo[2] + rz) * n + (B.lo[1] + ry)) * n + (B.lo[0] + rx);
+    if (packed) {
+      // SLH_F32_BF16: v_ij as BF16 pairs in slots SLOT_V0 .. SLOT_V0 + 2
 #pragma unroll
-    for (int c = 0; c < 6; ++c) out[c * n3 + dst] = y[src + (GW_V0 + c) * B.cs];
+      for (int c = 0; c < 6; ++c) {
+        const unsigned w = __float_as_uint((float)y[src + (SLOT_V0 + c / 2) * B.cs]);
+        out[c * n3 + dst] = (T)__uint_as_float((c & 1) ? (w & 0xFFFF0000u) : (w << 16));
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) out[c * n3 + dst] = y[src + (GW_V0 + c) * B.cs];
+    }
   }
 }
 
@@ -271,7 +280,8 @@ static slh_status spectrum_t(slh_ctx* c, int ptype, std::vector<double>* bins_h,
   long long blocks = (L.lay.nvalid + threads - 1) / threads;
   if (blocks > (long long)c->num_sms * 16) blocks = (long long)c->num_sms * 16;
   gather_v_kernel<T><<<(int)std::max<long long>(1, blocks), threads, 0, c->stream>>>(
-      L.d_boxes, (int)L.boxes.size(), L.lay.nvalid, static_cast<const T*>(L.buf[L.role_y]), c->g, n, dense);
+      L.d_boxes, (int)L.boxes.size(), L.lay.nvalid, static_cast<const T*>(L.buf[L.role_y]), c->g, n, dense,
+      c->prec == SLH_F32_BF16 ? 1 : 0);
   if ((e = cudaGetLastError()) != cudaSuccess) {
     cleanup();
     return cuda_fail(e, "gather_v_kernel");

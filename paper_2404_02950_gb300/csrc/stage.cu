@@ -86,7 +86,8 @@ slh_status build_gw_tmaps(slh_ctx* c, Level& L, int G, int TX, int TY, CUtensorM
     *out = static_cast<CUtensorMap*>(it->second);
     return SLH_OK;
   }
-  if (c->prec == SLH_F64 || c->ncomp != NCOMP_GW) return fail(SLH_ERR_STATE, "gw tensor maps: FP32 16-field levels only");
+  if (c->prec != SLH_F32_KAHAN || c->ncomp != NCOMP_GW)
+    return fail(SLH_ERR_STATE, "gw tensor maps: FP32 16-field levels only");
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return fail(SLH_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
   const size_t es = 4;

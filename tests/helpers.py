@@ -60,9 +60,9 @@ def tags_domain(tags_dense, boxes, n):
 
 
 def box_padded_views(h, lev, role=None):
-    """Per-box padded (ncomp, pnz, pny, pitch) torch views of a level buffer."""
+    """Per-box padded (slots, pnz, pny, pitch) torch views of a level buffer."""
     info = h.levels[lev]
-    nc = h.ncomp
+    nc = h.nslots
     offs, geom, _, _ = slh.slh_level_layout(h.nghost, info["boxes"], nc)
     buf = h.state_buffer(lev) if role is None else info["bufs"][role]
     views = []
