@@ -303,6 +303,94 @@ def _gw_form(slh, torch, n, dist, peak, K=GW_K):
                                "(over the 288 GB of HBM); the largest lattice under 150 GB is 768^3")}
 
 
+C4_N, C4_K, C4_W = 1024, 4, 2
+C4_WORKLOAD = ("largest single-GPU run: 1024^3 periodic base + 2 ratio-2 levels (each a 256^3 cube of eight 128^3 "
+               "boxes at the centre of the level below), 16 fields: psi, Pi in FP32, u_ij, v_ij stored BF16 and "
+               "accumulated FP32, low-storage SSPRK3 (integrator type 10) on three level buffers, 4th-order "
+               "Laplacian and gradients, quartic prolongation, Gaussian psi (k_max = pi/(4 dx) on a 512^3 lattice, "
+               "tiled twice per axis), u = v = 0, dx0 = 1/8, dt0 = dx0/4, eta0 = 0.1; subcycled coarse steps "
+               "replayed from CUDA graphs")
+C4_GW_SLOTS = (14, 20, 20)   # 4-byte slots the BF16 GW stage moves per cell at SSPRK3 stages 1..3
+
+
+def _c4_level_boxes(n0, side=128):
+    """Fixed refined levels 1 and 2: a cube of 2 side cells at the centre of
+    the level's index space, cut into eight boxes of side^3 (nested in the
+    level below with room to spare for n0 >= 4 side)."""
+    out = []
+    for lev in (1, 2):
+        lo = (n0 << lev) // 2 - side
+        out.append([((lo + side * i, lo + side * j, lo + side * k),
+                     (lo + side * (i + 1) - 1, lo + side * (j + 1) - 1, lo + side * (k + 1) - 1))
+                    for k in range(2) for j in range(2) for i in range(2)])
+    return out
+
+
+def _c4_form(slh, torch, peak, n=C4_N, K=C4_K, W=C4_W):
+    """The largest single-GPU workload with BF16 tensor storage: footprint,
+    whole-step throughput and the BF16 GW stage kernel's HBM fraction."""
+    from paper_2404_02950_gb300 import inputs
+    n_small = n // 2
+    y = inputs.gaussian_field(n_small, n_small / 4.0, seed=11)
+    h = slh.Hierarchy(n, DX, nghost=2, bf=16, prec="f32bf16", max_levels=3, gw=True)
+    h.init_level(0, [((0, 0, 0), (n - 1,) * 3)])    # every buffer zeroed: Pi = u = v = 0
+    # psi1, psi2: the n/2 lattice tiled twice per axis, written into the padded
+    # state buffer on the device (slots 0 and 1)
+    offs, geom, _, _ = slh.slh_level_layout(2, [((0, 0, 0), (n - 1,) * 3)], slh.SLH_SLOTS_BF16)
+    pitch, pny, pnz, cs = (int(v) for v in geom[0])
+    buf = h.state_buffer(0)
+    for c in range(2):
+        v = buf[int(offs[0]) + c * cs:int(offs[0]) + c * cs + pitch * pny * pnz].view(pnz, pny, pitch)
+        t = torch.from_numpy(y[c].astype(np.float32)).cuda()
+        v[2:2 + n, 2:2 + n, 4:4 + n].copy_(t.repeat(2, 2, 2))
+        del t
+    del y
+    h.set_eta(ETA0)
+    for lev, boxes in enumerate(_c4_level_boxes(n), start=1):
+        h.regrid_level(lev, boxes)
+    p = slh.EOMParams(order=4, interp_type=4, integrator=10)
+    footprint = sum(b.numel() * b.element_size() for info in h.levels.values() for b in info["bufs"] if b is not None)
+    for _ in range(W):
+        h.advance(DT, p, flags=slh.SLH_USE_GRAPH)
+    h.sync()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(h.stream)
+    for _ in range(K):
+        h.advance(DT, p, flags=slh.SLH_USE_GRAPH)
+    ev1.record(h.stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    updates = sum(info["nvalid"] * 2 ** lev for lev, info in h.levels.items())
+    # the same steps launched directly with the per-kernel profile on
+    h.profile(True, True)
+    for _ in range(K):
+        h.advance(DT, p)
+    h.sync()
+    gwk = h.profile_read(slh.SLH_PROF_GW)
+    stg = h.profile_read(slh.SLH_PROF_STAGE)
+    gho = h.profile_read(slh.SLH_PROF_GHOST)
+    h.profile(False, True)
+    E = h.reduce_energy(p)
+    levels = {str(l): {"boxes": len(info["boxes"]), "cells": info["nvalid"]} for l, info in h.levels.items()}
+    h.close()
+    del h
+    torch.cuda.empty_cache()
+    ach = gwk[2] / (gwk[0] / 1e3) / 1e9 if gwk[0] > 0 else None
+    return {"workload": C4_WORKLOAD, "unit": "cell-updates/s", "value": updates * K / (ms / 1e3),
+            "ms_per_coarse_step": ms / K, "coarse_steps_timed": K, "levels": levels,
+            "hbm_footprint_gb": footprint / 1e9,
+            "footprint_note": ("3 level buffers x (4 FP32 + 6 BF16-pair slots) = 120 B per cell; the < 150 GB "
+                               "target of the 1024^3 + 2-level run"),
+            "gw_kernel": {"achieved": ach, "peak": peak, "unit": "GB/s", "frac": (ach / peak) if ach else None,
+                          "ms_per_coarse_step_direct": gwk[0] / K, "launches": gwk[1],
+                          "alg_slots_per_cell_update": sum(C4_GW_SLOTS), "slot_bytes": 4},
+            "scalar_stage_ms_per_coarse_step_direct": stg[0] / K, "ghost_ms_per_coarse_step_direct": gho[0] / K,
+            "string_length_end": E[4],
+            "error_vs_f64": "tests/test_gpu_bf16.py: the 128^3 crop after 100 steps against the FP64 oracle"}
+
+
 AMR_N, AMR_LEVELS, AMR_NBUF, AMR_BF, AMR_MAXBOX, AMR_RELAX, AMR_EVERY = 256, 4, 4, 16, 128, 300, 4
 AMR_ORDER = 4
 AMR_K32, AMR_K64 = 16, 4   # coarse steps timed (FP32 batched, FP64 plain)
@@ -398,6 +486,9 @@ def run_ours(args, rank, world, local_rank, dist):
         return
     if args.profile_only == "gw":
         _gw_form(slh, torch, n, dist, peak, K=K)
+        return
+    if args.profile_only == "gw4":
+        _c4_form(slh, torch, peak, n=n, K=K, W=W)
         return
     y0 = inputs.gaussian_field(n, n / 16.0, seed=rank)
     boxes = [((0, 0, 0), (n - 1, n - 1, n - 1))]
@@ -524,9 +615,12 @@ def run_ours(args, rank, world, local_rank, dist):
 
     # gravitational-wave tensor fields
     gw = None
+    c4 = None
     if not args.no_gw:
         gw = _gw_form(slh, torch, GW_N, dist, peak)
         gw["value"] *= world
+        c4 = _c4_form(slh, torch, peak)
+        c4["value"] *= world
 
     ms = r32["ms"]
     e2e_ms = e2e_s * 1e3
@@ -570,6 +664,7 @@ def run_ours(args, rank, world, local_rank, dist):
         "rkn5": rkn5,
         "plain_step": plain,
         "gw": gw,
+        "gw_1024_bf16": c4,
         "gpu_launches": launches,
         "clocks": clocks,
     }
@@ -594,10 +689,10 @@ def main():
                     help="with --profile-only: use this stage-kernel tile variant instead of autotuning")
     ap.add_argument("--diag-tile", type=int, default=None,
                     help="with --profile-only --tile: the diagnostics stage-1 tile variant (default: --tile)")
-    ap.add_argument("--profile-only", nargs="?", const="uniform", default=None, choices=["uniform", "amr", "gw"],
+    ap.add_argument("--profile-only", nargs="?", const="uniform", default=None, choices=["uniform", "amr", "gw", "gw4"],
                     help="short run for ncu captures of a small case, printing nothing: the FP32 uniform form "
-                         "(default), the dynamic-AMR form (base --cells^3, --steps coarse steps) or the "
-                         "16-field lattice")
+                         "(default), the dynamic-AMR form (base --cells^3, --steps coarse steps), the "
+                         "16-field lattice or the BF16 16-field hierarchy (base --cells^3)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

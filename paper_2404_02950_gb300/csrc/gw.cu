@@ -591,8 +591,8 @@ static slh_status gw_stage_t(slh_ctx* c, Level& L, const slh_eom_params& p, cons
   if constexpr (sizeof(T) == 4) {
     if (c->prec == SLH_F32_BF16) {
       // BF16 tensor storage: SSPRK3 only (three level buffers)
-      if (!s.ssp) return fail(SLH_ERR_INVALID_ARG, "BF16 tensor storage runs SSPRK3 only");
       if (s.dry) return SLH_OK;
+      if (!s.ssp) return fail(SLH_ERR_INVALID_ARG, "BF16 tensor storage runs SSPRK3 only");
       const dim3 block(COL_TX, COL_TY);
       switch (p.lap_order) {
         case 2: gw_bf16_kernel<1><<<L.ncol_items, block, 0, c->stream>>>(A); break;

@@ -705,34 +705,26 @@ __global__ void __launch_bounds__(Geo<T, G, TX, TY, P, DIAG>::NTHREADS, (DIAG &&
         w |= (unsigned long long)((bs[slot][dir][sr >> 5] >> (sr & 31)) & 1u) << 33;
         return w;
       };
-      // masks and tag words are spread over the warps (warp w owns row w, and
-      // warp 0 also owner row -1), so that no warp carries a long serial
-      // chain into the next barrier: lanes 0-2 of a warp compute the three
-      // orientations of its row, lanes 3-5 of warp 0 those of row -1
       auto masks = [&](int pm) {
-        const int o = lane < 3 ? lane : lane - 3;
-        if (!(lane < 3 || (warp == 0 && lane < 6))) return;
-        const int r = lane < 3 ? warp + 1 : 0;   // owner row r - 1
-        const int s0 = pm & 3, s1 = (pm + 1) & 3;
-        // W = T0 ^ (T1 >> sh) ^ T2 ^ T3 (edge words; X = bit shift, Y = next
-        // row, Z = next plane):  xy: C.ex X.ey Y.ex C.ey;  yz: C.ey Y.ez Z.ey
-        // C.ez;  zx: C.ez X.ez Z.ex C.ex
-        const int d0 = o, d1 = o == 0 ? 1 : 2, d2 = o == 1 ? 1 : 0, d3 = o == 0 ? 1 : (o == 1 ? 2 : 0);
-        const unsigned long long t0 = row_word(s0, d0, r);
-        const unsigned long long t1 = row_word(s0, d1, o == 1 ? r + 1 : r);
-        const unsigned long long t2 = row_word(o == 0 ? s0 : s1, d2, o == 0 ? r + 1 : r);
-        const unsigned long long t3 = row_word(s0, d3, r);
+        if (warp != 0 || lane > TY) return;
+        const int s0 = pm & 3, s1 = (pm + 1) & 3, r = lane;   // owner row r - 1
+        const unsigned long long ex = row_word(s0, 0, r), ey = row_word(s0, 1, r), ez = row_word(s0, 2, r);
+        const unsigned long long exY = row_word(s0, 0, r + 1), ezY = row_word(s0, 2, r + 1);
+        const unsigned long long exZ = row_word(s1, 0, r), eyZ = row_word(s1, 1, r);
         constexpr unsigned long long OWN = (1ull << (TX + 1)) - 1;   // owners x = -1 .. TX-1
-        mw[pm & 3][o][r] = (t0 ^ (t1 >> (o == 1 ? 0 : 1)) ^ t2 ^ t3) & OWN;
+        // xy: C.ex X.ey Y.ex C.ey;  yz: C.ey Y.ez Z.ey C.ez;  zx: C.ez Z.ex X.ez C.ex
+        mw[pm & 3][0][r] = (ex ^ (ey >> 1) ^ exY ^ ey) & OWN;
+        mw[pm & 3][1][r] = (ey ^ ezY ^ eyZ ^ ez) & OWN;
+        mw[pm & 3][2][r] = (ez ^ exZ ^ (ez >> 1) ^ ex) & OWN;
       };
       auto words = [&](int pt) {
-        if (lane != 0) return;
-        const int a = pt & 3, b = (pt - 1) & 3, r = warp + 1, rm = warp;   // owner rows y and y-1
+        if (warp != 1 || lane >= TY) return;
+        const int a = pt & 3, b = (pt - 1) & 3, r = lane + 1, rm = lane;   // owner rows y and y-1
         const unsigned long long xy0 = mw[a][0][r], xy1 = mw[a][0][rm], zx0 = mw[a][2][r], zx1 = mw[b][2][r];
         const unsigned long long tg = xy0 | (xy0 << 1) | xy1 | (xy1 << 1) | mw[a][1][r] | mw[a][1][rm] | mw[b][1][r] |
                                       mw[b][1][rm] | zx0 | (zx0 << 1) | zx1 | (zx1 << 1);
-        tw[pt & 1][warp] = tg;
-        const int yv = cc.y0 + warp;
+        tw[pt & 1][lane] = tg;
+        const int yv = cc.y0 + lane;
         if (yv >= B.n[1]) return;
         const int nx = min(TX, B.n[0] - cc.x0);
         unsigned long long valid = ((1ull << nx) - 1) << 1;
