@@ -753,12 +753,9 @@ __global__ void regrid_fill_kernel(const RegridFillArgs<T> A) {
     const int cx = gx & 1, cy = gy & 1, cz = gz & 1;
     const int rad = A.itype == 4 ? 2 : (A.itype == 2 ? 1 : 0);
     bool bad = false;
-    // fields in groups of four (one stencil walk per group): four slots of
-    // one field each, or two slots of two BF16 fields each
-    for (int c0 = 0; c0 < A.ncomp;) {
-      const bool pk = c0 >= A.nscalar;
-      const int nsl = pk ? min(2, A.ncomp - c0) : NCOMP;   // slots of this group
-      double acc[NCOMP] = {0.0, 0.0, 0.0, 0.0};
+    // one stencil walk per group of four values: four slots of one field
+    // each, then (SLH_F32_BF16) two slots of two BF16 fields each
+    auto walk = [&](int c0, bool pk, double (&acc)[NCOMP]) {
       for (int oz = -rad; oz <= rad; ++oz) {
         const double wzv = pw(A.itype, cz, oz);
         const int qz = wrapi(Pz + oz, A.cndom);
@@ -776,34 +773,39 @@ __global__ void regrid_fill_kernel(const RegridFillArgs<T> A) {
             const BoxDev C = A.cboxes[cown];
             const long long ci = cell_index(C, A.gl, qx - C.lo[0], qy - C.lo[1], qz - C.lo[2]) + c0 * C.cs;
             const double wgt = wzv * wyv * wxv;
-            if constexpr (sizeof(T) == 4) {
-              if (pk) {
-                for (int k = 0; k < nsl; ++k) {
-                  const float v = A.cy[ci + k * C.cs];
-                  acc[2 * k] += wgt * (double)bf16_half(v, 0);
-                  acc[2 * k + 1] += wgt * (double)bf16_half(v, 1);
-                }
-                continue;
-              }
-            }
+            if (pk) {
+              const float v0 = (float)A.cy[ci], v1 = (float)A.cy[ci + C.cs];
+              acc[0] += wgt * (double)bf16_half(v0, 0);
+              acc[1] += wgt * (double)bf16_half(v0, 1);
+              acc[2] += wgt * (double)bf16_half(v1, 0);
+              acc[3] += wgt * (double)bf16_half(v1, 1);
+            } else {
 #pragma unroll
-            for (int c = 0; c < NCOMP; ++c) acc[c] += wgt * (double)A.cy[ci + c * C.cs];
+              for (int c = 0; c < NCOMP; ++c) acc[c] += wgt * (double)A.cy[ci + c * C.cs];
+            }
           }
         }
       }
-      if constexpr (sizeof(T) == 4) {
-        if (pk) {
-          for (int k = 0; k < nsl; ++k) A.ny[dst + (c0 + k) * B.cs] = bf16_pack((float)acc[2 * k], (float)acc[2 * k + 1]);
-          c0 += nsl;
-          continue;
-        }
-      }
+    };
+#pragma unroll 1
+    for (int c0 = 0; c0 < A.nscalar; c0 += NCOMP) {
+      double acc[NCOMP] = {0.0, 0.0, 0.0, 0.0};
+      walk(c0, false, acc);
 #pragma unroll
       for (int c = 0; c < NCOMP; ++c) {
         A.ny[dst + (c0 + c) * B.cs] = (T)acc[c];
         if (A.nc) A.nc[dst + (c0 + c) * B.cs] = (T)0;
       }
-      c0 += NCOMP;
+    }
+    if constexpr (sizeof(T) == 4) {
+      // packed slots come in pairs (SLH_SLOTS_BF16 - 4 = 6)
+#pragma unroll 1
+      for (int c0 = A.nscalar; c0 + 1 < A.ncomp; c0 += 2) {
+        double acc[NCOMP] = {0.0, 0.0, 0.0, 0.0};
+        walk(c0, true, acc);
+        A.ny[dst + c0 * B.cs] = bf16_pack((float)acc[0], (float)acc[1]);
+        A.ny[dst + (c0 + 1) * B.cs] = bf16_pack((float)acc[2], (float)acc[3]);
+      }
     }
     if (bad) atomicCAS(A.err, 0, DERR_NESTING);
   }

@@ -242,6 +242,8 @@ slh_status launch_gw_stage(slh_ctx* c, Level& L, const slh_eom_params& p, const 
 slh_status build_gw_tmaps(slh_ctx* c, Level& L, int G, int TX, int TY, ::CUtensorMap_st** out);
 slh_status build_tmaps(slh_ctx* c, Level& L, int G, int TX, int TY, ::CUtensorMap_st** out);
 slh_status launch_stage_rkn(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s, int* ctas_used);
+slh_status launch_stage_diag(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s, int* ctas_used,
+                             bool rkn);
 // Kreiss-Oliger dissipation of the stage input in_buf: out += cout Q, D += cd Q (psi, Pi)
 slh_status launch_ko(slh_ctx* c, Level& L, const slh_eom_params& p, int in_buf, int out_buf, int d_buf, double cout,
                      double cd);

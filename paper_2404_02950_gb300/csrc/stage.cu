@@ -1,8 +1,9 @@
 // Host side of the fused stage kernel (stage_kernel.cuh): tensor maps of the
 // level buffers, the tile variants the autotuners choose among, and the
-// dispatch of a stage launch to its kernel instantiation.  The classic RK4
-// and SSPRK3 instantiations are compiled here, the RKN4 ones in
-// stage_rkn.cu.
+// dispatch of a stage launch to its kernel instantiation.  The plain classic
+// RK4 and SSPRK3 instantiations are compiled here, the plain Nystrom ones in
+// stage_rkn.cu and every diagnostics stage 1 in stage_diag.cu (translation
+// units of their own, compiled in parallel).
 #include <map>
 #include <mutex>
 
@@ -126,13 +127,14 @@ slh_status build_gw_tmaps(slh_ctx* c, Level& L, int G, int TX, int TY, CUtensorM
 // Tile variants (x extent, y extent, pipeline depth) the autotuner chooses
 // among; variant 0 is the default.
 const TileVariant* tile_variants(int prec, int* n) {
-  static const TileVariant f32[] = {{32, 16, 2, 64}, {32, 8, 3, 64}, {32, 16, 3, 128}, {16, 16, 2, 64}};
+  static const TileVariant f32[] = {{32, 16, 2, 64}, {32, 8, 3, 64}, {32, 16, 3, 128}, {16, 16, 2, 64},
+                                    {64, 8, 2, 64}, {32, 8, 3, 128}};
   static const TileVariant f64[] = {{32, 8, 2, 64}, {32, 4, 3, 64}, {16, 8, 2, 64}};
   if (prec == SLH_F64) {
     *n = 3;
     return f64;
   }
-  *n = 4;
+  *n = 6;
   return f32;
 }
 
@@ -140,9 +142,9 @@ const TileVariant* tile_variants(int prec, int* n) {
 // diagnostics tile, every other stage on its plain tile; RKN4 stages run the
 // kernels instantiated in stage_rkn.cu
 slh_status launch_stage(slh_ctx* c, Level& L, const slh_eom_params& p, const StageLaunch& s, int* ctas_used) {
-  if (s.rkn) return launch_stage_rkn(c, L, p, s, ctas_used);
   const bool diag = s.tags != nullptr || s.epart != nullptr;
-  return diag ? launch_tile<true, false>(c, L, p, s, ctas_used) : launch_tile<false, false>(c, L, p, s, ctas_used);
+  if (s.rkn) return diag ? launch_stage_diag(c, L, p, s, ctas_used, true) : launch_stage_rkn(c, L, p, s, ctas_used);
+  return diag ? launch_stage_diag(c, L, p, s, ctas_used, false) : launch_tile<false, false>(c, L, p, s, ctas_used);
 }
 
 void free_tmaps(Level& L) {

