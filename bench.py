@@ -37,6 +37,18 @@ ETA0 = 0.1
 ORDER = 6
 KAHAN_VALUES = 76          # field values moved per cell-update, FP32 + Kahan (fused schedule)
 F64_VALUES = 68            # FP64
+
+
+def fp64_ops_per_cell_update(order):
+    """FP64 pipe operations (an add, a multiply or a fused multiply-add each
+    take one issue slot) per cell-update of the classic RK4 stage kernel,
+    diagnostics excluded: per stage and component, the textbook Laplacian
+    w0-term (1), G pair sums of 6 neighbours (5 adds + 1 FMA each) and the
+    1/dx^2 scale (1); |psi|^2 (2), the potential factor (2) and Pi' for two
+    components (2 each); the stage combine adds 8 per stage."""
+    g = order // 2
+    lap = 2 * (2 + 6 * g)
+    return 4 * (lap + 8) + 4 * 8
 WORKLOAD = ("uniform 512^3 periodic lattice, 6th-order Laplacian, classic RK4, Gaussian init "
             "k_max=pi/(8dx), dx=1/8, dt=dx/4, eta0=0.1, tags+energy fused in stage 1")
 
@@ -490,6 +502,16 @@ def run_ours(args, rank, world, local_rank, dist):
     if args.profile_only == "gw4":
         _c4_form(slh, torch, peak, n=n, K=K, W=W)
         return
+    if args.profile_only == "alu":
+        # FMA issue rates with the clocks sampled over the measurement
+        with ClockSampler(_gpu_index(local_rank)) as clk:
+            fma64 = slh.slh_alu_rate(slh.SLH_F64, 12)
+            fma32 = slh.slh_alu_rate(slh.SLH_F32_KAHAN, 12)
+        print(json.dumps({"fp64_fma_per_s": fma64, "fp64_tflops": 2 * fma64 / 1e12,
+                          "fp32_fma_per_s": fma32, "fp32_tflops": 2 * fma32 / 1e12,
+                          "sms": torch.cuda.get_device_properties(local_rank).multi_processor_count,
+                          "clocks": clk.summary()}), flush=True)
+        return
     y0 = inputs.gaussian_field(n, n / 16.0, seed=rank)
     boxes = [((0, 0, 0), (n - 1, n - 1, n - 1))]
     dense = slh.dense_from_boxes(y0, boxes)
@@ -541,6 +563,9 @@ def run_ours(args, rank, world, local_rank, dist):
     h64.close()
     del h64, st32
     torch.cuda.empty_cache()
+    # the FP64 form's ALU roofline: the device's measured FP64 FMA rate
+    fma64 = slh.slh_alu_rate(slh.SLH_F64, 5)
+    fma32 = slh.slh_alu_rate(slh.SLH_F32_KAHAN, 5)
 
     # dynamic AMR (config 3 workload), FP32 batched and FP64 plain
     amr = None
@@ -630,6 +655,7 @@ def run_ours(args, rank, world, local_rank, dist):
     launches = r32["stage_launches"] + r32["ghost_launches"] + r32["time_launches"]
     achieved = r32["stage_bytes"] / (r32["stage_ms"] / 1e3) / 1e9
     ach64 = r64["stage_bytes"] / (r64["stage_ms"] / 1e3) / 1e9
+    ops64 = fp64_ops_per_cell_update(ORDER) * cells * K / (r64["stage_ms"] / 1e3)
     if rank != 0:
         return
     line = {
@@ -648,7 +674,12 @@ def run_ours(args, rank, world, local_rank, dist):
         "error_vs_f64": err,
         "fp64_plain": {"value": job_value(world, cells, K, ms64), "unit": "cell-updates/s",
                        "ms_per_step": ms64 / K, "stage_achieved_gbs": ach64,
-                       "hbm_frac": ach64 / peak, "alg_bytes_per_cell_update": F64_VALUES * 8},
+                       "hbm_frac": ach64 / peak, "alg_bytes_per_cell_update": F64_VALUES * 8,
+                       "alu_roofline": {"bound": "alu", "achieved": ops64 / 1e12, "peak": fma64 / 1e12,
+                                        "unit": "T FP64 op/s", "frac": ops64 / fma64,
+                                        "ops_per_cell_update": fp64_ops_per_cell_update(ORDER),
+                                        "peak_kind": "measured live (slh_alu_rate: FP64 FMA issue rate)",
+                                        "fp32_fma_per_s": fma32}},
         "stage_share": r32["stage_ms"] / ms,
         "per_stage_ms": {"f32": r32["per_stage_ms"], "f64": r64["per_stage_ms"]},
         "autotune": {"f32": {"chosen": r32["tile_variant"], "ms": r32["tune_ms"],
@@ -689,10 +720,11 @@ def main():
                     help="with --profile-only: use this stage-kernel tile variant instead of autotuning")
     ap.add_argument("--diag-tile", type=int, default=None,
                     help="with --profile-only --tile: the diagnostics stage-1 tile variant (default: --tile)")
-    ap.add_argument("--profile-only", nargs="?", const="uniform", default=None, choices=["uniform", "amr", "gw", "gw4"],
+    ap.add_argument("--profile-only", nargs="?", const="uniform", default=None, choices=["uniform", "amr", "gw", "gw4", "alu"],
                     help="short run for ncu captures of a small case, printing nothing: the FP32 uniform form "
                          "(default), the dynamic-AMR form (base --cells^3, --steps coarse steps), the "
-                         "16-field lattice or the BF16 16-field hierarchy (base --cells^3)")
+                         "16-field lattice or the BF16 16-field hierarchy (base --cells^3); 'alu' prints "
+                         "the device's measured FP64 and FP32 FMA rates with the clocks seen")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -537,6 +537,18 @@ slh_status slh_autotune_diag(slh_ctx* ctx, int32_t lev, const slh_eom_params* p,
 slh_status slh_energy_noalloc(const void* fields_dev, int32_t n, int32_t prec, double dx, double eta,
                               const slh_eom_params* p, double* out_dev, void* stream);
 
+/* Measured FMA issue rate of the current device (the ALU roofline of the
+ * FP64 form, whose ~56 FP64 operations per cell and stage outweigh its
+ * HBM traffic on a part that issues FP64 at a small fraction of its FP32
+ * rate).  prec SLH_F64 (double FMAs) or SLH_F32_KAHAN (float FMAs).  A grid
+ * of 8 CTAs of 256 threads per SM, each thread running 8 independent fma
+ * recurrences, is timed with CUDA events on the legacy default stream, best
+ * of reps (1..100) launches of ~25-65 ms each after one warm-up launch;
+ * *fma_per_s receives fused multiply-adds per second for the whole device
+ * (one FMA = 2 flops).  Synchronises the device; allocates nothing.
+ * Errors: INVALID_ARG, CUDA. */
+slh_status slh_alu_rate(int32_t prec, int32_t reps, double* fma_per_s);
+
 /* Self-test of the bounded-wait path: launches one CTA that waits, for at
  * most `polls` polls (1..2^22), on an mbarrier phase that never completes
  * and latches the timeout exactly as the stage kernel's waits do.  The next

@@ -53,7 +53,7 @@ ABI_SYMBOLS = (
     "slh_autotune", "slh_autotune_diag",
     "slh_energy_noalloc", "slh_regrid_level", "slh_selftest_wait_timeout",
     "slh_set_tagging", "slh_shadow_init", "slh_shadow_compare", "slh_tee_tags", "slh_gw_spectrum",
-    "slh_local_regrid_boxes", "slh_regrid", "slh_level_roles",
+    "slh_local_regrid_boxes", "slh_regrid", "slh_level_roles", "slh_alu_rate",
 )
 
 
@@ -158,6 +158,7 @@ def lib():
         "slh_local_regrid_boxes": (i32, [i32, i32, i32, P(vp), P(slh_box), P(i32), P(slh_box), i32, P(i32)]),
         "slh_regrid": (i32, [vp, P(slh_regrid_params), SLH_LEVEL_ALLOC_FN, vp, P(i32), P(dbl)]),
         "slh_level_roles": (i32, [vp, i32, P(i32)]),
+        "slh_alu_rate": (i32, [i32, i32, P(dbl)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -274,6 +275,15 @@ def slh_energy_noalloc(fields_dev, n, dx, eta, params: EOMParams, out_dev, strea
         _check(lib().slh_energy_noalloc(ctypes.c_void_p(fields_dev.data_ptr()), n, prec, float(dx), float(eta),
                                         ctypes.byref(p), ctypes.c_void_p(out_dev.data_ptr()),
                                         ctypes.c_void_p(st.cuda_stream)))
+
+
+def slh_alu_rate(prec=SLH_F64, reps=5):
+    """Measured fused multiply-adds per second of the current device, FP64
+    (``SLH_F64``) or FP32 (``SLH_F32_KAHAN``): the ALU roofline of the FP64
+    form.  Synchronises the device."""
+    out = ctypes.c_double(0.0)
+    _check(lib().slh_alu_rate(int(prec), int(reps), ctypes.byref(out)))
+    return out.value
 
 
 def _bf16_bits(a):

@@ -21,7 +21,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libslh.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SRCS = ["api.cu", "stage.cu", "stage_rkn.cu", "stage_diag.cu", "gw.cu", "ghost.cu", "tee.cu", "spectrum.cu", "ko.cu", "diag.cu", "noalloc.cu"]
+CUDA_SRCS = ["api.cu", "stage.cu", "stage_rkn.cu", "stage_diag.cu", "gw.cu", "ghost.cu", "tee.cu", "spectrum.cu", "ko.cu", "diag.cu", "noalloc.cu", "alu_rate.cu"]
 CXX_SRCS = ["regrid.cpp", "regrid_policy.cpp"]
 
 
