@@ -543,7 +543,7 @@ slh_status slh_energy_noalloc(const void* fields_dev, int32_t n, int32_t prec, d
  * rate).  prec SLH_F64 (double FMAs) or SLH_F32_KAHAN (float FMAs).  A grid
  * of 8 CTAs of 256 threads per SM, each thread running 8 independent fma
  * recurrences, is timed with CUDA events on the legacy default stream, best
- * of reps (1..100) launches of ~25-65 ms each after one warm-up launch;
+ * of reps (1..100) launches of ~15-80 ms each after one warm-up launch;
  * *fma_per_s receives fused multiply-adds per second for the whole device
  * (one FMA = 2 flops).  Synchronises the device; allocates nothing.
  * Errors: INVALID_ARG, CUDA. */

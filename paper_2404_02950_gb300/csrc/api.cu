@@ -483,10 +483,18 @@ static slh_status plan_ghost_regions(slh_ctx* c, int lev, Level& L, std::vector<
       R->kind = GHOST_MIXED;
     }
   };
-  auto emit = [&](const BoxDev& B, int b, const int glo[3], const int ghi[3]) {
+  // each box is planned on its own (host threads); piece indexes are local
+  // to the box until the plans are joined in box order
+  struct BoxPlan {
+    std::vector<GhostRegion> copies, others;
+    std::vector<PatchPiece> pieces;
+    long long total = 0;
+  };
+  std::vector<BoxPlan> plans(L.lay.boxes.size());
+  auto emit = [&](BoxPlan& bp, const BoxDev& B, int b, const int glo[3], const int ghi[3]) {
     GhostRegion R;
     classify(B, b, glo, ghi, &R);
-    R.p0 = (int)pieces->size();
+    R.p0 = (int)bp.pieces.size();
     R.np = 0;
     R.covered = 0;
     if (lev > 0 && R.kind != GHOST_COPY) {
@@ -495,19 +503,20 @@ static slh_status plan_ghost_regions(slh_ctx* c, int lev, Level& L, std::vector<
         flo[d] = glo[d];
         fhi[d] = ghi[d];
       }
-      R.covered = plan_patch(c->lev[lev - 1], bf, flo, fhi, pieces) ? 1 : 0;
-      R.np = (int)pieces->size() - R.p0;
+      R.covered = plan_patch(c->lev[lev - 1], bf, flo, fhi, &bp.pieces) ? 1 : 0;
+      R.np = (int)bp.pieces.size() - R.p0;
     }
-    (R.kind == GHOST_COPY ? copies : others).push_back(R);
-    *total += (long long)R.ext[0] * R.ext[1] * R.ext[2];
+    (R.kind == GHOST_COPY ? bp.copies : bp.others).push_back(R);
+    bp.total += (long long)R.ext[0] * R.ext[1] * R.ext[2];
   };
   auto same_key = [](const GhostRegion& a, const GhostRegion& b) {
     return a.kind == b.kind && a.kind != GHOST_MIXED && a.src == b.src && a.d[0] == b.d[0] && a.d[1] == b.d[1] &&
            a.d[2] == b.d[2];
   };
-  std::vector<std::pair<int, int>> sx, sy, sz, cut[3];
-  std::vector<GhostRegion> sub;
-  for (size_t b = 0; b < L.lay.boxes.size(); ++b) {
+  parallel_for((int)L.lay.boxes.size(), 4096, [&](int b) {
+    std::vector<std::pair<int, int>> sx, sy, sz, cut[3];
+    std::vector<GhostRegion> sub;
+    BoxPlan& bp = plans[b];
     const BoxDev& B = L.lay.boxes[b];
     const int nn[3] = {B.n[0], B.n[1], B.n[2]};
     // six slabs: (lo, hi) valid-relative, inclusive
@@ -531,7 +540,7 @@ static slh_status plan_ghost_regions(slh_ctx* c, int lev, Level& L, std::vector<
             GhostRegion R;
             classify(B, (int)b, glo, ghi, &R);
             if (R.kind != GHOST_MIXED) {
-              emit(B, (int)b, glo, ghi);
+              emit(bp, B, b, glo, ghi);
               continue;
             }
             // cut at the block boundaries (of the wrapped coordinates)
@@ -582,13 +591,26 @@ static slh_status plan_ghost_regions(slh_ctx* c, int lev, Level& L, std::vector<
                 for (auto& r : runs) {
                   const int l[3] = {cut[0][r.first].first, cut[1][iy].first, cut[2][iz].first};
                   const int h[3] = {cut[0][r.second].second, cut[1][jy].second, cut[2][iz].second};
-                  emit(B, (int)b, l, h);
+                  emit(bp, B, b, l, h);
                 }
                 iy = jy + 1;
               }
             }
           }
     }
+  });
+  for (BoxPlan& bp : plans) {
+    const int off = (int)pieces->size();
+    for (GhostRegion& R : bp.copies) {
+      R.p0 += off;
+      copies.push_back(R);
+    }
+    for (GhostRegion& R : bp.others) {
+      R.p0 += off;
+      others.push_back(R);
+    }
+    pieces->insert(pieces->end(), bp.pieces.begin(), bp.pieces.end());
+    *total += bp.total;
   }
   *ncopy = (int)copies.size();
   out->reserve(copies.size() + others.size());

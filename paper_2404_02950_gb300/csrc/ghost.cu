@@ -699,8 +699,7 @@ namespace slh {
 template <typename T>
 struct RegridFillArgs {
   const BoxDev* nboxes;
-  int nnb;
-  long long nvalid;
+  const int4* items;     // column items (box, x0, y0, z0) of the new level
   T* ny;
   T* nc;                 // new Kahan buffer or null
   const BoxDev* oboxes;  // old level (null: none)
@@ -721,21 +720,34 @@ struct RegridFillArgs {
   int* err;
 };
 
+// One CTA of COL_TX x COL_TY threads per column item of the new level, a
+// thread per cell column (no index division).  Prolonged cells sum the
+// tensor-product stencil in the field precision (FP64 for FP64 levels, FP32
+// otherwise, as the ghost prolongation does; the weights are dyadic and exact
+// in both); where the stencil's coarse footprint lies inside one coarse box
+// it is addressed linearly from one lookup, else cell by cell with the
+// periodic wrap.
 template <typename T>
-__global__ void regrid_fill_kernel(const RegridFillArgs<T> A) {
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < A.nvalid; t += stride) {
-    int lo = 0, hi = A.nnb - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (A.nboxes[mid].voff <= t) lo = mid; else hi = mid - 1;
-    }
-    const BoxDev B = A.nboxes[lo];
-    const long long loc = t - B.voff;
-    const int rx = (int)(loc % B.n[0]);
-    const int ry = (int)((loc / B.n[0]) % B.n[1]);
-    const int rz = (int)(loc / ((long long)B.n[0] * B.n[1]));
-    const int gx = B.lo[0] + rx, gy = B.lo[1] + ry, gz = B.lo[2] + rz;
+__global__ void __launch_bounds__(COL_TX * COL_TY) regrid_fill_kernel(const RegridFillArgs<T> A) {
+  using Acc = T;
+  const int4 it = A.items[blockIdx.x];
+  const BoxDev B = A.nboxes[it.x];
+  const int rx = it.y + threadIdx.x, ry = it.z + threadIdx.y;
+  if (rx >= B.n[0] || ry >= B.n[1]) return;
+  const int z1 = min(it.w + COL_ZLEN, B.n[2]);
+  const int gx = B.lo[0] + rx, gy = B.lo[1] + ry;
+  const int rad = A.itype == 4 ? 2 : (A.itype == 2 ? 1 : 0);
+  const int Px = gx >> 1, Py = gy >> 1, cx = gx & 1, cy = gy & 1;
+  Acc wx[5], wy[5];
+#pragma unroll
+  for (int o = -2; o <= 2; ++o) {
+    wx[o + 2] = (Acc)pw(A.itype, cx, o);
+    wy[o + 2] = (Acc)pw(A.itype, cy, o);
+  }
+  bool bad = false;
+#pragma unroll 1
+  for (int rz = it.w; rz < z1; ++rz) {
+    const int gz = B.lo[2] + rz;
     const long long dst = cell_index(B, A.gl, rx, ry, rz);
     if (A.oboxes != nullptr) {
       const int own = A.obmap[((long long)(gz >> A.bshift) * A.nbd + (gy >> A.bshift)) * A.nbd + (gx >> A.bshift)];
@@ -749,47 +761,73 @@ __global__ void regrid_fill_kernel(const RegridFillArgs<T> A) {
         continue;
       }
     }
-    const int Px = gx >> 1, Py = gy >> 1, Pz = gz >> 1;
-    const int cx = gx & 1, cy = gy & 1, cz = gz & 1;
-    const int rad = A.itype == 4 ? 2 : (A.itype == 2 ? 1 : 0);
-    bool bad = false;
+    const int Pz = gz >> 1, cz = gz & 1;
+    // the coarse box holding the whole footprint, if one does
+    const int own0 = A.cbmap[((long long)(Pz >> A.bshift) * A.cnbd + (Py >> A.bshift)) * A.cnbd + (Px >> A.bshift)];
+    BoxDev C0;
+    bool inside = false;
+    if (own0 >= 0) {
+      C0 = A.cboxes[own0];
+      inside = Px - rad >= C0.lo[0] && Px + rad < C0.lo[0] + C0.n[0] && Py - rad >= C0.lo[1] &&
+               Py + rad < C0.lo[1] + C0.n[1] && Pz - rad >= C0.lo[2] && Pz + rad < C0.lo[2] + C0.n[2];
+    }
     // one stencil walk per group of four values: four slots of one field
-    // each, then (SLH_F32_BF16) two slots of two BF16 fields each
-    auto walk = [&](int c0, bool pk, double (&acc)[NCOMP]) {
+    // each, then (SLH_F32_BF16) two slots of two BF16 fields each; the same
+    // summation order on both paths
+    auto add = [&](const T* q, long long cs, Acc wgt, bool pk, Acc (&acc)[NCOMP]) {
+      if (pk) {
+        const float v0 = (float)q[0], v1 = (float)q[cs];
+        acc[0] += wgt * (Acc)bf16_half(v0, 0);
+        acc[1] += wgt * (Acc)bf16_half(v0, 1);
+        acc[2] += wgt * (Acc)bf16_half(v1, 0);
+        acc[3] += wgt * (Acc)bf16_half(v1, 1);
+      } else {
+#pragma unroll
+        for (int c = 0; c < NCOMP; ++c) acc[c] += wgt * (Acc)q[c * cs];
+      }
+    };
+    auto walk = [&](int c0, bool pk, Acc (&acc)[NCOMP]) {
+      if (inside) {
+        const long long sy = C0.pitch, sz = (long long)C0.pitch * C0.pny;
+        const T* base = A.cy + cell_index(C0, A.gl, Px - C0.lo[0], Py - C0.lo[1], Pz - C0.lo[2]) + c0 * C0.cs;
+#pragma unroll 1
+        for (int oz = -rad; oz <= rad; ++oz) {
+          const Acc wzv = (Acc)pw(A.itype, cz, oz);
+#pragma unroll 1
+          for (int oy = -rad; oy <= rad; ++oy) {
+            const Acc wyz = wzv * wy[oy + 2];
+            const T* rowp = base + oz * sz + oy * sy;
+            for (int ox = -rad; ox <= rad; ++ox) add(rowp + ox, C0.cs, wyz * wx[ox + 2], pk, acc);
+          }
+        }
+        return;
+      }
+#pragma unroll 1
       for (int oz = -rad; oz <= rad; ++oz) {
-        const double wzv = pw(A.itype, cz, oz);
+        const Acc wzv = (Acc)pw(A.itype, cz, oz);
         const int qz = wrapi(Pz + oz, A.cndom);
+#pragma unroll 1
         for (int oy = -rad; oy <= rad; ++oy) {
-          const double wyv = pw(A.itype, cy, oy);
+          const Acc wyz = wzv * wy[oy + 2];
           const int qy = wrapi(Py + oy, A.cndom);
+#pragma unroll 1
           for (int ox = -rad; ox <= rad; ++ox) {
-            const double wxv = pw(A.itype, cx, ox);
             const int qx = wrapi(Px + ox, A.cndom);
             const int cown = A.cbmap[((long long)(qz >> A.bshift) * A.cnbd + (qy >> A.bshift)) * A.cnbd + (qx >> A.bshift)];
             if (cown < 0) {
               bad = true;
               continue;
             }
-            const BoxDev C = A.cboxes[cown];
-            const long long ci = cell_index(C, A.gl, qx - C.lo[0], qy - C.lo[1], qz - C.lo[2]) + c0 * C.cs;
-            const double wgt = wzv * wyv * wxv;
-            if (pk) {
-              const float v0 = (float)A.cy[ci], v1 = (float)A.cy[ci + C.cs];
-              acc[0] += wgt * (double)bf16_half(v0, 0);
-              acc[1] += wgt * (double)bf16_half(v0, 1);
-              acc[2] += wgt * (double)bf16_half(v1, 0);
-              acc[3] += wgt * (double)bf16_half(v1, 1);
-            } else {
-#pragma unroll
-              for (int c = 0; c < NCOMP; ++c) acc[c] += wgt * (double)A.cy[ci + c * C.cs];
-            }
+            const BoxDev& C = A.cboxes[cown];
+            add(A.cy + cell_index(C, A.gl, qx - C.lo[0], qy - C.lo[1], qz - C.lo[2]) + c0 * C.cs, C.cs,
+                wyz * wx[ox + 2], pk, acc);
           }
         }
       }
     };
 #pragma unroll 1
     for (int c0 = 0; c0 < A.nscalar; c0 += NCOMP) {
-      double acc[NCOMP] = {0.0, 0.0, 0.0, 0.0};
+      Acc acc[NCOMP] = {0, 0, 0, 0};
       walk(c0, false, acc);
 #pragma unroll
       for (int c = 0; c < NCOMP; ++c) {
@@ -801,14 +839,14 @@ __global__ void regrid_fill_kernel(const RegridFillArgs<T> A) {
       // packed slots come in pairs (SLH_SLOTS_BF16 - 4 = 6)
 #pragma unroll 1
       for (int c0 = A.nscalar; c0 + 1 < A.ncomp; c0 += 2) {
-        double acc[NCOMP] = {0.0, 0.0, 0.0, 0.0};
+        Acc acc[NCOMP] = {0, 0, 0, 0};
         walk(c0, true, acc);
         A.ny[dst + c0 * B.cs] = bf16_pack((float)acc[0], (float)acc[1]);
         A.ny[dst + (c0 + 1) * B.cs] = bf16_pack((float)acc[2], (float)acc[3]);
       }
     }
-    if (bad) atomicCAS(A.err, 0, DERR_NESTING);
   }
+  if (bad) atomicCAS(A.err, 0, DERR_NESTING);
 }
 
 template <typename T>
@@ -816,8 +854,7 @@ static slh_status regrid_fill_t(slh_ctx* c, int lev, Level& N, Level* O) {
   Level& C = c->lev[lev - 1];
   RegridFillArgs<T> A;
   A.nboxes = N.d_boxes;
-  A.nnb = (int)N.boxes.size();
-  A.nvalid = N.lay.nvalid;
+  A.items = N.d_col_items;
   A.ny = static_cast<T*>(N.buf[N.role_y]);
   A.nc = static_cast<T*>(N.buf[SLH_BUF_C]);
   if (O != nullptr && O->defined) {
@@ -845,12 +882,8 @@ static slh_status regrid_fill_t(slh_ctx* c, int lev, Level& N, Level* O) {
   A.ncomp = c->nslots;
   A.nscalar = c->prec == SLH_F32_BF16 ? NCOMP : c->nslots;
   A.err = c->d_err;
-  const int threads = 256;
-  long long blocks = (A.nvalid + threads - 1) / threads;
-  const long long cap = (long long)c->num_sms * 16;
-  if (blocks > cap) blocks = cap;
-  if (blocks < 1) blocks = 1;
-  regrid_fill_kernel<T><<<(int)blocks, threads, 0, c->stream>>>(A);
+  if (N.ncol_items < 1) return SLH_OK;
+  regrid_fill_kernel<T><<<N.ncol_items, dim3(COL_TX, COL_TY), 0, c->stream>>>(A);
   SLH_CUDA(cudaGetLastError());
   return SLH_OK;
 }

@@ -276,8 +276,7 @@ __global__ void __launch_bounds__(COL_TX * COL_TY, 4) gw_bf16_kernel(const GwArg
       const T* f = in + eu;
       const T uc = __ldg(f);
       const T u0[2] = {bf_lo(uc), bf_hi(uc)};
-      // difference-form Laplacians of both fields of the pair
-      T acc[2] = {0, 0};
+      T acc[2] = {(T)(3.0 * lap_w<G>(0)) * u0[0], (T)(3.0 * lap_w<G>(0)) * u0[1]};
 #pragma unroll
       for (int m = 1; m <= G; ++m) {
         const T w = (T)lap_w<G>(m);
@@ -285,8 +284,8 @@ __global__ void __launch_bounds__(COL_TX * COL_TY, 4) gw_bf16_kernel(const GwArg
 #pragma unroll
         for (int dir = 0; dir < 3; ++dir) {
           const T pv = __ldg(f + m * st[dir]), mv = __ldg(f - m * st[dir]);
-          sm[0] += (bf_lo(pv) - u0[0]) + (bf_lo(mv) - u0[0]);
-          sm[1] += (bf_hi(pv) - u0[1]) + (bf_hi(mv) - u0[1]);
+          sm[0] += bf_lo(pv) + bf_lo(mv);
+          sm[1] += bf_hi(pv) + bf_hi(mv);
         }
         acc[0] += w * sm[0];
         acc[1] += w * sm[1];

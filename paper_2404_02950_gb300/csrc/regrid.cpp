@@ -5,6 +5,8 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstdlib>
+#include <thread>
+#include <utility>
 #include <vector>
 
 #include "slh_internal.cuh"
@@ -21,19 +23,23 @@ struct Grid {
   uint8_t at(int x, int y, int z) const { return v[((size_t)z * ny + y) * nx + x]; }
 };
 
+// index of x + s on a periodic line of n cells (|s| <= n)
+inline int wrap(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
+
 // cube dilation with periodic wrap, one axis at a time
 Grid dilate(const Grid& in, int nbuf) {
   Grid cur = in;
   for (int axis = 0; axis < 3 && nbuf > 0; ++axis) {
     Grid nxt(cur.nx, cur.ny, cur.nz);
     const int n = axis == 0 ? cur.nx : axis == 1 ? cur.ny : cur.nz;
+    const int reach = std::min(nbuf, n);   // a reach of n covers the whole line
     for (int z = 0; z < cur.nz; ++z)
       for (int y = 0; y < cur.ny; ++y)
         for (int x = 0; x < cur.nx; ++x) {
           if (!cur.at(x, y, z)) continue;
-          for (int s = -nbuf; s <= nbuf; ++s) {
+          for (int s = -reach; s <= reach; ++s) {
             int p[3] = {x, y, z};
-            p[axis] = ((p[axis] + s) % n + n) % n;
+            p[axis] = wrap(p[axis] + s, n);
             nxt.at(p[0], p[1], p[2]) = 1;
           }
         }
@@ -42,34 +48,82 @@ Grid dilate(const Grid& in, int nbuf) {
   return cur;
 }
 
-// inclusive 3D prefix sums for O(1) box counts
+// the complement of dilate(complement of in, 1): a cell stays set when it
+// and its two neighbours along each axis in turn are set (periodic wrap).
+// Each pass ANDs whole rows: shifted copies of the row for x, the rows at
+// y -+ 1 for y, the rows of the planes at z -+ 1 for z.
+Grid erode1(Grid cur) {
+  const int nx = cur.nx, ny = cur.ny, nz = cur.nz;
+  Grid nxt(nx, ny, nz);
+  auto row = [&](Grid& g, int y, int z) { return &g.v[((size_t)z * ny + y) * nx]; };
+  for (int axis = 0; axis < 3; ++axis) {
+    parallel_for(nz, (size_t)nx * ny, [&](int z) {
+      for (int y = 0; y < ny; ++y) {
+        const uint8_t* c = row(cur, y, z);
+        uint8_t* o = row(nxt, y, z);
+        if (axis == 0) {
+          if (nx == 1) {
+            o[0] = c[0];
+            continue;
+          }
+          o[0] = (uint8_t)(c[0] & c[1] & c[nx - 1]);
+          for (int x = 1; x < nx - 1; ++x) o[x] = (uint8_t)(c[x] & c[x - 1] & c[x + 1]);
+          o[nx - 1] = (uint8_t)(c[nx - 1] & c[nx - 2] & c[0]);
+        } else {
+          const int n = axis == 1 ? ny : nz, pos = axis == 1 ? y : z;
+          const int lo = pos == 0 ? n - 1 : pos - 1, hi = pos == n - 1 ? 0 : pos + 1;
+          const uint8_t* a = axis == 1 ? row(cur, lo, z) : row(cur, y, lo);
+          const uint8_t* b = axis == 1 ? row(cur, hi, z) : row(cur, y, hi);
+          for (int x = 0; x < nx; ++x) o[x] = (uint8_t)(c[x] & a[x] & b[x]);
+        }
+      }
+    });
+    cur.v.swap(nxt.v);
+  }
+  return cur;
+}
+
+// storage of the two prefix tables, kept between calls so that a regrid does
+// not page in tens of MB of fresh memory each time; 32-bit entries (a block
+// grid holds fewer than 2^31 cells: checked by the caller)
+thread_local std::vector<int32_t> prefix_store[2];
+
 struct Prefix {
   int nx, ny, nz;
-  std::vector<int64_t> s;
+  std::vector<int32_t>& s;
   // one running sum per axis in turn (rows, then columns, then planes):
-  // three streaming passes instead of an eight-term recurrence per cell
-  explicit Prefix(const Grid& g) : nx(g.nx), ny(g.ny), nz(g.nz), s((size_t)(nx + 1) * (ny + 1) * (nz + 1), 0) {
-    for (int z = 0; z < nz; ++z)
+  // three streaming passes instead of an eight-term recurrence per cell; the
+  // first two run per plane, the third per stretch of a plane, in parallel
+  Prefix(const Grid& g, std::vector<int32_t>& store) : nx(g.nx), ny(g.ny), nz(g.nz), s(store) {
+    const size_t plane = (size_t)(nx + 1) * (ny + 1);
+    s.resize(plane * (nz + 1));
+    std::fill(s.begin(), s.begin() + plane, 0);
+    parallel_for(nz, plane, [&](int z) {
+      int32_t* pl = &s[plane * (z + 1)];
+      std::fill(pl, pl + nx + 1, 0);
       for (int y = 0; y < ny; ++y) {
-        int64_t run = 0;
+        int32_t run = 0;
         const uint8_t* row = &g.v[((size_t)z * ny + y) * nx];
-        int64_t* out = &S(1, y + 1, z + 1);
-        for (int x = 0; x < nx; ++x) out[x] = (run += row[x]);
+        int32_t* out = pl + (size_t)(y + 1) * (nx + 1);
+        out[0] = 0;
+        for (int x = 0; x < nx; ++x) out[x + 1] = (run += row[x]);
       }
-    for (int z = 1; z <= nz; ++z)
       for (int y = 2; y <= ny; ++y) {
-        int64_t* cur = &S(1, y, z);
-        const int64_t* prev = &S(1, y - 1, z);
+        int32_t* cur = pl + (size_t)y * (nx + 1) + 1;
+        const int32_t* prev = cur - (nx + 1);
         for (int x = 0; x < nx; ++x) cur[x] += prev[x];
       }
-    const size_t plane = (size_t)(nx + 1) * (ny + 1);
-    for (int z = 2; z <= nz; ++z) {
-      int64_t* cur = &S(0, 0, z);
-      const int64_t* prev = cur - plane;
-      for (size_t i = 0; i < plane; ++i) cur[i] += prev[i];
-    }
+    });
+    const int nchunk = (int)std::min<size_t>(64, plane);
+    parallel_for(nchunk, plane / nchunk * nz, [&](int c) {
+      const size_t a = plane * c / nchunk, b = plane * (c + 1) / nchunk;
+      for (int z = 2; z <= nz; ++z) {
+        int32_t* cur = &s[plane * z];
+        const int32_t* prev = cur - plane;
+        for (size_t i = a; i < b; ++i) cur[i] += prev[i];
+      }
+    });
   }
-  int64_t& S(int x, int y, int z) { return s[((size_t)z * (ny + 1) + y) * (nx + 1) + x]; }
   int64_t S(int x, int y, int z) const { return s[((size_t)z * (ny + 1) + y) * (nx + 1) + x]; }
   int64_t count(const int lo[3], const int hi[3]) const {
     const int x0 = lo[0], y0 = lo[1], z0 = lo[2], x1 = hi[0] + 1, y1 = hi[1] + 1, z1 = hi[2] + 1;
@@ -227,15 +281,31 @@ slh_status regrid_boxes_impl(const uint8_t* tags, const int dims[3], int bf, int
   const int r = bf / 2;
   for (int d = 0; d < 3; ++d)
     if (dims[d] <= 0 || dims[d] % r) return fail(SLH_ERR_INVALID_ARG, "regrid: dims must be positive multiples of blocking_factor/2");
-  Grid T(dims[0], dims[1], dims[2]);
-  for (size_t i = 0; i < T.v.size(); ++i) T.v[i] = tags[i] ? 1 : 0;
-  Grid D = dilate(T, nbuf);
   const int bx = dims[0] / r, by = dims[1] / r, bz = dims[2] / r;
+  if ((long long)(bx + 1) * (by + 1) * (bz + 1) >= (1LL << 31))
+    return fail(SLH_ERR_OUT_OF_RANGE, "regrid: %d x %d x %d blocks exceed 2^31", bx, by, bz);
+  const size_t cplane = (size_t)dims[0] * dims[1];
   Grid B(bx, by, bz);
-  for (int z = 0; z < dims[2]; ++z)
-    for (int y = 0; y < dims[1]; ++y)
-      for (int x = 0; x < dims[0]; ++x)
-        if (D.at(x, y, z)) B.at(x / r, y / r, z / r) = 1;
+  if (nbuf == 0) {
+    // no growth: blocks straight from the tags
+    parallel_for(bz, cplane * r, [&](int zb) {
+      for (int z = zb * r; z < (zb + 1) * r; ++z)
+        for (int y = 0; y < dims[1]; ++y) {
+          const uint8_t* row = tags + (size_t)z * cplane + (size_t)y * dims[0];
+          uint8_t* brow = &B.at(0, y / r, zb);
+          for (int x = 0; x < dims[0]; ++x)
+            if (row[x]) brow[x / r] = 1;
+        }
+    });
+  } else {
+    Grid T(dims[0], dims[1], dims[2]);
+    for (size_t i = 0; i < T.v.size(); ++i) T.v[i] = tags[i] ? 1 : 0;
+    Grid D = dilate(T, nbuf);
+    for (int z = 0; z < dims[2]; ++z)
+      for (int y = 0; y < dims[1]; ++y)
+        for (int x = 0; x < dims[0]; ++x)
+          if (D.at(x, y, z)) B.at(x / r, y / r, z / r) = 1;
+  }
   Grid A(bx, by, bz);
   if (parent == nullptr || nparent == 0) {
     std::fill(A.v.begin(), A.v.end(), 1);
@@ -247,20 +317,21 @@ slh_status regrid_boxes_impl(const uint8_t* tags, const int dims[3], int bf, int
         if (pb.lo[d] % r || (pb.hi[d] + 1) % r || pb.lo[d] < 0 || pb.hi[d] >= dims[d] || pb.hi[d] < pb.lo[d])
           return fail(SLH_ERR_INVALID_ARG, "regrid: parent box %d not aligned to blocking_factor/2 or outside dims", i);
       }
-      for (int z = pb.lo[2] / r; z < (pb.hi[2] + 1) / r; ++z)
-        for (int y = pb.lo[1] / r; y < (pb.hi[1] + 1) / r; ++y)
-          for (int x = pb.lo[0] / r; x < (pb.hi[0] + 1) / r; ++x) P.at(x, y, z) = 1;
+      const int x0 = pb.lo[0] / r, x1 = (pb.hi[0] + 1) / r, y0 = pb.lo[1] / r, y1 = (pb.hi[1] + 1) / r,
+                z0 = pb.lo[2] / r, z1 = (pb.hi[2] + 1) / r;
+      for (int z = z0; z < z1; ++z)
+        for (int y = y0; y < y1; ++y) std::fill(&P.at(x0, y, z), &P.at(x0, y, z) + (x1 - x0), (uint8_t)1);
     }
-    Grid notP(bx, by, bz);
-    for (size_t i = 0; i < P.v.size(); ++i) notP.v[i] = P.v[i] ? 0 : 1;
-    Grid G = dilate(notP, 1);
-    for (size_t i = 0; i < G.v.size(); ++i) A.v[i] = G.v[i] ? 0 : 1;
+    A = erode1(std::move(P));
   }
   Grid M(bx, by, bz);
-  for (size_t i = 0; i < M.v.size(); ++i) M.v[i] = (B.v[i] && A.v[i]) ? 1 : 0;
-  Prefix PM(M);
+  const size_t bplane = (size_t)bx * by;
+  parallel_for(bz, bplane, [&](int z) {
+    for (size_t i = z * bplane; i < (z + 1) * bplane; ++i) M.v[i] = (uint8_t)(B.v[i] & A.v[i]);
+  });
+  Prefix PM(M, prefix_store[0]);
   // without a parent every block is allowed: no count of allowed blocks needed
-  const Prefix PA(parent == nullptr || nparent == 0 ? Grid(1, 1, 1) : A);
+  const Prefix PA(parent == nullptr || nparent == 0 ? Grid(1, 1, 1) : A, prefix_store[1]);
   BR br(M, PM, PA, max_box / bf, parent != nullptr && nparent > 0);
   int lo[3] = {0, 0, 0}, hi[3] = {bx - 1, by - 1, bz - 1};
   br.rec(lo, hi);

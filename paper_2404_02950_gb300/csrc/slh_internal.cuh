@@ -4,8 +4,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <map>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "slh.h"
@@ -197,6 +199,29 @@ namespace slh {
 
 // error reporting (thread-local message)
 slh_status fail(slh_status code, const char* fmt, ...);
+
+// Host helper: f(i) for i in [0, n) on up to 16 threads in contiguous chunks
+// (a plain loop below about 64K units of work, work_per_i units per i).
+// Every caller writes disjoint data per i, so results do not depend on the
+// thread count.
+template <typename F>
+void parallel_for(int n, size_t work_per_i, F f) {
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int nt = (int)std::min<size_t>({(size_t)hw, (size_t)16, (size_t)std::max(n, 1), (size_t)n * work_per_i / 65536 + 1});
+  if (nt <= 1) {
+    for (int i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve(nt - 1);
+  auto chunk = [&](int t) {
+    const int a = (int)((long long)n * t / nt), b = (int)((long long)n * (t + 1) / nt);
+    for (int i = a; i < b; ++i) f(i);
+  };
+  for (int t = 1; t < nt; ++t) th.emplace_back(chunk, t);
+  chunk(0);
+  for (std::thread& x : th) x.join();
+}
 slh_status cuda_fail(cudaError_t e, const char* what);
 
 #define SLH_CUDA(call)                                  \

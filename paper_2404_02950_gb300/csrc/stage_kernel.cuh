@@ -684,9 +684,9 @@ __global__ void __launch_bounds__(Geo<T, G, TX, TY, P, DIAG>::NTHREADS, (DIAG &&
       //                 premask step); a warp (one row of 32 cells) packs
       //                 them with ballots, side columns into words of their
       //                 own;
-      //  masks(z-2):    warp 0, one lane per owner row -1..TY-1, from the
+      //  masks(z-2):    the last warp, one lane per owner row -1..TY-1, from the
       //                 edge words of planes z-2 and z-1;
-      //  words(z-3):    warp 1, one lane per row, the tag word (OR of the 12
+      //  words(z-3):    the warp before it, one lane per row, the tag word (OR of the 12
       //                 plaquettes around each cell) from the masks of planes
       //                 z-3 and z-4, with the pierced-plaquette and tag counts;
       //  stores(z-4):   every thread stores its cell's tag byte.
@@ -698,6 +698,10 @@ __global__ void __launch_bounds__(Geo<T, G, TX, TY, P, DIAG>::NTHREADS, (DIAG &&
       __shared__ unsigned long long mw[4][3][TY + 1];    // masks (plane & 3, normal z/x/y, owner row + 1)
       __shared__ unsigned long long tw[2][TY];           // tag words (plane & 1, row)
       const int lane = tid & 31, warp = tid >> 5;
+      // the edge cells beyond one per thread (the last rows and the side
+      // columns) fall to the first warps, so masks and tag words go to the last
+      constexpr int MASK_WARP = TXY / 32 - 1, WORD_WARP = TXY / 32 - 2;
+      static_assert(TXY / 32 >= 3, "bit-sliced winding needs at least 3 warps");
       auto row_word = [&](int slot, int dir, int rr) -> unsigned long long {
         unsigned long long w = (unsigned long long)bw[slot][dir][rr] << 1;
         const int sl = 2 * rr, sr = 2 * rr + 1;
@@ -706,19 +710,28 @@ __global__ void __launch_bounds__(Geo<T, G, TX, TY, P, DIAG>::NTHREADS, (DIAG &&
         return w;
       };
       auto masks = [&](int pm) {
-        if (warp != 0 || lane > TY) return;
-        const int s0 = pm & 3, s1 = (pm + 1) & 3, r = lane;   // owner row r - 1
-        const unsigned long long ex = row_word(s0, 0, r), ey = row_word(s0, 1, r), ez = row_word(s0, 2, r);
-        const unsigned long long exY = row_word(s0, 0, r + 1), ezY = row_word(s0, 2, r + 1);
-        const unsigned long long exZ = row_word(s1, 0, r), eyZ = row_word(s1, 1, r);
+        if (warp != MASK_WARP) return;
+        const int s0 = pm & 3, s1 = (pm + 1) & 3;
         constexpr unsigned long long OWN = (1ull << (TX + 1)) - 1;   // owners x = -1 .. TX-1
+        // one lane per (owner row r - 1, orientation o):
         // xy: C.ex X.ey Y.ex C.ey;  yz: C.ey Y.ez Z.ey C.ez;  zx: C.ez Z.ex X.ez C.ex
-        mw[pm & 3][0][r] = (ex ^ (ey >> 1) ^ exY ^ ey) & OWN;
-        mw[pm & 3][1][r] = (ey ^ ezY ^ eyZ ^ ez) & OWN;
-        mw[pm & 3][2][r] = (ez ^ exZ ^ (ez >> 1) ^ ex) & OWN;
+        for (int idx = lane; idx < 3 * (TY + 1); idx += 32) {
+          const int r = idx / 3, o = idx - 3 * r;
+          unsigned long long m;
+          if (o == 0) {
+            const unsigned long long ex = row_word(s0, 0, r), ey = row_word(s0, 1, r);
+            m = ex ^ (ey >> 1) ^ row_word(s0, 0, r + 1) ^ ey;
+          } else if (o == 1) {
+            m = row_word(s0, 1, r) ^ row_word(s0, 2, r + 1) ^ row_word(s1, 1, r) ^ row_word(s0, 2, r);
+          } else {
+            const unsigned long long ez = row_word(s0, 2, r);
+            m = ez ^ row_word(s1, 0, r) ^ (ez >> 1) ^ row_word(s0, 0, r);
+          }
+          mw[pm & 3][o][r] = m & OWN;
+        }
       };
       auto words = [&](int pt) {
-        if (warp != 1 || lane >= TY) return;
+        if (warp != WORD_WARP || lane >= TY) return;
         const int a = pt & 3, b = (pt - 1) & 3, r = lane + 1, rm = lane;   // owner rows y and y-1
         const unsigned long long xy0 = mw[a][0][r], xy1 = mw[a][0][rm], zx0 = mw[a][2][r], zx1 = mw[b][2][r];
         const unsigned long long tg = xy0 | (xy0 << 1) | xy1 | (xy1 << 1) | mw[a][1][r] | mw[a][1][rm] | mw[b][1][r] |

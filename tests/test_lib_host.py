@@ -173,3 +173,19 @@ def test_local_regrid_matches_oracle(seed):
     norm = lambda L: [[(tuple(int(v) for v in lo), tuple(int(v) for v in hi)) for lo, hi in lb] for lb in L]
     assert norm(got) == norm(exp)
     assert any(len(g) > len(b) for g, b in zip(got, boxes)) or not any(m.any() for m in masks)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_regrid_parents_at_the_periodic_edge_match_oracle(seed):
+    """Parents that touch the domain's faces (the allowed region wraps
+    around), on a grid large enough that the clustering's grid passes run
+    on several host threads."""
+    rng = np.random.default_rng(300 + seed)
+    n = 64
+    tags = _random_tags(rng, n)
+    parent = [((0, 0, 0), (19, 63, 31)), ((44, 0, 0), (63, 63, 31)), ((20, 8, 0), (43, 23, 15)),
+              ((0, 0, 32), (63, 15, 63)), ((8, 40, 40), (55, 63, 63))]
+    for bf, nbuf in ((2, 0), (2, 1), (4, 2)):
+        a = slh.slh_regrid_boxes(tags, bf, nbuf, 4 * bf, parent=parent)
+        b = oregrid.regrid_boxes(tags, bf, nbuf, 4 * bf, parent_boxes=parent)
+        assert a == b, (bf, nbuf)
