@@ -704,9 +704,9 @@ __global__ void __launch_bounds__(Geo<T, G, TX, TY, P, DIAG>::NTHREADS, (DIAG &&
       static_assert(TXY / 32 >= 3, "bit-sliced winding needs at least 3 warps");
       auto row_word = [&](int slot, int dir, int rr) -> unsigned long long {
         unsigned long long w = (unsigned long long)bw[slot][dir][rr] << 1;
-        const int sl = 2 * rr, sr = 2 * rr + 1;
-        w |= (unsigned long long)((bs[slot][dir][sl >> 5] >> (sl & 31)) & 1u);
-        w |= (unsigned long long)((bs[slot][dir][sr >> 5] >> (sr & 31)) & 1u) << 33;
+        // the row's two side bits, 2 rr and 2 rr + 1, share one word
+        const unsigned sw = bs[slot][dir][rr >> 4] >> ((2 * rr) & 31);
+        w |= (unsigned long long)(sw & 1u) | ((unsigned long long)((sw >> 1) & 1u) << 33);
         return w;
       };
       auto masks = [&](int pm) {
