@@ -17,6 +17,7 @@ the CPU FP64 oracle on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import collections
 import hashlib
 import json
 import os
@@ -427,8 +428,13 @@ def _amr_form(slh, torch, prec, y0_dense, K, n=AMR_N, peak=None, relax=AMR_RELAX
         h.advance(DT, p, flags=slh.SLH_USE_GRAPH)
     h.sync()
     h.regrid(AMR_LEVELS, AMR_NBUF, AMR_MAXBOX)
+    tiles = {}
     for lev in sorted(h.levels):
-        h.autotune(lev, p, reps=2)
+        ch, ms_t = h.autotune(lev, p, reps=2)
+        tiles[str(lev)] = {"chosen": ch, "ms": [round(v, 3) for v in ms_t]}
+    # x extents of the refined levels' boxes (the tiles the autotuner weighs them against)
+    widths = {str(lev): {str(w): n for w, n in sorted(collections.Counter(
+        hi[0] - lo[0] + 1 for lo, hi in info["boxes"]).items())} for lev, info in sorted(h.levels.items()) if lev > 0}
     h.advance(DT, p, flags=slh.SLH_USE_GRAPH)   # first capture outside the timed pass
     h.sync()
     h.profile(False, True)                       # clears the host-phase counters
@@ -474,6 +480,7 @@ def _amr_form(slh, torch, prec, y0_dense, K, n=AMR_N, peak=None, relax=AMR_RELAX
                      "capture_ms_per_regrid": round(cap_ms / max(1, ncap), 2),
                      "step_ms_excl_regrid_capture": round((el - regrid_s - cap_ms / 1e3) / K * 1e3, 3)},
            "device_ms_direct": prof, "direct_pass_cell_updates": upd2,
+           "autotune_after_first_regrid": tiles, "box_x_extents_after_first_regrid": widths,
            "stage_kernels": {"achieved_gbs": stage_gbs, "frac": (stage_gbs / peak) if (stage_gbs and peak) else None,
                              "peak": peak},
            "cell_updates": updates, "eta_end": h.get_eta(0)}
