@@ -991,7 +991,25 @@ static slh_status rk_step_impl(slh_ctx* c, int lev, int sub, double dt0, const s
     const double cs = ssp ? cSSP[k] : (rkn5 ? c5[k] : cRK[k]);
     const double alpha = lev > 0 ? (sub + cs) / 2.0 : 1.0;
     prof_begin(c, SLH_PROF_GHOST, (double)L.nghost_cells * ghost_fields(c) * 2 * s);
-    st = launch_ghosts(c, lev, in_role[k], alpha, p.interp_type, ko);
+    if (c->ghost_reuse && lev > 0) {
+      // within one step of the coarser level its old and new states are
+      // fixed, so a fill at a time fraction an earlier fill of this step
+      // used (RK4: stages 2 and 3; the last stage of the first substep and
+      // the first of the second) repeats its prolonged values bit for bit:
+      // copy them from the buffer that holds them
+      if (sub == 0 && k == 0)
+        for (int b = 0; b < SLH_NBUF; ++b) L.gc_key[b] = -1;
+      const int key = (ko ? 8 : 0) | p.interp_type;
+      const int dst = in_role[k];
+      int src = -1;
+      for (int b = 0; b < SLH_NBUF; ++b)
+        if (L.gc_key[b] == key && L.gc_alpha[b] == alpha && (src < 0 || b == dst)) src = b;
+      st = src >= 0 ? launch_ghosts_reuse(c, lev, dst, src, ko) : launch_ghosts(c, lev, dst, alpha, p.interp_type, ko);
+      L.gc_key[dst] = key;
+      L.gc_alpha[dst] = alpha;
+    } else {
+      st = launch_ghosts(c, lev, in_role[k], alpha, p.interp_type, ko);
+    }
     prof_end(c);
     if (st != SLH_OK) return st;
     StageLaunch sl;
@@ -1099,6 +1117,7 @@ slh_status slh_rk_step(slh_ctx* c, int32_t lev, int32_t sub, double dt0, const s
 static slh_status fill_impl(slh_ctx* c, int lev, double alpha, int itype, int mode) {
   NvtxRange range(mode == SLH_RESTRICT ? "slh level %d restrict + ghost fill" : "slh level %d ghost fill", lev);
   Level& L = c->lev[lev];
+  for (int b = 0; b < SLH_NBUF; ++b) L.gc_key[b] = -1;   // the coarser level may have changed
   const size_t s = elem_size(c);
   if (mode == SLH_RESTRICT) {
     prof_begin(c, SLH_PROF_RESTRICT, (double)L.nrcells * c->nslots * 9 * s);
@@ -1154,6 +1173,17 @@ slh_status slh_advance(slh_ctx* c, double dt0, const slh_eom_params* p, uint32_t
   if (c->stale_from < c->nlevels) return fail(SLH_ERR_STATE, "advance: level %d must be regridded first", c->stale_from);
   if (!(dt0 > 0.0)) return fail(SLH_ERR_INVALID_ARG, "advance: dt0 must be positive");
   NvtxRange range("slh coarse step (%d levels)", c->nlevels);
+  // prolonged ghosts are reused only inside one coarse step, whose order of
+  // level steps advance_rec fixes
+  struct ReuseScope {
+    slh_ctx* c;
+    explicit ReuseScope(slh_ctx* cc) : c(cc) {
+      for (int l = 0; l < MAX_LEVELS; ++l)
+        for (int b = 0; b < SLH_NBUF; ++b) c->lev[l].gc_key[b] = -1;
+      c->ghost_reuse = true;
+    }
+    ~ReuseScope() { c->ghost_reuse = false; }
+  } reuse_scope(c);
   if (!(flags & SLH_USE_GRAPH) || c->prof) return advance_rec(c, 0, 0, dt0, *p, flags);
 
   // graph replay: one graph per buffer-role configuration of the levels at

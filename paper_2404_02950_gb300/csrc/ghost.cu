@@ -5,6 +5,8 @@
 // small kernel that advances the per-level conformal time.
 #include <cuda_bf16.h>
 
+#include <cstring>
+
 #include "slh_internal.cuh"
 
 namespace slh {
@@ -460,6 +462,51 @@ __global__ void __launch_bounds__(256, 5) ghost_region_kernel(const GhostArgs<T>
   }
 }
 
+// Prolongation regions [r0, nregions) of a fill whose prolonged values are
+// already known: they are copied cell by cell from buffer ysrc of the same
+// level, which a fill with the same coarse data and time fraction wrote
+// (nothing to copy when ysrc is the buffer itself); cells of mixed regions
+// that a box of the level covers are copied from that box, as the
+// prolongation kernel does.
+template <typename T>
+__global__ void __launch_bounds__(256) ghost_reuse_kernel(const GhostArgs<T> A, const T* __restrict__ ysrc) {
+  const bool same = ysrc == A.y;
+  for (int r = A.r0 + blockIdx.x; r < A.nregions; r += gridDim.x) {
+    const GhostRegion R = A.regions[r];
+    if (same && R.kind != GHOST_MIXED) continue;
+    const BoxDev B = A.boxes[R.box];
+    const int ncell = R.ext[0] * R.ext[1] * R.ext[2];
+    const Split3 sp(R.ext[0], R.ext[1]);
+    for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
+      int i, j, k;
+      sp(t, i, j, k);
+      const int rx = R.lo[0] + i, ry = R.lo[1] + j, rz = R.lo[2] + k;
+      const long long dg = cell_index(B, A.gl, rx, ry, rz);
+      if (R.kind == GHOST_MIXED) {
+        const int gx = B.lo[0] + rx, gy = B.lo[1] + ry, gz = B.lo[2] + rz;
+        const int wx = wrapi(gx, A.ndom), wy = wrapi(gy, A.ndom), wz = wrapi(gz, A.ndom);
+        const int own = A.bmap[((long long)(wz >> A.bshift) * A.nbd + (wy >> A.bshift)) * A.nbd + (wx >> A.bshift)];
+        if (own >= 0) {
+          const BoxDev Sb = A.boxes[own];
+          const long long sg = cell_index(Sb, A.gl, wx - Sb.lo[0], wy - Sb.lo[1], wz - Sb.lo[2]);
+          for (int q = 0; q < A.npairs; ++q) {
+            const int c0 = A.pc[q];
+            A.y[dg + c0 * B.cs] = A.y[sg + c0 * Sb.cs];
+            if (!((A.packed >> q) & 1)) A.y[dg + (c0 + 1) * B.cs] = A.y[sg + (c0 + 1) * Sb.cs];
+          }
+          continue;
+        }
+      }
+      if (same) continue;
+      for (int q = 0; q < A.npairs; ++q) {
+        const int c0 = A.pc[q];
+        A.y[dg + c0 * B.cs] = ysrc[dg + c0 * B.cs];
+        if (!((A.packed >> q) & 1)) A.y[dg + (c0 + 1) * B.cs] = ysrc[dg + (c0 + 1) * B.cs];
+      }
+    }
+  }
+}
+
 template <typename T>
 static slh_status ghosts_t(slh_ctx* c, int lev, int role, double alpha, int itype, bool with_pi) {
   Level& L = c->lev[lev];
@@ -537,6 +584,51 @@ slh_status launch_ghosts(slh_ctx* c, int lev, int role, double alpha, int itype,
     return fail(SLH_ERR_INVALID_ARG, "interp_type must be 0, 2 or 4 (got %d)", itype);
   return c->prec == SLH_F64 ? ghosts_t<double>(c, lev, role, alpha, itype, with_pi)
                             : ghosts_t<float>(c, lev, role, alpha, itype, with_pi);
+}
+
+template <typename T>
+static slh_status ghosts_reuse_t(slh_ctx* c, int lev, int role, int src, bool with_pi) {
+  Level& L = c->lev[lev];
+  if (L.ngregions == 0) return SLH_OK;
+  GhostArgs<T> A;
+  memset(&A, 0, sizeof(A));
+  A.boxes = L.d_boxes;
+  A.regions = L.d_gregions;
+  A.r0 = L.ncopyregions;
+  A.nregions = L.ngregions;
+  A.y = static_cast<T*>(L.buf[role]);
+  A.gl = c->g;
+  A.bmap = L.d_bmap;
+  int sh = 0;
+  while ((1 << sh) < c->bf) ++sh;
+  A.bshift = sh;
+  A.nbd = L.nb_dom;
+  A.ndom = L.n_dom;
+  A.pc[A.npairs++] = 0;
+  if (with_pi) A.pc[A.npairs++] = 2;
+  if (c->ncomp == NCOMP_GW)
+    for (int q = 0; q < 3; ++q) {
+      if (c->prec == SLH_F32_BF16) A.packed |= 1 << A.npairs;
+      A.pc[A.npairs] = c->prec == SLH_F32_BF16 ? SLOT_U0 + q : GW_U0 + 2 * q;
+      ++A.npairs;
+    }
+  A.err = c->d_err;
+  const long long cap = (long long)c->num_sms * 16;
+  if (A.r0 > 0) {
+    ghost_copy_kernel<T><<<(int)std::min<long long>(A.r0, cap), 256, 0, c->stream>>>(A);
+    SLH_CUDA(cudaGetLastError());
+  }
+  if (A.nregions > A.r0) {
+    ghost_reuse_kernel<T><<<(int)std::min<long long>(A.nregions - A.r0, cap), 256, 0, c->stream>>>(
+        A, static_cast<const T*>(L.buf[src]));
+    SLH_CUDA(cudaGetLastError());
+  }
+  return SLH_OK;
+}
+
+slh_status launch_ghosts_reuse(slh_ctx* c, int lev, int role, int src, bool with_pi) {
+  return c->prec == SLH_F64 ? ghosts_reuse_t<double>(c, lev, role, src, with_pi)
+                            : ghosts_reuse_t<float>(c, lev, role, src, with_pi);
 }
 
 // ---------------------------------------------------------------------------

@@ -136,6 +136,12 @@ struct Level {
   int fused_energy_ctas = 0;     // CTAs of the last fused-energy stage 1
   uint8_t* d_tagtmp = nullptr;   // internal tags for slh_tag_blocks
   uint8_t* d_tee = nullptr;      // truncation-error-estimate tags (per valid cell)
+  // Within one step of the coarser level, the prolonged ghost cells a fill
+  // wrote into buffer b (time fraction alpha, key = fields and interpolation
+  // type) stay valid until the coarser level changes: a later fill with the
+  // same alpha copies them instead of prolonging again (slh_advance only).
+  double gc_alpha[SLH_NBUF] = {0, 0, 0, 0, 0};
+  int gc_key[SLH_NBUF] = {-1, -1, -1, -1, -1};   // -1: nothing cached
 };
 
 struct ProfRec {
@@ -168,6 +174,7 @@ struct slh_ctx {
   size_t blockmask_cap = 0;
   // profiling
   bool prof = false;
+  bool ghost_reuse = false;       // set while slh_advance steps the hierarchy
   std::vector<slh::ProfRec> prof_open;
   double prof_ms[SLH_PROF_NKINDS] = {0};
   long long prof_n[SLH_PROF_NKINDS] = {0};
@@ -275,6 +282,10 @@ slh_status launch_ko(slh_ctx* c, Level& L, const slh_eom_params& p, int in_buf, 
 constexpr int COL_TX = 32, COL_TY = 8, COL_ZLEN = 32;
 
 slh_status launch_ghosts(slh_ctx* c, int lev, int role, double alpha, int itype, bool with_pi = false);
+// Ghost fill of buffer `role` whose prolonged cells are copied from buffer
+// `src` of the same level (filled earlier with the same coarse data and time
+// fraction; src == role: they are in place); same-level copies as usual.
+slh_status launch_ghosts_reuse(slh_ctx* c, int lev, int role, int src, bool with_pi = false);
 slh_status launch_restrict(slh_ctx* c, int fine_lev);
 slh_status launch_energy_final(slh_ctx* c, const double* epart, int n, double* out4);
 slh_status launch_tag_blocks(slh_ctx* c, Level& L, const uint8_t* tags, const uint8_t* tags2, int nbuf, int r,

@@ -169,6 +169,38 @@ def test_graph_replay_on_hierarchy_matches_direct():
         assert np.array_equal(ha.get_state(l), hb.get_state(l))
 
 
+@pytest.mark.parametrize("prec,integrator,ko", [("f32", 4, 0), ("f64", 4, 0), ("f32", 10, 0), ("f32", 21, 0),
+                                                 ("f32", 22, 0), ("f32", 4, 3)])
+def test_advance_equals_single_level_steps_bit_for_bit(prec, integrator, ko):
+    """slh_advance copies prolonged ghost values a fill already computed in the
+    same step of the coarser level (same coarse states, same time fraction)
+    instead of prolonging again; the same subcycled order built from single
+    level steps and restrictions, where every fill prolongs afresh, gives the
+    same bits on every level, for each integrator and with dissipation."""
+    p = slh.EOMParams(order=4, interp_type=4, integrator=integrator, friction=integrator != 22,
+                      ko_order=ko, ko_eps=0.02 if ko else 0.0)
+    oh = _oracle_hierarchy(p, 3)
+    a = _gpu_hierarchy(oh, prec=prec)
+    b = _gpu_hierarchy(oh, prec=prec)
+
+    def level_step(lev, sub):
+        b.rk_step(lev, DT0, p, sub=sub)
+        if lev + 1 < 3:
+            for i in range(2):
+                level_step(lev + 1, i)
+            b.fill_ghosts(lev + 1, 1.0, p.interp_type, mode=slh.SLH_RESTRICT)
+
+    for _ in range(2):
+        a.advance(DT0, p)
+        level_step(0, 0)
+    for l in range(3):
+        assert np.array_equal(a.get_state(l), b.get_state(l)), l
+    a.advance(DT0, p, flags=slh.SLH_USE_GRAPH)
+    level_step(0, 0)
+    for l in range(3):
+        assert np.array_equal(a.get_state(l), b.get_state(l)), l
+
+
 def test_nonfinite_coarse_value_is_not_a_nesting_error():
     """A NaN in a covered coarse cell is a field value, not a box-layout
     error: the ghost fill returns OK and carries the NaN into the ghost cells
