@@ -501,7 +501,8 @@ def run_ours(args, rank, world, local_rank, dist):
     if args.profile_only == "amr":
         # short dynamic-AMR run for profilers (base n^3, K coarse steps)
         ya = inputs.gaussian_field(n, n / 8.0, seed=rank)
-        _amr_form(slh, torch, "f32", slh.dense_from_boxes(ya, [((0, 0, 0), (n - 1,) * 3)]), K, n=n, peak=peak)
+        _amr_form(slh, torch, "f32", slh.dense_from_boxes(ya, [((0, 0, 0), (n - 1,) * 3)]), K, n=n, peak=peak,
+                  relax=args.amr_relax)
         return
     if args.profile_only == "gw":
         _gw_form(slh, torch, n, dist, peak, K=K)
@@ -725,6 +726,8 @@ def main():
     ap.add_argument("--no-rkn", action="store_true", help="skip the RKN4 and RKN5 lines")
     ap.add_argument("--tile", type=int, default=None,
                     help="with --profile-only: use this stage-kernel tile variant instead of autotuning")
+    ap.add_argument("--amr-relax", type=int, default=AMR_RELAX,
+                    help="--profile-only amr: coarse steps of the base level before the first regrid")
     ap.add_argument("--diag-tile", type=int, default=None,
                     help="with --profile-only --tile: the diagnostics stage-1 tile variant (default: --tile)")
     ap.add_argument("--profile-only", nargs="?", const="uniform", default=None, choices=["uniform", "amr", "gw", "gw4", "alu"],
