@@ -470,32 +470,69 @@ __global__ void __launch_bounds__(256, 5) ghost_region_kernel(const GhostArgs<T>
 // prolongation kernel does.
 template <typename T>
 __global__ void __launch_bounds__(256) ghost_reuse_kernel(const GhostArgs<T> A, const T* __restrict__ ysrc) {
+  constexpr int CU = 4;
   const bool same = ysrc == A.y;
+  const int tid = threadIdx.x, nt = blockDim.x;
   for (int r = A.r0 + blockIdx.x; r < A.nregions; r += gridDim.x) {
     const GhostRegion R = A.regions[r];
     if (same && R.kind != GHOST_MIXED) continue;
     const BoxDev B = A.boxes[R.box];
     const int ncell = R.ext[0] * R.ext[1] * R.ext[2];
     const Split3 sp(R.ext[0], R.ext[1]);
-    for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
+    if (R.kind != GHOST_MIXED) {
+      // a pure prolongation region: every cell from ysrc, CU cells per
+      // thread in flight (source and destination buffers differ)
+      for (int t0 = tid; t0 < ncell; t0 += CU * nt) {
+        long long dg[CU];
+        bool ok[CU];
+#pragma unroll
+        for (int u = 0; u < CU; ++u) {
+          const int t = t0 + u * nt;
+          ok[u] = t < ncell;
+          int i = 0, j = 0, k = 0;
+          if (ok[u]) sp(t, i, j, k);
+          dg[u] = cell_index(B, A.gl, R.lo[0] + i, R.lo[1] + j, R.lo[2] + k);
+        }
+        for (int q = 0; q < A.npairs; ++q) {
+          const long long o0 = A.pc[q] * B.cs, o1 = o0 + B.cs;
+          const bool two = !((A.packed >> q) & 1);   // a packed pair is one slot
+          T v0[CU], v1[CU];
+#pragma unroll
+          for (int u = 0; u < CU; ++u)
+            if (ok[u]) {
+              v0[u] = ysrc[dg[u] + o0];
+              if (two) v1[u] = ysrc[dg[u] + o1];
+            }
+#pragma unroll
+          for (int u = 0; u < CU; ++u)
+            if (ok[u]) {
+              A.y[dg[u] + o0] = v0[u];
+              if (two) A.y[dg[u] + o1] = v1[u];
+            }
+        }
+      }
+      continue;
+    }
+    for (int t = tid; t < ncell; t += nt) {
       int i, j, k;
       sp(t, i, j, k);
       const int rx = R.lo[0] + i, ry = R.lo[1] + j, rz = R.lo[2] + k;
       const long long dg = cell_index(B, A.gl, rx, ry, rz);
-      if (R.kind == GHOST_MIXED) {
-        const int gx = B.lo[0] + rx, gy = B.lo[1] + ry, gz = B.lo[2] + rz;
-        const int wx = wrapi(gx, A.ndom), wy = wrapi(gy, A.ndom), wz = wrapi(gz, A.ndom);
-        const int own = A.bmap[((long long)(wz >> A.bshift) * A.nbd + (wy >> A.bshift)) * A.nbd + (wx >> A.bshift)];
-        if (own >= 0) {
-          const BoxDev Sb = A.boxes[own];
-          const long long sg = cell_index(Sb, A.gl, wx - Sb.lo[0], wy - Sb.lo[1], wz - Sb.lo[2]);
-          for (int q = 0; q < A.npairs; ++q) {
-            const int c0 = A.pc[q];
-            A.y[dg + c0 * B.cs] = A.y[sg + c0 * Sb.cs];
-            if (!((A.packed >> q) & 1)) A.y[dg + (c0 + 1) * B.cs] = A.y[sg + (c0 + 1) * Sb.cs];
-          }
-          continue;
+      const int gx = B.lo[0] + rx, gy = B.lo[1] + ry, gz = B.lo[2] + rz;
+      const int wx = wrapi(gx, A.ndom), wy = wrapi(gy, A.ndom), wz = wrapi(gz, A.ndom);
+      const int own = A.bmap[((long long)(wz >> A.bshift) * A.nbd + (wy >> A.bshift)) * A.nbd + (wx >> A.bshift)];
+      const T* src;
+      long long sg;
+      if (own >= 0) {   // a box of the level covers the cell: its current value
+        const BoxDev& Sb = A.boxes[own];
+        src = A.y;
+        sg = cell_index(Sb, A.gl, wx - Sb.lo[0], wy - Sb.lo[1], wz - Sb.lo[2]);
+        for (int q = 0; q < A.npairs; ++q) {
+          const int c0 = A.pc[q];
+          A.y[dg + c0 * B.cs] = src[sg + c0 * Sb.cs];
+          if (!((A.packed >> q) & 1)) A.y[dg + (c0 + 1) * B.cs] = src[sg + (c0 + 1) * Sb.cs];
         }
+        continue;
       }
       if (same) continue;
       for (int q = 0; q < A.npairs; ++q) {
