@@ -81,15 +81,52 @@ struct StageArgs {
 // gives delta + 1 (0..2) for N edges at once.
 
 // FP64 inputs: X from two correctly rounded products and one correctly
-// rounded difference, the form the oracle uses.
+// rounded difference, the form the oracle uses.  The sign classes of the
+// four values decide most edges without X, in integer arithmetic on the bit
+// patterns (GB300 issues FP64 at 1/64 of the FP32 rate):
+//  - Im a >= 0 and Im b >= 0, or both < 0: delta = 0 whatever X is;
+//  - the sign of Im changes and Re a, Re b >= 0 (-0 included): the two
+//    rounded products have the signs that make X <= 0 on the way down and
+//    X >= 0 on the way up (rounding keeps signs), so delta = 0;
+//  - the sign of Im changes and Re a, Re b < 0: X > 0 down, X < 0 up, when
+//    neither product underflows to zero, which holds for magnitudes in
+//    [2^-500, 2^501) or zero ("safe" below);
+//  - otherwise (mixed signs of Re, unsafe magnitudes, Inf or NaN) X itself
+//    decides, out of line.
+__device__ __forceinline__ unsigned dclass(double v) {
+  // bit 0: v < 0 (sign bit set, nonzero); bit 1: v is zero or safe
+  const int hi = __double2hiint(v);
+  const unsigned mag = (unsigned)hi & 0x7FFFFFFFu;
+  const bool zero = (mag | (unsigned)__double2loint(v)) == 0u;
+  const bool safe = zero || ((mag >> 20) - 0x20Bu <= 0x3E8u);   // exponent field 0x20B .. 0x5F3
+  return (unsigned)(hi < 0 && !zero) | ((unsigned)safe << 1);
+}
+
+static __device__ __noinline__ unsigned exact_edge_term_f64(double ar, double ai, double br, double bi) {
+  const bool ua = ai >= 0.0, ub = bi >= 0.0;
+  const double X = __dsub_rn(__dmul_rn(ar, bi), __dmul_rn(ai, br));
+  return 1u + (unsigned)(ua && !ub && X > 0.0) - (unsigned)(!ua && ub && X < 0.0);
+}
+
 template <int N>
 __device__ __forceinline__ void edge_terms(const double (&ar)[N], const double (&ai)[N], const double (&br)[N],
                                            const double (&bi)[N], unsigned (&out)[N]) {
+  unsigned need[N], any = 0;
 #pragma unroll
   for (int k = 0; k < N; ++k) {
-    const bool ua = ai[k] >= 0.0, ub = bi[k] >= 0.0;
-    const double X = __dsub_rn(__dmul_rn(ar[k], bi[k]), __dmul_rn(ai[k], br[k]));
-    out[k] = 1u + (unsigned)(ua && !ub && X > 0.0) - (unsigned)(!ua && ub && X < 0.0);
+    const unsigned ca = dclass(ai[k]), cb = dclass(bi[k]), ra = dclass(ar[k]), rb = dclass(br[k]);
+    const unsigned dI = (ca ^ cb) & 1u;                 // the sign of Im changes
+    const unsigned both_neg = ra & rb & 1u;
+    const unsigned safe = (ca & cb & ra & rb) >> 1;
+    const unsigned fast = dI & both_neg;                // +1 down (Im a >= 0), -1 up
+    out[k] = 1u + (fast & ~ca & 1u) - (fast & ca & 1u);
+    need[k] = dI & (((ra ^ rb) & 1u) | (both_neg & ~safe & 1u));
+    any |= need[k];
+  }
+  if (any) {
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+      if (need[k]) out[k] = exact_edge_term_f64(ar[k], ai[k], br[k], bi[k]);
   }
 }
 

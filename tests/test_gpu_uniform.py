@@ -352,7 +352,45 @@ def test_bounded_wait_expiry_is_reported_and_context_survives():
     assert max(rel_l2(g[c], ref[c]) for c in range(4)) <= 1e-5
 
 
-@pytest.mark.parametrize("prec,nvar", [("f32", 4), ("f64", 3)])
+def test_f64_tags_bit_exact_with_extreme_magnitudes():
+    """FP64 winding tags where the sign classes of the values cannot stand in
+    for the sign of X: products that underflow (subnormal and tiny values) or
+    magnitudes outside the range the shortcut trusts, mixed with ordinary
+    values and signed zeros.  On every FP64 diagnostics tile the fused tags of
+    the state and the standalone tags equal the oracle's on the same snapshot."""
+    n, dx = 24, 0.125
+    rng = np.random.default_rng(13)
+    # a smooth field (about one string per few hundred cells) with 12 % of its
+    # values rescaled, signs kept: tiny, subnormal, huge or (signed) zero
+    y = inputs.gaussian_field(n, 3.0, seed=5)
+    p1, p2 = y[0].copy(), y[1].copy()
+    for a in (p1, p2):
+        m = rng.random((n, n, n)) < 0.12
+        f = rng.choice([1e-200, 1e-320, 1e160, 0.0], size=(n, n, n))
+        a[m] = a[m] * f[m]
+    z = np.zeros((n, n, n))
+    y0 = [p1, p2, z, z.copy()]
+    boxes = [((0, 0, 0), (23, 11, 23)), ((0, 12, 0), (23, 23, 23))]
+    p = slh.EOMParams(order=4)
+    for v in range(3):
+        h, _ = uniform_hierarchy(n, dx, prec="f64", nghost=3, bf=4, boxes=boxes, fused_tags=True)
+        h.set_diag_tile(0, v)
+        upload(h, 0, y0, boxes)
+        h.set_eta(0.5)
+        snap = download_domain(h, 0, boxes, n)
+        with np.errstate(all="ignore"):   # X overflows (inf - inf) on some edges, as on the GPU
+            exp = owinding.cell_tags_periodic(snap[0], snap[1])
+        assert 0 < int(exp.sum()) < exp.size
+        t, cnt = h.tag(0)
+        assert np.array_equal(tags_domain(t.cpu().numpy(), boxes, n), exp), v
+        assert cnt == int(exp.sum())
+        with np.errstate(all="ignore"):
+            h.rk_step(0, 0.02, p, flags=slh.SLH_FUSE_TAG)   # the stepped state may overflow; its input's tags count
+        assert np.array_equal(tags_domain(h.fused_tags(0), boxes, n), exp), v
+        h.close()
+
+
+@pytest.mark.parametrize("prec,nvar", [("f32", 6), ("f64", 3)])
 def test_tags_bit_exact_on_ties_signed_zeros_and_near_ties(prec, nvar):
     """Winding tags where the method meets its degenerate cases: values from a
     small set with signed zeros (Im = +-0 counts as upper, X = 0 on many
