@@ -694,6 +694,19 @@ struct RestrictArgs {
   int* err;
 };
 
+// FP32 -> FP64 widening (exact) in integer arithmetic for zeros and normal
+// numbers, which GB300 would otherwise convert on its 1/62-rate FP64 pipe;
+// subnormals, Inf and NaN take the conversion instruction.
+__device__ __forceinline__ double widen(float v) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e - 1u < 254u)   // normal: rebias the exponent, move the 23 fraction bits up by 29
+    return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3)), (int)(u << 29));
+  if ((u & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+  return (double)v;
+}
+__device__ __forceinline__ double widen(double v) { return v; }
+
 template <typename T>
 __global__ void restrict_kernel(const RestrictArgs<T> A) {
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -722,14 +735,14 @@ __global__ void restrict_kernel(const RestrictArgs<T> A) {
     bool hit = false;
     for (int c = 0; c < A.ncomp; ++c) {
       const T* f = A.fy + f000 + c * F.cs;
-      double s = (double)f[0];
-      s += (double)f[1];
-      s += (double)f[sy];
-      s += (double)f[sy + 1];
-      s += (double)f[sz];
-      s += (double)f[sz + 1];
-      s += (double)f[sz + sy];
-      s += (double)f[sz + sy + 1];
+      double s = widen(f[0]);
+      s += widen(f[1]);
+      s += widen(f[sy]);
+      s += widen(f[sy + 1]);
+      s += widen(f[sz]);
+      s += widen(f[sz + 1]);
+      s += widen(f[sz + sy]);
+      s += widen(f[sz + sy + 1]);
       s *= 0.125;
       if (A.tee != nullptr && c < 4 && A.eps[c] > 0.0) hit |= fabs((double)A.cy[dsti + c * C.cs] - s) > A.eps[c];
       A.cy[dsti + c * C.cs] = (T)s;
@@ -741,8 +754,8 @@ __global__ void restrict_kernel(const RestrictArgs<T> A) {
         double s0 = 0.0, s1 = 0.0;
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
-          s0 += (double)bf16_half(f[off[a]], 0);
-          s1 += (double)bf16_half(f[off[a]], 1);
+          s0 += widen(bf16_half(f[off[a]], 0));
+          s1 += widen(bf16_half(f[off[a]], 1));
         }
         A.cy[dsti + c * C.cs] = bf16_pack((float)(s0 * 0.125), (float)(s1 * 0.125));
       }
