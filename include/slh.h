@@ -478,8 +478,11 @@ slh_status slh_reduce_energy(slh_ctx* ctx, const slh_eom_params* p, int32_t mode
 
 /* Stage-kernel tile shape of level lev: variant indexes a fixed table of
  * (x extent, y extent, TMA pipeline depth, z-march length) shapes; 0 is the
- * default.  Sets the tile of every stage, the diagnostics stage 1 (fused
- * tags and energy) included.  Synchronises.
+ * default.  FP32 forms: 32x16/2/64, 32x8/3/64, 32x16/3/128, 16x16/2/64,
+ * 64x8/2/64, 32x8/3/128, 128x4/2/64 (7 variants); FP64: 32x8/2/64,
+ * 32x4/3/64, 16x8/2/64 (3).  The autotuners' ms_out needs one entry per
+ * variant (8 always suffice).  Sets the tile of every stage, the diagnostics
+ * stage 1 (fused tags and energy) included.  Synchronises.
  * Errors: INVALID_ARG, STATE, OUT_OF_RANGE. */
 slh_status slh_set_tile(slh_ctx* ctx, int32_t lev, int32_t variant);
 

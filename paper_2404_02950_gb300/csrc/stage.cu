@@ -128,13 +128,13 @@ slh_status build_gw_tmaps(slh_ctx* c, Level& L, int G, int TX, int TY, CUtensorM
 // among; variant 0 is the default.
 const TileVariant* tile_variants(int prec, int* n) {
   static const TileVariant f32[] = {{32, 16, 2, 64}, {32, 8, 3, 64}, {32, 16, 3, 128}, {16, 16, 2, 64},
-                                    {64, 8, 2, 64}, {32, 8, 3, 128}};
+                                    {64, 8, 2, 64}, {32, 8, 3, 128}, {128, 4, 2, 64}};
   static const TileVariant f64[] = {{32, 8, 2, 64}, {32, 4, 3, 64}, {16, 8, 2, 64}};
   if (prec == SLH_F64) {
     *n = 3;
     return f64;
   }
-  *n = 6;
+  *n = 7;
   return f32;
 }
 

@@ -1191,6 +1191,7 @@ static slh_status launch_tile(slh_ctx* c, Level& L, const slh_eom_params& p, con
     if (v.tx == 32 && v.ty == 16 && v.p == 3) return by_order<float, 32, 16, 3, DIAG, RKN>(c, L, p, s, u);
     if (v.tx == 16 && v.ty == 16 && v.p == 2) return by_order<float, 16, 16, 2, DIAG, RKN>(c, L, p, s, u);
     if (v.tx == 64 && v.ty == 8 && v.p == 2) return by_order<float, 64, 8, 2, DIAG, RKN>(c, L, p, s, u);
+    if (v.tx == 128 && v.ty == 4 && v.p == 2) return by_order<float, 128, 4, 2, DIAG, RKN>(c, L, p, s, u);
   }
   return fail(SLH_ERR_STATE, "no stage kernel for tile %dx%d depth %d", v.tx, v.ty, v.p);
 }

@@ -268,7 +268,7 @@ def test_max_size_1024_f32_sampled():
 
 
 @pytest.mark.parametrize("which", ["both", "diag_only"])
-@pytest.mark.parametrize("prec,nvar", [("f64", 3), ("f32", 6)])
+@pytest.mark.parametrize("prec,nvar", [("f64", 3), ("f32", 7)])
 def test_every_tile_variant_matches_oracle(prec, nvar, which):
     """Each stage-kernel tile shape the autotuner may pick gives the oracle's
     result (ragged 40-cell boxes, 6th order, fused tags in stage 1), set for
@@ -315,7 +315,7 @@ def test_autotune_keeps_state_and_picks_a_variant():
     h.set_eta(0.3)
     before = h.get_state(0)
     chosen, ms = h.autotune(0, p, reps=2)
-    assert 0 <= chosen < len(ms) and len(ms) == 6 and all(m > 0 for m in ms)   # the FP32 tile variants
+    assert 0 <= chosen < len(ms) and len(ms) == 7 and all(m > 0 for m in ms)   # the FP32 tile variants
     assert ms[chosen] == min(ms)
     assert np.array_equal(before, h.get_state(0))
     # the diagnostics stage is tuned on its own; the fused partials it
@@ -324,7 +324,7 @@ def test_autotune_keeps_state_and_picks_a_variant():
     h.reduce_energy(p, mode=1)
     before = h.get_state(0)
     chosen_d, ms_d = h.autotune(0, p, reps=2, diag=True)
-    assert 0 <= chosen_d < len(ms_d) and len(ms_d) == 6 and all(m > 0 for m in ms_d)
+    assert 0 <= chosen_d < len(ms_d) and len(ms_d) == 7 and all(m > 0 for m in ms_d)
     assert ms_d[chosen_d] == min(ms_d)
     assert np.array_equal(before, h.get_state(0))
     with pytest.raises(slh.SlhError) as e:
@@ -390,7 +390,7 @@ def test_f64_tags_bit_exact_with_extreme_magnitudes():
         h.close()
 
 
-@pytest.mark.parametrize("prec,nvar", [("f32", 6), ("f64", 3)])
+@pytest.mark.parametrize("prec,nvar", [("f32", 7), ("f64", 3)])
 def test_tags_bit_exact_on_ties_signed_zeros_and_near_ties(prec, nvar):
     """Winding tags where the method meets its degenerate cases: values from a
     small set with signed zeros (Im = +-0 counts as upper, X = 0 on many
