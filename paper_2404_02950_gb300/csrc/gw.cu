@@ -235,7 +235,7 @@ __device__ __forceinline__ float bf_pack(float lo, float hi) {
 }
 
 template <int G>
-__global__ void __launch_bounds__(COL_TX * COL_TY, 4) gw_bf16_kernel(const GwArgs<float> A) {
+__global__ void __launch_bounds__(COL_TX * COL_TY, 6) gw_bf16_kernel(const GwArgs<float> A) {
   using T = float;
   const int4 it = A.items[blockIdx.x];
   const BoxDev B = A.boxes[it.x];
