@@ -280,7 +280,7 @@ __device__ __forceinline__ void final_pass_any(int ax, const T* src, int sstr, c
 // before writing them (source and destination cells never overlap: the
 // source is valid cells of a box, the destination ghost cells).
 template <typename T>
-__global__ void __launch_bounds__(256) ghost_copy_kernel(const GhostArgs<T> A) {
+__global__ void __launch_bounds__(256, 4) ghost_copy_kernel(const GhostArgs<T> A) {
   constexpr int CU = 4;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int r = blockIdx.x; r < A.r0; r += gridDim.x) {
@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(256, 5) ghost_region_kernel(const GhostArgs<T>
 // that a box of the level covers are copied from that box, as the
 // prolongation kernel does.
 template <typename T>
-__global__ void __launch_bounds__(256) ghost_reuse_kernel(const GhostArgs<T> A, const T* __restrict__ ysrc) {
+__global__ void __launch_bounds__(256, 4) ghost_reuse_kernel(const GhostArgs<T> A, const T* __restrict__ ysrc) {
   constexpr int CU = 4;
   const bool same = ysrc == A.y;
   const int tid = threadIdx.x, nt = blockDim.x;
