@@ -235,7 +235,7 @@ __device__ __forceinline__ float bf_pack(float lo, float hi) {
 }
 
 template <int G>
-__global__ void __launch_bounds__(COL_TX * COL_TY, 6) gw_bf16_kernel(const GwArgs<float> A) {
+__global__ void __launch_bounds__(COL_TX * COL_TY, 4) gw_bf16_kernel(const GwArgs<float> A) {
   using T = float;
   const int4 it = A.items[blockIdx.x];
   const BoxDev B = A.boxes[it.x];
@@ -253,12 +253,22 @@ __global__ void __launch_bounds__(COL_TX * COL_TY, 6) gw_bf16_kernel(const GwArg
   const int stage = A.stage;
   const T sa = (T)A.sa, sb = (T)A.sb;
   long long e = B.off + ((long long)(it.w + A.gl) * B.pny + (y + A.gl)) * B.pitch + x + XPAD;
+  // psi1, psi2 on planes z-G .. z+G of the column, rolled one plane per step
+  // (the z differences of the gradients come from registers)
+  T w1[2 * G + 1], w2[2 * G + 1];
+#pragma unroll
+  for (int k = 0; k < 2 * G; ++k) {
+    w1[k] = __ldg(in + e + (k - G) * sz);
+    w2[k] = __ldg(in + e + cs + (k - G) * sz);
+  }
 #pragma unroll 1
   for (int z = it.w; z < z1; ++z, e += sz) {
+    w1[2 * G] = __ldg(in + e + G * sz);
+    w2[2 * G] = __ldg(in + e + cs + G * sz);
     // gradients of psi1, psi2 (FP32 slots 0 and 1)
     T g1[3], g2[3];
 #pragma unroll
-    for (int dir = 0; dir < 3; ++dir) {
+    for (int dir = 0; dir < 2; ++dir) {
       T a1 = 0, a2 = 0;
 #pragma unroll
       for (int m = 1; m <= G; ++m) {
@@ -269,6 +279,22 @@ __global__ void __launch_bounds__(COL_TX * COL_TY, 6) gw_bf16_kernel(const GwArg
       }
       g1[dir] = a1 * idx;
       g2[dir] = a2 * idx;
+    }
+    {
+      T a1 = 0, a2 = 0;
+#pragma unroll
+      for (int m = 1; m <= G; ++m) {
+        const T w = (T)grad_w<G>(m);
+        a1 += w * (w1[G + m] - w1[G - m]);
+        a2 += w * (w2[G + m] - w2[G - m]);
+      }
+      g1[2] = a1 * idx;
+      g2[2] = a2 * idx;
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * G; ++k) {
+      w1[k] = w1[k + 1];
+      w2[k] = w2[k + 1];
     }
 #pragma unroll 1
     for (int q = 0; q < 3; ++q) {
