@@ -116,7 +116,7 @@ static void free_level(Level& L) {
   cudaFree(L.d_pieces);
   cudaFree(L.d_covered);
   cudaFree(L.d_ritems);
-  cudaFree(L.d_roff);
+  cudaFree(L.d_rchunks);
   cudaFree(L.d_epart);
   cudaFree(L.d_tagtmp);
   cudaFree(L.d_tee);
@@ -676,20 +676,22 @@ static slh_status build_level(slh_ctx* c, int lev, Level& L, const slh_box* boxe
   // restriction items onto lev-1
   if (lev > 0) {
     std::vector<RestrictItem> ri;
-    std::vector<long long> roff;
+    std::vector<int2> chunks;
     long long rt = 0;
     for (int b = 0; b < nboxes; ++b) {
       RestrictItem it;
       it.fbox = b;
       for (int d = 0; d < 3; ++d) it.n[d] = L.lay.boxes[b].n[d] / 2;
+      const int ncell = it.n[0] * it.n[1] * it.n[2];
+      for (int c0 = 0; c0 < ncell; c0 += RESTRICT_CHUNK) chunks.push_back(make_int2((int)ri.size(), c0));
       ri.push_back(it);
-      roff.push_back(rt);
-      rt += (long long)it.n[0] * it.n[1] * it.n[2];
+      rt += ncell;
     }
     L.nritems = (int)ri.size();
+    L.nrchunks = (int)chunks.size();
     L.nrcells = rt;
     if ((st = upload(&L.d_ritems, ri)) != SLH_OK) return st;
-    if ((st = upload(&L.d_roff, roff)) != SLH_OK) return st;
+    if ((st = upload(&L.d_rchunks, chunks)) != SLH_OK) return st;
   }
 
   // truncation-error-estimate tags

@@ -678,9 +678,8 @@ template <typename T>
 struct RestrictArgs {
   const BoxDev* fboxes;
   const RestrictItem* items;
-  const long long* off;
-  int nitems;
-  long long total;
+  const int2* chunks;    // (item, first coarse cell) of each chunk
+  int nchunks;
   const T* fy;
   const BoxDev* cboxes;
   T* cy;
@@ -708,19 +707,17 @@ __device__ __forceinline__ double widen(float v) {
 __device__ __forceinline__ double widen(double v) { return v; }
 
 template <typename T>
-__global__ void restrict_kernel(const RestrictArgs<T> A) {
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < A.total; t += stride) {
-    int lo = 0, hi = A.nitems - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (A.off[mid] <= t) lo = mid; else hi = mid - 1;
-    }
-    const RestrictItem I = A.items[lo];
-    const long long loc = t - A.off[lo];
-    const int i = (int)(loc % I.n[0]);
-    const int j = (int)((loc / I.n[0]) % I.n[1]);
-    const int k = (int)(loc / ((long long)I.n[0] * I.n[1]));
+__global__ void __launch_bounds__(RESTRICT_CHUNK) restrict_kernel(const RestrictArgs<T> A) {
+  // a CTA takes chunks of RESTRICT_CHUNK consecutive coarse cells of one
+  // fine box (x fastest), a thread one cell of the chunk
+  for (int ck = blockIdx.x; ck < A.nchunks; ck += gridDim.x) {
+    const int2 chunk = A.chunks[ck];
+    const RestrictItem I = A.items[chunk.x];
+    const int loc = chunk.y + (int)threadIdx.x;
+    if (loc >= I.n[0] * I.n[1] * I.n[2]) continue;
+    const int i = loc % I.n[0];
+    const int j = (loc / I.n[0]) % I.n[1];
+    const int k = loc / (I.n[0] * I.n[1]);
     const BoxDev F = A.fboxes[I.fbox];
     const int gx = (F.lo[0] >> 1) + i, gy = (F.lo[1] >> 1) + j, gz = (F.lo[2] >> 1) + k;
     const int own = A.cbmap[((long long)(gz >> A.cbshift) * A.cnbd + (gy >> A.cbshift)) * A.cnbd + (gx >> A.cbshift)];
@@ -779,9 +776,8 @@ static slh_status restrict_t(slh_ctx* c, int fl) {
   RestrictArgs<T> A;
   A.fboxes = F.d_boxes;
   A.items = F.d_ritems;
-  A.off = F.d_roff;
-  A.nitems = F.nritems;
-  A.total = F.nrcells;
+  A.chunks = F.d_rchunks;
+  A.nchunks = F.nrchunks;
   A.fy = static_cast<const T*>(F.buf[F.role_y]);
   A.cboxes = C.d_boxes;
   A.cy = static_cast<T*>(C.buf[C.role_y]);
@@ -796,11 +792,8 @@ static slh_status restrict_t(slh_ctx* c, int fl) {
   A.tee = (c->tag_criteria & SLH_TAG_TEE) ? F.d_tee : nullptr;
   for (int q = 0; q < 4; ++q) A.eps[q] = c->te_crit[q];
   A.err = c->d_err;
-  const int threads = 256;
-  long long blocks = (F.nrcells + threads - 1) / threads;
-  const long long cap = (long long)c->num_sms * 8;
-  if (blocks > cap) blocks = cap;
-  restrict_kernel<T><<<(int)blocks, threads, 0, c->stream>>>(A);
+  const int blocks = std::min(F.nrchunks, c->num_sms * 8);
+  restrict_kernel<T><<<blocks, RESTRICT_CHUNK, 0, c->stream>>>(A);
   SLH_CUDA(cudaGetLastError());
   return SLH_OK;
 }

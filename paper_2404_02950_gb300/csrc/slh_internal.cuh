@@ -76,6 +76,7 @@ struct RestrictItem {
   int fbox;
   int n[3];         // coarse extents = fine extents / 2
 };
+constexpr int RESTRICT_CHUNK = 256;   // coarse cells per restriction CTA step
 
 // A stage-kernel tile shape: x and y extent of the CTA's cell column, the
 // TMA pipeline depth (planes in flight) and the z-march length of one item.
@@ -127,9 +128,9 @@ struct Level {
   std::map<unsigned long long, void*> tmaps;   // device tensor maps per (G, TX, TY)
   uint8_t* d_covered = nullptr;  // covered by the finer level, blocks of bf/2 cells
   int ncov = 0;
-  RestrictItem* d_ritems = nullptr;  // restriction of this level onto lev-1
-  long long* d_roff = nullptr;
-  int nritems = 0;
+  RestrictItem* d_ritems = nullptr;  // restriction of this level onto lev-1, per fine box
+  int2* d_rchunks = nullptr;         // (item, first coarse cell) chunks of RESTRICT_CHUNK cells
+  int nritems = 0, nrchunks = 0;
   long long nrcells = 0;
   double* d_epart = nullptr;     // energy partials (per CTA x 4)
   int epart_cap = 0;
